@@ -1,0 +1,109 @@
+"""Pins of the oracle's decoupling and linear solvers (Sec. 3.2 and the
+solver settings of Sec. 4.3) against dense LAPACK solves and the defining
+properties of ILU(0)."""
+import numpy as np
+import pytest
+
+import isc_inputs as inp
+from oracle import linalg, model, sim
+
+
+def _system(case, seed, dt=200.0):
+    st = inp.random_state(case, seed)
+    u0, c0 = sim.initial_state(case)
+    acc_old = model.old_accumulation(case, u0, c0)
+    rp, col, val = model.jacobian(case, st["u"], st["coke"], acc_old, dt)
+    F = model.residual(case, st["u"], st["coke"], acc_old, dt)
+    return rp, col, val, -F.T.copy()
+
+
+def test_gauss_jordan_gives_identity_diagonal_and_equals_inverse_scaling():
+    case = inp.small_box(4, 3, 2)
+    rp, col, val, b = _system(case, 31)
+    vd, bd = linalg.gauss_jordan_decouple(rp, col, val, b)
+    rows = np.repeat(np.arange(case.n), np.diff(rp))
+    diag = col == rows
+    assert np.all(vd[diag] == np.eye(8))
+    Dinv = np.linalg.inv(val[diag])          # LAPACK inverse of every J_ii
+    ref = np.einsum("bij,bjk->bik", Dinv[rows], val)
+    scale = np.abs(ref).reshape(len(ref), -1).max(axis=1)
+    err = np.abs(vd - ref).reshape(len(ref), -1).max(axis=1)
+    assert np.all(err[~diag] <= 1e-11 * np.maximum(scale[~diag], 1.0))
+    assert np.allclose(bd, np.einsum("nij,nj->ni", Dinv, b), rtol=1e-11, atol=1e-11 * np.abs(bd).max())
+
+
+def test_gauss_jordan_pivoting_handles_zero_leading_entry_and_detects_singular():
+    rp = np.array([0, 1])
+    col = np.array([0])
+    A = np.random.default_rng(1).standard_normal((8, 8))
+    A[:, 0] = 0.0
+    A[3, 0] = 2.0                            # only row 3 can pivot column 0
+    b = np.arange(8.0)[None, :]
+    vd, bd = linalg.gauss_jordan_decouple(rp, col, A[None], b)
+    assert np.allclose(bd[0], np.linalg.solve(A, b[0]), rtol=1e-12)
+    A[3, 0] = 0.0
+    with pytest.raises(linalg.SingularBlockError):
+        linalg.gauss_jordan_decouple(rp, col, A[None], b)
+
+
+def test_decoupled_and_original_systems_have_the_same_solution():
+    case = inp.small_box(3, 2, 2)
+    rp, col, val, b = _system(case, 32)
+    x0 = np.linalg.solve(linalg.bsr_to_dense(rp, col, val), b.reshape(-1))
+    vd, bd = linalg.gauss_jordan_decouple(rp, col, val, b)
+    A1 = linalg.bsr_to_dense(rp, col, vd)
+    x1 = np.linalg.solve(A1, bd.reshape(-1))
+    # both are backward-stable solves of the same system: they differ by at
+    # most cond * eps in the variable-scaled norm
+    scale = np.tile(np.array([1e6, 1, 1, 1, 1, 100.0, 1, 1]), case.n)
+    cond = np.linalg.cond(A1 * scale[None, :])
+    d = np.max(np.abs(x1 - x0) / scale) / np.max(np.abs(x0) / scale)
+    assert d <= 100 * cond * 2.2e-16
+
+
+def test_ilu0_is_exact_lu_on_a_tube():
+    # a block-tridiagonal matrix has no fill, so ILU(0) is the exact LU
+    case = inp.tube_case(n_cells=20)
+    rp, col, val, b = _system(case, 33)
+    vd, bd = linalg.gauss_jordan_decouple(rp, col, val, b)
+    M = linalg.ILU0Preconditioner(rp, col, vd)
+    x = M.apply(bd)
+    ref = np.linalg.solve(linalg.bsr_to_dense(rp, col, vd), bd.reshape(-1))
+    assert np.allclose(x.reshape(-1), ref, rtol=1e-10, atol=1e-12 * np.abs(ref).max())
+
+
+def test_ilu0_product_reproduces_matrix_on_its_pattern():
+    # defining property: (L U)_ij = A_ij for every (i, j) in the pattern
+    case = inp.small_box(4, 3, 3)
+    rp, col, val, b = _system(case, 34)
+    vd, _ = linalg.gauss_jordan_decouple(rp, col, val, b)
+    F = linalg.block_ilu0(rp, col, vd)
+    n = case.n
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    L = np.zeros((n * 8, n * 8))
+    U = np.zeros((n * 8, n * 8))
+    for bb in range(len(col)):
+        r, c = rows[bb], col[bb]
+        (L if c < r else U)[r * 8:r * 8 + 8, c * 8:c * 8 + 8] = F[bb]
+    L += np.eye(n * 8)
+    P = L @ U
+    A = linalg.bsr_to_dense(rp, col, vd)
+    for bb in range(len(col)):
+        r, c = rows[bb], col[bb]
+        assert np.allclose(P[r * 8:r * 8 + 8, c * 8:c * 8 + 8], A[r * 8:r * 8 + 8, c * 8:c * 8 + 8], atol=1e-11 * np.abs(A).max())
+
+
+@pytest.mark.parametrize("solver", ["gmres", "bicgstab"])
+@pytest.mark.parametrize("prec", ["ilu0", "bjacobi", "none"])
+def test_krylov_matches_dense_lu(solver, prec):
+    case = inp.small_box(4, 3, 2)      # 192 unknowns
+    rp, col, val, b = _system(case, 35)
+    opts = sim.SolveOptions(solver=solver, prec=prec, rtol=1e-11, maxit=2000, restart=30)
+    x, its, rel = sim.linear_solve(rp, col, val, b, opts)
+    A = linalg.bsr_to_dense(rp, col, val)
+    ref = np.linalg.solve(A, b.reshape(-1))
+    vd, bd = linalg.gauss_jordan_decouple(rp, col, val, b)
+    res = np.linalg.norm(bd.reshape(-1) - linalg.bsr_to_dense(rp, col, vd) @ x.reshape(-1)) / np.linalg.norm(bd)
+    assert res <= 2e-11
+    cond = np.linalg.cond(linalg.bsr_to_dense(rp, col, vd))
+    assert np.linalg.norm(x.reshape(-1) - ref) <= 10 * cond * 1e-11 * np.linalg.norm(ref)

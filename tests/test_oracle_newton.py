@@ -1,0 +1,164 @@
+"""Pins of the oracle's Newton step and time loop: quadratic convergence of
+Newton with the exact Jacobian, invariance of the Newton update under
+Gauss-Jordan decoupling (Sec. 3.2), and a non-reacting water flood against
+the Buckley-Leverett solution."""
+import copy
+
+import numpy as np
+import pytest
+
+import isc_inputs as inp
+from oracle import model, sim
+
+
+def test_newton_converges_quadratically_on_the_tube():
+    case = inp.tube_case()
+    u, coke = sim.initial_state(case)
+    acc_old = model.old_accumulation(case, u, coke)
+    opts = sim.NewtonOptions(tol=1e-13)
+    opts.solve.solver = "dense"
+    norms = []
+    for _ in range(30):
+        r = sim.newton_step(case, u, coke, acc_old, 20.0, opts)
+        norms.append(r["norm"])
+        if r["converged"]:
+            break
+        u = r["u"]
+    # the tail of the sequence shows e_{k+1} ~ C e_k^2 (exact Jacobian)
+    tail = [n for n in norms if 1e-12 < n < 1e-1]
+    assert len(tail) >= 2
+    ratios = [np.log(tail[i + 1]) / np.log(tail[i]) for i in range(len(tail) - 1)]
+    assert max(ratios) > 1.7
+
+
+def test_decoupling_leaves_the_newton_update_unchanged():
+    case = inp.small_box(3, 2, 2)
+    st = inp.random_state(case, 41)
+    u0, c0 = sim.initial_state(case)
+    acc_old = model.old_accumulation(case, u0, c0)
+    o1 = sim.NewtonOptions(tol=0.0)
+    o1.solve.solver = "dense"
+    o1.solve.decouple = True
+    o2 = copy.deepcopy(o1)
+    o2.solve.decouple = False
+    r1 = sim.newton_step(case, st["u"], st["coke"], acc_old, 100.0, o1)
+    r2 = sim.newton_step(case, st["u"], st["coke"], acc_old, 100.0, o2)
+    scale = np.array([1e6, 1, 1, 1, 1, 100.0, 1, 1])[:, None]
+    d = np.max(np.abs(r1["du"] - r2["du"]) / scale) / np.max(np.abs(r2["du"]) / scale)
+    assert d < 1e-9
+
+
+def test_saturation_safeguard_halves_instead_of_going_negative():
+    u = np.array([[5e6], [0.4], [0.2], [0.3], [0.1], [400.0], [0.2], [0.3]])
+    du = np.array([[4e6], [-0.9], [-0.5], [0.1], [0.0], [120.0], [-0.5], [0.1]])
+    un = sim.apply_update(u, du)
+    assert un[0, 0] == pytest.approx(6e6)        # |dp| <= 0.2 p
+    assert un[5, 0] == pytest.approx(450.0)      # |dT| <= 50 K
+    assert un[1, 0] == pytest.approx(0.2)        # x_LO halves
+    assert un[2, 0] == pytest.approx(0.1)        # y_O2 halves
+    assert un[6, 0] == pytest.approx(0.1)        # S_w halves
+    du2 = np.array([[0.0], [0.0], [0.0], [0.0], [0.0], [0.0], [0.2], [0.5]])
+    un2 = sim.apply_update(u, du2)
+    assert 1 - un2[6, 0] - un2[7, 0] == pytest.approx(0.5 * (1 - 0.2 - 0.3))
+
+
+def test_tube_runs_to_two_hours():
+    case = inp.tube_case()
+    opts = sim.NewtonOptions(tol=1e-6)
+    opts.solve.solver = "dense"
+    u, coke, dts, stats = sim.run(case, case.t_end, 5.0, 150.0, opts)
+    assert stats["t"] == pytest.approx(case.t_end)
+    assert 40 <= stats["steps"] <= 80
+    So = 1 - u[6] - u[7]
+    assert np.all(u[6] > 0) and np.all(u[7] > 0) and np.all(So > 0)
+    assert np.all(np.abs(u[2] + u[3] + u[4] - 1) < 1.0)
+
+
+# ------------------------------------------------------------ Buckley-Leverett
+def _waterflood_case(n):
+    case = inp.tube_case(n_cells=n)
+    length = 1.0
+    case.dx = length / n
+    fl = case.fluid
+    fl["cp"] = np.zeros(3)
+    fl["ct1"] = np.zeros(3)
+    fl["kv"] = fl["kv"].copy()
+    fl["kv"][:, 0] = 0.0                 # non-volatile water and oil
+    case.rock["cpor"] = 0.0
+    case.reactions["A"] = np.zeros(4)
+    case.init.update(Sw=0.15, Sg=0.02, So=0.83)
+    case.ignited = np.array([], np.int32)
+    rho_w = fl["rho_ref"][0]
+    q_vol = 1.7e-8                           # m3/s of water
+    k = case.perm[0, 0]
+    area = case.dy * case.dz
+    inj = inp.Well(inp.WELL_RATE_INJECTOR, np.array([0], np.int32), np.array([1.0]), q_vol * rho_w,
+                   np.array([1.0, 0, 0, 0, 0, 0]), 300.0, inj_phase=0)
+    prod = inp.Well(inp.WELL_BHP_PRODUCER, np.array([n - 1], np.int32), np.array([2 * k * area / case.dx]), 5.0e6)
+    case.wells = [inj, prod]
+    return case, q_vol, area
+
+
+def _bl_profile(case, q_vol, area, t, x):
+    fl = case.fluid
+    T = 300.0
+    mu_w = fl["avisc"][0] * np.exp(fl["bvisc"][0] / T)
+    ln_mu_o = 0.744 * np.log(fl["avisc"][1] * np.exp(fl["bvisc"][1] / T)) + 0.256 * np.log(fl["avisc"][2] * np.exp(fl["bvisc"][2] / T))
+    mu_o = np.exp(ln_mu_o)
+    S = np.linspace(0.15, 0.8, 20001)
+    krw, kro, _ = model.rel_perms(fl, S, np.full_like(S, 0.02))
+    fw = (krw / mu_w) / (krw / mu_w + kro / mu_o)
+    dfw = np.gradient(fw, S)
+    swi = 0.15
+    slope = fw / np.maximum(S - swi, 1e-12)
+    i_f = int(np.argmax(np.where(S > swi + 1e-3, slope, 0)))   # Welge tangent point
+    Sf = S[i_f]
+    phi = case.phi_ref[0]
+    xd = q_vol * t / (area * phi)
+    xf = xd * fw[i_f] / (Sf - swi)
+    prof = np.full_like(x, swi)
+    behind = x < xf
+    # rarefaction: dfw/dS (S) = x / xd for S >= Sf
+    Sr = S[i_f:]
+    dr = dfw[i_f:]
+    order = np.argsort(dr)
+    prof[behind] = np.interp(x[behind] / xd, dr[order], Sr[order])
+    return prof, xf, Sf
+
+
+def _flood(n, t_end, steps):
+    case, q_vol, area = _waterflood_case(n)
+    opts = sim.NewtonOptions(tol=1e-8)
+    opts.solve.solver = "gmres"
+    opts.solve.prec = "ilu0"
+    opts.solve.rtol = 1e-12
+    dt = t_end / steps
+    u, coke, dts, stats = sim.run(case, t_end, dt, dt, opts, dts=[dt] * steps)
+    x = (np.arange(n) + 0.5) * case.dx
+    prof, xf, Sf = _bl_profile(case, q_vol, area, t_end, x)
+    return u[6], prof, xf, Sf, case.dx, x
+
+
+def test_waterflood_matches_buckley_leverett():
+    """Front and profile converge to the Buckley-Leverett solution under grid
+    refinement (first-order upwinding smears the shock over a few cells at
+    this oil/water mobility ratio of about 45), and the injected water is
+    all accounted for."""
+    t_end = 1.0e4
+    errs, front = [], []
+    for n in (16, 32, 64):
+        sw, prof, xf, Sf, dx, x = _flood(n, t_end, 2 * n)
+        errs.append(np.mean(np.abs(sw - prof)))
+        mid = 0.5 * (0.15 + Sf)
+        i = int(np.argmax(sw < mid))
+        x_num = x[i - 1] + (mid - sw[i - 1]) / (sw[i] - sw[i - 1]) * dx
+        front.append(abs(x_num - xf))
+        assert 0.4 < xf < 0.8
+        # water balance: injected volume = water gained (incompressible, closed tube)
+        case, q_vol, area = _waterflood_case(n)
+        gained = np.sum(sw - 0.15) * dx * area * case.phi_ref[0]
+        assert gained == pytest.approx(q_vol * t_end, rel=1e-9)
+        if n == 32:
+            assert front[-1] <= 4 * dx
+    assert errs[1] < errs[0] and errs[2] < errs[1]
+    assert front[1] < front[0] and front[2] < front[1]

@@ -1,0 +1,190 @@
+"""Pins of the oracle's property correlations (Sec. 2.2) against values the
+paper prints, textbook physics, closed forms and library routines."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import isc_inputs as inp
+from oracle import model
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "printed_values.json")))
+FL = inp.tube_fluid()
+
+
+def test_water_k_value_is_one_at_boiling_point():
+    g = GOLD["water_K_at_boiling"]
+    K = model.k_value(FL, inp.W, g["p_psi"] * inp.PSI, inp.degF_to_K(g["T_F"]))
+    assert abs(K - g["K"]) <= g["rtol"]
+
+
+def test_k_value_field_units_match_si_conversion():
+    # the correlation in the paper's own units (psi, F) against the SI form
+    for c in range(3):
+        kv1 = [1.7202e6, 1.4546e5, 2.7454e5][c]
+        kv4 = [-6869.59, -4458.73, -8424.83][c]
+        kv5 = [-376.64, -387.78, -205.69][c]
+        for p_psi, T_F in ((100.0, 150.0), (725.2, 300.0), (2014.7, 700.0)):
+            K_field = kv1 / p_psi * np.exp(kv4 / (T_F - kv5))
+            K_si = model.k_value(FL, c, p_psi * inp.PSI, inp.degF_to_K(T_F))
+            assert K_si == pytest.approx(K_field, rel=1e-12)
+
+
+def test_oil_viscosity_at_initial_temperature():
+    g = GOLD["oil_viscosity_initial"]
+    T = inp.degF_to_K(g["T_F"])
+    for c in (inp.LO, inp.HO):
+        mu = FL["avisc"][c] * np.exp(FL["bvisc"][c] / T) / inp.CP
+        assert mu == pytest.approx(g["mu_cp"], rel=g["rtol"])
+    # the oil-phase mixture of two equal-viscosity components keeps that value
+    case = inp.tube_case()
+    u = np.array([[5e6], [0.744], [0.2], [0.7], [0.0], [T], [0.3], [0.1]])
+    bp = model.base_properties(case, u)
+    assert bp["mu_o"][0] / inp.CP == pytest.approx(g["mu_cp"], rel=g["rtol"])
+
+
+def test_water_latent_heat_matches_steam_tables():
+    g = GOLD["water_latent_heat_212F"]
+    Hv = model.vaporisation_enthalpy(FL, inp.W, np.array([inp.degF_to_K(g["T_F"])]))[0]
+    assert Hv / inp.BTU_PER_LBMOL == pytest.approx(g["Hv_btu_per_lbmol"], rel=g["rtol"])
+    # Heaviside: no latent heat above the critical temperature
+    assert model.vaporisation_enthalpy(FL, inp.W, np.array([FL["Tc"][0] + 1.0]))[0] == 0.0
+
+
+def test_gas_enthalpy_derivative_is_heat_capacity():
+    g = GOLD["steam_cp_100F"]
+    T = inp.degF_to_K(g["T_F"])
+    h = 1e-3
+    cp = (model.gas_enthalpy_component(FL, inp.W, T + h) - model.gas_enthalpy_component(FL, inp.W, T - h)) / (2 * h)
+    assert cp / (inp.BTU_PER_LBMOL * 1.8) == pytest.approx(g["cp_btu_per_lbmol_F"], rel=g["rtol"])
+    assert model.gas_enthalpy_component(FL, inp.W, FL["T_ref"]) == 0.0
+
+
+def test_gas_viscosity_nitrogen():
+    g = GOLD["nitrogen_viscosity_100F"]
+    T = inp.degF_to_K(g["T_F"])
+    mu = FL["avg"][inp.N2] * T ** FL["bvg"][inp.N2] / inp.CP
+    assert mu == pytest.approx(g["mu_cp"], rel=g["rtol"])
+
+
+def test_per_factor_values():
+    eps = FL["per_eps"]
+    assert model.per_factor(GOLD["per_half_at_eps"]["s_over_eps"] * eps, eps) == pytest.approx(GOLD["per_half_at_eps"]["f"], rel=1e-15)
+    d = np.imag(model.per_factor(1e-30j, eps)) / 1e-30
+    assert d * eps == pytest.approx(GOLD["per_slope_at_zero"]["fprime_times_eps"], rel=1e-14)
+
+
+def test_printed_stoichiometry_nearly_conserves_mass():
+    g = GOLD["tube_stoichiometry_printed"]
+    for row in g["reactions"]:
+        imb = sum(v * g["M"][k] for k, v in row.items())
+        scale = sum(abs(v) * g["M"][k] for k, v in row.items()) / 2
+        assert abs(imb) / scale <= g["max_rel_imbalance"]
+
+
+def test_build_stoichiometry_conserves_mass_exactly():
+    rx = inp.tube_reactions()
+    M = np.concatenate([FL["M"], [FL["coke_M"]]])
+    NM = rx["stoich"] @ M
+    assert np.all(np.abs(NM) <= 1e-14 * np.abs(rx["stoich"]) @ M)
+
+
+@pytest.mark.parametrize("c", range(6))
+def test_rk_mixing_single_component_reproduces_critical_point(c):
+    # with a pure component the mixing rule must give back its own Tc and pc
+    Tc, pc = FL["Tc"], FL["pc"]
+    a = Tc[c] ** 1.25 / np.sqrt(pc[c])
+    b = Tc[c] / pc[c]
+    Tcm = (a * a / b) ** (2.0 / 3.0)
+    assert Tcm == pytest.approx(Tc[c], rel=1e-13)
+    assert Tcm / b == pytest.approx(pc[c], rel=1e-13)
+    # and the Z factor equals the pure-component RK root from np.roots
+    y = [np.zeros(1) for _ in range(6)]
+    y[c] = np.ones(1)
+    p, T = np.array([3e6]), np.array([500.0])
+    Z = model.z_factor(FL, p, T, y)[0]
+    A = 0.42748 * (p[0] / pc[c]) * (Tc[c] / T[0]) ** 2.5
+    B = 0.08664 * (p[0] / pc[c]) * (Tc[c] / T[0])
+    roots = np.roots([1.0, -1.0, A - B - B * B, -A * B])
+    zr = max(r.real for r in roots if abs(r.imag) < 1e-9 * abs(r))
+    assert Z == pytest.approx(zr, rel=1e-12)
+
+
+def test_z_factor_ideal_gas_limit_and_cubic_residual():
+    rng = np.random.default_rng(3)
+    n = 400
+    y = [rng.uniform(0.0, 1.0, n) for _ in range(6)]
+    s = sum(y)
+    y = [v / s for v in y]
+    T = rng.uniform(280.0, 900.0, n)
+    p = np.full(n, 1.0)
+    assert np.all(np.abs(model.z_factor(FL, p, T, y) - 1.0) < 1e-5)
+    p = rng.uniform(1e5, 2e7, n)
+    Z = model.z_factor(FL, p, T, y)
+    # recompute A, B from the mixing rule and check the cubic and the root choice
+    Tc, pc = FL["Tc"], FL["pc"]
+    a = sum(y[c] * Tc[c] ** 1.25 / np.sqrt(pc[c]) for c in range(6))
+    b = sum(y[c] * Tc[c] / pc[c] for c in range(6))
+    Tcm = (a * a / b) ** (2 / 3)
+    A = 0.42748 * p / (Tcm / b) * (Tcm / T) ** 2.5
+    B = 0.08664 * p / (Tcm / b) * (Tcm / T)
+    res = Z ** 3 - Z ** 2 + (A - B - B * B) * Z - A * B
+    assert np.max(np.abs(res)) < 1e-13
+    for i in range(0, n, 7):
+        roots = np.roots([1.0, -1.0, A[i] - B[i] - B[i] ** 2, -A[i] * B[i]])
+        zr = max(r.real for r in roots if abs(r.imag) <= 1e-7 * max(1.0, abs(r)))
+        assert Z[i] == pytest.approx(zr, rel=1e-9)
+
+
+def test_liquid_density_reference_and_oil_harmonic_mixing():
+    p, T = np.array([FL["p_ref"]]), np.array([FL["T_ref"]])
+    for c in range(3):
+        assert model.liquid_density(FL, c, p, T)[0] == FL["rho_ref"][c]
+    case = inp.tube_case()
+    u = np.array([[FL["p_ref"]], [0.3], [0.2], [0.7], [0.0], [FL["T_ref"]], [0.3], [0.1]])
+    bp = model.base_properties(case, u)
+    v = 0.3 / FL["rho_ref"][1] + 0.7 / FL["rho_ref"][2]
+    assert bp["rho_o"][0] == pytest.approx(1.0 / v, rel=1e-14)
+
+
+def test_stone2_reduces_to_two_phase_curves():
+    # no gas: k_ro equals k_row; water at connate: k_ro equals k_rog
+    Sw = np.linspace(0.15, 0.8, 27)
+    krw, kro, krg = model.rel_perms(FL, Sw, np.zeros_like(Sw))
+    krow = np.clip((1 - Sw - FL["Sorw"]) / (1 - FL["Swc"] - FL["Sorw"]), 0, 1) ** 2
+    assert np.allclose(kro, krow, rtol=0, atol=1e-15)
+    Sg = np.linspace(0.0, 0.6, 25)
+    krw, kro, krg = model.rel_perms(FL, np.full_like(Sg, FL["Swc"]), Sg)
+    krog = np.clip((1 - Sg - FL["Swc"] - FL["Sorg"]) / (1 - FL["Swc"] - FL["Sorg"]), 0, 1) ** 2
+    assert np.allclose(kro, krog, rtol=0, atol=1e-15)
+    assert np.all(krw == 0.0)
+
+
+def test_coke_backward_euler_closed_form_for_coke_oxidation_only():
+    # with cracking switched off, C = C^n / (1 + dt k4 y_O2 p)
+    case = inp.tube_case()
+    case.reactions["A"] = case.reactions["A"].copy()
+    case.reactions["A"][2] = 0.0
+    st = inp.random_state(case, 5)
+    u = st["u"]
+    bp = model.base_properties(case, u)
+    dt = 37.0
+    C = model.solve_coke(case, bp, st["coke"], dt)
+    k4 = case.reactions["A"][3] * np.exp(-case.reactions["Ea"][3] / (model.R_GAS * u[5]))
+    expect = st["coke"] / (1.0 + dt * k4 * u[2] * u[0])
+    assert np.allclose(C, expect, rtol=1e-13, atol=0)
+
+
+def test_coke_solve_satisfies_its_equation():
+    case = inp.tube_case()
+    st = inp.random_state(case, 6)
+    u = st["u"].copy()
+    u[5] = np.linspace(500, 900, case.n)
+    bp = model.base_properties(case, u)
+    dt = 300.0
+    C = model.solve_coke(case, bp, st["coke"], dt)
+    rates = model.reaction_rates(case, bp, C)
+    s = case.reactions["stoich"][:, 6]
+    g = C - st["coke"] - dt * sum(s[r] * rates[r] for r in range(4))
+    assert np.max(np.abs(g) / (np.abs(C) + np.abs(st["coke"]))) < 1e-13
