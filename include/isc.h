@@ -1,0 +1,296 @@
+/*
+ * isc.h -- C ABI of the GB300 in-situ-combustion Newton step library (libisc).
+ *
+ * The library implements the Newton linearise-and-solve step of the fully
+ * implicit FDM in-situ-combustion model of He, Yang, Liu and Chen,
+ * "A New In-Situ Combustion Simulator for Parallel Computers" (arXiv 1811.11992):
+ *   property evaluation (Sec. 2.2), residual and analytical Jacobian on the
+ *   7-point stencil (Sec. 3.1), Gauss-Jordan decoupling (Sec. 3.2) and the
+ *   preconditioned Krylov solve of the resulting block-sparse system.
+ *
+ * Conventions
+ *   - All reals are double, SI units (Pa, K, m, s, mol, J, kg/mol, Pa*s).
+ *   - All indices are int32_t. Cell id = i + nx*(j + ny*k).
+ *   - Components: 0 W, 1 LO, 2 HO, 3 O2, 4 N2, 5 CO2; coke is species 6 in
+ *     stoichiometry rows.
+ *   - Primary unknowns per cell (natural variables of Tab:nco&ncg with x_HO
+ *     and C_c eliminated locally): u = (p, x_LO, y_O2, y_N2, y_CO2, T, S_w, S_g).
+ *   - Equation rows per cell: mass W, LO, HO, O2, N2, CO2, energy, gas
+ *     constraint sum(y) - 1.
+ *   - "SoA state" means u[k*N + cell], k = 0..7.
+ *   - "block-major vector" means v[cell*8 + k].
+ *   - BSR: rowptr[N+1], col[nnzb] sorted per row, val[nnzb*64] with block b
+ *     stored row-major: val[b*64 + r*8 + c] = dF_r(row cell)/du_c(col cell).
+ *   - Host pointers are read during the call and not retained: arrays passed
+ *     to isc_create are copied; the handle owns all device memory it uses.
+ *   - Every function returns ISC_OK (0) or a negative ISC_ERR_* code; no C++
+ *     exception crosses the ABI. After an error the handle stays valid and
+ *     isc_last_error() describes it.
+ *   - All GPU work of a handle is issued on the stream given in isc_options
+ *     (NULL = the legacy default stream); calls that return host data
+ *     synchronise that stream before returning.
+ */
+#ifndef ISC_H
+#define ISC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ISC_NC 6          /* fluid components */
+#define ISC_NU 8          /* unknowns (and equations) per cell */
+#define ISC_MAX_RXN 8
+
+enum isc_status {
+  ISC_OK = 0,
+  ISC_ERR_INVALID_ARG = -1,
+  ISC_ERR_CUDA = -2,
+  ISC_ERR_NOMEM = -3,
+  ISC_ERR_SINGULAR_BLOCK = -4,  /* zero pivot in Gauss-Jordan or ILU(0) */
+  ISC_ERR_KRYLOV_NOCONV = -5,
+  ISC_ERR_NEWTON_NOCONV = -6,
+  ISC_ERR_NONFINITE = -7,
+  ISC_ERR_COKE = -8,            /* per-cell coke equation did not converge */
+  ISC_ERR_TIMEOUT = -9,         /* a bounded device-side wait gave up */
+  ISC_ERR_UNIMPLEMENTED = -10,
+  ISC_ERR_STATE = -11           /* call order violated (e.g. solve before assemble) */
+};
+
+enum isc_krylov { ISC_KRYLOV_GMRES = 0, ISC_KRYLOV_BICGSTAB = 1 };
+enum isc_prec { ISC_PREC_NONE = 0, ISC_PREC_BJACOBI = 1, ISC_PREC_BILU0 = 2 };
+enum isc_rxn_kind {
+  ISC_RXN_OIL_OXIDATION = 0,   /* r = A e^{-Ea/RT} (y_O2 p)(phi_f S_o rho_o x_i)           */
+  ISC_RXN_CRACKING = 1,        /* r = A e^{-Ea/RT} (phi_f S_o rho_o x_i)(1-(C_c/C_max)^5)  */
+  ISC_RXN_COKE_OXIDATION = 2   /* r = A e^{-Ea/RT} (y_O2 p) C_c                            */
+};
+enum isc_well_kind { ISC_WELL_RATE_INJECTOR = 0, ISC_WELL_BHP_PRODUCER = 1 };
+
+/* Cartesian grid (Sec. 3.1). depth: N cell-centre depths in m (increasing
+ * downwards), or NULL for depth = (k + 0.5) dz. */
+typedef struct isc_grid {
+  int32_t nx, ny, nz;
+  double dx, dy, dz;
+  const double* depth;
+} isc_grid;
+
+/* Rock (Sec. 2.2 Porosity, Non-isothermal Description). phi_ref: N values.
+ * perm: 3N values, k_x of all cells, then k_y, then k_z (m^2).
+ * phi = phi_ref (1 + cpor (p-p_ref) - ctpor (T-T_ref) + cptpor (p-p_ref)(T-T_ref)),
+ * U_r = cv1 (T-T_ref) + cv2/2 (T^2 - T_ref^2) in J/m^3, K_rock in W/m/K. */
+typedef struct isc_rock {
+  const double* phi_ref;
+  const double* perm;
+  double cpor, ctpor, cptpor, p_ref, T_ref, cv1, cv2, K_rock;
+} isc_rock;
+
+/* Fluid data (Sec. 2.2), SI, T absolute. Arrays [6] are per component,
+ * arrays [3] are per liquid-capable component (W, LO, HO).
+ *   K-values: K = (kv1/p + kv2 p + kv3) exp(kv4/(T-kv5)), kv[c] = {kv1..kv5}
+ *   liquid density: rho = rho_ref exp(cp dp - ct1 dT - ct2/2 dT^2 + cpt dp dT),
+ *                   dp = p - p_ref, dT = T - T_ref
+ *   gas enthalpy: H_g,c = int_{T_ref}^T sum_k cpg[c][k] t^k dt
+ *   vaporisation: H_v,c = hvr (Tc - T)^ev for T < Tc (Tc from Tc[c]), else 0
+ *   viscosities: mu_c = avisc exp(bvisc/T) (liquids), mu_g,c = avg T^bvg
+ *   Corey endpoints Swc, Sorw, Sgc, Sorg (exponent 2), PER epsilon per_eps. */
+typedef struct isc_fluid {
+  double M[6], pc[6], Tc[6];
+  double rho_ref[3], cp[3], ct1[3], ct2[3], cpt[3];
+  double p_ref, T_ref;
+  double cpg[6][4];
+  double hvr[3], ev[3];
+  double avg[6], bvg[6], avisc[3], bvisc[3];
+  double kv[3][5];
+  double K_phase[3];            /* thermal conductivity of water, oil, gas phases */
+  double coke_rho, coke_cp, coke_K, coke_M;
+  double Swc, Sorw, Sgc, Sorg;
+  double per_eps, gravity;
+} isc_fluid;
+
+/* Reactions (Sec. 2.1 Chemical Reaction, Sec. 2.2 Reaction Model).
+ * stoich[r][0..6]: coefficients of W, LO, HO, O2, N2, CO2, coke (products
+ * positive). comp[r]: the oil component (1 LO or 2 HO) of oxidation/cracking
+ * rates. Validated: |sum_c stoich[r][c] M_c| <= 1e-12 sum_c |stoich[r][c]| M_c
+ * (the paper's N M = 0 check), else ISC_ERR_INVALID_ARG. */
+typedef struct isc_reactions {
+  int32_t nr;
+  int32_t kind[ISC_MAX_RXN];
+  int32_t comp[ISC_MAX_RXN];
+  double stoich[ISC_MAX_RXN][7];
+  double A[ISC_MAX_RXN], Ea[ISC_MAX_RXN], dH[ISC_MAX_RXN];
+  double coke_max;
+} isc_reactions;
+
+/* Wells (Sec. 2.2 Well Modeling). A BHP producer perforation at cell i takes
+ * Q_alpha = WI rho_alpha k_r,alpha/mu_alpha (bhp - p_i) when p_i > bhp (no
+ * cross-flow). A rate injector puts target mol/s of composition inj_y at
+ * T_inj, split over its perforations in proportion to WI; inj_phase 2 carries
+ * gas enthalpy, inj_phase 0 liquid-water enthalpy. A cell may be perforated by
+ * at most one well. */
+typedef struct isc_well {
+  int32_t kind;
+  int32_t n_perf;
+  const int32_t* cells;
+  const double* WI;
+  double target;
+  double inj_y[6];
+  double inj_T;
+  int32_t inj_phase;
+} isc_well;
+
+typedef struct isc_wells {
+  int32_t nw;
+  const isc_well* wells;
+} isc_wells;
+
+/* Solver and Newton options. stream is a cudaStream_t (NULL = default). */
+typedef struct isc_options {
+  int32_t krylov;               /* isc_krylov */
+  int32_t restart;              /* GMRES restart length, 1..64 */
+  int32_t prec;                 /* isc_prec */
+  int32_t decouple;             /* 1: Gauss-Jordan decoupling before the solve */
+  double tol_lin;               /* relative residual of the (decoupled) system */
+  int32_t maxit_lin;
+  double tol_newton;            /* scaled residual norm */
+  int32_t maxit_newton;
+  double max_dp_frac;           /* |dp| <= max_dp_frac p (0.2) */
+  double max_dT;                /* |dT| <= max_dT (50 K) */
+  int32_t profile;              /* 1: record per-kernel CUDA-event times */
+  void* stream;
+} isc_options;
+
+typedef struct isc_newton_info {
+  int32_t status;
+  int32_t converged;            /* 1 if the residual was already below tol (no solve done) */
+  double norm;                  /* scaled residual norm before the step */
+  double norm_mass, norm_energy, norm_gs;
+  int32_t krylov_iterations;
+  double krylov_rel_residual;
+} isc_newton_info;
+
+typedef struct isc_step_info {
+  int32_t status;
+  int32_t newton_iterations;
+  int32_t krylov_iterations;
+  double final_norm;
+} isc_step_info;
+
+/* Per-kernel-class timing (milliseconds, CUDA events on the handle's stream,
+ * accumulated while options.profile = 1) and launch counts. */
+enum isc_kernel_class {
+  ISC_K_PROPS = 0, ISC_K_FLUX = 1, ISC_K_NORM = 2, ISC_K_GJ = 3, ISC_K_ILU_FACTOR = 4,
+  ISC_K_SPMV = 5, ISC_K_PREC_APPLY = 6, ISC_K_BLAS1 = 7, ISC_K_UPDATE = 8, ISC_K_COUNT = 9
+};
+typedef struct isc_stats {
+  double ms[ISC_K_COUNT];
+  int64_t launches[ISC_K_COUNT];
+  int64_t calls[ISC_K_COUNT];   /* timed regions (one region may hold several launches) */
+} isc_stats;
+
+/* ---------------------------------------------------------------- lifecycle */
+
+/* Create a handle: validates the input, precomputes face transmissibilities
+ * (harmonic average of A k/h, Sec. 3.1) and the BSR pattern of the 7-point
+ * stencil (fixed, Sec. 3.1 end), allocates device memory. opts may be NULL
+ * for defaults (GMRES(30), block ILU(0), decoupling on, tol_lin 1e-6,
+ * tol_newton 1e-6). *out receives the handle or NULL on error. */
+int isc_create(const isc_grid* grid, const isc_rock* rock, const isc_fluid* fluid,
+               const isc_reactions* reactions, const isc_wells* wells,
+               const isc_options* opts, struct isc_handle** out);
+void isc_destroy(struct isc_handle* h);
+int isc_set_options(struct isc_handle* h, const isc_options* opts);
+void isc_default_options(isc_options* opts);
+const char* isc_status_string(int status);
+const char* isc_last_error(const struct isc_handle* h);
+int32_t isc_num_cells(const struct isc_handle* h);
+int32_t isc_nnzb(const struct isc_handle* h);
+
+/* ---------------------------------------------------------------- state */
+
+/* Initial-state recipe: uniform p0, T0, S_w0, S_o0 (S_g = 1 - S_w0 - S_o0),
+ * x_LO0; gas y_W = f(S_w)K_W, y_LO = K_LO x_LO, y_HO = f(S_o)K_HO x_HO
+ * (Tab4.4 with eq. PER1/PER2) and the remainder split over O2, N2, CO2 in the
+ * ratios y_rest[3]; n_ignited cells start at T_ignite; C_c = 0. Also makes
+ * this the accepted state of the time step (see isc_begin_step). */
+int isc_init_equilibrium(struct isc_handle* h, double p0, double T0, double Sw0, double So0,
+                         double x_LO0, const double y_rest[3], int32_t n_ignited,
+                         const int32_t* ignited, double T_ignite);
+/* Copy in / out the Newton iterate u (host, SoA 8N) and coke C_c (host, N;
+ * may be NULL on get). set_state does not touch the accepted state. */
+int isc_set_state(struct isc_handle* h, const double* u, const double* coke);
+int isc_get_state(struct isc_handle* h, double* u, double* coke);
+/* Device-pointer variants (SoA 8N and N doubles in device memory), ordered on
+ * the handle's stream, no synchronisation. */
+int isc_set_state_device(struct isc_handle* h, const double* d_u, const double* d_coke);
+int isc_get_state_device(struct isc_handle* h, double* d_u, double* d_coke);
+/* Make the current iterate (u, C_c) the accepted state of time level n: stores
+ * C_c^n and the accumulation N^n, E^n used by the next residuals. */
+int isc_begin_step(struct isc_handle* h);
+
+/* ---------------------------------------------------------------- hot path */
+
+/* Assemble the residual F (Sec. 3.1 discrete equations, outflow positive) and
+ * its analytical Jacobian dF/du at the current iterate for step size dt. */
+int isc_assemble(struct isc_handle* h, double dt);
+/* Gauss-Jordan decoupling with partial pivoting of the assembled system
+ * (Sec. 3.2): J <- C_L J, F <- C_L F with C_L = blockdiag(J_ii)^-1, done by
+ * elementary row operations on each block row; the diagonal blocks become I.
+ * ISC_ERR_SINGULAR_BLOCK on a zero pivot. */
+int isc_decouple(struct isc_handle* h);
+/* Solve J du = -F on the assembled (decoupled, if done) system with the
+ * handle's Krylov method and preconditioner; du stays on the device. */
+int isc_solve(struct isc_handle* h, isc_newton_info* info);
+/* u <- u + du with the safeguards (|dp| <= max_dp_frac p, |dT| <= max_dT,
+ * saturations and mole fractions that would turn negative are halved: the
+ * 0.5 S rule of Sec. 2.2 Phase Equilibrium). */
+int isc_update(struct isc_handle* h);
+/* One Newton linearise-and-solve step: assemble, convergence test (returns
+ * with info->converged = 1 if the scaled norm is below tol_newton), decouple,
+ * precondition, Krylov solve, safeguarded update. */
+int isc_newton_step(struct isc_handle* h, double dt, isc_newton_info* info);
+/* One implicit-Euler time step: Newton until converged (at most
+ * maxit_newton solves); on failure the accepted state is restored and
+ * ISC_ERR_NEWTON_NOCONV (or the failing status) is returned; on success the
+ * converged state becomes the accepted state. */
+int isc_timestep(struct isc_handle* h, double dt, isc_step_info* info);
+
+/* ---------------------------------------------------------------- exports */
+
+/* Residual F of the last assembly (host, block-major 8N), after decoupling
+ * if isc_decouple ran. */
+int isc_get_residual(struct isc_handle* h, double* F);
+/* BSR Jacobian of the last assembly (after decoupling if it ran). rowptr
+ * (N+1), col (nnzb), val (nnzb*64); any may be NULL. */
+int isc_get_jacobian_bsr(struct isc_handle* h, int32_t* rowptr, int32_t* col, double* val);
+/* Newton update du of the last isc_solve (host, block-major 8N). */
+int isc_get_update(struct isc_handle* h, double* du);
+/* Coke C_c solved during the last assembly (host, N). */
+int isc_get_coke(struct isc_handle* h, double* coke);
+/* y = A x with the handle's current BSR matrix (host, block-major 8N). */
+int isc_spmv(struct isc_handle* h, const double* x, double* y);
+/* z = M^-1 r with the preconditioner built by the last isc_solve or
+ * isc_build_preconditioner (host, block-major 8N). */
+int isc_build_preconditioner(struct isc_handle* h);
+int isc_precond_apply(struct isc_handle* h, const double* r, double* z);
+int isc_get_stats(struct isc_handle* h, isc_stats* stats);
+int isc_reset_stats(struct isc_handle* h);
+
+/* ---------------------------------------------------------------- kernels */
+
+/* y = A x for a BSR matrix with 8x8 FP64 blocks, all pointers in device
+ * memory (x, y block-major), ordered on stream. unit_diag = 1 asserts the
+ * diagonal blocks are the identity (as after decoupling) and skips them. */
+int isc_bsr_spmv_device(int32_t nrows, const int32_t* d_rowptr, const int32_t* d_col,
+                        const double* d_val, const double* d_x, double* d_y,
+                        int32_t unit_diag, void* stream);
+
+/* Discrete adjoint of the time loop: not implemented yet. */
+int isc_adjoint(struct isc_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ISC_H */

@@ -1,0 +1,1021 @@
+// Host implementation of the isc.h C ABI: handle lifecycle, Newton and time
+// step drivers, Krylov solvers (GMRES(m) and BiCGSTAB, both right
+// preconditioned), exports and per-kernel timing.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "isc_internal.cuh"
+
+using namespace isc;
+
+struct isc_handle : public Handle {
+  struct Rec {
+    int cls;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+};
+
+namespace {
+
+// scalar slots in Handle::scal
+constexpr int S_NORM = 0;     // 3 norms (bit patterns of doubles, atomicMax)
+constexpr int S_H0 = 8;       // 72 Gram-Schmidt coefficients
+constexpr int S_H1 = 80;      // 72 re-orthogonalisation coefficients
+constexpr int S_NRM = 152;    // squared norm
+constexpr int S_Y = 160;      // 72 solution coefficients
+constexpr int S_BICG = 232;   // BiCGSTAB scalars
+constexpr int NSCAL = 256;
+constexpr int MAX_RESTART = 64;
+
+int set_err(isc_handle* h, int code, const std::string& msg) {
+  if (h) h->last_error = msg;
+  return code;
+}
+
+#define CUDA_TRY(h, expr)                                                                       \
+  do {                                                                                          \
+    cudaError_t e_ = (expr);                                                                    \
+    if (e_ != cudaSuccess) return set_err(h, ISC_ERR_CUDA, std::string(#expr ": ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+cudaEvent_t take_event(isc_handle* h) {
+  if (!h->pool.empty()) {
+    cudaEvent_t e = h->pool.back();
+    h->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+struct Region {
+  isc_handle* h;
+  int cls;
+  cudaEvent_t b = nullptr;
+  cudaEvent_t a = nullptr;
+  Region(isc_handle* h_, int cls_, int launches) : h(h_), cls(cls_) {
+    h->stats.launches[cls] += launches;
+    h->stats.calls[cls] += 1;
+    if (h->opt.profile) {
+      a = take_event(h);
+      b = take_event(h);
+      cudaEventRecord(a, h->stream);
+    }
+  }
+  ~Region() {
+    if (a) {
+      cudaEventRecord(b, h->stream);
+      h->recs.push_back({cls, a, b});
+    }
+  }
+};
+
+void resolve_timers(isc_handle* h) {
+  if (h->recs.empty()) return;
+  cudaStreamSynchronize(h->stream);
+  for (auto& r : h->recs) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) h->stats.ms[r.cls] += ms;
+    h->pool.push_back(r.a);
+    h->pool.push_back(r.b);
+  }
+  h->recs.clear();
+}
+
+int check_device_status(isc_handle* h) {
+  CUDA_TRY(h, cudaMemcpyAsync(h->h_status, h->dstatus, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  int s = *h->h_status;
+  if (s == 0) return ISC_OK;
+  CUDA_TRY(h, cudaMemsetAsync(h->dstatus, 0, sizeof(int), h->stream));
+  if (s & DS_SINGULAR) return set_err(h, ISC_ERR_SINGULAR_BLOCK, "zero pivot in a diagonal block");
+  if (s & DS_COKE) return set_err(h, ISC_ERR_COKE, "coke equation did not converge in a cell");
+  if (s & DS_NONFINITE) return set_err(h, ISC_ERR_NONFINITE, "non-finite residual");
+  if (s & DS_TIMEOUT) return set_err(h, ISC_ERR_TIMEOUT, "bounded device wait gave up");
+  return set_err(h, ISC_ERR_CUDA, "unknown device status");
+}
+
+template <typename T>
+int dalloc(isc_handle* h, T** p, size_t count) {
+  cudaError_t e = cudaMalloc((void**)p, sizeof(T) * std::max<size_t>(count, 1));
+  if (e != cudaSuccess) return set_err(h, ISC_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  return ISC_OK;
+}
+
+void free_all(isc_handle* h) {
+  void* ptrs[] = {h->rowptr, h->col, h->level_cells, h->phi_ref, h->depth, h->tx, h->ty, h->tz, h->well_slot,
+                  h->slots, h->u, h->coke, h->u_n, h->coke_n, h->acc_n, h->props, h->R, h->J, h->ntot, h->du,
+                  h->rhs, h->dinv, h->V, h->Z, h->w, h->tmp, h->partial, h->scal, h->dstatus};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (h->h_scal) cudaFreeHost(h->h_scal);
+  if (h->h_status) cudaFreeHost(h->h_status);
+  for (auto& r : h->recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : h->pool) cudaEventDestroy(e);
+}
+
+double host_dot(isc_handle* h, const double* a, const double* b, int off) {
+  launch_mdot(*h, a, 1, b, off, h->stream);
+  cudaMemcpyAsync(h->h_scal + off, h->scal + off, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  cudaStreamSynchronize(h->stream);
+  return h->h_scal[off];
+}
+
+void spmv(isc_handle* h, const double* x, double* y) {
+  Region rg(h, ISC_K_SPMV, 1);
+  launch_spmv(h->n, h->rowptr, h->col, h->J, x, y, h->decoupled ? 1 : 0, h->stream);
+}
+
+void prec(isc_handle* h, const double* r, double* z) {
+  int launches = h->opt.prec == ISC_PREC_BILU0 ? 2 * h->nlevels : 1;
+  Region rg(h, ISC_K_PREC_APPLY, launches);
+  launch_prec_apply(*h, r, z, h->stream);
+}
+
+int build_prec(isc_handle* h) {
+  if (h->opt.prec == ISC_PREC_BILU0) {
+    Region rg(h, ISC_K_ILU_FACTOR, h->nlevels);
+    launch_ilu_factor(*h, h->stream);
+  } else if (h->opt.prec == ISC_PREC_BJACOBI) {
+    Region rg(h, ISC_K_ILU_FACTOR, 1);
+    launch_bjacobi_factor(*h, h->stream);
+  }
+  h->prec_built = true;
+  return check_device_status(h);
+}
+
+// Right-preconditioned restarted GMRES(m), classical Gram-Schmidt applied twice,
+// Givens rotations on the host. Solves A x = b, x0 = 0.
+int gmres(isc_handle* h, const double* b, double* x, int* its_out, double* rel_out) {
+  const int len = h->n * 8;
+  const int m = std::min(h->opt.restart, h->restart_alloc);
+  cudaStream_t s = h->stream;
+  double* V = h->V;
+  double* Z = h->Z;
+  cudaMemsetAsync(x, 0, sizeof(double) * len, s);
+  double bnorm;
+  {
+    Region rg(h, ISC_K_BLAS1, 2);
+    bnorm = sqrt(host_dot(h, b, b, S_NRM));
+  }
+  *its_out = 0;
+  *rel_out = 0.0;
+  if (bnorm == 0.0) return ISC_OK;
+  if (!isfinite(bnorm)) return set_err(h, ISC_ERR_NONFINITE, "non-finite right-hand side");
+  int its = 0;
+  double rel = 1.0;
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+  bool first = true;
+  while (its < h->opt.maxit_lin) {
+    double beta;
+    if (first) {
+      cudaMemcpyAsync(V, b, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
+      beta = bnorm;
+    } else {
+      spmv(h, x, h->w);
+      Region rg(h, ISC_K_BLAS1, 3);
+      cudaMemcpyAsync(V, b, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
+      launch_axpby(len, -1.0, h->w, 1.0, V, s);
+      beta = sqrt(host_dot(h, V, V, S_NRM));
+    }
+    first = false;
+    rel = beta / bnorm;
+    if (rel <= h->opt.tol_lin) break;
+    {
+      Region rg(h, ISC_K_BLAS1, 1);
+      launch_scale_copy(len, 1.0 / beta, V, V, s);
+    }
+    std::fill(H.begin(), H.end(), 0.0);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int jdone = 0;
+    for (int j = 0; j < m; ++j) {
+      double* Vj = V + (size_t)j * len;
+      double* Zj = Z + (size_t)j * len;
+      prec(h, Vj, Zj);
+      spmv(h, Zj, h->w);
+      {
+        Region rg(h, ISC_K_BLAS1, 10);
+        launch_mdot(*h, V, j + 1, h->w, S_H0, s);
+        launch_maxpy(*h, h->w, V, j + 1, S_H0, -1.0, s);
+        launch_mdot(*h, V, j + 1, h->w, S_H1, s);
+        launch_maxpy(*h, h->w, V, j + 1, S_H1, -1.0, s);
+        launch_mdot(*h, h->w, 1, h->w, S_NRM, s);
+        cudaMemcpyAsync(h->h_scal, h->scal, sizeof(double) * NSCAL, cudaMemcpyDeviceToHost, s);
+        cudaStreamSynchronize(s);
+      }
+      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = h->h_scal[S_H0 + i] + h->h_scal[S_H1 + i];
+      double hn = sqrt(std::max(h->h_scal[S_NRM], 0.0));
+      if (!isfinite(hn)) return set_err(h, ISC_ERR_NONFINITE, "non-finite Krylov vector");
+      H[(size_t)(j + 1) * m + j] = hn;
+      for (int i = 0; i < j; ++i) {
+        double a = H[(size_t)i * m + j], c = H[(size_t)(i + 1) * m + j];
+        H[(size_t)i * m + j] = cs[i] * a + sn[i] * c;
+        H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+      }
+      double a = H[(size_t)j * m + j], c = H[(size_t)(j + 1) * m + j];
+      double den = hypot(a, c);
+      cs[j] = a / den;
+      sn[j] = c / den;
+      H[(size_t)j * m + j] = den;
+      H[(size_t)(j + 1) * m + j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++its;
+      jdone = j + 1;
+      rel = fabs(g[j + 1]) / bnorm;
+      if (rel <= h->opt.tol_lin || its >= h->opt.maxit_lin || hn == 0.0) break;
+      Region rg(h, ISC_K_BLAS1, 1);
+      launch_scale_copy(len, 1.0 / hn, h->w, V + (size_t)(j + 1) * len, s);
+    }
+    for (int i = jdone - 1; i >= 0; --i) {
+      double acc = g[i];
+      for (int k = i + 1; k < jdone; ++k) acc -= H[(size_t)i * m + k] * y[k];
+      y[i] = acc / H[(size_t)i * m + i];
+    }
+    {
+      Region rg(h, ISC_K_BLAS1, 1);
+      memcpy(h->h_scal + S_Y, y.data(), sizeof(double) * jdone);
+      cudaMemcpyAsync(h->scal + S_Y, h->h_scal + S_Y, sizeof(double) * jdone, cudaMemcpyHostToDevice, s);
+      launch_maxpy(*h, x, Z, jdone, S_Y, 1.0, s);
+    }
+    if (rel <= h->opt.tol_lin) {
+      spmv(h, x, h->w);
+      Region rg(h, ISC_K_BLAS1, 3);
+      cudaMemcpyAsync(h->tmp, b, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
+      launch_axpby(len, -1.0, h->w, 1.0, h->tmp, s);
+      rel = sqrt(host_dot(h, h->tmp, h->tmp, S_NRM)) / bnorm;
+      if (rel <= h->opt.tol_lin) break;
+    }
+  }
+  *its_out = its;
+  *rel_out = rel;
+  if (rel > h->opt.tol_lin) return set_err(h, ISC_ERR_KRYLOV_NOCONV, "GMRES did not reach tol_lin");
+  return ISC_OK;
+}
+
+// Right-preconditioned BiCGSTAB, x0 = 0.
+int bicgstab(isc_handle* h, const double* b, double* x, int* its_out, double* rel_out) {
+  const int len = h->n * 8;
+  cudaStream_t s = h->stream;
+  double* r = h->V;
+  double* rhat = r + len;
+  double* p = rhat + len;
+  double* v = p + len;
+  double* sv = v + len;
+  double* t = sv + len;
+  double* phat = h->Z;
+  double* shat = phat + len;
+  cudaMemsetAsync(x, 0, sizeof(double) * len, s);
+  double bnorm;
+  {
+    Region rg(h, ISC_K_BLAS1, 2);
+    bnorm = sqrt(host_dot(h, b, b, S_NRM));
+  }
+  *its_out = 0;
+  *rel_out = 0.0;
+  if (bnorm == 0.0) return ISC_OK;
+  cudaMemcpyAsync(r, b, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(rhat, b, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
+  cudaMemsetAsync(p, 0, sizeof(double) * len, s);
+  cudaMemsetAsync(v, 0, sizeof(double) * len, s);
+  double rho_old = 1.0, alpha = 1.0, omega = 1.0, rel = 1.0;
+  int it;
+  for (it = 1; it <= h->opt.maxit_lin; ++it) {
+    double rho;
+    {
+      Region rg(h, ISC_K_BLAS1, 2);
+      rho = host_dot(h, rhat, r, S_BICG);
+    }
+    if (rho == 0.0) break;
+    {
+      Region rg(h, ISC_K_BLAS1, 2);
+      if (it == 1) {
+        cudaMemcpyAsync(p, r, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
+      } else {
+        double beta = (rho / rho_old) * (alpha / omega);
+        launch_axpby(len, -omega, v, 1.0, p, s);
+        launch_axpby(len, 1.0, r, beta, p, s);
+      }
+    }
+    prec(h, p, phat);
+    spmv(h, phat, v);
+    double rv;
+    {
+      Region rg(h, ISC_K_BLAS1, 2);
+      rv = host_dot(h, rhat, v, S_BICG + 1);
+    }
+    alpha = rho / rv;
+    double snorm;
+    {
+      Region rg(h, ISC_K_BLAS1, 4);
+      cudaMemcpyAsync(sv, r, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
+      launch_axpby(len, -alpha, v, 1.0, sv, s);
+      snorm = sqrt(host_dot(h, sv, sv, S_BICG + 2));
+    }
+    if (snorm / bnorm <= h->opt.tol_lin) {
+      Region rg(h, ISC_K_BLAS1, 1);
+      launch_axpby(len, alpha, phat, 1.0, x, s);
+      rel = snorm / bnorm;
+      break;
+    }
+    prec(h, sv, shat);
+    spmv(h, shat, t);
+    double ts, tt;
+    {
+      Region rg(h, ISC_K_BLAS1, 4);
+      ts = host_dot(h, t, sv, S_BICG + 3);
+      tt = host_dot(h, t, t, S_BICG + 4);
+    }
+    omega = tt > 0.0 ? ts / tt : 0.0;
+    {
+      Region rg(h, ISC_K_BLAS1, 5);
+      launch_axpby(len, alpha, phat, 1.0, x, s);
+      launch_axpby(len, omega, shat, 1.0, x, s);
+      cudaMemcpyAsync(r, sv, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
+      launch_axpby(len, -omega, t, 1.0, r, s);
+      rel = sqrt(host_dot(h, r, r, S_BICG + 5)) / bnorm;
+    }
+    rho_old = rho;
+    if (!isfinite(rel)) return set_err(h, ISC_ERR_NONFINITE, "non-finite BiCGSTAB residual");
+    if (rel <= h->opt.tol_lin || omega == 0.0) break;
+  }
+  *its_out = std::min(it, h->opt.maxit_lin);
+  *rel_out = rel;
+  if (rel > h->opt.tol_lin) return set_err(h, ISC_ERR_KRYLOV_NOCONV, "BiCGSTAB did not reach tol_lin");
+  return ISC_OK;
+}
+
+int validate_options(isc_handle* h, const isc_options& o) {
+  if (o.restart < 1 || o.restart > MAX_RESTART) return set_err(h, ISC_ERR_INVALID_ARG, "restart must be 1..64");
+  if (o.krylov != ISC_KRYLOV_GMRES && o.krylov != ISC_KRYLOV_BICGSTAB)
+    return set_err(h, ISC_ERR_INVALID_ARG, "unknown krylov method");
+  if (o.prec < ISC_PREC_NONE || o.prec > ISC_PREC_BILU0) return set_err(h, ISC_ERR_INVALID_ARG, "unknown preconditioner");
+  if (!(o.tol_lin > 0.0) || o.maxit_lin < 1 || !(o.tol_newton >= 0.0) || o.maxit_newton < 1)
+    return set_err(h, ISC_ERR_INVALID_ARG, "tolerances must be positive and iteration limits >= 1");
+  return ISC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void isc_default_options(isc_options* o) {
+  memset(o, 0, sizeof(*o));
+  o->krylov = ISC_KRYLOV_GMRES;
+  o->restart = 30;
+  o->prec = ISC_PREC_BILU0;
+  o->decouple = 1;
+  o->tol_lin = 1e-6;
+  o->maxit_lin = 600;
+  o->tol_newton = 1e-6;
+  o->maxit_newton = 25;
+  o->max_dp_frac = 0.2;
+  o->max_dT = 50.0;
+  o->profile = 0;
+  o->stream = nullptr;
+}
+
+const char* isc_status_string(int st) {
+  switch (st) {
+    case ISC_OK: return "ok";
+    case ISC_ERR_INVALID_ARG: return "invalid argument";
+    case ISC_ERR_CUDA: return "CUDA error";
+    case ISC_ERR_NOMEM: return "out of device memory";
+    case ISC_ERR_SINGULAR_BLOCK: return "singular diagonal block";
+    case ISC_ERR_KRYLOV_NOCONV: return "Krylov solver did not converge";
+    case ISC_ERR_NEWTON_NOCONV: return "Newton did not converge";
+    case ISC_ERR_NONFINITE: return "non-finite value";
+    case ISC_ERR_COKE: return "coke equation did not converge";
+    case ISC_ERR_TIMEOUT: return "device wait timed out";
+    case ISC_ERR_UNIMPLEMENTED: return "not implemented";
+    case ISC_ERR_STATE: return "call order violated";
+    default: return "unknown status";
+  }
+}
+
+const char* isc_last_error(const isc_handle* h) { return h ? h->last_error.c_str() : "null handle"; }
+int32_t isc_num_cells(const isc_handle* h) { return h ? h->n : 0; }
+int32_t isc_nnzb(const isc_handle* h) { return h ? h->nnzb : 0; }
+
+int isc_create(const isc_grid* grid, const isc_rock* rock, const isc_fluid* fl, const isc_reactions* rx,
+               const isc_wells* wells, const isc_options* opts, isc_handle** out) {
+  if (!out) return ISC_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!grid || !rock || !fl || !rx || !wells) return ISC_ERR_INVALID_ARG;
+  if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || !(grid->dx > 0) || !(grid->dy > 0) || !(grid->dz > 0))
+    return ISC_ERR_INVALID_ARG;
+  long long nll = (long long)grid->nx * grid->ny * grid->nz;
+  if (nll * 7 * 64 > (long long)INT32_MAX * 64LL || nll > (1LL << 28)) return ISC_ERR_INVALID_ARG;
+  if (!rock->phi_ref || !rock->perm) return ISC_ERR_INVALID_ARG;
+  if (rx->nr < 0 || rx->nr > ISC_MAX_RXN) return ISC_ERR_INVALID_ARG;
+  isc_handle* h = new (std::nothrow) isc_handle();
+  if (!h) return ISC_ERR_NOMEM;
+  isc_options o;
+  if (opts)
+    o = *opts;
+  else
+    isc_default_options(&o);
+  int st = validate_options(h, o);
+  if (st) {
+    delete h;
+    return st;
+  }
+  h->opt = o;
+  h->stream = (cudaStream_t)o.stream;
+  const int nx = grid->nx, ny = grid->ny, nz = grid->nz, n = (int)nll;
+  h->nx = nx;
+  h->ny = ny;
+  h->nz = nz;
+  h->n = n;
+  // N M = 0 check of every reaction (Sec. 2.1)
+  double Mfull[7];
+  for (int c = 0; c < 6; ++c) Mfull[c] = fl->M[c];
+  Mfull[6] = fl->coke_M;
+  for (int r = 0; r < rx->nr; ++r) {
+    double s = 0, a = 0;
+    for (int c = 0; c < 7; ++c) {
+      s += rx->stoich[r][c] * Mfull[c];
+      a += fabs(rx->stoich[r][c]) * Mfull[c];
+    }
+    if (fabs(s) > 1e-12 * a) {
+      int e = set_err(h, ISC_ERR_INVALID_ARG, "reaction " + std::to_string(r) + " violates N M = 0");
+      *out = nullptr;
+      delete h;
+      return e;
+    }
+    if (rx->kind[r] < 0 || rx->kind[r] > 2 || (rx->kind[r] != ISC_RXN_COKE_OXIDATION && rx->comp[r] != 1 && rx->comp[r] != 2)) {
+      delete h;
+      return ISC_ERR_INVALID_ARG;
+    }
+  }
+  // parameters
+  Params& P = h->P;
+  P.nx = nx;
+  P.ny = ny;
+  P.nz = nz;
+  P.n = n;
+  P.V = grid->dx * grid->dy * grid->dz;
+  P.gx = grid->dy * grid->dz / grid->dx;
+  P.gy = grid->dx * grid->dz / grid->dy;
+  P.gz = grid->dx * grid->dy / grid->dz;
+  for (int c = 0; c < 6; ++c) {
+    P.M[c] = fl->M[c];
+    P.a_rk[c] = pow(fl->Tc[c], 1.25) / sqrt(fl->pc[c]);
+    P.b_rk[c] = fl->Tc[c] / fl->pc[c];
+    P.sqM[c] = sqrt(fl->M[c]);
+    P.avg[c] = fl->avg[c];
+    P.bvg[c] = fl->bvg[c];
+    for (int k = 0; k < 4; ++k) P.cpg[c][k] = fl->cpg[c][k];
+  }
+  for (int c = 0; c < 3; ++c) {
+    P.rho_ref[c] = fl->rho_ref[c];
+    P.cp[c] = fl->cp[c];
+    P.ct1[c] = fl->ct1[c];
+    P.ct2[c] = fl->ct2[c];
+    P.cpt[c] = fl->cpt[c];
+    P.hvr[c] = fl->hvr[c];
+    P.ev[c] = fl->ev[c];
+    P.Tc[c] = fl->Tc[c];
+    P.ln_avisc[c] = log(fl->avisc[c]);
+    P.bvisc[c] = fl->bvisc[c];
+    for (int k = 0; k < 5; ++k) P.kv[c][k] = fl->kv[c][k];
+    P.K_phase[c] = fl->K_phase[c];
+  }
+  P.p_ref = fl->p_ref;
+  P.T_ref = fl->T_ref;
+  P.coke_rho = fl->coke_rho;
+  P.coke_cp = fl->coke_cp;
+  P.coke_K = fl->coke_K;
+  P.Swc = fl->Swc;
+  P.Sorw = fl->Sorw;
+  P.Sgc = fl->Sgc;
+  P.Sorg = fl->Sorg;
+  P.per_eps = fl->per_eps;
+  P.gravity = fl->gravity;
+  P.cpor = rock->cpor;
+  P.ctpor = rock->ctpor;
+  P.cptpor = rock->cptpor;
+  P.rock_p_ref = rock->p_ref;
+  P.rock_T_ref = rock->T_ref;
+  P.cv1 = rock->cv1;
+  P.cv2 = rock->cv2;
+  P.K_rock = rock->K_rock;
+  P.cv_scale = rock->cv1;
+  P.nr = rx->nr;
+  for (int r = 0; r < rx->nr; ++r) {
+    P.kind[r] = rx->kind[r];
+    P.comp[r] = rx->comp[r];
+    for (int c = 0; c < 7; ++c) P.stoich[r][c] = rx->stoich[r][c];
+    P.A[r] = rx->A[r];
+    P.EaR[r] = rx->Ea[r] / R_GAS;
+    P.dH[r] = rx->dH[r];
+  }
+  P.coke_max = rx->coke_max;
+  // BSR pattern of the 7-point stencil (columns sorted) and hyperplane levels
+  h->h_rowptr.resize(n + 1);
+  h->h_col.reserve((size_t)n * 7);
+  h->h_rowptr[0] = 0;
+  for (int c = 0; c < n; ++c) {
+    int ix = c % nx, iy = (c / nx) % ny, iz = c / (nx * ny);
+    if (iz > 0) h->h_col.push_back(c - nx * ny);
+    if (iy > 0) h->h_col.push_back(c - nx);
+    if (ix > 0) h->h_col.push_back(c - 1);
+    h->h_col.push_back(c);
+    if (ix < nx - 1) h->h_col.push_back(c + 1);
+    if (iy < ny - 1) h->h_col.push_back(c + nx);
+    if (iz < nz - 1) h->h_col.push_back(c + nx * ny);
+    h->h_rowptr[c + 1] = (int32_t)h->h_col.size();
+  }
+  h->nnzb = (int)h->h_col.size();
+  h->nlevels = nx + ny + nz - 2;
+  std::vector<int32_t> level_cells(n);
+  h->h_level_ptr.assign(h->nlevels + 1, 0);
+  for (int c = 0; c < n; ++c) {
+    int L = c % nx + (c / nx) % ny + c / (nx * ny);
+    h->h_level_ptr[L + 1]++;
+  }
+  for (int L = 0; L < h->nlevels; ++L) h->h_level_ptr[L + 1] += h->h_level_ptr[L];
+  {
+    std::vector<int32_t> fill(h->h_level_ptr.begin(), h->h_level_ptr.end() - 1);
+    for (int c = 0; c < n; ++c) {
+      int L = c % nx + (c / nx) % ny + c / (nx * ny);
+      level_cells[fill[L]++] = c;
+    }
+  }
+  // transmissibilities: harmonic average of (A k / h) of the two cells (Sec. 3.1)
+  std::vector<double> tx(n, 0.0), ty(n, 0.0), tz(n, 0.0), depth(n);
+  const double* kx = rock->perm;
+  const double* ky = rock->perm + n;
+  const double* kz = rock->perm + 2 * (size_t)n;
+  auto harm = [](double a, double b) { return 2.0 * a * b / (a + b); };
+  const double ax = grid->dy * grid->dz / grid->dx, ay = grid->dx * grid->dz / grid->dy,
+               az = grid->dx * grid->dy / grid->dz;
+  for (int c = 0; c < n; ++c) {
+    int ix = c % nx, iy = (c / nx) % ny, iz = c / (nx * ny);
+    if (ix < nx - 1) tx[c] = harm(ax * kx[c], ax * kx[c + 1]);
+    if (iy < ny - 1) ty[c] = harm(ay * ky[c], ay * ky[c + nx]);
+    if (iz < nz - 1) tz[c] = harm(az * kz[c], az * kz[c + nx * ny]);
+    depth[c] = grid->depth ? grid->depth[c] : (iz + 0.5) * grid->dz;
+    if (!(rock->phi_ref[c] > 0.0) || !(kx[c] > 0) || !(ky[c] > 0) || !(kz[c] > 0)) {
+      delete h;
+      return ISC_ERR_INVALID_ARG;
+    }
+  }
+  // well slots
+  std::vector<int32_t> well_slot(n, -1);
+  std::vector<WellSlot> slots;
+  for (int w = 0; w < wells->nw; ++w) {
+    const isc_well& W = wells->wells[w];
+    if (W.n_perf < 1 || !W.cells || !W.WI) {
+      delete h;
+      return ISC_ERR_INVALID_ARG;
+    }
+    double wsum = 0;
+    for (int q = 0; q < W.n_perf; ++q) wsum += W.WI[q];
+    double Hinj = 0.0;
+    if (W.kind == ISC_WELL_RATE_INJECTOR) {
+      // molar enthalpy of the injected stream at T_inj
+      double T = W.inj_T, Tr = fl->T_ref;
+      for (int c = 0; c < 6; ++c) {
+        double hg = 0, tk = T, trk = Tr;
+        for (int k = 0; k < 4; ++k) {
+          hg += fl->cpg[c][k] / (k + 1) * (tk - trk);
+          tk *= T;
+          trk *= Tr;
+        }
+        if (W.inj_phase == 0) {
+          if (c == 0) {
+            double hv = (fl->Tc[0] > T) ? fl->hvr[0] * pow(fl->Tc[0] - T, fl->ev[0]) : 0.0;
+            Hinj += W.inj_y[0] * (hg - hv);
+          }
+        } else {
+          Hinj += W.inj_y[c] * hg;
+        }
+      }
+    }
+    for (int q = 0; q < W.n_perf; ++q) {
+      int c = W.cells[q];
+      if (c < 0 || c >= n || well_slot[c] >= 0) {
+        delete h;
+        return ISC_ERR_INVALID_ARG;
+      }
+      WellSlot sl{};
+      sl.kind = W.kind;
+      sl.WI = W.WI[q];
+      sl.bhp = W.target;
+      if (W.kind == ISC_WELL_RATE_INJECTOR) {
+        double share = W.WI[q] / wsum;
+        for (int k = 0; k < 6; ++k) sl.src[k] = share * W.target * W.inj_y[k];
+        sl.src[6] = share * W.target * Hinj;
+      }
+      well_slot[c] = (int32_t)slots.size();
+      slots.push_back(sl);
+    }
+  }
+  h->nslots = (int)slots.size();
+  // device memory
+  h->restart_alloc = std::max(o.restart, 8);
+  const size_t len = (size_t)n * 8;
+  h->red_blocks = 304;
+  int e = 0;
+  e |= dalloc(h, &h->rowptr, n + 1);
+  e |= dalloc(h, &h->col, h->nnzb);
+  e |= dalloc(h, &h->level_cells, n);
+  e |= dalloc(h, &h->phi_ref, n);
+  e |= dalloc(h, &h->depth, n);
+  e |= dalloc(h, &h->tx, n);
+  e |= dalloc(h, &h->ty, n);
+  e |= dalloc(h, &h->tz, n);
+  e |= dalloc(h, &h->well_slot, n);
+  e |= dalloc(h, &h->slots, std::max(h->nslots, 1));
+  e |= dalloc(h, &h->u, len);
+  e |= dalloc(h, &h->coke, n);
+  e |= dalloc(h, &h->u_n, len);
+  e |= dalloc(h, &h->coke_n, n);
+  e |= dalloc(h, &h->acc_n, (size_t)n * 7);
+  e |= dalloc(h, &h->props, (size_t)n * NQD);
+  e |= dalloc(h, &h->R, len);
+  e |= dalloc(h, &h->J, (size_t)h->nnzb * BB);
+  e |= dalloc(h, &h->ntot, n);
+  e |= dalloc(h, &h->du, len);
+  e |= dalloc(h, &h->rhs, len);
+  e |= dalloc(h, &h->dinv, (size_t)n * BB);
+  e |= dalloc(h, &h->V, (size_t)(h->restart_alloc + 1) * len);
+  e |= dalloc(h, &h->Z, (size_t)h->restart_alloc * len);
+  e |= dalloc(h, &h->w, len);
+  e |= dalloc(h, &h->tmp, len);
+  e |= dalloc(h, &h->partial, (size_t)h->red_blocks * (MAX_RESTART + 8));
+  e |= dalloc(h, &h->scal, NSCAL);
+  e |= dalloc(h, &h->dstatus, 1);
+  if (e) {
+    std::string msg = h->last_error;
+    free_all(h);
+    delete h;
+    return ISC_ERR_NOMEM;
+  }
+  if (cudaMallocHost((void**)&h->h_scal, sizeof(double) * NSCAL) != cudaSuccess ||
+      cudaMallocHost((void**)&h->h_status, sizeof(int)) != cudaSuccess) {
+    free_all(h);
+    delete h;
+    return ISC_ERR_NOMEM;
+  }
+  cudaStream_t s = h->stream;
+  cudaMemcpyAsync(h->rowptr, h->h_rowptr.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(h->col, h->h_col.data(), sizeof(int32_t) * h->nnzb, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(h->level_cells, level_cells.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(h->phi_ref, rock->phi_ref, sizeof(double) * n, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(h->depth, depth.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(h->tx, tx.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(h->ty, ty.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(h->tz, tz.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(h->well_slot, well_slot.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s);
+  if (h->nslots) cudaMemcpyAsync(h->slots, slots.data(), sizeof(WellSlot) * h->nslots, cudaMemcpyHostToDevice, s);
+  cudaMemsetAsync(h->dstatus, 0, sizeof(int), s);
+  cudaMemsetAsync(h->u, 0, sizeof(double) * len, s);
+  cudaMemsetAsync(h->coke, 0, sizeof(double) * n, s);
+  cudaMemsetAsync(h->coke_n, 0, sizeof(double) * n, s);
+  cudaError_t ce = cudaStreamSynchronize(s);
+  if (ce != cudaSuccess) {
+    free_all(h);
+    delete h;
+    return ISC_ERR_CUDA;
+  }
+  *out = h;
+  return ISC_OK;
+}
+
+void isc_destroy(isc_handle* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  free_all(h);
+  delete h;
+}
+
+int isc_set_options(isc_handle* h, const isc_options* o) {
+  if (!h || !o) return ISC_ERR_INVALID_ARG;
+  int st = validate_options(h, *o);
+  if (st) return st;
+  if (o->restart > h->restart_alloc) return set_err(h, ISC_ERR_INVALID_ARG, "restart larger than at creation");
+  if ((cudaStream_t)o->stream != h->stream) cudaStreamSynchronize(h->stream);
+  h->opt = *o;
+  h->stream = (cudaStream_t)o->stream;
+  h->prec_built = false;
+  return ISC_OK;
+}
+
+int isc_init_equilibrium(isc_handle* h, double p0, double T0, double Sw0, double So0, double x_LO0,
+                         const double y_rest[3], int32_t n_ignited, const int32_t* ignited, double T_ignite) {
+  if (!h || !y_rest || n_ignited < 0 || (n_ignited > 0 && !ignited)) return ISC_ERR_INVALID_ARG;
+  launch_init_equilibrium(*h, p0, T0, Sw0, So0, x_LO0, y_rest, h->stream);
+  for (int q = 0; q < n_ignited; ++q) {
+    int c = ignited[q];
+    if (c < 0 || c >= h->n) return set_err(h, ISC_ERR_INVALID_ARG, "ignited cell out of range");
+    CUDA_TRY(h, cudaMemcpyAsync(h->u + (size_t)5 * h->n + c, &T_ignite, sizeof(double), cudaMemcpyHostToDevice,
+                                h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  }
+  return isc_begin_step(h);
+}
+
+int isc_set_state(isc_handle* h, const double* u, const double* coke) {
+  if (!h || !u) return ISC_ERR_INVALID_ARG;
+  CUDA_TRY(h, cudaMemcpyAsync(h->u, u, sizeof(double) * 8 * h->n, cudaMemcpyHostToDevice, h->stream));
+  if (coke) CUDA_TRY(h, cudaMemcpyAsync(h->coke, coke, sizeof(double) * h->n, cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  h->assembled = h->decoupled = h->prec_built = false;
+  return ISC_OK;
+}
+
+int isc_get_state(isc_handle* h, double* u, double* coke) {
+  if (!h || !u) return ISC_ERR_INVALID_ARG;
+  CUDA_TRY(h, cudaMemcpyAsync(u, h->u, sizeof(double) * 8 * h->n, cudaMemcpyDeviceToHost, h->stream));
+  if (coke) CUDA_TRY(h, cudaMemcpyAsync(coke, h->coke, sizeof(double) * h->n, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return ISC_OK;
+}
+
+int isc_set_state_device(isc_handle* h, const double* d_u, const double* d_coke) {
+  if (!h || !d_u) return ISC_ERR_INVALID_ARG;
+  CUDA_TRY(h, cudaMemcpyAsync(h->u, d_u, sizeof(double) * 8 * h->n, cudaMemcpyDeviceToDevice, h->stream));
+  if (d_coke) CUDA_TRY(h, cudaMemcpyAsync(h->coke, d_coke, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, h->stream));
+  h->assembled = h->decoupled = h->prec_built = false;
+  return ISC_OK;
+}
+
+int isc_get_state_device(isc_handle* h, double* d_u, double* d_coke) {
+  if (!h || !d_u) return ISC_ERR_INVALID_ARG;
+  CUDA_TRY(h, cudaMemcpyAsync(d_u, h->u, sizeof(double) * 8 * h->n, cudaMemcpyDeviceToDevice, h->stream));
+  if (d_coke) CUDA_TRY(h, cudaMemcpyAsync(d_coke, h->coke, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, h->stream));
+  return ISC_OK;
+}
+
+int isc_begin_step(isc_handle* h) {
+  if (!h) return ISC_ERR_INVALID_ARG;
+  CUDA_TRY(h, cudaMemcpyAsync(h->u_n, h->u, sizeof(double) * 8 * h->n, cudaMemcpyDeviceToDevice, h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(h->coke_n, h->coke, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, h->stream));
+  launch_old_accumulation(*h, h->stream);
+  CUDA_TRY(h, cudaGetLastError());
+  h->have_acc = true;
+  return ISC_OK;
+}
+
+int isc_assemble(isc_handle* h, double dt) {
+  if (!h || !(dt > 0.0)) return ISC_ERR_INVALID_ARG;
+  if (!h->have_acc) return set_err(h, ISC_ERR_STATE, "isc_begin_step (or isc_init_equilibrium) must come first");
+  h->P.dt = dt;
+  h->P.inv_dt = 1.0 / dt;
+  {
+    Region rg(h, ISC_K_PROPS, 1);
+    launch_props(*h, h->stream);
+  }
+  {
+    Region rg(h, ISC_K_FLUX, 1);
+    launch_flux(*h, h->stream);
+  }
+  CUDA_TRY(h, cudaGetLastError());
+  h->assembled = true;
+  h->decoupled = false;
+  h->prec_built = false;
+  h->last_dt = dt;
+  return ISC_OK;
+}
+
+int isc_decouple(isc_handle* h) {
+  if (!h) return ISC_ERR_INVALID_ARG;
+  if (!h->assembled) return set_err(h, ISC_ERR_STATE, "assemble first");
+  if (h->decoupled) return ISC_OK;
+  {
+    Region rg(h, ISC_K_GJ, 1);
+    launch_gj(*h, h->stream);
+  }
+  CUDA_TRY(h, cudaGetLastError());
+  int st = check_device_status(h);
+  if (st) return st;
+  h->decoupled = true;
+  h->prec_built = false;
+  return ISC_OK;
+}
+
+int isc_build_preconditioner(isc_handle* h) {
+  if (!h) return ISC_ERR_INVALID_ARG;
+  if (!h->assembled) return set_err(h, ISC_ERR_STATE, "assemble first");
+  return build_prec(h);
+}
+
+int isc_solve(isc_handle* h, isc_newton_info* info) {
+  if (!h) return ISC_ERR_INVALID_ARG;
+  if (!h->assembled) return set_err(h, ISC_ERR_STATE, "assemble first");
+  int st = ISC_OK;
+  if (!h->prec_built) {
+    st = build_prec(h);
+    if (st) return st;
+  }
+  const int len = h->n * 8;
+  {
+    Region rg(h, ISC_K_BLAS1, 1);
+    launch_scale_copy(len, -1.0, h->R, h->rhs, h->stream);
+  }
+  int its = 0;
+  double rel = 0.0;
+  if (h->opt.krylov == ISC_KRYLOV_GMRES)
+    st = gmres(h, h->rhs, h->du, &its, &rel);
+  else
+    st = bicgstab(h, h->rhs, h->du, &its, &rel);
+  if (info) {
+    info->krylov_iterations = its;
+    info->krylov_rel_residual = rel;
+    info->status = st;
+  }
+  CUDA_TRY(h, cudaGetLastError());
+  return st;
+}
+
+int isc_update(isc_handle* h) {
+  if (!h) return ISC_ERR_INVALID_ARG;
+  {
+    Region rg(h, ISC_K_UPDATE, 1);
+    launch_update(*h, h->stream);
+  }
+  CUDA_TRY(h, cudaGetLastError());
+  h->assembled = h->decoupled = h->prec_built = false;
+  return ISC_OK;
+}
+
+int isc_newton_step(isc_handle* h, double dt, isc_newton_info* info) {
+  if (!h) return ISC_ERR_INVALID_ARG;
+  isc_newton_info loc{};
+  if (!info) info = &loc;
+  memset(info, 0, sizeof(*info));
+  int st = isc_assemble(h, dt);
+  if (st) return st;
+  {
+    Region rg(h, ISC_K_NORM, 2);
+    launch_norms(*h, h->stream);
+  }
+  CUDA_TRY(h, cudaMemcpyAsync(h->h_scal, h->scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  st = check_device_status(h);  // synchronises
+  if (st) {
+    info->status = st;
+    return st;
+  }
+  info->norm_mass = h->h_scal[0] * dt;
+  info->norm_energy = h->h_scal[1] * dt;
+  info->norm_gs = h->h_scal[2];
+  info->norm = std::max(info->norm_mass, std::max(info->norm_energy, info->norm_gs));
+  if (!isfinite(info->norm)) {
+    info->status = ISC_ERR_NONFINITE;
+    return set_err(h, ISC_ERR_NONFINITE, "non-finite residual norm");
+  }
+  if (info->norm <= h->opt.tol_newton) {
+    info->converged = 1;
+    return ISC_OK;
+  }
+  if (h->opt.decouple) {
+    st = isc_decouple(h);
+    if (st) {
+      info->status = st;
+      return st;
+    }
+  }
+  st = isc_solve(h, info);
+  if (st) {
+    info->status = st;
+    return st;
+  }
+  st = isc_update(h);
+  info->status = st;
+  return st;
+}
+
+int isc_timestep(isc_handle* h, double dt, isc_step_info* info) {
+  if (!h || !(dt > 0.0)) return ISC_ERR_INVALID_ARG;
+  isc_step_info loc{};
+  if (!info) info = &loc;
+  memset(info, 0, sizeof(*info));
+  if (!h->have_acc) return set_err(h, ISC_ERR_STATE, "isc_begin_step (or isc_init_equilibrium) must come first");
+  int st = ISC_OK;
+  bool conv = false;
+  for (int it = 0; it <= h->opt.maxit_newton; ++it) {
+    isc_newton_info ni;
+    st = isc_newton_step(h, dt, &ni);
+    info->final_norm = ni.norm;
+    if (st) break;
+    if (ni.converged) {
+      conv = true;
+      break;
+    }
+    info->newton_iterations++;
+    info->krylov_iterations += ni.krylov_iterations;
+  }
+  if (conv) {
+    st = isc_begin_step(h);
+    info->status = st;
+    return st;
+  }
+  // restore the accepted state
+  cudaMemcpyAsync(h->u, h->u_n, sizeof(double) * 8 * h->n, cudaMemcpyDeviceToDevice, h->stream);
+  cudaMemcpyAsync(h->coke, h->coke_n, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, h->stream);
+  cudaStreamSynchronize(h->stream);
+  h->assembled = h->decoupled = h->prec_built = false;
+  if (st == ISC_OK) st = set_err(h, ISC_ERR_NEWTON_NOCONV, "Newton did not converge within maxit_newton");
+  info->status = st;
+  return st;
+}
+
+int isc_get_residual(isc_handle* h, double* F) {
+  if (!h || !F) return ISC_ERR_INVALID_ARG;
+  if (!h->assembled) return set_err(h, ISC_ERR_STATE, "assemble first");
+  CUDA_TRY(h, cudaMemcpyAsync(F, h->R, sizeof(double) * 8 * h->n, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return ISC_OK;
+}
+
+int isc_get_jacobian_bsr(isc_handle* h, int32_t* rowptr, int32_t* col, double* val) {
+  if (!h) return ISC_ERR_INVALID_ARG;
+  if (rowptr) memcpy(rowptr, h->h_rowptr.data(), sizeof(int32_t) * (h->n + 1));
+  if (col) memcpy(col, h->h_col.data(), sizeof(int32_t) * h->nnzb);
+  if (val) {
+    if (!h->assembled) return set_err(h, ISC_ERR_STATE, "assemble first");
+    CUDA_TRY(h, cudaMemcpyAsync(val, h->J, sizeof(double) * BB * h->nnzb, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  }
+  return ISC_OK;
+}
+
+int isc_get_update(isc_handle* h, double* du) {
+  if (!h || !du) return ISC_ERR_INVALID_ARG;
+  CUDA_TRY(h, cudaMemcpyAsync(du, h->du, sizeof(double) * 8 * h->n, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return ISC_OK;
+}
+
+int isc_get_coke(isc_handle* h, double* coke) {
+  if (!h || !coke) return ISC_ERR_INVALID_ARG;
+  CUDA_TRY(h, cudaMemcpyAsync(coke, h->coke, sizeof(double) * h->n, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return ISC_OK;
+}
+
+int isc_spmv(isc_handle* h, const double* x, double* y) {
+  if (!h || !x || !y) return ISC_ERR_INVALID_ARG;
+  if (!h->assembled) return set_err(h, ISC_ERR_STATE, "assemble first");
+  const size_t len = (size_t)h->n * 8;
+  CUDA_TRY(h, cudaMemcpyAsync(h->w, x, sizeof(double) * len, cudaMemcpyHostToDevice, h->stream));
+  spmv(h, h->w, h->tmp);
+  CUDA_TRY(h, cudaMemcpyAsync(y, h->tmp, sizeof(double) * len, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return ISC_OK;
+}
+
+int isc_precond_apply(isc_handle* h, const double* r, double* z) {
+  if (!h || !r || !z) return ISC_ERR_INVALID_ARG;
+  if (!h->prec_built) return set_err(h, ISC_ERR_STATE, "build the preconditioner first");
+  const size_t len = (size_t)h->n * 8;
+  CUDA_TRY(h, cudaMemcpyAsync(h->w, r, sizeof(double) * len, cudaMemcpyHostToDevice, h->stream));
+  prec(h, h->w, h->V);
+  CUDA_TRY(h, cudaMemcpyAsync(z, h->V, sizeof(double) * len, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return ISC_OK;
+}
+
+int isc_get_stats(isc_handle* h, isc_stats* st) {
+  if (!h || !st) return ISC_ERR_INVALID_ARG;
+  resolve_timers(h);
+  *st = h->stats;
+  return ISC_OK;
+}
+
+int isc_reset_stats(isc_handle* h) {
+  if (!h) return ISC_ERR_INVALID_ARG;
+  resolve_timers(h);
+  memset(&h->stats, 0, sizeof(h->stats));
+  return ISC_OK;
+}
+
+int isc_bsr_spmv_device(int32_t nrows, const int32_t* d_rowptr, const int32_t* d_col, const double* d_val,
+                        const double* d_x, double* d_y, int32_t unit_diag, void* stream) {
+  if (nrows < 0 || (nrows > 0 && (!d_rowptr || !d_col || !d_val || !d_x || !d_y))) return ISC_ERR_INVALID_ARG;
+  if (nrows == 0) return ISC_OK;
+  launch_spmv(nrows, d_rowptr, d_col, d_val, d_x, d_y, unit_diag, (cudaStream_t)stream);
+  return cudaGetLastError() == cudaSuccess ? ISC_OK : ISC_ERR_CUDA;
+}
+
+int isc_adjoint(isc_handle* h) {
+  if (h) h->last_error = "the discrete adjoint is not implemented";
+  return ISC_ERR_UNIMPLEMENTED;
+}
+
+}  // extern "C"

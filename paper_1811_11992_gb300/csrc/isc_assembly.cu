@@ -1,0 +1,634 @@
+// Residual and analytical Jacobian assembly of the ISC model (Sec. 2.2, 3.1).
+//
+// k_props   one thread per cell: properties with exact derivatives
+//           (forward-mode, 8 tangents), local coke equation, accumulation,
+//           reactions and wells -> residual, diagonal Jacobian block and the
+//           staged face quantities (lambda_alpha * carried quantity, gamma,
+//           K_T with their derivatives).
+// k_flux    one thread per (cell, equation row): the six faces of the cell,
+//           upstream weighting per phase, harmonic transmissibility, face
+//           fluxes and their derivatives w.r.t. both cells; adds to the
+//           residual and the diagonal block, writes the off-diagonal blocks.
+//           Each face is evaluated in its canonical (lo, hi) orientation by
+//           the same code in both cells, so the two contributions are exact
+//           negatives of each other.
+#include <math.h>
+
+#include "dual8.cuh"
+#include "isc_internal.cuh"
+
+namespace isc {
+
+namespace {
+
+constexpr double OMEGA_A = 0.427480;
+constexpr double OMEGA_B = 0.086640;
+
+struct Base {
+  D8 p, T, Sw, Sg, So, xlo, xho;
+  D8 y[6];
+  D8 rho_w, rho_o, rho_g;
+  D8 lam[3];
+  D8 H[3];
+  D8 U[3];
+  D8 phi, Ur, Uc;
+  D8 gam[3];
+};
+
+__device__ __forceinline__ D8 clamp01(const D8& s) {
+  if (s.v <= 0.0) return dc(0.0);
+  if (s.v >= 1.0) return dc(1.0);
+  return s;
+}
+
+// largest real root of z^3 - z^2 + a1 z + a0 (trigonometric / Cardano), 2 Newton polishes
+__device__ double cubic_root(double a1, double a0) {
+  const double a2 = -1.0;
+  double pp = a1 - a2 * a2 / 3.0;
+  double qq = 2.0 * a2 * a2 * a2 / 27.0 - a2 * a1 / 3.0 + a0;
+  double disc = (qq * 0.5) * (qq * 0.5) + (pp / 3.0) * (pp / 3.0) * (pp / 3.0);
+  double z;
+  if (disc < 0.0) {
+    double m = 2.0 * sqrt(-pp / 3.0);
+    double arg = 3.0 * qq / (pp * m);
+    arg = fmin(1.0, fmax(-1.0, arg));
+    z = m * cos(acos(arg) / 3.0);
+  } else {
+    double sd = sqrt(disc);
+    z = cbrt(-qq * 0.5 + sd) + cbrt(-qq * 0.5 - sd);
+  }
+  z -= a2 / 3.0;
+  for (int it = 0; it < 2; ++it) {
+    double f = ((z - 1.0) * z + a1) * z + a0;
+    double df = (3.0 * z - 2.0) * z + a1;
+    z -= f / df;
+  }
+  return z;
+}
+
+__device__ __forceinline__ D8 k_value(const Params& P, int c, const D8& p, const D8& T) {
+  D8 pre = P.kv[c][0] / p + P.kv[c][1] * p + P.kv[c][2];
+  D8 ex = dexp(P.kv[c][3] / (T - P.kv[c][4]));
+  return pre * ex;
+}
+
+__device__ __forceinline__ D8 per_f(const Params& P, const D8& s) { return s / (s + P.per_eps); }
+
+__device__ __forceinline__ D8 liquid_rho(const Params& P, int c, const D8& dp, const D8& dT) {
+  D8 e = P.cp[c] * dp - P.ct1[c] * dT - (0.5 * P.ct2[c]) * (dT * dT) + P.cpt[c] * (dp * dT);
+  return P.rho_ref[c] * dexp(e);
+}
+
+__device__ __forceinline__ D8 gas_enthalpy(const Params& P, int c, const D8& T) {
+  double t = T.v, tr = P.T_ref;
+  double h = 0.0, cp = 0.0, tk = t, trk = tr, tpow = 1.0;
+  for (int k = 0; k < 4; ++k) {
+    h += P.cpg[c][k] / (k + 1) * (tk - trk);
+    cp += P.cpg[c][k] * tpow;
+    tpow *= t;
+    tk *= t;
+    trk *= tr;
+  }
+  return dchain(T, h, cp);
+}
+
+__device__ __forceinline__ D8 vap_enthalpy(const Params& P, int c, const D8& T) {
+  D8 d = P.Tc[c] - T;
+  if (d.v > 0.0) return P.hvr[c] * dpow(d, P.ev[c]);
+  return dc(0.0);
+}
+
+__device__ void base_properties(const Params& P, const double* __restrict__ u, int i, double phi_ref, Base& b) {
+  const int n = P.n;
+  b.p = dvar(u[0 * n + i], 0);
+  b.xlo = dvar(u[1 * n + i], 1);
+  D8 yo2 = dvar(u[2 * n + i], 2);
+  D8 yn2 = dvar(u[3 * n + i], 3);
+  D8 yco2 = dvar(u[4 * n + i], 4);
+  b.T = dvar(u[5 * n + i], 5);
+  b.Sw = dvar(u[6 * n + i], 6);
+  b.Sg = dvar(u[7 * n + i], 7);
+  b.So = 1.0 - b.Sw - b.Sg;
+  b.xho = 1.0 - b.xlo;
+  const D8& p = b.p;
+  const D8& T = b.T;
+  // gas mole fractions: Tab4.4 with the modified PER (eq. PER1/PER2)
+  b.y[0] = per_f(P, b.Sw) * k_value(P, 0, p, T);
+  b.y[1] = k_value(P, 1, p, T) * b.xlo;
+  b.y[2] = per_f(P, b.So) * k_value(P, 2, p, T) * b.xho;
+  b.y[3] = yo2;
+  b.y[4] = yn2;
+  b.y[5] = yco2;
+  // Redlich-Kwong Z factor with the mixing rule: A = Oa p a^2 / T^2.5, B = Ob p b / T
+  D8 am = dc(0.0), bm = dc(0.0), ym = dc(0.0), ysq = dc(0.0);
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    am = am + b.y[c] * P.a_rk[c];
+    bm = bm + b.y[c] * P.b_rk[c];
+    ym = ym + b.y[c] * P.M[c];
+    ysq = ysq + b.y[c] * P.sqM[c];
+  }
+  D8 T25 = dpow(T, 2.5);
+  D8 A = OMEGA_A * p * (am * am) / T25;
+  D8 B = OMEGA_B * p * bm / T;
+  double a1 = A.v - B.v - B.v * B.v;
+  double a0 = -A.v * B.v;
+  double z = cubic_root(a1, a0);
+  double fz = (3.0 * z - 2.0) * z + a1;
+  D8 Z;
+  Z.v = z;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    double da1 = A.d[k] - B.d[k] - 2.0 * B.v * B.d[k];
+    double da0 = -(A.d[k] * B.v + A.v * B.d[k]);
+    Z.d[k] = -(z * da1 + da0) / fz;
+  }
+  b.rho_g = p / (Z * (R_GAS * T));
+  // liquid densities (exponential correlation) and harmonic oil mixing
+  D8 dp = p - P.p_ref;
+  D8 dT = T - P.T_ref;
+  b.rho_w = liquid_rho(P, 0, dp, dT);
+  D8 rho_lo = liquid_rho(P, 1, dp, dT);
+  D8 rho_ho = liquid_rho(P, 2, dp, dT);
+  b.rho_o = 1.0 / (b.xlo / rho_lo + b.xho / rho_ho);
+  // viscosities: liquids avisc e^{bvisc/T}, oil log-mixing, gas sqrt(M)-weighted
+  D8 invT = 1.0 / T;
+  D8 mu_w = dexp(P.ln_avisc[0] + P.bvisc[0] * invT);
+  D8 mu_o = dexp(b.xlo * (P.ln_avisc[1] + P.bvisc[1] * invT) + b.xho * (P.ln_avisc[2] + P.bvisc[2] * invT));
+  D8 lnT = dlog(T);
+  D8 num = dc(0.0);
+#pragma unroll
+  for (int c = 0; c < 6; ++c) num = num + (P.avg[c] * P.sqM[c]) * (dexp(P.bvg[c] * lnT) * b.y[c]);
+  D8 mu_g = num / ysq;
+  // relative permeabilities: Corey (exponent 2) and Stone II with k_rocw = 1
+  D8 krw = clamp01((b.Sw - P.Swc) / (1.0 - P.Swc - P.Sorw));
+  krw = krw * krw;
+  D8 krow = clamp01((1.0 - b.Sw - P.Sorw) / (1.0 - P.Swc - P.Sorw));
+  krow = krow * krow;
+  D8 krg = clamp01((b.Sg - P.Sgc) / (1.0 - P.Swc - P.Sgc));
+  krg = krg * krg;
+  D8 krog = clamp01((1.0 - b.Sg - P.Swc - P.Sorg) / (1.0 - P.Swc - P.Sorg));
+  krog = krog * krog;
+  D8 kro = (krow + krw) * (krog + krg) - krw - krg;
+  if (kro.v < 0.0) kro = dc(0.0);
+  b.lam[0] = b.rho_w * krw / mu_w;
+  b.lam[1] = b.rho_o * kro / mu_o;
+  b.lam[2] = b.rho_g * krg / mu_g;
+  // enthalpies and internal energies
+  D8 Hg[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) Hg[c] = gas_enthalpy(P, c, T);
+  b.H[0] = Hg[0] - vap_enthalpy(P, 0, T);
+  b.H[1] = b.xlo * (Hg[1] - vap_enthalpy(P, 1, T)) + b.xho * (Hg[2] - vap_enthalpy(P, 2, T));
+  D8 hg = dc(0.0);
+#pragma unroll
+  for (int c = 0; c < 6; ++c) hg = hg + b.y[c] * Hg[c];
+  b.H[2] = hg;
+  b.U[0] = b.H[0] - p / b.rho_w;
+  b.U[1] = b.H[1] - p / b.rho_o;
+  b.U[2] = b.H[2] - p / b.rho_g;
+  // porosity and solid energies
+  D8 dpr = p - P.rock_p_ref;
+  D8 dTr = T - P.rock_T_ref;
+  b.phi = phi_ref * (1.0 + P.cpor * dpr - P.ctpor * dTr + P.cptpor * (dpr * dTr));
+  b.Ur = P.cv1 * dTr + (0.5 * P.cv2) * (T * T - P.rock_T_ref * P.rock_T_ref);
+  b.Uc = P.coke_cp * (T - P.T_ref);
+  // specific weights
+  b.gam[0] = b.rho_w * (P.M[0] * P.gravity);
+  b.gam[1] = b.rho_o * (b.xlo * P.M[1] + b.xho * P.M[2]) * P.gravity;
+  b.gam[2] = b.rho_g * ym * P.gravity;
+}
+
+// Arrhenius rate of reaction r (value and u-derivatives) at coke C (dual).
+__device__ __forceinline__ D8 rate(const Params& P, int r, const Base& b, const D8& kT, const D8& phif, const D8& C) {
+  D8 pO2 = b.y[3] * b.p;
+  int kind = P.kind[r];
+  if (kind == ISC_RXN_OIL_OXIDATION) {
+    const D8& x = (P.comp[r] == 1) ? b.xlo : b.xho;
+    return kT * pO2 * (phif * b.So * b.rho_o * x);
+  } else if (kind == ISC_RXN_CRACKING) {
+    const D8& x = (P.comp[r] == 1) ? b.xlo : b.xho;
+    D8 q = C / P.coke_max;
+    D8 q2 = q * q;
+    D8 lim = 1.0 - q2 * q2 * q;
+    return kT * (phif * b.So * b.rho_o * x) * lim;
+  }
+  return kT * pO2 * C;
+}
+
+// Solve the per-cell backward-Euler coke equation g(C) = C - C^n - dt sum_R s_R r_R(C) = 0
+// by Newton on values, then dC/du = -(dg/du)/(dg/dC) at the root.
+__device__ D8 solve_coke(const Params& P, const Base& b, const D8* kT, double C_old, int* dstatus) {
+  const double dt = P.dt;
+  double C = C_old;
+  double pO2 = b.y[3].v * b.p.v;
+  double oil = b.So.v * b.rho_o.v;
+  bool ok = false;
+  double dg = 1.0;
+  for (int it = 0; it < 60; ++it) {
+    double phif = b.phi.v - C / P.coke_rho;
+    double g = C - C_old;
+    dg = 1.0;
+    for (int r = 0; r < P.nr; ++r) {
+      double s = P.stoich[r][6];
+      if (s == 0.0) continue;
+      double k = kT[r].v;
+      int kind = P.kind[r];
+      double x = (P.comp[r] == 1) ? b.xlo.v : b.xho.v;
+      double rt, drt;
+      if (kind == ISC_RXN_OIL_OXIDATION) {
+        rt = k * pO2 * (phif * oil * x);
+        drt = k * pO2 * (-1.0 / P.coke_rho) * oil * x;
+      } else if (kind == ISC_RXN_CRACKING) {
+        double q = C / P.coke_max;
+        double q4 = q * q * q * q;
+        double lim = 1.0 - q4 * q;
+        double conc = phif * oil * x;
+        rt = k * conc * lim;
+        drt = k * ((-1.0 / P.coke_rho) * oil * x * lim + conc * (-5.0 * q4 / P.coke_max));
+      } else {
+        rt = k * pO2 * C;
+        drt = k * pO2;
+      }
+      g -= dt * s * rt;
+      dg -= dt * s * drt;
+    }
+    double step = g / dg;
+    C -= step;
+    if (fabs(step) <= 1e-14 * (fabs(C) + fabs(C_old) + 1e-300)) {
+      ok = true;
+      break;
+    }
+  }
+  if (!ok || !isfinite(C)) atomicOr(dstatus, DS_COKE);
+  // u-derivative of g at fixed C
+  D8 Cc = dc(C);
+  D8 phif = b.phi - C / P.coke_rho;
+  D8 gd = dc(0.0);
+  for (int r = 0; r < P.nr; ++r) {
+    double s = P.stoich[r][6];
+    if (s == 0.0) continue;
+    gd = gd - (dt * s) * rate(P, r, b, kT[r], phif, Cc);
+  }
+  D8 out;
+  out.v = C;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) out.d[k] = -gd.d[k] / dg;
+  return out;
+}
+
+__device__ __forceinline__ void store_q(double* __restrict__ props, int n, int i, int q, const D8& x) {
+  props[(size_t)(q * 9) * n + i] = x.v;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) props[(size_t)(q * 9 + 1 + k) * n + i] = x.d[k];
+}
+
+__device__ __forceinline__ int diag_slot(const Params& P, int i) {
+  int ix = i % P.nx, iy = (i / P.nx) % P.ny, iz = i / (P.nx * P.ny);
+  return (iz > 0) + (iy > 0) + (ix > 0);
+}
+
+__global__ void __launch_bounds__(128) k_props(Params P, const double* __restrict__ u, const double* __restrict__ coke_n,
+                                               const double* __restrict__ acc_n, const double* __restrict__ phi_ref,
+                                               const int32_t* __restrict__ well_slot, const WellSlot* __restrict__ slots,
+                                               const int32_t* __restrict__ rowptr, double* __restrict__ R,
+                                               double* __restrict__ J, double* __restrict__ props,
+                                               double* __restrict__ ntot, double* __restrict__ coke_out,
+                                               int* __restrict__ dstatus) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P.n) return;
+  const int n = P.n;
+  Base b;
+  base_properties(P, u, i, phi_ref[i], b);
+  D8 kT[ISC_MAX_RXN];
+  for (int r = 0; r < P.nr; ++r) kT[r] = P.A[r] * dexp(-P.EaR[r] * (1.0 / b.T));
+  D8 C = solve_coke(P, b, kT, coke_n[i], dstatus);
+  D8 phif = b.phi - C / P.coke_rho;
+  // accumulation (moles and energy per bulk volume)
+  D8 gas = b.rho_g * b.Sg;
+  D8 oil = b.rho_o * b.So;
+  D8 acc[7];
+  acc[0] = phif * (b.rho_w * b.Sw + gas * b.y[0]);
+  acc[1] = phif * (oil * b.xlo + gas * b.y[1]);
+  acc[2] = phif * (oil * b.xho + gas * b.y[2]);
+  acc[3] = phif * (gas * b.y[3]);
+  acc[4] = phif * (gas * b.y[4]);
+  acc[5] = phif * (gas * b.y[5]);
+  acc[6] = phif * (b.rho_w * b.Sw * b.U[0] + oil * b.U[1] + gas * b.U[2]) + (1.0 - b.phi) * b.Ur + C * b.Uc;
+  double nt = 0.0;
+  for (int c = 0; c < 6; ++c) nt += fabs(acc[c].v);
+  ntot[i] = nt;
+  const double Vdt = P.V * P.inv_dt;
+  D8 Rl[8];
+#pragma unroll
+  for (int r = 0; r < 7; ++r) Rl[r] = Vdt * (acc[r] - acc_n[(size_t)r * n + i]);
+  // reactions: q_c = sum_R s_cR r_R, Q = sum_R H_R r_R
+  for (int r = 0; r < P.nr; ++r) {
+    D8 rt = rate(P, r, b, kT[r], phif, C) * P.V;
+#pragma unroll
+    for (int c = 0; c < 6; ++c)
+      if (P.stoich[r][c] != 0.0) Rl[c] = Rl[c] - P.stoich[r][c] * rt;
+    Rl[6] = Rl[6] - P.dH[r] * rt;
+  }
+  // wells
+  int sl = well_slot[i];
+  if (sl >= 0) {
+    WellSlot w = slots[sl];
+    if (w.kind == ISC_WELL_RATE_INJECTOR) {
+#pragma unroll
+      for (int r = 0; r < 7; ++r) Rl[r] = Rl[r] - w.src[r];
+    } else {
+      D8 dpw = w.bhp - b.p;
+      if (dpw.v < 0.0) {
+        D8 Qw = (w.WI * b.lam[0]) * dpw;
+        D8 Qo = (w.WI * b.lam[1]) * dpw;
+        D8 Qg = (w.WI * b.lam[2]) * dpw;
+        Rl[0] = Rl[0] - Qw;
+        Rl[1] = Rl[1] - Qo * b.xlo;
+        Rl[2] = Rl[2] - Qo * b.xho;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) Rl[c] = Rl[c] - Qg * b.y[c];
+        Rl[6] = Rl[6] - Qw * b.H[0] - Qo * b.H[1] - Qg * b.H[2];
+      }
+    }
+  }
+  D8 sy = b.y[0] + b.y[1] + b.y[2] + b.y[3] + b.y[4] + b.y[5];
+  Rl[7] = sy - 1.0;
+  // residual (block-major) and diagonal block
+  double* Jd = J + (size_t)(rowptr[i] + diag_slot(P, i)) * BB;
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    R[(size_t)i * 8 + r] = Rl[r].v;
+#pragma unroll
+    for (int k = 0; k < 8; k += 2) {
+      double2 v = make_double2(Rl[r].d[k], Rl[r].d[k + 1]);
+      *reinterpret_cast<double2*>(Jd + r * 8 + k) = v;
+    }
+  }
+  coke_out[i] = C.v;
+  // staged face quantities
+  store_q(props, n, i, Q_LW, b.lam[0]);
+  store_q(props, n, i, Q_LWH, b.lam[0] * b.H[0]);
+  store_q(props, n, i, Q_LOX_LO, b.lam[1] * b.xlo);
+  store_q(props, n, i, Q_LOX_HO, b.lam[1] * b.xho);
+  store_q(props, n, i, Q_LOH, b.lam[1] * b.H[1]);
+#pragma unroll
+  for (int c = 0; c < 6; ++c) store_q(props, n, i, Q_LGY + c, b.lam[2] * b.y[c]);
+  store_q(props, n, i, Q_LGH, b.lam[2] * b.H[2]);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) store_q(props, n, i, Q_GAM + a, b.gam[a]);
+  D8 KT = phif * (b.Sw * P.K_phase[0] + b.So * P.K_phase[1] + b.Sg * P.K_phase[2]) + (1.0 - b.phi) * P.K_rock +
+          C * P.coke_K;
+  store_q(props, n, i, Q_KT, KT);
+  bool fin = isfinite(Rl[0].v) && isfinite(Rl[6].v) && isfinite(Rl[7].v);
+  if (!fin) atomicOr(dstatus, DS_NONFINITE);
+}
+
+__global__ void __launch_bounds__(128) k_old_acc(Params P, const double* __restrict__ u, const double* __restrict__ coke,
+                                                 const double* __restrict__ phi_ref, double* __restrict__ acc_n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P.n) return;
+  const int n = P.n;
+  Base b;
+  base_properties(P, u, i, phi_ref[i], b);
+  double C = coke[i];
+  D8 phif = b.phi - C / P.coke_rho;
+  D8 gas = b.rho_g * b.Sg;
+  D8 oil = b.rho_o * b.So;
+  acc_n[0 * (size_t)n + i] = (phif * (b.rho_w * b.Sw + gas * b.y[0])).v;
+  acc_n[1 * (size_t)n + i] = (phif * (oil * b.xlo + gas * b.y[1])).v;
+  acc_n[2 * (size_t)n + i] = (phif * (oil * b.xho + gas * b.y[2])).v;
+  acc_n[3 * (size_t)n + i] = (phif * (gas * b.y[3])).v;
+  acc_n[4 * (size_t)n + i] = (phif * (gas * b.y[4])).v;
+  acc_n[5 * (size_t)n + i] = (phif * (gas * b.y[5])).v;
+  acc_n[6 * (size_t)n + i] =
+      (phif * (b.rho_w * b.Sw * b.U[0] + oil * b.U[1] + gas * b.U[2]) + (1.0 - b.phi) * b.Ur + C * b.Uc).v;
+}
+
+// ------------------------------------------------------------------ fluxes
+struct Q9 {
+  double v, d[8];
+};
+
+__device__ __forceinline__ Q9 load_q(const double* __restrict__ props, int n, int q, int cell) {
+  Q9 x;
+  x.v = __ldg(props + (size_t)(q * 9) * n + cell);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) x.d[k] = __ldg(props + (size_t)(q * 9 + 1 + k) * n + cell);
+  return x;
+}
+
+// phases carrying row r: (phase, staged quantity); count in *m
+__device__ __forceinline__ int row_phases(int r, int* ph, int* q) {
+  switch (r) {
+    case 0: ph[0] = 0; q[0] = Q_LW; ph[1] = 2; q[1] = Q_LGY + 0; return 2;
+    case 1: ph[0] = 1; q[0] = Q_LOX_LO; ph[1] = 2; q[1] = Q_LGY + 1; return 2;
+    case 2: ph[0] = 1; q[0] = Q_LOX_HO; ph[1] = 2; q[1] = Q_LGY + 2; return 2;
+    case 3: ph[0] = 2; q[0] = Q_LGY + 3; return 1;
+    case 4: ph[0] = 2; q[0] = Q_LGY + 4; return 1;
+    case 5: ph[0] = 2; q[0] = Q_LGY + 5; return 1;
+    case 6: ph[0] = 0; q[0] = Q_LWH; ph[1] = 1; q[1] = Q_LOH; ph[2] = 2; q[2] = Q_LGH; return 3;
+    default: return 0;
+  }
+}
+
+// Flux of row r out of lo into hi over one face, with d/du_lo and d/du_hi.
+__device__ __forceinline__ double face_flux(const Params& P, int r, int lo, int hi, double Tf, double Gf, double dz,
+                                            const double* __restrict__ u, const double* __restrict__ props,
+                                            double* dlo, double* dhi) {
+  const int n = P.n;
+  int ph[3], qq[3];
+  int m = row_phases(r, ph, qq);
+  double F = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) dlo[k] = dhi[k] = 0.0;
+  double plo = __ldg(u + lo), phi_ = __ldg(u + hi);
+  for (int a = 0; a < m; ++a) {
+    Q9 glo = load_q(props, n, Q_GAM + ph[a], lo);
+    Q9 ghi = load_q(props, n, Q_GAM + ph[a], hi);
+    // potential difference: the decision quantity is formed without contraction
+    double gavg = __dmul_rn(0.5, __dadd_rn(glo.v, ghi.v));
+    double dphi = __dsub_rn(__dsub_rn(plo, phi_), __dmul_rn(gavg, dz));
+    bool up_lo = dphi >= 0.0;
+    Q9 q = load_q(props, n, qq[a], up_lo ? lo : hi);
+    double tq = Tf * q.v;
+    F += tq * dphi;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      double e = (k == 0) ? 1.0 : 0.0;
+      dlo[k] += tq * (e - 0.5 * dz * glo.d[k]);
+      dhi[k] += tq * (-e - 0.5 * dz * ghi.d[k]);
+    }
+    if (up_lo) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) dlo[k] += Tf * q.d[k] * dphi;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) dhi[k] += Tf * q.d[k] * dphi;
+    }
+  }
+  if (r == 6) {
+    Q9 Klo = load_q(props, n, Q_KT, lo);
+    Q9 Khi = load_q(props, n, Q_KT, hi);
+    double s = Klo.v + Khi.v;
+    double Kh = 2.0 * Klo.v * Khi.v / s;
+    double dKlo = 2.0 * Khi.v * Khi.v / (s * s);
+    double dKhi = 2.0 * Klo.v * Klo.v / (s * s);
+    double dT = __ldg(u + (size_t)5 * n + lo) - __ldg(u + (size_t)5 * n + hi);
+    F += Gf * Kh * dT;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      double e = (k == 5) ? 1.0 : 0.0;
+      dlo[k] += Gf * (dKlo * Klo.d[k] * dT + Kh * e);
+      dhi[k] += Gf * (dKhi * Khi.d[k] * dT - Kh * e);
+    }
+  }
+  return F;
+}
+
+__global__ void __launch_bounds__(256) k_flux(Params P, const double* __restrict__ u, const double* __restrict__ props,
+                                              const double* __restrict__ tx, const double* __restrict__ ty,
+                                              const double* __restrict__ tz, const double* __restrict__ depth,
+                                              const int32_t* __restrict__ rowptr, double* __restrict__ R,
+                                              double* __restrict__ J) {
+  const int r = threadIdx.x >> 5;
+  const int i = blockIdx.x * 32 + (threadIdx.x & 31);
+  if (i >= P.n || r == 7) return;
+  const int nx = P.nx, ny = P.ny, nxy = P.nx * P.ny;
+  const int ix = i % nx, iy = (i / nx) % ny, iz = i / nxy;
+  // neighbours in BSR column order: -z, -y, -x, (diag), +x, +y, +z
+  int nb[6];
+  bool has[6] = {iz > 0, iy > 0, ix > 0, ix < nx - 1, iy < ny - 1, iz < P.nz - 1};
+  nb[0] = i - nxy;
+  nb[1] = i - nx;
+  nb[2] = i - 1;
+  nb[3] = i + 1;
+  nb[4] = i + nx;
+  nb[5] = i + nxy;
+  const int base = rowptr[i];
+  const int dslot = (int)has[0] + (int)has[1] + (int)has[2];
+  double Rsum = 0.0;
+  double dd[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) dd[k] = 0.0;
+  int slot = 0;
+  for (int f = 0; f < 6; ++f) {
+    if (f == 3) ++slot;  // skip the diagonal slot
+    if (!has[f]) continue;
+    int j = nb[f];
+    int lo = min(i, j), hi = max(i, j);
+    double Tf, Gf;
+    if (f == 2 || f == 3) {
+      Tf = tx[lo];
+      Gf = P.gx;
+    } else if (f == 1 || f == 4) {
+      Tf = ty[lo];
+      Gf = P.gy;
+    } else {
+      Tf = tz[lo];
+      Gf = P.gz;
+    }
+    double dz = depth[lo] - depth[hi];
+    double dlo[8], dhi[8];
+    double F = face_flux(P, r, lo, hi, Tf, Gf, dz, u, props, dlo, dhi);
+    const bool own_lo = (i == lo);
+    double* Jb = J + (size_t)(base + slot) * BB + r * 8;
+    if (own_lo) {
+      Rsum += F;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) dd[k] += dlo[k];
+#pragma unroll
+      for (int k = 0; k < 8; k += 2) *reinterpret_cast<double2*>(Jb + k) = make_double2(dhi[k], dhi[k + 1]);
+    } else {
+      Rsum -= F;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) dd[k] -= dhi[k];
+#pragma unroll
+      for (int k = 0; k < 8; k += 2) *reinterpret_cast<double2*>(Jb + k) = make_double2(-dlo[k], -dlo[k + 1]);
+    }
+    ++slot;
+  }
+  R[(size_t)i * 8 + r] += Rsum;
+  double* Jd = J + (size_t)(base + dslot) * BB + r * 8;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) Jd[k] += dd[k];
+}
+
+// scaled max-norms: mass |F_c|/(V N_tot), energy |F_E|/(V cv), constraint |F_GS|
+__global__ void k_norms(Params P, const double* __restrict__ R, const double* __restrict__ ntot,
+                        unsigned long long* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double em = 0.0, ee = 0.0, eg = 0.0;
+  if (i < P.n) {
+    const double* Ri = R + (size_t)i * 8;
+    double s = P.V * ntot[i];
+    for (int c = 0; c < 6; ++c) em = fmax(em, fabs(Ri[c]) / s);
+    ee = fabs(Ri[6]) / (P.V * P.cv_scale);
+    eg = fabs(Ri[7]);
+    if (!isfinite(Ri[0] + Ri[1] + Ri[2] + Ri[3] + Ri[4] + Ri[5] + Ri[6] + Ri[7])) em = ee = eg = INFINITY;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    em = fmax(em, __shfl_xor_sync(0xffffffffu, em, o));
+    ee = fmax(ee, __shfl_xor_sync(0xffffffffu, ee, o));
+    eg = fmax(eg, __shfl_xor_sync(0xffffffffu, eg, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    // non-negative doubles order like their bit patterns
+    atomicMax(out + 0, (unsigned long long)__double_as_longlong(em));
+    atomicMax(out + 1, (unsigned long long)__double_as_longlong(ee));
+    atomicMax(out + 2, (unsigned long long)__double_as_longlong(eg));
+  }
+}
+
+__global__ void k_init_equilibrium(Params P, double p0, double T0, double Sw0, double So0, double xlo0, double r0,
+                                   double r1, double r2, double* __restrict__ u, double* __restrict__ coke) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P.n) return;
+  const int n = P.n;
+  D8 p = dc(p0), T = dc(T0), Sw = dc(Sw0), So = dc(So0), xlo = dc(xlo0);
+  D8 yW = per_f(P, Sw) * k_value(P, 0, p, T);
+  D8 yLO = k_value(P, 1, p, T) * xlo;
+  D8 yHO = per_f(P, So) * k_value(P, 2, p, T) * (1.0 - xlo);
+  double rest = 1.0 - (yW.v + yLO.v + yHO.v);
+  u[0 * (size_t)n + i] = p0;
+  u[1 * (size_t)n + i] = xlo0;
+  u[2 * (size_t)n + i] = r0 * rest;
+  u[3 * (size_t)n + i] = r1 * rest;
+  u[4 * (size_t)n + i] = r2 * rest;
+  u[5 * (size_t)n + i] = T0;
+  u[6 * (size_t)n + i] = Sw0;
+  u[7 * (size_t)n + i] = 1.0 - Sw0 - So0;
+  coke[i] = 0.0;
+}
+
+}  // namespace
+
+void launch_props(Handle& h, cudaStream_t s) {
+  int tb = 128;
+  k_props<<<(h.n + tb - 1) / tb, tb, 0, s>>>(h.P, h.u, h.coke_n, h.acc_n, h.phi_ref, h.well_slot, h.slots, h.rowptr,
+                                               h.R, h.J, h.props, h.ntot, h.coke, h.dstatus);
+}
+
+void launch_flux(Handle& h, cudaStream_t s) {
+  k_flux<<<(h.n + 31) / 32, 256, 0, s>>>(h.P, h.u, h.props, h.tx, h.ty, h.tz, h.depth, h.rowptr, h.R, h.J);
+}
+
+void launch_old_accumulation(Handle& h, cudaStream_t s) {
+  int tb = 128;
+  k_old_acc<<<(h.n + tb - 1) / tb, tb, 0, s>>>(h.P, h.u_n, h.coke_n, h.phi_ref, h.acc_n);
+}
+
+void launch_norms(Handle& h, cudaStream_t s) {
+  cudaMemsetAsync(h.scal, 0, 3 * sizeof(double), s);
+  int tb = 256;
+  k_norms<<<(h.n + tb - 1) / tb, tb, 0, s>>>(h.P, h.R, h.ntot, reinterpret_cast<unsigned long long*>(h.scal));
+}
+
+void launch_init_equilibrium(Handle& h, double p0, double T0, double Sw0, double So0, double xlo0,
+                             const double* y_rest, cudaStream_t s) {
+  int tb = 128;
+  k_init_equilibrium<<<(h.n + tb - 1) / tb, tb, 0, s>>>(h.P, p0, T0, Sw0, So0, xlo0, y_rest[0], y_rest[1], y_rest[2],
+                                                         h.u, h.coke);
+}
+
+}  // namespace isc

@@ -1,0 +1,151 @@
+// Internal declarations of libisc (GB300, sm_103a). Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "isc.h"
+
+namespace isc {
+
+constexpr int NU = 8;
+constexpr int NC = 6;
+constexpr int BS = 8;
+constexpr int BB = 64;          // doubles per 8x8 block
+constexpr int NQ = 16;          // staged face quantities per cell
+constexpr int NQD = NQ * 9;     // doubles per cell in the staged buffer (value + 8 tangents)
+constexpr double R_GAS = 8.314462618;
+
+// staged face quantities (value and d/du of each, per cell)
+enum FaceQ {
+  Q_LW = 0,        // lambda_w                (water carried by the water phase)
+  Q_LWH = 1,       // lambda_w H_w
+  Q_LOX_LO = 2,    // lambda_o x_LO
+  Q_LOX_HO = 3,    // lambda_o x_HO
+  Q_LOH = 4,       // lambda_o H_o
+  Q_LGY = 5,       // lambda_g y_c, c = 0..5  -> 5..10
+  Q_LGH = 11,      // lambda_g H_g
+  Q_GAM = 12,      // gamma_w, gamma_o, gamma_g -> 12..14
+  Q_KT = 15        // bulk thermal conductivity
+};
+
+// Parameters of the discrete model, passed to kernels by value (constant bank).
+struct Params {
+  int nx, ny, nz, n;
+  double V;                   // cell volume
+  double dt, inv_dt;
+  double gx, gy, gz;          // (A/h) of x, y, z faces (conduction)
+  // fluid
+  double M[6], a_rk[6], b_rk[6], sqM[6];
+  double rho_ref[3], cp[3], ct1[3], ct2[3], cpt[3];
+  double p_ref, T_ref;
+  double cpg[6][4];
+  double hvr[3], ev[3], Tc[3];
+  double avg[6], bvg[6], ln_avisc[3], bvisc[3];
+  double kv[3][5];
+  double K_phase[3];
+  double coke_rho, coke_cp, coke_K;
+  double Swc, Sorw, Sgc, Sorg;
+  double per_eps, gravity;
+  // rock
+  double cpor, ctpor, cptpor, rock_p_ref, rock_T_ref, cv1, cv2, K_rock;
+  // reactions
+  int nr;
+  int kind[ISC_MAX_RXN];
+  int comp[ISC_MAX_RXN];
+  double stoich[ISC_MAX_RXN][7];
+  double A[ISC_MAX_RXN], EaR[ISC_MAX_RXN], dH[ISC_MAX_RXN];
+  double coke_max;
+  // convergence scaling
+  double cv_scale;            // rock volumetric heat capacity for the energy norm
+};
+
+// One well perforation slot (a cell holds at most one).
+struct WellSlot {
+  int kind;                   // ISC_WELL_*
+  double WI;
+  double bhp;                 // producer
+  double src[7];              // injector: mol/s per component and J/s
+};
+
+// device status word bits
+enum DevStatus { DS_SINGULAR = 1, DS_COKE = 2, DS_NONFINITE = 4, DS_TIMEOUT = 8 };
+
+struct KTimer {
+  cudaEvent_t a = nullptr, b = nullptr;
+};
+
+struct Handle {
+  // sizes
+  int nx = 0, ny = 0, nz = 0, n = 0, nnzb = 0, nlevels = 0;
+  Params P{};
+  isc_options opt{};
+  cudaStream_t stream = nullptr;
+  std::string last_error;
+  // host copies
+  std::vector<int32_t> h_rowptr, h_col, h_level_ptr;
+  // device: static
+  int32_t *rowptr = nullptr, *col = nullptr, *level_cells = nullptr;
+  double *phi_ref = nullptr, *depth = nullptr, *tx = nullptr, *ty = nullptr, *tz = nullptr;
+  int32_t* well_slot = nullptr;
+  WellSlot* slots = nullptr;
+  int nslots = 0;
+  // device: state
+  double *u = nullptr, *coke = nullptr;          // iterate (SoA 8N), solved coke (N)
+  double *u_n = nullptr, *coke_n = nullptr;       // accepted state
+  double* acc_n = nullptr;                        // accumulation of the accepted state (7N SoA)
+  // device: assembly
+  double* props = nullptr;                        // staged face quantities (NQD * N)
+  double* R = nullptr;                            // residual, block-major 8N
+  double* J = nullptr;                            // BSR values nnzb*64
+  double* ntot = nullptr;                         // per-cell total moles (norm scaling)
+  double* du = nullptr;                           // Newton update, block-major 8N
+  double* rhs = nullptr;                          // -F, right-hand side of the solve
+  double* dinv = nullptr;                         // preconditioner diagonal inverses N*64
+  // Krylov workspace
+  double* V = nullptr;                            // (restart+1) vectors of 8N
+  double* Z = nullptr;                            // restart preconditioned vectors
+  double* w = nullptr;
+  double* tmp = nullptr;
+  double* partial = nullptr;                      // reduction partials
+  double* scal = nullptr;                         // device scalars
+  double* h_scal = nullptr;                       // pinned host mirror
+  int* dstatus = nullptr;
+  int* h_status = nullptr;                        // pinned
+  int restart_alloc = 0;
+  int red_blocks = 0;
+  // flags
+  bool assembled = false, decoupled = false, prec_built = false, have_acc = false;
+  double last_dt = 0.0;
+  // timing
+  isc_stats stats{};
+  KTimer timers[ISC_K_COUNT];
+};
+
+// --------------------------------------------------------------- launchers
+// assembly (isc_assembly.cu)
+void launch_props(Handle& h, cudaStream_t s);
+void launch_flux(Handle& h, cudaStream_t s);
+void launch_old_accumulation(Handle& h, cudaStream_t s);
+void launch_norms(Handle& h, cudaStream_t s);
+void launch_init_equilibrium(Handle& h, double p0, double T0, double Sw0, double So0, double xlo0,
+                             const double* y_rest, cudaStream_t s);
+// linear algebra (isc_linalg.cu)
+void launch_gj(Handle& h, cudaStream_t s);
+void launch_spmv(int nrows, const int32_t* rowptr, const int32_t* col, const double* val, const double* x,
+                 double* y, int unit_diag, cudaStream_t s);
+void launch_ilu_factor(Handle& h, cudaStream_t s);
+void launch_bjacobi_factor(Handle& h, cudaStream_t s);
+void launch_prec_apply(Handle& h, const double* r, double* z, cudaStream_t s);
+void launch_update(Handle& h, cudaStream_t s);
+// BLAS-1 with fixed-order two-stage reductions; results land in h.scal[off..]
+void launch_mdot(Handle& h, const double* V, int nvec, const double* w, int off, cudaStream_t s);
+void launch_maxpy(Handle& h, double* w, const double* V, int nvec, int coef_off, double sign, cudaStream_t s);
+void launch_axpby(int n, double a, const double* x, double b, double* y, cudaStream_t s);
+void launch_scale_copy(int n, double a, const double* x, double* y, cudaStream_t s);
+void launch_axpy_dev(int n, const double* coef, double sign, const double* x, double* y, cudaStream_t s);
+
+}  // namespace isc

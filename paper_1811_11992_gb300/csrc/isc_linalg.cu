@@ -1,0 +1,527 @@
+// Linear algebra of the Newton step on the 8x8 block-sparse system.
+//
+// k_gj          Gauss-Jordan decoupling (Sec. 3.2): one warp per block row,
+//               lanes own columns of the augmented row [J_i,* | F_i], partial
+//               pivoting with warp shuffles; the diagonal block becomes I.
+// k_spmv        y = A x, one warp per block row, each lane streams one double2
+//               per 8x8 block (512 contiguous bytes per warp and block).
+// k_ilu_factor  block ILU(0) diagonal recurrence D_i = A_ii - sum_k A_ik D_k^-1 A_ki
+//               over the lower neighbours (the 7-point pattern has no other
+//               fill), hyperplane wavefront i+j+k = level, 64 threads per cell.
+// k_ilu_fwd/bwd the two triangular sweeps of the D-ILU form, 8 threads per cell.
+// BLAS-1        dot products with fixed-order two-stage reductions.
+// k_update      safeguarded Newton update (Sec. 2.2 saturation treatment).
+#include <math.h>
+
+#include "isc_internal.cuh"
+
+namespace isc {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// slot of neighbour direction d (0 -z, 1 -y, 2 -x, 3 diag, 4 +x, 5 +y, 6 +z) in the sorted BSR row
+__device__ __forceinline__ int nbr_slot(int nx, int ny, int nz, int c, int d) {
+  int ix = c % nx, iy = (c / nx) % ny, iz = c / (nx * ny);
+  bool has[7] = {iz > 0, iy > 0, ix > 0, true, ix < nx - 1, iy < ny - 1, iz < nz - 1};
+  int s = 0;
+  for (int e = 0; e < d; ++e) s += has[e];
+  return s;
+}
+
+__device__ __forceinline__ bool nbr_exists(int nx, int ny, int nz, int c, int d, int* j) {
+  int ix = c % nx, iy = (c / nx) % ny, iz = c / (nx * ny);
+  switch (d) {
+    case 0: *j = c - nx * ny; return iz > 0;
+    case 1: *j = c - nx; return iy > 0;
+    case 2: *j = c - 1; return ix > 0;
+    case 4: *j = c + 1; return ix < nx - 1;
+    case 5: *j = c + nx; return iy < ny - 1;
+    case 6: *j = c + nx * ny; return iz < nz - 1;
+    default: *j = c; return true;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_gj(int n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                            double* __restrict__ J, double* __restrict__ R, int* __restrict__ dstatus) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  const int i = warp;
+  const int b0 = rowptr[i];
+  const int nb = rowptr[i + 1] - b0;
+  int d = 0;
+  for (int s = 0; s < nb; ++s)
+    if (col[b0 + s] == i) d = s;
+  const int nc = nb * 8;
+  double a[2][8];
+#pragma unroll
+  for (int m = 0; m < 2; ++m) {
+    int cc = lane + 32 * m;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      double v = 0.0;
+      if (cc < nc)
+        v = J[(size_t)(b0 + cc / 8) * BB + r * 8 + (cc & 7)];
+      else if (cc == nc)
+        v = R[(size_t)i * 8 + r];
+      a[m][r] = v;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int pc = d * 8 + k;
+    const int pl = pc & 31, pm = pc >> 5;
+    int piv = k;
+    if (lane == pl) {
+      double best = -1.0;
+#pragma unroll
+      for (int r = k; r < 8; ++r) {
+        double v = fabs(pm ? a[1][r] : a[0][r]);
+        if (v > best) {
+          best = v;
+          piv = r;
+        }
+      }
+    }
+    piv = __shfl_sync(FULL, piv, pl);
+    // max |a| of row piv inside the diagonal block (singularity test)
+    double rm = 0.0;
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+      int cc = lane + 32 * m;
+      if (cc >= d * 8 && cc < d * 8 + 8) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+          if (r == piv) rm = fmax(rm, fabs(a[m][r]));
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rm = fmax(rm, __shfl_xor_sync(FULL, rm, o));
+    // swap rows k and piv
+    if (piv != k) {
+#pragma unroll
+      for (int m = 0; m < 2; ++m) {
+#pragma unroll
+        for (int r = k + 1; r < 8; ++r) {
+          if (r == piv) {
+            double t = a[m][r];
+            a[m][r] = a[m][k];
+            a[m][k] = t;
+          }
+        }
+      }
+    }
+    double colk[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) colk[r] = __shfl_sync(FULL, pm ? a[1][r] : a[0][r], pl);
+    const double pv = colk[k];
+    if (!(fabs(pv) > 1e-300 * fmax(rm, 1e-300))) {
+      if (lane == 0) atomicOr(dstatus, DS_SINGULAR);
+      return;
+    }
+#pragma unroll
+    for (int m = 0; m < 2; ++m) a[m][k] = a[m][k] / pv;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      if (r == k) continue;
+#pragma unroll
+      for (int m = 0; m < 2; ++m) a[m][r] = a[m][r] - colk[r] * a[m][k];
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < 2; ++m) {
+    int cc = lane + 32 * m;
+    if (cc < nc) {
+      int s = cc / 8, c = cc & 7;
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        double v = (s == d) ? (r == c ? 1.0 : 0.0) : a[m][r];
+        J[(size_t)(b0 + s) * BB + r * 8 + c] = v;
+      }
+    } else if (cc == nc) {
+#pragma unroll
+      for (int r = 0; r < 8; ++r) R[(size_t)i * 8 + r] = a[m][r];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_spmv(int n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                              const double* __restrict__ val, const double* __restrict__ x,
+                                              double* __restrict__ y, int unit_diag) {
+  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  const int b0 = __ldg(rowptr + row), b1 = __ldg(rowptr + row + 1);
+  const int r = lane >> 2, c = (lane & 3) * 2;
+  double acc = 0.0;
+#pragma unroll 7
+  for (int b = b0; b < b1; ++b) {
+    int j = __ldg(col + b);
+    if (unit_diag && j == row) continue;
+    double2 v = __ldg(reinterpret_cast<const double2*>(val + (size_t)b * BB) + lane);
+    double2 xv = __ldg(reinterpret_cast<const double2*>(x + (size_t)j * 8 + c));
+    acc = fma(v.x, xv.x, acc);
+    acc = fma(v.y, xv.y, acc);
+  }
+  acc += __shfl_xor_sync(FULL, acc, 1);
+  acc += __shfl_xor_sync(FULL, acc, 2);
+  if ((lane & 3) == 0) y[(size_t)row * 8 + r] = acc + (unit_diag ? x[(size_t)row * 8 + r] : 0.0);
+}
+
+// ---------------------------------------------------------- block ILU(0)
+constexpr int FCELLS = 4;  // cells per 256-thread block in the factorisation
+
+__global__ void __launch_bounds__(256) k_ilu_factor(int nx, int ny, int nz, const int32_t* __restrict__ cells, int count,
+                                                    int use_lower, const int32_t* __restrict__ rowptr,
+                                                    const double* __restrict__ A, double* __restrict__ Dinv,
+                                                    int* __restrict__ dstatus) {
+  __shared__ double sD[FCELLS][64], sI[FCELLS][64], sL[FCELLS][64], sU[FCELLS][64], sM[FCELLS][64];
+  __shared__ int spiv[FCELLS];
+  __shared__ int sbad[FCELLS];
+  const int g = threadIdx.x >> 6;
+  const int t = threadIdx.x & 63;
+  const int r = t >> 3, c = t & 7;
+  const int ci = blockIdx.x * FCELLS + g;
+  const bool active = ci < count;
+  const int i = active ? cells[ci] : 0;
+  if (active) {
+    sD[g][t] = A[(size_t)(rowptr[i] + nbr_slot(nx, ny, nz, i, 3)) * BB + t];
+    sI[g][t] = (r == c) ? 1.0 : 0.0;
+  }
+  if (t == 0) sbad[g] = 0;
+  __syncthreads();
+  if (use_lower) {
+    for (int dlow = 0; dlow < 3; ++dlow) {
+      int k = 0;
+      bool ex = active && nbr_exists(nx, ny, nz, i, dlow, &k);
+      if (ex) {
+        sL[g][t] = A[(size_t)(rowptr[i] + nbr_slot(nx, ny, nz, i, dlow)) * BB + t];
+        sU[g][t] = A[(size_t)(rowptr[k] + nbr_slot(nx, ny, nz, k, 6 - dlow)) * BB + t];
+        sM[g][t] = Dinv[(size_t)k * BB + t];
+      }
+      __syncthreads();
+      double m = 0.0;
+      if (ex) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) m = fma(sM[g][r * 8 + q], sU[g][q * 8 + c], m);
+      }
+      __syncthreads();
+      if (ex) sM[g][t] = m;  // M = D_k^-1 A_ki
+      __syncthreads();
+      if (ex) {
+        double s = 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) s = fma(sL[g][r * 8 + q], sM[g][q * 8 + c], s);
+        sD[g][t] -= s;
+      }
+      __syncthreads();
+    }
+  }
+  // invert D by Gauss-Jordan with partial pivoting
+  for (int k = 0; k < 8; ++k) {
+    if (t == 0 && active) {
+      int piv = k;
+      double best = -1.0;
+      for (int q = k; q < 8; ++q) {
+        double v = fabs(sD[g][q * 8 + k]);
+        if (v > best) {
+          best = v;
+          piv = q;
+        }
+      }
+      spiv[g] = piv;
+      if (!(best > 0.0) || !isfinite(best)) sbad[g] = 1;
+    }
+    __syncthreads();
+    const int piv = spiv[g];
+    if (active && r == k && piv != k) {
+      double t1 = sD[g][k * 8 + c];
+      sD[g][k * 8 + c] = sD[g][piv * 8 + c];
+      sD[g][piv * 8 + c] = t1;
+      t1 = sI[g][k * 8 + c];
+      sI[g][k * 8 + c] = sI[g][piv * 8 + c];
+      sI[g][piv * 8 + c] = t1;
+    }
+    __syncthreads();
+    double pv = sD[g][k * 8 + k];
+    double f = sD[g][r * 8 + k];
+    __syncthreads();
+    if (active && r == k && !sbad[g]) {
+      sD[g][k * 8 + c] /= pv;
+      sI[g][k * 8 + c] /= pv;
+    }
+    __syncthreads();
+    if (active && r != k && !sbad[g]) {
+      sD[g][r * 8 + c] -= f * sD[g][k * 8 + c];
+      sI[g][r * 8 + c] -= f * sI[g][k * 8 + c];
+    }
+    __syncthreads();
+  }
+  if (active) {
+    if (sbad[g]) {
+      if (t == 0) atomicOr(dstatus, DS_SINGULAR);
+    } else {
+      Dinv[(size_t)i * BB + t] = sI[g][t];
+    }
+  }
+}
+
+// forward sweep of the D-ILU form: y_i = D_i^-1 (r_i - sum_{k<i} A_ik y_k)
+__global__ void __launch_bounds__(256) k_ilu_fwd(int nx, int ny, int nz, const int32_t* __restrict__ cells, int count,
+                                                 const int32_t* __restrict__ rowptr, const double* __restrict__ A,
+                                                 const double* __restrict__ Dinv, const double* __restrict__ rhs,
+                                                 double* __restrict__ y) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int ci = tid >> 3;
+  const int r = threadIdx.x & 7;
+  const bool active = ci < count;
+  const int i = active ? cells[ci] : 0;
+  double t = 0.0;
+  if (active) {
+    t = rhs[(size_t)i * 8 + r];
+    for (int dl = 0; dl < 3; ++dl) {
+      int k;
+      if (!nbr_exists(nx, ny, nz, i, dl, &k)) continue;
+      const double* Ab = A + (size_t)(rowptr[i] + nbr_slot(nx, ny, nz, i, dl)) * BB + r * 8;
+#pragma unroll
+      for (int m = 0; m < 8; ++m) t -= Ab[m] * y[(size_t)k * 8 + m];
+    }
+  }
+  double out = 0.0;
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    double tm = __shfl_sync(FULL, t, m, 8);
+    if (active) out = fma(Dinv[(size_t)i * BB + r * 8 + m], tm, out);
+  }
+  if (active) y[(size_t)i * 8 + r] = out;
+}
+
+// backward sweep: z_i = y_i - D_i^-1 sum_{j>i} A_ij z_j
+__global__ void __launch_bounds__(256) k_ilu_bwd(int nx, int ny, int nz, const int32_t* __restrict__ cells, int count,
+                                                 const int32_t* __restrict__ rowptr, const double* __restrict__ A,
+                                                 const double* __restrict__ Dinv, const double* __restrict__ y,
+                                                 double* __restrict__ z) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int ci = tid >> 3;
+  const int r = threadIdx.x & 7;
+  const bool active = ci < count;
+  const int i = active ? cells[ci] : 0;
+  double s = 0.0;
+  if (active) {
+    for (int du = 4; du < 7; ++du) {
+      int j;
+      if (!nbr_exists(nx, ny, nz, i, du, &j)) continue;
+      const double* Ab = A + (size_t)(rowptr[i] + nbr_slot(nx, ny, nz, i, du)) * BB + r * 8;
+#pragma unroll
+      for (int m = 0; m < 8; ++m) s += Ab[m] * z[(size_t)j * 8 + m];
+    }
+  }
+  double out = 0.0;
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    double sm = __shfl_sync(FULL, s, m, 8);
+    if (active) out = fma(Dinv[(size_t)i * BB + r * 8 + m], sm, out);
+  }
+  if (active) z[(size_t)i * 8 + r] = y[(size_t)i * 8 + r] - out;
+}
+
+__global__ void k_bjacobi_apply(int n, const double* __restrict__ Dinv, const double* __restrict__ rhs,
+                                double* __restrict__ z) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = tid >> 3, r = threadIdx.x & 7;
+  double v = (i < n) ? rhs[(size_t)i * 8 + r] : 0.0;
+  double out = 0.0;
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    double vm = __shfl_sync(FULL, v, m, 8);
+    if (i < n) out = fma(Dinv[(size_t)i * BB + r * 8 + m], vm, out);
+  }
+  if (i < n) z[(size_t)i * 8 + r] = out;
+}
+
+// ------------------------------------------------------------------ BLAS-1
+constexpr int RED_THREADS = 256;
+
+// partial[c * nblk + blk] = sum over the block's chunk of V_c . w
+__global__ void __launch_bounds__(RED_THREADS) k_mdot_partial(int len, const double* __restrict__ V, size_t vstride,
+                                                              const double* __restrict__ w, double* __restrict__ partial) {
+  const int c = blockIdx.y;
+  const double* v = V + (size_t)c * vstride;
+  double s = 0.0;
+  const int stride = gridDim.x * blockDim.x;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) s = fma(v[e], w[e], s);
+  __shared__ double sh[RED_THREADS / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < RED_THREADS / 32) ? sh[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+    if (threadIdx.x == 0) partial[(size_t)c * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+__global__ void k_mdot_final(int nblk, const double* __restrict__ partial, double* __restrict__ out) {
+  const int c = blockIdx.x;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += 32) s += partial[(size_t)c * nblk + b];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+  if (threadIdx.x == 0) out[c] = s;
+}
+
+// w += sign * sum_c coef[c] V_c
+__global__ void k_maxpy(int len, double* __restrict__ w, const double* __restrict__ V, size_t vstride, int nvec,
+                        const double* __restrict__ coef, double sign) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) {
+    double s = 0.0;
+    for (int c = 0; c < nvec; ++c) s = fma(coef[c], V[(size_t)c * vstride + e], s);
+    w[e] = fma(sign, s, w[e]);
+  }
+}
+
+__global__ void k_axpby(int len, double a, const double* __restrict__ x, double b, double* __restrict__ y) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) y[e] = a * x[e] + b * y[e];
+}
+
+__global__ void k_scale_copy(int len, double a, const double* __restrict__ x, double* __restrict__ y) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) y[e] = a * x[e];
+}
+
+// y += sign * (*coef) * x with the coefficient read on the device
+__global__ void k_axpy_dev(int len, const double* __restrict__ coef, double sign, const double* __restrict__ x,
+                           double* __restrict__ y) {
+  const double a = sign * coef[0];
+  const int stride = gridDim.x * blockDim.x;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) y[e] = fma(a, x[e], y[e]);
+}
+
+// ------------------------------------------------------------ Newton update
+__global__ void k_update(int n, double* __restrict__ u, const double* __restrict__ du, double max_dp_frac,
+                         double max_dT) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double uo[8], d[8], un[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    uo[k] = u[(size_t)k * n + i];
+    d[k] = du[(size_t)i * 8 + k];
+  }
+  const double p = uo[0];
+  un[0] = p + fmin(fmax(d[0], -max_dp_frac * p), max_dp_frac * p);
+  un[5] = uo[5] + fmin(fmax(d[5], -max_dT), max_dT);
+  double x = uo[1] + d[1];
+  if (x < 0.0) x = 0.5 * uo[1];
+  if (x > 1.0) x = 1.0 - 0.5 * (1.0 - uo[1]);
+  un[1] = x;
+  const int ks[5] = {2, 3, 4, 6, 7};
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    int k = ks[q];
+    double v = uo[k] + d[k];
+    un[k] = (v < 0.0) ? 0.5 * uo[k] : v;
+  }
+  const double so_old = 1.0 - uo[6] - uo[7];
+  const double so_new = 1.0 - un[6] - un[7];
+  if (so_new < 0.0) {
+    double target = 1.0 - 0.5 * so_old;
+    double s = un[6] + un[7];
+    un[6] *= target / s;
+    un[7] *= target / s;
+  }
+#pragma unroll
+  for (int k = 0; k < 8; ++k) u[(size_t)k * n + i] = un[k];
+}
+
+int grid_for(size_t work, int tb) {
+  size_t b = (work + tb - 1) / tb;
+  if (b > 152 * 16) b = 152 * 16;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+}  // namespace
+
+void launch_gj(Handle& h, cudaStream_t s) {
+  int tb = 256;
+  k_gj<<<(h.n * 32 + tb - 1) / tb, tb, 0, s>>>(h.n, h.rowptr, h.col, h.J, h.R, h.dstatus);
+}
+
+void launch_spmv(int nrows, const int32_t* rowptr, const int32_t* col, const double* val, const double* x, double* y,
+                 int unit_diag, cudaStream_t s) {
+  int tb = 256;
+  k_spmv<<<(int)(((size_t)nrows * 32 + tb - 1) / tb), tb, 0, s>>>(nrows, rowptr, col, val, x, y, unit_diag);
+}
+
+void launch_ilu_factor(Handle& h, cudaStream_t s) {
+  for (int L = 0; L < h.nlevels; ++L) {
+    int b = h.h_level_ptr[L], cnt = h.h_level_ptr[L + 1] - b;
+    k_ilu_factor<<<(cnt + FCELLS - 1) / FCELLS, 256, 0, s>>>(h.nx, h.ny, h.nz, h.level_cells + b, cnt, 1, h.rowptr,
+                                                               h.J, h.dinv, h.dstatus);
+  }
+}
+
+void launch_bjacobi_factor(Handle& h, cudaStream_t s) {
+  // all cells at once, no lower-neighbour terms; level_cells holds every cell
+  k_ilu_factor<<<(h.n + FCELLS - 1) / FCELLS, 256, 0, s>>>(h.nx, h.ny, h.nz, h.level_cells, h.n, 0, h.rowptr, h.J,
+                                                           h.dinv, h.dstatus);
+}
+
+void launch_prec_apply(Handle& h, const double* r, double* z, cudaStream_t s) {
+  const int len = h.n * 8;
+  if (h.opt.prec == ISC_PREC_NONE) {
+    cudaMemcpyAsync(z, r, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
+    return;
+  }
+  if (h.opt.prec == ISC_PREC_BJACOBI) {
+    k_bjacobi_apply<<<(h.n * 8 + 255) / 256, 256, 0, s>>>(h.n, h.dinv, r, z);
+    return;
+  }
+  for (int L = 0; L < h.nlevels; ++L) {
+    int b = h.h_level_ptr[L], cnt = h.h_level_ptr[L + 1] - b;
+    k_ilu_fwd<<<(cnt * 8 + 255) / 256, 256, 0, s>>>(h.nx, h.ny, h.nz, h.level_cells + b, cnt, h.rowptr, h.J, h.dinv, r,
+                                                    h.tmp);
+  }
+  for (int L = h.nlevels - 1; L >= 0; --L) {
+    int b = h.h_level_ptr[L], cnt = h.h_level_ptr[L + 1] - b;
+    k_ilu_bwd<<<(cnt * 8 + 255) / 256, 256, 0, s>>>(h.nx, h.ny, h.nz, h.level_cells + b, cnt, h.rowptr, h.J, h.dinv,
+                                                    h.tmp, z);
+  }
+}
+
+void launch_update(Handle& h, cudaStream_t s) {
+  k_update<<<(h.n + 127) / 128, 128, 0, s>>>(h.n, h.u, h.du, h.opt.max_dp_frac, h.opt.max_dT);
+}
+
+void launch_mdot(Handle& h, const double* V, int nvec, const double* w, int off, cudaStream_t s) {
+  const int len = h.n * 8;
+  dim3 grid(h.red_blocks, nvec);
+  k_mdot_partial<<<grid, RED_THREADS, 0, s>>>(len, V, (size_t)len, w, h.partial);
+  k_mdot_final<<<nvec, 32, 0, s>>>(h.red_blocks, h.partial, h.scal + off);
+}
+
+void launch_maxpy(Handle& h, double* w, const double* V, int nvec, int coef_off, double sign, cudaStream_t s) {
+  const int len = h.n * 8;
+  k_maxpy<<<grid_for(len, 256), 256, 0, s>>>(len, w, V, (size_t)len, nvec, h.scal + coef_off, sign);
+}
+
+void launch_axpby(int n, double a, const double* x, double b, double* y, cudaStream_t s) {
+  k_axpby<<<grid_for(n, 256), 256, 0, s>>>(n, a, x, b, y);
+}
+
+void launch_scale_copy(int n, double a, const double* x, double* y, cudaStream_t s) {
+  k_scale_copy<<<grid_for(n, 256), 256, 0, s>>>(n, a, x, y);
+}
+
+void launch_axpy_dev(int n, const double* coef, double sign, const double* x, double* y, cudaStream_t s) {
+  k_axpy_dev<<<grid_for(n, 256), 256, 0, s>>>(n, coef, sign, x, y);
+}
+
+}  // namespace isc

@@ -1,0 +1,394 @@
+"""Python binding of the libisc C ABI (include/isc.h): argument marshalling only.
+
+Every computation runs in libisc's CUDA kernels. There is no CPU fallback:
+loading fails loudly if the library has not been built (``build.build()``)
+or no CUDA device is available when a handle is created.
+
+Array conventions on this side: the state ``u`` is (8, N) (SoA, rows p, x_LO,
+y_O2, y_N2, y_CO2, T, S_w, S_g); residuals and Newton updates are returned as
+(8, N) as well (the library's block-major layout transposed); Jacobian blocks
+are (nnzb, 8, 8) with val[b][r][c] = dF_r/du_c.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from .build import LIB
+
+c_double_p = C.POINTER(C.c_double)
+c_int32_p = C.POINTER(C.c_int32)
+
+ISC_OK = 0
+STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "out of device memory",
+          -4: "singular diagonal block", -5: "Krylov solver did not converge",
+          -6: "Newton did not converge", -7: "non-finite value", -8: "coke equation did not converge",
+          -9: "device wait timed out", -10: "not implemented", -11: "call order violated"}
+KRYLOV = {"gmres": 0, "bicgstab": 1}
+PREC = {"none": 0, "bjacobi": 1, "bilu0": 2, "ilu0": 2}
+K_CLASSES = ("props", "flux", "norm", "gj", "ilu_factor", "spmv", "prec_apply", "blas1", "update")
+
+
+class isc_grid(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double), ("depth", c_double_p)]
+
+
+class isc_rock(C.Structure):
+    _fields_ = [("phi_ref", c_double_p), ("perm", c_double_p)] + [
+        (k, C.c_double) for k in ("cpor", "ctpor", "cptpor", "p_ref", "T_ref", "cv1", "cv2", "K_rock")]
+
+
+D6 = C.c_double * 6
+D3 = C.c_double * 3
+
+
+class isc_fluid(C.Structure):
+    _fields_ = [("M", D6), ("pc", D6), ("Tc", D6),
+                ("rho_ref", D3), ("cp", D3), ("ct1", D3), ("ct2", D3), ("cpt", D3),
+                ("p_ref", C.c_double), ("T_ref", C.c_double),
+                ("cpg", (C.c_double * 4) * 6), ("hvr", D3), ("ev", D3),
+                ("avg", D6), ("bvg", D6), ("avisc", D3), ("bvisc", D3),
+                ("kv", (C.c_double * 5) * 3), ("K_phase", D3),
+                ("coke_rho", C.c_double), ("coke_cp", C.c_double), ("coke_K", C.c_double), ("coke_M", C.c_double),
+                ("Swc", C.c_double), ("Sorw", C.c_double), ("Sgc", C.c_double), ("Sorg", C.c_double),
+                ("per_eps", C.c_double), ("gravity", C.c_double)]
+
+
+class isc_reactions(C.Structure):
+    _fields_ = [("nr", C.c_int32), ("kind", C.c_int32 * 8), ("comp", C.c_int32 * 8),
+                ("stoich", (C.c_double * 7) * 8), ("A", C.c_double * 8), ("Ea", C.c_double * 8),
+                ("dH", C.c_double * 8), ("coke_max", C.c_double)]
+
+
+class isc_well(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("n_perf", C.c_int32), ("cells", c_int32_p), ("WI", c_double_p),
+                ("target", C.c_double), ("inj_y", D6), ("inj_T", C.c_double), ("inj_phase", C.c_int32)]
+
+
+class isc_wells(C.Structure):
+    _fields_ = [("nw", C.c_int32), ("wells", C.POINTER(isc_well))]
+
+
+class isc_options(C.Structure):
+    _fields_ = [("krylov", C.c_int32), ("restart", C.c_int32), ("prec", C.c_int32), ("decouple", C.c_int32),
+                ("tol_lin", C.c_double), ("maxit_lin", C.c_int32), ("tol_newton", C.c_double),
+                ("maxit_newton", C.c_int32), ("max_dp_frac", C.c_double), ("max_dT", C.c_double),
+                ("profile", C.c_int32), ("stream", C.c_void_p)]
+
+
+class isc_newton_info(C.Structure):
+    _fields_ = [("status", C.c_int32), ("converged", C.c_int32), ("norm", C.c_double),
+                ("norm_mass", C.c_double), ("norm_energy", C.c_double), ("norm_gs", C.c_double),
+                ("krylov_iterations", C.c_int32), ("krylov_rel_residual", C.c_double)]
+
+
+class isc_step_info(C.Structure):
+    _fields_ = [("status", C.c_int32), ("newton_iterations", C.c_int32), ("krylov_iterations", C.c_int32),
+                ("final_norm", C.c_double)]
+
+
+class isc_stats(C.Structure):
+    _fields_ = [("ms", C.c_double * 9), ("launches", C.c_int64 * 9), ("calls", C.c_int64 * 9)]
+
+
+_lib = None
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "isc_create": (C.c_int, [C.POINTER(isc_grid), C.POINTER(isc_rock), C.POINTER(isc_fluid),
+                             C.POINTER(isc_reactions), C.POINTER(isc_wells), C.POINTER(isc_options),
+                             C.POINTER(C.c_void_p)]),
+    "isc_destroy": (None, [C.c_void_p]),
+    "isc_set_options": (C.c_int, [C.c_void_p, C.POINTER(isc_options)]),
+    "isc_default_options": (None, [C.POINTER(isc_options)]),
+    "isc_status_string": (C.c_char_p, [C.c_int]),
+    "isc_last_error": (C.c_char_p, [C.c_void_p]),
+    "isc_num_cells": (C.c_int32, [C.c_void_p]),
+    "isc_nnzb": (C.c_int32, [C.c_void_p]),
+    "isc_init_equilibrium": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
+                                       c_double_p, C.c_int32, c_int32_p, C.c_double]),
+    "isc_set_state": (C.c_int, [C.c_void_p, c_double_p, c_double_p]),
+    "isc_get_state": (C.c_int, [C.c_void_p, c_double_p, c_double_p]),
+    "isc_set_state_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "isc_get_state_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "isc_begin_step": (C.c_int, [C.c_void_p]),
+    "isc_assemble": (C.c_int, [C.c_void_p, C.c_double]),
+    "isc_decouple": (C.c_int, [C.c_void_p]),
+    "isc_solve": (C.c_int, [C.c_void_p, C.POINTER(isc_newton_info)]),
+    "isc_update": (C.c_int, [C.c_void_p]),
+    "isc_newton_step": (C.c_int, [C.c_void_p, C.c_double, C.POINTER(isc_newton_info)]),
+    "isc_timestep": (C.c_int, [C.c_void_p, C.c_double, C.POINTER(isc_step_info)]),
+    "isc_get_residual": (C.c_int, [C.c_void_p, c_double_p]),
+    "isc_get_jacobian_bsr": (C.c_int, [C.c_void_p, c_int32_p, c_int32_p, c_double_p]),
+    "isc_get_update": (C.c_int, [C.c_void_p, c_double_p]),
+    "isc_get_coke": (C.c_int, [C.c_void_p, c_double_p]),
+    "isc_spmv": (C.c_int, [C.c_void_p, c_double_p, c_double_p]),
+    "isc_build_preconditioner": (C.c_int, [C.c_void_p]),
+    "isc_precond_apply": (C.c_int, [C.c_void_p, c_double_p, c_double_p]),
+    "isc_get_stats": (C.c_int, [C.c_void_p, C.POINTER(isc_stats)]),
+    "isc_reset_stats": (C.c_int, [C.c_void_p]),
+    "isc_bsr_spmv_device": (C.c_int, [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.c_int32, C.c_void_p]),
+    "isc_adjoint": (C.c_int, [C.c_void_p]),
+}
+
+
+def load_library(path: str = LIB):
+    """Load libisc.so and declare every exported entry point."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libisc is not built ({path} missing): run paper_1811_11992_gb300.build.build()")
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class IscError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)} ({status}): {msg}")
+        self.status = status
+
+
+def _dp(a):
+    return a.ctypes.data_as(c_double_p)
+
+
+def _ip(a):
+    return a.ctypes.data_as(c_int32_p)
+
+
+def default_options(**kw) -> isc_options:
+    lib = load_library()
+    o = isc_options()
+    lib.isc_default_options(C.byref(o))
+    for k, v in kw.items():
+        if k == "krylov":
+            v = KRYLOV[v] if isinstance(v, str) else v
+        if k == "prec":
+            v = PREC[v] if isinstance(v, str) else v
+        setattr(o, k, v)
+    return o
+
+
+def _fill(arr, values):
+    flat = np.asarray(values, dtype=np.float64).reshape(-1)
+    C.memmove(C.addressof(arr), flat.ctypes.data, flat.nbytes)
+
+
+class Simulator:
+    """A libisc handle built from an ``isc_inputs.Case``."""
+
+    def __init__(self, case, options: isc_options | None = None, **opt_kw):
+        lib = load_library()
+        self.lib = lib
+        self.case = case
+        n = case.n
+        self.n = n
+        self._keep = []
+        g = isc_grid(case.nx, case.ny, case.nz, case.dx, case.dy, case.dz,
+                     _dp(self._k(np.ascontiguousarray(case.depth, np.float64))))
+        r = case.rock
+        rock = isc_rock(_dp(self._k(np.ascontiguousarray(case.phi_ref, np.float64))),
+                        _dp(self._k(np.ascontiguousarray(case.perm, np.float64).reshape(-1))),
+                        r["cpor"], r["ctpor"], r["cptpor"], r["p_ref"], r["T_ref"], r["cv1"], r["cv2"], r["K_rock"])
+        fl = isc_fluid()
+        f = case.fluid
+        for k in ("M", "pc", "Tc", "rho_ref", "cp", "ct1", "ct2", "cpt", "cpg", "hvr", "ev", "avg", "bvg",
+                  "avisc", "bvisc", "kv", "K_phase"):
+            _fill(getattr(fl, k), f[k])
+        for k in ("p_ref", "T_ref", "coke_rho", "coke_cp", "coke_K", "coke_M", "Swc", "Sorw", "Sgc", "Sorg",
+                  "per_eps", "gravity"):
+            setattr(fl, k, float(f[k]))
+        rx = isc_reactions()
+        x = case.reactions
+        rx.nr = int(x["nr"])
+        for i in range(rx.nr):
+            rx.kind[i] = int(x["kind"][i])
+            rx.comp[i] = int(x["comp"][i])
+            rx.A[i] = float(x["A"][i])
+            rx.Ea[i] = float(x["Ea"][i])
+            rx.dH[i] = float(x["dH"][i])
+            for c in range(7):
+                rx.stoich[i][c] = float(x["stoich"][i][c])
+        rx.coke_max = float(x["coke_max"])
+        wl = (isc_well * max(1, len(case.wells)))()
+        for i, w in enumerate(case.wells):
+            cells = self._k(np.ascontiguousarray(w.cells, np.int32))
+            WI = self._k(np.ascontiguousarray(w.WI, np.float64))
+            wl[i].kind = int(w.kind)
+            wl[i].n_perf = len(cells)
+            wl[i].cells = _ip(cells)
+            wl[i].WI = _dp(WI)
+            wl[i].target = float(w.target)
+            _fill(wl[i].inj_y, w.inj_y)
+            wl[i].inj_T = float(w.inj_T)
+            wl[i].inj_phase = int(getattr(w, "inj_phase", 2))
+        wells = isc_wells(len(case.wells), wl)
+        if options is None:
+            options = default_options(**opt_kw)
+        self.options = options
+        h = C.c_void_p()
+        st = lib.isc_create(C.byref(g), C.byref(rock), C.byref(fl), C.byref(rx), C.byref(wells),
+                            C.byref(options), C.byref(h))
+        self._keep = []
+        if st != ISC_OK:
+            raise IscError(st, "isc_create failed")
+        self.h = h
+        self.nnzb = lib.isc_nnzb(h)
+
+    def _k(self, a):
+        self._keep.append(a)
+        return a
+
+    def _check(self, st):
+        if st != ISC_OK:
+            raise IscError(st, self.lib.isc_last_error(self.h).decode())
+        return st
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.isc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------- options
+    def set_options(self, **kw):
+        for k, v in kw.items():
+            if k == "krylov":
+                v = KRYLOV[v] if isinstance(v, str) else v
+            if k == "prec":
+                v = PREC[v] if isinstance(v, str) else v
+            setattr(self.options, k, v)
+        self._check(self.lib.isc_set_options(self.h, C.byref(self.options)))
+
+    # --------------------------------------------------------------- state
+    def init_equilibrium(self):
+        ini = self.case.init
+        yr = np.ascontiguousarray(ini["y_rest"], np.float64)
+        ign = np.ascontiguousarray(self.case.ignited, np.int32)
+        self._check(self.lib.isc_init_equilibrium(self.h, ini["p"], ini["T"], ini["Sw"], ini["So"], ini["x_LO"],
+                                                  _dp(yr), len(ign), _ip(ign), ini["T_ignite"]))
+
+    def set_state(self, u, coke=None):
+        u = np.ascontiguousarray(u, np.float64).reshape(8, self.n)
+        cp = None if coke is None else _dp(np.ascontiguousarray(coke, np.float64))
+        cc = None if coke is None else np.ascontiguousarray(coke, np.float64)
+        self._check(self.lib.isc_set_state(self.h, _dp(u), None if cc is None else _dp(cc)))
+
+    def get_state(self):
+        u = np.empty((8, self.n))
+        coke = np.empty(self.n)
+        self._check(self.lib.isc_get_state(self.h, _dp(u), _dp(coke)))
+        return u, coke
+
+    def begin_step(self):
+        self._check(self.lib.isc_begin_step(self.h))
+
+    # ------------------------------------------------------------ hot path
+    def assemble(self, dt):
+        self._check(self.lib.isc_assemble(self.h, float(dt)))
+
+    def decouple(self):
+        self._check(self.lib.isc_decouple(self.h))
+
+    def solve(self):
+        info = isc_newton_info()
+        self._check(self.lib.isc_solve(self.h, C.byref(info)))
+        return info
+
+    def update(self):
+        self._check(self.lib.isc_update(self.h))
+
+    def newton_step(self, dt, check=True):
+        info = isc_newton_info()
+        st = self.lib.isc_newton_step(self.h, float(dt), C.byref(info))
+        if check:
+            self._check(st)
+        return info
+
+    def timestep(self, dt, check=True):
+        info = isc_step_info()
+        st = self.lib.isc_timestep(self.h, float(dt), C.byref(info))
+        if check:
+            self._check(st)
+        return info
+
+    # ------------------------------------------------------------- exports
+    def residual(self):
+        F = np.empty((self.n, 8))
+        self._check(self.lib.isc_get_residual(self.h, _dp(F)))
+        return F.T.copy()
+
+    def jacobian(self):
+        rowptr = np.empty(self.n + 1, np.int32)
+        col = np.empty(self.nnzb, np.int32)
+        val = np.empty((self.nnzb, 8, 8))
+        self._check(self.lib.isc_get_jacobian_bsr(self.h, _ip(rowptr), _ip(col), _dp(val)))
+        return rowptr, col, val
+
+    def newton_update(self):
+        du = np.empty((self.n, 8))
+        self._check(self.lib.isc_get_update(self.h, _dp(du)))
+        return du.T.copy()
+
+    def coke(self):
+        c = np.empty(self.n)
+        self._check(self.lib.isc_get_coke(self.h, _dp(c)))
+        return c
+
+    def spmv(self, x):
+        """y = A x for x given as (8, N)."""
+        xb = np.ascontiguousarray(np.asarray(x, np.float64).reshape(8, self.n).T)
+        y = np.empty((self.n, 8))
+        self._check(self.lib.isc_spmv(self.h, _dp(xb), _dp(y)))
+        return y.T.copy()
+
+    def build_preconditioner(self):
+        self._check(self.lib.isc_build_preconditioner(self.h))
+
+    def precond_apply(self, r):
+        rb = np.ascontiguousarray(np.asarray(r, np.float64).reshape(8, self.n).T)
+        z = np.empty((self.n, 8))
+        self._check(self.lib.isc_precond_apply(self.h, _dp(rb), _dp(z)))
+        return z.T.copy()
+
+    def stats(self):
+        s = isc_stats()
+        self._check(self.lib.isc_get_stats(self.h, C.byref(s)))
+        return {k: dict(ms=s.ms[i], launches=s.launches[i], calls=s.calls[i]) for i, k in enumerate(K_CLASSES)}
+
+    def reset_stats(self):
+        self._check(self.lib.isc_reset_stats(self.h))
+
+    def set_state_device(self, d_u, d_coke=None):
+        self._check(self.lib.isc_set_state_device(self.h, C.c_void_p(d_u), C.c_void_p(d_coke) if d_coke else None))
+
+    def get_state_device(self, d_u, d_coke=None):
+        self._check(self.lib.isc_get_state_device(self.h, C.c_void_p(d_u), C.c_void_p(d_coke) if d_coke else None))
+
+
+def bsr_spmv_device(nrows, d_rowptr, d_col, d_val, d_x, d_y, unit_diag=0, stream=None):
+    lib = load_library()
+    st = lib.isc_bsr_spmv_device(nrows, C.c_void_p(d_rowptr), C.c_void_p(d_col), C.c_void_p(d_val),
+                                 C.c_void_p(d_x), C.c_void_p(d_y), unit_diag, C.c_void_p(stream) if stream else None)
+    if st != ISC_OK:
+        raise IscError(st, "isc_bsr_spmv_device failed")
+
+
+# the binding uses the C-ABI names
+def isc_create(case, **opt):
+    return Simulator(case, **opt)

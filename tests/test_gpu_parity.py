@@ -1,0 +1,176 @@
+"""GPU parity: libisc (through the C ABI) against the CPU oracle, element by
+element on seeded inputs.
+
+Tolerances: residual and Jacobian 1e-10 relative (to the row's scale, since
+single entries can cancel to ~0); decoupled system and preconditioner 1e-11
+on identical inputs; Newton updates to the solver tolerance measured with the
+oracle's own matrix.
+"""
+import numpy as np
+import pytest
+
+import isc_inputs as inp
+from oracle import linalg, model, sim
+
+pytestmark = pytest.mark.gpu
+
+SCALE = np.array([1e6, 1, 1, 1, 1, 100.0, 1, 1])
+
+
+@pytest.fixture(scope="module")
+def Simulator():
+    from paper_1811_11992_gb300 import build
+    build.build()
+    from paper_1811_11992_gb300 import Simulator as S
+    return S
+
+
+def row_scaled_err(F, Fo):
+    scale = np.abs(Fo).max(axis=1, keepdims=True) + 1e-300
+    return np.max(np.abs(F - Fo) / scale)
+
+
+def jac_err(J, Jo, rowptr, n):
+    rows = np.repeat(np.arange(n), np.diff(rowptr))
+    Js = J * SCALE[None, None, :]
+    Jos = Jo * SCALE[None, None, :]
+    rowmax = np.zeros((n, 8))
+    np.maximum.at(rowmax, rows, np.abs(Jos).max(axis=2))
+    return np.max(np.abs(Js - Jos) / (rowmax[rows][:, :, None] + 1e-300))
+
+
+CASES = {
+    "tube12": lambda: inp.tube_case(n_cells=12),
+    "tube50": lambda: inp.tube_case(),
+    "box432": lambda: inp.small_box(4, 3, 2),
+    "box755": lambda: inp.small_box(7, 5, 5),
+}
+
+
+def _gpu_assembled(S, case, st_a, st_b, dt, **opt):
+    g = S(case, **opt)
+    g.set_state(st_a["u"], st_a["coke"])
+    g.begin_step()
+    g.set_state(st_b["u"])
+    g.assemble(dt)
+    return g
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_residual_and_jacobian_match_oracle(Simulator, name):
+    case = CASES[name]()
+    a = inp.random_state(case, 101)
+    b = inp.random_state(case, 202)
+    dt = 150.0
+    g = _gpu_assembled(Simulator, case, a, b, dt)
+    F = g.residual()
+    rp, col, J = g.jacobian()
+    acc_old = model.old_accumulation(case, a["u"], a["coke"])
+    Fo, co = model.residual(case, b["u"], a["coke"], acc_old, dt, return_coke=True)
+    rpo, colo, Jo = model.jacobian(case, b["u"], a["coke"], acc_old, dt)
+    assert np.array_equal(rp, rpo) and np.array_equal(col, colo)
+    assert np.allclose(g.coke(), co, rtol=1e-12, atol=1e-300)
+    assert row_scaled_err(F, Fo) < 1e-10
+    assert jac_err(J, Jo, rp, case.n) < 1e-10
+    g.close()
+
+
+def test_initial_state_and_ignited_assembly(Simulator):
+    case = inp.small_box(5, 4, 3)
+    g = Simulator(case)
+    g.init_equilibrium()
+    u0, c0 = sim.initial_state(case)
+    ug, cg = g.get_state()
+    assert np.allclose(ug, u0, rtol=1e-13, atol=1e-300)
+    assert np.all(cg == 0)
+    dt = 3600.0
+    g.assemble(dt)
+    acc_old = model.old_accumulation(case, u0, c0)
+    Fo = model.residual(case, u0, c0, acc_old, dt)
+    assert row_scaled_err(g.residual(), Fo) < 1e-10
+    rp, col, J = g.jacobian()
+    _, _, Jo = model.jacobian(case, u0, c0, acc_old, dt)
+    assert jac_err(J, Jo, rp, case.n) < 1e-10
+
+
+@pytest.mark.parametrize("name", ["tube12", "box432", "box755"])
+def test_gauss_jordan_kernel_matches_oracle_on_identical_input(Simulator, name):
+    case = CASES[name]()
+    a = inp.random_state(case, 303)
+    b = inp.random_state(case, 404)
+    g = _gpu_assembled(Simulator, case, a, b, 100.0)
+    F = g.residual()
+    rp, col, J = g.jacobian()
+    g.decouple()
+    Fd = g.residual()
+    _, _, Jd = g.jacobian()
+    vo, ro = linalg.gauss_jordan_decouple(rp.astype(np.int64), col.astype(np.int64), J, F.T.copy())
+    rows = np.repeat(np.arange(case.n), np.diff(rp))
+    assert np.all(Jd[col == rows] == np.eye(8))
+    err = np.abs(Jd - vo).reshape(len(col), -1).max(axis=1) / np.maximum(np.abs(vo).reshape(len(col), -1).max(axis=1), 1e-300)
+    assert err.max() < 1e-11
+    assert row_scaled_err(Fd, ro.T) < 1e-11
+    g.close()
+
+
+@pytest.mark.parametrize("name", ["tube12", "box432", "box755"])
+def test_spmv_and_ilu0_apply_match_oracle(Simulator, name):
+    case = CASES[name]()
+    a = inp.random_state(case, 505)
+    b = inp.random_state(case, 606)
+    g = _gpu_assembled(Simulator, case, a, b, 100.0)
+    g.decouple()
+    rp, col, Jd = g.jacobian()
+    rng = np.random.default_rng(7)
+    x = rng.standard_normal((8, case.n))
+    y = g.spmv(x)
+    yo = linalg.bsr_matvec(rp, col, Jd, x.T.copy()).T
+    assert np.max(np.abs(y - yo)) <= 1e-13 * np.abs(yo).max()
+    g.build_preconditioner()
+    z = g.precond_apply(x)
+    M = linalg.ILU0Preconditioner(rp.astype(np.int64), col.astype(np.int64), Jd)
+    zo = M.apply(x.T.copy()).T
+    assert np.max(np.abs(z - zo)) <= 1e-11 * np.abs(zo).max()
+    g.close()
+
+
+@pytest.mark.parametrize("krylov,prec", [("gmres", "bilu0"), ("gmres", "bjacobi"), ("bicgstab", "bilu0"), ("gmres", "none")])
+def test_krylov_solution_has_small_residual_in_oracle_matrix(Simulator, krylov, prec):
+    case = inp.small_box(4, 3, 2)
+    a = inp.random_state(case, 707)
+    b = inp.random_state(case, 808)
+    g = _gpu_assembled(Simulator, case, a, b, 100.0, krylov=krylov, prec=prec, tol_lin=1e-11, maxit_lin=2000)
+    F = g.residual()
+    rp, col, J = g.jacobian()
+    g.decouple()
+    info = g.solve()
+    du = g.newton_update()
+    assert info.krylov_rel_residual <= 1e-11
+    # residual of the GPU update in the oracle's decoupled system
+    vo, ro = linalg.gauss_jordan_decouple(rp.astype(np.int64), col.astype(np.int64), J, -F.T.copy())
+    r = ro - linalg.bsr_matvec(rp, col, vo, du.T.copy())
+    assert np.linalg.norm(r) <= 2e-11 * np.linalg.norm(ro)
+    ref = np.linalg.solve(linalg.bsr_to_dense(rp, col, J), -F.T.reshape(-1)).reshape(case.n, 8).T
+    assert np.max(np.abs(du - ref) / SCALE[:, None]) <= 1e-6 * np.max(np.abs(ref) / SCALE[:, None])
+    g.close()
+
+
+def test_newton_step_matches_oracle_on_tube(Simulator):
+    case = inp.tube_case()
+    dt = 20.0
+    g = Simulator(case, tol_lin=1e-12, maxit_lin=400, tol_newton=0.0)
+    g.init_equilibrium()
+    u0, c0 = sim.initial_state(case)
+    acc_old = model.old_accumulation(case, u0, c0)
+    opts = sim.NewtonOptions(tol=0.0)
+    opts.solve.solver = "dense"
+    u = u0
+    for k in range(3):
+        info = g.newton_step(dt)
+        r = sim.newton_step(case, u, c0, acc_old, dt, opts)
+        u = r["u"]
+        ug, _ = g.get_state()
+        d = np.max(np.abs(ug - u) / SCALE[:, None])
+        assert d < 1e-7, (k, d)
+        g.set_state(u)   # continue both from the oracle's iterate
+    g.close()
