@@ -1,0 +1,355 @@
+"""Benchmark: Newton linearise-and-solve steps per second of the in-situ-combustion
+model on the 60x60x20 field workload (72,000 cells, 8 unknowns per cell).
+
+One step = the whole hot path on one batch: restore the iterate, property
+evaluation + residual/Jacobian assembly, convergence norms, Gauss-Jordan
+decoupling, block ILU(0) factorisation, GMRES(30) to the relative tolerance,
+safeguarded update. Inputs are resident in HBM for ``value``; ``e2e`` goes
+through the C ABI with host buffers (state in, state out) every step.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl isc|reference]
+Under torchrun each rank runs an independent replica (the path has no
+data-path exchange on one GPU per problem); value sums all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Newton steps/s"
+UNIT = "Newton steps/s"
+FIELD = dict(nx=60, ny=60, nz=20)
+# algorithmic bytes per unit: one FP64 8x8 block = 512 B + 4 B column index
+BLOCK_BYTES = 516
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="isc", choices=["isc", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.t.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def field_case():
+    import isc_inputs as inp
+    return inp.config(2)
+
+
+def workload_config(case, dt, extra):
+    c = {"workload": f"field {case.nx}x{case.ny}x{case.nz} ({case.n} cells, 8 unknowns/cell), first Newton step of "
+                     f"the first time step (dt {dt:.0f} s) from the ignited initial state",
+         "solver": "GMRES(30), block ILU(0), Gauss-Jordan decoupling, FP64, tol_lin 1e-6",
+         "l2": "inputs larger than L2: the FP64 Jacobian (252 MB) and staged properties (83 MB) exceed the 129 MB L2"}
+    c.update(extra)
+    return c
+
+
+def run_isc(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_1811_11992_gb300 import build, isc
+    build.build()
+    case = field_case()
+    dt = case.dt0
+    g = isc.Simulator(case, profile=1)
+    g.init_equilibrium()
+    n = case.n
+    # resident snapshot of the starting iterate (torch owns the buffers)
+    u0 = torch.empty(8 * n, dtype=torch.float64, device="cuda")
+    c0 = torch.empty(n, dtype=torch.float64, device="cuda")
+    g.get_state_device(u0.data_ptr(), c0.data_ptr())
+    torch.cuda.synchronize()
+
+    def step():
+        g.set_state_device(u0.data_ptr(), c0.data_ptr())
+        return g.newton_step(dt)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    g.reset_stats()
+    infos = []
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    ev0.record()
+    for _ in range(args.steps):
+        infos.append(step())
+    ev1.record()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    wall = time.perf_counter() - t0
+    ms_dev = ev0.elapsed_time(ev1)
+    stats = g.stats()
+    clocks = sampler.stop()
+    ms_total = max(ms_dev, wall * 1e3)
+    if world > 1:
+        t = torch.tensor([ms_total], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+    value = world * args.steps / (ms_total / 1e3)
+    kry = [i.krylov_iterations for i in infos]
+    # end-to-end through the C ABI with host buffers
+    uh, ch = g.get_state()
+    u_host = torch.from_numpy(uh.reshape(-1).copy()).pin_memory().numpy()
+    c_host = torch.from_numpy(ch.copy()).pin_memory().numpy()
+    g.set_state_device(u0.data_ptr(), c0.data_ptr())
+    u_start, c_start = g.get_state()
+    u_start_p = torch.from_numpy(u_start.reshape(-1).copy()).pin_memory().numpy()
+    c_start_p = torch.from_numpy(c_start.copy()).pin_memory().numpy()
+    for _ in range(max(1, args.warmup // 2)):
+        g.set_state(u_start_p.reshape(8, n), c_start_p)
+        g.newton_step(dt)
+        g.get_state()
+    e2e_steps = max(3, args.steps // 2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        g.set_state(u_start_p.reshape(8, n), c_start_p)
+        g.newton_step(dt)
+        u_out, c_out = g.get_state()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_val = world * e2e_steps / e2e_s
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_val = world * e2e_steps / float(t.item())
+    io_bytes = 9 * n * 8
+    # roofline of the dominant kernel class
+    launches = sum(v["launches"] for v in stats.values())
+    dom = max(stats, key=lambda k: stats[k]["ms"])
+    roof = roofline(dom, stats, g, case, kry)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(case, dt, {"parallelism": f"replicas x{world}",
+                                             "krylov_iterations_per_step": statistics.median(kry) if kry else None}),
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes},
+        "gpu_launches": launches,
+        "kernel_ms": {k: round(v["ms"], 3) for k, v in stats.items()},
+        "kernel_launches": {k: v["launches"] for k, v in stats.items()},
+        "roofline": roof,
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(max_seconds=30.0)
+    g.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+FP64_PEAK_GFLOPS = 1200.0   # measured DFMA throughput on this GB300
+
+
+def roofline(dom, stats, g, case, kry):
+    """Algorithmic bytes (or flops) per call of the dominant kernel class over its
+    average CUDA-event duration."""
+    n, nnzb = case.n, g.nnzb
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    s = stats[dom]
+    calls = max(1, s["calls"])
+    ms = s["ms"] / calls
+    nlev = case.nx + case.ny + case.nz - 2
+    nlow = nnzb - n  # off-diagonal blocks (both triangles)
+    if dom == "spmv":
+        byts = (nnzb - n) * BLOCK_BYTES + 3 * n * 64
+        flops = 2 * 64 * (nnzb - n)
+    elif dom == "prec_apply":
+        byts = nlow * BLOCK_BYTES + 2 * n * 512 + 4 * n * 64
+        flops = 2 * 64 * (nlow + 2 * n)
+    elif dom == "ilu_factor":
+        byts = (nlow // 2) * 2 * BLOCK_BYTES + 2 * n * 512
+        flops = (nlow // 2) * 2 * 2 * 512 + n * 2 * 512 * 2
+    elif dom == "gj":
+        byts = 2 * (nnzb * BLOCK_BYTES + n * 64)
+        flops = n * 8 * 7 * 2 * 57
+    elif dom in ("props", "flux"):
+        byts = nnzb * 512 + n * (8 + 8 + 7 + 3) * 8
+        flops = None
+    else:
+        byts = 0
+        flops = None
+    ach_gbs = byts / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+    out = {"kernel": dom, "calls": calls, "ms_per_call": ms, "bytes_per_call": byts}
+    if flops is not None and ms > 0:
+        ach_tf = flops / (ms * 1e-3) / 1e9
+        # FP64 kernels on GB300 sit above the FP64 ridge (1.2 TFLOP/s / 6.8 TB/s = 0.18 flop/B)
+        if flops / max(byts, 1) > FP64_PEAK_GFLOPS / hbm:
+            out.update(bound="alu", achieved=ach_tf, peak=FP64_PEAK_GFLOPS, unit="GFLOP/s",
+                       frac=ach_tf / FP64_PEAK_GFLOPS, peak_source="measured FP64 DFMA probe",
+                       hbm_achieved_gbs=ach_gbs, hbm_frac=ach_gbs / hbm)
+        else:
+            out.update(bound="hbm", achieved=ach_gbs, peak=hbm, unit="GB/s", frac=ach_gbs / hbm,
+                       peak_source="MEASURED_PEAKS.json hbm_gbs")
+    else:
+        out.update(bound="hbm", achieved=ach_gbs, peak=hbm, unit="GB/s", frac=ach_gbs / hbm if hbm else None,
+                   peak_source="MEASURED_PEAKS.json hbm_gbs")
+    out["traffic"] = None
+    return out
+
+
+# ------------------------------------------------------------------ oracle
+SAMPLE = dict(nx=30, ny=30, nz=10)
+
+
+def oracle_sample_step():
+    """One oracle Newton step on a 30x30x10 block cut to the field workload's
+    recipe (same generator, 1/8 of the cells)."""
+    import isc_inputs as inp
+    from oracle import model, sim
+    case = inp.field_case(SAMPLE["nx"], SAMPLE["ny"], SAMPLE["nz"], 0, 1, "field sample 30x30x10", 30 * inp.DAY, 40)
+    u, c = sim.initial_state(case)
+    acc_old = model.old_accumulation(case, u, c)
+    opts = sim.NewtonOptions(tol=0.0)
+    opts.solve.rtol = 1e-6
+    t0 = time.perf_counter()
+    r = sim.newton_step(case, u, c, acc_old, case.dt0, opts)
+    return time.perf_counter() - t0, case.n, r
+
+
+def cpu_baseline(max_seconds=30.0):
+    full = FIELD["nx"] * FIELD["ny"] * FIELD["nz"]
+    secs = []
+    t_start = time.perf_counter()
+    while True:
+        dt, ncell, _ = oracle_sample_step()
+        secs.append(dt)
+        if time.perf_counter() - t_start + dt > max_seconds or len(secs) >= 3:
+            break
+    per = statistics.median(secs)
+    scale = ncell / full
+    return {"value": scale / per, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{len(secs)} oracle Newton step(s) on a 30x30x10 block of the field recipe "
+                      f"({ncell} cells, {per:.2f} s each), scaled by cell count to the 72,000-cell workload"}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample_step()
+    full = FIELD["nx"] * FIELD["ny"] * FIELD["nz"]
+    t0 = time.perf_counter()
+    ncell = None
+    for _ in range(args.steps):
+        _, ncell, _ = oracle_sample_step()
+    wall = time.perf_counter() - t0
+    per = wall / args.steps
+    value = (ncell / full) / per
+    case = field_case()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(case, case.dt0, {"parallelism": "host oracle, 1 thread"}),
+        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1,
+                         "sample": f"one oracle Newton step per timed step on a 30x30x10 block ({ncell} cells), "
+                                   f"scaled by cell count to the 72,000-cell workload"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_isc(a)

@@ -169,12 +169,13 @@ def next_dt(dt, u_old, u_new, dt_max, dT_target=20.0, dS_target=0.2):
 def run(case, t_end, dt0, dt_max, opts: NewtonOptions, max_cuts=8, max_steps=100000, dts=None):
     """Time loop with the deterministic controller; with ``dts`` given the
     accepted step sizes are replayed instead. Returns (u, coke, accepted dts,
-    stats)."""
+    stats); stats["its_per_step"] holds the Newton solves of each accepted step."""
     geom = model.faces(case)
     u, coke = initial_state(case)
     t = 0.0
     dt = dt0
     accepted = []
+    its_per_step = []
     newton_total = 0
     cuts = 0
     steps = 0
@@ -196,9 +197,10 @@ def run(case, t_end, dt0, dt_max, opts: NewtonOptions, max_cuts=8, max_steps=100
         if not ok:
             raise RuntimeError(f"time step failed after {max_cuts} cuts at t={t}")
         accepted.append(dt)
+        its_per_step.append(its)
         t += dt
         steps += 1
         nd = next_dt(dt, u, un, dt_max)
         u, coke = un, cn
         dt = nd
-    return u, coke, accepted, dict(newton=newton_total, cuts=cuts, steps=steps, t=t)
+    return u, coke, accepted, dict(newton=newton_total, cuts=cuts, steps=steps, t=t, its_per_step=its_per_step)

@@ -493,7 +493,7 @@ __global__ void __launch_bounds__(256) k_flux(Params P, const double* __restrict
                                               double* __restrict__ J) {
   const int r = threadIdx.x >> 5;
   const int i = blockIdx.x * 32 + (threadIdx.x & 31);
-  if (i >= P.n || r == 7) return;
+  if (i >= P.n) return;
   const int nx = P.nx, ny = P.ny, nxy = P.nx * P.ny;
   const int ix = i % nx, iy = (i / nx) % ny, iz = i / nxy;
   // neighbours in BSR column order: -z, -y, -x, (diag), +x, +y, +z
@@ -507,6 +507,18 @@ __global__ void __launch_bounds__(256) k_flux(Params P, const double* __restrict
   nb[5] = i + nxy;
   const int base = rowptr[i];
   const int dslot = (int)has[0] + (int)has[1] + (int)has[2];
+  if (r == 7) {
+    // the gas constraint has no flux: its off-diagonal rows are zero (the
+    // buffer may hold the previous, decoupled system)
+    const int nblk = rowptr[i + 1] - base;
+    for (int s = 0; s < nblk; ++s) {
+      if (s == dslot) continue;
+      double* Jb = J + (size_t)(base + s) * BB + 56;
+#pragma unroll
+      for (int k = 0; k < 8; k += 2) *reinterpret_cast<double2*>(Jb + k) = make_double2(0.0, 0.0);
+    }
+    return;
+  }
   double Rsum = 0.0;
   double dd[8];
 #pragma unroll

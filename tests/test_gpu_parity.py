@@ -155,6 +155,22 @@ def test_krylov_solution_has_small_residual_in_oracle_matrix(Simulator, krylov, 
     g.close()
 
 
+def test_reassembly_after_decoupling_overwrites_every_block(Simulator):
+    # the Jacobian buffer is reused: a second assembly must not see the
+    # previous (decoupled) system
+    case = inp.small_box(4, 3, 2)
+    a = inp.random_state(case, 11)
+    b = inp.random_state(case, 12)
+    g = _gpu_assembled(Simulator, case, a, b, 100.0)
+    g.decouple()
+    g.assemble(100.0)
+    rp, col, J = g.jacobian()
+    acc_old = model.old_accumulation(case, a["u"], a["coke"])
+    _, _, Jo = model.jacobian(case, b["u"], a["coke"], acc_old, 100.0)
+    assert jac_err(J, Jo, rp, case.n) < 1e-10
+    g.close()
+
+
 def test_newton_step_matches_oracle_on_tube(Simulator):
     case = inp.tube_case()
     dt = 20.0
