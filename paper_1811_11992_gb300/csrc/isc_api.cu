@@ -114,7 +114,7 @@ int dalloc(isc_handle* h, T** p, size_t count) {
 void free_all(isc_handle* h) {
   void* ptrs[] = {h->rowptr, h->col, h->level_cells, h->phi_ref, h->depth, h->tx, h->ty, h->tz, h->well_slot,
                   h->slots, h->u, h->coke, h->u_n, h->coke_n, h->acc_n, h->props, h->R, h->J, h->ntot, h->du,
-                  h->rhs, h->dinv, h->V, h->Z, h->w, h->tmp, h->partial, h->scal, h->dstatus};
+                  h->rhs, h->dinv, h->V, h->Z, h->w, h->tmp, h->partial, h->scal, h->dstatus, h->pipe};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->h_scal) cudaFreeHost(h->h_scal);
@@ -139,7 +139,7 @@ void spmv(isc_handle* h, const double* x, double* y) {
 }
 
 void prec(isc_handle* h, const double* r, double* z) {
-  int launches = h->opt.prec == ISC_PREC_BILU0 ? 2 * h->nlevels : 1;
+  int launches = h->opt.prec == ISC_PREC_BILU0 ? 2 : 1;
   Region rg(h, ISC_K_PREC_APPLY, launches);
   launch_prec_apply(*h, r, z, h->stream);
 }
@@ -660,6 +660,7 @@ int isc_create(const isc_grid* grid, const isc_rock* rock, const isc_fluid* fl, 
   e |= dalloc(h, &h->partial, (size_t)h->red_blocks * (MAX_RESTART + 8));
   e |= dalloc(h, &h->scal, NSCAL);
   e |= dalloc(h, &h->dstatus, 1);
+  e |= dalloc(h, &h->pipe, (size_t)ny * nz + 2);
   if (e) {
     std::string msg = h->last_error;
     free_all(h);

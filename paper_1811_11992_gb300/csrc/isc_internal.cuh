@@ -115,6 +115,7 @@ struct Handle {
   double* h_scal = nullptr;                       // pinned host mirror
   int* dstatus = nullptr;
   int* h_status = nullptr;                        // pinned
+  int* pipe = nullptr;                            // sweep counter, abort flag, per-pencil progress
   int restart_alloc = 0;
   int red_blocks = 0;
   // flags
@@ -140,6 +141,8 @@ void launch_spmv(int nrows, const int32_t* rowptr, const int32_t* col, const dou
 void launch_ilu_factor(Handle& h, cudaStream_t s);
 void launch_bjacobi_factor(Handle& h, cudaStream_t s);
 void launch_prec_apply(Handle& h, const double* r, double* z, cudaStream_t s);
+// pencil-pipelined ILU(0) sweeps (isc_ilu_pipe.cu)
+void launch_ilu_apply_pipe(Handle& h, const double* r, double* z, cudaStream_t s);
 void launch_update(Handle& h, cudaStream_t s);
 // BLAS-1 with fixed-order two-stage reductions; results land in h.scal[off..]
 void launch_mdot(Handle& h, const double* V, int nvec, const double* w, int off, cudaStream_t s);

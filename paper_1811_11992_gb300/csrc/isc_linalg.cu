@@ -8,7 +8,7 @@
 // k_ilu_factor  block ILU(0) diagonal recurrence D_i = A_ii - sum_k A_ik D_k^-1 A_ki
 //               over the lower neighbours (the 7-point pattern has no other
 //               fill), hyperplane wavefront i+j+k = level, 64 threads per cell.
-// k_ilu_fwd/bwd the two triangular sweeps of the D-ILU form, 8 threads per cell.
+// (the two triangular sweeps live in isc_ilu_pipe.cu)
 // BLAS-1        dot products with fixed-order two-stage reductions.
 // k_update      safeguarded Newton update (Sec. 2.2 saturation treatment).
 #include <math.h>
@@ -268,65 +268,6 @@ __global__ void __launch_bounds__(256) k_ilu_factor(int nx, int ny, int nz, cons
   }
 }
 
-// forward sweep of the D-ILU form: y_i = D_i^-1 (r_i - sum_{k<i} A_ik y_k)
-__global__ void __launch_bounds__(256) k_ilu_fwd(int nx, int ny, int nz, const int32_t* __restrict__ cells, int count,
-                                                 const int32_t* __restrict__ rowptr, const double* __restrict__ A,
-                                                 const double* __restrict__ Dinv, const double* __restrict__ rhs,
-                                                 double* __restrict__ y) {
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int ci = tid >> 3;
-  const int r = threadIdx.x & 7;
-  const bool active = ci < count;
-  const int i = active ? cells[ci] : 0;
-  double t = 0.0;
-  if (active) {
-    t = rhs[(size_t)i * 8 + r];
-    for (int dl = 0; dl < 3; ++dl) {
-      int k;
-      if (!nbr_exists(nx, ny, nz, i, dl, &k)) continue;
-      const double* Ab = A + (size_t)(rowptr[i] + nbr_slot(nx, ny, nz, i, dl)) * BB + r * 8;
-#pragma unroll
-      for (int m = 0; m < 8; ++m) t -= Ab[m] * y[(size_t)k * 8 + m];
-    }
-  }
-  double out = 0.0;
-#pragma unroll
-  for (int m = 0; m < 8; ++m) {
-    double tm = __shfl_sync(FULL, t, m, 8);
-    if (active) out = fma(Dinv[(size_t)i * BB + r * 8 + m], tm, out);
-  }
-  if (active) y[(size_t)i * 8 + r] = out;
-}
-
-// backward sweep: z_i = y_i - D_i^-1 sum_{j>i} A_ij z_j
-__global__ void __launch_bounds__(256) k_ilu_bwd(int nx, int ny, int nz, const int32_t* __restrict__ cells, int count,
-                                                 const int32_t* __restrict__ rowptr, const double* __restrict__ A,
-                                                 const double* __restrict__ Dinv, const double* __restrict__ y,
-                                                 double* __restrict__ z) {
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int ci = tid >> 3;
-  const int r = threadIdx.x & 7;
-  const bool active = ci < count;
-  const int i = active ? cells[ci] : 0;
-  double s = 0.0;
-  if (active) {
-    for (int du = 4; du < 7; ++du) {
-      int j;
-      if (!nbr_exists(nx, ny, nz, i, du, &j)) continue;
-      const double* Ab = A + (size_t)(rowptr[i] + nbr_slot(nx, ny, nz, i, du)) * BB + r * 8;
-#pragma unroll
-      for (int m = 0; m < 8; ++m) s += Ab[m] * z[(size_t)j * 8 + m];
-    }
-  }
-  double out = 0.0;
-#pragma unroll
-  for (int m = 0; m < 8; ++m) {
-    double sm = __shfl_sync(FULL, s, m, 8);
-    if (active) out = fma(Dinv[(size_t)i * BB + r * 8 + m], sm, out);
-  }
-  if (active) z[(size_t)i * 8 + r] = y[(size_t)i * 8 + r] - out;
-}
-
 __global__ void k_bjacobi_apply(int n, const double* __restrict__ Dinv, const double* __restrict__ rhs,
                                 double* __restrict__ z) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -484,16 +425,7 @@ void launch_prec_apply(Handle& h, const double* r, double* z, cudaStream_t s) {
     k_bjacobi_apply<<<(h.n * 8 + 255) / 256, 256, 0, s>>>(h.n, h.dinv, r, z);
     return;
   }
-  for (int L = 0; L < h.nlevels; ++L) {
-    int b = h.h_level_ptr[L], cnt = h.h_level_ptr[L + 1] - b;
-    k_ilu_fwd<<<(cnt * 8 + 255) / 256, 256, 0, s>>>(h.nx, h.ny, h.nz, h.level_cells + b, cnt, h.rowptr, h.J, h.dinv, r,
-                                                    h.tmp);
-  }
-  for (int L = h.nlevels - 1; L >= 0; --L) {
-    int b = h.h_level_ptr[L], cnt = h.h_level_ptr[L + 1] - b;
-    k_ilu_bwd<<<(cnt * 8 + 255) / 256, 256, 0, s>>>(h.nx, h.ny, h.nz, h.level_cells + b, cnt, h.rowptr, h.J, h.dinv,
-                                                    h.tmp, z);
-  }
+  launch_ilu_apply_pipe(h, r, z, s);
 }
 
 void launch_update(Handle& h, cudaStream_t s) {

@@ -24,7 +24,7 @@ def test_tube_trajectory_matches_oracle():
     opts.solve.solver = "dense"
     u_o, c_o, dts, stats = sim.run(case, case.t_end, 5.0, 150.0, opts)
     assert 40 <= len(dts) <= 80
-    g = Simulator(case, tol_newton=0.0, tol_lin=1e-13, maxit_lin=400)
+    g = Simulator(case, tol_newton=0.0, tol_lin=1e-12, maxit_lin=400)
     g.init_equilibrium()
     for dt, its in zip(dts, stats["its_per_step"]):
         for _ in range(its):
