@@ -8,10 +8,12 @@
 // (j-1,k) and (j,k-1) at the same x. One warp owns a whole x-pencil, so the
 // x-recurrence stays in registers; pencils are taken from a counter in
 // dependency order (so a warp only ever waits on pencils already held by
-// running warps), and the cross-pencil hand-off is a per-pencil progress
-// counter written with release and read with acquire semantics. Every wait
-// is bounded: on timeout the kernel raises DS_TIMEOUT and a global abort flag
-// that makes every other waiter return.
+// running warps). The cross-pencil hand-off is the data itself: the output
+// vector is NaN-filled before a sweep and a consumer polls the neighbour's
+// 64-byte block vector until it holds numbers. Matrix operands are
+// prefetched PF cells ahead into a register ring. Every wait is bounded: on
+// timeout the kernel raises DS_TIMEOUT and a global abort flag that makes
+// every other waiter return.
 //
 // Lane layout per 8x8 block (row-major, 64 doubles): lane l holds the double2
 // at offset 2l, i.e. row r = l/4, columns c = 2(l%4), c+1; a row sum is a
@@ -25,59 +27,91 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int SPIN_LIMIT = 1 << 22;
 
-__device__ __forceinline__ int ld_acquire(const int* p) {
-  int v;
-  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
 __device__ __forceinline__ int ld_relaxed(const int* p) {
   int v;
   asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
 
-__device__ __forceinline__ void st_release(int* p, int v) {
-  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+// morally strong store paired with the relaxed polling loads of other warps
+__device__ __forceinline__ void st_relaxed(double* p, double v) {
+  asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
 }
-
-__device__ __forceinline__ double2 ld_cg2(const double* p) { return __ldcg(reinterpret_cast<const double2*>(p)); }
 
 __device__ __forceinline__ double2 ld_nc2(const double* p) { return __ldg(reinterpret_cast<const double2*>(p)); }
 
-// Wait (lane 0 polls) until prog[q] >= need. Returns false if the sweep was aborted.
-__device__ __forceinline__ bool wait_for(const int* prog_q, int need, int& known, int* abortf, int* dstatus,
-                                         int lane) {
-  if (known >= need) return true;
-  int ok = 1, v = 0;
-  if (lane == 0) {
-    v = ld_acquire(prog_q);
-    int spins = 0;
-    while (v < need) {
-      if (ld_relaxed(abortf)) {
-        ok = 0;
-        break;
-      }
-      if (++spins > SPIN_LIMIT) {
+// Poll the 64-byte block vector v[8] of a neighbouring pencil until every
+// entry is a number: the output vector is filled with NaN before the sweep and
+// each 8-byte store is single-copy atomic, so a non-NaN entry is final. The
+// data itself is the hand-off (one L2 round trip, no flags or fences).
+// Returns false if the sweep was aborted (timeout here or elsewhere).
+__device__ __forceinline__ bool poll_vec(const double* v, int c, double2& out, int* abortf, int* dstatus) {
+  const double* p = v + c;
+  for (int spins = 0;; ++spins) {
+    double a, b;
+    asm volatile("ld.relaxed.gpu.global.v2.f64 {%0, %1}, [%2];" : "=d"(a), "=d"(b) : "l"(p) : "memory");
+    const bool ok = !isnan(a) && !isnan(b);
+    if (__all_sync(FULL, ok)) {
+      out = make_double2(a, b);
+      return true;
+    }
+    if ((spins & 63) == 63 && __any_sync(FULL, ld_relaxed(abortf) != 0)) return false;
+    if (spins > SPIN_LIMIT) {
+      if ((threadIdx.x & 31) == 0) {
         atomicOr(dstatus, DS_TIMEOUT);
         atomicExch(abortf, 1);
-        ok = 0;
-        break;
       }
-      __nanosleep(32);
-      v = ld_acquire(prog_q);
+      return false;
     }
+    __nanosleep(20);
   }
-  ok = __shfl_sync(FULL, ok, 0);
-  known = __shfl_sync(FULL, v, 0);
-  __syncwarp();
-  return ok != 0;
 }
 
 __device__ __forceinline__ double quad_sum(double v) {
   v += __shfl_xor_sync(FULL, v, 1);
   v += __shfl_xor_sync(FULL, v, 2);
   return v;
+}
+
+// operands of one cell that do not depend on the sweep
+struct Ops {
+  double2 a0, a1, a2, d;  // up to three off-diagonal blocks (lane's double2) and D^-1
+  double ri;
+};
+
+constexpr int PF = 4;  // prefetch distance in cells (register ring)
+
+__device__ __forceinline__ Ops load_fwd(int x, int nx, int base_jk, bool hy, bool hz, const int32_t* __restrict__ rowptr,
+                                        const double* __restrict__ A, const double* __restrict__ Dinv,
+                                        const double* __restrict__ rhs, int lane, int r) {
+  Ops o;
+  const int i = base_jk + x;
+  const int base = __ldg(rowptr + i);
+  int s = 0;
+  const double2 zero = make_double2(0.0, 0.0);
+  o.a0 = hz ? ld_nc2(A + (size_t)(base + s++) * BB + 2 * lane) : zero;  // -z
+  o.a1 = hy ? ld_nc2(A + (size_t)(base + s++) * BB + 2 * lane) : zero;  // -y
+  o.a2 = (x > 0) ? ld_nc2(A + (size_t)(base + s) * BB + 2 * lane) : zero;  // -x
+  o.d = ld_nc2(Dinv + (size_t)i * BB + 2 * lane);
+  o.ri = __ldg(rhs + (size_t)i * 8 + r);
+  return o;
+}
+
+__device__ __forceinline__ Ops load_bwd(int x, int nx, int base_jk, int nlow_jk, bool hy, bool hz,
+                                        const int32_t* __restrict__ rowptr, const double* __restrict__ A,
+                                        const double* __restrict__ Dinv, const double* __restrict__ yin, int lane,
+                                        int r) {
+  Ops o;
+  const int i = base_jk + x;
+  const int base = __ldg(rowptr + i);
+  int s = nlow_jk + (x > 0) + 1;  // first slot after the diagonal
+  const double2 zero = make_double2(0.0, 0.0);
+  o.a2 = (x < nx - 1) ? ld_nc2(A + (size_t)(base + s++) * BB + 2 * lane) : zero;  // +x
+  o.a1 = hy ? ld_nc2(A + (size_t)(base + s++) * BB + 2 * lane) : zero;            // +y
+  o.a0 = hz ? ld_nc2(A + (size_t)(base + s) * BB + 2 * lane) : zero;              // +z
+  o.d = ld_nc2(Dinv + (size_t)i * BB + 2 * lane);
+  o.ri = __ldg(yin + (size_t)i * 8 + r);
+  return o;
 }
 
 __global__ void __launch_bounds__(256) k_ilu_fwd_pipe(int nx, int ny, int nz, const int32_t* __restrict__ rowptr,
@@ -89,7 +123,6 @@ __global__ void __launch_bounds__(256) k_ilu_fwd_pipe(int nx, int ny, int nz, co
   const int npen = ny * nz, nxy = nx * ny;
   int* counter = pipe;
   int* abortf = pipe + 1;
-  int* prog = pipe + 2;
   for (;;) {
     int p = 0;
     if (lane == 0) p = atomicAdd(counter, 1);
@@ -97,39 +130,38 @@ __global__ void __launch_bounds__(256) k_ilu_fwd_pipe(int nx, int ny, int nz, co
     if (p >= npen) return;
     const int j = p % ny, k = p / ny;
     const bool hy = j > 0, hz = k > 0;
-    int known_y = 0, known_z = 0;
+    const int base_jk = nx * (j + ny * k);
+    Ops ring[PF];
+#pragma unroll
+    for (int q = 0; q < PF; ++q)
+      if (q < nx) ring[q] = load_fwd(q, nx, base_jk, hy, hz, rowptr, A, Dinv, rhs, lane, r);
     double yp0 = 0.0, yp1 = 0.0;
-    for (int x = 0; x < nx; ++x) {
-      const int i = x + nx * (j + ny * k);
-      const int base = __ldg(rowptr + i);
-      // operands that do not depend on the sweep are loaded before any wait
-      int s = 0;
-      double2 az = make_double2(0.0, 0.0), ay = az, ax = az;
-      if (hz) az = ld_nc2(A + (size_t)(base + s++) * BB + 2 * lane);
-      if (hy) ay = ld_nc2(A + (size_t)(base + s++) * BB + 2 * lane);
-      if (x > 0) ax = ld_nc2(A + (size_t)(base + s) * BB + 2 * lane);
-      const double2 d = ld_nc2(Dinv + (size_t)i * BB + 2 * lane);
-      const double ri = __ldg(rhs + (size_t)i * 8 + r);
-      double acc = 0.0;
-      if (x > 0) acc = fma(ax.x, yp0, fma(ax.y, yp1, acc));
-      if (hz) {
-        if (!wait_for(prog + p - ny, x + 1, known_z, abortf, dstatus, lane)) return;
-        const double2 v = ld_cg2(y + (size_t)(i - nxy) * 8 + c);
-        acc = fma(az.x, v.x, fma(az.y, v.y, acc));
+    for (int x0 = 0; x0 < nx; x0 += PF) {
+#pragma unroll
+      for (int q = 0; q < PF; ++q) {
+        const int x = x0 + q;
+        if (x >= nx) break;
+        const Ops o = ring[q];
+        if (x + PF < nx) ring[q] = load_fwd(x + PF, nx, base_jk, hy, hz, rowptr, A, Dinv, rhs, lane, r);
+        const int i = base_jk + x;
+        double acc = fma(o.a2.x, yp0, o.a2.y * yp1);
+        if (hz) {
+          double2 v;
+          if (!poll_vec(y + (size_t)(i - nxy) * 8, c, v, abortf, dstatus)) return;
+          acc = fma(o.a0.x, v.x, fma(o.a0.y, v.y, acc));
+        }
+        if (hy) {
+          double2 v;
+          if (!poll_vec(y + (size_t)(i - nx) * 8, c, v, abortf, dstatus)) return;
+          acc = fma(o.a1.x, v.x, fma(o.a1.y, v.y, acc));
+        }
+        const double t = o.ri - quad_sum(acc);
+        const double t0 = __shfl_sync(FULL, t, 4 * c), t1 = __shfl_sync(FULL, t, 4 * c + 4);
+        const double yr = quad_sum(fma(o.d.x, t0, o.d.y * t1));
+        if ((lane & 3) == 0) st_relaxed(y + (size_t)i * 8 + r, yr);
+        yp0 = __shfl_sync(FULL, yr, 4 * c);
+        yp1 = __shfl_sync(FULL, yr, 4 * c + 4);
       }
-      if (hy) {
-        if (!wait_for(prog + p - 1, x + 1, known_y, abortf, dstatus, lane)) return;
-        const double2 v = ld_cg2(y + (size_t)(i - nx) * 8 + c);
-        acc = fma(ay.x, v.x, fma(ay.y, v.y, acc));
-      }
-      const double t = ri - quad_sum(acc);
-      const double t0 = __shfl_sync(FULL, t, 4 * c), t1 = __shfl_sync(FULL, t, 4 * c + 4);
-      const double yr = quad_sum(fma(d.x, t0, d.y * t1));
-      if ((lane & 3) == 0) y[(size_t)i * 8 + r] = yr;
-      yp0 = __shfl_sync(FULL, yr, 4 * c);
-      yp1 = __shfl_sync(FULL, yr, 4 * c + 4);
-      __syncwarp();
-      if (lane == 0) st_release(prog + p, x + 1);
     }
   }
 }
@@ -143,7 +175,6 @@ __global__ void __launch_bounds__(256) k_ilu_bwd_pipe(int nx, int ny, int nz, co
   const int npen = ny * nz, nxy = nx * ny;
   int* counter = pipe;
   int* abortf = pipe + 1;
-  int* prog = pipe + 2;
   for (;;) {
     int g = 0;
     if (lane == 0) g = atomicAdd(counter, 1);
@@ -153,39 +184,40 @@ __global__ void __launch_bounds__(256) k_ilu_bwd_pipe(int nx, int ny, int nz, co
     const int j = p % ny, k = p / ny;
     const bool hy = j < ny - 1, hz = k < nz - 1;
     const int nlow_jk = (k > 0) + (j > 0);
-    int known_y = 0, known_z = 0;
+    const int base_jk = nx * (j + ny * k);
+    Ops ring[PF];
+#pragma unroll
+    for (int q = 0; q < PF; ++q)
+      if (q < nx) ring[q] = load_bwd(nx - 1 - q, nx, base_jk, nlow_jk, hy, hz, rowptr, A, Dinv, yin, lane, r);
     double zp0 = 0.0, zp1 = 0.0;
-    for (int x = nx - 1; x >= 0; --x) {
-      const int i = x + nx * (j + ny * k);
-      const int base = __ldg(rowptr + i);
-      int s = nlow_jk + (x > 0) + 1;  // first slot after the diagonal
-      double2 ax = make_double2(0.0, 0.0), ay = ax, az = ax;
-      if (x < nx - 1) ax = ld_nc2(A + (size_t)(base + s++) * BB + 2 * lane);
-      if (hy) ay = ld_nc2(A + (size_t)(base + s++) * BB + 2 * lane);
-      if (hz) az = ld_nc2(A + (size_t)(base + s) * BB + 2 * lane);
-      const double2 d = ld_nc2(Dinv + (size_t)i * BB + 2 * lane);
-      const double yi = __ldg(yin + (size_t)i * 8 + r);
-      const int done = nx - x;
-      double acc = 0.0;
-      if (x < nx - 1) acc = fma(ax.x, zp0, fma(ax.y, zp1, acc));
-      if (hz) {
-        if (!wait_for(prog + p + ny, done, known_z, abortf, dstatus, lane)) return;
-        const double2 v = ld_cg2(z + (size_t)(i + nxy) * 8 + c);
-        acc = fma(az.x, v.x, fma(az.y, v.y, acc));
+    for (int x0 = 0; x0 < nx; x0 += PF) {
+#pragma unroll
+      for (int q = 0; q < PF; ++q) {
+        const int step = x0 + q;
+        if (step >= nx) break;
+        const int x = nx - 1 - step;
+        const Ops o = ring[q];
+        if (step + PF < nx)
+          ring[q] = load_bwd(x - PF, nx, base_jk, nlow_jk, hy, hz, rowptr, A, Dinv, yin, lane, r);
+        const int i = base_jk + x;
+        double acc = fma(o.a2.x, zp0, o.a2.y * zp1);
+        if (hz) {
+          double2 v;
+          if (!poll_vec(z + (size_t)(i + nxy) * 8, c, v, abortf, dstatus)) return;
+          acc = fma(o.a0.x, v.x, fma(o.a0.y, v.y, acc));
+        }
+        if (hy) {
+          double2 v;
+          if (!poll_vec(z + (size_t)(i + nx) * 8, c, v, abortf, dstatus)) return;
+          acc = fma(o.a1.x, v.x, fma(o.a1.y, v.y, acc));
+        }
+        const double sr = quad_sum(acc);
+        const double s0 = __shfl_sync(FULL, sr, 4 * c), s1 = __shfl_sync(FULL, sr, 4 * c + 4);
+        const double zr = o.ri - quad_sum(fma(o.d.x, s0, o.d.y * s1));
+        if ((lane & 3) == 0) st_relaxed(z + (size_t)i * 8 + r, zr);
+        zp0 = __shfl_sync(FULL, zr, 4 * c);
+        zp1 = __shfl_sync(FULL, zr, 4 * c + 4);
       }
-      if (hy) {
-        if (!wait_for(prog + p + 1, done, known_y, abortf, dstatus, lane)) return;
-        const double2 v = ld_cg2(z + (size_t)(i + nx) * 8 + c);
-        acc = fma(ay.x, v.x, fma(ay.y, v.y, acc));
-      }
-      const double sr = quad_sum(acc);
-      const double s0 = __shfl_sync(FULL, sr, 4 * c), s1 = __shfl_sync(FULL, sr, 4 * c + 4);
-      const double zr = yi - quad_sum(fma(d.x, s0, d.y * s1));
-      if ((lane & 3) == 0) z[(size_t)i * 8 + r] = zr;
-      zp0 = __shfl_sync(FULL, zr, 4 * c);
-      zp1 = __shfl_sync(FULL, zr, 4 * c + 4);
-      __syncwarp();
-      if (lane == 0) st_release(prog + p, done);
     }
   }
 }
@@ -199,11 +231,13 @@ int pipe_blocks(int npen) {
 
 void launch_ilu_apply_pipe(Handle& h, const double* r, double* z, cudaStream_t s) {
   const int npen = h.ny * h.nz;
-  const size_t bytes = sizeof(int) * (size_t)(npen + 2);
-  cudaMemsetAsync(h.pipe, 0, bytes, s);
+  const size_t vbytes = sizeof(double) * (size_t)h.n * 8;
+  cudaMemsetAsync(h.pipe, 0, 2 * sizeof(int), s);
+  cudaMemsetAsync(h.tmp, 0xff, vbytes, s);  // NaN sentinel
   k_ilu_fwd_pipe<<<pipe_blocks(npen), 256, 0, s>>>(h.nx, h.ny, h.nz, h.rowptr, h.J, h.dinv, r, h.tmp, h.pipe,
                                                     h.dstatus);
-  cudaMemsetAsync(h.pipe, 0, bytes, s);
+  cudaMemsetAsync(h.pipe, 0, 2 * sizeof(int), s);
+  cudaMemsetAsync(z, 0xff, vbytes, s);
   k_ilu_bwd_pipe<<<pipe_blocks(npen), 256, 0, s>>>(h.nx, h.ny, h.nz, h.rowptr, h.J, h.dinv, h.tmp, z, h.pipe,
                                                     h.dstatus);
 }
