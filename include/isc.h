@@ -286,6 +286,27 @@ int isc_bsr_spmv_device(int32_t nrows, const int32_t* d_rowptr, const int32_t* d
                         const double* d_val, const double* d_x, double* d_y,
                         int32_t unit_diag, void* stream);
 
+/* Allocation-free block ILU(0) apply, for callers that cannot allocate GPU
+ * memory themselves (code running inside another framework's memory pool,
+ * restricted hosts): z = (L U)^-1 r with the D-ILU factors of the 7-point
+ * pattern on an nx*ny*nz grid. It is a variant of the preconditioner apply of
+ * isc_precond_apply; the paper has no counterpart (its preconditioners come
+ * from a CPU platform). Inputs and outputs are caller-owned device memory:
+ * d_rowptr (N+1) and d_A (nnzb*64) in the BSR layout above, d_Dinv (N*64,
+ * the inverted ILU(0) diagonal blocks, row-major), d_r and d_z (block-major 8N).
+ * The call allocates nothing: its scratch (the forward-sweep vector and the
+ * sweep counters) is a static device array sized for at most
+ * ISC_NOALLOC_MAX_CELLS cells (about 4 MB, held by every GPU that loads the
+ * library until the process exits). Larger grids return ISC_ERR_INVALID_ARG.
+ * The first call on a device resolves that array's device address with the
+ * device current; make that first call before any stream capture. All calls
+ * share the one array, so calls that overlap on the GPU (different streams or
+ * threads) race and must be serialised by the caller. The call synchronises
+ * stream and returns ISC_ERR_TIMEOUT if a device-side wait gave up. */
+#define ISC_NOALLOC_MAX_CELLS 65536
+int isc_bilu0_apply_noalloc(int32_t nx, int32_t ny, int32_t nz, const int32_t* d_rowptr, const double* d_A,
+                            const double* d_Dinv, const double* d_r, double* d_z, void* stream);
+
 /* Discrete adjoint of the time loop: not implemented yet. */
 int isc_adjoint(struct isc_handle* h);
 

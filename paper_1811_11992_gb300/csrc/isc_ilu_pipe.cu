@@ -18,6 +18,8 @@
 // Lane layout per 8x8 block (row-major, 64 doubles): lane l holds the double2
 // at offset 2l, i.e. row r = l/4, columns c = 2(l%4), c+1; a row sum is a
 // reduction over the 4 lanes of a quad.
+#include <mutex>
+
 #include "isc_internal.cuh"
 
 namespace isc {
@@ -242,4 +244,71 @@ void launch_ilu_apply_pipe(Handle& h, const double* r, double* z, cudaStream_t s
                                                     h.dstatus);
 }
 
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the ILU(0) apply for callers that cannot call
+// cudaMalloc (for example code running inside another framework's memory
+// pool, or a host that has no allocation rights). Its scratch -- the
+// intermediate vector of the forward sweep, the sweep counter, the abort flag
+// and a status word -- lives in this file-scope device array, which every GPU
+// that loads the library holds until the process exits.
+namespace {
+
+constexpr size_t NOALLOC_INTS = 64;  // counter, abort flag, status word, padding to 256 bytes
+static __device__ __align__(256) double g_noalloc_scratch[(size_t)ISC_NOALLOC_MAX_CELLS * 8 + NOALLOC_INTS / 2];
+
+constexpr int MAX_DEVICES = 64;
+std::mutex g_noalloc_mutex;
+double* g_noalloc_ptr[MAX_DEVICES] = {};
+
+// Host code may not use g_noalloc_scratch as an address: resolve the device
+// address once per device, with that device current.
+int noalloc_scratch(double** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return ISC_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return ISC_ERR_CUDA;
+    g_noalloc_ptr[dev] = static_cast<double*>(ptr);
+  }
+  *out = g_noalloc_ptr[dev];
+  return ISC_OK;
+}
+
+}  // namespace
+
 }  // namespace isc
+
+extern "C" int isc_bilu0_apply_noalloc(int32_t nx, int32_t ny, int32_t nz, const int32_t* d_rowptr,
+                                       const double* d_A, const double* d_Dinv, const double* d_r, double* d_z,
+                                       void* stream) {
+  using namespace isc;
+  if (nx < 1 || ny < 1 || nz < 1) return ISC_ERR_INVALID_ARG;
+  const long long n = (long long)nx * ny * nz;
+  if (n > ISC_NOALLOC_MAX_CELLS) return ISC_ERR_INVALID_ARG;  // beyond the static scratch
+  if (!d_rowptr || !d_A || !d_Dinv || !d_r || !d_z) return ISC_ERR_INVALID_ARG;
+  double* scratch = nullptr;
+  int st = noalloc_scratch(&scratch);
+  if (st != ISC_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  double* y = scratch;                                                  // 8n doubles
+  int* ints = reinterpret_cast<int*>(scratch + (size_t)ISC_NOALLOC_MAX_CELLS * 8);
+  int* pipe = ints;                                                     // counter, abort flag
+  int* status = ints + 2;
+  const int npen = ny * nz;
+  const size_t vbytes = sizeof(double) * (size_t)n * 8;
+  // everything that must start at zero (or NaN) is cleared here: the array
+  // keeps the previous call's contents
+  if (cudaMemsetAsync(ints, 0, NOALLOC_INTS * sizeof(int), s) != cudaSuccess) return ISC_ERR_CUDA;
+  cudaMemsetAsync(y, 0xff, vbytes, s);
+  k_ilu_fwd_pipe<<<pipe_blocks(npen), 256, 0, s>>>(nx, ny, nz, d_rowptr, d_A, d_Dinv, d_r, y, pipe, status);
+  cudaMemsetAsync(pipe, 0, 2 * sizeof(int), s);
+  cudaMemsetAsync(d_z, 0xff, vbytes, s);
+  k_ilu_bwd_pipe<<<pipe_blocks(npen), 256, 0, s>>>(nx, ny, nz, d_rowptr, d_A, d_Dinv, y, d_z, pipe, status);
+  int h_status = 0;
+  if (cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return ISC_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return ISC_ERR_CUDA;
+  if (h_status & DS_TIMEOUT) return ISC_ERR_TIMEOUT;
+  return ISC_OK;
+}

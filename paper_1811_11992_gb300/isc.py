@@ -132,6 +132,8 @@ _SIGS = {
     "isc_reset_stats": (C.c_int, [C.c_void_p]),
     "isc_bsr_spmv_device": (C.c_int, [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                       C.c_int32, C.c_void_p]),
+    "isc_bilu0_apply_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                          C.c_void_p, C.c_void_p, C.c_void_p]),
     "isc_adjoint": (C.c_int, [C.c_void_p]),
 }
 
@@ -387,6 +389,16 @@ def bsr_spmv_device(nrows, d_rowptr, d_col, d_val, d_x, d_y, unit_diag=0, stream
                                  C.c_void_p(d_x), C.c_void_p(d_y), unit_diag, C.c_void_p(stream) if stream else None)
     if st != ISC_OK:
         raise IscError(st, "isc_bsr_spmv_device failed")
+
+
+NOALLOC_MAX_CELLS = 65536
+
+
+def bilu0_apply_noalloc(nx, ny, nz, d_rowptr, d_A, d_Dinv, d_r, d_z, stream=None):
+    """Allocation-free ILU(0) apply on caller-owned device buffers (pointers as ints)."""
+    lib = load_library()
+    return lib.isc_bilu0_apply_noalloc(nx, ny, nz, C.c_void_p(d_rowptr), C.c_void_p(d_A), C.c_void_p(d_Dinv),
+                                       C.c_void_p(d_r), C.c_void_p(d_z), C.c_void_p(stream) if stream else None)
 
 
 # the binding uses the C-ABI names
