@@ -39,6 +39,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="isc", choices=["isc", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--grid", default=None,
+                    help="NXxNYxNZ: run the same field recipe on a smaller grid (profiling captures)")
     return ap.parse_args()
 
 
@@ -101,8 +103,11 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def field_case():
+def field_case(grid=None):
     import isc_inputs as inp
+    if grid:
+        nx, ny, nz = (int(v) for v in grid.lower().split("x"))
+        return inp.field_case(nx, ny, nz, 0, 1, f"field {nx}x{ny}x{nz}", 30 * inp.DAY, 40)
     return inp.config(2)
 
 
@@ -126,7 +131,7 @@ def run_isc(args):
     torch.cuda.set_device(local)
     from paper_1811_11992_gb300 import build, isc
     build.build()
-    case = field_case()
+    case = field_case(args.grid)
     dt = case.dt0
     g = isc.Simulator(case, profile=1)
     g.init_equilibrium()
