@@ -114,7 +114,7 @@ int dalloc(isc_handle* h, T** p, size_t count) {
 void free_all(isc_handle* h) {
   void* ptrs[] = {h->rowptr, h->col, h->level_cells, h->phi_ref, h->depth, h->tx, h->ty, h->tz, h->well_slot,
                   h->slots, h->u, h->coke, h->u_n, h->coke_n, h->acc_n, h->props, h->R, h->J, h->ntot, h->du,
-                  h->rhs, h->dinv, h->V, h->Z, h->w, h->tmp, h->partial, h->scal, h->dstatus, h->pipe};
+                  h->rhs, h->dinv, h->V, h->Z, h->w, h->tmp, h->partial, h->scal, h->dstatus, h->pipe, h->red_counter};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->h_scal) cudaFreeHost(h->h_scal);
@@ -146,7 +146,7 @@ void prec(isc_handle* h, const double* r, double* z) {
 
 int build_prec(isc_handle* h) {
   if (h->opt.prec == ISC_PREC_BILU0) {
-    Region rg(h, ISC_K_ILU_FACTOR, h->nlevels);
+    Region rg(h, ISC_K_ILU_FACTOR, 1);
     launch_ilu_factor(*h, h->stream);
   } else if (h->opt.prec == ISC_PREC_BJACOBI) {
     Region rg(h, ISC_K_ILU_FACTOR, 1);
@@ -207,13 +207,14 @@ int gmres(isc_handle* h, const double* b, double* x, int* its_out, double* rel_o
       prec(h, Vj, Zj);
       spmv(h, Zj, h->w);
       {
-        Region rg(h, ISC_K_BLAS1, 10);
+        // classical Gram-Schmidt applied twice; the second update also yields ||w||^2
+        Region rg(h, ISC_K_BLAS1, 4);
         launch_mdot(*h, V, j + 1, h->w, S_H0, s);
         launch_maxpy(*h, h->w, V, j + 1, S_H0, -1.0, s);
         launch_mdot(*h, V, j + 1, h->w, S_H1, s);
-        launch_maxpy(*h, h->w, V, j + 1, S_H1, -1.0, s);
-        launch_mdot(*h, h->w, 1, h->w, S_NRM, s);
-        cudaMemcpyAsync(h->h_scal, h->scal, sizeof(double) * NSCAL, cudaMemcpyDeviceToHost, s);
+        launch_maxpy_norm(*h, h->w, V, j + 1, S_H1, S_NRM, s);
+        cudaMemcpyAsync(h->h_scal + S_H0, h->scal + S_H0, sizeof(double) * (S_NRM + 1 - S_H0), cudaMemcpyDeviceToHost,
+                        s);
         cudaStreamSynchronize(s);
       }
       for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = h->h_scal[S_H0 + i] + h->h_scal[S_H1 + i];
@@ -660,7 +661,8 @@ int isc_create(const isc_grid* grid, const isc_rock* rock, const isc_fluid* fl, 
   e |= dalloc(h, &h->partial, (size_t)h->red_blocks * (MAX_RESTART + 8));
   e |= dalloc(h, &h->scal, NSCAL);
   e |= dalloc(h, &h->dstatus, 1);
-  e |= dalloc(h, &h->pipe, (size_t)ny * nz + 2);
+  e |= dalloc(h, &h->pipe, 2);
+  e |= dalloc(h, &h->red_counter, 1);
   if (e) {
     std::string msg = h->last_error;
     free_all(h);
@@ -685,6 +687,7 @@ int isc_create(const isc_grid* grid, const isc_rock* rock, const isc_fluid* fl, 
   cudaMemcpyAsync(h->well_slot, well_slot.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s);
   if (h->nslots) cudaMemcpyAsync(h->slots, slots.data(), sizeof(WellSlot) * h->nslots, cudaMemcpyHostToDevice, s);
   cudaMemsetAsync(h->dstatus, 0, sizeof(int), s);
+  cudaMemsetAsync(h->red_counter, 0, sizeof(unsigned), s);
   cudaMemsetAsync(h->u, 0, sizeof(double) * len, s);
   cudaMemsetAsync(h->coke, 0, sizeof(double) * n, s);
   cudaMemsetAsync(h->coke_n, 0, sizeof(double) * n, s);

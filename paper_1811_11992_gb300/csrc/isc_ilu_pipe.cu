@@ -224,12 +224,178 @@ __global__ void __launch_bounds__(256) k_ilu_bwd_pipe(int nx, int ny, int nz, co
   }
 }
 
+// slot of neighbour direction d (0 -z, 1 -y, 2 -x, 3 diag, 4 +x, 5 +y, 6 +z) in the sorted BSR row of cell c
+__device__ __forceinline__ int slot_of(int nx, int ny, int nz, int c, int d) {
+  const int ix = c % nx, iy = (c / nx) % ny, iz = c / (nx * ny);
+  const bool has[7] = {iz > 0, iy > 0, ix > 0, true, ix < nx - 1, iy < ny - 1, iz < nz - 1};
+  int s = 0;
+#pragma unroll
+  for (int e = 0; e < 7; ++e)
+    if (e < d) s += has[e];
+  return s;
+}
+
+// Factorisation D_i = A_ii - sum_{k lower} A_ik D_k^-1 A_ki and D_i^-1 (Gauss-Jordan with partial
+// pivoting), same pencil pipeline; the hand-off is the neighbour's D^-1 block (NaN-filled before).
+constexpr int FWARPS = 4;
+
+__global__ void __launch_bounds__(FWARPS * 32) k_ilu_factor_pipe(int nx, int ny, int nz,
+                                                                 const int32_t* __restrict__ rowptr,
+                                                                 const double* __restrict__ A, double* __restrict__ Dinv,
+                                                                 int* __restrict__ pipe, int* __restrict__ dstatus) {
+  __shared__ double sm[FWARPS][6][64];
+  const int lane = threadIdx.x & 31;
+  const int wid = threadIdx.x >> 5;
+  double* sD = sm[wid][0];
+  double* sI = sm[wid][1];
+  double* sL = sm[wid][2];
+  double* sU = sm[wid][3];
+  double* sK = sm[wid][4];
+  double* sP = sm[wid][5];  // D^-1 of the previous cell of this pencil
+  const int r = lane >> 2, c = (lane & 3) * 2;
+  const int npen = ny * nz, nxy = nx * ny;
+  int* counter = pipe;
+  int* abortf = pipe + 1;
+  for (;;) {
+    int p = 0;
+    if (lane == 0) p = atomicAdd(counter, 1);
+    p = __shfl_sync(FULL, p, 0);
+    if (p >= npen) return;
+    const int j = p % ny, k = p / ny;
+    const int base_jk = nx * (j + ny * k);
+    for (int x = 0; x < nx; ++x) {
+      const int i = base_jk + x;
+      const int base = __ldg(rowptr + i);
+      const int nlow = (k > 0) + (j > 0) + (x > 0);
+      double2 d = ld_nc2(A + (size_t)(base + nlow) * BB + 2 * lane);
+      // lower neighbours in pattern order -z, -y, -x
+#pragma unroll
+      for (int dl = 0; dl < 3; ++dl) {
+        const bool ex = (dl == 0) ? (k > 0) : (dl == 1) ? (j > 0) : (x > 0);
+        if (!ex) continue;
+        const int kk = (dl == 0) ? i - nxy : (dl == 1) ? i - nx : i - 1;
+        const int sl = slot_of(nx, ny, nz, i, dl);
+        const int su = slot_of(nx, ny, nz, kk, 6 - dl);
+        const double2 aik = ld_nc2(A + (size_t)(base + sl) * BB + 2 * lane);
+        const double2 aki = ld_nc2(A + (size_t)(__ldg(rowptr + kk) + su) * BB + 2 * lane);
+        double2 dk;
+        if (dl < 2) {
+          if (!poll_vec(Dinv + (size_t)kk * BB, 2 * lane, dk, abortf, dstatus)) return;
+        } else {
+          dk = make_double2(sP[2 * lane], sP[2 * lane + 1]);
+        }
+        __syncwarp();
+        sL[2 * lane] = aik.x;
+        sL[2 * lane + 1] = aik.y;
+        sU[2 * lane] = aki.x;
+        sU[2 * lane + 1] = aki.y;
+        sK[2 * lane] = dk.x;
+        sK[2 * lane + 1] = dk.y;
+        __syncwarp();
+        // M = D_k^-1 A_ki (entries (r, c), (r, c+1))
+        double m0 = 0.0, m1 = 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          m0 = fma(sK[r * 8 + q], sU[q * 8 + c], m0);
+          m1 = fma(sK[r * 8 + q], sU[q * 8 + c + 1], m1);
+        }
+        __syncwarp();
+        sU[r * 8 + c] = m0;  // reuse sU for M
+        sU[r * 8 + c + 1] = m1;
+        __syncwarp();
+        double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          s0 = fma(sL[r * 8 + q], sU[q * 8 + c], s0);
+          s1 = fma(sL[r * 8 + q], sU[q * 8 + c + 1], s1);
+        }
+        d.x -= s0;
+        d.y -= s1;
+        __syncwarp();
+      }
+      // invert D by Gauss-Jordan with partial pivoting
+      sD[2 * lane] = d.x;
+      sD[2 * lane + 1] = d.y;
+      sI[2 * lane] = (r == c) ? 1.0 : 0.0;
+      sI[2 * lane + 1] = (r == c + 1) ? 1.0 : 0.0;
+      __syncwarp();
+      bool bad = false;
+      for (int kp = 0; kp < 8; ++kp) {
+        int piv = kp;
+        double best = -1.0;
+        for (int q = kp; q < 8; ++q) {
+          const double v = fabs(sD[q * 8 + kp]);
+          if (v > best) {
+            best = v;
+            piv = q;
+          }
+        }
+        if (!(best > 0.0) || !isfinite(best)) {
+          bad = true;
+          break;
+        }
+        if (piv != kp && r == kp) {
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            double t1 = sD[kp * 8 + c + e];
+            sD[kp * 8 + c + e] = sD[piv * 8 + c + e];
+            sD[piv * 8 + c + e] = t1;
+            t1 = sI[kp * 8 + c + e];
+            sI[kp * 8 + c + e] = sI[piv * 8 + c + e];
+            sI[piv * 8 + c + e] = t1;
+          }
+        }
+        __syncwarp();
+        const double inv = 1.0 / sD[kp * 8 + kp];
+        const double f = sD[r * 8 + kp];
+        __syncwarp();
+        if (r == kp) {
+          sD[kp * 8 + c] *= inv;
+          sD[kp * 8 + c + 1] *= inv;
+          sI[kp * 8 + c] *= inv;
+          sI[kp * 8 + c + 1] *= inv;
+        }
+        __syncwarp();
+        if (r != kp) {
+          sD[r * 8 + c] -= f * sD[kp * 8 + c];
+          sD[r * 8 + c + 1] -= f * sD[kp * 8 + c + 1];
+          sI[r * 8 + c] -= f * sI[kp * 8 + c];
+          sI[r * 8 + c + 1] -= f * sI[kp * 8 + c + 1];
+        }
+        __syncwarp();
+      }
+      if (bad) {
+        if (lane == 0) {
+          atomicOr(dstatus, DS_SINGULAR);
+          atomicExch(abortf, 1);
+        }
+        return;
+      }
+      const double o0 = sI[2 * lane], o1 = sI[2 * lane + 1];
+      st_relaxed(Dinv + (size_t)i * BB + 2 * lane, o0);
+      st_relaxed(Dinv + (size_t)i * BB + 2 * lane + 1, o1);
+      sP[2 * lane] = o0;
+      sP[2 * lane + 1] = o1;
+      __syncwarp();
+    }
+  }
+}
+
 int pipe_blocks(int npen) {
   int warps = npen < 152 * 16 ? npen : 152 * 16;
   return (warps + 7) / 8;
 }
 
 }  // namespace
+
+void launch_ilu_factor_pipe(Handle& h, cudaStream_t s) {
+  const int npen = h.ny * h.nz;
+  cudaMemsetAsync(h.pipe, 0, 2 * sizeof(int), s);
+  cudaMemsetAsync(h.dinv, 0xff, sizeof(double) * (size_t)h.n * BB, s);  // NaN sentinel
+  const int warps = npen < 152 * 8 ? npen : 152 * 8;
+  k_ilu_factor_pipe<<<(warps + FWARPS - 1) / FWARPS, FWARPS * 32, 0, s>>>(h.nx, h.ny, h.nz, h.rowptr, h.J, h.dinv,
+                                                                          h.pipe, h.dstatus);
+}
 
 void launch_ilu_apply_pipe(Handle& h, const double* r, double* z, cudaStream_t s) {
   const int npen = h.ny * h.nz;

@@ -115,7 +115,8 @@ struct Handle {
   double* h_scal = nullptr;                       // pinned host mirror
   int* dstatus = nullptr;
   int* h_status = nullptr;                        // pinned
-  int* pipe = nullptr;                            // sweep counter, abort flag, per-pencil progress
+  int* pipe = nullptr;                            // sweep counter, abort flag
+  unsigned* red_counter = nullptr;                // last-block counter of the fused reductions
   int restart_alloc = 0;
   int red_blocks = 0;
   // flags
@@ -143,10 +144,12 @@ void launch_bjacobi_factor(Handle& h, cudaStream_t s);
 void launch_prec_apply(Handle& h, const double* r, double* z, cudaStream_t s);
 // pencil-pipelined ILU(0) sweeps (isc_ilu_pipe.cu)
 void launch_ilu_apply_pipe(Handle& h, const double* r, double* z, cudaStream_t s);
+void launch_ilu_factor_pipe(Handle& h, cudaStream_t s);
 void launch_update(Handle& h, cudaStream_t s);
 // BLAS-1 with fixed-order two-stage reductions; results land in h.scal[off..]
 void launch_mdot(Handle& h, const double* V, int nvec, const double* w, int off, cudaStream_t s);
 void launch_maxpy(Handle& h, double* w, const double* V, int nvec, int coef_off, double sign, cudaStream_t s);
+void launch_maxpy_norm(Handle& h, double* w, const double* V, int nvec, int coef_off, int out_off, cudaStream_t s);
 void launch_axpby(int n, double a, const double* x, double b, double* y, cudaStream_t s);
 void launch_scale_copy(int n, double a, const double* x, double* y, cudaStream_t s);
 void launch_axpy_dev(int n, const double* coef, double sign, const double* x, double* y, cudaStream_t s);

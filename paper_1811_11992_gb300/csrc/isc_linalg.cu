@@ -121,8 +121,9 @@ __global__ void __launch_bounds__(256) k_gj(int n, const int32_t* __restrict__ r
       if (lane == 0) atomicOr(dstatus, DS_SINGULAR);
       return;
     }
+    const double inv = 1.0 / pv;
 #pragma unroll
-    for (int m = 0; m < 2; ++m) a[m][k] = a[m][k] / pv;
+    for (int m = 0; m < 2; ++m) a[m][k] = a[m][k] * inv;
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
       if (r == k) continue;
@@ -285,34 +286,75 @@ __global__ void k_bjacobi_apply(int n, const double* __restrict__ Dinv, const do
 // ------------------------------------------------------------------ BLAS-1
 constexpr int RED_THREADS = 256;
 
-// partial[c * nblk + blk] = sum over the block's chunk of V_c . w
-__global__ void __launch_bounds__(RED_THREADS) k_mdot_partial(int len, const double* __restrict__ V, size_t vstride,
-                                                              const double* __restrict__ w, double* __restrict__ partial) {
-  const int c = blockIdx.y;
-  const double* v = V + (size_t)c * vstride;
-  double s = 0.0;
-  const int stride = gridDim.x * blockDim.x;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) s = fma(v[e], w[e], s);
-  __shared__ double sh[RED_THREADS / 32];
+__device__ __forceinline__ double block_sum(double s, double* sh) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+  __syncthreads();
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
   __syncthreads();
+  s = (threadIdx.x < RED_THREADS / 32) ? sh[threadIdx.x] : 0.0;
   if (threadIdx.x < 32) {
-    s = (threadIdx.x < RED_THREADS / 32) ? sh[threadIdx.x] : 0.0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
-    if (threadIdx.x == 0) partial[(size_t)c * gridDim.x + blockIdx.x] = s;
   }
+  return s;  // valid in thread 0
 }
 
-__global__ void k_mdot_final(int nblk, const double* __restrict__ partial, double* __restrict__ out) {
-  const int c = blockIdx.x;
-  double s = 0.0;
-  for (int b = threadIdx.x; b < nblk; b += 32) s += partial[(size_t)c * nblk + b];
+// The last block to finish sums the per-block partials of every result in a
+// fixed order (deterministic), writes out[c] and re-arms the counter.
+__device__ __forceinline__ void last_block_finish(int nres, const double* __restrict__ partial, unsigned* counter,
+                                                  double* __restrict__ out) {
+  __shared__ bool last;
+  __threadfence();
+  if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int c = warp; c < nres; c += RED_THREADS / 32) {
+    double s = 0.0;
+    for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(partial + (size_t)c * gridDim.x + b);
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
-  if (threadIdx.x == 0) out[c] = s;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+    if (lane == 0) out[c] = s;
+  }
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
+// out[c] = V_c . w for c < nvec, one pass over the vectors
+__global__ void __launch_bounds__(RED_THREADS) k_mdot(int len, const double* __restrict__ V, size_t vstride, int nvec,
+                                                      const double* __restrict__ w, double* __restrict__ partial,
+                                                      unsigned* counter, double* __restrict__ out) {
+  __shared__ double sh[RED_THREADS / 32];
+  const int stride = gridDim.x * blockDim.x;
+  for (int c = 0; c < nvec; ++c) {
+    const double* v = V + (size_t)c * vstride;
+    double s = 0.0;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) s = fma(v[e], w[e], s);
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) partial[(size_t)c * gridDim.x + blockIdx.x] = s;
+  }
+  last_block_finish(nvec, partial, counter, out);
+}
+
+// w -= sum_c coef[c] V_c and out[0] = ||w||^2 of the result
+__global__ void __launch_bounds__(RED_THREADS) k_maxpy_norm(int len, double* __restrict__ w, const double* __restrict__ V,
+                                                            size_t vstride, int nvec, const double* __restrict__ coef,
+                                                            double* __restrict__ partial, unsigned* counter,
+                                                            double* __restrict__ out) {
+  __shared__ double sh[RED_THREADS / 32];
+  const int stride = gridDim.x * blockDim.x;
+  double nrm = 0.0;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) {
+    double s = 0.0;
+    for (int c = 0; c < nvec; ++c) s = fma(coef[c], V[(size_t)c * vstride + e], s);
+    const double we = w[e] - s;
+    w[e] = we;
+    nrm = fma(we, we, nrm);
+  }
+  nrm = block_sum(nrm, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = nrm;
+  last_block_finish(1, partial, counter, out);
 }
 
 // w += sign * sum_c coef[c] V_c
@@ -401,13 +443,7 @@ void launch_spmv(int nrows, const int32_t* rowptr, const int32_t* col, const dou
   k_spmv<<<(int)(((size_t)nrows * 32 + tb - 1) / tb), tb, 0, s>>>(nrows, rowptr, col, val, x, y, unit_diag);
 }
 
-void launch_ilu_factor(Handle& h, cudaStream_t s) {
-  for (int L = 0; L < h.nlevels; ++L) {
-    int b = h.h_level_ptr[L], cnt = h.h_level_ptr[L + 1] - b;
-    k_ilu_factor<<<(cnt + FCELLS - 1) / FCELLS, 256, 0, s>>>(h.nx, h.ny, h.nz, h.level_cells + b, cnt, 1, h.rowptr,
-                                                               h.J, h.dinv, h.dstatus);
-  }
-}
+void launch_ilu_factor(Handle& h, cudaStream_t s) { launch_ilu_factor_pipe(h, s); }
 
 void launch_bjacobi_factor(Handle& h, cudaStream_t s) {
   // all cells at once, no lower-neighbour terms; level_cells holds every cell
@@ -434,9 +470,13 @@ void launch_update(Handle& h, cudaStream_t s) {
 
 void launch_mdot(Handle& h, const double* V, int nvec, const double* w, int off, cudaStream_t s) {
   const int len = h.n * 8;
-  dim3 grid(h.red_blocks, nvec);
-  k_mdot_partial<<<grid, RED_THREADS, 0, s>>>(len, V, (size_t)len, w, h.partial);
-  k_mdot_final<<<nvec, 32, 0, s>>>(h.red_blocks, h.partial, h.scal + off);
+  k_mdot<<<h.red_blocks, RED_THREADS, 0, s>>>(len, V, (size_t)len, nvec, w, h.partial, h.red_counter, h.scal + off);
+}
+
+void launch_maxpy_norm(Handle& h, double* w, const double* V, int nvec, int coef_off, int out_off, cudaStream_t s) {
+  const int len = h.n * 8;
+  k_maxpy_norm<<<h.red_blocks, RED_THREADS, 0, s>>>(len, w, V, (size_t)len, nvec, h.scal + coef_off, h.partial,
+                                                    h.red_counter, h.scal + out_off);
 }
 
 void launch_maxpy(Handle& h, double* w, const double* V, int nvec, int coef_off, double sign, cudaStream_t s) {
