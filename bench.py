@@ -205,6 +205,29 @@ def run_isc(args):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         e2e_val = world * e2e_steps / float(t.item())
     io_bytes = 9 * n * 8
+    # mixed precision on the same step: FP32 ILU(0) factors and sweeps inside the FP64 FGMRES
+    g.set_options(precision="mixed")
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    g.reset_stats()
+    ev0.record()
+    minfo = [step() for _ in range(args.steps)]
+    ev1.record()
+    torch.cuda.synchronize()
+    ms_mixed = ev0.elapsed_time(ev1) / args.steps
+    mstats = g.stats()
+    g.set_options(precision="fp64")
+    mixed = {"value": 1e3 / ms_mixed, "unit": UNIT, "ms_per_step": ms_mixed,
+             "krylov_iterations_per_step": statistics.median([i.krylov_iterations for i in minfo]),
+             "rel_residual": max(i.krylov_rel_residual for i in minfo),
+             "prec_apply_ms_per_call": mstats["prec_apply"]["ms"] / max(1, mstats["prec_apply"]["calls"]),
+             "solve_speedup_vs_fp64": None}
+    solve_fp64 = sum(stats[k]["ms"] for k in ("spmv", "prec_apply", "blas1", "ilu_factor")) / args.steps
+    solve_mixed = sum(mstats[k]["ms"] for k in ("spmv", "prec_apply", "blas1", "ilu_factor")) / args.steps
+    mixed["solve_ms_fp64"] = solve_fp64
+    mixed["solve_ms_mixed"] = solve_mixed
+    mixed["solve_speedup_vs_fp64"] = solve_fp64 / solve_mixed if solve_mixed > 0 else None
     # roofline of the dominant kernel class
     launches = sum(v["launches"] for v in stats.values())
     dom = max(stats, key=lambda k: stats[k]["ms"])
@@ -221,6 +244,7 @@ def run_isc(args):
         "kernel_launches": {k: v["launches"] for k, v in stats.items()},
         "roofline": roof,
         "clocks": clocks,
+        "mixed": mixed,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(max_seconds=30.0)

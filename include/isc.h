@@ -61,6 +61,10 @@ enum isc_status {
 
 enum isc_krylov { ISC_KRYLOV_GMRES = 0, ISC_KRYLOV_BICGSTAB = 1 };
 enum isc_prec { ISC_PREC_NONE = 0, ISC_PREC_BJACOBI = 1, ISC_PREC_BILU0 = 2 };
+/* Precision of the preconditioner: FP64 throughout, or mixed: the block
+ * ILU(0) factors are computed in FP64, stored and applied in FP32 inside the
+ * FP64 flexible GMRES (residual, SpMV, orthogonalisation and update stay FP64). */
+enum isc_precision { ISC_PRECISION_FP64 = 0, ISC_PRECISION_MIXED = 1 };
 enum isc_rxn_kind {
   ISC_RXN_OIL_OXIDATION = 0,   /* r = A e^{-Ea/RT} (y_O2 p)(phi_f S_o rho_o x_i)           */
   ISC_RXN_CRACKING = 1,        /* r = A e^{-Ea/RT} (phi_f S_o rho_o x_i)(1-(C_c/C_max)^5)  */
@@ -158,6 +162,7 @@ typedef struct isc_options {
   double max_dp_frac;           /* |dp| <= max_dp_frac p (0.2) */
   double max_dT;                /* |dT| <= max_dT (50 K) */
   int32_t profile;              /* 1: record per-kernel CUDA-event times */
+  int32_t precision;            /* isc_precision (applies to ISC_PREC_BILU0) */
   void* stream;
 } isc_options;
 

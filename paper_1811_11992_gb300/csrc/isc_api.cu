@@ -114,7 +114,7 @@ int dalloc(isc_handle* h, T** p, size_t count) {
 void free_all(isc_handle* h) {
   void* ptrs[] = {h->rowptr, h->col, h->level_cells, h->phi_ref, h->depth, h->tx, h->ty, h->tz, h->well_slot,
                   h->slots, h->u, h->coke, h->u_n, h->coke_n, h->acc_n, h->props, h->R, h->J, h->ntot, h->du,
-                  h->rhs, h->dinv, h->V, h->Z, h->w, h->tmp, h->partial, h->scal, h->dstatus, h->pipe, h->red_counter};
+                  h->rhs, h->dinv, h->J32, h->dinv32, h->vec32, h->V, h->Z, h->w, h->tmp, h->partial, h->scal, h->dstatus, h->pipe, h->red_counter};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->h_scal) cudaFreeHost(h->h_scal);
@@ -146,8 +146,21 @@ void prec(isc_handle* h, const double* r, double* z) {
 
 int build_prec(isc_handle* h) {
   if (h->opt.prec == ISC_PREC_BILU0) {
-    Region rg(h, ISC_K_ILU_FACTOR, 1);
+    const bool mixed = h->opt.precision == ISC_PRECISION_MIXED;
+    if (mixed && !h->J32) {
+      // first mixed-precision use: FP32 copies of the blocks and D^-1, two FP32 sweep vectors
+      int e = 0;
+      e |= dalloc(h, &h->J32, (size_t)h->nnzb * BB);
+      e |= dalloc(h, &h->dinv32, (size_t)h->n * BB);
+      e |= dalloc(h, &h->vec32, (size_t)h->n * 16);
+      if (e) return ISC_ERR_NOMEM;
+    }
+    Region rg(h, ISC_K_ILU_FACTOR, mixed ? 3 : 1);
     launch_ilu_factor(*h, h->stream);
+    if (mixed) {
+      launch_to_f32((size_t)h->nnzb * BB, h->J, h->J32, h->stream);
+      launch_to_f32((size_t)h->n * BB, h->dinv, h->dinv32, h->stream);
+    }
   } else if (h->opt.prec == ISC_PREC_BJACOBI) {
     Region rg(h, ISC_K_ILU_FACTOR, 1);
     launch_bjacobi_factor(*h, h->stream);
@@ -364,6 +377,8 @@ int validate_options(isc_handle* h, const isc_options& o) {
   if (o.krylov != ISC_KRYLOV_GMRES && o.krylov != ISC_KRYLOV_BICGSTAB)
     return set_err(h, ISC_ERR_INVALID_ARG, "unknown krylov method");
   if (o.prec < ISC_PREC_NONE || o.prec > ISC_PREC_BILU0) return set_err(h, ISC_ERR_INVALID_ARG, "unknown preconditioner");
+  if (o.precision != ISC_PRECISION_FP64 && o.precision != ISC_PRECISION_MIXED)
+    return set_err(h, ISC_ERR_INVALID_ARG, "unknown precision");
   if (!(o.tol_lin > 0.0) || o.maxit_lin < 1 || !(o.tol_newton >= 0.0) || o.maxit_newton < 1)
     return set_err(h, ISC_ERR_INVALID_ARG, "tolerances must be positive and iteration limits >= 1");
   return ISC_OK;
@@ -386,6 +401,7 @@ void isc_default_options(isc_options* o) {
   o->max_dp_frac = 0.2;
   o->max_dT = 50.0;
   o->profile = 0;
+  o->precision = ISC_PRECISION_FP64;
   o->stream = nullptr;
 }
 

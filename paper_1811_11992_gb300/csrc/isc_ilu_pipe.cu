@@ -42,19 +42,38 @@ __device__ __forceinline__ void st_relaxed(double* p, double v) {
 
 __device__ __forceinline__ double2 ld_nc2(const double* p) { return __ldg(reinterpret_cast<const double2*>(p)); }
 
-// Poll the 64-byte block vector v[8] of a neighbouring pencil until every
-// entry is a number: the output vector is filled with NaN before the sweep and
-// each 8-byte store is single-copy atomic, so a non-NaN entry is final. The
-// data itself is the hand-off (one L2 round trip, no flags or fences).
-// Returns false if the sweep was aborted (timeout here or elsewhere).
-__device__ __forceinline__ bool poll_vec(const double* v, int c, double2& out, int* abortf, int* dstatus) {
-  const double* p = v + c;
+// Vector element types of the sweeps: FP64 (all-FP64 solve) or FP32 (factors,
+// off-diagonal blocks and the hand-off vector of the mixed-precision solve).
+template <typename T> struct V2;
+template <> struct V2<double> { using t = double2; };
+template <> struct V2<float> { using t = float2; };
+
+__device__ __forceinline__ void ld_relaxed_v2(const double* p, double& a, double& b) {
+  asm volatile("ld.relaxed.gpu.global.v2.f64 {%0, %1}, [%2];" : "=d"(a), "=d"(b) : "l"(p) : "memory");
+}
+__device__ __forceinline__ void ld_relaxed_v2(const float* p, float& a, float& b) {
+  asm volatile("ld.relaxed.gpu.global.v2.f32 {%0, %1}, [%2];" : "=f"(a), "=f"(b) : "l"(p) : "memory");
+}
+__device__ __forceinline__ void st_relaxed(float* p, float v) {
+  asm volatile("st.relaxed.gpu.global.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+__device__ __forceinline__ float2 ld_nc2(const float* p) { return __ldg(reinterpret_cast<const float2*>(p)); }
+
+// Poll the block vector v[8] of a neighbouring pencil until every entry is a
+// number: the vector is filled with NaN before the sweep and each store is
+// single-copy atomic, so a non-NaN entry is final. The data itself is the
+// hand-off (one L2 round trip, no flags or fences). Returns false if the
+// sweep was aborted (timeout here or elsewhere).
+template <typename T>
+__device__ __forceinline__ bool poll_vec(const T* v, int c, typename V2<T>::t& out, int* abortf, int* dstatus) {
+  const T* p = v + c;
   for (int spins = 0;; ++spins) {
-    double a, b;
-    asm volatile("ld.relaxed.gpu.global.v2.f64 {%0, %1}, [%2];" : "=d"(a), "=d"(b) : "l"(p) : "memory");
+    T a, b;
+    ld_relaxed_v2(p, a, b);
     const bool ok = !isnan(a) && !isnan(b);
     if (__all_sync(FULL, ok)) {
-      out = make_double2(a, b);
+      out.x = a;
+      out.y = b;
       return true;
     }
     if ((spins & 63) == 63 && __any_sync(FULL, ld_relaxed(abortf) != 0)) return false;
@@ -69,57 +88,69 @@ __device__ __forceinline__ bool poll_vec(const double* v, int c, double2& out, i
   }
 }
 
-__device__ __forceinline__ double quad_sum(double v) {
+template <typename T>
+__device__ __forceinline__ T quad_sum(T v) {
   v += __shfl_xor_sync(FULL, v, 1);
   v += __shfl_xor_sync(FULL, v, 2);
   return v;
 }
 
 // operands of one cell that do not depend on the sweep
+template <typename T>
 struct Ops {
-  double2 a0, a1, a2, d;  // up to three off-diagonal blocks (lane's double2) and D^-1
-  double ri;
+  typename V2<T>::t a0, a1, a2, d;  // up to three off-diagonal blocks (lane's pair) and D^-1
+  T ri;
 };
 
 constexpr int PF = 4;  // prefetch distance in cells (register ring)
 
-__device__ __forceinline__ Ops load_fwd(int x, int nx, int base_jk, bool hy, bool hz, const int32_t* __restrict__ rowptr,
-                                        const double* __restrict__ A, const double* __restrict__ Dinv,
-                                        const double* __restrict__ rhs, int lane, int r) {
-  Ops o;
+template <typename T>
+__device__ __forceinline__ typename V2<T>::t zero2() {
+  typename V2<T>::t z;
+  z.x = T(0);
+  z.y = T(0);
+  return z;
+}
+
+template <typename TM, typename TR>
+__device__ __forceinline__ Ops<TM> load_fwd(int x, int base_jk, bool hy, bool hz, const int32_t* __restrict__ rowptr,
+                                            const TM* __restrict__ A, const TM* __restrict__ Dinv,
+                                            const TR* __restrict__ rhs, int lane, int r) {
+  Ops<TM> o;
   const int i = base_jk + x;
   const int base = __ldg(rowptr + i);
   int s = 0;
-  const double2 zero = make_double2(0.0, 0.0);
-  o.a0 = hz ? ld_nc2(A + (size_t)(base + s++) * BB + 2 * lane) : zero;  // -z
-  o.a1 = hy ? ld_nc2(A + (size_t)(base + s++) * BB + 2 * lane) : zero;  // -y
-  o.a2 = (x > 0) ? ld_nc2(A + (size_t)(base + s) * BB + 2 * lane) : zero;  // -x
+  o.a0 = hz ? ld_nc2(A + (size_t)(base + s++) * BB + 2 * lane) : zero2<TM>();    // -z
+  o.a1 = hy ? ld_nc2(A + (size_t)(base + s++) * BB + 2 * lane) : zero2<TM>();    // -y
+  o.a2 = (x > 0) ? ld_nc2(A + (size_t)(base + s) * BB + 2 * lane) : zero2<TM>();  // -x
   o.d = ld_nc2(Dinv + (size_t)i * BB + 2 * lane);
-  o.ri = __ldg(rhs + (size_t)i * 8 + r);
+  o.ri = (TM)__ldg(rhs + (size_t)i * 8 + r);
   return o;
 }
 
-__device__ __forceinline__ Ops load_bwd(int x, int nx, int base_jk, int nlow_jk, bool hy, bool hz,
-                                        const int32_t* __restrict__ rowptr, const double* __restrict__ A,
-                                        const double* __restrict__ Dinv, const double* __restrict__ yin, int lane,
-                                        int r) {
-  Ops o;
+template <typename TM>
+__device__ __forceinline__ Ops<TM> load_bwd(int x, int nx, int base_jk, int nlow_jk, bool hy, bool hz,
+                                            const int32_t* __restrict__ rowptr, const TM* __restrict__ A,
+                                            const TM* __restrict__ Dinv, const TM* __restrict__ yin, int lane, int r) {
+  Ops<TM> o;
   const int i = base_jk + x;
   const int base = __ldg(rowptr + i);
   int s = nlow_jk + (x > 0) + 1;  // first slot after the diagonal
-  const double2 zero = make_double2(0.0, 0.0);
-  o.a2 = (x < nx - 1) ? ld_nc2(A + (size_t)(base + s++) * BB + 2 * lane) : zero;  // +x
-  o.a1 = hy ? ld_nc2(A + (size_t)(base + s++) * BB + 2 * lane) : zero;            // +y
-  o.a0 = hz ? ld_nc2(A + (size_t)(base + s) * BB + 2 * lane) : zero;              // +z
+  o.a2 = (x < nx - 1) ? ld_nc2(A + (size_t)(base + s++) * BB + 2 * lane) : zero2<TM>();  // +x
+  o.a1 = hy ? ld_nc2(A + (size_t)(base + s++) * BB + 2 * lane) : zero2<TM>();            // +y
+  o.a0 = hz ? ld_nc2(A + (size_t)(base + s) * BB + 2 * lane) : zero2<TM>();              // +z
   o.d = ld_nc2(Dinv + (size_t)i * BB + 2 * lane);
   o.ri = __ldg(yin + (size_t)i * 8 + r);
   return o;
 }
 
+// forward sweep: TM = matrix/vector precision, rhs always FP64
+template <typename TM>
 __global__ void __launch_bounds__(256) k_ilu_fwd_pipe(int nx, int ny, int nz, const int32_t* __restrict__ rowptr,
-                                                      const double* __restrict__ A, const double* __restrict__ Dinv,
-                                                      const double* __restrict__ rhs, double* __restrict__ y,
+                                                      const TM* __restrict__ A, const TM* __restrict__ Dinv,
+                                                      const double* __restrict__ rhs, TM* __restrict__ y,
                                                       int* __restrict__ pipe, int* __restrict__ dstatus) {
+  using T2 = typename V2<TM>::t;
   const int lane = threadIdx.x & 31;
   const int r = lane >> 2, c = (lane & 3) * 2;
   const int npen = ny * nz, nxy = nx * ny;
@@ -133,33 +164,33 @@ __global__ void __launch_bounds__(256) k_ilu_fwd_pipe(int nx, int ny, int nz, co
     const int j = p % ny, k = p / ny;
     const bool hy = j > 0, hz = k > 0;
     const int base_jk = nx * (j + ny * k);
-    Ops ring[PF];
+    Ops<TM> ring[PF];
 #pragma unroll
     for (int q = 0; q < PF; ++q)
-      if (q < nx) ring[q] = load_fwd(q, nx, base_jk, hy, hz, rowptr, A, Dinv, rhs, lane, r);
-    double yp0 = 0.0, yp1 = 0.0;
+      if (q < nx) ring[q] = load_fwd<TM, double>(q, base_jk, hy, hz, rowptr, A, Dinv, rhs, lane, r);
+    TM yp0 = TM(0), yp1 = TM(0);
     for (int x0 = 0; x0 < nx; x0 += PF) {
 #pragma unroll
       for (int q = 0; q < PF; ++q) {
         const int x = x0 + q;
         if (x >= nx) break;
-        const Ops o = ring[q];
-        if (x + PF < nx) ring[q] = load_fwd(x + PF, nx, base_jk, hy, hz, rowptr, A, Dinv, rhs, lane, r);
+        const Ops<TM> o = ring[q];
+        if (x + PF < nx) ring[q] = load_fwd<TM, double>(x + PF, base_jk, hy, hz, rowptr, A, Dinv, rhs, lane, r);
         const int i = base_jk + x;
-        double acc = fma(o.a2.x, yp0, o.a2.y * yp1);
+        TM acc = fma(o.a2.x, yp0, o.a2.y * yp1);
         if (hz) {
-          double2 v;
-          if (!poll_vec(y + (size_t)(i - nxy) * 8, c, v, abortf, dstatus)) return;
+          T2 v;
+          if (!poll_vec<TM>(y + (size_t)(i - nxy) * 8, c, v, abortf, dstatus)) return;
           acc = fma(o.a0.x, v.x, fma(o.a0.y, v.y, acc));
         }
         if (hy) {
-          double2 v;
-          if (!poll_vec(y + (size_t)(i - nx) * 8, c, v, abortf, dstatus)) return;
+          T2 v;
+          if (!poll_vec<TM>(y + (size_t)(i - nx) * 8, c, v, abortf, dstatus)) return;
           acc = fma(o.a1.x, v.x, fma(o.a1.y, v.y, acc));
         }
-        const double t = o.ri - quad_sum(acc);
-        const double t0 = __shfl_sync(FULL, t, 4 * c), t1 = __shfl_sync(FULL, t, 4 * c + 4);
-        const double yr = quad_sum(fma(o.d.x, t0, o.d.y * t1));
+        const TM t = o.ri - quad_sum(acc);
+        const TM t0 = __shfl_sync(FULL, t, 4 * c), t1 = __shfl_sync(FULL, t, 4 * c + 4);
+        const TM yr = quad_sum(fma(o.d.x, t0, o.d.y * t1));
         if ((lane & 3) == 0) st_relaxed(y + (size_t)i * 8 + r, yr);
         yp0 = __shfl_sync(FULL, yr, 4 * c);
         yp1 = __shfl_sync(FULL, yr, 4 * c + 4);
@@ -168,10 +199,14 @@ __global__ void __launch_bounds__(256) k_ilu_fwd_pipe(int nx, int ny, int nz, co
   }
 }
 
+// backward sweep: hand-off through zs (precision TM); z64, if given, receives the FP64 result
+template <typename TM>
 __global__ void __launch_bounds__(256) k_ilu_bwd_pipe(int nx, int ny, int nz, const int32_t* __restrict__ rowptr,
-                                                      const double* __restrict__ A, const double* __restrict__ Dinv,
-                                                      const double* __restrict__ yin, double* __restrict__ z,
-                                                      int* __restrict__ pipe, int* __restrict__ dstatus) {
+                                                      const TM* __restrict__ A, const TM* __restrict__ Dinv,
+                                                      const TM* __restrict__ yin, TM* __restrict__ zs,
+                                                      double* __restrict__ z64, int* __restrict__ pipe,
+                                                      int* __restrict__ dstatus) {
+  using T2 = typename V2<TM>::t;
   const int lane = threadIdx.x & 31;
   const int r = lane >> 2, c = (lane & 3) * 2;
   const int npen = ny * nz, nxy = nx * ny;
@@ -187,36 +222,39 @@ __global__ void __launch_bounds__(256) k_ilu_bwd_pipe(int nx, int ny, int nz, co
     const bool hy = j < ny - 1, hz = k < nz - 1;
     const int nlow_jk = (k > 0) + (j > 0);
     const int base_jk = nx * (j + ny * k);
-    Ops ring[PF];
+    Ops<TM> ring[PF];
 #pragma unroll
     for (int q = 0; q < PF; ++q)
-      if (q < nx) ring[q] = load_bwd(nx - 1 - q, nx, base_jk, nlow_jk, hy, hz, rowptr, A, Dinv, yin, lane, r);
-    double zp0 = 0.0, zp1 = 0.0;
+      if (q < nx) ring[q] = load_bwd<TM>(nx - 1 - q, nx, base_jk, nlow_jk, hy, hz, rowptr, A, Dinv, yin, lane, r);
+    TM zp0 = TM(0), zp1 = TM(0);
     for (int x0 = 0; x0 < nx; x0 += PF) {
 #pragma unroll
       for (int q = 0; q < PF; ++q) {
         const int step = x0 + q;
         if (step >= nx) break;
         const int x = nx - 1 - step;
-        const Ops o = ring[q];
+        const Ops<TM> o = ring[q];
         if (step + PF < nx)
-          ring[q] = load_bwd(x - PF, nx, base_jk, nlow_jk, hy, hz, rowptr, A, Dinv, yin, lane, r);
+          ring[q] = load_bwd<TM>(x - PF, nx, base_jk, nlow_jk, hy, hz, rowptr, A, Dinv, yin, lane, r);
         const int i = base_jk + x;
-        double acc = fma(o.a2.x, zp0, o.a2.y * zp1);
+        TM acc = fma(o.a2.x, zp0, o.a2.y * zp1);
         if (hz) {
-          double2 v;
-          if (!poll_vec(z + (size_t)(i + nxy) * 8, c, v, abortf, dstatus)) return;
+          T2 v;
+          if (!poll_vec<TM>(zs + (size_t)(i + nxy) * 8, c, v, abortf, dstatus)) return;
           acc = fma(o.a0.x, v.x, fma(o.a0.y, v.y, acc));
         }
         if (hy) {
-          double2 v;
-          if (!poll_vec(z + (size_t)(i + nx) * 8, c, v, abortf, dstatus)) return;
+          T2 v;
+          if (!poll_vec<TM>(zs + (size_t)(i + nx) * 8, c, v, abortf, dstatus)) return;
           acc = fma(o.a1.x, v.x, fma(o.a1.y, v.y, acc));
         }
-        const double sr = quad_sum(acc);
-        const double s0 = __shfl_sync(FULL, sr, 4 * c), s1 = __shfl_sync(FULL, sr, 4 * c + 4);
-        const double zr = o.ri - quad_sum(fma(o.d.x, s0, o.d.y * s1));
-        if ((lane & 3) == 0) st_relaxed(z + (size_t)i * 8 + r, zr);
+        const TM sr = quad_sum(acc);
+        const TM s0 = __shfl_sync(FULL, sr, 4 * c), s1 = __shfl_sync(FULL, sr, 4 * c + 4);
+        const TM zr = o.ri - quad_sum(fma(o.d.x, s0, o.d.y * s1));
+        if ((lane & 3) == 0) {
+          st_relaxed(zs + (size_t)i * 8 + r, zr);
+          if (z64) z64[(size_t)i * 8 + r] = (double)zr;
+        }
         zp0 = __shfl_sync(FULL, zr, 4 * c);
         zp1 = __shfl_sync(FULL, zr, 4 * c + 4);
       }
@@ -280,7 +318,7 @@ __global__ void __launch_bounds__(FWARPS * 32) k_ilu_factor_pipe(int nx, int ny,
         const double2 aki = ld_nc2(A + (size_t)(__ldg(rowptr + kk) + su) * BB + 2 * lane);
         double2 dk;
         if (dl < 2) {
-          if (!poll_vec(Dinv + (size_t)kk * BB, 2 * lane, dk, abortf, dstatus)) return;
+          if (!poll_vec<double>(Dinv + (size_t)kk * BB, 2 * lane, dk, abortf, dstatus)) return;
         } else {
           dk = make_double2(sP[2 * lane], sP[2 * lane + 1]);
         }
@@ -399,17 +437,28 @@ void launch_ilu_factor_pipe(Handle& h, cudaStream_t s) {
 
 void launch_ilu_apply_pipe(Handle& h, const double* r, double* z, cudaStream_t s) {
   const int npen = h.ny * h.nz;
-  const size_t vbytes = sizeof(double) * (size_t)h.n * 8;
+  const size_t n8 = (size_t)h.n * 8;
   cudaMemsetAsync(h.pipe, 0, 2 * sizeof(int), s);
-  cudaMemsetAsync(h.tmp, 0xff, vbytes, s);  // NaN sentinel
-  k_ilu_fwd_pipe<<<pipe_blocks(npen), 256, 0, s>>>(h.nx, h.ny, h.nz, h.rowptr, h.J, h.dinv, r, h.tmp, h.pipe,
-                                                    h.dstatus);
+  if (h.opt.precision == ISC_PRECISION_MIXED) {
+    float* y32 = h.vec32;
+    float* z32 = h.vec32 + n8;
+    cudaMemsetAsync(y32, 0xff, sizeof(float) * n8, s);  // NaN sentinel
+    k_ilu_fwd_pipe<float><<<pipe_blocks(npen), 256, 0, s>>>(h.nx, h.ny, h.nz, h.rowptr, h.J32, h.dinv32, r, y32,
+                                                             h.pipe, h.dstatus);
+    cudaMemsetAsync(h.pipe, 0, 2 * sizeof(int), s);
+    cudaMemsetAsync(z32, 0xff, sizeof(float) * n8, s);
+    k_ilu_bwd_pipe<float><<<pipe_blocks(npen), 256, 0, s>>>(h.nx, h.ny, h.nz, h.rowptr, h.J32, h.dinv32, y32, z32,
+                                                             z, h.pipe, h.dstatus);
+    return;
+  }
+  cudaMemsetAsync(h.tmp, 0xff, sizeof(double) * n8, s);  // NaN sentinel
+  k_ilu_fwd_pipe<double><<<pipe_blocks(npen), 256, 0, s>>>(h.nx, h.ny, h.nz, h.rowptr, h.J, h.dinv, r, h.tmp, h.pipe,
+                                                            h.dstatus);
   cudaMemsetAsync(h.pipe, 0, 2 * sizeof(int), s);
-  cudaMemsetAsync(z, 0xff, vbytes, s);
-  k_ilu_bwd_pipe<<<pipe_blocks(npen), 256, 0, s>>>(h.nx, h.ny, h.nz, h.rowptr, h.J, h.dinv, h.tmp, z, h.pipe,
-                                                    h.dstatus);
+  cudaMemsetAsync(z, 0xff, sizeof(double) * n8, s);
+  k_ilu_bwd_pipe<double><<<pipe_blocks(npen), 256, 0, s>>>(h.nx, h.ny, h.nz, h.rowptr, h.J, h.dinv, h.tmp, z, nullptr,
+                                                            h.pipe, h.dstatus);
 }
-
 
 // ---------------------------------------------------------------------------
 // Allocation-free variant of the ILU(0) apply for callers that cannot call
@@ -468,10 +517,11 @@ extern "C" int isc_bilu0_apply_noalloc(int32_t nx, int32_t ny, int32_t nz, const
   // keeps the previous call's contents
   if (cudaMemsetAsync(ints, 0, NOALLOC_INTS * sizeof(int), s) != cudaSuccess) return ISC_ERR_CUDA;
   cudaMemsetAsync(y, 0xff, vbytes, s);
-  k_ilu_fwd_pipe<<<pipe_blocks(npen), 256, 0, s>>>(nx, ny, nz, d_rowptr, d_A, d_Dinv, d_r, y, pipe, status);
+  k_ilu_fwd_pipe<double><<<pipe_blocks(npen), 256, 0, s>>>(nx, ny, nz, d_rowptr, d_A, d_Dinv, d_r, y, pipe, status);
   cudaMemsetAsync(pipe, 0, 2 * sizeof(int), s);
   cudaMemsetAsync(d_z, 0xff, vbytes, s);
-  k_ilu_bwd_pipe<<<pipe_blocks(npen), 256, 0, s>>>(nx, ny, nz, d_rowptr, d_A, d_Dinv, y, d_z, pipe, status);
+  k_ilu_bwd_pipe<double><<<pipe_blocks(npen), 256, 0, s>>>(nx, ny, nz, d_rowptr, d_A, d_Dinv, y, d_z, nullptr, pipe,
+                                                            status);
   int h_status = 0;
   if (cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return ISC_ERR_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return ISC_ERR_CUDA;

@@ -105,6 +105,9 @@ struct Handle {
   double* du = nullptr;                           // Newton update, block-major 8N
   double* rhs = nullptr;                          // -F, right-hand side of the solve
   double* dinv = nullptr;                         // preconditioner diagonal inverses N*64
+  float* J32 = nullptr;                           // mixed precision: FP32 copy of the decoupled blocks
+  float* dinv32 = nullptr;                        // mixed precision: FP32 D^-1
+  float* vec32 = nullptr;                         // mixed precision: 2 x 8N FP32 sweep vectors
   // Krylov workspace
   double* V = nullptr;                            // (restart+1) vectors of 8N
   double* Z = nullptr;                            // restart preconditioned vectors
@@ -146,6 +149,7 @@ void launch_prec_apply(Handle& h, const double* r, double* z, cudaStream_t s);
 void launch_ilu_apply_pipe(Handle& h, const double* r, double* z, cudaStream_t s);
 void launch_ilu_factor_pipe(Handle& h, cudaStream_t s);
 void launch_update(Handle& h, cudaStream_t s);
+void launch_to_f32(size_t n, const double* x, float* y, cudaStream_t s);
 // BLAS-1 with fixed-order two-stage reductions; results land in h.scal[off..]
 void launch_mdot(Handle& h, const double* V, int nvec, const double* w, int off, cudaStream_t s);
 void launch_maxpy(Handle& h, double* w, const double* V, int nvec, int coef_off, double sign, cudaStream_t s);

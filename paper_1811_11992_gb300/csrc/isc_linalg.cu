@@ -302,18 +302,18 @@ __device__ __forceinline__ double block_sum(double s, double* sh) {
 
 // The last block to finish sums the per-block partials of every result in a
 // fixed order (deterministic), writes out[c] and re-arms the counter.
-__device__ __forceinline__ void last_block_finish(int nres, const double* __restrict__ partial, unsigned* counter,
-                                                  double* __restrict__ out) {
+__device__ __forceinline__ void last_block_finish(int nres, int nblk_x, const double* __restrict__ partial,
+                                                  unsigned* counter, double* __restrict__ out) {
   __shared__ bool last;
   __threadfence();
-  if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x * gridDim.y - 1);
   __syncthreads();
   if (!last) return;
   __threadfence();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int c = warp; c < nres; c += RED_THREADS / 32) {
     double s = 0.0;
-    for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(partial + (size_t)c * gridDim.x + b);
+    for (int b = lane; b < nblk_x; b += 32) s += __ldcg(partial + (size_t)c * nblk_x + b);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
     if (lane == 0) out[c] = s;
@@ -321,20 +321,39 @@ __device__ __forceinline__ void last_block_finish(int nres, const double* __rest
   if (threadIdx.x == 0) *counter = 0u;
 }
 
-// out[c] = V_c . w for c < nvec, one pass over the vectors
+constexpr int DOT_G = 8;  // vectors per block row of the grid (register accumulators)
+
+// out[c] = V_c . w for c < nvec; blockIdx.y takes vectors DOT_G*y .. DOT_G*y+DOT_G-1
 __global__ void __launch_bounds__(RED_THREADS) k_mdot(int len, const double* __restrict__ V, size_t vstride, int nvec,
                                                       const double* __restrict__ w, double* __restrict__ partial,
                                                       unsigned* counter, double* __restrict__ out) {
-  __shared__ double sh[RED_THREADS / 32];
+  __shared__ double sh[DOT_G][RED_THREADS / 32];
+  const int c0 = blockIdx.y * DOT_G;
   const int stride = gridDim.x * blockDim.x;
-  for (int c = 0; c < nvec; ++c) {
-    const double* v = V + (size_t)c * vstride;
-    double s = 0.0;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) s = fma(v[e], w[e], s);
-    s = block_sum(s, sh);
-    if (threadIdx.x == 0) partial[(size_t)c * gridDim.x + blockIdx.x] = s;
+  double acc[DOT_G];
+#pragma unroll
+  for (int g = 0; g < DOT_G; ++g) acc[g] = 0.0;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) {
+    const double we = w[e];
+#pragma unroll
+    for (int g = 0; g < DOT_G; ++g)
+      if (c0 + g < nvec) acc[g] = fma(V[(size_t)(c0 + g) * vstride + e], we, acc[g]);
   }
-  last_block_finish(nvec, partial, counter, out);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int g = 0; g < DOT_G; ++g) {
+    double v = acc[g];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    if (lane == 0) sh[g][warp] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < DOT_G && c0 + (int)threadIdx.x < nvec) {
+    double v = 0.0;
+    for (int q = 0; q < RED_THREADS / 32; ++q) v += sh[threadIdx.x][q];
+    partial[(size_t)(c0 + threadIdx.x) * gridDim.x + blockIdx.x] = v;
+  }
+  last_block_finish(nvec, gridDim.x, partial, counter, out);
 }
 
 // w -= sum_c coef[c] V_c and out[0] = ||w||^2 of the result
@@ -354,7 +373,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_maxpy_norm(int len, double* __r
   }
   nrm = block_sum(nrm, sh);
   if (threadIdx.x == 0) partial[blockIdx.x] = nrm;
-  last_block_finish(1, partial, counter, out);
+  last_block_finish(1, gridDim.x, partial, counter, out);
 }
 
 // w += sign * sum_c coef[c] V_c
@@ -423,6 +442,11 @@ __global__ void k_update(int n, double* __restrict__ u, const double* __restrict
   for (int k = 0; k < 8; ++k) u[(size_t)k * n + i] = un[k];
 }
 
+__global__ void k_to_f32(size_t n, const double* __restrict__ x, float* __restrict__ y) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += stride) y[e] = (float)x[e];
+}
+
 int grid_for(size_t work, int tb) {
   size_t b = (work + tb - 1) / tb;
   if (b > 152 * 16) b = 152 * 16;
@@ -464,13 +488,18 @@ void launch_prec_apply(Handle& h, const double* r, double* z, cudaStream_t s) {
   launch_ilu_apply_pipe(h, r, z, s);
 }
 
+void launch_to_f32(size_t n, const double* x, float* y, cudaStream_t s) {
+  k_to_f32<<<grid_for(n, 256), 256, 0, s>>>(n, x, y);
+}
+
 void launch_update(Handle& h, cudaStream_t s) {
   k_update<<<(h.n + 127) / 128, 128, 0, s>>>(h.n, h.u, h.du, h.opt.max_dp_frac, h.opt.max_dT);
 }
 
 void launch_mdot(Handle& h, const double* V, int nvec, const double* w, int off, cudaStream_t s) {
   const int len = h.n * 8;
-  k_mdot<<<h.red_blocks, RED_THREADS, 0, s>>>(len, V, (size_t)len, nvec, w, h.partial, h.red_counter, h.scal + off);
+  dim3 grid(h.red_blocks, (nvec + DOT_G - 1) / DOT_G);
+  k_mdot<<<grid, RED_THREADS, 0, s>>>(len, V, (size_t)len, nvec, w, h.partial, h.red_counter, h.scal + off);
 }
 
 void launch_maxpy_norm(Handle& h, double* w, const double* V, int nvec, int coef_off, int out_off, cudaStream_t s) {

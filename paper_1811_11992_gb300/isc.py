@@ -28,6 +28,7 @@ STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "out of device 
           -9: "device wait timed out", -10: "not implemented", -11: "call order violated"}
 KRYLOV = {"gmres": 0, "bicgstab": 1}
 PREC = {"none": 0, "bjacobi": 1, "bilu0": 2, "ilu0": 2}
+PRECISION = {"fp64": 0, "mixed": 1}
 K_CLASSES = ("props", "flux", "norm", "gj", "ilu_factor", "spmv", "prec_apply", "blas1", "update")
 
 
@@ -76,7 +77,7 @@ class isc_options(C.Structure):
     _fields_ = [("krylov", C.c_int32), ("restart", C.c_int32), ("prec", C.c_int32), ("decouple", C.c_int32),
                 ("tol_lin", C.c_double), ("maxit_lin", C.c_int32), ("tol_newton", C.c_double),
                 ("maxit_newton", C.c_int32), ("max_dp_frac", C.c_double), ("max_dT", C.c_double),
-                ("profile", C.c_int32), ("stream", C.c_void_p)]
+                ("profile", C.c_int32), ("precision", C.c_int32), ("stream", C.c_void_p)]
 
 
 class isc_newton_info(C.Structure):
@@ -177,6 +178,8 @@ def default_options(**kw) -> isc_options:
             v = KRYLOV[v] if isinstance(v, str) else v
         if k == "prec":
             v = PREC[v] if isinstance(v, str) else v
+        if k == "precision":
+            v = PRECISION[v] if isinstance(v, str) else v
         setattr(o, k, v)
     return o
 
@@ -274,6 +277,8 @@ class Simulator:
                 v = KRYLOV[v] if isinstance(v, str) else v
             if k == "prec":
                 v = PREC[v] if isinstance(v, str) else v
+            if k == "precision":
+                v = PRECISION[v] if isinstance(v, str) else v
             setattr(self.options, k, v)
         self._check(self.lib.isc_set_options(self.h, C.byref(self.options)))
 

@@ -190,3 +190,42 @@ def test_newton_step_matches_oracle_on_tube(Simulator):
         assert d < 1e-7, (k, d)
         g.set_state(u)   # continue both from the oracle's iterate
     g.close()
+
+
+def _degenerate(name):
+    if name == "single":
+        case = inp.tube_case(n_cells=1)
+        case.wells = case.wells[:1]           # one cell holds one well
+        return case
+    if name == "pair":
+        return inp.tube_case(n_cells=2)
+    if name == "nx1":
+        return inp.small_box(1, 4, 3)
+    if name == "flat":
+        return inp.small_box(5, 3, 1)
+    raise ValueError(name)
+
+
+@pytest.mark.parametrize("name", ["single", "pair", "nx1", "flat"])
+def test_degenerate_grids(Simulator, name):
+    case = _degenerate(name)
+    a = inp.random_state(case, 31)
+    b = inp.random_state(case, 32)
+    dt = 60.0
+    g = _gpu_assembled(Simulator, case, a, b, dt)
+    acc_old = model.old_accumulation(case, a["u"], a["coke"])
+    Fo = model.residual(case, b["u"], a["coke"], acc_old, dt)
+    rp, col, J = g.jacobian()
+    _, _, Jo = model.jacobian(case, b["u"], a["coke"], acc_old, dt)
+    assert row_scaled_err(g.residual(), Fo) < 1e-10
+    assert jac_err(J, Jo, rp, case.n) < 1e-10
+    g.decouple()
+    rp, col, Jd = g.jacobian()
+    x = np.random.default_rng(2).standard_normal((8, case.n))
+    g.build_preconditioner()
+    z = g.precond_apply(x)
+    zo = linalg.ILU0Preconditioner(rp.astype(np.int64), col.astype(np.int64), Jd).apply(x.T.copy()).T
+    assert np.max(np.abs(z - zo)) <= 1e-11 * np.abs(zo).max()
+    info = g.solve()
+    assert info.krylov_rel_residual <= 1e-6
+    g.close()
