@@ -333,6 +333,9 @@ def faces(case):
         T = 2.0 * t_lo * t_hi / (t_lo + t_hi)
         gam = np.full(lo.size, area / h)
         out.append((lo, hi, T, gam))
+    if not out:   # a single cell has no interior faces
+        e = np.zeros(0, dtype=np.int64)
+        return e, e, np.zeros(0), np.zeros(0), np.zeros(0)
     lo = np.concatenate([o[0] for o in out])
     hi = np.concatenate([o[1] for o in out])
     T = np.concatenate([o[2] for o in out])

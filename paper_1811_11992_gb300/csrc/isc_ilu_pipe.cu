@@ -262,6 +262,207 @@ __global__ void __launch_bounds__(256) k_ilu_bwd_pipe(int nx, int ny, int nz, co
   }
 }
 
+// ------------------------------------------------------------------ tiled sweeps
+// A CTA of TW warps owns TW consecutive pencils (j0..j0+TW-1) of one k-plane.
+// Each warp keeps its whole pencil result in shared memory (NaN-filled), so
+// the j-neighbour hand-off inside the CTA is a shared-memory poll; only the
+// first (forward) / last (backward) warp of a tile and every k-neighbour go
+// through global memory. Tiles are taken from a counter in dependency order.
+// A warp that meets an abort stops its pencil but still reaches the CTA
+// barriers; the CTA then leaves together.
+constexpr int TW = 8;
+constexpr int TILE_MAX_NX = 256;
+
+__device__ __forceinline__ double ld_shared_volatile(const double* p) { return *(const volatile double*)p; }
+__device__ __forceinline__ float ld_shared_volatile(const float* p) { return *(const volatile float*)p; }
+
+template <typename T>
+__device__ __forceinline__ bool poll_smem(const T* v, int c, typename V2<T>::t& out, int* abortf, int* dstatus) {
+  for (int spins = 0;; ++spins) {
+    const T a = ld_shared_volatile(v + c), b = ld_shared_volatile(v + c + 1);
+    const bool ok = !isnan(a) && !isnan(b);
+    if (__all_sync(FULL, ok)) {
+      out.x = a;
+      out.y = b;
+      return true;
+    }
+    if ((spins & 255) == 255 && __any_sync(FULL, ld_relaxed(abortf) != 0)) return false;
+    if (spins > SPIN_LIMIT) {
+      if ((threadIdx.x & 31) == 0) {
+        atomicOr(dstatus, DS_TIMEOUT);
+        atomicExch(abortf, 1);
+      }
+      return false;
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void st_shared_volatile(T* p, T v) {
+  *(volatile T*)p = v;
+}
+
+template <typename TM>
+__global__ void __launch_bounds__(TW * 32) k_ilu_fwd_tile(int nx, int ny, int nz, const int32_t* __restrict__ rowptr,
+                                                          const TM* __restrict__ A, const TM* __restrict__ Dinv,
+                                                          const double* __restrict__ rhs, TM* __restrict__ y,
+                                                          int* __restrict__ pipe, int* __restrict__ dstatus) {
+  using T2 = typename V2<TM>::t;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TM* sy = reinterpret_cast<TM*>(smem_raw);
+  __shared__ int s_tile, s_abort;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int r = lane >> 2, c = (lane & 3) * 2;
+  const int nxy = nx * ny, ntj = (ny + TW - 1) / TW, ntiles = ntj * nz;
+  int* counter = pipe;
+  int* abortf = pipe + 1;
+  TM* mine = sy + (size_t)w * nx * 8;
+  const TM* prev = (w > 0) ? sy + (size_t)(w - 1) * nx * 8 : nullptr;
+  const TM nanv = TM(NAN);
+  for (;;) {
+    if (threadIdx.x == 0) {
+      s_tile = atomicAdd(counter, 1);
+      s_abort = 0;
+    }
+    for (int e = lane; e < nx * 8; e += 32) mine[e] = nanv;
+    __syncthreads();
+    const int t = s_tile;
+    if (t >= ntiles) return;
+    const int jt = t % ntj, k = t / ntj;
+    const int j = jt * TW + w;
+    bool ok = true;
+    if (j < ny) {
+      const bool hy = j > 0, hz = k > 0;
+      const int base_jk = nx * (j + ny * k);
+      Ops<TM> ring[PF];
+#pragma unroll
+      for (int q = 0; q < PF; ++q)
+        if (q < nx) ring[q] = load_fwd<TM, double>(q, base_jk, hy, hz, rowptr, A, Dinv, rhs, lane, r);
+      TM yp0 = TM(0), yp1 = TM(0);
+      for (int x0 = 0; x0 < nx && ok; x0 += PF) {
+#pragma unroll
+        for (int q = 0; q < PF; ++q) {
+          const int x = x0 + q;
+          if (x >= nx || !ok) break;
+          const Ops<TM> o = ring[q];
+          if (x + PF < nx) ring[q] = load_fwd<TM, double>(x + PF, base_jk, hy, hz, rowptr, A, Dinv, rhs, lane, r);
+          const int i = base_jk + x;
+          TM acc = fma(o.a2.x, yp0, o.a2.y * yp1);
+          if (hz) {
+            T2 v;
+            ok = poll_vec<TM>(y + (size_t)(i - nxy) * 8, c, v, abortf, dstatus);
+            if (!ok) break;
+            acc = fma(o.a0.x, v.x, fma(o.a0.y, v.y, acc));
+          }
+          if (hy) {
+            T2 v;
+            ok = (w > 0) ? poll_smem<TM>(prev + x * 8, c, v, abortf, dstatus)
+                         : poll_vec<TM>(y + (size_t)(i - nx) * 8, c, v, abortf, dstatus);
+            if (!ok) break;
+            acc = fma(o.a1.x, v.x, fma(o.a1.y, v.y, acc));
+          }
+          const TM tt = o.ri - quad_sum(acc);
+          const TM t0 = __shfl_sync(FULL, tt, 4 * c), t1 = __shfl_sync(FULL, tt, 4 * c + 4);
+          const TM yr = quad_sum(fma(o.d.x, t0, o.d.y * t1));
+          if ((lane & 3) == 0) {
+            st_relaxed(y + (size_t)i * 8 + r, yr);
+            st_shared_volatile(mine + x * 8 + r, yr);
+          }
+          yp0 = __shfl_sync(FULL, yr, 4 * c);
+          yp1 = __shfl_sync(FULL, yr, 4 * c + 4);
+        }
+      }
+    }
+    if (!ok && lane == 0) s_abort = 1;
+    __syncthreads();
+    if (s_abort) return;
+  }
+}
+
+template <typename TM>
+__global__ void __launch_bounds__(TW * 32) k_ilu_bwd_tile(int nx, int ny, int nz, const int32_t* __restrict__ rowptr,
+                                                          const TM* __restrict__ A, const TM* __restrict__ Dinv,
+                                                          const TM* __restrict__ yin, TM* __restrict__ zs,
+                                                          double* __restrict__ z64, int* __restrict__ pipe,
+                                                          int* __restrict__ dstatus) {
+  using T2 = typename V2<TM>::t;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TM* sz = reinterpret_cast<TM*>(smem_raw);
+  __shared__ int s_tile, s_abort;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int r = lane >> 2, c = (lane & 3) * 2;
+  const int nxy = nx * ny, ntj = (ny + TW - 1) / TW, ntiles = ntj * nz;
+  int* counter = pipe;
+  int* abortf = pipe + 1;
+  TM* mine = sz + (size_t)w * nx * 8;
+  const TM* next = (w < TW - 1) ? sz + (size_t)(w + 1) * nx * 8 : nullptr;
+  const TM nanv = TM(NAN);
+  for (;;) {
+    if (threadIdx.x == 0) {
+      s_tile = atomicAdd(counter, 1);
+      s_abort = 0;
+    }
+    for (int e = lane; e < nx * 8; e += 32) mine[e] = nanv;
+    __syncthreads();
+    const int g = s_tile;
+    if (g >= ntiles) return;
+    const int t = ntiles - 1 - g;
+    const int jt = t % ntj, k = t / ntj;
+    const int j = jt * TW + w;
+    bool ok = true;
+    if (j < ny) {
+      const bool hy = j < ny - 1, hz = k < nz - 1;
+      const bool hy_local = hy && (w < TW - 1);
+      const int nlow_jk = (k > 0) + (j > 0);
+      const int base_jk = nx * (j + ny * k);
+      Ops<TM> ring[PF];
+#pragma unroll
+      for (int q = 0; q < PF; ++q)
+        if (q < nx) ring[q] = load_bwd<TM>(nx - 1 - q, nx, base_jk, nlow_jk, hy, hz, rowptr, A, Dinv, yin, lane, r);
+      TM zp0 = TM(0), zp1 = TM(0);
+      for (int x0 = 0; x0 < nx && ok; x0 += PF) {
+#pragma unroll
+        for (int q = 0; q < PF; ++q) {
+          const int step = x0 + q;
+          if (step >= nx || !ok) break;
+          const int x = nx - 1 - step;
+          const Ops<TM> o = ring[q];
+          if (step + PF < nx)
+            ring[q] = load_bwd<TM>(x - PF, nx, base_jk, nlow_jk, hy, hz, rowptr, A, Dinv, yin, lane, r);
+          const int i = base_jk + x;
+          TM acc = fma(o.a2.x, zp0, o.a2.y * zp1);
+          if (hz) {
+            T2 v;
+            ok = poll_vec<TM>(zs + (size_t)(i + nxy) * 8, c, v, abortf, dstatus);
+            if (!ok) break;
+            acc = fma(o.a0.x, v.x, fma(o.a0.y, v.y, acc));
+          }
+          if (hy) {
+            T2 v;
+            ok = hy_local ? poll_smem<TM>(next + x * 8, c, v, abortf, dstatus)
+                          : poll_vec<TM>(zs + (size_t)(i + nx) * 8, c, v, abortf, dstatus);
+            if (!ok) break;
+            acc = fma(o.a1.x, v.x, fma(o.a1.y, v.y, acc));
+          }
+          const TM sr = quad_sum(acc);
+          const TM s0 = __shfl_sync(FULL, sr, 4 * c), s1 = __shfl_sync(FULL, sr, 4 * c + 4);
+          const TM zr = o.ri - quad_sum(fma(o.d.x, s0, o.d.y * s1));
+          if ((lane & 3) == 0) {
+            st_relaxed(zs + (size_t)i * 8 + r, zr);
+            st_shared_volatile(mine + x * 8 + r, zr);
+            if (z64) z64[(size_t)i * 8 + r] = (double)zr;
+          }
+          zp0 = __shfl_sync(FULL, zr, 4 * c);
+          zp1 = __shfl_sync(FULL, zr, 4 * c + 4);
+        }
+      }
+    }
+    if (!ok && lane == 0) s_abort = 1;
+    __syncthreads();
+    if (s_abort) return;
+  }
+}
+
 // slot of neighbour direction d (0 -z, 1 -y, 2 -x, 3 diag, 4 +x, 5 +y, 6 +z) in the sorted BSR row of cell c
 __device__ __forceinline__ int slot_of(int nx, int ny, int nz, int c, int d) {
   const int ix = c % nx, iy = (c / nx) % ny, iz = c / (nx * ny);
@@ -435,29 +636,41 @@ void launch_ilu_factor_pipe(Handle& h, cudaStream_t s) {
                                                                           h.pipe, h.dstatus);
 }
 
-void launch_ilu_apply_pipe(Handle& h, const double* r, double* z, cudaStream_t s) {
+template <typename TM>
+void sweep_pair(Handle& h, const TM* A, const TM* Dinv, const double* r, TM* y, TM* zs, double* z64, cudaStream_t s) {
   const int npen = h.ny * h.nz;
   const size_t n8 = (size_t)h.n * 8;
   cudaMemsetAsync(h.pipe, 0, 2 * sizeof(int), s);
-  if (h.opt.precision == ISC_PRECISION_MIXED) {
-    float* y32 = h.vec32;
-    float* z32 = h.vec32 + n8;
-    cudaMemsetAsync(y32, 0xff, sizeof(float) * n8, s);  // NaN sentinel
-    k_ilu_fwd_pipe<float><<<pipe_blocks(npen), 256, 0, s>>>(h.nx, h.ny, h.nz, h.rowptr, h.J32, h.dinv32, r, y32,
-                                                             h.pipe, h.dstatus);
+  cudaMemsetAsync(y, 0xff, sizeof(TM) * n8, s);  // NaN sentinel
+  if (h.nx <= TILE_MAX_NX) {
+    const int ntiles = ((h.ny + TW - 1) / TW) * h.nz;
+    const int blocks = ntiles < 152 ? ntiles : 152;
+    const size_t smem = sizeof(TM) * (size_t)TW * h.nx * 8;
+    if (smem > 48 * 1024) {
+      cudaFuncSetAttribute(k_ilu_fwd_tile<TM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(k_ilu_bwd_tile<TM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    }
+    k_ilu_fwd_tile<TM><<<blocks, TW * 32, smem, s>>>(h.nx, h.ny, h.nz, h.rowptr, A, Dinv, r, y, h.pipe, h.dstatus);
     cudaMemsetAsync(h.pipe, 0, 2 * sizeof(int), s);
-    cudaMemsetAsync(z32, 0xff, sizeof(float) * n8, s);
-    k_ilu_bwd_pipe<float><<<pipe_blocks(npen), 256, 0, s>>>(h.nx, h.ny, h.nz, h.rowptr, h.J32, h.dinv32, y32, z32,
-                                                             z, h.pipe, h.dstatus);
+    cudaMemsetAsync(zs, 0xff, sizeof(TM) * n8, s);
+    k_ilu_bwd_tile<TM><<<blocks, TW * 32, smem, s>>>(h.nx, h.ny, h.nz, h.rowptr, A, Dinv, y, zs, z64, h.pipe,
+                                                     h.dstatus);
     return;
   }
-  cudaMemsetAsync(h.tmp, 0xff, sizeof(double) * n8, s);  // NaN sentinel
-  k_ilu_fwd_pipe<double><<<pipe_blocks(npen), 256, 0, s>>>(h.nx, h.ny, h.nz, h.rowptr, h.J, h.dinv, r, h.tmp, h.pipe,
-                                                            h.dstatus);
+  k_ilu_fwd_pipe<TM><<<pipe_blocks(npen), 256, 0, s>>>(h.nx, h.ny, h.nz, h.rowptr, A, Dinv, r, y, h.pipe, h.dstatus);
   cudaMemsetAsync(h.pipe, 0, 2 * sizeof(int), s);
-  cudaMemsetAsync(z, 0xff, sizeof(double) * n8, s);
-  k_ilu_bwd_pipe<double><<<pipe_blocks(npen), 256, 0, s>>>(h.nx, h.ny, h.nz, h.rowptr, h.J, h.dinv, h.tmp, z, nullptr,
-                                                            h.pipe, h.dstatus);
+  cudaMemsetAsync(zs, 0xff, sizeof(TM) * n8, s);
+  k_ilu_bwd_pipe<TM><<<pipe_blocks(npen), 256, 0, s>>>(h.nx, h.ny, h.nz, h.rowptr, A, Dinv, y, zs, z64, h.pipe,
+                                                        h.dstatus);
+}
+
+void launch_ilu_apply_pipe(Handle& h, const double* r, double* z, cudaStream_t s) {
+  if (h.opt.precision == ISC_PRECISION_MIXED) {
+    const size_t n8 = (size_t)h.n * 8;
+    sweep_pair<float>(h, h.J32, h.dinv32, r, h.vec32, h.vec32 + n8, z, s);
+    return;
+  }
+  sweep_pair<double>(h, h.J, h.dinv, r, h.tmp, z, nullptr, s);
 }
 
 // ---------------------------------------------------------------------------

@@ -322,6 +322,7 @@ __device__ __forceinline__ void last_block_finish(int nres, int nblk_x, const do
 }
 
 constexpr int DOT_G = 8;  // vectors per block row of the grid (register accumulators)
+constexpr int MAX_VEC = 72;
 
 // out[c] = V_c . w for c < nvec; blockIdx.y takes vectors DOT_G*y .. DOT_G*y+DOT_G-1
 __global__ void __launch_bounds__(RED_THREADS) k_mdot(int len, const double* __restrict__ V, size_t vstride, int nvec,
@@ -356,18 +357,33 @@ __global__ void __launch_bounds__(RED_THREADS) k_mdot(int len, const double* __r
   last_block_finish(nvec, gridDim.x, partial, counter, out);
 }
 
+// s = sum_c coef[c] V_c[e] with DOT_G independent loads in flight per element
+__device__ __forceinline__ double comb(const double* __restrict__ V, size_t vstride, int nvec, const double* sc, int e) {
+  double s = 0.0;
+  for (int c0 = 0; c0 < nvec; c0 += DOT_G) {
+    double v[DOT_G];
+#pragma unroll
+    for (int g = 0; g < DOT_G; ++g) v[g] = (c0 + g < nvec) ? V[(size_t)(c0 + g) * vstride + e] : 0.0;
+#pragma unroll
+    for (int g = 0; g < DOT_G; ++g)
+      if (c0 + g < nvec) s = fma(sc[c0 + g], v[g], s);
+  }
+  return s;
+}
+
 // w -= sum_c coef[c] V_c and out[0] = ||w||^2 of the result
 __global__ void __launch_bounds__(RED_THREADS) k_maxpy_norm(int len, double* __restrict__ w, const double* __restrict__ V,
                                                             size_t vstride, int nvec, const double* __restrict__ coef,
                                                             double* __restrict__ partial, unsigned* counter,
                                                             double* __restrict__ out) {
   __shared__ double sh[RED_THREADS / 32];
+  __shared__ double sc[MAX_VEC];
+  for (int c = threadIdx.x; c < nvec; c += blockDim.x) sc[c] = coef[c];
+  __syncthreads();
   const int stride = gridDim.x * blockDim.x;
   double nrm = 0.0;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) {
-    double s = 0.0;
-    for (int c = 0; c < nvec; ++c) s = fma(coef[c], V[(size_t)c * vstride + e], s);
-    const double we = w[e] - s;
+    const double we = w[e] - comb(V, vstride, nvec, sc, e);
     w[e] = we;
     nrm = fma(we, we, nrm);
   }
@@ -379,12 +395,12 @@ __global__ void __launch_bounds__(RED_THREADS) k_maxpy_norm(int len, double* __r
 // w += sign * sum_c coef[c] V_c
 __global__ void k_maxpy(int len, double* __restrict__ w, const double* __restrict__ V, size_t vstride, int nvec,
                         const double* __restrict__ coef, double sign) {
+  __shared__ double sc[MAX_VEC];
+  for (int c = threadIdx.x; c < nvec; c += blockDim.x) sc[c] = coef[c];
+  __syncthreads();
   const int stride = gridDim.x * blockDim.x;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) {
-    double s = 0.0;
-    for (int c = 0; c < nvec; ++c) s = fma(coef[c], V[(size_t)c * vstride + e], s);
-    w[e] = fma(sign, s, w[e]);
-  }
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride)
+    w[e] = fma(sign, comb(V, vstride, nvec, sc, e), w[e]);
 }
 
 __global__ void k_axpby(int len, double a, const double* __restrict__ x, double b, double* __restrict__ y) {
