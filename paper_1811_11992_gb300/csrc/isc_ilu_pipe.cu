@@ -144,8 +144,23 @@ __device__ __forceinline__ Ops<TM> load_bwd(int x, int nx, int base_jk, int nlow
   return o;
 }
 
-// forward sweep: TM = matrix/vector precision, rhs always FP64
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
+// Pull the operands of a cell that is PD cells ahead into L2 (one request per
+// 128-byte line): the lower (forward) or upper (backward) blocks of its row and
+// its D^-1 block.
 template <typename TM>
+__device__ __forceinline__ void prefetch_cell(int i, int first_slot, int nblk, const int32_t* __restrict__ rowptr,
+                                              const TM* __restrict__ A, const TM* __restrict__ Dinv, int lane) {
+  constexpr int LANES_PER_LINE = 128 / (2 * sizeof(TM));
+  if (lane % LANES_PER_LINE != 0) return;
+  const int base = __ldg(rowptr + i);
+  for (int b = 0; b < nblk; ++b) prefetch_l2(A + (size_t)(base + first_slot + b) * BB + 2 * lane);
+  prefetch_l2(Dinv + (size_t)i * BB + 2 * lane);
+}
+
+// forward sweep: TM = matrix/vector precision, rhs always FP64
+template <typename TM, int PD>
 __global__ void __launch_bounds__(256) k_ilu_fwd_pipe(int nx, int ny, int nz, const int32_t* __restrict__ rowptr,
                                                       const TM* __restrict__ A, const TM* __restrict__ Dinv,
                                                       const double* __restrict__ rhs, TM* __restrict__ y,
@@ -176,6 +191,7 @@ __global__ void __launch_bounds__(256) k_ilu_fwd_pipe(int nx, int ny, int nz, co
         if (x >= nx) break;
         const Ops<TM> o = ring[q];
         if (x + PF < nx) ring[q] = load_fwd<TM, double>(x + PF, base_jk, hy, hz, rowptr, A, Dinv, rhs, lane, r);
+        if (PD > 0 && x + PD < nx) prefetch_cell<TM>(base_jk + x + PD, 0, (int)hz + (int)hy + 1, rowptr, A, Dinv, lane);
         const int i = base_jk + x;
         TM acc = fma(o.a2.x, yp0, o.a2.y * yp1);
         if (hz) {
@@ -200,7 +216,7 @@ __global__ void __launch_bounds__(256) k_ilu_fwd_pipe(int nx, int ny, int nz, co
 }
 
 // backward sweep: hand-off through zs (precision TM); z64, if given, receives the FP64 result
-template <typename TM>
+template <typename TM, int PD>
 __global__ void __launch_bounds__(256) k_ilu_bwd_pipe(int nx, int ny, int nz, const int32_t* __restrict__ rowptr,
                                                       const TM* __restrict__ A, const TM* __restrict__ Dinv,
                                                       const TM* __restrict__ yin, TM* __restrict__ zs,
@@ -236,6 +252,8 @@ __global__ void __launch_bounds__(256) k_ilu_bwd_pipe(int nx, int ny, int nz, co
         const Ops<TM> o = ring[q];
         if (step + PF < nx)
           ring[q] = load_bwd<TM>(x - PF, nx, base_jk, nlow_jk, hy, hz, rowptr, A, Dinv, yin, lane, r);
+        if (PD > 0 && step + PD < nx)
+          prefetch_cell<TM>(base_jk + x - PD, nlow_jk + (x - PD > 0) + 1, (int)hz + (int)hy + 1, rowptr, A, Dinv, lane);
         const int i = base_jk + x;
         TM acc = fma(o.a2.x, zp0, o.a2.y * zp1);
         if (hz) {
@@ -271,6 +289,9 @@ __global__ void __launch_bounds__(256) k_ilu_bwd_pipe(int nx, int ny, int nz, co
 // A warp that meets an abort stops its pencil but still reaches the CTA
 // barriers; the CTA then leaves together.
 constexpr int TW = 8;
+#ifndef SWEEP_PD
+#define SWEEP_PD 16  // L2 prefetch distance of the sweeps, in cells
+#endif
 constexpr int TILE_MAX_NX = 256;
 
 __device__ __forceinline__ double ld_shared_volatile(const double* p) { return *(const volatile double*)p; }
@@ -302,7 +323,7 @@ __device__ __forceinline__ void st_shared_volatile(T* p, T v) {
   *(volatile T*)p = v;
 }
 
-template <typename TM>
+template <typename TM, int PD>
 __global__ void __launch_bounds__(TW * 32) k_ilu_fwd_tile(int nx, int ny, int nz, const int32_t* __restrict__ rowptr,
                                                           const TM* __restrict__ A, const TM* __restrict__ Dinv,
                                                           const double* __restrict__ rhs, TM* __restrict__ y,
@@ -346,6 +367,8 @@ __global__ void __launch_bounds__(TW * 32) k_ilu_fwd_tile(int nx, int ny, int nz
           if (x >= nx || !ok) break;
           const Ops<TM> o = ring[q];
           if (x + PF < nx) ring[q] = load_fwd<TM, double>(x + PF, base_jk, hy, hz, rowptr, A, Dinv, rhs, lane, r);
+          if (PD > 0 && x + PD < nx)
+            prefetch_cell<TM>(base_jk + x + PD, 0, (int)hz + (int)hy + 1, rowptr, A, Dinv, lane);
           const int i = base_jk + x;
           TM acc = fma(o.a2.x, yp0, o.a2.y * yp1);
           if (hz) {
@@ -379,7 +402,7 @@ __global__ void __launch_bounds__(TW * 32) k_ilu_fwd_tile(int nx, int ny, int nz
   }
 }
 
-template <typename TM>
+template <typename TM, int PD>
 __global__ void __launch_bounds__(TW * 32) k_ilu_bwd_tile(int nx, int ny, int nz, const int32_t* __restrict__ rowptr,
                                                           const TM* __restrict__ A, const TM* __restrict__ Dinv,
                                                           const TM* __restrict__ yin, TM* __restrict__ zs,
@@ -429,6 +452,8 @@ __global__ void __launch_bounds__(TW * 32) k_ilu_bwd_tile(int nx, int ny, int nz
           const Ops<TM> o = ring[q];
           if (step + PF < nx)
             ring[q] = load_bwd<TM>(x - PF, nx, base_jk, nlow_jk, hy, hz, rowptr, A, Dinv, yin, lane, r);
+          if (PD > 0 && step + PD < nx)
+            prefetch_cell<TM>(base_jk + x - PD, nlow_jk + (x - PD > 0) + 1, (int)hz + (int)hy + 1, rowptr, A, Dinv, lane);
           const int i = base_jk + x;
           TM acc = fma(o.a2.x, zp0, o.a2.y * zp1);
           if (hz) {
@@ -647,20 +672,20 @@ void sweep_pair(Handle& h, const TM* A, const TM* Dinv, const double* r, TM* y, 
     const int blocks = ntiles < 152 ? ntiles : 152;
     const size_t smem = sizeof(TM) * (size_t)TW * h.nx * 8;
     if (smem > 48 * 1024) {
-      cudaFuncSetAttribute(k_ilu_fwd_tile<TM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      cudaFuncSetAttribute(k_ilu_bwd_tile<TM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(k_ilu_fwd_tile<TM, SWEEP_PD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(k_ilu_bwd_tile<TM, SWEEP_PD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     }
-    k_ilu_fwd_tile<TM><<<blocks, TW * 32, smem, s>>>(h.nx, h.ny, h.nz, h.rowptr, A, Dinv, r, y, h.pipe, h.dstatus);
+    k_ilu_fwd_tile<TM, SWEEP_PD><<<blocks, TW * 32, smem, s>>>(h.nx, h.ny, h.nz, h.rowptr, A, Dinv, r, y, h.pipe, h.dstatus);
     cudaMemsetAsync(h.pipe, 0, 2 * sizeof(int), s);
     cudaMemsetAsync(zs, 0xff, sizeof(TM) * n8, s);
-    k_ilu_bwd_tile<TM><<<blocks, TW * 32, smem, s>>>(h.nx, h.ny, h.nz, h.rowptr, A, Dinv, y, zs, z64, h.pipe,
+    k_ilu_bwd_tile<TM, SWEEP_PD><<<blocks, TW * 32, smem, s>>>(h.nx, h.ny, h.nz, h.rowptr, A, Dinv, y, zs, z64, h.pipe,
                                                      h.dstatus);
     return;
   }
-  k_ilu_fwd_pipe<TM><<<pipe_blocks(npen), 256, 0, s>>>(h.nx, h.ny, h.nz, h.rowptr, A, Dinv, r, y, h.pipe, h.dstatus);
+  k_ilu_fwd_pipe<TM, SWEEP_PD><<<pipe_blocks(npen), 256, 0, s>>>(h.nx, h.ny, h.nz, h.rowptr, A, Dinv, r, y, h.pipe, h.dstatus);
   cudaMemsetAsync(h.pipe, 0, 2 * sizeof(int), s);
   cudaMemsetAsync(zs, 0xff, sizeof(TM) * n8, s);
-  k_ilu_bwd_pipe<TM><<<pipe_blocks(npen), 256, 0, s>>>(h.nx, h.ny, h.nz, h.rowptr, A, Dinv, y, zs, z64, h.pipe,
+  k_ilu_bwd_pipe<TM, SWEEP_PD><<<pipe_blocks(npen), 256, 0, s>>>(h.nx, h.ny, h.nz, h.rowptr, A, Dinv, y, zs, z64, h.pipe,
                                                         h.dstatus);
 }
 
@@ -730,10 +755,10 @@ extern "C" int isc_bilu0_apply_noalloc(int32_t nx, int32_t ny, int32_t nz, const
   // keeps the previous call's contents
   if (cudaMemsetAsync(ints, 0, NOALLOC_INTS * sizeof(int), s) != cudaSuccess) return ISC_ERR_CUDA;
   cudaMemsetAsync(y, 0xff, vbytes, s);
-  k_ilu_fwd_pipe<double><<<pipe_blocks(npen), 256, 0, s>>>(nx, ny, nz, d_rowptr, d_A, d_Dinv, d_r, y, pipe, status);
+  k_ilu_fwd_pipe<double, 0><<<pipe_blocks(npen), 256, 0, s>>>(nx, ny, nz, d_rowptr, d_A, d_Dinv, d_r, y, pipe, status);
   cudaMemsetAsync(pipe, 0, 2 * sizeof(int), s);
   cudaMemsetAsync(d_z, 0xff, vbytes, s);
-  k_ilu_bwd_pipe<double><<<pipe_blocks(npen), 256, 0, s>>>(nx, ny, nz, d_rowptr, d_A, d_Dinv, y, d_z, nullptr, pipe,
+  k_ilu_bwd_pipe<double, 0><<<pipe_blocks(npen), 256, 0, s>>>(nx, ny, nz, d_rowptr, d_A, d_Dinv, y, d_z, nullptr, pipe,
                                                             status);
   int h_status = 0;
   if (cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return ISC_ERR_CUDA;
