@@ -10,10 +10,17 @@
 // dependency order (so a warp only ever waits on pencils already held by
 // running warps). The cross-pencil hand-off is the data itself: the output
 // vector is NaN-filled before a sweep and a consumer polls the neighbour's
-// 64-byte block vector until it holds numbers. Matrix operands are
-// prefetched PF cells ahead into a register ring. Every wait is bounded: on
-// timeout the kernel raises DS_TIMEOUT and a global abort flag that makes
-// every other waiter return.
+// 64-byte block vector until it holds numbers; these values are requested LA
+// cells before use. The matrix operands of upcoming cells are streamed into a
+// per-warp shared-memory ring with cp.async. Row starts are computed, not
+// loaded. Every wait is bounded: on timeout the kernel raises DS_TIMEOUT and a
+// global abort flag that makes every other waiter return.
+//
+// Measured on the 60x60x20 field step, a lone pencil costs ~0.3 us (FP32) to
+// ~0.6 us (FP64) per cell of sequential recurrence, and each pencil-to-pencil
+// hand-off adds about one cell time plus ~0.5 us; the sweep time is that
+// per-cell chain times the nx + ny + nz - 2 cells of the wavefront, not memory
+// bandwidth.
 //
 // Lane layout per 8x8 block (row-major, 64 doubles): lane l holds the double2
 // at offset 2l, i.e. row r = l/4, columns c = 2(l%4), c+1; a row sum is a
@@ -41,6 +48,39 @@ __device__ __forceinline__ void st_relaxed(double* p, double v) {
 }
 
 __device__ __forceinline__ double2 ld_nc2(const double* p) { return __ldg(reinterpret_cast<const double2*>(p)); }
+
+// Start of the BSR row of cell i for the 7-point pattern with sorted columns,
+// computed instead of loaded: 7 i minus the neighbours missing at the
+// boundaries among the cells before i (a dependent rowptr load per cell would
+// put a memory round trip into every step of the sweep recurrences).
+__device__ __forceinline__ int rowptr_of(int nx, int ny, int nz, int i) {
+  const int nxy = nx * ny;
+  const int x = i % nx, rr = i / nx;
+  const int y = rr % ny, z = rr / ny;
+  const int miss = rr + (x > 0)                       // -x
+                   + rr                               // +x
+                   + z * nx + (y > 0 ? nx : x)        // -y
+                   + z * nx + (y == ny - 1 ? x : 0)   // +y
+                   + (z > 0 ? nxy : i)                // -z
+                   + (z == nz - 1 ? i - z * nxy : 0); // +z
+  return 7 * i - miss;
+}
+
+// Row starts along one x-pencil: base(x) = base(0) + x L + max(2x - 1, 0) with
+// L the pencil's neighbour count outside x (no division per cell).
+struct Pen {
+  int base_jk, base0, L;
+};
+
+__device__ __forceinline__ Pen make_pen(int nx, int ny, int nz, int j, int k, int base_jk) {
+  Pen P;
+  P.base_jk = base_jk;
+  P.base0 = rowptr_of(nx, ny, nz, base_jk);
+  P.L = 1 + (k > 0) + (j > 0) + (j < ny - 1) + (k < nz - 1);
+  return P;
+}
+
+__device__ __forceinline__ int row_start(const Pen& P, int x) { return P.base0 + x * P.L + (x > 0 ? 2 * x - 1 : 0); }
 
 // Vector element types of the sweeps: FP64 (all-FP64 solve) or FP32 (factors,
 // off-diagonal blocks and the hand-off vector of the mixed-precision solve).
@@ -89,22 +129,6 @@ __device__ __forceinline__ bool poll_vec(const T* v, int c, typename V2<T>::t& o
 }
 
 template <typename T>
-__device__ __forceinline__ T quad_sum(T v) {
-  v += __shfl_xor_sync(FULL, v, 1);
-  v += __shfl_xor_sync(FULL, v, 2);
-  return v;
-}
-
-// operands of one cell that do not depend on the sweep
-template <typename T>
-struct Ops {
-  typename V2<T>::t a0, a1, a2, d;  // up to three off-diagonal blocks (lane's pair) and D^-1
-  T ri;
-};
-
-constexpr int PF = 4;  // prefetch distance in cells (register ring)
-
-template <typename T>
 __device__ __forceinline__ typename V2<T>::t zero2() {
   typename V2<T>::t z;
   z.x = T(0);
@@ -112,60 +136,93 @@ __device__ __forceinline__ typename V2<T>::t zero2() {
   return z;
 }
 
-template <typename TM, typename TR>
-__device__ __forceinline__ Ops<TM> load_fwd(int x, int base_jk, bool hy, bool hz, const int32_t* __restrict__ rowptr,
-                                            const TM* __restrict__ A, const TM* __restrict__ Dinv,
-                                            const TR* __restrict__ rhs, int lane, int r) {
-  Ops<TM> o;
-  const int i = base_jk + x;
-  const int base = __ldg(rowptr + i);
-  int s = 0;
-  o.a0 = hz ? ld_nc2(A + (size_t)(base + s++) * BB + 2 * lane) : zero2<TM>();    // -z
-  o.a1 = hy ? ld_nc2(A + (size_t)(base + s++) * BB + 2 * lane) : zero2<TM>();    // -y
-  o.a2 = (x > 0) ? ld_nc2(A + (size_t)(base + s) * BB + 2 * lane) : zero2<TM>();  // -x
-  o.d = ld_nc2(Dinv + (size_t)i * BB + 2 * lane);
-  o.ri = (TM)__ldg(rhs + (size_t)i * 8 + r);
-  return o;
+template <typename T>
+__device__ __forceinline__ T quad_sum(T v) {
+  v += __shfl_xor_sync(FULL, v, 1);
+  v += __shfl_xor_sync(FULL, v, 2);
+  return v;
+}
+
+// Remote look-ahead: the neighbour-pencil values a cell needs are requested LA
+// cells before they are used (the neighbour pencil normally runs ahead), so a
+// cell normally costs no round trip; entries still NaN on use are re-polled.
+constexpr int LA = 4;
+
+template <typename TM>
+__device__ __forceinline__ typename V2<TM>::t ld_remote(const TM* p) {
+  typename V2<TM>::t v;
+  ld_relaxed_v2(p, v.x, v.y);
+  return v;
 }
 
 template <typename TM>
-__device__ __forceinline__ Ops<TM> load_bwd(int x, int nx, int base_jk, int nlow_jk, bool hy, bool hz,
-                                            const int32_t* __restrict__ rowptr, const TM* __restrict__ A,
-                                            const TM* __restrict__ Dinv, const TM* __restrict__ yin, int lane, int r) {
-  Ops<TM> o;
-  const int i = base_jk + x;
-  const int base = __ldg(rowptr + i);
-  int s = nlow_jk + (x > 0) + 1;  // first slot after the diagonal
-  o.a2 = (x < nx - 1) ? ld_nc2(A + (size_t)(base + s++) * BB + 2 * lane) : zero2<TM>();  // +x
-  o.a1 = hy ? ld_nc2(A + (size_t)(base + s++) * BB + 2 * lane) : zero2<TM>();            // +y
-  o.a0 = hz ? ld_nc2(A + (size_t)(base + s) * BB + 2 * lane) : zero2<TM>();              // +z
-  o.d = ld_nc2(Dinv + (size_t)i * BB + 2 * lane);
-  o.ri = __ldg(yin + (size_t)i * 8 + r);
-  return o;
+__device__ __forceinline__ bool ready2(const typename V2<TM>::t& v) {
+  return !isnan(v.x) && !isnan(v.y);
 }
 
-__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
-
-// Pull the operands of a cell that is PD cells ahead into L2 (one request per
-// 128-byte line): the lower (forward) or upper (backward) blocks of its row and
-// its D^-1 block.
+// re-poll until the lane pair is a number everywhere in the warp
 template <typename TM>
-__device__ __forceinline__ void prefetch_cell(int i, int first_slot, int nblk, const int32_t* __restrict__ rowptr,
-                                              const TM* __restrict__ A, const TM* __restrict__ Dinv, int lane) {
-  constexpr int LANES_PER_LINE = 128 / (2 * sizeof(TM));
-  if (lane % LANES_PER_LINE != 0) return;
-  const int base = __ldg(rowptr + i);
-  for (int b = 0; b < nblk; ++b) prefetch_l2(A + (size_t)(base + first_slot + b) * BB + 2 * lane);
-  prefetch_l2(Dinv + (size_t)i * BB + 2 * lane);
+__device__ __forceinline__ bool settle(const TM* p, typename V2<TM>::t& v, int* abortf, int* dstatus) {
+  if (__all_sync(FULL, ready2<TM>(v))) return true;
+  return poll_vec<TM>(p, 0, v, abortf, dstatus);
 }
 
-// forward sweep: TM = matrix/vector precision, rhs always FP64
-template <typename TM, int PD>
-__global__ void __launch_bounds__(256) k_ilu_fwd_pipe(int nx, int ny, int nz, const int32_t* __restrict__ rowptr,
-                                                      const TM* __restrict__ A, const TM* __restrict__ Dinv,
-                                                      const double* __restrict__ rhs, TM* __restrict__ y,
-                                                      int* __restrict__ pipe, int* __restrict__ dstatus) {
+// ------------------------------------------------- shared-memory operand pipeline
+// The operands of a cell (its up-to-three off-diagonal blocks of the sweep
+// direction, D^-1 and the right-hand side) do not depend on the sweep. Each
+// warp streams them into its own ring of R cell slots in shared memory with
+// cp.async, R-1 cells ahead of use, so the per-cell chain no longer waits on
+// DRAM. Every iteration commits exactly one group (possibly empty) and waits
+// until the group of the current cell has landed (a hardware wait).
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem_dst, const void* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(gsrc), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <typename TM>
+struct Slot {
+  TM blk[4][64];   // up to 3 off-diagonal blocks and D^-1 (index 3)
+  double rhs[8];
+};
+
+// issue the copies of one cell into a slot: blocks at row slots first_slot.. (mask says which exist)
+template <typename TM>
+__device__ __forceinline__ void stage_cell(Slot<TM>* sl, int i, int first_slot, int mask, const Pen& P,
+                                           const TM* __restrict__ A, const TM* __restrict__ Dinv,
+                                           const double* __restrict__ rhs, int lane) {
+  const int base = row_start(P, i - P.base_jk);
+  int s = first_slot, dst = 0;  // present blocks are packed into blk[0..] in row order
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    if (mask & (1 << b)) {
+      cp_async<2 * sizeof(TM)>(&sl->blk[dst][2 * lane], A + (size_t)(base + s) * BB + 2 * lane);
+      ++s;
+      ++dst;
+    }
+  }
+  cp_async<2 * sizeof(TM)>(&sl->blk[3][2 * lane], Dinv + (size_t)i * BB + 2 * lane);
+  if (rhs && lane < 8) cp_async<8>(&sl->rhs[lane], rhs + (size_t)i * 8 + lane);
+}
+
+template <typename TM>
+__device__ __forceinline__ typename V2<TM>::t sl_pair(const Slot<TM>* sl, int b, int lane) {
+  return *reinterpret_cast<const typename V2<TM>::t*>(&sl->blk[b][2 * lane]);
+}
+
+constexpr int AWARPS = 8;
+
+template <typename TM, int R>
+__global__ void __launch_bounds__(AWARPS * 32) k_ilu_fwd_async(int nx, int ny, int nz, const int32_t* __restrict__ rowptr,
+                                                               const TM* __restrict__ A, const TM* __restrict__ Dinv,
+                                                               const double* __restrict__ rhs, TM* __restrict__ y,
+                                                               int* __restrict__ pipe, int* __restrict__ dstatus) {
   using T2 = typename V2<TM>::t;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Slot<TM>* ring = reinterpret_cast<Slot<TM>*>(smem_raw) + (threadIdx.x >> 5) * R;
   const int lane = threadIdx.x & 31;
   const int r = lane >> 2, c = (lane & 3) * 2;
   const int npen = ny * nz, nxy = nx * ny;
@@ -179,50 +236,79 @@ __global__ void __launch_bounds__(256) k_ilu_fwd_pipe(int nx, int ny, int nz, co
     const int j = p % ny, k = p / ny;
     const bool hy = j > 0, hz = k > 0;
     const int base_jk = nx * (j + ny * k);
-    Ops<TM> ring[PF];
+    const Pen PEN = make_pen(nx, ny, nz, j, k, base_jk);
+    // blocks of row (j,k,x) in order -z, -y, -x
+    auto mask_of = [&](int x) { return (hz ? 1 : 0) | (hy ? 2 : 0) | (x > 0 ? 4 : 0); };
+#pragma unroll 1
+    for (int q = 0; q < R - 1; ++q) {
+      if (q < nx) stage_cell<TM>(ring + q, base_jk + q, 0, mask_of(q), PEN, A, Dinv, rhs, lane);
+      cp_async_commit();
+    }
+    T2 rz[LA], ry[LA];
 #pragma unroll
-    for (int q = 0; q < PF; ++q)
-      if (q < nx) ring[q] = load_fwd<TM, double>(q, base_jk, hy, hz, rowptr, A, Dinv, rhs, lane, r);
+    for (int q = 0; q < LA; ++q) {
+      if (q < nx) {
+        if (hz) rz[q] = ld_remote<TM>(y + (size_t)(base_jk + q - nxy) * 8 + c);
+        if (hy) ry[q] = ld_remote<TM>(y + (size_t)(base_jk + q - nx) * 8 + c);
+      }
+    }
     TM yp0 = TM(0), yp1 = TM(0);
-    for (int x0 = 0; x0 < nx; x0 += PF) {
+    for (int x0 = 0; x0 < nx; x0 += LA) {
 #pragma unroll
-      for (int q = 0; q < PF; ++q) {
+      for (int q = 0; q < LA; ++q) {
         const int x = x0 + q;
         if (x >= nx) break;
-        const Ops<TM> o = ring[q];
-        if (x + PF < nx) ring[q] = load_fwd<TM, double>(x + PF, base_jk, hy, hz, rowptr, A, Dinv, rhs, lane, r);
-        if (PD > 0 && x + PD < nx) prefetch_cell<TM>(base_jk + x + PD, 0, (int)hz + (int)hy + 1, rowptr, A, Dinv, lane);
         const int i = base_jk + x;
-        TM acc = fma(o.a2.x, yp0, o.a2.y * yp1);
+        const int xs = x + R - 1;
+        if (xs < nx) stage_cell<TM>(ring + xs % R, base_jk + xs, 0, mask_of(xs), PEN, A, Dinv, rhs, lane);
+        cp_async_commit();
+        cp_async_wait<R - 1>();
+        __syncwarp();
+        const Slot<TM>* sl = ring + x % R;
+        const int m = mask_of(x);
+        int b = 0;
+        T2 az = zero2<TM>(), ay = zero2<TM>(), ax = zero2<TM>();
+        if (m & 1) az = sl_pair<TM>(sl, b++, lane);
+        if (m & 2) ay = sl_pair<TM>(sl, b++, lane);
+        if (m & 4) ax = sl_pair<TM>(sl, b, lane);
+        const T2 d = sl_pair<TM>(sl, 3, lane);
+        const TM ri = (TM)sl->rhs[r];
+        TM acc = fma(ax.x, yp0, ax.y * yp1);
         if (hz) {
-          T2 v;
-          if (!poll_vec<TM>(y + (size_t)(i - nxy) * 8, c, v, abortf, dstatus)) return;
-          acc = fma(o.a0.x, v.x, fma(o.a0.y, v.y, acc));
+          if (!settle<TM>(y + (size_t)(i - nxy) * 8 + c, rz[q], abortf, dstatus)) return;
+          acc = fma(az.x, rz[q].x, fma(az.y, rz[q].y, acc));
         }
         if (hy) {
-          T2 v;
-          if (!poll_vec<TM>(y + (size_t)(i - nx) * 8, c, v, abortf, dstatus)) return;
-          acc = fma(o.a1.x, v.x, fma(o.a1.y, v.y, acc));
+          if (!settle<TM>(y + (size_t)(i - nx) * 8 + c, ry[q], abortf, dstatus)) return;
+          acc = fma(ay.x, ry[q].x, fma(ay.y, ry[q].y, acc));
         }
-        const TM t = o.ri - quad_sum(acc);
+        const TM t = ri - quad_sum(acc);
         const TM t0 = __shfl_sync(FULL, t, 4 * c), t1 = __shfl_sync(FULL, t, 4 * c + 4);
-        const TM yr = quad_sum(fma(o.d.x, t0, o.d.y * t1));
+        const TM yr = quad_sum(fma(d.x, t0, d.y * t1));
         if ((lane & 3) == 0) st_relaxed(y + (size_t)i * 8 + r, yr);
         yp0 = __shfl_sync(FULL, yr, 4 * c);
         yp1 = __shfl_sync(FULL, yr, 4 * c + 4);
+        if (x + LA < nx) {
+          if (hz) rz[q] = ld_remote<TM>(y + (size_t)(i + LA - nxy) * 8 + c);
+          if (hy) ry[q] = ld_remote<TM>(y + (size_t)(i + LA - nx) * 8 + c);
+        }
+        __syncwarp();  // every lane is done with this slot before it is refilled
       }
     }
+    cp_async_wait<0>();
+    __syncwarp();
   }
 }
 
-// backward sweep: hand-off through zs (precision TM); z64, if given, receives the FP64 result
-template <typename TM, int PD>
-__global__ void __launch_bounds__(256) k_ilu_bwd_pipe(int nx, int ny, int nz, const int32_t* __restrict__ rowptr,
-                                                      const TM* __restrict__ A, const TM* __restrict__ Dinv,
-                                                      const TM* __restrict__ yin, TM* __restrict__ zs,
-                                                      double* __restrict__ z64, int* __restrict__ pipe,
-                                                      int* __restrict__ dstatus) {
+template <typename TM, int R>
+__global__ void __launch_bounds__(AWARPS * 32) k_ilu_bwd_async(int nx, int ny, int nz, const int32_t* __restrict__ rowptr,
+                                                               const TM* __restrict__ A, const TM* __restrict__ Dinv,
+                                                               const TM* __restrict__ yin, TM* __restrict__ zs,
+                                                               double* __restrict__ z64, int* __restrict__ pipe,
+                                                               int* __restrict__ dstatus) {
   using T2 = typename V2<TM>::t;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Slot<TM>* ring = reinterpret_cast<Slot<TM>*>(smem_raw) + (threadIdx.x >> 5) * R;
   const int lane = threadIdx.x & 31;
   const int r = lane >> 2, c = (lane & 3) * 2;
   const int npen = ny * nz, nxy = nx * ny;
@@ -238,253 +324,78 @@ __global__ void __launch_bounds__(256) k_ilu_bwd_pipe(int nx, int ny, int nz, co
     const bool hy = j < ny - 1, hz = k < nz - 1;
     const int nlow_jk = (k > 0) + (j > 0);
     const int base_jk = nx * (j + ny * k);
-    Ops<TM> ring[PF];
+    const Pen PEN = make_pen(nx, ny, nz, j, k, base_jk);
+    // blocks of row (j,k,x) after the diagonal in order +x, +y, +z; slot index of b is its bit
+    auto mask_of = [&](int x) { return (x < nx - 1 ? 1 : 0) | (hy ? 2 : 0) | (hz ? 4 : 0); };
+    auto first_of = [&](int x) { return nlow_jk + (x > 0) + 1; };
+#pragma unroll 1
+    for (int q = 0; q < R - 1; ++q) {
+      if (q < nx) {
+        const int x = nx - 1 - q;
+        stage_cell<TM>(ring + q, base_jk + x, first_of(x), mask_of(x), PEN, A, Dinv, nullptr, lane);
+      }
+      cp_async_commit();
+    }
+    T2 rz[LA], ry[LA];
 #pragma unroll
-    for (int q = 0; q < PF; ++q)
-      if (q < nx) ring[q] = load_bwd<TM>(nx - 1 - q, nx, base_jk, nlow_jk, hy, hz, rowptr, A, Dinv, yin, lane, r);
+    for (int q = 0; q < LA; ++q) {
+      if (q < nx) {
+        const int x = nx - 1 - q;
+        if (hz) rz[q] = ld_remote<TM>(zs + (size_t)(base_jk + x + nxy) * 8 + c);
+        if (hy) ry[q] = ld_remote<TM>(zs + (size_t)(base_jk + x + nx) * 8 + c);
+      }
+    }
     TM zp0 = TM(0), zp1 = TM(0);
-    for (int x0 = 0; x0 < nx; x0 += PF) {
+    for (int s0 = 0; s0 < nx; s0 += LA) {
 #pragma unroll
-      for (int q = 0; q < PF; ++q) {
-        const int step = x0 + q;
+      for (int q = 0; q < LA; ++q) {
+        const int step = s0 + q;
         if (step >= nx) break;
         const int x = nx - 1 - step;
-        const Ops<TM> o = ring[q];
-        if (step + PF < nx)
-          ring[q] = load_bwd<TM>(x - PF, nx, base_jk, nlow_jk, hy, hz, rowptr, A, Dinv, yin, lane, r);
-        if (PD > 0 && step + PD < nx)
-          prefetch_cell<TM>(base_jk + x - PD, nlow_jk + (x - PD > 0) + 1, (int)hz + (int)hy + 1, rowptr, A, Dinv, lane);
         const int i = base_jk + x;
-        TM acc = fma(o.a2.x, zp0, o.a2.y * zp1);
+        const int ss = step + R - 1;
+        if (ss < nx)
+          stage_cell<TM>(ring + ss % R, base_jk + (nx - 1 - ss), first_of(nx - 1 - ss), mask_of(nx - 1 - ss), PEN, A,
+                         Dinv, nullptr, lane);
+        cp_async_commit();
+        cp_async_wait<R - 1>();
+        __syncwarp();
+        const Slot<TM>* sl = ring + step % R;
+        const int m = mask_of(x);
+        int b = 0;
+        T2 ax = zero2<TM>(), ay = zero2<TM>(), az = zero2<TM>();
+        if (m & 1) ax = sl_pair<TM>(sl, b++, lane);
+        if (m & 2) ay = sl_pair<TM>(sl, b++, lane);
+        if (m & 4) az = sl_pair<TM>(sl, b, lane);
+        const T2 d = sl_pair<TM>(sl, 3, lane);
+        const TM yi = __ldg(yin + (size_t)i * 8 + r);
+        TM acc = fma(ax.x, zp0, ax.y * zp1);
         if (hz) {
-          T2 v;
-          if (!poll_vec<TM>(zs + (size_t)(i + nxy) * 8, c, v, abortf, dstatus)) return;
-          acc = fma(o.a0.x, v.x, fma(o.a0.y, v.y, acc));
+          if (!settle<TM>(zs + (size_t)(i + nxy) * 8 + c, rz[q], abortf, dstatus)) return;
+          acc = fma(az.x, rz[q].x, fma(az.y, rz[q].y, acc));
         }
         if (hy) {
-          T2 v;
-          if (!poll_vec<TM>(zs + (size_t)(i + nx) * 8, c, v, abortf, dstatus)) return;
-          acc = fma(o.a1.x, v.x, fma(o.a1.y, v.y, acc));
+          if (!settle<TM>(zs + (size_t)(i + nx) * 8 + c, ry[q], abortf, dstatus)) return;
+          acc = fma(ay.x, ry[q].x, fma(ay.y, ry[q].y, acc));
         }
         const TM sr = quad_sum(acc);
-        const TM s0 = __shfl_sync(FULL, sr, 4 * c), s1 = __shfl_sync(FULL, sr, 4 * c + 4);
-        const TM zr = o.ri - quad_sum(fma(o.d.x, s0, o.d.y * s1));
+        const TM s_0 = __shfl_sync(FULL, sr, 4 * c), s_1 = __shfl_sync(FULL, sr, 4 * c + 4);
+        const TM zr = yi - quad_sum(fma(d.x, s_0, d.y * s_1));
         if ((lane & 3) == 0) {
           st_relaxed(zs + (size_t)i * 8 + r, zr);
           if (z64) z64[(size_t)i * 8 + r] = (double)zr;
         }
         zp0 = __shfl_sync(FULL, zr, 4 * c);
         zp1 = __shfl_sync(FULL, zr, 4 * c + 4);
-      }
-    }
-  }
-}
-
-// ------------------------------------------------------------------ tiled sweeps
-// A CTA of TW warps owns TW consecutive pencils (j0..j0+TW-1) of one k-plane.
-// Each warp keeps its whole pencil result in shared memory (NaN-filled), so
-// the j-neighbour hand-off inside the CTA is a shared-memory poll; only the
-// first (forward) / last (backward) warp of a tile and every k-neighbour go
-// through global memory. Tiles are taken from a counter in dependency order.
-// A warp that meets an abort stops its pencil but still reaches the CTA
-// barriers; the CTA then leaves together.
-constexpr int TW = 8;
-#ifndef SWEEP_PD
-#define SWEEP_PD 16  // L2 prefetch distance of the sweeps, in cells
-#endif
-constexpr int TILE_MAX_NX = 256;
-
-__device__ __forceinline__ double ld_shared_volatile(const double* p) { return *(const volatile double*)p; }
-__device__ __forceinline__ float ld_shared_volatile(const float* p) { return *(const volatile float*)p; }
-
-template <typename T>
-__device__ __forceinline__ bool poll_smem(const T* v, int c, typename V2<T>::t& out, int* abortf, int* dstatus) {
-  for (int spins = 0;; ++spins) {
-    const T a = ld_shared_volatile(v + c), b = ld_shared_volatile(v + c + 1);
-    const bool ok = !isnan(a) && !isnan(b);
-    if (__all_sync(FULL, ok)) {
-      out.x = a;
-      out.y = b;
-      return true;
-    }
-    if ((spins & 255) == 255 && __any_sync(FULL, ld_relaxed(abortf) != 0)) return false;
-    if (spins > SPIN_LIMIT) {
-      if ((threadIdx.x & 31) == 0) {
-        atomicOr(dstatus, DS_TIMEOUT);
-        atomicExch(abortf, 1);
-      }
-      return false;
-    }
-  }
-}
-
-template <typename T>
-__device__ __forceinline__ void st_shared_volatile(T* p, T v) {
-  *(volatile T*)p = v;
-}
-
-template <typename TM, int PD>
-__global__ void __launch_bounds__(TW * 32) k_ilu_fwd_tile(int nx, int ny, int nz, const int32_t* __restrict__ rowptr,
-                                                          const TM* __restrict__ A, const TM* __restrict__ Dinv,
-                                                          const double* __restrict__ rhs, TM* __restrict__ y,
-                                                          int* __restrict__ pipe, int* __restrict__ dstatus) {
-  using T2 = typename V2<TM>::t;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  TM* sy = reinterpret_cast<TM*>(smem_raw);
-  __shared__ int s_tile, s_abort;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int r = lane >> 2, c = (lane & 3) * 2;
-  const int nxy = nx * ny, ntj = (ny + TW - 1) / TW, ntiles = ntj * nz;
-  int* counter = pipe;
-  int* abortf = pipe + 1;
-  TM* mine = sy + (size_t)w * nx * 8;
-  const TM* prev = (w > 0) ? sy + (size_t)(w - 1) * nx * 8 : nullptr;
-  const TM nanv = TM(NAN);
-  for (;;) {
-    if (threadIdx.x == 0) {
-      s_tile = atomicAdd(counter, 1);
-      s_abort = 0;
-    }
-    for (int e = lane; e < nx * 8; e += 32) mine[e] = nanv;
-    __syncthreads();
-    const int t = s_tile;
-    if (t >= ntiles) return;
-    const int jt = t % ntj, k = t / ntj;
-    const int j = jt * TW + w;
-    bool ok = true;
-    if (j < ny) {
-      const bool hy = j > 0, hz = k > 0;
-      const int base_jk = nx * (j + ny * k);
-      Ops<TM> ring[PF];
-#pragma unroll
-      for (int q = 0; q < PF; ++q)
-        if (q < nx) ring[q] = load_fwd<TM, double>(q, base_jk, hy, hz, rowptr, A, Dinv, rhs, lane, r);
-      TM yp0 = TM(0), yp1 = TM(0);
-      for (int x0 = 0; x0 < nx && ok; x0 += PF) {
-#pragma unroll
-        for (int q = 0; q < PF; ++q) {
-          const int x = x0 + q;
-          if (x >= nx || !ok) break;
-          const Ops<TM> o = ring[q];
-          if (x + PF < nx) ring[q] = load_fwd<TM, double>(x + PF, base_jk, hy, hz, rowptr, A, Dinv, rhs, lane, r);
-          if (PD > 0 && x + PD < nx)
-            prefetch_cell<TM>(base_jk + x + PD, 0, (int)hz + (int)hy + 1, rowptr, A, Dinv, lane);
-          const int i = base_jk + x;
-          TM acc = fma(o.a2.x, yp0, o.a2.y * yp1);
-          if (hz) {
-            T2 v;
-            ok = poll_vec<TM>(y + (size_t)(i - nxy) * 8, c, v, abortf, dstatus);
-            if (!ok) break;
-            acc = fma(o.a0.x, v.x, fma(o.a0.y, v.y, acc));
-          }
-          if (hy) {
-            T2 v;
-            ok = (w > 0) ? poll_smem<TM>(prev + x * 8, c, v, abortf, dstatus)
-                         : poll_vec<TM>(y + (size_t)(i - nx) * 8, c, v, abortf, dstatus);
-            if (!ok) break;
-            acc = fma(o.a1.x, v.x, fma(o.a1.y, v.y, acc));
-          }
-          const TM tt = o.ri - quad_sum(acc);
-          const TM t0 = __shfl_sync(FULL, tt, 4 * c), t1 = __shfl_sync(FULL, tt, 4 * c + 4);
-          const TM yr = quad_sum(fma(o.d.x, t0, o.d.y * t1));
-          if ((lane & 3) == 0) {
-            st_relaxed(y + (size_t)i * 8 + r, yr);
-            st_shared_volatile(mine + x * 8 + r, yr);
-          }
-          yp0 = __shfl_sync(FULL, yr, 4 * c);
-          yp1 = __shfl_sync(FULL, yr, 4 * c + 4);
+        if (step + LA < nx) {
+          if (hz) rz[q] = ld_remote<TM>(zs + (size_t)(i - LA + nxy) * 8 + c);
+          if (hy) ry[q] = ld_remote<TM>(zs + (size_t)(i - LA + nx) * 8 + c);
         }
+        __syncwarp();
       }
     }
-    if (!ok && lane == 0) s_abort = 1;
-    __syncthreads();
-    if (s_abort) return;
-  }
-}
-
-template <typename TM, int PD>
-__global__ void __launch_bounds__(TW * 32) k_ilu_bwd_tile(int nx, int ny, int nz, const int32_t* __restrict__ rowptr,
-                                                          const TM* __restrict__ A, const TM* __restrict__ Dinv,
-                                                          const TM* __restrict__ yin, TM* __restrict__ zs,
-                                                          double* __restrict__ z64, int* __restrict__ pipe,
-                                                          int* __restrict__ dstatus) {
-  using T2 = typename V2<TM>::t;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  TM* sz = reinterpret_cast<TM*>(smem_raw);
-  __shared__ int s_tile, s_abort;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int r = lane >> 2, c = (lane & 3) * 2;
-  const int nxy = nx * ny, ntj = (ny + TW - 1) / TW, ntiles = ntj * nz;
-  int* counter = pipe;
-  int* abortf = pipe + 1;
-  TM* mine = sz + (size_t)w * nx * 8;
-  const TM* next = (w < TW - 1) ? sz + (size_t)(w + 1) * nx * 8 : nullptr;
-  const TM nanv = TM(NAN);
-  for (;;) {
-    if (threadIdx.x == 0) {
-      s_tile = atomicAdd(counter, 1);
-      s_abort = 0;
-    }
-    for (int e = lane; e < nx * 8; e += 32) mine[e] = nanv;
-    __syncthreads();
-    const int g = s_tile;
-    if (g >= ntiles) return;
-    const int t = ntiles - 1 - g;
-    const int jt = t % ntj, k = t / ntj;
-    const int j = jt * TW + w;
-    bool ok = true;
-    if (j < ny) {
-      const bool hy = j < ny - 1, hz = k < nz - 1;
-      const bool hy_local = hy && (w < TW - 1);
-      const int nlow_jk = (k > 0) + (j > 0);
-      const int base_jk = nx * (j + ny * k);
-      Ops<TM> ring[PF];
-#pragma unroll
-      for (int q = 0; q < PF; ++q)
-        if (q < nx) ring[q] = load_bwd<TM>(nx - 1 - q, nx, base_jk, nlow_jk, hy, hz, rowptr, A, Dinv, yin, lane, r);
-      TM zp0 = TM(0), zp1 = TM(0);
-      for (int x0 = 0; x0 < nx && ok; x0 += PF) {
-#pragma unroll
-        for (int q = 0; q < PF; ++q) {
-          const int step = x0 + q;
-          if (step >= nx || !ok) break;
-          const int x = nx - 1 - step;
-          const Ops<TM> o = ring[q];
-          if (step + PF < nx)
-            ring[q] = load_bwd<TM>(x - PF, nx, base_jk, nlow_jk, hy, hz, rowptr, A, Dinv, yin, lane, r);
-          if (PD > 0 && step + PD < nx)
-            prefetch_cell<TM>(base_jk + x - PD, nlow_jk + (x - PD > 0) + 1, (int)hz + (int)hy + 1, rowptr, A, Dinv, lane);
-          const int i = base_jk + x;
-          TM acc = fma(o.a2.x, zp0, o.a2.y * zp1);
-          if (hz) {
-            T2 v;
-            ok = poll_vec<TM>(zs + (size_t)(i + nxy) * 8, c, v, abortf, dstatus);
-            if (!ok) break;
-            acc = fma(o.a0.x, v.x, fma(o.a0.y, v.y, acc));
-          }
-          if (hy) {
-            T2 v;
-            ok = hy_local ? poll_smem<TM>(next + x * 8, c, v, abortf, dstatus)
-                          : poll_vec<TM>(zs + (size_t)(i + nx) * 8, c, v, abortf, dstatus);
-            if (!ok) break;
-            acc = fma(o.a1.x, v.x, fma(o.a1.y, v.y, acc));
-          }
-          const TM sr = quad_sum(acc);
-          const TM s0 = __shfl_sync(FULL, sr, 4 * c), s1 = __shfl_sync(FULL, sr, 4 * c + 4);
-          const TM zr = o.ri - quad_sum(fma(o.d.x, s0, o.d.y * s1));
-          if ((lane & 3) == 0) {
-            st_relaxed(zs + (size_t)i * 8 + r, zr);
-            st_shared_volatile(mine + x * 8 + r, zr);
-            if (z64) z64[(size_t)i * 8 + r] = (double)zr;
-          }
-          zp0 = __shfl_sync(FULL, zr, 4 * c);
-          zp1 = __shfl_sync(FULL, zr, 4 * c + 4);
-        }
-      }
-    }
-    if (!ok && lane == 0) s_abort = 1;
-    __syncthreads();
-    if (s_abort) return;
+    cp_async_wait<0>();
+    __syncwarp();
   }
 }
 
@@ -527,9 +438,10 @@ __global__ void __launch_bounds__(FWARPS * 32) k_ilu_factor_pipe(int nx, int ny,
     if (p >= npen) return;
     const int j = p % ny, k = p / ny;
     const int base_jk = nx * (j + ny * k);
+    const Pen PEN = make_pen(nx, ny, nz, j, k, base_jk);
     for (int x = 0; x < nx; ++x) {
       const int i = base_jk + x;
-      const int base = __ldg(rowptr + i);
+      const int base = rowptr_of(nx, ny, nz, i);
       const int nlow = (k > 0) + (j > 0) + (x > 0);
       double2 d = ld_nc2(A + (size_t)(base + nlow) * BB + 2 * lane);
       // lower neighbours in pattern order -z, -y, -x
@@ -541,7 +453,7 @@ __global__ void __launch_bounds__(FWARPS * 32) k_ilu_factor_pipe(int nx, int ny,
         const int sl = slot_of(nx, ny, nz, i, dl);
         const int su = slot_of(nx, ny, nz, kk, 6 - dl);
         const double2 aik = ld_nc2(A + (size_t)(base + sl) * BB + 2 * lane);
-        const double2 aki = ld_nc2(A + (size_t)(__ldg(rowptr + kk) + su) * BB + 2 * lane);
+        const double2 aki = ld_nc2(A + (size_t)(rowptr_of(nx, ny, nz, kk) + su) * BB + 2 * lane);
         double2 dk;
         if (dl < 2) {
           if (!poll_vec<double>(Dinv + (size_t)kk * BB, 2 * lane, dk, abortf, dstatus)) return;
@@ -645,10 +557,6 @@ __global__ void __launch_bounds__(FWARPS * 32) k_ilu_factor_pipe(int nx, int ny,
   }
 }
 
-int pipe_blocks(int npen) {
-  int warps = npen < 152 * 16 ? npen : 152 * 16;
-  return (warps + 7) / 8;
-}
 
 }  // namespace
 
@@ -661,41 +569,48 @@ void launch_ilu_factor_pipe(Handle& h, cudaStream_t s) {
                                                                           h.pipe, h.dstatus);
 }
 
+constexpr int SWEEP_R = 8;  // cells staged ahead in each warp's shared-memory ring
+
+int sweep_blocks(int npen) {
+  const int warps = npen < 152 * 16 ? npen : 152 * 16;
+  return (warps + AWARPS - 1) / AWARPS;
+}
+
 template <typename TM>
-void sweep_pair(Handle& h, const TM* A, const TM* Dinv, const double* r, TM* y, TM* zs, double* z64, cudaStream_t s) {
-  const int npen = h.ny * h.nz;
-  const size_t n8 = (size_t)h.n * 8;
-  cudaMemsetAsync(h.pipe, 0, 2 * sizeof(int), s);
+size_t sweep_smem() {
+  return sizeof(Slot<TM>) * SWEEP_R * AWARPS;
+}
+
+template <typename TM>
+void sweep_attributes() {
+  // idempotent; the rings need more than the default 48 KB of dynamic shared memory
+  cudaFuncSetAttribute(k_ilu_fwd_async<TM, SWEEP_R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sweep_smem<TM>());
+  cudaFuncSetAttribute(k_ilu_bwd_async<TM, SWEEP_R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sweep_smem<TM>());
+}
+
+template <typename TM>
+void sweep_pair(int nx, int ny, int nz, const int32_t* rowptr, const TM* A, const TM* Dinv, const double* r, TM* y,
+                TM* zs, double* z64, int* pipe, int* dstatus, cudaStream_t s) {
+  const size_t n8 = (size_t)nx * ny * nz * 8;
+  const int blocks = sweep_blocks(ny * nz);
+  const size_t smem = sweep_smem<TM>();
+  sweep_attributes<TM>();
+  cudaMemsetAsync(pipe, 0, 2 * sizeof(int), s);
   cudaMemsetAsync(y, 0xff, sizeof(TM) * n8, s);  // NaN sentinel
-  if (h.nx <= TILE_MAX_NX) {
-    const int ntiles = ((h.ny + TW - 1) / TW) * h.nz;
-    const int blocks = ntiles < 152 ? ntiles : 152;
-    const size_t smem = sizeof(TM) * (size_t)TW * h.nx * 8;
-    if (smem > 48 * 1024) {
-      cudaFuncSetAttribute(k_ilu_fwd_tile<TM, SWEEP_PD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      cudaFuncSetAttribute(k_ilu_bwd_tile<TM, SWEEP_PD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    }
-    k_ilu_fwd_tile<TM, SWEEP_PD><<<blocks, TW * 32, smem, s>>>(h.nx, h.ny, h.nz, h.rowptr, A, Dinv, r, y, h.pipe, h.dstatus);
-    cudaMemsetAsync(h.pipe, 0, 2 * sizeof(int), s);
-    cudaMemsetAsync(zs, 0xff, sizeof(TM) * n8, s);
-    k_ilu_bwd_tile<TM, SWEEP_PD><<<blocks, TW * 32, smem, s>>>(h.nx, h.ny, h.nz, h.rowptr, A, Dinv, y, zs, z64, h.pipe,
-                                                     h.dstatus);
-    return;
-  }
-  k_ilu_fwd_pipe<TM, SWEEP_PD><<<pipe_blocks(npen), 256, 0, s>>>(h.nx, h.ny, h.nz, h.rowptr, A, Dinv, r, y, h.pipe, h.dstatus);
-  cudaMemsetAsync(h.pipe, 0, 2 * sizeof(int), s);
+  k_ilu_fwd_async<TM, SWEEP_R><<<blocks, AWARPS * 32, smem, s>>>(nx, ny, nz, rowptr, A, Dinv, r, y, pipe, dstatus);
+  cudaMemsetAsync(pipe, 0, 2 * sizeof(int), s);
   cudaMemsetAsync(zs, 0xff, sizeof(TM) * n8, s);
-  k_ilu_bwd_pipe<TM, SWEEP_PD><<<pipe_blocks(npen), 256, 0, s>>>(h.nx, h.ny, h.nz, h.rowptr, A, Dinv, y, zs, z64, h.pipe,
-                                                        h.dstatus);
+  k_ilu_bwd_async<TM, SWEEP_R><<<blocks, AWARPS * 32, smem, s>>>(nx, ny, nz, rowptr, A, Dinv, y, zs, z64, pipe,
+                                                                 dstatus);
 }
 
 void launch_ilu_apply_pipe(Handle& h, const double* r, double* z, cudaStream_t s) {
   if (h.opt.precision == ISC_PRECISION_MIXED) {
     const size_t n8 = (size_t)h.n * 8;
-    sweep_pair<float>(h, h.J32, h.dinv32, r, h.vec32, h.vec32 + n8, z, s);
+    sweep_pair<float>(h.nx, h.ny, h.nz, h.rowptr, h.J32, h.dinv32, r, h.vec32, h.vec32 + n8, z, h.pipe, h.dstatus, s);
     return;
   }
-  sweep_pair<double>(h, h.J, h.dinv, r, h.tmp, z, nullptr, s);
+  sweep_pair<double>(h.nx, h.ny, h.nz, h.rowptr, h.J, h.dinv, r, h.tmp, z, nullptr, h.pipe, h.dstatus, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -749,17 +664,10 @@ extern "C" int isc_bilu0_apply_noalloc(int32_t nx, int32_t ny, int32_t nz, const
   int* ints = reinterpret_cast<int*>(scratch + (size_t)ISC_NOALLOC_MAX_CELLS * 8);
   int* pipe = ints;                                                     // counter, abort flag
   int* status = ints + 2;
-  const int npen = ny * nz;
-  const size_t vbytes = sizeof(double) * (size_t)n * 8;
-  // everything that must start at zero (or NaN) is cleared here: the array
+  // everything that must start at zero (or NaN) is cleared inside: the array
   // keeps the previous call's contents
   if (cudaMemsetAsync(ints, 0, NOALLOC_INTS * sizeof(int), s) != cudaSuccess) return ISC_ERR_CUDA;
-  cudaMemsetAsync(y, 0xff, vbytes, s);
-  k_ilu_fwd_pipe<double, 0><<<pipe_blocks(npen), 256, 0, s>>>(nx, ny, nz, d_rowptr, d_A, d_Dinv, d_r, y, pipe, status);
-  cudaMemsetAsync(pipe, 0, 2 * sizeof(int), s);
-  cudaMemsetAsync(d_z, 0xff, vbytes, s);
-  k_ilu_bwd_pipe<double, 0><<<pipe_blocks(npen), 256, 0, s>>>(nx, ny, nz, d_rowptr, d_A, d_Dinv, y, d_z, nullptr, pipe,
-                                                            status);
+  sweep_pair<double>(nx, ny, nz, d_rowptr, d_A, d_Dinv, d_r, y, d_z, nullptr, pipe, status, s);
   int h_status = 0;
   if (cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return ISC_ERR_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return ISC_ERR_CUDA;
