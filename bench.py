@@ -44,6 +44,23 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(x, device="cpu"):
+    """Largest value of x over the ranks of the default process group (x itself
+    without one): the whole job is as slow as its slowest replica."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, steps, ms_max):
+    """Whole-job Newton steps per second: every rank ran `steps` steps."""
+    return world * steps / (ms_max / 1e3)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -171,12 +188,8 @@ def run_isc(args):
     ms_dev = ev0.elapsed_time(ev1)
     stats = g.stats()
     clocks = sampler.stop()
-    ms_total = max(ms_dev, wall * 1e3)
-    if world > 1:
-        t = torch.tensor([ms_total], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
-    value = world * args.steps / (ms_total / 1e3)
+    ms_total = max_over_ranks(max(ms_dev, wall * 1e3), "cuda")
+    value = job_throughput(world, args.steps, ms_total)
     kry = [i.krylov_iterations for i in infos]
     # end-to-end through the C ABI with host buffers
     uh, ch = g.get_state()
@@ -199,11 +212,7 @@ def run_isc(args):
         u_out, c_out = g.get_state()
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    e2e_val = world * e2e_steps / e2e_s
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_val = world * e2e_steps / float(t.item())
+    e2e_val = job_throughput(world, e2e_steps, max_over_ranks(e2e_s * 1e3, "cuda"))
     io_bytes = 9 * n * 8
     # mixed precision on the same step: FP32 ILU(0) factors and sweeps inside the FP64 FGMRES
     g.set_options(precision="mixed")
