@@ -435,9 +435,11 @@ __global__ void k_update(int n, double* __restrict__ u, const double* __restrict
   const double p = uo[0];
   un[0] = p + fmin(fmax(d[0], -max_dp_frac * p), max_dp_frac * p);
   un[5] = uo[5] + fmin(fmax(d[5], -max_dT), max_dT);
+  // values taken in the halving branches are formed without contraction, so the
+  // update is bit-identical to a plain evaluation of the same formulas
   double x = uo[1] + d[1];
   if (x < 0.0) x = 0.5 * uo[1];
-  if (x > 1.0) x = 1.0 - 0.5 * (1.0 - uo[1]);
+  if (x > 1.0) x = __dsub_rn(1.0, __dmul_rn(0.5, __dsub_rn(1.0, uo[1])));
   un[1] = x;
   const int ks[5] = {2, 3, 4, 6, 7};
 #pragma unroll
@@ -449,7 +451,7 @@ __global__ void k_update(int n, double* __restrict__ u, const double* __restrict
   const double so_old = 1.0 - uo[6] - uo[7];
   const double so_new = 1.0 - un[6] - un[7];
   if (so_new < 0.0) {
-    double target = 1.0 - 0.5 * so_old;
+    double target = __dsub_rn(1.0, __dmul_rn(0.5, so_old));
     double s = un[6] + un[7];
     un[6] *= target / s;
     un[7] *= target / s;
