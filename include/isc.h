@@ -186,7 +186,8 @@ typedef struct isc_step_info {
  * accumulated while options.profile = 1) and launch counts. */
 enum isc_kernel_class {
   ISC_K_PROPS = 0, ISC_K_FLUX = 1, ISC_K_NORM = 2, ISC_K_GJ = 3, ISC_K_ILU_FACTOR = 4,
-  ISC_K_SPMV = 5, ISC_K_PREC_APPLY = 6, ISC_K_BLAS1 = 7, ISC_K_UPDATE = 8, ISC_K_COUNT = 9
+  ISC_K_SPMV = 5, ISC_K_PREC_APPLY = 6, ISC_K_BLAS1 = 7, ISC_K_UPDATE = 8, ISC_K_ADJOINT = 9,
+  ISC_K_COUNT = 10
 };
 typedef struct isc_stats {
   double ms[ISC_K_COUNT];
@@ -312,8 +313,68 @@ int isc_bsr_spmv_device(int32_t nrows, const int32_t* d_rowptr, const int32_t* d
 int isc_bilu0_apply_noalloc(int32_t nx, int32_t ny, int32_t nz, const int32_t* d_rowptr, const double* d_A,
                             const double* d_Dinv, const double* d_r, double* d_z, void* stream);
 
-/* Discrete adjoint of the time loop: not implemented yet. */
-int isc_adjoint(struct isc_handle* h);
+/* ------------------------------------------------------------ sensitivities */
+
+/* Parameters theta of the sensitivity analysis. The paper computes no
+ * sensitivities; these calls differentiate its discrete equations (Sec. 3.1)
+ * exactly.
+ *   log_k  N host doubles: per-cell ln k multipliers m_i. The permeabilities
+ *          become k_d,i = k_d,i(create) exp(m_i) for d = x, y, z, so the
+ *          harmonic face transmissibilities change, and so does the well index
+ *          of a perforation in cell i, WI_i(create) exp(m_i) (Peaceman WI is
+ *          linear in k). A rate injector's perforation shares WI_i / sum WI
+ *          follow. All zero at creation.
+ *   Ea     nr host doubles: activation energies E_a (J/mol) of the reactions.
+ *   lnA    nr host doubles: ln of the pre-exponential factors A.
+ * A NULL pointer leaves that group unchanged. The arrays are copied; the call
+ * synchronises the handle's stream. Non-finite values: ISC_ERR_INVALID_ARG. */
+int isc_set_parameters(struct isc_handle* h, const double* log_k, const double* Ea, const double* lnA);
+/* The current parameters (NULL skips a group). */
+int isc_get_parameters(struct isc_handle* h, double* log_k, double* Ea, double* lnA);
+
+typedef struct isc_adjoint_spec {
+  int32_t n_steps;           /* implicit-Euler steps of the time loop, >= 1 */
+  const double* dt;          /* host [n_steps] step sizes (s); the sequence is frozen (no step cutting) */
+  int32_t checkpoint_every;  /* states kept on the device every this many steps; the reverse sweep
+                                recomputes each segment from its checkpoint (>= 1) */
+  double tol_adjoint;        /* relative residual of every transposed linear solve (0: options.tol_lin) */
+} isc_adjoint_spec;
+
+typedef struct isc_adjoint_info {
+  int32_t status;
+  int32_t newton_iterations;          /* forward and recomputed steps */
+  int32_t krylov_iterations_forward;  /* Krylov iterations of those Newton solves */
+  int32_t krylov_iterations_adjoint;  /* Krylov iterations of the transposed solves */
+  int32_t recomputed_steps;
+  double loss;
+  double adjoint_rel_residual;        /* largest final relative residual of a transposed solve */
+} isc_adjoint_info;
+
+/* Discrete adjoint of the time loop. From the handle's accepted state (after
+ * isc_init_equilibrium or a converged isc_timestep) the call runs the
+ * spec->n_steps implicit-Euler steps with Newton as isc_timestep does (the
+ * handle's options), and evaluates the loss
+ *     L = sum_n dt_n sum_{BHP producer perforations} (M_LO (Q_o x_LO + Q_g y_LO)
+ *                                                     + M_HO (Q_o x_HO + Q_g y_HO))
+ * the cumulative LO + HO mass (kg) produced in any phase at the converged
+ * states (Peaceman rates of Sec. 2.2, outflow only). If any gradient pointer
+ * is non-NULL it then sweeps the steps backwards: per step one transposed
+ * linear solve J_n^T lambda_n = ubar_n with the preconditioned Krylov method
+ * of the options (the transposed blocks are decoupled and factored like J),
+ * the coke equation entering through the implicit-function theorem, and
+ * accumulates
+ *   g_log_k  N host doubles  dL/d log_k (as set by isc_set_parameters),
+ *   g_Ea     nr host doubles dL/dE_a (per J/mol),
+ *   g_lnA    nr host doubles dL/d ln A.
+ * Each may be NULL. States are kept every spec->checkpoint_every steps
+ * ((ceil(n_steps/K) + K + 2) x 9N doubles of device memory, allocated on first
+ * use and kept with the handle) and recomputed bit-exactly during the reverse
+ * sweep. loss (may be NULL) and info->loss receive L. On success the handle is
+ * at the final state of the loop. A step that does not converge returns
+ * ISC_ERR_NEWTON_NOCONV (the handle keeps its last accepted state); a
+ * transposed solve that misses tol_adjoint returns ISC_ERR_KRYLOV_NOCONV. */
+int isc_adjoint(struct isc_handle* h, const isc_adjoint_spec* spec, double* loss, double* g_log_k,
+                double* g_Ea, double* g_lnA, isc_adjoint_info* info);
 
 #ifdef __cplusplus
 }

@@ -318,6 +318,15 @@ def config(n: int, seed: int = 0) -> Case:
     raise ValueError(n)
 
 
+def adjoint_steps(case: Case, first: float = 60.0, ratio: float = 1.8) -> list:
+    """Frozen step sizes of a sensitivity run: a geometric ramp from ``first``
+    seconds by ``ratio`` per step, capped at the case's nominal step, for the
+    case's number of steps. Newton from the ignited initial state needs the
+    short first steps; for the 40x40x10 adjoint workload (20 steps, cap 1 day)
+    the loop covers 8.8 days."""
+    return [min(first * ratio ** k, case.dt0) for k in range(case.n_steps)]
+
+
 def small_box(nx=4, ny=3, nz=2, seed=0) -> Case:
     """A tiny 3D case for dense-LU comparisons and element-by-element parity."""
     return field_case(nx, ny, nz, seed, 7, f"box {nx}x{ny}x{nz}", 1 * DAY, 4, air_rate_std=2e-4)

@@ -114,7 +114,9 @@ int dalloc(isc_handle* h, T** p, size_t count) {
 void free_all(isc_handle* h) {
   void* ptrs[] = {h->rowptr, h->col, h->level_cells, h->phi_ref, h->depth, h->tx, h->ty, h->tz, h->well_slot,
                   h->slots, h->u, h->coke, h->u_n, h->coke_n, h->acc_n, h->props, h->R, h->J, h->ntot, h->du,
-                  h->rhs, h->dinv, h->J32, h->dinv32, h->vec32, h->V, h->Z, h->w, h->tmp, h->partial, h->scal, h->dstatus, h->pipe, h->red_counter};
+                  h->rhs, h->dinv, h->J32, h->dinv32, h->vec32, h->V, h->Z, h->w, h->tmp, h->partial, h->scal, h->dstatus, h->pipe, h->red_counter,
+                  h->wx, h->wy, h->wz, h->adj.store, h->adj.ubar, h->adj.cbar, h->adj.lam, h->adj.glnk, h->adj.grx,
+                  h->adj.scond, h->adj.kd, h->adj.loss_cell, h->adj.sums, h->adj.inj_first, h->adj.inj_count};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->h_scal) cudaFreeHost(h->h_scal);
@@ -372,6 +374,65 @@ int bicgstab(isc_handle* h, const double* b, double* x, int* its_out, double* re
   return ISC_OK;
 }
 
+// Transmissibilities (harmonic average of A k / h of the two cells, Sec. 3.1),
+// the face weights d ln T / d ln k_lo = t_hi / (t_lo + t_hi), the well
+// indices and the injector shares at the current ln k multipliers; uploaded
+// on the handle's stream (the host vectors live until the copies finish).
+int refresh_parameters(isc_handle* h) {
+  const int n = h->n, nx = h->nx, ny = h->ny, nz = h->nz;
+  std::vector<double> tx(n, 0.0), ty(n, 0.0), tz(n, 0.0), wx(n, 0.0), wy(n, 0.0), wz(n, 0.0);
+  std::vector<double> k(3 * (size_t)n);
+  for (int d = 0; d < 3; ++d)
+    for (int c = 0; c < n; ++c) k[(size_t)d * n + c] = h->h_perm0[(size_t)d * n + c] * exp(h->h_lnk[c]);
+  const double* kx = k.data();
+  const double* ky = kx + n;
+  const double* kz = ky + n;
+  auto harm = [](double a, double b) { return 2.0 * a * b / (a + b); };
+  const double ax = h->face_area[0], ay = h->face_area[1], az = h->face_area[2];
+  for (int c = 0; c < n; ++c) {
+    int ix = c % nx, iy = (c / nx) % ny, iz = c / (nx * ny);
+    if (ix < nx - 1) {
+      tx[c] = harm(ax * kx[c], ax * kx[c + 1]);
+      wx[c] = kx[c + 1] / (kx[c] + kx[c + 1]);
+    }
+    if (iy < ny - 1) {
+      ty[c] = harm(ay * ky[c], ay * ky[c + nx]);
+      wy[c] = ky[c + nx] / (ky[c] + ky[c + nx]);
+    }
+    if (iz < nz - 1) {
+      tz[c] = harm(az * kz[c], az * kz[c + nx * ny]);
+      wz[c] = kz[c + nx * ny] / (kz[c] + kz[c + nx * ny]);
+    }
+  }
+  // well indices scale with the cell's permeability (Peaceman WI is linear in k)
+  for (const WellInfo& W : h->h_wells) {
+    double wsum = 0.0;
+    for (int q = 0; q < W.count; ++q) {
+      WellSlot& sl = h->h_slots[W.first + q];
+      sl.WI = h->h_WI0[W.first + q] * exp(h->h_lnk[sl.cell]);
+      wsum += sl.WI;
+    }
+    if (W.kind != ISC_WELL_RATE_INJECTOR) continue;
+    for (int q = 0; q < W.count; ++q) {
+      WellSlot& sl = h->h_slots[W.first + q];
+      sl.share = sl.WI / wsum;
+      for (int c = 0; c < 6; ++c) sl.src[c] = sl.share * W.target * W.inj_y[c];
+      sl.src[6] = sl.share * W.target * W.Hinj;
+    }
+  }
+  cudaStream_t s = h->stream;
+  CUDA_TRY(h, cudaMemcpyAsync(h->tx, tx.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(h, cudaMemcpyAsync(h->ty, ty.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(h, cudaMemcpyAsync(h->tz, tz.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(h, cudaMemcpyAsync(h->wx, wx.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(h, cudaMemcpyAsync(h->wy, wy.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(h, cudaMemcpyAsync(h->wz, wz.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+  if (h->nslots)
+    CUDA_TRY(h, cudaMemcpyAsync(h->slots, h->h_slots.data(), sizeof(WellSlot) * h->nslots, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(h, cudaStreamSynchronize(s));
+  return ISC_OK;
+}
+
 int validate_options(isc_handle* h, const isc_options& o) {
   if (o.restart < 1 || o.restart > MAX_RESTART) return set_err(h, ISC_ERR_INVALID_ARG, "restart must be 1..64");
   if (o.krylov != ISC_KRYLOV_GMRES && o.krylov != ISC_KRYLOV_BICGSTAB)
@@ -572,40 +633,47 @@ int isc_create(const isc_grid* grid, const isc_rock* rock, const isc_fluid* fl, 
       level_cells[fill[L]++] = c;
     }
   }
-  // transmissibilities: harmonic average of (A k / h) of the two cells (Sec. 3.1)
-  std::vector<double> tx(n, 0.0), ty(n, 0.0), tz(n, 0.0), depth(n);
+  // permeabilities and depths (the transmissibilities follow from the ln k
+  // multipliers, all zero at creation, in refresh_parameters)
   const double* kx = rock->perm;
   const double* ky = rock->perm + n;
   const double* kz = rock->perm + 2 * (size_t)n;
-  auto harm = [](double a, double b) { return 2.0 * a * b / (a + b); };
-  const double ax = grid->dy * grid->dz / grid->dx, ay = grid->dx * grid->dz / grid->dy,
-               az = grid->dx * grid->dy / grid->dz;
+  std::vector<double> depth(n);
   for (int c = 0; c < n; ++c) {
-    int ix = c % nx, iy = (c / nx) % ny, iz = c / (nx * ny);
-    if (ix < nx - 1) tx[c] = harm(ax * kx[c], ax * kx[c + 1]);
-    if (iy < ny - 1) ty[c] = harm(ay * ky[c], ay * ky[c + nx]);
-    if (iz < nz - 1) tz[c] = harm(az * kz[c], az * kz[c + nx * ny]);
+    int iz = c / (nx * ny);
     depth[c] = grid->depth ? grid->depth[c] : (iz + 0.5) * grid->dz;
     if (!(rock->phi_ref[c] > 0.0) || !(kx[c] > 0) || !(ky[c] > 0) || !(kz[c] > 0)) {
       delete h;
       return ISC_ERR_INVALID_ARG;
     }
   }
+  h->h_perm0.assign(rock->perm, rock->perm + 3 * (size_t)n);
+  h->h_lnk.assign(n, 0.0);
+  h->face_area[0] = grid->dy * grid->dz / grid->dx;
+  h->face_area[1] = grid->dx * grid->dz / grid->dy;
+  h->face_area[2] = grid->dx * grid->dy / grid->dz;
+  for (int r = 0; r < rx->nr; ++r) {
+    h->h_Ea[r] = rx->Ea[r];
+    h->h_lnA[r] = log(rx->A[r]);
+  }
   // well slots
   std::vector<int32_t> well_slot(n, -1);
-  std::vector<WellSlot> slots;
+  std::vector<int32_t> inj_first, inj_count;
   for (int w = 0; w < wells->nw; ++w) {
     const isc_well& W = wells->wells[w];
     if (W.n_perf < 1 || !W.cells || !W.WI) {
       delete h;
       return ISC_ERR_INVALID_ARG;
     }
-    double wsum = 0;
-    for (int q = 0; q < W.n_perf; ++q) wsum += W.WI[q];
-    double Hinj = 0.0;
+    WellInfo info{};
+    info.kind = W.kind;
+    info.first = (int)h->h_slots.size();
+    info.count = W.n_perf;
+    info.target = W.target;
+    for (int c = 0; c < 6; ++c) info.inj_y[c] = W.inj_y[c];
     if (W.kind == ISC_WELL_RATE_INJECTOR) {
       // molar enthalpy of the injected stream at T_inj
-      double T = W.inj_T, Tr = fl->T_ref;
+      double T = W.inj_T, Tr = fl->T_ref, Hinj = 0.0;
       for (int c = 0; c < 6; ++c) {
         double hg = 0, tk = T, trk = Tr;
         for (int k = 0; k < 4; ++k) {
@@ -622,6 +690,9 @@ int isc_create(const isc_grid* grid, const isc_rock* rock, const isc_fluid* fl, 
           Hinj += W.inj_y[c] * hg;
         }
       }
+      info.Hinj = Hinj;
+      inj_first.push_back(info.first);
+      inj_count.push_back(info.count);
     }
     for (int q = 0; q < W.n_perf; ++q) {
       int c = W.cells[q];
@@ -631,18 +702,16 @@ int isc_create(const isc_grid* grid, const isc_rock* rock, const isc_fluid* fl, 
       }
       WellSlot sl{};
       sl.kind = W.kind;
-      sl.WI = W.WI[q];
+      sl.cell = c;
       sl.bhp = W.target;
-      if (W.kind == ISC_WELL_RATE_INJECTOR) {
-        double share = W.WI[q] / wsum;
-        for (int k = 0; k < 6; ++k) sl.src[k] = share * W.target * W.inj_y[k];
-        sl.src[6] = share * W.target * Hinj;
-      }
-      well_slot[c] = (int32_t)slots.size();
-      slots.push_back(sl);
+      well_slot[c] = (int32_t)h->h_slots.size();
+      h->h_slots.push_back(sl);
+      h->h_WI0.push_back(W.WI[q]);
     }
+    h->h_wells.push_back(info);
   }
-  h->nslots = (int)slots.size();
+  h->nslots = (int)h->h_slots.size();
+  h->adj.n_inj = (int)inj_first.size();
   // device memory
   h->restart_alloc = std::max(o.restart, 8);
   const size_t len = (size_t)n * 8;
@@ -656,6 +725,11 @@ int isc_create(const isc_grid* grid, const isc_rock* rock, const isc_fluid* fl, 
   e |= dalloc(h, &h->tx, n);
   e |= dalloc(h, &h->ty, n);
   e |= dalloc(h, &h->tz, n);
+  e |= dalloc(h, &h->wx, n);
+  e |= dalloc(h, &h->wy, n);
+  e |= dalloc(h, &h->wz, n);
+  e |= dalloc(h, &h->adj.inj_first, std::max(h->adj.n_inj, 1));
+  e |= dalloc(h, &h->adj.inj_count, std::max(h->adj.n_inj, 1));
   e |= dalloc(h, &h->well_slot, n);
   e |= dalloc(h, &h->slots, std::max(h->nslots, 1));
   e |= dalloc(h, &h->u, len);
@@ -697,11 +771,16 @@ int isc_create(const isc_grid* grid, const isc_rock* rock, const isc_fluid* fl, 
   cudaMemcpyAsync(h->level_cells, level_cells.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(h->phi_ref, rock->phi_ref, sizeof(double) * n, cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(h->depth, depth.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s);
-  cudaMemcpyAsync(h->tx, tx.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s);
-  cudaMemcpyAsync(h->ty, ty.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s);
-  cudaMemcpyAsync(h->tz, tz.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(h->well_slot, well_slot.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s);
-  if (h->nslots) cudaMemcpyAsync(h->slots, slots.data(), sizeof(WellSlot) * h->nslots, cudaMemcpyHostToDevice, s);
+  if (h->adj.n_inj) {
+    cudaMemcpyAsync(h->adj.inj_first, inj_first.data(), sizeof(int32_t) * h->adj.n_inj, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(h->adj.inj_count, inj_count.data(), sizeof(int32_t) * h->adj.n_inj, cudaMemcpyHostToDevice, s);
+  }
+  if (refresh_parameters(h) != ISC_OK) {
+    free_all(h);
+    delete h;
+    return ISC_ERR_CUDA;
+  }
   cudaMemsetAsync(h->dstatus, 0, sizeof(int), s);
   cudaMemsetAsync(h->red_counter, 0, sizeof(unsigned), s);
   cudaMemsetAsync(h->u, 0, sizeof(double) * len, s);
@@ -1033,9 +1112,216 @@ int isc_bsr_spmv_device(int32_t nrows, const int32_t* d_rowptr, const int32_t* d
   return cudaGetLastError() == cudaSuccess ? ISC_OK : ISC_ERR_CUDA;
 }
 
-int isc_adjoint(isc_handle* h) {
-  if (h) h->last_error = "the discrete adjoint is not implemented";
-  return ISC_ERR_UNIMPLEMENTED;
+int isc_set_parameters(isc_handle* h, const double* log_k, const double* Ea, const double* lnA) {
+  if (!h) return ISC_ERR_INVALID_ARG;
+  if (log_k) {
+    for (int c = 0; c < h->n; ++c)
+      if (!isfinite(log_k[c])) return set_err(h, ISC_ERR_INVALID_ARG, "non-finite ln k multiplier");
+  }
+  for (int r = 0; r < h->P.nr; ++r) {
+    if (Ea && !isfinite(Ea[r])) return set_err(h, ISC_ERR_INVALID_ARG, "non-finite activation energy");
+    if (lnA && !isfinite(lnA[r])) return set_err(h, ISC_ERR_INVALID_ARG, "non-finite ln A");
+  }
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  if (log_k) {
+    h->h_lnk.assign(log_k, log_k + h->n);
+    int st = refresh_parameters(h);
+    if (st) return st;
+  }
+  for (int r = 0; r < h->P.nr; ++r) {
+    if (Ea) {
+      h->h_Ea[r] = Ea[r];
+      h->P.EaR[r] = Ea[r] / R_GAS;
+    }
+    if (lnA) {
+      h->h_lnA[r] = lnA[r];
+      h->P.A[r] = exp(lnA[r]);
+    }
+  }
+  h->assembled = h->decoupled = h->prec_built = false;
+  return ISC_OK;
+}
+
+int isc_get_parameters(isc_handle* h, double* log_k, double* Ea, double* lnA) {
+  if (!h) return ISC_ERR_INVALID_ARG;
+  if (log_k) memcpy(log_k, h->h_lnk.data(), sizeof(double) * h->n);
+  for (int r = 0; r < h->P.nr; ++r) {
+    if (Ea) Ea[r] = h->h_Ea[r];
+    if (lnA) lnA[r] = h->h_lnA[r];
+  }
+  return ISC_OK;
+}
+
+int isc_adjoint(isc_handle* h, const isc_adjoint_spec* spec, double* loss, double* g_log_k, double* g_Ea,
+                double* g_lnA, isc_adjoint_info* info) {
+  if (!h || !spec) return ISC_ERR_INVALID_ARG;
+  isc_adjoint_info loc{};
+  if (!info) info = &loc;
+  memset(info, 0, sizeof(*info));
+  const int N = spec->n_steps, K = spec->checkpoint_every;
+  if (N < 1 || K < 1 || !spec->dt) return set_err(h, ISC_ERR_INVALID_ARG, "n_steps and checkpoint_every must be >= 1");
+  for (int q = 0; q < N; ++q)
+    if (!(spec->dt[q] > 0.0) || !isfinite(spec->dt[q])) return set_err(h, ISC_ERR_INVALID_ARG, "step sizes must be > 0");
+  if (!(spec->tol_adjoint >= 0.0)) return set_err(h, ISC_ERR_INVALID_ARG, "tol_adjoint must be >= 0");
+  if (!h->have_acc) return set_err(h, ISC_ERR_STATE, "isc_begin_step (or isc_init_equilibrium) must come first");
+  const bool want_grad = g_log_k || g_Ea || g_lnA;
+  const int n = h->n, nr = h->P.nr;
+  const size_t len = (size_t)n * 8, SN = (size_t)n * 9;
+  const int ncp = (N + K - 1) / K;
+  const int need = ncp + K + 2;                 // checkpoints, K+1 segment states, the final state
+  const int traj0 = ncp, fin = ncp + K + 1;
+  AdjointWork& A = h->adj;
+  cudaStream_t s = h->stream;
+  // workspace
+  if (!A.ubar) {
+    int e = 0;
+    e |= dalloc(h, &A.ubar, len);
+    e |= dalloc(h, &A.cbar, n);
+    e |= dalloc(h, &A.lam, len);
+    e |= dalloc(h, &A.glnk, n);
+    e |= dalloc(h, &A.grx, (size_t)2 * ISC_MAX_RXN * n);
+    e |= dalloc(h, &A.scond, n);
+    e |= dalloc(h, &A.kd, n);
+    e |= dalloc(h, &A.loss_cell, n);
+    e |= dalloc(h, &A.sums, 1 + 2 * ISC_MAX_RXN);
+    if (e) return ISC_ERR_NOMEM;
+  }
+  if (A.cap_states < need) {
+    if (A.store) cudaFree(A.store);
+    A.store = nullptr;
+    A.cap_states = 0;
+    if (dalloc(h, &A.store, (size_t)need * SN)) return ISC_ERR_NOMEM;
+    A.cap_states = need;
+  }
+  auto slot = [&](int k) { return A.store + (size_t)k * SN; };
+  auto save = [&](int k) -> int {
+    CUDA_TRY(h, cudaMemcpyAsync(slot(k), h->u, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(h, cudaMemcpyAsync(slot(k) + len, h->coke, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    return ISC_OK;
+  };
+  auto load_accepted = [&](int k) -> int {
+    CUDA_TRY(h, cudaMemcpyAsync(h->u, slot(k), sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(h, cudaMemcpyAsync(h->coke, slot(k) + len, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    return isc_begin_step(h);
+  };
+  auto step = [&](int q, bool recompute) -> int {
+    isc_step_info si;
+    int st = isc_timestep(h, spec->dt[q], &si);
+    info->newton_iterations += si.newton_iterations;
+    info->krylov_iterations_forward += si.krylov_iterations;
+    if (recompute) info->recomputed_steps++;
+    return st;
+  };
+  int st;
+  // ---------------------------------------------------------- forward sweep
+  CUDA_TRY(h, cudaMemsetAsync(A.loss_cell, 0, sizeof(double) * n, s));
+  if ((st = save(0)) || (st = save(traj0))) return st;
+  int seg0 = 0;
+  for (int q = 1; q <= N; ++q) {
+    if ((st = step(q - 1, false))) return info->status = st;
+    {
+      Region rg(h, ISC_K_ADJOINT, 1);
+      launch_oil_rate(*h, spec->dt[q - 1], s);
+    }
+    const int j = q - seg0;
+    if ((st = save(traj0 + j))) return st;
+    if (j == K && q < N) {
+      seg0 = q;
+      if ((st = save(q / K)) || (st = save(traj0))) return st;
+    }
+  }
+  if ((st = save(fin))) return st;
+  launch_row_sums(1, n, A.loss_cell, A.sums, s);
+  double Lsum = 0.0;
+  CUDA_TRY(h, cudaMemcpyAsync(&Lsum, A.sums, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(h, cudaStreamSynchronize(s));
+  info->loss = Lsum;
+  if (loss) *loss = Lsum;
+  if (!want_grad) return ISC_OK;
+  // --------------------------------------------------------- reverse sweep
+  CUDA_TRY(h, cudaMemsetAsync(A.ubar, 0, sizeof(double) * len, s));
+  CUDA_TRY(h, cudaMemsetAsync(A.cbar, 0, sizeof(double) * n, s));
+  CUDA_TRY(h, cudaMemsetAsync(A.glnk, 0, sizeof(double) * n, s));
+  CUDA_TRY(h, cudaMemsetAsync(A.grx, 0, sizeof(double) * 2 * ISC_MAX_RXN * n, s));
+  const double tol_saved = h->opt.tol_lin;
+  const double tol_adj = spec->tol_adjoint > 0.0 ? spec->tol_adjoint : tol_saved;
+  int result = ISC_OK;
+  for (int seg = ncp - 1; seg >= 0 && result == ISC_OK; --seg) {
+    const int s0 = seg * K, s1 = std::min(s0 + K, N);
+    if (seg < ncp - 1) {
+      // recompute the segment's states from its checkpoint (the Newton path is deterministic)
+      if ((result = load_accepted(seg))) break;
+      if ((result = save(traj0))) break;
+      for (int q = s0 + 1; q <= s1 && result == ISC_OK; ++q) {
+        result = step(q - 1, true);
+        if (!result) result = save(traj0 + q - s0);
+      }
+      if (result) break;
+    }
+    for (int q = s1; q > s0; --q) {
+      const double dt = spec->dt[q - 1];
+      const double* old = slot(traj0 + q - 1 - s0);
+      const double* cur = slot(traj0 + q - s0);
+      cudaMemcpyAsync(h->u_n, old, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
+      cudaMemcpyAsync(h->coke_n, old + len, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+      launch_old_accumulation(*h, s);
+      h->have_acc = true;
+      cudaMemcpyAsync(h->u, cur, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
+      {
+        Region rg(h, ISC_K_ADJOINT, 1);
+        launch_adj_pre(*h, dt, s);
+      }
+      if ((result = isc_assemble(h, dt))) break;
+      {
+        Region rg(h, ISC_K_ADJOINT, 1);
+        launch_bsr_transpose(*h, s);
+      }
+      // J^T lambda = ubar (the transposed system is decoupled and preconditioned like J)
+      cudaMemcpyAsync(h->R, A.ubar, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
+      if (h->opt.decouple && (result = isc_decouple(h))) break;
+      if ((result = build_prec(h))) break;
+      {
+        Region rg(h, ISC_K_BLAS1, 1);
+        launch_scale_copy((int)len, 1.0, h->R, h->rhs, s);
+      }
+      int its = 0;
+      double rel = 0.0;
+      h->opt.tol_lin = tol_adj;
+      if (h->opt.krylov == ISC_KRYLOV_GMRES)
+        result = gmres(h, h->rhs, A.lam, &its, &rel);
+      else
+        result = bicgstab(h, h->rhs, A.lam, &its, &rel);
+      h->opt.tol_lin = tol_saved;
+      info->krylov_iterations_adjoint += its;
+      info->adjoint_rel_residual = std::max(info->adjoint_rel_residual, rel);
+      if (result) break;
+      {
+        Region rg(h, ISC_K_ADJOINT, q > 1 ? 4 : 3);
+        launch_adj_post(*h, q > 1, s);
+      }
+      CUDA_TRY(h, cudaGetLastError());
+    }
+  }
+  h->opt.tol_lin = tol_saved;
+  h->assembled = h->decoupled = h->prec_built = false;
+  if (result == ISC_OK) result = check_device_status(h);
+  // leave the handle at the final state of the time loop
+  int st2 = load_accepted(fin);
+  if (result) return info->status = result;
+  if (st2) return info->status = st2;
+  if (g_log_k) CUDA_TRY(h, cudaMemcpyAsync(g_log_k, A.glnk, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+  if (nr > 0) {
+    launch_row_sums(2 * nr, n, A.grx, A.sums + 1, s);
+    double sums[2 * ISC_MAX_RXN];
+    CUDA_TRY(h, cudaMemcpyAsync(sums, A.sums + 1, sizeof(double) * 2 * nr, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(h, cudaStreamSynchronize(s));
+    for (int r = 0; r < nr; ++r) {
+      if (g_lnA) g_lnA[r] = sums[r];
+      if (g_Ea) g_Ea[r] = sums[nr + r];
+    }
+  }
+  CUDA_TRY(h, cudaStreamSynchronize(s));
+  return ISC_OK;
 }
 
 }  // extern "C"

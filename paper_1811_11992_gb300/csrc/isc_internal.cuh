@@ -66,9 +66,38 @@ struct Params {
 // One well perforation slot (a cell holds at most one).
 struct WellSlot {
   int kind;                   // ISC_WELL_*
+  int cell;                   // perforated cell
   double WI;
   double bhp;                 // producer
+  double share;               // injector: WI / sum of the well's WI
   double src[7];              // injector: mol/s per component and J/s
+};
+
+// Host record of one well (the slots of a well are contiguous).
+struct WellInfo {
+  int kind;
+  int first, count;           // slot range
+  double target;
+  double inj_y[6];
+  double Hinj;                // molar enthalpy of the injected stream
+};
+
+// Workspace of the discrete adjoint (allocated on first use).
+struct AdjointWork {
+  int cap_states = 0;         // states (9N doubles: u SoA 8N, then coke N) the store holds
+  double* store = nullptr;
+  double* ubar = nullptr;     // adjoint of u^n, block-major 8N
+  double* cbar = nullptr;     // adjoint of the coke C^n (N)
+  double* lam = nullptr;      // multiplier of the step's residual, block-major 8N
+  double* glnk = nullptr;     // dL/d ln k per cell (N)
+  double* grx = nullptr;      // per-cell parts of dL/d ln A_r (rows 0..nr-1) and dL/d Ea_r (rows nr..2nr-1)
+  double* scond = nullptr;    // conduction sensitivity per cell (N)
+  double* kd = nullptr;       // (C-bar - gamma) / (dg/dC) per cell (N)
+  double* loss_cell = nullptr;// per-cell cumulative produced oil mass (N)
+  double* sums = nullptr;     // reduced loss and reaction gradients
+  int32_t* inj_first = nullptr;  // injector wells: first slot and slot count
+  int32_t* inj_count = nullptr;
+  int n_inj = 0;
 };
 
 // device status word bits
@@ -93,6 +122,15 @@ struct Handle {
   int32_t* well_slot = nullptr;
   WellSlot* slots = nullptr;
   int nslots = 0;
+  double *wx = nullptr, *wy = nullptr, *wz = nullptr;  // face weights d ln T / d ln k_lo, indexed by lo
+  // sensitivity parameters: creation-time permeabilities and well indices, the
+  // per-cell ln k multipliers and the host copies they generate
+  std::vector<double> h_perm0, h_WI0, h_lnk;
+  std::vector<WellSlot> h_slots;
+  std::vector<WellInfo> h_wells;
+  double face_area[3] = {0, 0, 0};                 // A/h of x, y, z faces
+  double h_Ea[ISC_MAX_RXN] = {}, h_lnA[ISC_MAX_RXN] = {};  // current reaction parameters
+  AdjointWork adj;
   // device: state
   double *u = nullptr, *coke = nullptr;          // iterate (SoA 8N), solved coke (N)
   double *u_n = nullptr, *coke_n = nullptr;       // accepted state
@@ -149,6 +187,12 @@ void launch_prec_apply(Handle& h, const double* r, double* z, cudaStream_t s);
 void launch_ilu_apply_pipe(Handle& h, const double* r, double* z, cudaStream_t s);
 void launch_ilu_factor_pipe(Handle& h, cudaStream_t s);
 void launch_update(Handle& h, cudaStream_t s);
+// discrete adjoint (isc_adjoint.cu)
+void launch_oil_rate(Handle& h, double dt, cudaStream_t s);
+void launch_adj_pre(Handle& h, double dt, cudaStream_t s);
+void launch_bsr_transpose(Handle& h, cudaStream_t s);
+void launch_adj_post(Handle& h, bool has_old, cudaStream_t s);
+void launch_row_sums(int nrows, int len, const double* x, double* out, cudaStream_t s);
 void launch_to_f32(size_t n, const double* x, float* y, cudaStream_t s);
 // BLAS-1 with fixed-order two-stage reductions; results land in h.scal[off..]
 void launch_mdot(Handle& h, const double* V, int nvec, const double* w, int off, cudaStream_t s);

@@ -29,7 +29,7 @@ STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "out of device 
 KRYLOV = {"gmres": 0, "bicgstab": 1}
 PREC = {"none": 0, "bjacobi": 1, "bilu0": 2, "ilu0": 2}
 PRECISION = {"fp64": 0, "mixed": 1}
-K_CLASSES = ("props", "flux", "norm", "gj", "ilu_factor", "spmv", "prec_apply", "blas1", "update")
+K_CLASSES = ("props", "flux", "norm", "gj", "ilu_factor", "spmv", "prec_apply", "blas1", "update", "adjoint")
 
 
 class isc_grid(C.Structure):
@@ -92,7 +92,18 @@ class isc_step_info(C.Structure):
 
 
 class isc_stats(C.Structure):
-    _fields_ = [("ms", C.c_double * 9), ("launches", C.c_int64 * 9), ("calls", C.c_int64 * 9)]
+    _fields_ = [("ms", C.c_double * 10), ("launches", C.c_int64 * 10), ("calls", C.c_int64 * 10)]
+
+
+class isc_adjoint_spec(C.Structure):
+    _fields_ = [("n_steps", C.c_int32), ("dt", c_double_p), ("checkpoint_every", C.c_int32),
+                ("tol_adjoint", C.c_double)]
+
+
+class isc_adjoint_info(C.Structure):
+    _fields_ = [("status", C.c_int32), ("newton_iterations", C.c_int32), ("krylov_iterations_forward", C.c_int32),
+                ("krylov_iterations_adjoint", C.c_int32), ("recomputed_steps", C.c_int32), ("loss", C.c_double),
+                ("adjoint_rel_residual", C.c_double)]
 
 
 _lib = None
@@ -135,7 +146,10 @@ _SIGS = {
                                       C.c_int32, C.c_void_p]),
     "isc_bilu0_apply_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
                                           C.c_void_p, C.c_void_p, C.c_void_p]),
-    "isc_adjoint": (C.c_int, [C.c_void_p]),
+    "isc_set_parameters": (C.c_int, [C.c_void_p, c_double_p, c_double_p, c_double_p]),
+    "isc_get_parameters": (C.c_int, [C.c_void_p, c_double_p, c_double_p, c_double_p]),
+    "isc_adjoint": (C.c_int, [C.c_void_p, C.POINTER(isc_adjoint_spec), c_double_p, c_double_p, c_double_p,
+                              c_double_p, C.POINTER(isc_adjoint_info)]),
 }
 
 
@@ -380,6 +394,44 @@ class Simulator:
 
     def reset_stats(self):
         self._check(self.lib.isc_reset_stats(self.h))
+
+    # -------------------------------------------------------- sensitivities
+    def set_parameters(self, log_k=None, Ea=None, lnA=None):
+        """Per-cell ln k multipliers (N), activation energies E_a (J/mol) and
+        ln A of the reactions (nr); None leaves a group unchanged."""
+        nr = int(self.case.reactions["nr"])
+        lk = None if log_k is None else np.ascontiguousarray(log_k, np.float64).reshape(self.n)
+        ea = None if Ea is None else np.ascontiguousarray(Ea, np.float64).reshape(nr)
+        la = None if lnA is None else np.ascontiguousarray(lnA, np.float64).reshape(nr)
+        self._check(self.lib.isc_set_parameters(self.h, None if lk is None else _dp(lk),
+                                                None if ea is None else _dp(ea), None if la is None else _dp(la)))
+
+    def get_parameters(self):
+        nr = int(self.case.reactions["nr"])
+        lk, ea, la = np.empty(self.n), np.empty(max(nr, 1)), np.empty(max(nr, 1))
+        self._check(self.lib.isc_get_parameters(self.h, _dp(lk), _dp(ea), _dp(la)))
+        return lk, ea[:nr], la[:nr]
+
+    def adjoint(self, dts, checkpoint_every=5, tol_adjoint=0.0, gradient=True):
+        """Run the time loop with the frozen step sizes dts from the current
+        accepted state; return (L, g_log_k, g_Ea, g_lnA, info) with L the
+        cumulative produced oil mass (kg). With gradient=False only L is
+        computed and the gradients are None."""
+        nr = int(self.case.reactions["nr"])
+        d = np.ascontiguousarray(dts, np.float64).reshape(-1)
+        spec = isc_adjoint_spec(len(d), _dp(d), int(checkpoint_every), float(tol_adjoint))
+        info = isc_adjoint_info()
+        L = C.c_double(0.0)
+        if gradient:
+            gk, ge, ga = np.empty(self.n), np.empty(max(nr, 1)), np.empty(max(nr, 1))
+            st = self.lib.isc_adjoint(self.h, C.byref(spec), C.byref(L), _dp(gk), _dp(ge), _dp(ga), C.byref(info))
+        else:
+            st = self.lib.isc_adjoint(self.h, C.byref(spec), C.byref(L), None, None, None, C.byref(info))
+        self._check(st)
+        info_d = {k: getattr(info, k) for k, _ in isc_adjoint_info._fields_}
+        if not gradient:
+            return L.value, None, None, None, info_d
+        return L.value, gk, ge[:nr], ga[:nr], info_d
 
     def set_state_device(self, d_u, d_coke=None):
         self._check(self.lib.isc_set_state_device(self.h, C.c_void_p(d_u), C.c_void_p(d_coke) if d_coke else None))
