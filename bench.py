@@ -5,7 +5,9 @@ One step = the whole hot path on one batch: restore the iterate, property
 evaluation + residual/Jacobian assembly, convergence norms, Gauss-Jordan
 decoupling, block ILU(0) factorisation, GMRES(30) to the relative tolerance,
 safeguarded update. Inputs are resident in HBM for ``value``; ``e2e`` goes
-through the C ABI with host buffers (state in, state out) every step.
+through the C ABI with host buffers (state in, state out) every step. The
+line also carries the same step with the FP32 preconditioner (``mixed``) and
+the discrete adjoint of a 40x40x10 time loop (``adjoint``).
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl isc|reference]
 Under torchrun each rank runs an independent replica (the path has no
@@ -39,6 +41,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="isc", choices=["isc", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the discrete-adjoint measurement")
     ap.add_argument("--grid", default=None,
                     help="NXxNYxNZ: run the same field recipe on a smaller grid (profiling captures)")
     return ap.parse_args()
@@ -255,6 +258,8 @@ def run_isc(args):
         "clocks": clocks,
         "mixed": mixed,
     }
+    if not args.no_adjoint and args.grid is None:
+        line["adjoint"] = adjoint_block()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(max_seconds=30.0)
     g.close()
@@ -262,6 +267,41 @@ def run_isc(args):
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def adjoint_block():
+    """The discrete adjoint on the 40x40x10 workload (20 frozen steps, states
+    checkpointed every 5): wall time of the loss alone and of loss + gradient
+    (forward sweep, recomputation, 20 transposed solves), CUDA-event time of
+    the adjoint kernels."""
+    import isc_inputs as inp
+    from paper_1811_11992_gb300 import isc
+    case = inp.config(4)
+    dts = inp.adjoint_steps(case)
+    g = isc.Simulator(case, tol_newton=1e-9, tol_lin=1e-6, maxit_newton=40, maxit_lin=3000, profile=1)
+    g.init_equilibrium()
+    g.adjoint(dts, checkpoint_every=5, tol_adjoint=1e-10)      # warm-up (allocates the checkpoint store)
+    g.init_equilibrium()
+    t0 = time.perf_counter()
+    L_only = g.adjoint(dts, checkpoint_every=5, gradient=False)[0]
+    t_fwd = time.perf_counter() - t0
+    g.init_equilibrium()
+    g.reset_stats()
+    t0 = time.perf_counter()
+    L, gk, ge, ga, info = g.adjoint(dts, checkpoint_every=5, tol_adjoint=1e-10)
+    t_grad = time.perf_counter() - t0
+    st = g.stats()
+    g.close()
+    return {"workload": f"adjoint {case.nx}x{case.ny}x{case.nz} ({case.n} cells), {len(dts)} frozen steps "
+                        f"({sum(dts) / inp.DAY:.1f} d), checkpoints every 5, gradient w.r.t. {case.n} ln k + "
+                        f"{2 * int(case.reactions['nr'])} reaction parameters",
+            "loss_kg": L, "loss_only_s": t_fwd, "loss_and_gradient_s": t_grad,
+            "gradient_cost_ratio": t_grad / t_fwd, "same_loss": L == L_only,
+            "newton_iterations": info["newton_iterations"], "recomputed_steps": info["recomputed_steps"],
+            "krylov_iterations_forward": info["krylov_iterations_forward"],
+            "krylov_iterations_adjoint": info["krylov_iterations_adjoint"],
+            "adjoint_rel_residual": info["adjoint_rel_residual"],
+            "kernel_ms": {k: round(v["ms"], 3) for k, v in st.items()}}
 
 
 def measured_peaks():
