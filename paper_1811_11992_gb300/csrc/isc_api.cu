@@ -1086,8 +1086,7 @@ int isc_precond_apply(isc_handle* h, const double* r, double* z) {
   CUDA_TRY(h, cudaMemcpyAsync(h->w, r, sizeof(double) * len, cudaMemcpyHostToDevice, h->stream));
   prec(h, h->w, h->V);
   CUDA_TRY(h, cudaMemcpyAsync(z, h->V, sizeof(double) * len, cudaMemcpyDeviceToHost, h->stream));
-  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-  return ISC_OK;
+  return check_device_status(h);  // synchronises; reports a sweep whose bounded wait gave up
 }
 
 int isc_get_stats(isc_handle* h, isc_stats* st) {
