@@ -14,6 +14,10 @@ linalg  Gauss-Jordan decoupling with partial pivoting (Sec. 3.2), textbook block
 sim     the Newton linearise-decouple-solve-update step with the paper's
         saturation safeguard (Sec. 2.2, "Phase Equilibrium"), the time step loop
         and the initial-state recipe.
+cpr     the CPR-PF two-stage preconditioner (Sec. 4, Example 2): aggregation
+        multigrid on the decoupled pressure matrix, then block ILU(0).
+adjoint the tangent-linear model of the time loop's cumulative oil production
+        (sensitivities; not in the paper).
 
 Parity status: every function is pinned by ``tests/test_oracle_*.py`` against
 values printed in the paper, closed forms, invariants or library routines,
