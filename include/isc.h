@@ -60,7 +60,13 @@ enum isc_status {
 };
 
 enum isc_krylov { ISC_KRYLOV_GMRES = 0, ISC_KRYLOV_BICGSTAB = 1 };
-enum isc_prec { ISC_PREC_NONE = 0, ISC_PREC_BJACOBI = 1, ISC_PREC_BILU0 = 2 };
+/* ISC_PREC_CPR is the two-stage CPR-PF preconditioner of Sec. 4 (Example 2):
+ * on the decoupled system, one V-cycle of an aggregation multigrid on the
+ * pressure matrix (the (0,0) entry of every block: 2x2 x-y aggregates with
+ * Galerkin coarse operators, red-black z-line Gauss-Seidel, one pre- and one
+ * post-smoothing sweep), then block ILU(0) on the remaining residual; the
+ * ILU(0) stage follows options.precision. It expects options.decouple = 1. */
+enum isc_prec { ISC_PREC_NONE = 0, ISC_PREC_BJACOBI = 1, ISC_PREC_BILU0 = 2, ISC_PREC_CPR = 3 };
 /* Precision of the preconditioner: FP64 throughout, or mixed: the block
  * ILU(0) factors are computed in FP64, stored and applied in FP32 inside the
  * FP64 flexible GMRES (residual, SpMV, orthogonalisation and update stay FP64). */
@@ -187,7 +193,8 @@ typedef struct isc_step_info {
 enum isc_kernel_class {
   ISC_K_PROPS = 0, ISC_K_FLUX = 1, ISC_K_NORM = 2, ISC_K_GJ = 3, ISC_K_ILU_FACTOR = 4,
   ISC_K_SPMV = 5, ISC_K_PREC_APPLY = 6, ISC_K_BLAS1 = 7, ISC_K_UPDATE = 8, ISC_K_ADJOINT = 9,
-  ISC_K_COUNT = 10
+  ISC_K_CPR = 10,   /* CPR pressure stage: extraction and coarsening, V-cycle, second-stage residual */
+  ISC_K_COUNT = 11
 };
 typedef struct isc_stats {
   double ms[ISC_K_COUNT];

@@ -16,7 +16,7 @@ preconditioners; the paper gives no further detail of it. Readings taken here:
   M_p^-1 one multigrid V-cycle on A_p from a zero guess, M^-1 the block ILU(0)
   preconditioner of the whole system.
 * Pressure multigrid (the platform's pressure solver is not described): x-y
-  aggregation of 2 x 2 cells (piecewise-constant prolongation P, restriction
+  aggregation of agg x agg cells, agg = 2 (piecewise-constant prolongation P, restriction
   P^T, Galerkin coarse operator P^T A P), z not coarsened, repeated until one
   column remains; smoothing by red-black z-line Gauss-Seidel (columns coloured
   by (x + y) mod 2, colour 0 first; each column's z-tridiagonal system is
@@ -40,23 +40,23 @@ def pressure_matrix(rowptr, col, val):
     return sp.csr_matrix((val[:, 0, 0], (rows, col)), shape=(n, n))
 
 
-def aggregation_1d(m):
+def aggregation_1d(m, agg=2):
     """Piecewise-constant prolongation of one direction: fine cell x belongs to
-    aggregate x // 2 (a trailing odd cell forms an aggregate of one)."""
-    mc = (m + 1) // 2
-    return sp.csr_matrix((np.ones(m), (np.arange(m), np.arange(m) // 2)), shape=(m, mc)), mc
+    aggregate x // agg (the trailing aggregate may hold fewer cells)."""
+    mc = (m + agg - 1) // agg
+    return sp.csr_matrix((np.ones(m), (np.arange(m), np.arange(m) // agg)), shape=(m, mc)), mc
 
 
 class AggregationMG:
     """Levels (A_l, dims_l) with P_l from level l to l + 1; cell index
     x + nx (y + ny z) on every level."""
 
-    def __init__(self, A, nx, ny, nz, nu1=1, nu2=1):
+    def __init__(self, A, nx, ny, nz, nu1=1, nu2=1, agg=2):
         self.nu1, self.nu2 = nu1, nu2
         self.A, self.P, self.dims = [A.tocsr()], [], [(nx, ny, nz)]
         while nx > 1 or ny > 1:
-            Px, cx = aggregation_1d(nx)
-            Py, cy = aggregation_1d(ny)
+            Px, cx = aggregation_1d(nx, agg)
+            Py, cy = aggregation_1d(ny, agg)
             P = sp.kron(sp.identity(nz), sp.kron(Py, Px)).tocsr()
             self.P.append(P)
             self.A.append((P.T @ self.A[-1] @ P).tocsr())
@@ -105,10 +105,10 @@ class AggregationMG:
 class CPRPreconditioner:
     """z = E M_p^-1 r_p + M^-1 (r - A E M_p^-1 r_p) on the decoupled system."""
 
-    def __init__(self, rowptr, col, val, nx, ny, nz, nu1=1, nu2=1, second=None):
+    def __init__(self, rowptr, col, val, nx, ny, nz, nu1=1, nu2=1, second=None, agg=2):
         self.n = len(rowptr) - 1
         self.A = linalg.bsr_to_scipy(rowptr, col, val)
-        self.mg = AggregationMG(pressure_matrix(rowptr, col, val), nx, ny, nz, nu1, nu2)
+        self.mg = AggregationMG(pressure_matrix(rowptr, col, val), nx, ny, nz, nu1, nu2, agg)
         self.second = second if second is not None else linalg.ILU0Preconditioner(rowptr, col, val)
 
     def apply(self, r):

@@ -119,6 +119,7 @@ void free_all(isc_handle* h) {
                   h->adj.scond, h->adj.kd, h->adj.loss_cell, h->adj.sums, h->adj.inj_first, h->adj.inj_count};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  cpr_free(*h);
   if (h->h_scal) cudaFreeHost(h->h_scal);
   if (h->h_status) cudaFreeHost(h->h_status);
   for (auto& r : h->recs) {
@@ -141,13 +142,34 @@ void spmv(isc_handle* h, const double* x, double* y) {
 }
 
 void prec(isc_handle* h, const double* r, double* z) {
+  if (h->opt.prec == ISC_PREC_CPR) {
+    {
+      Region rg(h, ISC_K_CPR, cpr_pressure_launches(*h));
+      launch_cpr_pressure(*h, r, h->stream);
+    }
+    {
+      Region rg(h, ISC_K_PREC_APPLY, 2);
+      launch_ilu_apply_pipe(*h, h->cpr.r1, z, h->stream);
+    }
+    Region rg(h, ISC_K_CPR, 1);
+    launch_cpr_finish(*h, z, h->stream);
+    return;
+  }
   int launches = h->opt.prec == ISC_PREC_BILU0 ? 2 : 1;
   Region rg(h, ISC_K_PREC_APPLY, launches);
   launch_prec_apply(*h, r, z, h->stream);
 }
 
 int build_prec(isc_handle* h) {
-  if (h->opt.prec == ISC_PREC_BILU0) {
+  if (h->opt.prec == ISC_PREC_CPR) {
+    if (h->cpr.nlev == 0) {
+      int st = cpr_setup_levels(*h);
+      if (st) return set_err(h, st, "CPR multigrid workspace");
+    }
+    Region rg(h, ISC_K_CPR, h->cpr.nlev);
+    launch_cpr_setup(*h, h->stream);
+  }
+  if (h->opt.prec == ISC_PREC_BILU0 || h->opt.prec == ISC_PREC_CPR) {
     const bool mixed = h->opt.precision == ISC_PRECISION_MIXED;
     if (mixed && !h->J32) {
       // first mixed-precision use: FP32 copies of the blocks and D^-1, two FP32 sweep vectors
@@ -437,7 +459,7 @@ int validate_options(isc_handle* h, const isc_options& o) {
   if (o.restart < 1 || o.restart > MAX_RESTART) return set_err(h, ISC_ERR_INVALID_ARG, "restart must be 1..64");
   if (o.krylov != ISC_KRYLOV_GMRES && o.krylov != ISC_KRYLOV_BICGSTAB)
     return set_err(h, ISC_ERR_INVALID_ARG, "unknown krylov method");
-  if (o.prec < ISC_PREC_NONE || o.prec > ISC_PREC_BILU0) return set_err(h, ISC_ERR_INVALID_ARG, "unknown preconditioner");
+  if (o.prec < ISC_PREC_NONE || o.prec > ISC_PREC_CPR) return set_err(h, ISC_ERR_INVALID_ARG, "unknown preconditioner");
   if (o.precision != ISC_PRECISION_FP64 && o.precision != ISC_PRECISION_MIXED)
     return set_err(h, ISC_ERR_INVALID_ARG, "unknown precision");
   if (!(o.tol_lin > 0.0) || o.maxit_lin < 1 || !(o.tol_newton >= 0.0) || o.maxit_newton < 1)

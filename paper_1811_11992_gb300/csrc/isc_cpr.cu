@@ -1,0 +1,429 @@
+// CPR-PF two-stage preconditioner (Sec. 4, Example 2: the solver's
+// preconditioner changes from RAS to CPR-PF). On the Gauss-Jordan-decoupled
+// system (unit diagonal blocks, Sec. 3.2) row 0 of a block row is the equation
+// paired with the cell's pressure; the pressure matrix A_p is the (0,0) entry
+// of every block. One application:
+//   p  = one V-cycle of A_p p = r_p (r_p the pressure rows of r, zero guess)
+//   r1 = r - A E p            (E injects p into unknown 0 of every cell)
+//   z  = ILU(0)^-1 r1 + E p
+// Pressure multigrid: MG_AGG x MG_AGG x-y aggregates (piecewise-constant
+// prolongation, Galerkin coarse operators, which keep the 7-point structure),
+// z not coarsened, down to a single column; red-black z-line Gauss-Seidel
+// (columns coloured by (x + y) mod 2, colour 0 first, each column's
+// tridiagonal system solved exactly); one pre- and one post-smoothing sweep;
+// exact column solve on the coarsest level.
+//
+// The tridiagonal factors of every column (1/pivot and upper/pivot of the
+// Thomas elimination) are computed once per setup, so an application does no
+// division: on GB300 a warp-wide FP64 division costs tens of FP64 issue
+// slots. The level arrays are FP64, or FP32 when the preconditioner runs in
+// mixed precision (the second-stage residual stays FP64).
+//
+// Kernels: k_cpr_extract (A_p stencil and the unknown-0 column of every
+// block), k_mg_coarsen (Galerkin sums over an aggregate), k_mg_factor (column
+// factors), k_zline (one thread per column of a colour), k_mg_restrict,
+// k_mg_prolong, k_mg_coarse (the levels of at most MG_BLOCK_CELLS cells in
+// one thread block with barriers), k_cpr_gather, k_cpr_residual, k_cpr_add.
+#include "isc_internal.cuh"
+
+namespace isc {
+
+namespace {
+
+// stencil directions: 0 -z, 1 -y, 2 -x, 3 diagonal, 4 +x, 5 +y, 6 +z
+template <typename T>
+__device__ __forceinline__ int nb_index(const MGLevel<T>& L, int i, int d) {
+  const int nxy = L.nx * L.ny;
+  switch (d) {
+    case 0: return i - nxy;
+    case 1: return i - L.nx;
+    case 2: return i - 1;
+    case 4: return i + 1;
+    case 5: return i + L.nx;
+    case 6: return i + nxy;
+    default: return i;
+  }
+}
+
+// A_p stencil and the unknown-0 column of every block, from the decoupled J
+template <typename T>
+__global__ void k_cpr_extract(int nx, int ny, int nz, const int32_t* __restrict__ rowptr,
+                              const double* __restrict__ J, T* __restrict__ c, double* __restrict__ col0) {
+  const int n = nx * ny * nz;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int nxy = nx * ny;
+  double cd[7] = {0, 0, 0, 0, 0, 0, 0};
+  // the row holds the existing neighbours in the order -z, -y, -x, diagonal, +x, +y, +z
+  const int x = i % nx, y = (i / nx) % ny, z = i / nxy;
+  const bool has[7] = {z > 0, y > 0, x > 0, true, x < nx - 1, y < ny - 1, z < nz - 1};
+  int b = rowptr[i];
+  for (int d = 0; d < 7; ++d) {
+    if (!has[d]) continue;
+    const double* B = J + (size_t)b * BB;
+    cd[d] = B[0];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) col0[(size_t)b * 8 + r] = B[r * 8];
+    ++b;
+  }
+#pragma unroll
+  for (int d = 0; d < 7; ++d) c[(size_t)d * n + i] = (T)cd[d];
+}
+
+// Galerkin coarse operator of the x-y aggregation: sums of the fine entries
+template <typename T>
+__device__ __forceinline__ void coarsen_cell(const MGLevel<T>& F, const MGLevel<T>& C, int I) {
+  const int X = I % C.nx, Y = (I / C.nx) % C.ny, k = I / (C.nx * C.ny);
+  const int x0 = MG_AGG * X, y0 = MG_AGG * Y;
+  T cd[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (int fy = y0; fy < y0 + MG_AGG && fy < F.ny; ++fy) {
+    for (int fx = x0; fx < x0 + MG_AGG && fx < F.nx; ++fx) {
+      const int f = fx + F.nx * (fy + F.ny * k);
+      cd[0] += F.c[(size_t)0 * F.n + f];
+      cd[6] += F.c[(size_t)6 * F.n + f];
+      cd[3] += F.c[(size_t)3 * F.n + f];
+      // x and y couplings stay inside the aggregate (diagonal) or cross to a neighbour aggregate
+      cd[(fx - 1 >= x0) ? 3 : 2] += F.c[(size_t)2 * F.n + f];
+      cd[(fx + 1 < x0 + MG_AGG) ? 3 : 4] += F.c[(size_t)4 * F.n + f];
+      cd[(fy - 1 >= y0) ? 3 : 1] += F.c[(size_t)1 * F.n + f];
+      cd[(fy + 1 < y0 + MG_AGG) ? 3 : 5] += F.c[(size_t)5 * F.n + f];
+    }
+  }
+#pragma unroll
+  for (int d = 0; d < 7; ++d) C.c[(size_t)d * C.n + I] = cd[d];
+}
+
+// Thomas factors of column (cx, cy): e_k = 1 / (b_k - a_k f_{k-1}), f_k = c_k e_k
+template <typename T>
+__device__ __forceinline__ void factor_column(const MGLevel<T>& L, int cx, int cy) {
+  const int nxy = L.nx * L.ny, n = L.n;
+  T fp = 0;
+  for (int k = 0; k < L.nz; ++k) {
+    const int i = cx + L.nx * cy + nxy * k;
+    const T lo = (k > 0) ? L.c[(size_t)0 * n + i] : T(0);
+    const T e = T(1) / (L.c[(size_t)3 * n + i] - lo * fp);
+    fp = (k < L.nz - 1) ? L.c[(size_t)6 * n + i] * e : T(0);
+    L.e[i] = e;
+    L.f[i] = fp;
+  }
+}
+
+// Solve column (cx, cy)'s z-tridiagonal system with the other columns' current
+// values (zero_guess: the other columns are zero).
+template <typename T>
+__device__ __forceinline__ void zline_column(const MGLevel<T>& L, int cx, int cy, bool zero_guess) {
+  const int nxy = L.nx * L.ny, n = L.n;
+  const T* __restrict__ c = L.c;
+  T* __restrict__ x = L.x;
+  const int i0 = cx + L.nx * cy;
+  T bp = 0;
+#pragma unroll 4
+  for (int k = 0; k < L.nz; ++k) {
+    const int i = i0 + nxy * k;
+    T rhs = L.b[i];
+    if (!zero_guess) {
+      if (cy > 0) rhs -= c[(size_t)1 * n + i] * x[i - L.nx];
+      if (cx > 0) rhs -= c[(size_t)2 * n + i] * x[i - 1];
+      if (cx < L.nx - 1) rhs -= c[(size_t)4 * n + i] * x[i + 1];
+      if (cy < L.ny - 1) rhs -= c[(size_t)5 * n + i] * x[i + L.nx];
+    }
+    const T lo = (k > 0) ? c[(size_t)0 * n + i] : T(0);
+    bp = (rhs - lo * bp) * L.e[i];
+    x[i] = bp;
+  }
+#pragma unroll 4
+  for (int k = L.nz - 2; k >= 0; --k) {
+    const int i = i0 + nxy * k;
+    bp = x[i] - L.f[i] * bp;
+    x[i] = bp;
+  }
+}
+
+// b_C = sum over the aggregate of (b_F - A_F x_F)
+template <typename T>
+__device__ __forceinline__ void restrict_cell(const MGLevel<T>& F, const MGLevel<T>& C, int I) {
+  const int X = I % C.nx, Y = (I / C.nx) % C.ny, k = I / (C.nx * C.ny);
+  const int x0 = MG_AGG * X, y0 = MG_AGG * Y;
+  T s = 0;
+  for (int fy = y0; fy < y0 + MG_AGG && fy < F.ny; ++fy) {
+    for (int fx = x0; fx < x0 + MG_AGG && fx < F.nx; ++fx) {
+      const int f = fx + F.nx * (fy + F.ny * k);
+      T r = F.b[f];
+      const bool has[7] = {k > 0, fy > 0, fx > 0, true, fx < F.nx - 1, fy < F.ny - 1, k < F.nz - 1};
+#pragma unroll
+      for (int d = 0; d < 7; ++d)
+        if (has[d]) r -= F.c[(size_t)d * F.n + f] * F.x[nb_index(F, f, d)];
+      s += r;
+    }
+  }
+  C.b[I] = s;
+}
+
+template <typename T>
+__device__ __forceinline__ void prolong_cell(const MGLevel<T>& C, const MGLevel<T>& F, int f) {
+  const int fx = f % F.nx, fy = (f / F.nx) % F.ny, k = f / (F.nx * F.ny);
+  F.x[f] += C.x[(fx / MG_AGG) + C.nx * ((fy / MG_AGG) + C.ny * k)];
+}
+
+// column q of colour `colour` (columns with (cx + cy) % 2 == colour, row-major): its (cx, cy)
+__device__ __forceinline__ bool colour_column(int nx, int ny, int colour, int q, int* cx, int* cy) {
+  const int per_row0 = (nx + 1) / 2, per_row1 = nx / 2;  // colour-(row parity) columns in a row
+  // rows alternate which parity comes first; count row by row
+  const int pair = per_row0 + per_row1;                    // columns of one colour in two rows
+  const int r2 = q / pair, rem = q % pair;
+  int row, idx;
+  const int first = (colour == 0) ? per_row0 : per_row1;   // this colour's count in an even row
+  if (rem < first) {
+    row = 2 * r2;
+    idx = rem;
+  } else {
+    row = 2 * r2 + 1;
+    idx = rem - first;
+  }
+  if (row >= ny) return false;
+  // in row `row` the columns of this colour have x parity (colour + row) & 1
+  const int x = 2 * idx + ((colour + row) & 1);
+  if (x >= nx) return false;
+  *cx = x;
+  *cy = row;
+  return true;
+}
+
+__host__ __device__ __forceinline__ int colour_count(int nx, int ny, int colour) {
+  // columns (x, y) with (x + y) % 2 == colour
+  const int even = ((nx * ny) + 1) / 2;
+  return colour == 0 ? even : nx * ny - even;
+}
+
+template <typename T>
+__global__ void k_mg_coarsen(const MGLevel<T>* __restrict__ lv, int l) {
+  const MGLevel<T> F = lv[l], C = lv[l + 1];
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I < C.n) coarsen_cell(F, C, I);
+}
+
+template <typename T>
+__global__ void k_mg_factor(const MGLevel<T>* __restrict__ lv, int l) {
+  const MGLevel<T> L = lv[l];
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < L.nx * L.ny) factor_column(L, t % L.nx, t / L.nx);
+}
+
+template <typename T>
+__global__ void k_zline(const MGLevel<T>* __restrict__ lv, int l, int colour, int zero_guess) {
+  const MGLevel<T> L = lv[l];
+  int cx, cy;
+  if (colour_column(L.nx, L.ny, colour, blockIdx.x * blockDim.x + threadIdx.x, &cx, &cy))
+    zline_column(L, cx, cy, zero_guess != 0);
+}
+
+template <typename T>
+__global__ void k_mg_restrict(const MGLevel<T>* __restrict__ lv, int l) {
+  const MGLevel<T> F = lv[l], C = lv[l + 1];
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I < C.n) restrict_cell(F, C, I);
+}
+
+template <typename T>
+__global__ void k_mg_prolong(const MGLevel<T>* __restrict__ lv, int l) {
+  const MGLevel<T> C = lv[l + 1], F = lv[l];
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f < F.n) prolong_cell(C, F, f);
+}
+
+template <typename T>
+__device__ __forceinline__ void block_smooth(const MGLevel<T>& L, bool zero_guess) {
+  for (int colour = 0; colour < 2; ++colour) {
+    const int cnt = colour_count(L.nx, L.ny, colour);
+    for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+      int cx, cy;
+      if (colour_column(L.nx, L.ny, colour, q, &cx, &cy)) zline_column(L, cx, cy, zero_guess && colour == 0);
+    }
+    __syncthreads();
+  }
+}
+
+// Levels l0 .. nlev-1 of the V-cycle in one thread block (b of level l0 is set).
+template <typename T>
+__global__ void __launch_bounds__(1024) k_mg_coarse(const MGLevel<T>* __restrict__ lv, int l0, int nlev) {
+  const int t = threadIdx.x, TT = blockDim.x;
+  for (int l = l0; l < nlev - 1; ++l) {
+    const MGLevel<T> L = lv[l], C = lv[l + 1];
+    block_smooth(L, true);
+    for (int I = t; I < C.n; I += TT) restrict_cell(L, C, I);
+    __syncthreads();
+  }
+  {
+    const MGLevel<T> L = lv[nlev - 1];
+    for (int q = t; q < L.nx * L.ny; q += TT) zline_column(L, q % L.nx, q / L.nx, true);
+    __syncthreads();
+  }
+  for (int l = nlev - 2; l >= l0; --l) {
+    const MGLevel<T> L = lv[l], C = lv[l + 1];
+    for (int f = t; f < L.n; f += TT) prolong_cell(C, L, f);
+    __syncthreads();
+    block_smooth(L, false);
+  }
+}
+
+template <typename T>
+__global__ void k_cpr_gather(int n, const double* __restrict__ r, T* __restrict__ b) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (T)r[(size_t)i * 8];
+}
+
+// r1 = r - A E p: thread (i, row) sums the unknown-0 column entries of row i's blocks
+template <typename T>
+__global__ void k_cpr_residual(int n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                               const double* __restrict__ col0, const double* __restrict__ r, const T* __restrict__ p,
+                               double* __restrict__ r1) {
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (size_t)n * 8) return;
+  const int i = (int)(e >> 3), row = (int)(e & 7);
+  double s = r[e];
+  for (int b = rowptr[i]; b < rowptr[i + 1]; ++b) s -= col0[(size_t)b * 8 + row] * (double)p[col[b]];
+  r1[e] = s;
+}
+
+template <typename T>
+__global__ void k_cpr_add(int n, const T* __restrict__ p, double* __restrict__ z) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) z[(size_t)i * 8] += (double)p[i];
+}
+
+inline int nblk(long long n, int tb) { return (int)((n + tb - 1) / tb); }
+
+template <typename T>
+std::vector<MGLevel<T>>& table(CprWork& W);
+template <>
+std::vector<MGLevel<double>>& table<double>(CprWork& W) {
+  return W.h64;
+}
+template <>
+std::vector<MGLevel<float>>& table<float>(CprWork& W) {
+  return W.h32;
+}
+
+template <typename T>
+int setup_levels_t(Handle& h) {
+  CprWork& W = h.cpr;
+  std::vector<MGLevel<T>> lv;
+  int nx = h.nx, ny = h.ny, nz = h.nz;
+  for (;;) {
+    MGLevel<T> L{};
+    L.nx = nx;
+    L.ny = ny;
+    L.nz = nz;
+    L.n = nx * ny * nz;
+    lv.push_back(L);
+    if (nx == 1 && ny == 1) break;
+    nx = (nx + MG_AGG - 1) / MG_AGG;
+    ny = (ny + MG_AGG - 1) / MG_AGG;
+  }
+  size_t total = 0;
+  for (auto& L : lv) total += (size_t)L.n * 11;
+  if (cudaMalloc(&W.pool, sizeof(T) * total) != cudaSuccess) return ISC_ERR_NOMEM;
+  T* q = static_cast<T*>(W.pool);
+  for (auto& L : lv) {
+    L.c = q;
+    q += (size_t)7 * L.n;
+    L.x = q;
+    q += L.n;
+    L.b = q;
+    q += L.n;
+    L.e = q;
+    q += L.n;
+    L.f = q;
+    q += L.n;
+  }
+  if (cudaMalloc(&W.d_levels, sizeof(MGLevel<T>) * lv.size()) != cudaSuccess) return ISC_ERR_NOMEM;
+  if (cudaMemcpy(W.d_levels, lv.data(), sizeof(MGLevel<T>) * lv.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    return ISC_ERR_CUDA;
+  W.nlev = (int)lv.size();
+  W.ngrid = 0;
+  while (W.ngrid < W.nlev - 1 && lv[W.ngrid].n > MG_BLOCK_CELLS) ++W.ngrid;
+  table<T>(W) = lv;
+  return ISC_OK;
+}
+
+template <typename T>
+void setup_t(Handle& h, cudaStream_t s) {
+  CprWork& W = h.cpr;
+  const auto& lv = table<T>(W);
+  const MGLevel<T>* d = static_cast<const MGLevel<T>*>(W.d_levels);
+  const int tb = 128;
+  k_cpr_extract<T><<<nblk(h.n, tb), tb, 0, s>>>(h.nx, h.ny, h.nz, h.rowptr, h.J, lv[0].c, W.col0);
+  for (int l = 0; l + 1 < W.nlev; ++l) k_mg_coarsen<T><<<nblk(lv[l + 1].n, tb), tb, 0, s>>>(d, l);
+  for (int l = 0; l < W.nlev; ++l) k_mg_factor<T><<<nblk(lv[l].nx * lv[l].ny, tb), tb, 0, s>>>(d, l);
+}
+
+template <typename T>
+void pressure_t(Handle& h, const double* r, cudaStream_t s) {
+  CprWork& W = h.cpr;
+  const auto& lv = table<T>(W);
+  const MGLevel<T>* d = static_cast<const MGLevel<T>*>(W.d_levels);
+  const int tb = 128;
+  k_cpr_gather<T><<<nblk(h.n, tb), tb, 0, s>>>(h.n, r, lv[0].b);
+  for (int l = 0; l < W.ngrid; ++l) {
+    k_zline<T><<<nblk(colour_count(lv[l].nx, lv[l].ny, 0), tb), tb, 0, s>>>(d, l, 0, 1);
+    k_zline<T><<<nblk(colour_count(lv[l].nx, lv[l].ny, 1), tb), tb, 0, s>>>(d, l, 1, 0);
+    k_mg_restrict<T><<<nblk(lv[l + 1].n, tb), tb, 0, s>>>(d, l);
+  }
+  k_mg_coarse<T><<<1, 1024, 0, s>>>(d, W.ngrid, W.nlev);
+  for (int l = W.ngrid - 1; l >= 0; --l) {
+    k_mg_prolong<T><<<nblk(lv[l].n, tb), tb, 0, s>>>(d, l);
+    k_zline<T><<<nblk(colour_count(lv[l].nx, lv[l].ny, 0), tb), tb, 0, s>>>(d, l, 0, 0);
+    k_zline<T><<<nblk(colour_count(lv[l].nx, lv[l].ny, 1), tb), tb, 0, s>>>(d, l, 1, 0);
+  }
+  k_cpr_residual<T><<<nblk((long long)h.n * 8, 256), 256, 0, s>>>(h.n, h.rowptr, h.col, W.col0, r, lv[0].x, W.r1);
+}
+
+}  // namespace
+
+int cpr_setup_levels(Handle& h) {
+  CprWork& W = h.cpr;
+  const bool fp32 = h.opt.precision == ISC_PRECISION_MIXED;
+  if (W.nlev > 0 && W.fp32 == fp32) return ISC_OK;
+  cpr_free(h);
+  W.fp32 = fp32;
+  if (cudaMalloc((void**)&W.col0, sizeof(double) * (size_t)h.nnzb * 8) != cudaSuccess) return ISC_ERR_NOMEM;
+  if (cudaMalloc((void**)&W.r1, sizeof(double) * (size_t)h.n * 8) != cudaSuccess) return ISC_ERR_NOMEM;
+  return fp32 ? setup_levels_t<float>(h) : setup_levels_t<double>(h);
+}
+
+void launch_cpr_setup(Handle& h, cudaStream_t s) {
+  if (h.cpr.fp32)
+    setup_t<float>(h, s);
+  else
+    setup_t<double>(h, s);
+}
+
+// first stage and the second stage's right-hand side: p (level 0's x) and r1 = r - A E p
+void launch_cpr_pressure(Handle& h, const double* r, cudaStream_t s) {
+  if (h.cpr.fp32)
+    pressure_t<float>(h, r, s);
+  else
+    pressure_t<double>(h, r, s);
+}
+
+// z += E p after the second stage wrote z = ILU^-1 r1
+void launch_cpr_finish(Handle& h, double* z, cudaStream_t s) {
+  const int tb = 128;
+  if (h.cpr.fp32)
+    k_cpr_add<float><<<nblk(h.n, tb), tb, 0, s>>>(h.n, h.cpr.h32[0].x, z);
+  else
+    k_cpr_add<double><<<nblk(h.n, tb), tb, 0, s>>>(h.n, h.cpr.h64[0].x, z);
+}
+
+int cpr_pressure_launches(const Handle& h) { return 1 + 6 * h.cpr.ngrid + 1 + 1; }
+
+void cpr_free(Handle& h) {
+  CprWork& W = h.cpr;
+  if (W.pool) cudaFree(W.pool);
+  if (W.d_levels) cudaFree(W.d_levels);
+  if (W.col0) cudaFree(W.col0);
+  if (W.r1) cudaFree(W.r1);
+  W = CprWork{};
+}
+
+}  // namespace isc

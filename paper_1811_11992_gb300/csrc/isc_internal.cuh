@@ -100,6 +100,31 @@ struct AdjointWork {
   int n_inj = 0;
 };
 
+// One level of the CPR pressure multigrid: a 7-point stencil on nx*ny*nz
+// cells (coefficients SoA c[d*n + i], d = -z, -y, -x, diagonal, +x, +y, +z,
+// cell index x + nx (y + ny z)), iterate, right-hand side and the factors of
+// every column's z-tridiagonal system (e = 1/pivot, f = upper / pivot).
+// T is double, or float when the preconditioner runs in mixed precision.
+template <typename T>
+struct MGLevel {
+  int nx, ny, nz, n;
+  T *c, *x, *b, *e, *f;
+};
+constexpr int MG_AGG = 2;             // x-y aggregation factor (MG_AGG x MG_AGG fine columns per coarse column)
+constexpr int MG_BLOCK_CELLS = 8192;  // levels this small run inside one thread block
+
+// Workspace of the CPR-PF preconditioner (allocated on first use, for one precision).
+struct CprWork {
+  std::vector<MGLevel<double>> h64;   // level tables (the one of the current precision is set)
+  std::vector<MGLevel<float>> h32;
+  void* d_levels = nullptr;           // device copy of the current table
+  void* pool = nullptr;               // every level's arrays
+  double* col0 = nullptr;             // unknown-0 column of every block, nnzb x 8
+  double* r1 = nullptr;               // right-hand side of the second stage, block-major 8N
+  int nlev = 0, ngrid = 0;            // levels; levels done by grid-wide kernels
+  bool fp32 = false;                  // precision of the level arrays
+};
+
 // device status word bits
 enum DevStatus { DS_SINGULAR = 1, DS_COKE = 2, DS_NONFINITE = 4, DS_TIMEOUT = 8 };
 
@@ -131,6 +156,7 @@ struct Handle {
   double face_area[3] = {0, 0, 0};                 // A/h of x, y, z faces
   double h_Ea[ISC_MAX_RXN] = {}, h_lnA[ISC_MAX_RXN] = {};  // current reaction parameters
   AdjointWork adj;
+  CprWork cpr;
   // device: state
   double *u = nullptr, *coke = nullptr;          // iterate (SoA 8N), solved coke (N)
   double *u_n = nullptr, *coke_n = nullptr;       // accepted state
@@ -187,6 +213,13 @@ void launch_prec_apply(Handle& h, const double* r, double* z, cudaStream_t s);
 void launch_ilu_apply_pipe(Handle& h, const double* r, double* z, cudaStream_t s);
 void launch_ilu_factor_pipe(Handle& h, cudaStream_t s);
 void launch_update(Handle& h, cudaStream_t s);
+// CPR-PF preconditioner (isc_cpr.cu)
+int cpr_setup_levels(Handle& h);
+void launch_cpr_setup(Handle& h, cudaStream_t s);
+void launch_cpr_pressure(Handle& h, const double* r, cudaStream_t s);
+void launch_cpr_finish(Handle& h, double* z, cudaStream_t s);
+int cpr_pressure_launches(const Handle& h);
+void cpr_free(Handle& h);
 // discrete adjoint (isc_adjoint.cu)
 void launch_oil_rate(Handle& h, double dt, cudaStream_t s);
 void launch_adj_pre(Handle& h, double dt, cudaStream_t s);

@@ -27,9 +27,10 @@ STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "out of device 
           -6: "Newton did not converge", -7: "non-finite value", -8: "coke equation did not converge",
           -9: "device wait timed out", -10: "not implemented", -11: "call order violated"}
 KRYLOV = {"gmres": 0, "bicgstab": 1}
-PREC = {"none": 0, "bjacobi": 1, "bilu0": 2, "ilu0": 2}
+PREC = {"none": 0, "bjacobi": 1, "bilu0": 2, "ilu0": 2, "cpr": 3}
 PRECISION = {"fp64": 0, "mixed": 1}
-K_CLASSES = ("props", "flux", "norm", "gj", "ilu_factor", "spmv", "prec_apply", "blas1", "update", "adjoint")
+K_CLASSES = ("props", "flux", "norm", "gj", "ilu_factor", "spmv", "prec_apply", "blas1", "update", "adjoint",
+             "cpr")
 
 
 class isc_grid(C.Structure):
@@ -92,7 +93,7 @@ class isc_step_info(C.Structure):
 
 
 class isc_stats(C.Structure):
-    _fields_ = [("ms", C.c_double * 10), ("launches", C.c_int64 * 10), ("calls", C.c_int64 * 10)]
+    _fields_ = [("ms", C.c_double * 11), ("launches", C.c_int64 * 11), ("calls", C.c_int64 * 11)]
 
 
 class isc_adjoint_spec(C.Structure):
