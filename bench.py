@@ -7,7 +7,8 @@ decoupling, block ILU(0) factorisation, GMRES(30) to the relative tolerance,
 safeguarded update. Inputs are resident in HBM for ``value``; ``e2e`` goes
 through the C ABI with host buffers (state in, state out) every step. The
 line also carries the same step with the FP32 preconditioner (``mixed``) and
-the discrete adjoint of a 40x40x10 time loop (``adjoint``).
+the discrete adjoint of a 40x40x10 time loop (``adjoint``) and the step with
+the CPR-PF preconditioner (``cpr``, FP64 and mixed).
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl isc|reference]
 Under torchrun each rank runs an independent replica (the path has no
@@ -240,6 +241,28 @@ def run_isc(args):
     mixed["solve_ms_fp64"] = solve_fp64
     mixed["solve_ms_mixed"] = solve_mixed
     mixed["solve_speedup_vs_fp64"] = solve_fp64 / solve_mixed if solve_mixed > 0 else None
+    # CPR-PF (the paper's Example-2 preconditioner) on the same step, FP64 and mixed
+    cpr_block = {}
+    for precision in ("fp64", "mixed"):
+        g.set_options(prec="cpr", precision=precision)
+        for _ in range(max(1, args.warmup)):
+            step()
+        torch.cuda.synchronize()
+        g.reset_stats()
+        ev0.record()
+        cinfo = [step() for _ in range(args.steps)]
+        ev1.record()
+        torch.cuda.synchronize()
+        ms_c = ev0.elapsed_time(ev1) / args.steps
+        cst = g.stats()
+        cpr_block[precision] = {
+            "value": 1e3 / ms_c, "unit": UNIT, "ms_per_step": ms_c,
+            "krylov_iterations_per_step": statistics.median([i.krylov_iterations for i in cinfo]),
+            "rel_residual": max(i.krylov_rel_residual for i in cinfo),
+            "pressure_stage_ms_per_step": cst["cpr"]["ms"] / args.steps,
+            "ilu_stage_ms_per_step": cst["prec_apply"]["ms"] / args.steps,
+            "speedup_vs_ilu0_fp64": ms_total / args.steps / ms_c}
+    g.set_options(prec="bilu0", precision="fp64")
     # roofline of the dominant kernel class
     launches = sum(v["launches"] for v in stats.values())
     dom = max(stats, key=lambda k: stats[k]["ms"])
@@ -257,6 +280,7 @@ def run_isc(args):
         "roofline": roof,
         "clocks": clocks,
         "mixed": mixed,
+        "cpr": cpr_block,
     }
     if not args.no_adjoint and args.grid is None:
         line["adjoint"] = adjoint_block()

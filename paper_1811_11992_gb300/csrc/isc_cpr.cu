@@ -93,49 +93,98 @@ __device__ __forceinline__ void coarsen_cell(const MGLevel<T>& F, const MGLevel<
   for (int d = 0; d < 7; ++d) C.c[(size_t)d * C.n + I] = cd[d];
 }
 
+// z-levels staged per chunk: a column's loads of one chunk are independent and
+// in flight together; only the recurrences run in order, from registers
+template <typename T> struct ZChunk;
+template <> struct ZChunk<double> { static constexpr int v = 16; };
+template <> struct ZChunk<float> { static constexpr int v = 32; };
+
 // Thomas factors of column (cx, cy): e_k = 1 / (b_k - a_k f_{k-1}), f_k = c_k e_k
 template <typename T>
 __device__ __forceinline__ void factor_column(const MGLevel<T>& L, int cx, int cy) {
-  const int nxy = L.nx * L.ny, n = L.n;
+  constexpr int ZC = ZChunk<T>::v;
+  const int nxy = L.nx * L.ny, n = L.n, i0 = cx + L.nx * cy;
+  T lo[ZC], dg[ZC], up[ZC];
   T fp = 0;
-  for (int k = 0; k < L.nz; ++k) {
-    const int i = cx + L.nx * cy + nxy * k;
-    const T lo = (k > 0) ? L.c[(size_t)0 * n + i] : T(0);
-    const T e = T(1) / (L.c[(size_t)3 * n + i] - lo * fp);
-    fp = (k < L.nz - 1) ? L.c[(size_t)6 * n + i] * e : T(0);
-    L.e[i] = e;
-    L.f[i] = fp;
+  for (int k0 = 0; k0 < L.nz; k0 += ZC) {
+#pragma unroll
+    for (int q = 0; q < ZC; ++q) {
+      const int k = k0 + q, i = i0 + nxy * k;
+      if (k < L.nz) {
+        lo[q] = (k > 0) ? L.c[(size_t)0 * n + i] : T(0);
+        dg[q] = L.c[(size_t)3 * n + i];
+        up[q] = (k < L.nz - 1) ? L.c[(size_t)6 * n + i] : T(0);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < ZC; ++q) {
+      const int k = k0 + q, i = i0 + nxy * k;
+      if (k < L.nz) {
+        const T e = T(1) / (dg[q] - lo[q] * fp);
+        fp = up[q] * e;
+        L.e[i] = e;
+        L.f[i] = fp;
+      }
+    }
   }
 }
 
 // Solve column (cx, cy)'s z-tridiagonal system with the other columns' current
-// values (zero_guess: the other columns are zero).
+// values (zero_guess: the other columns are zero). Forward y_k = e_k rhs_k -
+// e_k a_k y_{k-1}, backward x_k = y_k - f_k x_{k+1}.
 template <typename T>
 __device__ __forceinline__ void zline_column(const MGLevel<T>& L, int cx, int cy, bool zero_guess) {
-  const int nxy = L.nx * L.ny, n = L.n;
+  constexpr int ZC = ZChunk<T>::v;
+  const int nxy = L.nx * L.ny, n = L.n, i0 = cx + L.nx * cy;
   const T* __restrict__ c = L.c;
   T* __restrict__ x = L.x;
-  const int i0 = cx + L.nx * cy;
+  T g[ZC], a[ZC];
   T bp = 0;
-#pragma unroll 4
-  for (int k = 0; k < L.nz; ++k) {
-    const int i = i0 + nxy * k;
-    T rhs = L.b[i];
-    if (!zero_guess) {
-      if (cy > 0) rhs -= c[(size_t)1 * n + i] * x[i - L.nx];
-      if (cx > 0) rhs -= c[(size_t)2 * n + i] * x[i - 1];
-      if (cx < L.nx - 1) rhs -= c[(size_t)4 * n + i] * x[i + 1];
-      if (cy < L.ny - 1) rhs -= c[(size_t)5 * n + i] * x[i + L.nx];
+  for (int k0 = 0; k0 < L.nz; k0 += ZC) {
+#pragma unroll
+    for (int q = 0; q < ZC; ++q) {
+      const int k = k0 + q, i = i0 + nxy * k;
+      if (k < L.nz) {
+        T rhs = L.b[i];
+        if (!zero_guess) {
+          if (cy > 0) rhs -= c[(size_t)1 * n + i] * x[i - L.nx];
+          if (cx > 0) rhs -= c[(size_t)2 * n + i] * x[i - 1];
+          if (cx < L.nx - 1) rhs -= c[(size_t)4 * n + i] * x[i + 1];
+          if (cy < L.ny - 1) rhs -= c[(size_t)5 * n + i] * x[i + L.nx];
+        }
+        const T e = L.e[i];
+        g[q] = e * rhs;
+        a[q] = (k > 0) ? -c[(size_t)0 * n + i] * e : T(0);
+      }
     }
-    const T lo = (k > 0) ? c[(size_t)0 * n + i] : T(0);
-    bp = (rhs - lo * bp) * L.e[i];
-    x[i] = bp;
+#pragma unroll
+    for (int q = 0; q < ZC; ++q) {
+      const int k = k0 + q;
+      if (k < L.nz) {
+        bp = fma(a[q], bp, g[q]);
+        x[i0 + nxy * k] = bp;
+      }
+    }
   }
-#pragma unroll 4
-  for (int k = L.nz - 2; k >= 0; --k) {
-    const int i = i0 + nxy * k;
-    bp = x[i] - L.f[i] * bp;
-    x[i] = bp;
+  T xn = 0;
+  for (int k1 = L.nz; k1 > 0; k1 -= ZC) {
+    const int k0 = k1 - ZC;
+#pragma unroll
+    for (int q = 0; q < ZC; ++q) {
+      const int k = k0 + q;
+      if (k >= 0) {
+        g[q] = x[i0 + nxy * k];
+        a[q] = L.f[i0 + nxy * k];
+      }
+    }
+#pragma unroll
+    for (int q = ZC - 1; q >= 0; --q) {
+      const int k = k0 + q;
+      if (k >= 0) {
+        xn = g[q] - a[q] * xn;
+        x[i0 + nxy * k] = xn;
+      }
+    }
   }
 }
 
@@ -245,7 +294,7 @@ __device__ __forceinline__ void block_smooth(const MGLevel<T>& L, bool zero_gues
 
 // Levels l0 .. nlev-1 of the V-cycle in one thread block (b of level l0 is set).
 template <typename T>
-__global__ void __launch_bounds__(1024) k_mg_coarse(const MGLevel<T>* __restrict__ lv, int l0, int nlev) {
+__global__ void __launch_bounds__(256) k_mg_coarse(const MGLevel<T>* __restrict__ lv, int l0, int nlev) {
   const int t = threadIdx.x, TT = blockDim.x;
   for (int l = l0; l < nlev - 1; ++l) {
     const MGLevel<T> L = lv[l], C = lv[l + 1];
@@ -369,7 +418,7 @@ void pressure_t(Handle& h, const double* r, cudaStream_t s) {
     k_zline<T><<<nblk(colour_count(lv[l].nx, lv[l].ny, 1), tb), tb, 0, s>>>(d, l, 1, 0);
     k_mg_restrict<T><<<nblk(lv[l + 1].n, tb), tb, 0, s>>>(d, l);
   }
-  k_mg_coarse<T><<<1, 1024, 0, s>>>(d, W.ngrid, W.nlev);
+  k_mg_coarse<T><<<1, 256, 0, s>>>(d, W.ngrid, W.nlev);
   for (int l = W.ngrid - 1; l >= 0; --l) {
     k_mg_prolong<T><<<nblk(lv[l].n, tb), tb, 0, s>>>(d, l);
     k_zline<T><<<nblk(colour_count(lv[l].nx, lv[l].ny, 0), tb), tb, 0, s>>>(d, l, 0, 0);
