@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--impl", default="isc", choices=["isc", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the discrete-adjoint measurement")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="time only the headline step (no mixed, CPR-PF, adjoint or end-to-end legs); for profiling")
     ap.add_argument("--grid", default=None,
                     help="NXxNYxNZ: run the same field recipe on a smaller grid (profiling captures)")
     return ap.parse_args()
@@ -195,74 +197,77 @@ def run_isc(args):
     ms_total = max_over_ranks(max(ms_dev, wall * 1e3), "cuda")
     value = job_throughput(world, args.steps, ms_total)
     kry = [i.krylov_iterations for i in infos]
-    # end-to-end through the C ABI with host buffers
-    uh, ch = g.get_state()
-    u_host = torch.from_numpy(uh.reshape(-1).copy()).pin_memory().numpy()
-    c_host = torch.from_numpy(ch.copy()).pin_memory().numpy()
-    g.set_state_device(u0.data_ptr(), c0.data_ptr())
-    u_start, c_start = g.get_state()
-    u_start_p = torch.from_numpy(u_start.reshape(-1).copy()).pin_memory().numpy()
-    c_start_p = torch.from_numpy(c_start.copy()).pin_memory().numpy()
-    for _ in range(max(1, args.warmup // 2)):
-        g.set_state(u_start_p.reshape(8, n), c_start_p)
-        g.newton_step(dt)
-        g.get_state()
-    e2e_steps = max(3, args.steps // 2)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        g.set_state(u_start_p.reshape(8, n), c_start_p)
-        g.newton_step(dt)
-        u_out, c_out = g.get_state()
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    e2e_val = job_throughput(world, e2e_steps, max_over_ranks(e2e_s * 1e3, "cuda"))
-    io_bytes = 9 * n * 8
-    # mixed precision on the same step: FP32 ILU(0) factors and sweeps inside the FP64 FGMRES
-    g.set_options(precision="mixed")
-    for _ in range(max(1, args.warmup)):
-        step()
-    torch.cuda.synchronize()
-    g.reset_stats()
-    ev0.record()
-    minfo = [step() for _ in range(args.steps)]
-    ev1.record()
-    torch.cuda.synchronize()
-    ms_mixed = ev0.elapsed_time(ev1) / args.steps
-    mstats = g.stats()
-    g.set_options(precision="fp64")
-    mixed = {"value": 1e3 / ms_mixed, "unit": UNIT, "ms_per_step": ms_mixed,
-             "krylov_iterations_per_step": statistics.median([i.krylov_iterations for i in minfo]),
-             "rel_residual": max(i.krylov_rel_residual for i in minfo),
-             "prec_apply_ms_per_call": mstats["prec_apply"]["ms"] / max(1, mstats["prec_apply"]["calls"]),
-             "solve_speedup_vs_fp64": None}
-    solve_fp64 = sum(stats[k]["ms"] for k in ("spmv", "prec_apply", "blas1", "ilu_factor")) / args.steps
-    solve_mixed = sum(mstats[k]["ms"] for k in ("spmv", "prec_apply", "blas1", "ilu_factor")) / args.steps
-    mixed["solve_ms_fp64"] = solve_fp64
-    mixed["solve_ms_mixed"] = solve_mixed
-    mixed["solve_speedup_vs_fp64"] = solve_fp64 / solve_mixed if solve_mixed > 0 else None
-    # CPR-PF (the paper's Example-2 preconditioner) on the same step, FP64 and mixed
-    cpr_block = {}
-    for precision in ("fp64", "mixed"):
-        g.set_options(prec="cpr", precision=precision)
+    e2e = mixed = cpr_block = None
+    if not args.no_extras:
+        # end-to-end through the C ABI with host buffers
+        uh, ch = g.get_state()
+        u_host = torch.from_numpy(uh.reshape(-1).copy()).pin_memory().numpy()
+        c_host = torch.from_numpy(ch.copy()).pin_memory().numpy()
+        g.set_state_device(u0.data_ptr(), c0.data_ptr())
+        u_start, c_start = g.get_state()
+        u_start_p = torch.from_numpy(u_start.reshape(-1).copy()).pin_memory().numpy()
+        c_start_p = torch.from_numpy(c_start.copy()).pin_memory().numpy()
+        for _ in range(max(1, args.warmup // 2)):
+            g.set_state(u_start_p.reshape(8, n), c_start_p)
+            g.newton_step(dt)
+            g.get_state()
+        e2e_steps = max(3, args.steps // 2)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            g.set_state(u_start_p.reshape(8, n), c_start_p)
+            g.newton_step(dt)
+            u_out, c_out = g.get_state()
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        e2e_val = job_throughput(world, e2e_steps, max_over_ranks(e2e_s * 1e3, "cuda"))
+        io_bytes = 9 * n * 8
+        e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes}
+        # mixed precision on the same step: FP32 ILU(0) factors and sweeps inside the FP64 FGMRES
+        g.set_options(precision="mixed")
         for _ in range(max(1, args.warmup)):
             step()
         torch.cuda.synchronize()
         g.reset_stats()
         ev0.record()
-        cinfo = [step() for _ in range(args.steps)]
+        minfo = [step() for _ in range(args.steps)]
         ev1.record()
         torch.cuda.synchronize()
-        ms_c = ev0.elapsed_time(ev1) / args.steps
-        cst = g.stats()
-        cpr_block[precision] = {
-            "value": 1e3 / ms_c, "unit": UNIT, "ms_per_step": ms_c,
-            "krylov_iterations_per_step": statistics.median([i.krylov_iterations for i in cinfo]),
-            "rel_residual": max(i.krylov_rel_residual for i in cinfo),
-            "pressure_stage_ms_per_step": cst["cpr"]["ms"] / args.steps,
-            "ilu_stage_ms_per_step": cst["prec_apply"]["ms"] / args.steps,
-            "speedup_vs_ilu0_fp64": ms_total / args.steps / ms_c}
-    g.set_options(prec="bilu0", precision="fp64")
+        ms_mixed = ev0.elapsed_time(ev1) / args.steps
+        mstats = g.stats()
+        g.set_options(precision="fp64")
+        mixed = {"value": 1e3 / ms_mixed, "unit": UNIT, "ms_per_step": ms_mixed,
+                 "krylov_iterations_per_step": statistics.median([i.krylov_iterations for i in minfo]),
+                 "rel_residual": max(i.krylov_rel_residual for i in minfo),
+                 "prec_apply_ms_per_call": mstats["prec_apply"]["ms"] / max(1, mstats["prec_apply"]["calls"]),
+                 "solve_speedup_vs_fp64": None}
+        solve_fp64 = sum(stats[k]["ms"] for k in ("spmv", "prec_apply", "blas1", "ilu_factor")) / args.steps
+        solve_mixed = sum(mstats[k]["ms"] for k in ("spmv", "prec_apply", "blas1", "ilu_factor")) / args.steps
+        mixed["solve_ms_fp64"] = solve_fp64
+        mixed["solve_ms_mixed"] = solve_mixed
+        mixed["solve_speedup_vs_fp64"] = solve_fp64 / solve_mixed if solve_mixed > 0 else None
+        # CPR-PF (the paper's Example-2 preconditioner) on the same step, FP64 and mixed
+        cpr_block = {}
+        for precision in ("fp64", "mixed"):
+            g.set_options(prec="cpr", precision=precision)
+            for _ in range(max(1, args.warmup)):
+                step()
+            torch.cuda.synchronize()
+            g.reset_stats()
+            ev0.record()
+            cinfo = [step() for _ in range(args.steps)]
+            ev1.record()
+            torch.cuda.synchronize()
+            ms_c = ev0.elapsed_time(ev1) / args.steps
+            cst = g.stats()
+            cpr_block[precision] = {
+                "value": 1e3 / ms_c, "unit": UNIT, "ms_per_step": ms_c,
+                "krylov_iterations_per_step": statistics.median([i.krylov_iterations for i in cinfo]),
+                "rel_residual": max(i.krylov_rel_residual for i in cinfo),
+                "pressure_stage_ms_per_step": cst["cpr"]["ms"] / args.steps,
+                "ilu_stage_ms_per_step": cst["prec_apply"]["ms"] / args.steps,
+                "speedup_vs_ilu0_fp64": ms_total / args.steps / ms_c}
+        g.set_options(prec="bilu0", precision="fp64")
     # roofline of the dominant kernel class
     launches = sum(v["launches"] for v in stats.values())
     dom = max(stats, key=lambda k: stats[k]["ms"])
@@ -273,7 +278,7 @@ def run_isc(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_config(case, dt, {"parallelism": f"replicas x{world}",
                                              "krylov_iterations_per_step": statistics.median(kry) if kry else None}),
-        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes},
+        "e2e": e2e,
         "gpu_launches": launches,
         "kernel_ms": {k: round(v["ms"], 3) for k, v in stats.items()},
         "kernel_launches": {k: v["launches"] for k, v in stats.items()},
@@ -282,7 +287,7 @@ def run_isc(args):
         "mixed": mixed,
         "cpr": cpr_block,
     }
-    if not args.no_adjoint and args.grid is None:
+    if not args.no_adjoint and not args.no_extras and args.grid is None:
         line["adjoint"] = adjoint_block()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(max_seconds=30.0)

@@ -9,9 +9,9 @@
 // x-recurrence stays in registers; pencils are taken from a counter in
 // dependency order (so a warp only ever waits on pencils already held by
 // running warps). The cross-pencil hand-off is the data itself: the output
-// vector is NaN-filled before a sweep and a consumer polls the neighbour's
-// 64-byte block vector until it holds numbers; these values are requested LA
-// cells before use. The matrix operands of upcoming cells are streamed into a
+// vector is filled with a NaN sentinel before a sweep and a consumer polls the
+// neighbour's 64-byte block vector until the sentinel is gone; these values
+// are requested LA cells before use. The matrix operands of upcoming cells are streamed into a
 // per-warp shared-memory ring with cp.async. Row starts are computed, not
 // loaded. Every wait is bounded: on timeout the kernel raises DS_TIMEOUT and a
 // global abort flag that makes every other waiter return.
@@ -99,18 +99,25 @@ __device__ __forceinline__ void st_relaxed(float* p, float v) {
 }
 __device__ __forceinline__ float2 ld_nc2(const float* p) { return __ldg(reinterpret_cast<const float2*>(p)); }
 
-// Poll the block vector v[8] of a neighbouring pencil until every entry is a
-// number: the vector is filled with NaN before the sweep and each store is
-// single-copy atomic, so a non-NaN entry is final. The data itself is the
-// hand-off (one L2 round trip, no flags or fences). Returns false if the
-// sweep was aborted (timeout here or elsewhere).
+// The hand-off sentinel is the all-ones bit pattern the vector is filled with
+// before a sweep (a NaN no arithmetic produces). It is tested with an integer
+// compare: on GB300 the FP64 pipe is the sweep's scarcest resource, and a
+// floating-point NaN test would spend it on every poll of a waiting warp.
+__device__ __forceinline__ bool arrived(double a) { return __double_as_longlong(a) != -1LL; }
+__device__ __forceinline__ bool arrived(float a) { return __float_as_int(a) != -1; }
+
+// Poll the block vector v[8] of a neighbouring pencil until every entry has
+// arrived: each store is single-copy atomic, so an entry that is not the
+// sentinel is final. The data itself is the hand-off (one L2 round trip, no
+// flags or fences). Returns false if the sweep was aborted (timeout here or
+// elsewhere).
 template <typename T>
 __device__ __forceinline__ bool poll_vec(const T* v, int c, typename V2<T>::t& out, int* abortf, int* dstatus) {
   const T* p = v + c;
   for (int spins = 0;; ++spins) {
     T a, b;
     ld_relaxed_v2(p, a, b);
-    const bool ok = !isnan(a) && !isnan(b);
+    const bool ok = arrived(a) && arrived(b);
     if (__all_sync(FULL, ok)) {
       out.x = a;
       out.y = b;
@@ -157,7 +164,7 @@ __device__ __forceinline__ typename V2<TM>::t ld_remote(const TM* p) {
 
 template <typename TM>
 __device__ __forceinline__ bool ready2(const typename V2<TM>::t& v) {
-  return !isnan(v.x) && !isnan(v.y);
+  return arrived(v.x) && arrived(v.y);
 }
 
 // re-poll until the lane pair is a number everywhere in the warp
