@@ -162,10 +162,9 @@ void prec(isc_handle* h, const double* r, double* z) {
 
 int build_prec(isc_handle* h) {
   if (h->opt.prec == ISC_PREC_CPR) {
-    if (h->cpr.nlev == 0) {
-      int st = cpr_setup_levels(*h);
-      if (st) return set_err(h, st, "CPR multigrid workspace");
-    }
+    // (re)allocates when the precision of the multigrid arrays changed
+    int st = cpr_setup_levels(*h);
+    if (st) return set_err(h, st, "CPR multigrid workspace");
     Region rg(h, ISC_K_CPR, h->cpr.nlev);
     launch_cpr_setup(*h, h->stream);
   }

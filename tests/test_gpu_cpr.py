@@ -60,6 +60,29 @@ def test_mixed_precision_cpr_apply_matches_oracle_to_fp32(Simulator):
     g.close()
 
 
+def test_switching_precision_rebuilds_the_multigrid(Simulator):
+    """Changing options.precision on a live handle must rebuild the multigrid
+    in the new precision: the apply then equals a fresh handle's."""
+    dims = (13, 7, 3)
+    case = inp.field_case(*dims, 0, 1, "cpr", 30 * inp.DAY, 40)
+    r = np.random.default_rng(9).standard_normal((8, case.n))
+    g = _first_matrix(Simulator, case)
+    z64 = g.precond_apply(r)
+    g.set_options(precision="mixed")
+    g.build_preconditioner()
+    z_switched = g.precond_apply(r)
+    g.set_options(precision="fp64")
+    g.build_preconditioner()
+    z_back = g.precond_apply(r)
+    g.close()
+    f = _first_matrix(Simulator, case, precision="mixed")
+    z32 = f.precond_apply(r)
+    f.close()
+    np.testing.assert_array_equal(z_switched, z32)
+    np.testing.assert_array_equal(z_back, z64)
+    assert not np.array_equal(z32, z64)
+
+
 def test_cpr_gmres_solve_on_a_field_block(Simulator):
     case = inp.field_case(16, 12, 6, 0, 1, "cpr", 30 * inp.DAY, 40)
     g = _first_matrix(Simulator, case)
