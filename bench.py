@@ -341,6 +341,8 @@ def measured_peaks():
 
 
 FP64_PEAK_GFLOPS = 1200.0   # measured DFMA throughput on this GB300
+# dram__bytes_read.sum + dram__bytes_write.sum per call (forward + backward FP64 sweep)
+MEASURED_TRAFFIC = {("prec_apply", 60, 60, 20): (316.65e6, "profiles/k_ilu_sweeps_field_60x60x20.md")}
 
 
 def roofline(dom, stats, g, case, kry):
@@ -387,7 +389,11 @@ def roofline(dom, stats, g, case, kry):
     else:
         out.update(bound="hbm", achieved=ach_gbs, peak=hbm, unit="GB/s", frac=ach_gbs / hbm if hbm else None,
                    peak_source="MEASURED_PEAKS.json hbm_gbs")
-    out["traffic"] = None
+    # DRAM bytes per call from one ncu capture of the current kernels on this grid
+    measured = MEASURED_TRAFFIC.get((dom, case.nx, case.ny, case.nz))
+    out["traffic"] = measured[0] if measured else None
+    if measured:
+        out["traffic_source"] = measured[1]
     return out
 
 
