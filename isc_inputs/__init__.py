@@ -47,6 +47,12 @@ RXN_COKE_OXIDATION = 2  # k(T) * (y_O2 p) * C_c
 
 WELL_RATE_INJECTOR = 0
 WELL_BHP_PRODUCER = 1
+WELL_COUPLED_PRODUCER = 2      # producer with a bottom-hole-pressure unknown and a well equation
+
+# controls of a coupled producer: 0 fixes the bottom-hole pressure; otherwise the
+# bits select the phases (1 water, 2 oil, 4 gas) whose summed molar production
+# rate (mol/s, positive out of the reservoir) is fixed
+CTRL_BHP, CTRL_WATER_RATE, CTRL_OIL_RATE, CTRL_LIQUID_RATE, CTRL_GAS_RATE, CTRL_TOTAL_RATE = 0, 1, 2, 3, 4, 7
 
 
 def tube_fluid() -> dict:
@@ -154,6 +160,9 @@ class Well:
     inj_y: np.ndarray = field(default_factory=lambda: np.zeros(NC))
     inj_T: float = 300.0
     inj_phase: int = 2         # phase of the injected stream: 0 water (liquid), 2 gas
+    control: int = CTRL_BHP    # coupled producer: CTRL_* (target in Pa for CTRL_BHP, else mol/s)
+    ref_depth: float = 0.0     # coupled producer: depth (m) at which the bottom-hole pressure is defined
+    bhp_init: float = 0.0      # coupled producer: initial bottom-hole pressure (Pa)
 
 
 @dataclass
@@ -325,6 +334,26 @@ def adjoint_steps(case: Case, first: float = 60.0, ratio: float = 1.8) -> list:
     short first steps; for the 40x40x10 adjoint workload (20 steps, cap 1 day)
     the loop covers 8.8 days."""
     return [min(first * ratio ** k, case.dt0) for k in range(case.n_steps)]
+
+
+def with_coupled_producer(case: Case, control: int, target: float, bhp_init: float) -> Case:
+    """A copy of the case whose BHP producers become coupled producers with the
+    given control and target, their bottom-hole pressure defined at the depth
+    of the shallowest perforation and starting at bhp_init."""
+    import copy
+    c = copy.copy(case)
+    wells = []
+    for w in case.wells:
+        if w.kind == WELL_BHP_PRODUCER:
+            w = copy.copy(w)
+            w.kind = WELL_COUPLED_PRODUCER
+            w.control = control
+            w.target = target
+            w.ref_depth = float(np.min(case.depth[w.cells]))
+            w.bhp_init = bhp_init
+        wells.append(w)
+    c.wells = wells
+    return c
 
 
 def small_box(nx=4, ny=3, nz=2, seed=0) -> Case:

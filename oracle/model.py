@@ -355,7 +355,44 @@ def old_accumulation(case, u_old, coke_old):
     return np.array(accumulation(case, bp, coke_old))
 
 
-def residual(case, u, coke_old, acc_old, dt, geom=None, return_coke=False):
+def coupled_wells(case):
+    """The coupled producers (bottom-hole pressure unknown), in case order."""
+    return [w for w in case.wells if w.kind == 2]
+
+
+def coupled_phase_rates(case, bp, w, bhp):
+    """Peaceman phase rates (Sec. 2.2, Well Modeling) of a coupled producer's
+    perforations, positive into the reservoir:
+        Q_alpha = WI lambda_alpha (bhp - p - gamma_alpha (z_bh - z))
+    with gamma_alpha the phase's specific weight in the perforated cell
+    (gravity included) and z depth; outflow only (a perforation whose driving
+    difference is positive does not inject). Returns the three (nperf,) arrays."""
+    c = w.cells
+    p = bp["p"][c]
+    out = []
+    for a in range(3):
+        dphi = bhp - p - bp["gam"][a][c] * (w.ref_depth - case.depth[c])
+        out.append(_where(_re(dphi) < 0.0, w.WI * bp["lam"][a][c] * dphi, 0.0 * dphi))
+    return out
+
+
+def well_equations(case, u, bhp):
+    """Well equations of the coupled producers (Sec. 2.2): bhp - c for a fixed
+    bottom-hole pressure, else the summed production rate (mol/s, positive
+    out of the reservoir) of the controlled phases minus c."""
+    bp = base_properties(case, u)
+    F = []
+    for k, w in enumerate(coupled_wells(case)):
+        if w.control == 0:
+            F.append(bhp[k] - w.target)
+            continue
+        Q = coupled_phase_rates(case, bp, w, bhp[k])
+        rate = sum(-np.sum(Q[a]) for a in range(3) if w.control & (1 << a))
+        F.append(rate - w.target)
+    return np.array(F, dtype=np.result_type(u, np.asarray(bhp)))
+
+
+def residual(case, u, coke_old, acc_old, dt, geom=None, return_coke=False, bhp=None):
     """Discrete residual F (8, N) of Sec. 3.1 at unknowns u (8, N).
 
     Sign convention (the printed flux sign is inverted relative to its own
@@ -414,6 +451,15 @@ def residual(case, u, coke_old, acc_old, dt, geom=None, return_coke=False):
             for c in range(6):
                 F[c, cells] -= share * w.target * w.inj_y[c]
             F[6, cells] -= share * w.target * Hinj
+        elif w.kind == 2:  # coupled producer: the bottom-hole pressure is an unknown
+            k = next(i for i, cw in enumerate(coupled_wells(case)) if cw is w)
+            Q = coupled_phase_rates(case, bp, w, bhp[k])
+            xi = ([1.0], [bp["x_lo"][cells], bp["x_ho"][cells]], [y[c][cells] for c in range(6)])
+            rows = ([W], [LO, HO], list(range(6)))
+            for a in range(3):
+                for row, x in zip(rows[a], xi[a]):
+                    F[row, cells] -= Q[a] * x
+                F[6, cells] -= Q[a] * H[a][cells]
         else:             # fixed-BHP producer, outflow only
             dp = w.target - p[cells]
             open_ = _re(dp) < 0.0
@@ -482,9 +528,10 @@ def stencil_colouring(case):
     return color % ncolor, ncolor
 
 
-def jacobian(case, u, coke_old, acc_old, dt, h=1e-30, geom=None):
+def jacobian(case, u, coke_old, acc_old, dt, h=1e-30, geom=None, bhp=None):
     """Exact Jacobian dF/du in BSR form (rowptr, col, val[nnzb, 8, 8]) with
-    val[b][r][k] = dF_r(row cell)/du_k(col cell).
+    val[b][r][k] = dF_r(row cell)/du_k(col cell) (the coupled producers'
+    bottom-hole pressures held at bhp).
 
     Computed by complex-step differentiation of ``residual`` (derivative
     accurate to rounding, no subtraction error), with the cells split into
@@ -506,10 +553,40 @@ def jacobian(case, u, coke_old, acc_old, dt, h=1e-30, geom=None):
         for k in range(NU):
             uc = u.astype(np.complex128)
             uc[k, sel] += 1j * h
-            F = residual(case, uc, coke_old, acc_old, dt, geom)
+            F = residual(case, uc, coke_old, acc_old, dt, geom, bhp=bhp)
             dF = np.imag(F) / h
             val[blocks, :, k] = dF[:, rows[blocks]].T
     return rowptr, col, val
+
+
+def coupled_blocks(case, u, bhp, coke_old, acc_old, dt, h=1e-30, geom=None):
+    """The border of the Newton system of the coupled producers (Sec. 2.2,
+    Well Modeling: the bottom-hole pressure becomes an unknown), by complex
+    step. For the perforations of the coupled wells in case order:
+        B[q] = dF(cell of q)/d bhp(well of q)       (8,)
+        C[q] = dF_w(well of q)/d u(cell of q)       (8,)
+    and per coupled well D[w] = dF_w/d bhp_w, Fw = the well equations."""
+    if geom is None:
+        geom = faces(case)
+    wells = coupled_wells(case)
+    bhp = np.asarray(bhp, dtype=float)
+    B, C = [], []
+    D = np.zeros(len(wells))
+    for k, w in enumerate(wells):
+        bc = bhp.astype(np.complex128)
+        bc[k] += 1j * h
+        dF = np.imag(residual(case, u.astype(np.complex128), coke_old, acc_old, dt, geom, bhp=bc)) / h
+        D[k] = np.imag(well_equations(case, u.astype(np.complex128), bc)[k]) / h
+        for c in w.cells:
+            B.append(dF[:, c].copy())
+            row = np.zeros(NU)
+            for j in range(NU):
+                uc = u.astype(np.complex128)
+                uc[j, c] += 1j * h
+                row[j] = np.imag(well_equations(case, uc, bhp.astype(np.complex128))[k]) / h
+            C.append(row)
+    Fw = np.real(well_equations(case, u, bhp))
+    return np.array(B).reshape(-1, NU), np.array(C).reshape(-1, NU), D, Fw
 
 
 def residual_fd_jacobian(case, u, coke_old, acc_old, dt, rel=1e-7, geom=None):

@@ -159,6 +159,66 @@ def timestep(case, u, coke, dt, opts: NewtonOptions, geom=None):
     return u, coke, opts.maxit, False
 
 
+def well_norms(case, Fw):
+    """Scaled well-equation residuals: |F_w| / |c| with c the well's target
+    (Pa for a fixed bottom-hole pressure, mol/s for a fixed rate)."""
+    return [abs(float(f)) / abs(w.target) for f, w in zip(Fw, model.coupled_wells(case))]
+
+
+def newton_step_coupled(case, u, bhp, coke_old, acc_old, dt, opts: NewtonOptions, geom=None):
+    """Newton step with coupled producers (Sec. 2.2, Well Modeling): unknowns
+    (u, bhp), equations (F, F_w); the bordered system
+        [ J  B ] [du  ]     [F  ]
+        [ C  D ] [dbhp] = - [F_w]
+    is solved densely (small cases). bhp takes the pressure safeguard
+    |dbhp| <= max_dp_frac bhp. Returns a dict like newton_step plus bhp."""
+    if geom is None:
+        geom = model.faces(case)
+    bhp = np.asarray(bhp, dtype=float)
+    F, coke = model.residual(case, u, coke_old, acc_old, dt, geom, return_coke=True, bhp=bhp)
+    e = convergence_norms(case, F, u, coke)
+    Fw = np.real(model.well_equations(case, u, bhp))
+    ew = well_norms(case, Fw)
+    norm = max([e[0] * dt, e[1] * dt, e[2]] + ew)
+    if norm <= opts.tol:
+        return dict(u=u, bhp=bhp, coke=coke, converged=True, norm=norm, norms=e, F=F, Fw=Fw, its=0)
+    rowptr, col, val = model.jacobian(case, u, coke_old, acc_old, dt, geom=geom, bhp=bhp)
+    B, C, D, _ = model.coupled_blocks(case, u, bhp, coke_old, acc_old, dt, geom=geom)
+    n, nw = case.n, len(bhp)
+    A = np.zeros((8 * n + nw, 8 * n + nw))
+    A[:8 * n, :8 * n] = linalg.bsr_to_dense(rowptr, col, val)
+    q = 0
+    for k, w in enumerate(model.coupled_wells(case)):
+        for c in w.cells:
+            A[8 * c:8 * c + 8, 8 * n + k] = B[q]
+            A[8 * n + k, 8 * c:8 * c + 8] = C[q]
+            q += 1
+        A[8 * n + k, 8 * n + k] = D[k]
+    rhs = -np.concatenate([F.T.reshape(-1), Fw])
+    x = np.linalg.solve(A, rhs)
+    du = x[:8 * n].reshape(n, 8).T
+    dbhp = np.clip(x[8 * n:], -0.2 * bhp, 0.2 * bhp)
+    un = apply_update(u, du)
+    return dict(u=un, bhp=bhp + dbhp, du=du, dbhp=x[8 * n:], coke=coke, converged=False, norm=norm, norms=e,
+                F=F, Fw=Fw, its=0)
+
+
+def timestep_coupled(case, u, bhp, coke, dt, opts: NewtonOptions, geom=None):
+    """Implicit-Euler step with coupled producers. Returns (u, bhp, coke, its, ok)."""
+    if geom is None:
+        geom = model.faces(case)
+    acc_old = model.old_accumulation(case, u, coke)
+    un, bn = u.copy(), np.asarray(bhp, dtype=float).copy()
+    for it in range(opts.maxit + 1):
+        r = newton_step_coupled(case, un, bn, coke, acc_old, dt, opts, geom)
+        if r["converged"]:
+            return r["u"], r["bhp"], r["coke"], it, True
+        un, bn = r["u"], r["bhp"]
+        if not (np.all(np.isfinite(un)) and np.all(np.isfinite(bn))):
+            break
+    return u, bhp, coke, opts.maxit, False
+
+
 def next_dt(dt, u_old, u_new, dt_max, dT_target=20.0, dS_target=0.2):
     dT = float(np.max(np.abs(u_new[5] - u_old[5])))
     dS = float(max(np.max(np.abs(u_new[6] - u_old[6])), np.max(np.abs(u_new[7] - u_old[7]))))
