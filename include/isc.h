@@ -76,7 +76,15 @@ enum isc_rxn_kind {
   ISC_RXN_CRACKING = 1,        /* r = A e^{-Ea/RT} (phi_f S_o rho_o x_i)(1-(C_c/C_max)^5)  */
   ISC_RXN_COKE_OXIDATION = 2   /* r = A e^{-Ea/RT} (y_O2 p) C_c                            */
 };
-enum isc_well_kind { ISC_WELL_RATE_INJECTOR = 0, ISC_WELL_BHP_PRODUCER = 1 };
+enum isc_well_kind { ISC_WELL_RATE_INJECTOR = 0, ISC_WELL_BHP_PRODUCER = 1, ISC_WELL_COUPLED_PRODUCER = 2 };
+/* Controls of a coupled producer: ISC_CTRL_BHP fixes the bottom-hole pressure
+ * (target in Pa); otherwise the bits select the phases (1 water, 2 oil, 4 gas)
+ * whose summed molar production rate (mol/s, positive out of the reservoir)
+ * is fixed at target. */
+enum isc_well_control {
+  ISC_CTRL_BHP = 0, ISC_CTRL_WATER_RATE = 1, ISC_CTRL_OIL_RATE = 2, ISC_CTRL_LIQUID_RATE = 3,
+  ISC_CTRL_GAS_RATE = 4, ISC_CTRL_TOTAL_RATE = 7
+};
 
 /* Cartesian grid (Sec. 3.1). depth: N cell-centre depths in m (increasing
  * downwards), or NULL for depth = (k + 0.5) dz. */
@@ -137,8 +145,13 @@ typedef struct isc_reactions {
  * Q_alpha = WI rho_alpha k_r,alpha/mu_alpha (bhp - p_i) when p_i > bhp (no
  * cross-flow). A rate injector puts target mol/s of composition inj_y at
  * T_inj, split over its perforations in proportion to WI; inj_phase 2 carries
- * gas enthalpy, inj_phase 0 liquid-water enthalpy. A cell may be perforated by
- * at most one well. */
+ * gas enthalpy, inj_phase 0 liquid-water enthalpy. A coupled producer has
+ * its bottom-hole pressure bhp, defined at depth ref_depth, as an unknown and
+ * one well equation (control, target; see isc_well_control); its perforation
+ * at cell i takes Q_alpha = WI lambda_alpha (bhp - p_i - gamma_alpha (ref_depth
+ * - z_i)) per phase when that is negative (gamma_alpha the phase's specific
+ * weight in the cell), and bhp starts at bhp_init. A cell may be perforated
+ * by at most one well. */
 typedef struct isc_well {
   int32_t kind;
   int32_t n_perf;
@@ -148,6 +161,9 @@ typedef struct isc_well {
   double inj_y[6];
   double inj_T;
   int32_t inj_phase;
+  int32_t control;    /* coupled producer: isc_well_control */
+  double ref_depth;   /* coupled producer: depth of the bottom-hole pressure (m) */
+  double bhp_init;    /* coupled producer: initial bottom-hole pressure (Pa) */
 } isc_well;
 
 typedef struct isc_wells {
@@ -239,8 +255,25 @@ int isc_get_state(struct isc_handle* h, double* u, double* coke);
 int isc_set_state_device(struct isc_handle* h, const double* d_u, const double* d_coke);
 int isc_get_state_device(struct isc_handle* h, double* d_u, double* d_coke);
 /* Make the current iterate (u, C_c) the accepted state of time level n: stores
- * C_c^n and the accumulation N^n, E^n used by the next residuals. */
+ * C_c^n and the accumulation N^n, E^n used by the next residuals (and the
+ * coupled producers' bottom-hole pressures). */
 int isc_begin_step(struct isc_handle* h);
+/* Coupled producers (ISC_WELL_COUPLED_PRODUCER), in the order of the wells
+ * given at creation. With nwc > 0 the Newton system is bordered: unknowns
+ * (u, bhp), equations (F, F_w); Krylov vectors, isc_spmv and
+ * isc_precond_apply then have length 8N + nwc (the well entries last), and
+ * the preconditioner is block lower-triangular (the cells' preconditioner,
+ * then z_w = (r_w - C z) / D_w). Bottom-hole pressures in and out (host, nwc
+ * doubles); set_well_bhp does not touch the accepted state. */
+int32_t isc_num_coupled_wells(const struct isc_handle* h);
+int isc_set_well_bhp(struct isc_handle* h, const double* bhp);
+int isc_get_well_bhp(struct isc_handle* h, double* bhp);
+/* After isc_assemble (before decoupling): the border of the Newton system,
+ * for the coupled producers' perforations in creation order,
+ * B[q*8 + r] = dF_r(cell of q)/d bhp, C[q*8 + k] = dF_w/du_k(cell of q), and
+ * per coupled well D[w] = dF_w/d bhp_w and Fw[w] the well equation (host
+ * arrays; any may be NULL). */
+int isc_get_well_system(struct isc_handle* h, double* B, double* C, double* D, double* Fw);
 
 /* ---------------------------------------------------------------- hot path */
 

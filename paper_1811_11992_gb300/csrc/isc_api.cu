@@ -115,7 +115,7 @@ void free_all(isc_handle* h) {
   void* ptrs[] = {h->rowptr, h->col, h->level_cells, h->phi_ref, h->depth, h->tx, h->ty, h->tz, h->well_slot,
                   h->slots, h->u, h->coke, h->u_n, h->coke_n, h->acc_n, h->props, h->R, h->J, h->ntot, h->du,
                   h->rhs, h->dinv, h->J32, h->dinv32, h->vec32, h->V, h->Z, h->w, h->tmp, h->partial, h->scal, h->dstatus, h->pipe, h->red_counter,
-                  h->wx, h->wy, h->wz, h->adj.store, h->adj.ubar, h->adj.cbar, h->adj.lam, h->adj.glnk, h->adj.grx,
+                  h->wx, h->wy, h->wz, h->cw, h->bhp, h->bhp_n, h->Dw, h->Bv, h->Cv, h->Fq, h->Dq, h->adj.store, h->adj.ubar, h->adj.cbar, h->adj.lam, h->adj.glnk, h->adj.grx,
                   h->adj.scond, h->adj.kd, h->adj.loss_cell, h->adj.sums, h->adj.inj_first, h->adj.inj_count};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -137,11 +137,23 @@ double host_dot(isc_handle* h, const double* a, const double* b, int off) {
 }
 
 void spmv(isc_handle* h, const double* x, double* y) {
-  Region rg(h, ISC_K_SPMV, 1);
+  Region rg(h, ISC_K_SPMV, h->nwc ? 3 : 1);
   launch_spmv(h->n, h->rowptr, h->col, h->J, x, y, h->decoupled ? 1 : 0, h->stream);
+  launch_well_border_spmv(*h, x, y, h->stream);
 }
 
+void prec_cells(isc_handle* h, const double* r, double* z);
+
+// block lower-triangular: the cells' preconditioner, then the coupled wells' rows
 void prec(isc_handle* h, const double* r, double* z) {
+  prec_cells(h, r, z);
+  if (h->nwc) {
+    Region rg(h, ISC_K_PREC_APPLY, 1);
+    launch_well_prec(*h, r, z, h->stream);
+  }
+}
+
+void prec_cells(isc_handle* h, const double* r, double* z) {
   if (h->opt.prec == ISC_PREC_CPR) {
     {
       Region rg(h, ISC_K_CPR, cpr_pressure_launches(*h));
@@ -195,7 +207,7 @@ int build_prec(isc_handle* h) {
 // Right-preconditioned restarted GMRES(m), classical Gram-Schmidt applied twice,
 // Givens rotations on the host. Solves A x = b, x0 = 0.
 int gmres(isc_handle* h, const double* b, double* x, int* its_out, double* rel_out) {
-  const int len = h->n * 8;
+  const int len = h->vlen;
   const int m = std::min(h->opt.restart, h->restart_alloc);
   cudaStream_t s = h->stream;
   double* V = h->V;
@@ -238,8 +250,8 @@ int gmres(isc_handle* h, const double* b, double* x, int* its_out, double* rel_o
     g[0] = beta;
     int jdone = 0;
     for (int j = 0; j < m; ++j) {
-      double* Vj = V + (size_t)j * len;
-      double* Zj = Z + (size_t)j * len;
+      double* Vj = V + (size_t)j * h->vstride;
+      double* Zj = Z + (size_t)j * h->vstride;
       prec(h, Vj, Zj);
       spmv(h, Zj, h->w);
       {
@@ -275,7 +287,7 @@ int gmres(isc_handle* h, const double* b, double* x, int* its_out, double* rel_o
       rel = fabs(g[j + 1]) / bnorm;
       if (rel <= h->opt.tol_lin || its >= h->opt.maxit_lin || hn == 0.0) break;
       Region rg(h, ISC_K_BLAS1, 1);
-      launch_scale_copy(len, 1.0 / hn, h->w, V + (size_t)(j + 1) * len, s);
+      launch_scale_copy(len, 1.0 / hn, h->w, V + (size_t)(j + 1) * h->vstride, s);
     }
     for (int i = jdone - 1; i >= 0; --i) {
       double acc = g[i];
@@ -305,16 +317,17 @@ int gmres(isc_handle* h, const double* b, double* x, int* its_out, double* rel_o
 
 // Right-preconditioned BiCGSTAB, x0 = 0.
 int bicgstab(isc_handle* h, const double* b, double* x, int* its_out, double* rel_out) {
-  const int len = h->n * 8;
+  const int len = h->vlen;
   cudaStream_t s = h->stream;
+  const size_t vs = h->vstride;
   double* r = h->V;
-  double* rhat = r + len;
-  double* p = rhat + len;
-  double* v = p + len;
-  double* sv = v + len;
-  double* t = sv + len;
+  double* rhat = r + vs;
+  double* p = rhat + vs;
+  double* v = p + vs;
+  double* sv = v + vs;
+  double* t = sv + vs;
   double* phat = h->Z;
-  double* shat = phat + len;
+  double* shat = phat + vs;
   cudaMemsetAsync(x, 0, sizeof(double) * len, s);
   double bnorm;
   {
@@ -680,11 +693,29 @@ int isc_create(const isc_grid* grid, const isc_rock* rock, const isc_fluid* fl, 
   // well slots
   std::vector<int32_t> well_slot(n, -1);
   std::vector<int32_t> inj_first, inj_count;
+  std::vector<CoupledWell> coupled;
   for (int w = 0; w < wells->nw; ++w) {
     const isc_well& W = wells->wells[w];
-    if (W.n_perf < 1 || !W.cells || !W.WI) {
+    if (W.n_perf < 1 || !W.cells || !W.WI || W.kind < ISC_WELL_RATE_INJECTOR || W.kind > ISC_WELL_COUPLED_PRODUCER) {
       delete h;
       return ISC_ERR_INVALID_ARG;
+    }
+    const bool is_coupled = W.kind == ISC_WELL_COUPLED_PRODUCER;
+    if (is_coupled) {
+      const int ctl = W.control;
+      const bool ok = (ctl == ISC_CTRL_BHP || (ctl >= 1 && ctl <= 7)) && W.target == W.target &&
+                      W.target != 0.0 && W.bhp_init > 0.0;
+      if (!ok) {
+        delete h;
+        return ISC_ERR_INVALID_ARG;
+      }
+      CoupledWell cw{};
+      cw.control = ctl;
+      cw.first = (int)h->h_slots.size();
+      cw.count = W.n_perf;
+      cw.target = W.target;
+      coupled.push_back(cw);
+      h->h_bhp_init.push_back(W.bhp_init);
     }
     WellInfo info{};
     info.kind = W.kind;
@@ -725,6 +756,9 @@ int isc_create(const isc_grid* grid, const isc_rock* rock, const isc_fluid* fl, 
       sl.kind = W.kind;
       sl.cell = c;
       sl.bhp = W.target;
+      sl.wc = is_coupled ? (int)coupled.size() - 1 : -1;
+      sl.control = W.control;
+      sl.zref = W.ref_depth;
       well_slot[c] = (int32_t)h->h_slots.size();
       h->h_slots.push_back(sl);
       h->h_WI0.push_back(W.WI[q]);
@@ -733,9 +767,13 @@ int isc_create(const isc_grid* grid, const isc_rock* rock, const isc_fluid* fl, 
   }
   h->nslots = (int)h->h_slots.size();
   h->adj.n_inj = (int)inj_first.size();
-  // device memory
+  h->nwc = (int)coupled.size();
+  // device memory; Krylov vectors hold the cells' 8N unknowns and the coupled wells' bottom-hole pressures
   h->restart_alloc = std::max(o.restart, 8);
-  const size_t len = (size_t)n * 8;
+  h->vlen = n * 8 + h->nwc;
+  // vectors start on 64-byte boundaries (the sweeps and SpMV use 16-byte vector accesses)
+  h->vstride = (h->vlen + 7) / 8 * 8;
+  const size_t len = (size_t)h->vstride;
   h->red_blocks = 304;
   int e = 0;
   e |= dalloc(h, &h->rowptr, n + 1);
@@ -753,9 +791,17 @@ int isc_create(const isc_grid* grid, const isc_rock* rock, const isc_fluid* fl, 
   e |= dalloc(h, &h->adj.inj_count, std::max(h->adj.n_inj, 1));
   e |= dalloc(h, &h->well_slot, n);
   e |= dalloc(h, &h->slots, std::max(h->nslots, 1));
-  e |= dalloc(h, &h->u, len);
+  e |= dalloc(h, &h->cw, std::max(h->nwc, 1));
+  e |= dalloc(h, &h->bhp, std::max(h->nwc, 1));
+  e |= dalloc(h, &h->bhp_n, std::max(h->nwc, 1));
+  e |= dalloc(h, &h->Dw, std::max(h->nwc, 1));
+  e |= dalloc(h, &h->Bv, (size_t)std::max(h->nslots, 1) * 8);
+  e |= dalloc(h, &h->Cv, (size_t)std::max(h->nslots, 1) * 8);
+  e |= dalloc(h, &h->Fq, std::max(h->nslots, 1));
+  e |= dalloc(h, &h->Dq, std::max(h->nslots, 1));
+  e |= dalloc(h, &h->u, (size_t)n * 8);
   e |= dalloc(h, &h->coke, n);
-  e |= dalloc(h, &h->u_n, len);
+  e |= dalloc(h, &h->u_n, (size_t)n * 8);
   e |= dalloc(h, &h->coke_n, n);
   e |= dalloc(h, &h->acc_n, (size_t)n * 7);
   e |= dalloc(h, &h->props, (size_t)n * NQD);
@@ -793,6 +839,13 @@ int isc_create(const isc_grid* grid, const isc_rock* rock, const isc_fluid* fl, 
   cudaMemcpyAsync(h->phi_ref, rock->phi_ref, sizeof(double) * n, cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(h->depth, depth.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(h->well_slot, well_slot.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s);
+  if (h->nwc) {
+    cudaMemcpyAsync(h->cw, coupled.data(), sizeof(CoupledWell) * h->nwc, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(h->bhp, h->h_bhp_init.data(), sizeof(double) * h->nwc, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(h->bhp_n, h->h_bhp_init.data(), sizeof(double) * h->nwc, cudaMemcpyHostToDevice, s);
+  }
+  cudaMemsetAsync(h->Bv, 0, sizeof(double) * std::max(h->nslots, 1) * 8, s);
+  cudaMemsetAsync(h->Cv, 0, sizeof(double) * std::max(h->nslots, 1) * 8, s);
   if (h->adj.n_inj) {
     cudaMemcpyAsync(h->adj.inj_first, inj_first.data(), sizeof(int32_t) * h->adj.n_inj, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(h->adj.inj_count, inj_count.data(), sizeof(int32_t) * h->adj.n_inj, cudaMemcpyHostToDevice, s);
@@ -804,7 +857,7 @@ int isc_create(const isc_grid* grid, const isc_rock* rock, const isc_fluid* fl, 
   }
   cudaMemsetAsync(h->dstatus, 0, sizeof(int), s);
   cudaMemsetAsync(h->red_counter, 0, sizeof(unsigned), s);
-  cudaMemsetAsync(h->u, 0, sizeof(double) * len, s);
+  cudaMemsetAsync(h->u, 0, sizeof(double) * (size_t)n * 8, s);
   cudaMemsetAsync(h->coke, 0, sizeof(double) * n, s);
   cudaMemsetAsync(h->coke_n, 0, sizeof(double) * n, s);
   cudaError_t ce = cudaStreamSynchronize(s);
@@ -840,6 +893,9 @@ int isc_init_equilibrium(isc_handle* h, double p0, double T0, double Sw0, double
                          const double y_rest[3], int32_t n_ignited, const int32_t* ignited, double T_ignite) {
   if (!h || !y_rest || n_ignited < 0 || (n_ignited > 0 && !ignited)) return ISC_ERR_INVALID_ARG;
   launch_init_equilibrium(*h, p0, T0, Sw0, So0, x_LO0, y_rest, h->stream);
+  if (h->nwc)
+    CUDA_TRY(h, cudaMemcpyAsync(h->bhp, h->h_bhp_init.data(), sizeof(double) * h->nwc, cudaMemcpyHostToDevice,
+                                h->stream));
   for (int q = 0; q < n_ignited; ++q) {
     int c = ignited[q];
     if (c < 0 || c >= h->n) return set_err(h, ISC_ERR_INVALID_ARG, "ignited cell out of range");
@@ -886,6 +942,8 @@ int isc_begin_step(isc_handle* h) {
   if (!h) return ISC_ERR_INVALID_ARG;
   CUDA_TRY(h, cudaMemcpyAsync(h->u_n, h->u, sizeof(double) * 8 * h->n, cudaMemcpyDeviceToDevice, h->stream));
   CUDA_TRY(h, cudaMemcpyAsync(h->coke_n, h->coke, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, h->stream));
+  if (h->nwc)
+    CUDA_TRY(h, cudaMemcpyAsync(h->bhp_n, h->bhp, sizeof(double) * h->nwc, cudaMemcpyDeviceToDevice, h->stream));
   launch_old_accumulation(*h, h->stream);
   CUDA_TRY(h, cudaGetLastError());
   h->have_acc = true;
@@ -904,6 +962,10 @@ int isc_assemble(isc_handle* h, double dt) {
   {
     Region rg(h, ISC_K_FLUX, 1);
     launch_flux(*h, h->stream);
+  }
+  if (h->nwc) {
+    Region rg(h, ISC_K_PROPS, 1);
+    launch_well_equations(*h, h->stream);
   }
   CUDA_TRY(h, cudaGetLastError());
   h->assembled = true;
@@ -943,7 +1005,7 @@ int isc_solve(isc_handle* h, isc_newton_info* info) {
     st = build_prec(h);
     if (st) return st;
   }
-  const int len = h->n * 8;
+  const int len = h->vlen;
   {
     Region rg(h, ISC_K_BLAS1, 1);
     launch_scale_copy(len, -1.0, h->R, h->rhs, h->stream);
@@ -966,8 +1028,9 @@ int isc_solve(isc_handle* h, isc_newton_info* info) {
 int isc_update(isc_handle* h) {
   if (!h) return ISC_ERR_INVALID_ARG;
   {
-    Region rg(h, ISC_K_UPDATE, 1);
+    Region rg(h, ISC_K_UPDATE, h->nwc ? 2 : 1);
     launch_update(*h, h->stream);
+    launch_well_update(*h, h->stream);
   }
   CUDA_TRY(h, cudaGetLastError());
   h->assembled = h->decoupled = h->prec_built = false;
@@ -985,7 +1048,7 @@ int isc_newton_step(isc_handle* h, double dt, isc_newton_info* info) {
     Region rg(h, ISC_K_NORM, 2);
     launch_norms(*h, h->stream);
   }
-  CUDA_TRY(h, cudaMemcpyAsync(h->h_scal, h->scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(h->h_scal, h->scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   st = check_device_status(h);  // synchronises
   if (st) {
     info->status = st;
@@ -995,6 +1058,7 @@ int isc_newton_step(isc_handle* h, double dt, isc_newton_info* info) {
   info->norm_energy = h->h_scal[1] * dt;
   info->norm_gs = h->h_scal[2];
   info->norm = std::max(info->norm_mass, std::max(info->norm_energy, info->norm_gs));
+  if (h->nwc) info->norm = std::max(info->norm, h->h_scal[3]);  // coupled wells: max |F_w| / |target|
   if (!isfinite(info->norm)) {
     info->status = ISC_ERR_NONFINITE;
     return set_err(h, ISC_ERR_NONFINITE, "non-finite residual norm");
@@ -1048,6 +1112,7 @@ int isc_timestep(isc_handle* h, double dt, isc_step_info* info) {
   // restore the accepted state
   cudaMemcpyAsync(h->u, h->u_n, sizeof(double) * 8 * h->n, cudaMemcpyDeviceToDevice, h->stream);
   cudaMemcpyAsync(h->coke, h->coke_n, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, h->stream);
+  if (h->nwc) cudaMemcpyAsync(h->bhp, h->bhp_n, sizeof(double) * h->nwc, cudaMemcpyDeviceToDevice, h->stream);
   cudaStreamSynchronize(h->stream);
   h->assembled = h->decoupled = h->prec_built = false;
   if (st == ISC_OK) st = set_err(h, ISC_ERR_NEWTON_NOCONV, "Newton did not converge within maxit_newton");
@@ -1092,7 +1157,7 @@ int isc_get_coke(isc_handle* h, double* coke) {
 int isc_spmv(isc_handle* h, const double* x, double* y) {
   if (!h || !x || !y) return ISC_ERR_INVALID_ARG;
   if (!h->assembled) return set_err(h, ISC_ERR_STATE, "assemble first");
-  const size_t len = (size_t)h->n * 8;
+  const size_t len = (size_t)h->vlen;
   CUDA_TRY(h, cudaMemcpyAsync(h->w, x, sizeof(double) * len, cudaMemcpyHostToDevice, h->stream));
   spmv(h, h->w, h->tmp);
   CUDA_TRY(h, cudaMemcpyAsync(y, h->tmp, sizeof(double) * len, cudaMemcpyDeviceToHost, h->stream));
@@ -1103,7 +1168,7 @@ int isc_spmv(isc_handle* h, const double* x, double* y) {
 int isc_precond_apply(isc_handle* h, const double* r, double* z) {
   if (!h || !r || !z) return ISC_ERR_INVALID_ARG;
   if (!h->prec_built) return set_err(h, ISC_ERR_STATE, "build the preconditioner first");
-  const size_t len = (size_t)h->n * 8;
+  const size_t len = (size_t)h->vlen;
   CUDA_TRY(h, cudaMemcpyAsync(h->w, r, sizeof(double) * len, cudaMemcpyHostToDevice, h->stream));
   prec(h, h->w, h->V);
   CUDA_TRY(h, cudaMemcpyAsync(z, h->V, sizeof(double) * len, cudaMemcpyDeviceToHost, h->stream));
@@ -1130,6 +1195,50 @@ int isc_bsr_spmv_device(int32_t nrows, const int32_t* d_rowptr, const int32_t* d
   if (nrows == 0) return ISC_OK;
   launch_spmv(nrows, d_rowptr, d_col, d_val, d_x, d_y, unit_diag, (cudaStream_t)stream);
   return cudaGetLastError() == cudaSuccess ? ISC_OK : ISC_ERR_CUDA;
+}
+
+int32_t isc_num_coupled_wells(const isc_handle* h) { return h ? h->nwc : 0; }
+
+int isc_set_well_bhp(isc_handle* h, const double* bhp) {
+  if (!h || (h->nwc && !bhp)) return ISC_ERR_INVALID_ARG;
+  if (h->nwc) {
+    CUDA_TRY(h, cudaMemcpyAsync(h->bhp, bhp, sizeof(double) * h->nwc, cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  }
+  h->assembled = h->decoupled = h->prec_built = false;
+  return ISC_OK;
+}
+
+int isc_get_well_bhp(isc_handle* h, double* bhp) {
+  if (!h || (h->nwc && !bhp)) return ISC_ERR_INVALID_ARG;
+  if (h->nwc) {
+    CUDA_TRY(h, cudaMemcpyAsync(bhp, h->bhp, sizeof(double) * h->nwc, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  }
+  return ISC_OK;
+}
+
+int isc_get_well_system(isc_handle* h, double* B, double* C, double* D, double* Fw) {
+  if (!h) return ISC_ERR_INVALID_ARG;
+  if (!h->assembled || h->decoupled) return set_err(h, ISC_ERR_STATE, "assemble first (and do not decouple)");
+  if (h->nwc == 0) return ISC_OK;
+  // the coupled wells' slots, in creation order
+  std::vector<int> order;
+  for (int q = 0; q < h->nslots; ++q)
+    if (h->h_slots[q].wc >= 0) order.push_back(q);
+  std::vector<double> bv((size_t)h->nslots * 8), cv((size_t)h->nslots * 8);
+  CUDA_TRY(h, cudaMemcpyAsync(bv.data(), h->Bv, sizeof(double) * bv.size(), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(cv.data(), h->Cv, sizeof(double) * cv.size(), cudaMemcpyDeviceToHost, h->stream));
+  if (D) CUDA_TRY(h, cudaMemcpyAsync(D, h->Dw, sizeof(double) * h->nwc, cudaMemcpyDeviceToHost, h->stream));
+  if (Fw)
+    CUDA_TRY(h, cudaMemcpyAsync(Fw, h->R + (size_t)h->n * 8, sizeof(double) * h->nwc, cudaMemcpyDeviceToHost,
+                                h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  for (size_t k = 0; k < order.size(); ++k) {
+    if (B) memcpy(B + k * 8, bv.data() + (size_t)order[k] * 8, sizeof(double) * 8);
+    if (C) memcpy(C + k * 8, cv.data() + (size_t)order[k] * 8, sizeof(double) * 8);
+  }
+  return ISC_OK;
 }
 
 int isc_set_parameters(isc_handle* h, const double* log_k, const double* Ea, const double* lnA) {
@@ -1184,6 +1293,7 @@ int isc_adjoint(isc_handle* h, const isc_adjoint_spec* spec, double* loss, doubl
     if (!(spec->dt[q] > 0.0) || !isfinite(spec->dt[q])) return set_err(h, ISC_ERR_INVALID_ARG, "step sizes must be > 0");
   if (!(spec->tol_adjoint >= 0.0)) return set_err(h, ISC_ERR_INVALID_ARG, "tol_adjoint must be >= 0");
   if (!h->have_acc) return set_err(h, ISC_ERR_STATE, "isc_begin_step (or isc_init_equilibrium) must come first");
+  if (h->nwc) return set_err(h, ISC_ERR_UNIMPLEMENTED, "the adjoint does not cover coupled producers");
   const bool want_grad = g_log_k || g_Ea || g_lnA;
   const int n = h->n, nr = h->P.nr;
   const size_t len = (size_t)n * 8, SN = (size_t)n * 9;

@@ -39,7 +39,10 @@ __global__ void __launch_bounds__(128) k_props(Params P, const double* __restric
                                                const int32_t* __restrict__ rowptr, double* __restrict__ R,
                                                double* __restrict__ J, double* __restrict__ props,
                                                double* __restrict__ ntot, double* __restrict__ coke_out,
-                                               int* __restrict__ dstatus) {
+                                               int* __restrict__ dstatus, const double* __restrict__ depth,
+                                               const double* __restrict__ bhp, double* __restrict__ Bv,
+                                               double* __restrict__ Cv, double* __restrict__ Fq,
+                                               double* __restrict__ Dq) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= P.n) return;
   const int n = P.n;
@@ -82,6 +85,54 @@ __global__ void __launch_bounds__(128) k_props(Params P, const double* __restric
     if (w.kind == ISC_WELL_RATE_INJECTOR) {
 #pragma unroll
       for (int r = 0; r < 7; ++r) Rl[r] = Rl[r] - w.src[r];
+    } else if (w.kind == ISC_WELL_COUPLED_PRODUCER) {
+      // Peaceman rates with the bottom-hole pressure unknown and the hydrostatic
+      // head between its reference depth and the perforation (Sec. 2.2):
+      // Q_a = WI lambda_a (bhp - p - gamma_a (z_ref - z)), outflow only.
+      // Also the border of the Newton system: dF/d bhp (B), and for a rate
+      // control the perforation's part of the well equation, its u-gradient
+      // (C) and its bhp-derivative.
+      const double bw = bhp[w.wc];
+      const double zi = depth[i];
+      double bcol[8] = {0, 0, 0, 0, 0, 0, 0, 0}, crow[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      double fq = 0.0, dq = 0.0;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const D8 dphi = bw - b.p - b.gam[a] * (w.zref - zi);
+        if (!(dphi.v < 0.0)) continue;
+        const D8 Q = (w.WI * b.lam[a]) * dphi;
+        const double dQ = w.WI * b.lam[a].v;
+        if (a == 0) {
+          Rl[0] = Rl[0] - Q;
+          bcol[0] -= dQ;
+        } else if (a == 1) {
+          Rl[1] = Rl[1] - Q * b.xlo;
+          Rl[2] = Rl[2] - Q * b.xho;
+          bcol[1] -= dQ * b.xlo.v;
+          bcol[2] -= dQ * b.xho.v;
+        } else {
+#pragma unroll
+          for (int c = 0; c < 6; ++c) {
+            Rl[c] = Rl[c] - Q * b.y[c];
+            bcol[c] -= dQ * b.y[c].v;
+          }
+        }
+        Rl[6] = Rl[6] - Q * b.H[a];
+        bcol[6] -= dQ * b.H[a].v;
+        if (w.control & (1 << a)) {
+          fq -= Q.v;
+          dq -= dQ;
+#pragma unroll
+          for (int k = 0; k < 8; ++k) crow[k] -= Q.d[k];
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        Bv[(size_t)sl * 8 + k] = bcol[k];
+        Cv[(size_t)sl * 8 + k] = (w.control == ISC_CTRL_BHP) ? 0.0 : crow[k];
+      }
+      Fq[sl] = fq;
+      Dq[sl] = dq;
     } else {
       D8 dpw = w.bhp - b.p;
       if (dpw.v < 0.0) {
@@ -311,6 +362,37 @@ __global__ void __launch_bounds__(256) k_flux(Params P, const double* __restrict
   for (int k = 0; k < 8; ++k) Jd[k] += dd[k];
 }
 
+// Well equations of the coupled producers (Sec. 2.2): bhp - c, or the summed
+// production rate of the controlled phases minus c; their bhp-derivatives;
+// and max |F_w| / |c| into norm_out. One thread, fixed order (wells are few).
+__global__ void k_well_eq(int nwc, const CoupledWell* __restrict__ cw, const double* __restrict__ Fq,
+                          const double* __restrict__ Dq, const double* __restrict__ bhp, double* __restrict__ Rw,
+                          double* __restrict__ Dw, double* __restrict__ norm_out) {
+  if (blockIdx.x * blockDim.x + threadIdx.x != 0) return;
+  double e = 0.0;
+  for (int w = 0; w < nwc; ++w) {
+    const CoupledWell c = cw[w];
+    double F, D;
+    if (c.control == ISC_CTRL_BHP) {
+      F = bhp[w] - c.target;
+      D = 1.0;
+    } else {
+      F = 0.0;
+      D = 0.0;
+      for (int q = c.first; q < c.first + c.count; ++q) {
+        F += Fq[q];
+        D += Dq[q];
+      }
+      F -= c.target;
+    }
+    Rw[w] = F;
+    Dw[w] = D;
+    e = fmax(e, fabs(F) / fmax(fabs(c.target), 1e-300));
+    if (!isfinite(F)) e = INFINITY;
+  }
+  *norm_out = e;
+}
+
 // scaled max-norms: mass |F_c|/(V N_tot), energy |F_E|/(V cv), constraint |F_GS|
 __global__ void k_norms(Params P, const double* __restrict__ R, const double* __restrict__ ntot,
                         unsigned long long* __restrict__ out) {
@@ -363,7 +445,8 @@ __global__ void k_init_equilibrium(Params P, double p0, double T0, double Sw0, d
 void launch_props(Handle& h, cudaStream_t s) {
   int tb = 128;
   k_props<<<(h.n + tb - 1) / tb, tb, 0, s>>>(h.P, h.u, h.coke_n, h.acc_n, h.phi_ref, h.well_slot, h.slots, h.rowptr,
-                                               h.R, h.J, h.props, h.ntot, h.coke, h.dstatus);
+                                               h.R, h.J, h.props, h.ntot, h.coke, h.dstatus, h.depth, h.bhp, h.Bv,
+                                               h.Cv, h.Fq, h.Dq);
 }
 
 void launch_flux(Handle& h, cudaStream_t s) {
@@ -373,6 +456,11 @@ void launch_flux(Handle& h, cudaStream_t s) {
 void launch_old_accumulation(Handle& h, cudaStream_t s) {
   int tb = 128;
   k_old_acc<<<(h.n + tb - 1) / tb, tb, 0, s>>>(h.P, h.u_n, h.coke_n, h.phi_ref, h.acc_n);
+}
+
+void launch_well_equations(Handle& h, cudaStream_t s) {
+  if (h.nwc == 0) return;
+  k_well_eq<<<1, 32, 0, s>>>(h.nwc, h.cw, h.Fq, h.Dq, h.bhp, h.R + (size_t)h.n * 8, h.Dw, h.scal + 3);
 }
 
 void launch_norms(Handle& h, cudaStream_t s) {

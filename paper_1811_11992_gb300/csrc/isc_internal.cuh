@@ -71,6 +71,16 @@ struct WellSlot {
   double bhp;                 // producer
   double share;               // injector: WI / sum of the well's WI
   double src[7];              // injector: mol/s per component and J/s
+  int wc;                     // coupled producer: its index among the coupled wells, else -1
+  int control;                // coupled producer: ISC_CTRL_*
+  double zref;                // coupled producer: depth of the bottom-hole pressure
+};
+
+// One coupled producer (bottom-hole pressure unknown) on the device.
+struct CoupledWell {
+  int control;
+  int first, count;           // slot range
+  double target;
 };
 
 // Host record of one well (the slots of a well are contiguous).
@@ -148,6 +158,16 @@ struct Handle {
   WellSlot* slots = nullptr;
   int nslots = 0;
   double *wx = nullptr, *wy = nullptr, *wz = nullptr;  // face weights d ln T / d ln k_lo, indexed by lo
+  // coupled producers: count, vector length of the bordered system (8N + nwc)
+  int nwc = 0;
+  int vlen = 0;                                   // logical length of a Krylov vector
+  int vstride = 0;                                // its storage stride (vlen rounded up to 8 doubles)
+  CoupledWell* cw = nullptr;                      // nwc
+  double *bhp = nullptr, *bhp_n = nullptr;        // iterate and accepted bottom-hole pressures (nwc)
+  double *Bv = nullptr, *Cv = nullptr;            // border per slot (nslots x 8)
+  double *Fq = nullptr, *Dq = nullptr;            // per-slot parts of F_w and D_w (nslots)
+  double* Dw = nullptr;                           // dF_w/d bhp_w (nwc)
+  std::vector<double> h_bhp_init;
   // sensitivity parameters: creation-time permeabilities and well indices, the
   // per-cell ln k multipliers and the host copies they generate
   std::vector<double> h_perm0, h_WI0, h_lnk;
@@ -200,6 +220,11 @@ void launch_props(Handle& h, cudaStream_t s);
 void launch_flux(Handle& h, cudaStream_t s);
 void launch_old_accumulation(Handle& h, cudaStream_t s);
 void launch_norms(Handle& h, cudaStream_t s);
+void launch_well_equations(Handle& h, cudaStream_t s);
+// bordered-system pieces of the coupled producers (isc_linalg.cu)
+void launch_well_border_spmv(Handle& h, const double* x, double* y, cudaStream_t s);
+void launch_well_prec(Handle& h, const double* r, double* z, cudaStream_t s);
+void launch_well_update(Handle& h, cudaStream_t s);
 void launch_init_equilibrium(Handle& h, double p0, double T0, double Sw0, double So0, double xlo0,
                              const double* y_rest, cudaStream_t s);
 // linear algebra (isc_linalg.cu)

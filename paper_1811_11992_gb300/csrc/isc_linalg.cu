@@ -44,7 +44,9 @@ __device__ __forceinline__ bool nbr_exists(int nx, int ny, int nz, int c, int d,
 }
 
 __global__ void __launch_bounds__(256) k_gj(int n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                                            double* __restrict__ J, double* __restrict__ R, int* __restrict__ dstatus) {
+                                            double* __restrict__ J, double* __restrict__ R, int* __restrict__ dstatus,
+                                            const int32_t* __restrict__ well_slot, const WellSlot* __restrict__ slots,
+                                            double* __restrict__ Bv) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= n) return;
@@ -55,6 +57,13 @@ __global__ void __launch_bounds__(256) k_gj(int n, const int32_t* __restrict__ r
   for (int s = 0; s < nb; ++s)
     if (col[b0 + s] == i) d = s;
   const int nc = nb * 8;
+  // a perforation of a coupled producer carries its border column dF/d bhp as
+  // one more column of the augmented row (at most 7*8 + 2 = 58 of 64 columns)
+  int bs = -1;
+  if (Bv) {
+    const int sl = well_slot[i];
+    if (sl >= 0 && slots[sl].wc >= 0) bs = sl;
+  }
   double a[2][8];
 #pragma unroll
   for (int m = 0; m < 2; ++m) {
@@ -66,6 +75,8 @@ __global__ void __launch_bounds__(256) k_gj(int n, const int32_t* __restrict__ r
         v = J[(size_t)(b0 + cc / 8) * BB + r * 8 + (cc & 7)];
       else if (cc == nc)
         v = R[(size_t)i * 8 + r];
+      else if (cc == nc + 1 && bs >= 0)
+        v = Bv[(size_t)bs * 8 + r];
       a[m][r] = v;
     }
   }
@@ -144,8 +155,64 @@ __global__ void __launch_bounds__(256) k_gj(int n, const int32_t* __restrict__ r
     } else if (cc == nc) {
 #pragma unroll
       for (int r = 0; r < 8; ++r) R[(size_t)i * 8 + r] = a[m][r];
+    } else if (cc == nc + 1 && bs >= 0) {
+#pragma unroll
+      for (int r = 0; r < 8; ++r) Bv[(size_t)bs * 8 + r] = a[m][r];
     }
   }
+}
+
+// ----------------------------------------------------- coupled producers
+// Border of the Newton system: y_c(cell of q) += B_q x_w(well of q)
+__global__ void k_well_border_cells(int nslots, const WellSlot* __restrict__ slots, const double* __restrict__ Bv,
+                                    const double* __restrict__ x, double* __restrict__ y, size_t n8) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nslots * 8) return;
+  const int q = e >> 3, r = e & 7;
+  const int wc = slots[q].wc;
+  if (wc < 0) return;
+  y[(size_t)slots[q].cell * 8 + r] += Bv[(size_t)q * 8 + r] * x[n8 + wc];
+}
+
+// well rows: y_w = sum_q C_q . x_c(cell of q) + D_w x_w (one thread per well)
+__global__ void k_well_border_rows(int nwc, const CoupledWell* __restrict__ cw, const WellSlot* __restrict__ slots,
+                                   const double* __restrict__ Cv, const double* __restrict__ Dw,
+                                   const double* __restrict__ x, double* __restrict__ y, size_t n8) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= nwc) return;
+  const CoupledWell c = cw[w];
+  double s = Dw[w] * x[n8 + w];
+  for (int q = c.first; q < c.first + c.count; ++q) {
+    const double* xc = x + (size_t)slots[q].cell * 8;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += Cv[(size_t)q * 8 + k] * xc[k];
+  }
+  y[n8 + w] = s;
+}
+
+// block lower-triangular preconditioner, well part: z_w = (r_w - sum_q C_q . z_c) / D_w
+__global__ void k_well_prec(int nwc, const CoupledWell* __restrict__ cw, const WellSlot* __restrict__ slots,
+                            const double* __restrict__ Cv, const double* __restrict__ Dw, const double* __restrict__ r,
+                            double* __restrict__ z, size_t n8) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= nwc) return;
+  const CoupledWell c = cw[w];
+  double s = r[n8 + w];
+  for (int q = c.first; q < c.first + c.count; ++q) {
+    const double* zc = z + (size_t)slots[q].cell * 8;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s -= Cv[(size_t)q * 8 + k] * zc[k];
+  }
+  z[n8 + w] = s / Dw[w];
+}
+
+// bhp_w += du_w with the pressure safeguard |d bhp| <= max_dp_frac bhp
+__global__ void k_well_update(int nwc, const double* __restrict__ du, size_t n8, double max_dp_frac,
+                              double* __restrict__ bhp) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= nwc) return;
+  const double b = bhp[w];
+  bhp[w] = b + fmin(fmax(du[n8 + w], -max_dp_frac * b), max_dp_frac * b);
 }
 
 __global__ void __launch_bounds__(256) k_spmv(int n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
@@ -476,7 +543,25 @@ int grid_for(size_t work, int tb) {
 
 void launch_gj(Handle& h, cudaStream_t s) {
   int tb = 256;
-  k_gj<<<(h.n * 32 + tb - 1) / tb, tb, 0, s>>>(h.n, h.rowptr, h.col, h.J, h.R, h.dstatus);
+  k_gj<<<(h.n * 32 + tb - 1) / tb, tb, 0, s>>>(h.n, h.rowptr, h.col, h.J, h.R, h.dstatus, h.well_slot, h.slots,
+                                               h.nwc > 0 ? h.Bv : nullptr);
+}
+
+void launch_well_border_spmv(Handle& h, const double* x, double* y, cudaStream_t s) {
+  if (h.nwc == 0) return;
+  const size_t n8 = (size_t)h.n * 8;
+  k_well_border_cells<<<(h.nslots * 8 + 127) / 128, 128, 0, s>>>(h.nslots, h.slots, h.Bv, x, y, n8);
+  k_well_border_rows<<<(h.nwc + 31) / 32, 32, 0, s>>>(h.nwc, h.cw, h.slots, h.Cv, h.Dw, x, y, n8);
+}
+
+void launch_well_prec(Handle& h, const double* r, double* z, cudaStream_t s) {
+  if (h.nwc == 0) return;
+  k_well_prec<<<(h.nwc + 31) / 32, 32, 0, s>>>(h.nwc, h.cw, h.slots, h.Cv, h.Dw, r, z, (size_t)h.n * 8);
+}
+
+void launch_well_update(Handle& h, cudaStream_t s) {
+  if (h.nwc == 0) return;
+  k_well_update<<<(h.nwc + 31) / 32, 32, 0, s>>>(h.nwc, h.du, (size_t)h.n * 8, h.opt.max_dp_frac, h.bhp);
 }
 
 void launch_spmv(int nrows, const int32_t* rowptr, const int32_t* col, const double* val, const double* x, double* y,
@@ -515,20 +600,20 @@ void launch_update(Handle& h, cudaStream_t s) {
 }
 
 void launch_mdot(Handle& h, const double* V, int nvec, const double* w, int off, cudaStream_t s) {
-  const int len = h.n * 8;
+  const int len = h.vlen;
   dim3 grid(h.red_blocks, (nvec + DOT_G - 1) / DOT_G);
-  k_mdot<<<grid, RED_THREADS, 0, s>>>(len, V, (size_t)len, nvec, w, h.partial, h.red_counter, h.scal + off);
+  k_mdot<<<grid, RED_THREADS, 0, s>>>(len, V, (size_t)h.vstride, nvec, w, h.partial, h.red_counter, h.scal + off);
 }
 
 void launch_maxpy_norm(Handle& h, double* w, const double* V, int nvec, int coef_off, int out_off, cudaStream_t s) {
-  const int len = h.n * 8;
-  k_maxpy_norm<<<h.red_blocks, RED_THREADS, 0, s>>>(len, w, V, (size_t)len, nvec, h.scal + coef_off, h.partial,
+  const int len = h.vlen;
+  k_maxpy_norm<<<h.red_blocks, RED_THREADS, 0, s>>>(len, w, V, (size_t)h.vstride, nvec, h.scal + coef_off, h.partial,
                                                     h.red_counter, h.scal + out_off);
 }
 
 void launch_maxpy(Handle& h, double* w, const double* V, int nvec, int coef_off, double sign, cudaStream_t s) {
-  const int len = h.n * 8;
-  k_maxpy<<<grid_for(len, 256), 256, 0, s>>>(len, w, V, (size_t)len, nvec, h.scal + coef_off, sign);
+  const int len = h.vlen;
+  k_maxpy<<<grid_for(len, 256), 256, 0, s>>>(len, w, V, (size_t)h.vstride, nvec, h.scal + coef_off, sign);
 }
 
 void launch_axpby(int n, double a, const double* x, double b, double* y, cudaStream_t s) {

@@ -67,7 +67,9 @@ class isc_reactions(C.Structure):
 
 class isc_well(C.Structure):
     _fields_ = [("kind", C.c_int32), ("n_perf", C.c_int32), ("cells", c_int32_p), ("WI", c_double_p),
-                ("target", C.c_double), ("inj_y", D6), ("inj_T", C.c_double), ("inj_phase", C.c_int32)]
+                ("target", C.c_double), ("inj_y", C.c_double * 6), ("inj_T", C.c_double),
+                ("inj_phase", C.c_int32), ("control", C.c_int32), ("ref_depth", C.c_double),
+                ("bhp_init", C.c_double)]
 
 
 class isc_wells(C.Structure):
@@ -148,6 +150,10 @@ _SIGS = {
     "isc_bilu0_apply_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
                                           C.c_void_p, C.c_void_p, C.c_void_p]),
     "isc_set_parameters": (C.c_int, [C.c_void_p, c_double_p, c_double_p, c_double_p]),
+    "isc_num_coupled_wells": (C.c_int32, [C.c_void_p]),
+    "isc_set_well_bhp": (C.c_int, [C.c_void_p, c_double_p]),
+    "isc_get_well_bhp": (C.c_int, [C.c_void_p, c_double_p]),
+    "isc_get_well_system": (C.c_int, [C.c_void_p, c_double_p, c_double_p, c_double_p, c_double_p]),
     "isc_get_parameters": (C.c_int, [C.c_void_p, c_double_p, c_double_p, c_double_p]),
     "isc_adjoint": (C.c_int, [C.c_void_p, C.POINTER(isc_adjoint_spec), c_double_p, c_double_p, c_double_p,
                               c_double_p, C.POINTER(isc_adjoint_info)]),
@@ -252,6 +258,9 @@ class Simulator:
             _fill(wl[i].inj_y, w.inj_y)
             wl[i].inj_T = float(w.inj_T)
             wl[i].inj_phase = int(getattr(w, "inj_phase", 2))
+            wl[i].control = int(getattr(w, "control", 0))
+            wl[i].ref_depth = float(getattr(w, "ref_depth", 0.0))
+            wl[i].bhp_init = float(getattr(w, "bhp_init", 0.0))
         wells = isc_wells(len(case.wells), wl)
         if options is None:
             options = default_options(**opt_kw)
@@ -264,6 +273,7 @@ class Simulator:
             raise IscError(st, "isc_create failed")
         self.h = h
         self.nnzb = lib.isc_nnzb(h)
+        self.nwc = lib.isc_num_coupled_wells(h)
 
     def _k(self, a):
         self._keep.append(a)
@@ -373,7 +383,9 @@ class Simulator:
         return c
 
     def spmv(self, x):
-        """y = A x for x given as (8, N)."""
+        """y = A x for x given as (8, N) (no coupled producers; else spmv_full)."""
+        if self.nwc:
+            raise ValueError("the system has coupled producers: use spmv_full")
         xb = np.ascontiguousarray(np.asarray(x, np.float64).reshape(8, self.n).T)
         y = np.empty((self.n, 8))
         self._check(self.lib.isc_spmv(self.h, _dp(xb), _dp(y)))
@@ -383,6 +395,8 @@ class Simulator:
         self._check(self.lib.isc_build_preconditioner(self.h))
 
     def precond_apply(self, r):
+        if self.nwc:
+            raise ValueError("the system has coupled producers: use precond_apply_full")
         rb = np.ascontiguousarray(np.asarray(r, np.float64).reshape(8, self.n).T)
         z = np.empty((self.n, 8))
         self._check(self.lib.isc_precond_apply(self.h, _dp(rb), _dp(z)))
@@ -395,6 +409,37 @@ class Simulator:
 
     def reset_stats(self):
         self._check(self.lib.isc_reset_stats(self.h))
+
+    # ---------------------------------------------------- coupled producers
+    def well_bhp(self):
+        b = np.empty(max(self.nwc, 1))
+        self._check(self.lib.isc_get_well_bhp(self.h, _dp(b)))
+        return b[:self.nwc]
+
+    def set_well_bhp(self, bhp):
+        b = np.ascontiguousarray(bhp, np.float64).reshape(self.nwc)
+        self._check(self.lib.isc_set_well_bhp(self.h, _dp(b)))
+
+    def well_system(self):
+        """(B (nperf, 8), C (nperf, 8), D (nwc,), Fw (nwc,)) after assemble."""
+        nperf = sum(len(w.cells) for w in self.case.wells if w.kind == 2)
+        B, Cm = np.empty((max(nperf, 1), 8)), np.empty((max(nperf, 1), 8))
+        D, Fw = np.empty(max(self.nwc, 1)), np.empty(max(self.nwc, 1))
+        self._check(self.lib.isc_get_well_system(self.h, _dp(B), _dp(Cm), _dp(D), _dp(Fw)))
+        return B[:nperf], Cm[:nperf], D[:self.nwc], Fw[:self.nwc]
+
+    def spmv_full(self, x):
+        """y = [J B; C D] x on the flat vector (8N block-major, then the wells)."""
+        x = np.ascontiguousarray(x, np.float64).reshape(-1)
+        y = np.empty_like(x)
+        self._check(self.lib.isc_spmv(self.h, _dp(x), _dp(y)))
+        return y
+
+    def precond_apply_full(self, r):
+        r = np.ascontiguousarray(r, np.float64).reshape(-1)
+        z = np.empty_like(r)
+        self._check(self.lib.isc_precond_apply(self.h, _dp(r), _dp(z)))
+        return z
 
     # -------------------------------------------------------- sensitivities
     def set_parameters(self, log_k=None, Ea=None, lnA=None):

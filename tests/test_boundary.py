@@ -44,3 +44,35 @@ def test_missing_library_fails_loudly(tmp_path):
             isc.load_library(str(tmp_path / "nope.so"))
     finally:
         isc._lib = saved
+
+
+def test_ctypes_structures_match_the_header(tmp_path):
+    """Every structure the binding declares has the header's size and field
+    offsets (a C probe compiled against include/isc.h)."""
+    import ctypes
+    import shutil
+    import subprocess
+    from paper_1811_11992_gb300 import isc
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [getattr(isc, n) for n in dir(isc)
+               if n.startswith("isc_") and isinstance(getattr(isc, n), type)
+               and issubclass(getattr(isc, n), ctypes.Structure)]
+    assert len(structs) >= 10
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "isc.h"', "int main(void) {"]
+    for S in structs:
+        lines.append(f'printf("{S.__name__} size %zu\\n", sizeof({S.__name__}));')
+        for f in S._fields_:
+            lines.append(f'printf("{S.__name__} {f[0]} %zu\\n", offsetof({S.__name__}, {f[0]}));')
+    lines.append("return 0; }")
+    src = tmp_path / "probe.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "probe"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for S in structs:
+        assert got[(S.__name__, "size")] == ctypes.sizeof(S), S.__name__
+        for f in S._fields_:
+            assert got[(S.__name__, f[0])] == getattr(S, f[0]).offset, (S.__name__, f[0])
