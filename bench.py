@@ -47,6 +47,8 @@ def parse():
                     help="time only the headline step (no mixed, CPR-PF, adjoint or end-to-end legs); for profiling")
     ap.add_argument("--grid", default=None,
                     help="NXxNYxNZ: run the same field recipe on a smaller grid (profiling captures)")
+    ap.add_argument("--workload", default="field", choices=["field", "mixed", "large"],
+                    help="field: 60x60x20 (the headline); mixed: 100x100x30; large: 200x200x50, 3 facies, 5-spot")
     return ap.parse_args()
 
 
@@ -126,19 +128,21 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def field_case(grid=None):
+def field_case(grid=None, workload="field"):
     import isc_inputs as inp
     if grid:
         nx, ny, nz = (int(v) for v in grid.lower().split("x"))
         return inp.field_case(nx, ny, nz, 0, 1, f"field {nx}x{ny}x{nz}", 30 * inp.DAY, 40)
-    return inp.config(2)
+    return inp.config({"field": 2, "mixed": 3, "large": 5}[workload])
 
 
-def workload_config(case, dt, extra):
-    c = {"workload": f"field {case.nx}x{case.ny}x{case.nz} ({case.n} cells, 8 unknowns/cell), first Newton step of "
+def workload_config(case, dt, extra, nnzb=None):
+    nnzb = nnzb if nnzb is not None else case.n * 7
+    c = {"workload": f"{case.name} ({case.n} cells, 8 unknowns/cell), first Newton step of "
                      f"the first time step (dt {dt:.0f} s) from the ignited initial state",
          "solver": "GMRES(30), block ILU(0), Gauss-Jordan decoupling, FP64, tol_lin 1e-6",
-         "l2": "inputs larger than L2: the FP64 Jacobian (252 MB) and staged properties (83 MB) exceed the 129 MB L2"}
+         "l2": f"inputs larger than L2: the FP64 Jacobian ({nnzb * 512 / 1e6:.0f} MB) and staged properties "
+               f"({case.n * 16 * 9 * 8 / 1e6:.0f} MB) exceed the 129 MB L2"}
     c.update(extra)
     return c
 
@@ -154,7 +158,7 @@ def run_isc(args):
     torch.cuda.set_device(local)
     from paper_1811_11992_gb300 import build, isc
     build.build()
-    case = field_case(args.grid)
+    case = field_case(args.grid, args.workload)
     dt = case.dt0
     g = isc.Simulator(case, profile=1)
     g.init_equilibrium()
@@ -277,7 +281,8 @@ def run_isc(args):
         "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_config(case, dt, {"parallelism": f"replicas x{world}",
-                                             "krylov_iterations_per_step": statistics.median(kry) if kry else None}),
+                                             "krylov_iterations_per_step": statistics.median(kry) if kry else None},
+                                  g.nnzb),
         "e2e": e2e,
         "gpu_launches": launches,
         "kernel_ms": {k: round(v["ms"], 3) for k, v in stats.items()},
@@ -287,9 +292,9 @@ def run_isc(args):
         "mixed": mixed,
         "cpr": cpr_block,
     }
-    if not args.no_adjoint and not args.no_extras and args.grid is None:
+    if not args.no_adjoint and not args.no_extras and args.grid is None and args.workload == "field":
         line["adjoint"] = adjoint_block()
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "field" and args.grid is None:
         line["cpu_baseline"] = cpu_baseline(max_seconds=30.0)
     g.close()
     if rank == 0:
