@@ -190,12 +190,9 @@ int build_prec(isc_handle* h) {
       e |= dalloc(h, &h->vec32, (size_t)h->n * 16);
       if (e) return ISC_ERR_NOMEM;
     }
-    Region rg(h, ISC_K_ILU_FACTOR, mixed ? 3 : 1);
+    // mixed precision: FP32 copy of the blocks, then the factorisation in FP32
+    Region rg(h, ISC_K_ILU_FACTOR, mixed ? 2 : 1);
     launch_ilu_factor(*h, h->stream);
-    if (mixed) {
-      launch_to_f32((size_t)h->nnzb * BB, h->J, h->J32, h->stream);
-      launch_to_f32((size_t)h->n * BB, h->dinv, h->dinv32, h->stream);
-    }
   } else if (h->opt.prec == ISC_PREC_BJACOBI) {
     Region rg(h, ISC_K_ILU_FACTOR, 1);
     launch_bjacobi_factor(*h, h->stream);

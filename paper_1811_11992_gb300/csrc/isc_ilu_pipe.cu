@@ -421,19 +421,21 @@ __device__ __forceinline__ int slot_of(int nx, int ny, int nz, int c, int d) {
 // pivoting), same pencil pipeline; the hand-off is the neighbour's D^-1 block (NaN-filled before).
 constexpr int FWARPS = 4;
 
+template <typename T>
 __global__ void __launch_bounds__(FWARPS * 32) k_ilu_factor_pipe(int nx, int ny, int nz,
                                                                  const int32_t* __restrict__ rowptr,
-                                                                 const double* __restrict__ A, double* __restrict__ Dinv,
+                                                                 const T* __restrict__ A, T* __restrict__ Dinv,
                                                                  int* __restrict__ pipe, int* __restrict__ dstatus) {
-  __shared__ double sm[FWARPS][6][64];
+  using T2 = typename V2<T>::t;
+  __shared__ T sm[FWARPS][6][64];
   const int lane = threadIdx.x & 31;
   const int wid = threadIdx.x >> 5;
-  double* sD = sm[wid][0];
-  double* sI = sm[wid][1];
-  double* sL = sm[wid][2];
-  double* sU = sm[wid][3];
-  double* sK = sm[wid][4];
-  double* sP = sm[wid][5];  // D^-1 of the previous cell of this pencil
+  T* sD = sm[wid][0];
+  T* sI = sm[wid][1];
+  T* sL = sm[wid][2];
+  T* sU = sm[wid][3];
+  T* sK = sm[wid][4];
+  T* sP = sm[wid][5];  // D^-1 of the previous cell of this pencil
   const int r = lane >> 2, c = (lane & 3) * 2;
   const int npen = ny * nz, nxy = nx * ny;
   int* counter = pipe;
@@ -450,7 +452,7 @@ __global__ void __launch_bounds__(FWARPS * 32) k_ilu_factor_pipe(int nx, int ny,
       const int i = base_jk + x;
       const int base = rowptr_of(nx, ny, nz, i);
       const int nlow = (k > 0) + (j > 0) + (x > 0);
-      double2 d = ld_nc2(A + (size_t)(base + nlow) * BB + 2 * lane);
+      T2 d = ld_nc2(A + (size_t)(base + nlow) * BB + 2 * lane);
       // lower neighbours in pattern order -z, -y, -x
 #pragma unroll
       for (int dl = 0; dl < 3; ++dl) {
@@ -459,13 +461,14 @@ __global__ void __launch_bounds__(FWARPS * 32) k_ilu_factor_pipe(int nx, int ny,
         const int kk = (dl == 0) ? i - nxy : (dl == 1) ? i - nx : i - 1;
         const int sl = slot_of(nx, ny, nz, i, dl);
         const int su = slot_of(nx, ny, nz, kk, 6 - dl);
-        const double2 aik = ld_nc2(A + (size_t)(base + sl) * BB + 2 * lane);
-        const double2 aki = ld_nc2(A + (size_t)(rowptr_of(nx, ny, nz, kk) + su) * BB + 2 * lane);
-        double2 dk;
+        const T2 aik = ld_nc2(A + (size_t)(base + sl) * BB + 2 * lane);
+        const T2 aki = ld_nc2(A + (size_t)(rowptr_of(nx, ny, nz, kk) + su) * BB + 2 * lane);
+        T2 dk;
         if (dl < 2) {
-          if (!poll_vec<double>(Dinv + (size_t)kk * BB, 2 * lane, dk, abortf, dstatus)) return;
+          if (!poll_vec<T>(Dinv + (size_t)kk * BB, 2 * lane, dk, abortf, dstatus)) return;
         } else {
-          dk = make_double2(sP[2 * lane], sP[2 * lane + 1]);
+          dk.x = sP[2 * lane];
+          dk.y = sP[2 * lane + 1];
         }
         __syncwarp();
         sL[2 * lane] = aik.x;
@@ -476,7 +479,7 @@ __global__ void __launch_bounds__(FWARPS * 32) k_ilu_factor_pipe(int nx, int ny,
         sK[2 * lane + 1] = dk.y;
         __syncwarp();
         // M = D_k^-1 A_ki (entries (r, c), (r, c+1))
-        double m0 = 0.0, m1 = 0.0;
+        T m0 = T(0), m1 = T(0);
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           m0 = fma(sK[r * 8 + q], sU[q * 8 + c], m0);
@@ -486,7 +489,7 @@ __global__ void __launch_bounds__(FWARPS * 32) k_ilu_factor_pipe(int nx, int ny,
         sU[r * 8 + c] = m0;  // reuse sU for M
         sU[r * 8 + c + 1] = m1;
         __syncwarp();
-        double s0 = 0.0, s1 = 0.0;
+        T s0 = T(0), s1 = T(0);
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           s0 = fma(sL[r * 8 + q], sU[q * 8 + c], s0);
@@ -499,28 +502,28 @@ __global__ void __launch_bounds__(FWARPS * 32) k_ilu_factor_pipe(int nx, int ny,
       // invert D by Gauss-Jordan with partial pivoting
       sD[2 * lane] = d.x;
       sD[2 * lane + 1] = d.y;
-      sI[2 * lane] = (r == c) ? 1.0 : 0.0;
-      sI[2 * lane + 1] = (r == c + 1) ? 1.0 : 0.0;
+      sI[2 * lane] = (r == c) ? T(1) : T(0);
+      sI[2 * lane + 1] = (r == c + 1) ? T(1) : T(0);
       __syncwarp();
       bool bad = false;
       for (int kp = 0; kp < 8; ++kp) {
         int piv = kp;
-        double best = -1.0;
+        T best = T(-1);
         for (int q = kp; q < 8; ++q) {
-          const double v = fabs(sD[q * 8 + kp]);
+          const T v = fabs(sD[q * 8 + kp]);
           if (v > best) {
             best = v;
             piv = q;
           }
         }
-        if (!(best > 0.0) || !isfinite(best)) {
+        if (!(best > T(0)) || !isfinite(best)) {
           bad = true;
           break;
         }
         if (piv != kp && r == kp) {
 #pragma unroll
           for (int e = 0; e < 2; ++e) {
-            double t1 = sD[kp * 8 + c + e];
+            T t1 = sD[kp * 8 + c + e];
             sD[kp * 8 + c + e] = sD[piv * 8 + c + e];
             sD[piv * 8 + c + e] = t1;
             t1 = sI[kp * 8 + c + e];
@@ -529,8 +532,8 @@ __global__ void __launch_bounds__(FWARPS * 32) k_ilu_factor_pipe(int nx, int ny,
           }
         }
         __syncwarp();
-        const double inv = 1.0 / sD[kp * 8 + kp];
-        const double f = sD[r * 8 + kp];
+        const T inv = T(1) / sD[kp * 8 + kp];
+        const T f = sD[r * 8 + kp];
         __syncwarp();
         if (r == kp) {
           sD[kp * 8 + c] *= inv;
@@ -554,7 +557,7 @@ __global__ void __launch_bounds__(FWARPS * 32) k_ilu_factor_pipe(int nx, int ny,
         }
         return;
       }
-      const double o0 = sI[2 * lane], o1 = sI[2 * lane + 1];
+      const T o0 = sI[2 * lane], o1 = sI[2 * lane + 1];
       st_relaxed(Dinv + (size_t)i * BB + 2 * lane, o0);
       st_relaxed(Dinv + (size_t)i * BB + 2 * lane + 1, o1);
       sP[2 * lane] = o0;
@@ -567,13 +570,23 @@ __global__ void __launch_bounds__(FWARPS * 32) k_ilu_factor_pipe(int nx, int ny,
 
 }  // namespace
 
+// Factor the decoupled blocks: FP64 into dinv, or under mixed precision FP32
+// from the FP32 copy of the blocks (J32, written first) into dinv32.
 void launch_ilu_factor_pipe(Handle& h, cudaStream_t s) {
   const int npen = h.ny * h.nz;
-  cudaMemsetAsync(h.pipe, 0, 2 * sizeof(int), s);
-  cudaMemsetAsync(h.dinv, 0xff, sizeof(double) * (size_t)h.n * BB, s);  // NaN sentinel
   const int warps = npen < 152 * 8 ? npen : 152 * 8;
-  k_ilu_factor_pipe<<<(warps + FWARPS - 1) / FWARPS, FWARPS * 32, 0, s>>>(h.nx, h.ny, h.nz, h.rowptr, h.J, h.dinv,
-                                                                          h.pipe, h.dstatus);
+  const int blocks = (warps + FWARPS - 1) / FWARPS;
+  cudaMemsetAsync(h.pipe, 0, 2 * sizeof(int), s);
+  if (h.opt.precision == ISC_PRECISION_MIXED) {
+    launch_to_f32((size_t)h.nnzb * BB, h.J, h.J32, s);
+    cudaMemsetAsync(h.dinv32, 0xff, sizeof(float) * (size_t)h.n * BB, s);  // NaN sentinel
+    k_ilu_factor_pipe<float><<<blocks, FWARPS * 32, 0, s>>>(h.nx, h.ny, h.nz, h.rowptr, h.J32, h.dinv32, h.pipe,
+                                                            h.dstatus);
+    return;
+  }
+  cudaMemsetAsync(h.dinv, 0xff, sizeof(double) * (size_t)h.n * BB, s);  // NaN sentinel
+  k_ilu_factor_pipe<double><<<blocks, FWARPS * 32, 0, s>>>(h.nx, h.ny, h.nz, h.rowptr, h.J, h.dinv, h.pipe,
+                                                           h.dstatus);
 }
 
 constexpr int SWEEP_R = 8;  // cells staged ahead in each warp's shared-memory ring
