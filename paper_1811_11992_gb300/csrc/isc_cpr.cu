@@ -188,6 +188,76 @@ __device__ __forceinline__ void zline_column(const MGLevel<T>& L, int cx, int cy
   }
 }
 
+// The same column solve by one warp (columns of at most 64 z-levels): lane l
+// holds levels 2l and 2l+1. With the factors precomputed both recurrences
+// are first-order linear, y_k = g_k + a_k y_{k-1} and x_k = y_k + b_k x_{k+1}
+// (b = -f), so each runs as a Kogge-Stone scan of affine maps across the
+// lanes: one round of independent loads and ten shuffle steps instead of a
+// chain of nz dependent steps. Levels at or beyond nz are identity maps.
+template <typename T>
+__device__ __forceinline__ void zline_column_warp(const MGLevel<T>& L, int cx, int cy, bool zero_guess) {
+  const unsigned FULLM = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int nxy = L.nx * L.ny, n = L.n, i0 = cx + L.nx * cy;
+  const T* __restrict__ c = L.c;
+  T* __restrict__ x = L.x;
+  T g[2], a[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int k = 2 * lane + h, i = i0 + nxy * k;
+    g[h] = T(0);
+    a[h] = T(0);
+    if (k < L.nz) {
+      T rhs = L.b[i];
+      if (!zero_guess) {
+        if (cy > 0) rhs -= c[(size_t)1 * n + i] * x[i - L.nx];
+        if (cx > 0) rhs -= c[(size_t)2 * n + i] * x[i - 1];
+        if (cx < L.nx - 1) rhs -= c[(size_t)4 * n + i] * x[i + 1];
+        if (cy < L.ny - 1) rhs -= c[(size_t)5 * n + i] * x[i + L.nx];
+      }
+      const T e = L.e[i];
+      g[h] = e * rhs;
+      a[h] = (k > 0) ? -c[(size_t)0 * n + i] * e : T(0);
+    }
+  }
+  // forward: the lane's map y_{2l-1} -> y_{2l+1}, then the inclusive scan over lanes
+  T A = a[1] * a[0], G = fma(a[1], g[0], g[1]);
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const T Ad = __shfl_up_sync(FULLM, A, d), Gd = __shfl_up_sync(FULLM, G, d);
+    if (lane >= d) {
+      G = fma(A, Gd, G);
+      A = A * Ad;
+    }
+  }
+  T yprev = __shfl_up_sync(FULLM, G, 1);  // y_{2l-1}
+  if (lane == 0) yprev = T(0);
+  const T y0 = fma(a[0], yprev, g[0]);
+  const T y1 = G;
+  // backward: x_k = y_k + b_k x_{k+1}; the lane's map x_{2l+2} -> x_{2l}
+  T bq[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int k = 2 * lane + h;
+    bq[h] = (k < L.nz) ? -L.f[i0 + nxy * k] : T(0);
+  }
+  T B = bq[0] * bq[1], X = fma(bq[0], y1, y0);
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const T Bd = __shfl_down_sync(FULLM, B, d), Xd = __shfl_down_sync(FULLM, X, d);
+    if (lane + d < 32) {
+      X = fma(B, Xd, X);
+      B = B * Bd;
+    }
+  }
+  T xnext = __shfl_down_sync(FULLM, X, 1);  // x_{2l+2}
+  if (lane == 31) xnext = T(0);
+  const T x0 = X;
+  const T x1 = fma(bq[1], xnext, y1);
+  if (2 * lane < L.nz) x[i0 + nxy * (2 * lane)] = x0;
+  if (2 * lane + 1 < L.nz) x[i0 + nxy * (2 * lane + 1)] = x1;
+}
+
 // b_C = sum over the aggregate of (b_F - A_F x_F)
 template <typename T>
 __device__ __forceinline__ void restrict_cell(const MGLevel<T>& F, const MGLevel<T>& C, int I) {
@@ -258,10 +328,18 @@ __global__ void k_mg_factor(const MGLevel<T>* __restrict__ lv, int l) {
   if (t < L.nx * L.ny) factor_column(L, t % L.nx, t / L.nx);
 }
 
-template <typename T>
+constexpr int ZWARP_MAX = 64;  // columns this short are solved by one warp (two levels per lane)
+
+// one warp per column of the colour (WARP: nz <= ZWARP_MAX), else one thread per column
+template <typename T, bool WARP>
 __global__ void k_zline(const MGLevel<T>* __restrict__ lv, int l, int colour, int zero_guess) {
   const MGLevel<T> L = lv[l];
   int cx, cy;
+  if (WARP) {
+    const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;  // the same in every lane
+    if (colour_column(L.nx, L.ny, colour, q, &cx, &cy)) zline_column_warp(L, cx, cy, zero_guess != 0);
+    return;
+  }
   if (colour_column(L.nx, L.ny, colour, blockIdx.x * blockDim.x + threadIdx.x, &cx, &cy))
     zline_column(L, cx, cy, zero_guess != 0);
 }
@@ -280,38 +358,46 @@ __global__ void k_mg_prolong(const MGLevel<T>* __restrict__ lv, int l) {
   if (f < F.n) prolong_cell(C, F, f);
 }
 
-template <typename T>
-__device__ __forceinline__ void block_smooth(const MGLevel<T>& L, bool zero_guess) {
-  for (int colour = 0; colour < 2; ++colour) {
-    const int cnt = colour_count(L.nx, L.ny, colour);
-    for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
-      int cx, cy;
-      if (colour_column(L.nx, L.ny, colour, q, &cx, &cy)) zline_column(L, cx, cy, zero_guess && colour == 0);
+// all columns of one level (warps over columns when WARP)
+template <typename T, bool WARP>
+__device__ __forceinline__ void block_columns(const MGLevel<T>& L, int colour, bool zero_guess) {
+  const int cnt = colour < 0 ? L.nx * L.ny : colour_count(L.nx, L.ny, colour);
+  if (WARP) {
+    for (int q = threadIdx.x >> 5; q < cnt; q += blockDim.x >> 5) {
+      int cx = q % L.nx, cy = q / L.nx;
+      if (colour < 0 || colour_column(L.nx, L.ny, colour, q, &cx, &cy)) zline_column_warp(L, cx, cy, zero_guess);
     }
-    __syncthreads();
+  } else {
+    for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+      int cx = q % L.nx, cy = q / L.nx;
+      if (colour < 0 || colour_column(L.nx, L.ny, colour, q, &cx, &cy)) zline_column(L, cx, cy, zero_guess);
+    }
   }
+  __syncthreads();
+}
+
+template <typename T, bool WARP>
+__device__ __forceinline__ void block_smooth(const MGLevel<T>& L, bool zero_guess) {
+  block_columns<T, WARP>(L, 0, zero_guess);
+  block_columns<T, WARP>(L, 1, false);
 }
 
 // Levels l0 .. nlev-1 of the V-cycle in one thread block (b of level l0 is set).
-template <typename T>
-__global__ void __launch_bounds__(256) k_mg_coarse(const MGLevel<T>* __restrict__ lv, int l0, int nlev) {
+template <typename T, bool WARP>
+__global__ void __launch_bounds__(512) k_mg_coarse(const MGLevel<T>* __restrict__ lv, int l0, int nlev) {
   const int t = threadIdx.x, TT = blockDim.x;
   for (int l = l0; l < nlev - 1; ++l) {
     const MGLevel<T> L = lv[l], C = lv[l + 1];
-    block_smooth(L, true);
+    block_smooth<T, WARP>(L, true);
     for (int I = t; I < C.n; I += TT) restrict_cell(L, C, I);
     __syncthreads();
   }
-  {
-    const MGLevel<T> L = lv[nlev - 1];
-    for (int q = t; q < L.nx * L.ny; q += TT) zline_column(L, q % L.nx, q / L.nx, true);
-    __syncthreads();
-  }
+  block_columns<T, WARP>(lv[nlev - 1], -1, true);  // the single-column level: exact solve
   for (int l = nlev - 2; l >= l0; --l) {
     const MGLevel<T> L = lv[l], C = lv[l + 1];
     for (int f = t; f < L.n; f += TT) prolong_cell(C, L, f);
     __syncthreads();
-    block_smooth(L, false);
+    block_smooth<T, WARP>(L, false);
   }
 }
 
@@ -413,16 +499,28 @@ void pressure_t(Handle& h, const double* r, cudaStream_t s) {
   const MGLevel<T>* d = static_cast<const MGLevel<T>*>(W.d_levels);
   const int tb = 128;
   k_cpr_gather<T><<<nblk(h.n, tb), tb, 0, s>>>(h.n, r, lv[0].b);
+  // threads of a z-line pass: a warp per column (nz <= ZWARP_MAX) or a thread per column
+  const bool warp = h.nz <= ZWARP_MAX;
+  auto zline = [&](int l, int colour, int zero) {
+    const long long cnt = colour_count(lv[l].nx, lv[l].ny, colour);
+    if (warp)
+      k_zline<T, true><<<nblk(32 * cnt, tb), tb, 0, s>>>(d, l, colour, zero);
+    else
+      k_zline<T, false><<<nblk(cnt, tb), tb, 0, s>>>(d, l, colour, zero);
+  };
   for (int l = 0; l < W.ngrid; ++l) {
-    k_zline<T><<<nblk(colour_count(lv[l].nx, lv[l].ny, 0), tb), tb, 0, s>>>(d, l, 0, 1);
-    k_zline<T><<<nblk(colour_count(lv[l].nx, lv[l].ny, 1), tb), tb, 0, s>>>(d, l, 1, 0);
+    zline(l, 0, 1);
+    zline(l, 1, 0);
     k_mg_restrict<T><<<nblk(lv[l + 1].n, tb), tb, 0, s>>>(d, l);
   }
-  k_mg_coarse<T><<<1, 256, 0, s>>>(d, W.ngrid, W.nlev);
+  if (warp)
+    k_mg_coarse<T, true><<<1, 512, 0, s>>>(d, W.ngrid, W.nlev);
+  else
+    k_mg_coarse<T, false><<<1, 512, 0, s>>>(d, W.ngrid, W.nlev);
   for (int l = W.ngrid - 1; l >= 0; --l) {
     k_mg_prolong<T><<<nblk(lv[l].n, tb), tb, 0, s>>>(d, l);
-    k_zline<T><<<nblk(colour_count(lv[l].nx, lv[l].ny, 0), tb), tb, 0, s>>>(d, l, 0, 0);
-    k_zline<T><<<nblk(colour_count(lv[l].nx, lv[l].ny, 1), tb), tb, 0, s>>>(d, l, 1, 0);
+    zline(l, 0, 0);
+    zline(l, 1, 0);
   }
   k_cpr_residual<T><<<nblk((long long)h.n * 8, 256), 256, 0, s>>>(h.n, h.rowptr, h.col, W.col0, r, lv[0].x, W.r1);
 }

@@ -121,7 +121,7 @@ struct MGLevel {
   T *c, *x, *b, *e, *f;
 };
 constexpr int MG_AGG = 2;             // x-y aggregation factor (MG_AGG x MG_AGG fine columns per coarse column)
-constexpr int MG_BLOCK_CELLS = 8192;  // levels this small run inside one thread block
+constexpr int MG_BLOCK_CELLS = 2048;  // levels this small run inside one thread block
 
 // Workspace of the CPR-PF preconditioner (allocated on first use, for one precision).
 struct CprWork {
