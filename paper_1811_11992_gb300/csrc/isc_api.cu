@@ -114,7 +114,7 @@ int dalloc(isc_handle* h, T** p, size_t count) {
 void free_all(isc_handle* h) {
   void* ptrs[] = {h->rowptr, h->col, h->level_cells, h->phi_ref, h->depth, h->tx, h->ty, h->tz, h->well_slot,
                   h->slots, h->u, h->coke, h->u_n, h->coke_n, h->acc_n, h->props, h->R, h->J, h->ntot, h->du,
-                  h->rhs, h->dinv, h->J32, h->dinv32, h->vec32, h->V, h->Z, h->w, h->tmp, h->partial, h->scal, h->dstatus, h->pipe, h->red_counter,
+                  h->rhs, h->dinv, h->J32, h->dinv32, h->vec32, h->V, h->Z, h->w, h->tmp, h->partial, h->scal, h->dstatus, h->pipe, h->red_counter, h->gmres,
                   h->wx, h->wy, h->wz, h->cw, h->bhp, h->bhp_n, h->Dw, h->Bv, h->Cv, h->Fq, h->Dq, h->adj.store, h->adj.ubar, h->adj.cbar, h->adj.lam, h->adj.glnk, h->adj.grx,
                   h->adj.scond, h->adj.kd, h->adj.loss_cell, h->adj.sums, h->adj.inj_first, h->adj.inj_count};
   for (void* p : ptrs)
@@ -122,6 +122,9 @@ void free_all(isc_handle* h) {
   cpr_free(*h);
   if (h->h_scal) cudaFreeHost(h->h_scal);
   if (h->h_status) cudaFreeHost(h->h_status);
+  if (h->h_ring) cudaFreeHost(h->h_ring);
+  for (auto& ev : h->gm_ev)
+    if (ev) cudaEventDestroy(ev);
   for (auto& r : h->recs) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -201,8 +204,13 @@ int build_prec(isc_handle* h) {
   return check_device_status(h);
 }
 
-// Right-preconditioned restarted GMRES(m), classical Gram-Schmidt applied twice,
-// Givens rotations on the host. Solves A x = b, x0 = 0.
+// Right-preconditioned restarted GMRES(m), classical Gram-Schmidt applied twice.
+// Solves A x = b, x0 = 0. The Hessenberg column, the Givens rotations and the
+// next basis vector's scaling are computed on the device; the host reads the
+// residual estimate one iteration behind (it has already queued the next
+// iteration when it waits), so the GPU never idles on a host round trip. At
+// convergence the one speculative iteration is discarded: the solution uses
+// the columns up to the converged one.
 int gmres(isc_handle* h, const double* b, double* x, int* its_out, double* rel_out) {
   const int len = h->vlen;
   const int m = std::min(h->opt.restart, h->restart_alloc);
@@ -221,7 +229,6 @@ int gmres(isc_handle* h, const double* b, double* x, int* its_out, double* rel_o
   if (!isfinite(bnorm)) return set_err(h, ISC_ERR_NONFINITE, "non-finite right-hand side");
   int its = 0;
   double rel = 1.0;
-  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
   bool first = true;
   while (its < h->opt.maxit_lin) {
     double beta;
@@ -239,62 +246,83 @@ int gmres(isc_handle* h, const double* b, double* x, int* its_out, double* rel_o
     rel = beta / bnorm;
     if (rel <= h->opt.tol_lin) break;
     {
-      Region rg(h, ISC_K_BLAS1, 1);
+      Region rg(h, ISC_K_BLAS1, 2);
       launch_scale_copy(len, 1.0 / beta, V, V, s);
+      launch_gmres_start(*h, m, beta, s);
     }
-    std::fill(H.begin(), H.end(), 0.0);
-    std::fill(g.begin(), g.end(), 0.0);
-    g[0] = beta;
+    const int jmax = std::min(m, h->opt.maxit_lin - its);
     int jdone = 0;
-    for (int j = 0; j < m; ++j) {
+    bool stop = false;
+    // the status of iteration j: (rel, 1/h, h) in ring slot j % 2
+    auto status = [&](int j, double* r, double* hn) -> int {
+      if (cudaEventSynchronize(h->gm_ev[j & 1]) != cudaSuccess) return ISC_ERR_CUDA;
+      *r = h->h_ring[3 * (j & 1)];
+      *hn = h->h_ring[3 * (j & 1) + 2];
+      if (!isfinite(*r) || !isfinite(*hn)) return set_err(h, ISC_ERR_NONFINITE, "non-finite Krylov vector");
+      return ISC_OK;
+    };
+    // residual estimates of the iterations read so far (to predict convergence)
+    double r_prev2 = -1.0, r_prev1 = -1.0;
+    bool read_prev = false;  // the status of iteration j - 1 was read before launching j
+    for (int j = 0; j < jmax; ++j) {
+      // when the observed reduction rate predicts that iteration j - 1 has converged,
+      // wait for its status instead of launching a speculative iteration
+      read_prev = false;
+      if (j >= 1 && r_prev2 > 0.0 && r_prev1 > 0.0 && r_prev1 * (r_prev1 / r_prev2) <= 4.0 * h->opt.tol_lin) {
+        double r, hn;
+        int st = status(j - 1, &r, &hn);
+        if (st) return st;
+        rel = r;
+        r_prev2 = r_prev1;
+        r_prev1 = r;
+        read_prev = true;
+        if (r <= h->opt.tol_lin || hn == 0.0) {
+          jdone = j;
+          stop = true;
+          break;
+        }
+      }
       double* Vj = V + (size_t)j * h->vstride;
       double* Zj = Z + (size_t)j * h->vstride;
       prec(h, Vj, Zj);
       spmv(h, Zj, h->w);
       {
         // classical Gram-Schmidt applied twice; the second update also yields ||w||^2
-        Region rg(h, ISC_K_BLAS1, 4);
+        Region rg(h, ISC_K_BLAS1, 6);
         launch_mdot(*h, V, j + 1, h->w, S_H0, s);
         launch_maxpy(*h, h->w, V, j + 1, S_H0, -1.0, s);
         launch_mdot(*h, V, j + 1, h->w, S_H1, s);
         launch_maxpy_norm(*h, h->w, V, j + 1, S_H1, S_NRM, s);
-        cudaMemcpyAsync(h->h_scal + S_H0, h->scal + S_H0, sizeof(double) * (S_NRM + 1 - S_H0), cudaMemcpyDeviceToHost,
-                        s);
-        cudaStreamSynchronize(s);
+        launch_gmres_givens(*h, j, m, bnorm, S_H0, S_H1, S_NRM, s);
+        launch_scale_dev(*h, h->w, V + (size_t)(j + 1) * h->vstride, s);
+        cudaMemcpyAsync(h->h_ring + 3 * (j & 1), gmres_status(*h), 3 * sizeof(double), cudaMemcpyDeviceToHost, s);
+        cudaEventRecord(h->gm_ev[j & 1], s);
       }
-      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = h->h_scal[S_H0 + i] + h->h_scal[S_H1 + i];
-      double hn = sqrt(std::max(h->h_scal[S_NRM], 0.0));
-      if (!isfinite(hn)) return set_err(h, ISC_ERR_NONFINITE, "non-finite Krylov vector");
-      H[(size_t)(j + 1) * m + j] = hn;
-      for (int i = 0; i < j; ++i) {
-        double a = H[(size_t)i * m + j], c = H[(size_t)(i + 1) * m + j];
-        H[(size_t)i * m + j] = cs[i] * a + sn[i] * c;
-        H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+      if (j >= 1 && !read_prev) {
+        double r, hn;
+        int st = status(j - 1, &r, &hn);
+        if (st) return st;
+        rel = r;
+        r_prev2 = r_prev1;
+        r_prev1 = r;
+        if (r <= h->opt.tol_lin || hn == 0.0) {
+          jdone = j;  // iteration j is speculative: discarded
+          stop = true;
+          break;
+        }
       }
-      double a = H[(size_t)j * m + j], c = H[(size_t)(j + 1) * m + j];
-      double den = hypot(a, c);
-      cs[j] = a / den;
-      sn[j] = c / den;
-      H[(size_t)j * m + j] = den;
-      H[(size_t)(j + 1) * m + j] = 0.0;
-      g[j + 1] = -sn[j] * g[j];
-      g[j] = cs[j] * g[j];
-      ++its;
-      jdone = j + 1;
-      rel = fabs(g[j + 1]) / bnorm;
-      if (rel <= h->opt.tol_lin || its >= h->opt.maxit_lin || hn == 0.0) break;
-      Region rg(h, ISC_K_BLAS1, 1);
-      launch_scale_copy(len, 1.0 / hn, h->w, V + (size_t)(j + 1) * h->vstride, s);
     }
-    for (int i = jdone - 1; i >= 0; --i) {
-      double acc = g[i];
-      for (int k = i + 1; k < jdone; ++k) acc -= H[(size_t)i * m + k] * y[k];
-      y[i] = acc / H[(size_t)i * m + i];
+    if (!stop) {
+      double r, hn;
+      int st = status(jmax - 1, &r, &hn);
+      if (st) return st;
+      rel = r;
+      jdone = jmax;
     }
+    its += jdone;
     {
-      Region rg(h, ISC_K_BLAS1, 1);
-      memcpy(h->h_scal + S_Y, y.data(), sizeof(double) * jdone);
-      cudaMemcpyAsync(h->scal + S_Y, h->h_scal + S_Y, sizeof(double) * jdone, cudaMemcpyHostToDevice, s);
+      Region rg(h, ISC_K_BLAS1, 2);
+      launch_gmres_backsub(*h, jdone, m, S_Y, s);
       launch_maxpy(*h, x, Z, jdone, S_Y, 1.0, s);
     }
     if (rel <= h->opt.tol_lin) {
@@ -817,6 +845,7 @@ int isc_create(const isc_grid* grid, const isc_rock* rock, const isc_fluid* fl, 
   e |= dalloc(h, &h->dstatus, 1);
   e |= dalloc(h, &h->pipe, 2);
   e |= dalloc(h, &h->red_counter, 1);
+  e |= dalloc(h, &h->gmres, GMRES_STATE);
   if (e) {
     std::string msg = h->last_error;
     free_all(h);
@@ -824,7 +853,10 @@ int isc_create(const isc_grid* grid, const isc_rock* rock, const isc_fluid* fl, 
     return ISC_ERR_NOMEM;
   }
   if (cudaMallocHost((void**)&h->h_scal, sizeof(double) * NSCAL) != cudaSuccess ||
-      cudaMallocHost((void**)&h->h_status, sizeof(int)) != cudaSuccess) {
+      cudaMallocHost((void**)&h->h_status, sizeof(int)) != cudaSuccess ||
+      cudaMallocHost((void**)&h->h_ring, sizeof(double) * 6) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->gm_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->gm_ev[1], cudaEventDisableTiming) != cudaSuccess) {
     free_all(h);
     delete h;
     return ISC_ERR_NOMEM;

@@ -204,6 +204,9 @@ struct Handle {
   int* h_status = nullptr;                        // pinned
   int* pipe = nullptr;                            // sweep counter, abort flag
   unsigned* red_counter = nullptr;                // last-block counter of the fused reductions
+  double* gmres = nullptr;                        // GMRES Hessenberg, rotations, g and status (device)
+  double* h_ring = nullptr;                       // pinned: two slots of GMRES status (rel, 1/h, h)
+  cudaEvent_t gm_ev[2] = {nullptr, nullptr};      // completion of those copies
   int restart_alloc = 0;
   int red_blocks = 0;
   // flags
@@ -252,6 +255,14 @@ void launch_bsr_transpose(Handle& h, cudaStream_t s);
 void launch_adj_post(Handle& h, bool has_old, cudaStream_t s);
 void launch_row_sums(int nrows, int len, const double* x, double* out, cudaStream_t s);
 void launch_to_f32(size_t n, const double* x, float* y, cudaStream_t s);
+// GMRES bookkeeping on the device (isc_linalg.cu); the buffer Handle::gmres holds
+// GMRES_STATE doubles
+constexpr int GMRES_STATE = 64 * 67 + 64 + 8;
+void launch_gmres_givens(Handle& h, int j, int m, double bnorm, int off_h0, int off_h1, int off_nrm, cudaStream_t s);
+void launch_gmres_start(Handle& h, int m, double beta, cudaStream_t s);
+void launch_gmres_backsub(Handle& h, int jdone, int m, int off_y, cudaStream_t s);
+void launch_scale_dev(Handle& h, const double* x, double* y, cudaStream_t s);
+const double* gmres_status(const Handle& h);
 // BLAS-1 with fixed-order two-stage reductions; results land in h.scal[off..]
 void launch_mdot(Handle& h, const double* V, int nvec, const double* w, int off, cudaStream_t s);
 void launch_maxpy(Handle& h, double* w, const double* V, int nvec, int coef_off, double sign, cudaStream_t s);

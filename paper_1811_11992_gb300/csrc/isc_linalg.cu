@@ -488,6 +488,67 @@ __global__ void k_axpy_dev(int len, const double* __restrict__ coef, double sign
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) y[e] = fma(a, x[e], y[e]);
 }
 
+// ------------------------------------------------------------ GMRES control
+// The Arnoldi bookkeeping of GMRES(m) on the device, one thread: column j of
+// the Hessenberg matrix from the two Gram-Schmidt passes (h0 + h1) and ||w||,
+// the previous Givens rotations, the new one, the rotated right-hand side g;
+// st[0] = |g[j+1]| / bnorm, st[1] = 1 / h_{j+1,j} (0 on breakdown), st[2] =
+// h_{j+1,j}. No host round trip is needed per iteration.
+constexpr int GM_MAX = 64;
+
+__global__ void k_gmres_givens(int j, int m, double bnorm, const double* __restrict__ h0,
+                               const double* __restrict__ h1, const double* __restrict__ nrm2,
+                               double* __restrict__ H, double* __restrict__ cs, double* __restrict__ sn,
+                               double* __restrict__ g, double* __restrict__ st) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double col[GM_MAX + 1];
+  for (int i = 0; i <= j; ++i) col[i] = h0[i] + h1[i];
+  const double hn = sqrt(fmax(*nrm2, 0.0));
+  col[j + 1] = hn;
+  for (int i = 0; i < j; ++i) {
+    const double a = col[i], c = col[i + 1];
+    col[i] = cs[i] * a + sn[i] * c;
+    col[i + 1] = -sn[i] * a + cs[i] * c;
+  }
+  const double a = col[j], c = col[j + 1];
+  const double den = hypot(a, c);
+  const double cj = den > 0.0 ? a / den : 1.0, sj = den > 0.0 ? c / den : 0.0;
+  cs[j] = cj;
+  sn[j] = sj;
+  col[j] = den > 0.0 ? den : a;
+  for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = col[i];
+  const double gj = g[j];
+  g[j + 1] = -sj * gj;
+  g[j] = cj * gj;
+  st[0] = fabs(g[j + 1]) / bnorm;
+  st[1] = (hn > 0.0 && isfinite(hn)) ? 1.0 / hn : 0.0;
+  st[2] = hn;
+}
+
+__global__ void k_gmres_start(int m, double beta, double* __restrict__ g) {
+  const int i = threadIdx.x;
+  if (i <= m) g[i] = (i == 0) ? beta : 0.0;
+}
+
+// y = R^-1 g over the first jdone columns (back substitution), into y
+__global__ void k_gmres_backsub(int jdone, int m, const double* __restrict__ H, const double* __restrict__ g,
+                                double* __restrict__ y) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int i = jdone - 1; i >= 0; --i) {
+    double acc = g[i];
+    for (int k = i + 1; k < jdone; ++k) acc -= H[(size_t)i * m + k] * y[k];
+    y[i] = acc / H[(size_t)i * m + i];
+  }
+}
+
+// y = (*coef) x with the coefficient read on the device
+__global__ void k_scale_dev(int len, const double* __restrict__ coef, const double* __restrict__ x,
+                            double* __restrict__ y) {
+  const double a = coef[0];
+  const int stride = gridDim.x * blockDim.x;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) y[e] = a * x[e];
+}
+
 // ------------------------------------------------------------ Newton update
 __global__ void k_update(int n, double* __restrict__ u, const double* __restrict__ du, double max_dp_frac,
                          double max_dT) {
@@ -590,6 +651,29 @@ void launch_prec_apply(Handle& h, const double* r, double* z, cudaStream_t s) {
   }
   launch_ilu_apply_pipe(h, r, z, s);
 }
+
+void launch_gmres_givens(Handle& h, int j, int m, double bnorm, int off_h0, int off_h1, int off_nrm,
+                         cudaStream_t s) {
+  double* G = h.gmres;
+  k_gmres_givens<<<1, 32, 0, s>>>(j, m, bnorm, h.scal + off_h0, h.scal + off_h1, h.scal + off_nrm, G,
+                                  G + GM_MAX * (GM_MAX + 1), G + GM_MAX * (GM_MAX + 2), G + GM_MAX * (GM_MAX + 3),
+                                  G + GM_MAX * (GM_MAX + 3) + GM_MAX + 1);
+}
+
+void launch_gmres_start(Handle& h, int m, double beta, cudaStream_t s) {
+  k_gmres_start<<<1, GM_MAX + 1, 0, s>>>(m, beta, h.gmres + GM_MAX * (GM_MAX + 3));
+}
+
+void launch_gmres_backsub(Handle& h, int jdone, int m, int off_y, cudaStream_t s) {
+  k_gmres_backsub<<<1, 32, 0, s>>>(jdone, m, h.gmres, h.gmres + GM_MAX * (GM_MAX + 3), h.scal + off_y);
+}
+
+void launch_scale_dev(Handle& h, const double* x, double* y, cudaStream_t s) {
+  // coefficient: 1 / h_{j+1,j} from the last k_gmres_givens
+  k_scale_dev<<<grid_for(h.vlen, 256), 256, 0, s>>>(h.vlen, h.gmres + GM_MAX * (GM_MAX + 3) + GM_MAX + 2, x, y);
+}
+
+const double* gmres_status(const Handle& h) { return h.gmres + GM_MAX * (GM_MAX + 3) + GM_MAX + 1; }
 
 void launch_to_f32(size_t n, const double* x, float* y, cudaStream_t s) {
   k_to_f32<<<grid_for(n, 256), 256, 0, s>>>(n, x, y);

@@ -127,9 +127,11 @@ def test_autograd_function_returns_the_adjoint_gradient(box):
 def test_adjoint_workload_central_differences():
     """40x40x10, 20 steps, checkpoints every 5: the adjoint directional
     derivative against central differences with a relative step of 1e-6 on 20
-    seeded directions: 14 in all parameters (ln k per cell, E_a relative,
-    ln A), 3 in E_a alone and 3 in ln A alone (the ln k part dominates the
-    mixed directions and would hide an error in the reaction gradients)."""
+    seeded directions: 14 in all parameters, 3 in E_a alone and 3 in ln A
+    alone (the ln k part dominates the mixed directions and would hide an
+    error in the reaction gradients). The step is relative to each
+    parameter's magnitude (E_a, ln A); the ln k multipliers are zero, so
+    their step is 1e-6 in ln k itself."""
     case = inp.config(4)
     n, nr = case.n, int(case.reactions["nr"])
     dts = inp.adjoint_steps(case)
@@ -145,7 +147,7 @@ def test_adjoint_workload_central_differences():
         group = "all" if d < 14 else ("Ea" if d < 17 else "lnA")
         vk = rng.standard_normal(n) * (group == "all")
         ve = Ea0 * rng.standard_normal(nr) * (group in ("all", "Ea"))
-        va = rng.standard_normal(nr) * (group in ("all", "lnA"))
+        va = np.abs(lnA0) * rng.standard_normal(nr) * (group in ("all", "lnA"))
         ad = gk @ vk + ge @ ve + ga @ va
         Ls = []
         for sgn in (1.0, -1.0):
