@@ -287,11 +287,11 @@ int gmres(isc_handle* h, const double* b, double* x, int* its_out, double* rel_o
       prec(h, Vj, Zj);
       spmv(h, Zj, h->w);
       {
-        // classical Gram-Schmidt applied twice; the second update also yields ||w||^2
-        Region rg(h, ISC_K_BLAS1, 6);
+        // classical Gram-Schmidt applied twice: h0 = V^T w; w -= V h0 fused with h1 = V^T w;
+        // w -= V h1 fused with ||w||^2
+        Region rg(h, ISC_K_BLAS1, j + 1 <= 32 ? 5 : 6);
         launch_mdot(*h, V, j + 1, h->w, S_H0, s);
-        launch_maxpy(*h, h->w, V, j + 1, S_H0, -1.0, s);
-        launch_mdot(*h, V, j + 1, h->w, S_H1, s);
+        launch_maxpy_mdot(*h, h->w, V, j + 1, S_H0, S_H1, s);
         launch_maxpy_norm(*h, h->w, V, j + 1, S_H1, S_NRM, s);
         launch_gmres_givens(*h, j, m, bnorm, S_H0, S_H1, S_NRM, s);
         launch_scale_dev(*h, h->w, V + (size_t)(j + 1) * h->vstride, s);

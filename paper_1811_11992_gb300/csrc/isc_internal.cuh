@@ -267,6 +267,8 @@ const double* gmres_status(const Handle& h);
 void launch_mdot(Handle& h, const double* V, int nvec, const double* w, int off, cudaStream_t s);
 void launch_maxpy(Handle& h, double* w, const double* V, int nvec, int coef_off, double sign, cudaStream_t s);
 void launch_maxpy_norm(Handle& h, double* w, const double* V, int nvec, int coef_off, int out_off, cudaStream_t s);
+// w <- w - V scal[coef_off..], then scal[out_off..] = V^T w (one read of V)
+void launch_maxpy_mdot(Handle& h, double* w, const double* V, int nvec, int coef_off, int out_off, cudaStream_t s);
 void launch_axpby(int n, double a, const double* x, double b, double* y, cudaStream_t s);
 void launch_scale_copy(int n, double a, const double* x, double* y, cudaStream_t s);
 void launch_axpy_dev(int n, const double* coef, double sign, const double* x, double* y, cudaStream_t s);
