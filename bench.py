@@ -6,9 +6,11 @@ evaluation + residual/Jacobian assembly, convergence norms, Gauss-Jordan
 decoupling, block ILU(0) factorisation, GMRES(30) to the relative tolerance,
 safeguarded update. Inputs are resident in HBM for ``value``; ``e2e`` goes
 through the C ABI with host buffers (state in, state out) every step. The
-line also carries the same step with the FP32 preconditioner (``mixed``) and
-the discrete adjoint of a 40x40x10 time loop (``adjoint``) and the step with
-the CPR-PF preconditioner (``cpr``, FP64 and mixed).
+line also carries the same step with the FP32 preconditioner (``mixed``), with
+an FP32 inner GMRES inside the flexible FP64 GMRES (``mixed_fgmres``, with the
+FP32 SpMV's roofline), the discrete adjoint of a 40x40x10 time loop
+(``adjoint``) and the step with the CPR-PF preconditioner (``cpr``, FP64 and
+mixed).
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl isc|reference]
 Under torchrun each rank runs an independent replica (the path has no
@@ -201,7 +203,7 @@ def run_isc(args):
     ms_total = max_over_ranks(max(ms_dev, wall * 1e3), "cuda")
     value = job_throughput(world, args.steps, ms_total)
     kry = [i.krylov_iterations for i in infos]
-    e2e = mixed = cpr_block = None
+    e2e = mixed = mixed_fgmres = cpr_block = None
     if not args.no_extras:
         # end-to-end through the C ABI with host buffers
         uh, ch = g.get_state()
@@ -227,29 +229,38 @@ def run_isc(args):
         e2e_val = job_throughput(world, e2e_steps, max_over_ranks(e2e_s * 1e3, "cuda"))
         io_bytes = 9 * n * 8
         e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes}
-        # mixed precision on the same step: FP32 ILU(0) factors and sweeps inside the FP64 FGMRES
-        g.set_options(precision="mixed")
-        for _ in range(max(1, args.warmup)):
-            step()
-        torch.cuda.synchronize()
-        g.reset_stats()
-        ev0.record()
-        minfo = [step() for _ in range(args.steps)]
-        ev1.record()
-        torch.cuda.synchronize()
-        ms_mixed = ev0.elapsed_time(ev1) / args.steps
-        mstats = g.stats()
-        g.set_options(precision="fp64")
-        mixed = {"value": 1e3 / ms_mixed, "unit": UNIT, "ms_per_step": ms_mixed,
-                 "krylov_iterations_per_step": statistics.median([i.krylov_iterations for i in minfo]),
-                 "rel_residual": max(i.krylov_rel_residual for i in minfo),
-                 "prec_apply_ms_per_call": mstats["prec_apply"]["ms"] / max(1, mstats["prec_apply"]["calls"]),
-                 "solve_speedup_vs_fp64": None}
-        solve_fp64 = sum(stats[k]["ms"] for k in ("spmv", "prec_apply", "blas1", "ilu_factor")) / args.steps
-        solve_mixed = sum(mstats[k]["ms"] for k in ("spmv", "prec_apply", "blas1", "ilu_factor")) / args.steps
-        mixed["solve_ms_fp64"] = solve_fp64
-        mixed["solve_ms_mixed"] = solve_mixed
-        mixed["solve_speedup_vs_fp64"] = solve_fp64 / solve_mixed if solve_mixed > 0 else None
+        solve_fp64 = sum(stats[k]["ms"] for k in SOLVE_CLASSES) / args.steps
+
+        def precision_leg(precision, **extra):
+            """The headline step again under another precision of the linear solve."""
+            g.set_options(precision=precision, **extra)
+            for _ in range(max(1, args.warmup)):
+                step()
+            torch.cuda.synchronize()
+            g.reset_stats()
+            ev0.record()
+            minfo = [step() for _ in range(args.steps)]
+            ev1.record()
+            torch.cuda.synchronize()
+            ms_leg = ev0.elapsed_time(ev1) / args.steps
+            mstats = g.stats()
+            g.set_options(precision="fp64")
+            solve_leg = sum(mstats[k]["ms"] for k in SOLVE_CLASSES) / args.steps
+            return mstats, {
+                "value": 1e3 / ms_leg, "unit": UNIT, "ms_per_step": ms_leg,
+                "krylov_iterations_per_step": statistics.median([i.krylov_iterations for i in minfo]),
+                "rel_residual": max(i.krylov_rel_residual for i in minfo),
+                "prec_apply_ms_per_call": mstats["prec_apply"]["ms"] / max(1, mstats["prec_apply"]["calls"]),
+                "solve_ms_fp64": solve_fp64, "solve_ms": solve_leg,
+                "solve_speedup_vs_fp64": solve_fp64 / solve_leg if solve_leg > 0 else None}
+
+        # mixed precision on the same step: FP32 ILU(0) factors and sweeps inside the FP64 GMRES
+        _, mixed = precision_leg("mixed")
+        # FP32 inner GMRES (FP32 SpMV, Gram-Schmidt and ILU(0)) inside the flexible FP64 GMRES
+        fst, mixed_fgmres = precision_leg("mixed_fgmres", inner_its=INNER_ITS)
+        mixed_fgmres["inner_its"] = INNER_ITS
+        mixed_fgmres["inner_iterations_per_step"] = mixed_fgmres["krylov_iterations_per_step"] * INNER_ITS
+        mixed_fgmres["roofline_spmv32"] = spmv32_roofline(fst, case, g.nnzb)
         # CPR-PF (the paper's Example-2 preconditioner) on the same step, FP64 and mixed
         cpr_block = {}
         for precision in ("fp64", "mixed"):
@@ -290,6 +301,7 @@ def run_isc(args):
         "roofline": roof,
         "clocks": clocks,
         "mixed": mixed,
+        "mixed_fgmres": mixed_fgmres,
         "cpr": cpr_block,
     }
     if not args.no_adjoint and not args.no_extras and args.grid is None and args.workload == "field":
@@ -348,6 +360,24 @@ def measured_peaks():
 FP64_PEAK_GFLOPS = 1200.0   # measured DFMA throughput on this GB300
 # dram__bytes_read.sum + dram__bytes_write.sum per call (forward + backward FP64 sweep)
 MEASURED_TRAFFIC = {("prec_apply", 60, 60, 20): (316.65e6, "profiles/k_ilu_sweeps_field_60x60x20.md")}
+
+
+SOLVE_CLASSES = ("spmv", "spmv32", "prec_apply", "blas1", "ilu_factor")
+INNER_ITS = 10
+
+
+def spmv32_roofline(stats, case, nnzb):
+    """The inner solve's FP32 SpMV: FP32 off-diagonal blocks and their column
+    indices, x read twice (neighbours and the unit diagonal) and y written."""
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    s = stats["spmv32"]
+    calls = max(1, s["calls"])
+    ms = s["ms"] / calls
+    byts = (nnzb - case.n) * (256 + 4) + 3 * case.n * 32
+    ach = byts / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+    return {"kernel": "k_spmv<float>", "bound": "hbm", "calls": calls, "ms_per_call": ms, "bytes_per_call": byts,
+            "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
 
 
 def roofline(dom, stats, g, case, kry):

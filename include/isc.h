@@ -67,10 +67,18 @@ enum isc_krylov { ISC_KRYLOV_GMRES = 0, ISC_KRYLOV_BICGSTAB = 1 };
  * post-smoothing sweep), then block ILU(0) on the remaining residual; the
  * ILU(0) stage follows options.precision. It expects options.decouple = 1. */
 enum isc_prec { ISC_PREC_NONE = 0, ISC_PREC_BJACOBI = 1, ISC_PREC_BILU0 = 2, ISC_PREC_CPR = 3 };
-/* Precision of the preconditioner: FP64 throughout, or mixed: the block
- * ILU(0) factors are computed in FP64, stored and applied in FP32 inside the
- * FP64 flexible GMRES (residual, SpMV, orthogonalisation and update stay FP64). */
-enum isc_precision { ISC_PRECISION_FP64 = 0, ISC_PRECISION_MIXED = 1 };
+/* Precision of the linear solve.
+ * ISC_PRECISION_FP64: FP64 throughout.
+ * ISC_PRECISION_MIXED: the block ILU(0) factors are computed, stored and applied
+ *   in FP32 (from an FP32 copy of the decoupled blocks; under CPR-PF the pressure
+ *   multigrid too) inside the FP64 GMRES (residual, SpMV, orthogonalisation and
+ *   update stay FP64).
+ * ISC_PRECISION_MIXED_FGMRES: the FP64 GMRES is flexible and its preconditioner
+ *   is options.inner_its iterations of an FP32 GMRES on the FP32 copy of the
+ *   decoupled matrix (FP32 SpMV, FP32 Gram-Schmidt, FP32 block ILU(0)); the
+ *   outer residual, SpMV, orthogonalisation and update stay FP64. Requires
+ *   krylov = GMRES and prec = BILU0. */
+enum isc_precision { ISC_PRECISION_FP64 = 0, ISC_PRECISION_MIXED = 1, ISC_PRECISION_MIXED_FGMRES = 2 };
 enum isc_rxn_kind {
   ISC_RXN_OIL_OXIDATION = 0,   /* r = A e^{-Ea/RT} (y_O2 p)(phi_f S_o rho_o x_i)           */
   ISC_RXN_CRACKING = 1,        /* r = A e^{-Ea/RT} (phi_f S_o rho_o x_i)(1-(C_c/C_max)^5)  */
@@ -184,8 +192,9 @@ typedef struct isc_options {
   double max_dp_frac;           /* |dp| <= max_dp_frac p (0.2) */
   double max_dT;                /* |dT| <= max_dT (50 K) */
   int32_t profile;              /* 1: record per-kernel CUDA-event times */
-  int32_t precision;            /* isc_precision (applies to ISC_PREC_BILU0) */
+  int32_t precision;            /* isc_precision (applies to ISC_PREC_BILU0; MIXED also to CPR) */
   void* stream;
+  int32_t inner_its;            /* ISC_PRECISION_MIXED_FGMRES: FP32 GMRES iterations per outer one, 1..32 (10) */
 } isc_options;
 
 typedef struct isc_newton_info {
@@ -210,7 +219,8 @@ enum isc_kernel_class {
   ISC_K_PROPS = 0, ISC_K_FLUX = 1, ISC_K_NORM = 2, ISC_K_GJ = 3, ISC_K_ILU_FACTOR = 4,
   ISC_K_SPMV = 5, ISC_K_PREC_APPLY = 6, ISC_K_BLAS1 = 7, ISC_K_UPDATE = 8, ISC_K_ADJOINT = 9,
   ISC_K_CPR = 10,   /* CPR pressure stage: extraction and coarsening, V-cycle, second-stage residual */
-  ISC_K_COUNT = 11
+  ISC_K_SPMV32 = 11, /* FP32 SpMV of the inner solve (ISC_PRECISION_MIXED_FGMRES) */
+  ISC_K_COUNT = 12
 };
 typedef struct isc_stats {
   double ms[ISC_K_COUNT];

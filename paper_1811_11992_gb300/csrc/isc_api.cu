@@ -114,7 +114,7 @@ int dalloc(isc_handle* h, T** p, size_t count) {
 void free_all(isc_handle* h) {
   void* ptrs[] = {h->rowptr, h->col, h->level_cells, h->phi_ref, h->depth, h->tx, h->ty, h->tz, h->well_slot,
                   h->slots, h->u, h->coke, h->u_n, h->coke_n, h->acc_n, h->props, h->R, h->J, h->ntot, h->du,
-                  h->rhs, h->dinv, h->J32, h->dinv32, h->vec32, h->V, h->Z, h->w, h->tmp, h->partial, h->scal, h->dstatus, h->pipe, h->red_counter, h->gmres,
+                  h->rhs, h->dinv, h->J32, h->dinv32, h->vec32, h->V32, h->Z32, h->w32, h->gm_in, h->scal_in, h->V, h->Z, h->w, h->tmp, h->partial, h->scal, h->dstatus, h->pipe, h->red_counter, h->gmres,
                   h->wx, h->wy, h->wz, h->cw, h->bhp, h->bhp_n, h->Dw, h->Bv, h->Cv, h->Fq, h->Dq, h->adj.store, h->adj.ubar, h->adj.cbar, h->adj.lam, h->adj.glnk, h->adj.grx,
                   h->adj.scond, h->adj.kd, h->adj.loss_cell, h->adj.sums, h->adj.inj_first, h->adj.inj_count};
   for (void* p : ptrs)
@@ -156,7 +156,13 @@ void prec(isc_handle* h, const double* r, double* z) {
   }
 }
 
+int inner_solve(isc_handle* h, const double* r, double* z);
+
 void prec_cells(isc_handle* h, const double* r, double* z) {
+  if (h->opt.precision == ISC_PRECISION_MIXED_FGMRES && h->opt.prec == ISC_PREC_BILU0) {
+    inner_solve(h, r, z);
+    return;
+  }
   if (h->opt.prec == ISC_PREC_CPR) {
     {
       Region rg(h, ISC_K_CPR, cpr_pressure_launches(*h));
@@ -175,6 +181,51 @@ void prec_cells(isc_handle* h, const double* r, double* z) {
   launch_prec_apply(*h, r, z, h->stream);
 }
 
+// z ~ A^-1 r by inner_its iterations of right-preconditioned GMRES in FP32 on the
+// FP32 copy of the (decoupled) matrix with the FP32 block ILU(0),
+// classical Gram-Schmidt applied twice, x0 = 0; the rotations and the final
+// back-substitution run on the device, so the whole solve is a fixed launch
+// sequence with no host round trip. A fixed iteration count keeps it cheap to
+// schedule; the outer GMRES is flexible, so the resulting operator may vary.
+int inner_solve(isc_handle* h, const double* r, double* z) {
+  const int m = h->opt.inner_its;
+  const int len = h->n * 8;
+  const size_t vs = (size_t)len;
+  cudaStream_t s = h->stream;
+  float* V = h->V32;
+  float* Z = h->Z32;
+  double* G = h->gm_in;
+  double* sc = h->scal_in;  // [0, 64) h0, [64, 128) h1, 128 ||w||^2, [136, 200) y
+  {
+    Region rg(h, ISC_K_BLAS1, 3);
+    launch_f32_nrm(*h, len, r, V, sc + 128, s);
+    launch_gmres_start_dev(G, m, sc + 128, s);
+    launch_scale_dev32(G, len, V, V, s);
+  }
+  for (int j = 0; j < m; ++j) {
+    float* Vj = V + (size_t)j * vs;
+    float* Zj = Z + (size_t)j * vs;
+    {
+      Region rg(h, ISC_K_PREC_APPLY, 2);
+      launch_ilu_apply_f32(*h, Vj, Zj, s);
+    }
+    {
+      Region rg(h, ISC_K_SPMV32, 1);
+      launch_spmv32(h->n, h->rowptr, h->col, h->J32, Zj, h->w32, h->decoupled ? 1 : 0, s);
+    }
+    Region rg(h, ISC_K_BLAS1, j + 1 < m ? 5 : 4);
+    launch_mdot32(*h, len, vs, V, j + 1, h->w32, sc, s);
+    launch_maxpy_mdot32(*h, len, vs, h->w32, V, j + 1, sc, sc + 64, s);
+    launch_maxpy_norm32(*h, len, vs, h->w32, V, j + 1, sc + 64, sc + 128, s);
+    launch_gmres_givens_at(G, j, m, sc, sc + 64, sc + 128, s);
+    if (j + 1 < m) launch_scale_dev32(G, len, h->w32, V + (size_t)(j + 1) * vs, s);
+  }
+  Region rg(h, ISC_K_BLAS1, 2);
+  launch_gmres_backsub_at(G, m, m, sc + 136, s);
+  launch_comb_out32(len, Z, vs, m, sc + 136, z, s);
+  return ISC_OK;
+}
+
 int build_prec(isc_handle* h) {
   if (h->opt.prec == ISC_PREC_CPR) {
     // (re)allocates when the precision of the multigrid arrays changed
@@ -184,7 +235,7 @@ int build_prec(isc_handle* h) {
     launch_cpr_setup(*h, h->stream);
   }
   if (h->opt.prec == ISC_PREC_BILU0 || h->opt.prec == ISC_PREC_CPR) {
-    const bool mixed = h->opt.precision == ISC_PRECISION_MIXED;
+    const bool mixed = h->opt.precision != ISC_PRECISION_FP64;
     if (mixed && !h->J32) {
       // first mixed-precision use: FP32 copies of the blocks and D^-1, two FP32 sweep vectors
       int e = 0;
@@ -192,6 +243,22 @@ int build_prec(isc_handle* h) {
       e |= dalloc(h, &h->dinv32, (size_t)h->n * BB);
       e |= dalloc(h, &h->vec32, (size_t)h->n * 16);
       if (e) return ISC_ERR_NOMEM;
+    }
+    if (h->opt.precision == ISC_PRECISION_MIXED_FGMRES && h->inner_alloc < h->opt.inner_its) {
+      // inner FP32 GMRES workspace, (re)allocated when inner_its grows
+      for (void* q : {(void*)h->V32, (void*)h->Z32, (void*)h->w32, (void*)h->gm_in, (void*)h->scal_in})
+        if (q) cudaFree(q);
+      h->V32 = h->Z32 = h->w32 = nullptr;
+      h->gm_in = h->scal_in = nullptr;
+      const size_t n8 = (size_t)h->n * 8;
+      int e = 0;
+      e |= dalloc(h, &h->V32, n8 * (h->opt.inner_its + 1));
+      e |= dalloc(h, &h->Z32, n8 * h->opt.inner_its);
+      e |= dalloc(h, &h->w32, n8);
+      e |= dalloc(h, &h->gm_in, GMRES_STATE);
+      e |= dalloc(h, &h->scal_in, 256);
+      if (e) return ISC_ERR_NOMEM;
+      h->inner_alloc = h->opt.inner_its;
     }
     // mixed precision: FP32 copy of the blocks, then the factorisation in FP32
     Region rg(h, ISC_K_ILU_FACTOR, mixed ? 2 : 1);
@@ -497,8 +564,14 @@ int validate_options(isc_handle* h, const isc_options& o) {
   if (o.krylov != ISC_KRYLOV_GMRES && o.krylov != ISC_KRYLOV_BICGSTAB)
     return set_err(h, ISC_ERR_INVALID_ARG, "unknown krylov method");
   if (o.prec < ISC_PREC_NONE || o.prec > ISC_PREC_CPR) return set_err(h, ISC_ERR_INVALID_ARG, "unknown preconditioner");
-  if (o.precision != ISC_PRECISION_FP64 && o.precision != ISC_PRECISION_MIXED)
+  if (o.precision != ISC_PRECISION_FP64 && o.precision != ISC_PRECISION_MIXED &&
+      o.precision != ISC_PRECISION_MIXED_FGMRES)
     return set_err(h, ISC_ERR_INVALID_ARG, "unknown precision");
+  if (o.precision == ISC_PRECISION_MIXED_FGMRES) {
+    if (o.krylov != ISC_KRYLOV_GMRES || o.prec != ISC_PREC_BILU0)
+      return set_err(h, ISC_ERR_INVALID_ARG, "mixed_fgmres needs krylov = GMRES and prec = BILU0");
+    if (o.inner_its < 1 || o.inner_its > 32) return set_err(h, ISC_ERR_INVALID_ARG, "inner_its must be 1..32");
+  }
   if (!(o.tol_lin > 0.0) || o.maxit_lin < 1 || !(o.tol_newton >= 0.0) || o.maxit_newton < 1)
     return set_err(h, ISC_ERR_INVALID_ARG, "tolerances must be positive and iteration limits >= 1");
   return ISC_OK;
@@ -523,6 +596,7 @@ void isc_default_options(isc_options* o) {
   o->profile = 0;
   o->precision = ISC_PRECISION_FP64;
   o->stream = nullptr;
+  o->inner_its = 10;
 }
 
 const char* isc_status_string(int st) {

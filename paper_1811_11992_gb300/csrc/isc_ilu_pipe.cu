@@ -197,10 +197,10 @@ struct Slot {
 };
 
 // issue the copies of one cell into a slot: blocks at row slots first_slot.. (mask says which exist)
-template <typename TM>
+template <typename TM, typename RT = double>
 __device__ __forceinline__ void stage_cell(Slot<TM>* sl, int i, int first_slot, int mask, const Pen& P,
                                            const TM* __restrict__ A, const TM* __restrict__ Dinv,
-                                           const double* __restrict__ rhs, int lane) {
+                                           const RT* __restrict__ rhs, int lane) {
   const int base = row_start(P, i - P.base_jk);
   int s = first_slot, dst = 0;  // present blocks are packed into blk[0..] in row order
 #pragma unroll
@@ -212,7 +212,8 @@ __device__ __forceinline__ void stage_cell(Slot<TM>* sl, int i, int first_slot, 
     }
   }
   cp_async<2 * sizeof(TM)>(&sl->blk[3][2 * lane], Dinv + (size_t)i * BB + 2 * lane);
-  if (rhs && lane < 8) cp_async<8>(&sl->rhs[lane], rhs + (size_t)i * 8 + lane);
+  // the right-hand side is FP64, or FP32 in the inner solve of the mixed-precision scheme
+  if (rhs && lane < 8) cp_async<sizeof(RT)>(reinterpret_cast<RT*>(sl->rhs) + lane, rhs + (size_t)i * 8 + lane);
 }
 
 template <typename TM>
@@ -222,10 +223,10 @@ __device__ __forceinline__ typename V2<TM>::t sl_pair(const Slot<TM>* sl, int b,
 
 constexpr int AWARPS = 8;
 
-template <typename TM, int R>
+template <typename TM, int R, typename RT = double>
 __global__ void __launch_bounds__(AWARPS * 32) k_ilu_fwd_async(int nx, int ny, int nz, const int32_t* __restrict__ rowptr,
                                                                const TM* __restrict__ A, const TM* __restrict__ Dinv,
-                                                               const double* __restrict__ rhs, TM* __restrict__ y,
+                                                               const RT* __restrict__ rhs, TM* __restrict__ y,
                                                                int* __restrict__ pipe, int* __restrict__ dstatus) {
   using T2 = typename V2<TM>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -248,7 +249,7 @@ __global__ void __launch_bounds__(AWARPS * 32) k_ilu_fwd_async(int nx, int ny, i
     auto mask_of = [&](int x) { return (hz ? 1 : 0) | (hy ? 2 : 0) | (x > 0 ? 4 : 0); };
 #pragma unroll 1
     for (int q = 0; q < R - 1; ++q) {
-      if (q < nx) stage_cell<TM>(ring + q, base_jk + q, 0, mask_of(q), PEN, A, Dinv, rhs, lane);
+      if (q < nx) stage_cell<TM, RT>(ring + q, base_jk + q, 0, mask_of(q), PEN, A, Dinv, rhs, lane);
       cp_async_commit();
     }
     T2 rz[LA], ry[LA];
@@ -267,7 +268,7 @@ __global__ void __launch_bounds__(AWARPS * 32) k_ilu_fwd_async(int nx, int ny, i
         if (x >= nx) break;
         const int i = base_jk + x;
         const int xs = x + R - 1;
-        if (xs < nx) stage_cell<TM>(ring + xs % R, base_jk + xs, 0, mask_of(xs), PEN, A, Dinv, rhs, lane);
+        if (xs < nx) stage_cell<TM, RT>(ring + xs % R, base_jk + xs, 0, mask_of(xs), PEN, A, Dinv, rhs, lane);
         cp_async_commit();
         cp_async_wait<R - 1>();
         __syncwarp();
@@ -279,7 +280,7 @@ __global__ void __launch_bounds__(AWARPS * 32) k_ilu_fwd_async(int nx, int ny, i
         if (m & 2) ay = sl_pair<TM>(sl, b++, lane);
         if (m & 4) ax = sl_pair<TM>(sl, b, lane);
         const T2 d = sl_pair<TM>(sl, 3, lane);
-        const TM ri = (TM)sl->rhs[r];
+        const TM ri = (TM)reinterpret_cast<const RT*>(sl->rhs)[r];
         TM acc = fma(ax.x, yp0, ax.y * yp1);
         if (hz) {
           if (!settle<TM>(y + (size_t)(i - nxy) * 8 + c, rz[q], abortf, dstatus)) return;
@@ -339,7 +340,7 @@ __global__ void __launch_bounds__(AWARPS * 32) k_ilu_bwd_async(int nx, int ny, i
     for (int q = 0; q < R - 1; ++q) {
       if (q < nx) {
         const int x = nx - 1 - q;
-        stage_cell<TM>(ring + q, base_jk + x, first_of(x), mask_of(x), PEN, A, Dinv, nullptr, lane);
+        stage_cell<TM>(ring + q, base_jk + x, first_of(x), mask_of(x), PEN, A, Dinv, (const double*)nullptr, lane);
       }
       cp_async_commit();
     }
@@ -363,7 +364,7 @@ __global__ void __launch_bounds__(AWARPS * 32) k_ilu_bwd_async(int nx, int ny, i
         const int ss = step + R - 1;
         if (ss < nx)
           stage_cell<TM>(ring + ss % R, base_jk + (nx - 1 - ss), first_of(nx - 1 - ss), mask_of(nx - 1 - ss), PEN, A,
-                         Dinv, nullptr, lane);
+                         Dinv, (const double*)nullptr, lane);
         cp_async_commit();
         cp_async_wait<R - 1>();
         __syncwarp();
@@ -577,7 +578,7 @@ void launch_ilu_factor_pipe(Handle& h, cudaStream_t s) {
   const int warps = npen < 152 * 8 ? npen : 152 * 8;
   const int blocks = (warps + FWARPS - 1) / FWARPS;
   cudaMemsetAsync(h.pipe, 0, 2 * sizeof(int), s);
-  if (h.opt.precision == ISC_PRECISION_MIXED) {
+  if (h.opt.precision != ISC_PRECISION_FP64) {
     launch_to_f32((size_t)h.nnzb * BB, h.J, h.J32, s);
     cudaMemsetAsync(h.dinv32, 0xff, sizeof(float) * (size_t)h.n * BB, s);  // NaN sentinel
     k_ilu_factor_pipe<float><<<blocks, FWARPS * 32, 0, s>>>(h.nx, h.ny, h.nz, h.rowptr, h.J32, h.dinv32, h.pipe,
@@ -605,6 +606,8 @@ template <typename TM>
 void sweep_attributes() {
   // idempotent; the rings need more than the default 48 KB of dynamic shared memory
   cudaFuncSetAttribute(k_ilu_fwd_async<TM, SWEEP_R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sweep_smem<TM>());
+  cudaFuncSetAttribute(k_ilu_fwd_async<TM, SWEEP_R, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)sweep_smem<TM>());
   cudaFuncSetAttribute(k_ilu_bwd_async<TM, SWEEP_R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sweep_smem<TM>());
 }
 
@@ -624,8 +627,24 @@ void sweep_pair(int nx, int ny, int nz, const int32_t* rowptr, const TM* A, cons
                                                                  dstatus);
 }
 
+// FP32 in, FP32 out (inner solve of ISC_PRECISION_MIXED_FGMRES): y in vec32, z written as the hand-off vector
+void launch_ilu_apply_f32(Handle& h, const float* r, float* z, cudaStream_t s) {
+  const size_t n8 = (size_t)h.n * 8;
+  const int blocks = sweep_blocks(h.ny * h.nz);
+  const size_t smem = sweep_smem<float>();
+  sweep_attributes<float>();
+  cudaMemsetAsync(h.pipe, 0, 2 * sizeof(int), s);
+  cudaMemsetAsync(h.vec32, 0xff, sizeof(float) * n8, s);  // NaN sentinel
+  k_ilu_fwd_async<float, SWEEP_R, float><<<blocks, AWARPS * 32, smem, s>>>(h.nx, h.ny, h.nz, h.rowptr, h.J32, h.dinv32,
+                                                                           r, h.vec32, h.pipe, h.dstatus);
+  cudaMemsetAsync(h.pipe, 0, 2 * sizeof(int), s);
+  cudaMemsetAsync(z, 0xff, sizeof(float) * n8, s);
+  k_ilu_bwd_async<float, SWEEP_R><<<blocks, AWARPS * 32, smem, s>>>(h.nx, h.ny, h.nz, h.rowptr, h.J32, h.dinv32, h.vec32,
+                                                                    z, nullptr, h.pipe, h.dstatus);
+}
+
 void launch_ilu_apply_pipe(Handle& h, const double* r, double* z, cudaStream_t s) {
-  if (h.opt.precision == ISC_PRECISION_MIXED) {
+  if (h.opt.precision != ISC_PRECISION_FP64) {
     const size_t n8 = (size_t)h.n * 8;
     sweep_pair<float>(h.nx, h.ny, h.nz, h.rowptr, h.J32, h.dinv32, r, h.vec32, h.vec32 + n8, z, h.pipe, h.dstatus, s);
     return;

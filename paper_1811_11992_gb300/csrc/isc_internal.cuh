@@ -205,6 +205,13 @@ struct Handle {
   int* pipe = nullptr;                            // sweep counter, abort flag
   unsigned* red_counter = nullptr;                // last-block counter of the fused reductions
   double* gmres = nullptr;                        // GMRES Hessenberg, rotations, g and status (device)
+  // inner FP32 GMRES of ISC_PRECISION_MIXED_FGMRES
+  float* V32 = nullptr;                           // (inner_alloc + 1) x 8N basis
+  float* Z32 = nullptr;                           // inner_alloc x 8N preconditioned basis
+  float* w32 = nullptr;                           // 8N
+  double* gm_in = nullptr;                        // GMRES_STATE
+  double* scal_in = nullptr;                      // 256: h0, h1, ||w||^2, y
+  int inner_alloc = 0;
   double* h_ring = nullptr;                       // pinned: two slots of GMRES status (rel, 1/h, h)
   cudaEvent_t gm_ev[2] = {nullptr, nullptr};      // completion of those copies
   int restart_alloc = 0;
@@ -263,6 +270,23 @@ void launch_gmres_start(Handle& h, int m, double beta, cudaStream_t s);
 void launch_gmres_backsub(Handle& h, int jdone, int m, int off_y, cudaStream_t s);
 void launch_scale_dev(Handle& h, const double* x, double* y, cudaStream_t s);
 const double* gmres_status(const Handle& h);
+// inner FP32 GMRES of the mixed-precision scheme (precision = ISC_PRECISION_MIXED_FGMRES);
+// G is a GMRES_STATE-sized device state, vectors are FP32 of length len stored vs apart
+void launch_f32_nrm(Handle& h, int len, const double* x, float* y, double* out, cudaStream_t s);
+void launch_gmres_start_dev(double* G, int m, const double* nrm2, cudaStream_t s);
+void launch_gmres_givens_at(double* G, int j, int m, const double* h0, const double* h1, const double* nrm, cudaStream_t s);
+void launch_gmres_backsub_at(double* G, int jdone, int m, double* y, cudaStream_t s);
+void launch_scale_dev32(double* G, int len, const float* x, float* y, cudaStream_t s);
+void launch_spmv32(int nrows, const int32_t* rowptr, const int32_t* col, const float* val, const float* x, float* y,
+                   int unit_diag, cudaStream_t s);
+void launch_mdot32(Handle& h, int len, size_t vs, const float* V, int nvec, const float* w, double* out, cudaStream_t s);
+void launch_maxpy_mdot32(Handle& h, int len, size_t vs, float* w, const float* V, int nvec, const double* coef,
+                         double* out, cudaStream_t s);
+void launch_maxpy_norm32(Handle& h, int len, size_t vs, float* w, const float* V, int nvec, const double* coef,
+                         double* out, cudaStream_t s);
+void launch_comb_out32(int len, const float* V, size_t vs, int nvec, const double* coef, double* out, cudaStream_t s);
+// FP32 ILU(0) apply on FP32 vectors (the factors of the mixed-precision modes)
+void launch_ilu_apply_f32(Handle& h, const float* r, float* z, cudaStream_t s);
 // BLAS-1 with fixed-order two-stage reductions; results land in h.scal[off..]
 void launch_mdot(Handle& h, const double* V, int nvec, const double* w, int off, cudaStream_t s);
 void launch_maxpy(Handle& h, double* w, const double* V, int nvec, int coef_off, double sign, cudaStream_t s);

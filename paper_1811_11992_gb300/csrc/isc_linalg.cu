@@ -215,27 +215,36 @@ __global__ void k_well_update(int nwc, const double* __restrict__ du, size_t n8,
   bhp[w] = b + fmin(fmax(du[n8 + w], -max_dp_frac * b), max_dp_frac * b);
 }
 
+template <typename TV> struct Pair;
+template <> struct Pair<double> { using t = double2; };
+template <> struct Pair<float> { using t = float2; };
+
+// y = A x for a BSR matrix with 8x8 blocks: one warp per block row, lane (r, c)
+// holds columns 2c, 2c+1 of row r of every block (FP64, or FP32 for the inner
+// solve of the mixed-precision scheme); unit_diag: the diagonal block is I
+template <typename TV>
 __global__ void __launch_bounds__(256) k_spmv(int n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                                              const double* __restrict__ val, const double* __restrict__ x,
-                                              double* __restrict__ y, int unit_diag) {
+                                              const TV* __restrict__ val, const TV* __restrict__ x,
+                                              TV* __restrict__ y, int unit_diag) {
+  using T2 = typename Pair<TV>::t;
   const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (row >= n) return;
   const int b0 = __ldg(rowptr + row), b1 = __ldg(rowptr + row + 1);
   const int r = lane >> 2, c = (lane & 3) * 2;
-  double acc = 0.0;
+  TV acc = TV(0);
 #pragma unroll 7
   for (int b = b0; b < b1; ++b) {
     int j = __ldg(col + b);
     if (unit_diag && j == row) continue;
-    double2 v = __ldg(reinterpret_cast<const double2*>(val + (size_t)b * BB) + lane);
-    double2 xv = __ldg(reinterpret_cast<const double2*>(x + (size_t)j * 8 + c));
+    T2 v = __ldg(reinterpret_cast<const T2*>(val + (size_t)b * BB) + lane);
+    T2 xv = __ldg(reinterpret_cast<const T2*>(x + (size_t)j * 8 + c));
     acc = fma(v.x, xv.x, acc);
     acc = fma(v.y, xv.y, acc);
   }
   acc += __shfl_xor_sync(FULL, acc, 1);
   acc += __shfl_xor_sync(FULL, acc, 2);
-  if ((lane & 3) == 0) y[(size_t)row * 8 + r] = acc + (unit_diag ? x[(size_t)row * 8 + r] : 0.0);
+  if ((lane & 3) == 0) y[(size_t)row * 8 + r] = acc + (unit_diag ? x[(size_t)row * 8 + r] : TV(0));
 }
 
 // ---------------------------------------------------------- block ILU(0)
@@ -444,21 +453,21 @@ __device__ __forceinline__ int red8_index(int lane) { return ((lane >> 2) & 1) *
 
 // out[c] = V_c . w for all c < nvec <= 8 NG in one pass: w is read once and each
 // thread keeps 8 NG accumulators; UE elements per iteration for more loads in flight
-template <int NG, int UE>
-__global__ void __launch_bounds__(RED_THREADS) k_mdot_t(int len, const double* __restrict__ V, size_t vstride, int nvec,
-                                                        const double* __restrict__ w, double* __restrict__ partial,
+template <typename TV, int NG, int UE>
+__global__ void __launch_bounds__(RED_THREADS) k_mdot_t(int len, const TV* __restrict__ V, size_t vstride, int nvec,
+                                                        const TV* __restrict__ w, double* __restrict__ partial,
                                                         unsigned* counter, double* __restrict__ out) {
   __shared__ double sh[NG * 8][RED_THREADS / 32];
-  double acc[NG][8];
+  TV acc[NG][8];
 #pragma unroll
   for (int g = 0; g < NG; ++g)
 #pragma unroll
-    for (int i = 0; i < 8; ++i) acc[g][i] = 0.0;
+    for (int i = 0; i < 8; ++i) acc[g][i] = TV(0);
   const int stride = gridDim.x * blockDim.x;
   for (int e0 = blockIdx.x * blockDim.x + threadIdx.x; e0 < len; e0 += UE * stride) {
-    double we[UE];
+    TV we[UE];
 #pragma unroll
-    for (int u = 0; u < UE; ++u) we[u] = (e0 + u * stride < len) ? w[e0 + u * stride] : 0.0;
+    for (int u = 0; u < UE; ++u) we[u] = (e0 + u * stride < len) ? w[e0 + u * stride] : TV(0);
 #pragma unroll
     for (int g = 0; g < NG; ++g)
 #pragma unroll
@@ -474,7 +483,10 @@ __global__ void __launch_bounds__(RED_THREADS) k_mdot_t(int len, const double* _
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
   for (int g = 0; g < NG; ++g) {
-    const double v = warp_reduce8(acc[g], lane);
+    double a8[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a8[i] = (double)acc[g][i];
+    const double v = warp_reduce8(a8, lane);
     if ((lane & 3) == 0) sh[g * 8 + red8_index(lane)][warp] = v;
   }
   __syncthreads();
@@ -489,34 +501,34 @@ __global__ void __launch_bounds__(RED_THREADS) k_mdot_t(int len, const double* _
 
 // The middle of classical Gram-Schmidt applied twice, fused: w <- w - V coef,
 // then out = V^T w, with each V_c[e] loaded once for both (nvec <= 8 NG)
-template <int NG>
-__global__ void __launch_bounds__(RED_THREADS) k_maxpy_mdot(int len, double* __restrict__ w, const double* __restrict__ V,
+template <typename TV, int NG>
+__global__ void __launch_bounds__(RED_THREADS) k_maxpy_mdot(int len, TV* __restrict__ w, const TV* __restrict__ V,
                                                             size_t vstride, int nvec, const double* __restrict__ coef,
                                                             double* __restrict__ partial, unsigned* counter,
                                                             double* __restrict__ out) {
   __shared__ double sh[NG * 8][RED_THREADS / 32];
-  __shared__ double sc[NG * 8];
-  for (int c = threadIdx.x; c < NG * 8; c += blockDim.x) sc[c] = c < nvec ? coef[c] : 0.0;
+  __shared__ TV sc[NG * 8];
+  for (int c = threadIdx.x; c < NG * 8; c += blockDim.x) sc[c] = c < nvec ? (TV)coef[c] : TV(0);
   __syncthreads();
-  double acc[NG][8];
+  TV acc[NG][8];
 #pragma unroll
   for (int g = 0; g < NG; ++g)
 #pragma unroll
-    for (int i = 0; i < 8; ++i) acc[g][i] = 0.0;
+    for (int i = 0; i < 8; ++i) acc[g][i] = TV(0);
   const int stride = gridDim.x * blockDim.x;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) {
-    double v[NG][8];
+    TV v[NG][8];
 #pragma unroll
     for (int g = 0; g < NG; ++g)
 #pragma unroll
-      for (int i = 0; i < 8; ++i) v[g][i] = (g * 8 + i < nvec) ? V[(size_t)(g * 8 + i) * vstride + e] : 0.0;
-    double t = 0.0;
+      for (int i = 0; i < 8; ++i) v[g][i] = (g * 8 + i < nvec) ? V[(size_t)(g * 8 + i) * vstride + e] : TV(0);
+    TV t = TV(0);
 #pragma unroll
     for (int g = 0; g < NG; ++g)
 #pragma unroll
       for (int i = 0; i < 8; ++i)
         if (g * 8 + i < nvec) t = fma(sc[g * 8 + i], v[g][i], t);
-    const double we = w[e] - t;
+    const TV we = w[e] - t;
     w[e] = we;
 #pragma unroll
     for (int g = 0; g < NG; ++g)
@@ -527,7 +539,10 @@ __global__ void __launch_bounds__(RED_THREADS) k_maxpy_mdot(int len, double* __r
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
   for (int g = 0; g < NG; ++g) {
-    const double r = warp_reduce8(acc[g], lane);
+    double a8[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a8[i] = (double)acc[g][i];
+    const double r = warp_reduce8(a8, lane);
     if ((lane & 3) == 0) sh[g * 8 + red8_index(lane)][warp] = r;
   }
   __syncthreads();
@@ -541,34 +556,36 @@ __global__ void __launch_bounds__(RED_THREADS) k_maxpy_mdot(int len, double* __r
 }
 
 // s = sum_c coef[c] V_c[e] with DOT_G independent loads in flight per element
-__device__ __forceinline__ double comb(const double* __restrict__ V, size_t vstride, int nvec, const double* sc, int e) {
-  double s = 0.0;
+template <typename TV, typename TS>
+__device__ __forceinline__ TV comb(const TV* __restrict__ V, size_t vstride, int nvec, const TS* sc, int e) {
+  TV s = TV(0);
   for (int c0 = 0; c0 < nvec; c0 += DOT_G) {
-    double v[DOT_G];
+    TV v[DOT_G];
 #pragma unroll
-    for (int g = 0; g < DOT_G; ++g) v[g] = (c0 + g < nvec) ? V[(size_t)(c0 + g) * vstride + e] : 0.0;
+    for (int g = 0; g < DOT_G; ++g) v[g] = (c0 + g < nvec) ? V[(size_t)(c0 + g) * vstride + e] : TV(0);
 #pragma unroll
     for (int g = 0; g < DOT_G; ++g)
-      if (c0 + g < nvec) s = fma(sc[c0 + g], v[g], s);
+      if (c0 + g < nvec) s = fma((TV)sc[c0 + g], v[g], s);
   }
   return s;
 }
 
 // w -= sum_c coef[c] V_c and out[0] = ||w||^2 of the result
-__global__ void __launch_bounds__(RED_THREADS) k_maxpy_norm(int len, double* __restrict__ w, const double* __restrict__ V,
+template <typename TV>
+__global__ void __launch_bounds__(RED_THREADS) k_maxpy_norm(int len, TV* __restrict__ w, const TV* __restrict__ V,
                                                             size_t vstride, int nvec, const double* __restrict__ coef,
                                                             double* __restrict__ partial, unsigned* counter,
                                                             double* __restrict__ out) {
   __shared__ double sh[RED_THREADS / 32];
-  __shared__ double sc[MAX_VEC];
-  for (int c = threadIdx.x; c < nvec; c += blockDim.x) sc[c] = coef[c];
+  __shared__ TV sc[MAX_VEC];
+  for (int c = threadIdx.x; c < nvec; c += blockDim.x) sc[c] = (TV)coef[c];
   __syncthreads();
   const int stride = gridDim.x * blockDim.x;
   double nrm = 0.0;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) {
-    const double we = w[e] - comb(V, vstride, nvec, sc, e);
+    const TV we = w[e] - comb<TV, TV>(V, vstride, nvec, sc, e);
     w[e] = we;
-    nrm = fma(we, we, nrm);
+    nrm = fma((double)we, (double)we, nrm);
   }
   nrm = block_sum(nrm, sh);
   if (threadIdx.x == 0) partial[blockIdx.x] = nrm;
@@ -583,7 +600,7 @@ __global__ void k_maxpy(int len, double* __restrict__ w, const double* __restric
   __syncthreads();
   const int stride = gridDim.x * blockDim.x;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride)
-    w[e] = fma(sign, comb(V, vstride, nvec, sc, e), w[e]);
+    w[e] = fma(sign, comb<double, double>(V, vstride, nvec, sc, e), w[e]);
 }
 
 __global__ void k_axpby(int len, double a, const double* __restrict__ x, double b, double* __restrict__ y) {
@@ -653,16 +670,56 @@ __global__ void k_gmres_backsub(int jdone, int m, const double* __restrict__ H, 
   for (int i = jdone - 1; i >= 0; --i) {
     double acc = g[i];
     for (int k = i + 1; k < jdone; ++k) acc -= H[(size_t)i * m + k] * y[k];
-    y[i] = acc / H[(size_t)i * m + i];
+    const double d = H[(size_t)i * m + i];
+    y[i] = d != 0.0 ? acc / d : 0.0;  // a zero pivot only follows an exact (lucky) breakdown
   }
 }
 
 // y = (*coef) x with the coefficient read on the device
-__global__ void k_scale_dev(int len, const double* __restrict__ coef, const double* __restrict__ x,
-                            double* __restrict__ y) {
-  const double a = coef[0];
+template <typename TV>
+__global__ void k_scale_dev(int len, const double* __restrict__ coef, const TV* __restrict__ x, TV* __restrict__ y) {
+  const TV a = (TV)coef[0];
   const int stride = gridDim.x * blockDim.x;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) y[e] = a * x[e];
+}
+
+// ------------------------------------------------ inner FP32 GMRES (mixed precision)
+// y32 = (float) x and out = ||y32||^2
+__global__ void __launch_bounds__(RED_THREADS) k_f32_nrm(int len, const double* __restrict__ x, float* __restrict__ y,
+                                                         double* __restrict__ partial, unsigned* counter,
+                                                         double* __restrict__ out) {
+  __shared__ double sh[RED_THREADS / 32];
+  const int stride = gridDim.x * blockDim.x;
+  double nrm = 0.0;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) {
+    const float v = (float)x[e];
+    y[e] = v;
+    nrm = fma((double)v, (double)v, nrm);
+  }
+  nrm = block_sum(nrm, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = nrm;
+  last_block_finish(1, gridDim.x, partial, counter, out);
+}
+
+// g = (beta, 0, ..., 0) with beta = sqrt(*nrm2) read on the device; inv = 1 / beta (0 for a zero vector)
+__global__ void k_gmres_start_dev(int m, const double* __restrict__ nrm2, double* __restrict__ g,
+                                  double* __restrict__ inv) {
+  const int i = threadIdx.x;
+  const double beta = sqrt(fmax(*nrm2, 0.0));
+  if (i <= m) g[i] = (i == 0) ? beta : 0.0;
+  if (i == 0) *inv = (beta > 0.0 && isfinite(beta)) ? 1.0 / beta : 0.0;
+}
+
+// out = sum_c coef[c] V_c (FP32 basis, FP64 result)
+template <typename TV>
+__global__ void k_comb_out(int len, const TV* __restrict__ V, size_t vstride, int nvec, const double* __restrict__ coef,
+                           double* __restrict__ out) {
+  __shared__ TV sc[MAX_VEC];
+  for (int c = threadIdx.x; c < nvec; c += blockDim.x) sc[c] = (TV)coef[c];
+  __syncthreads();
+  const int stride = gridDim.x * blockDim.x;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride)
+    out[e] = (double)comb<TV, TV>(V, vstride, nvec, sc, e);
 }
 
 // ------------------------------------------------------------ Newton update
@@ -744,7 +801,7 @@ void launch_well_update(Handle& h, cudaStream_t s) {
 void launch_spmv(int nrows, const int32_t* rowptr, const int32_t* col, const double* val, const double* x, double* y,
                  int unit_diag, cudaStream_t s) {
   int tb = 256;
-  k_spmv<<<(int)(((size_t)nrows * 32 + tb - 1) / tb), tb, 0, s>>>(nrows, rowptr, col, val, x, y, unit_diag);
+  k_spmv<double><<<(int)(((size_t)nrows * 32 + tb - 1) / tb), tb, 0, s>>>(nrows, rowptr, col, val, x, y, unit_diag);
 }
 
 void launch_ilu_factor(Handle& h, cudaStream_t s) { launch_ilu_factor_pipe(h, s); }
@@ -786,7 +843,7 @@ void launch_gmres_backsub(Handle& h, int jdone, int m, int off_y, cudaStream_t s
 
 void launch_scale_dev(Handle& h, const double* x, double* y, cudaStream_t s) {
   // coefficient: 1 / h_{j+1,j} from the last k_gmres_givens
-  k_scale_dev<<<grid_for(h.vlen, 256), 256, 0, s>>>(h.vlen, h.gmres + GM_MAX * (GM_MAX + 3) + GM_MAX + 2, x, y);
+  k_scale_dev<double><<<grid_for(h.vlen, 256), 256, 0, s>>>(h.vlen, h.gmres + GM_MAX * (GM_MAX + 3) + GM_MAX + 2, x, y);
 }
 
 const double* gmres_status(const Handle& h) { return h.gmres + GM_MAX * (GM_MAX + 3) + GM_MAX + 1; }
@@ -799,45 +856,56 @@ void launch_update(Handle& h, cudaStream_t s) {
   k_update<<<(h.n + 127) / 128, 128, 0, s>>>(h.n, h.u, h.du, h.opt.max_dp_frac, h.opt.max_dT);
 }
 
-void launch_mdot(Handle& h, const double* V, int nvec, const double* w, int off, cudaStream_t s) {
-  const int len = h.vlen;
+// Gram-Schmidt passes over vectors of length len stored vs apart (FP64 for the
+// outer Krylov solve, FP32 for the inner one of the mixed-precision scheme);
+// results (FP64) go to out; reductions use the handle's partial/counter buffers
+template <typename TV>
+bool mdot_t(Handle& h, int len, size_t vs, const TV* V, int nvec, const TV* w, double* out, cudaStream_t s) {
   // one pass over w for up to 32 vectors; grid and unrolling as measured best on GB300
-  // (576,000-element vectors: 22 / 43 / 53 / 70 us for 8 / 16 / 24 / 30 vectors against
-  // 49 / 57 / 70 / 100 us with the vectors split over blockIdx.y)
-  const size_t vs = (size_t)h.vstride;
-  double* out = h.scal + off;
+  // (576,000-element FP64 vectors: 22 / 43 / 53 / 70 us for 8 / 16 / 24 / 30 vectors
+  // against 49 / 57 / 70 / 100 us with the vectors split over blockIdx.y)
   switch ((nvec + 7) / 8) {
-    case 1: k_mdot_t<1, 1><<<2 * h.red_blocks, RED_THREADS, 0, s>>>(len, V, vs, nvec, w, h.partial, h.red_counter, out); return;
-    case 2: k_mdot_t<2, 2><<<2 * h.red_blocks, RED_THREADS, 0, s>>>(len, V, vs, nvec, w, h.partial, h.red_counter, out); return;
-    case 3: k_mdot_t<3, 1><<<h.red_blocks, RED_THREADS, 0, s>>>(len, V, vs, nvec, w, h.partial, h.red_counter, out); return;
-    case 4: k_mdot_t<4, 1><<<h.red_blocks, RED_THREADS, 0, s>>>(len, V, vs, nvec, w, h.partial, h.red_counter, out); return;
-    default: break;
+    case 1: k_mdot_t<TV, 1, 1><<<2 * h.red_blocks, RED_THREADS, 0, s>>>(len, V, vs, nvec, w, h.partial, h.red_counter, out); return true;
+    case 2: k_mdot_t<TV, 2, 2><<<2 * h.red_blocks, RED_THREADS, 0, s>>>(len, V, vs, nvec, w, h.partial, h.red_counter, out); return true;
+    case 3: k_mdot_t<TV, 3, 1><<<h.red_blocks, RED_THREADS, 0, s>>>(len, V, vs, nvec, w, h.partial, h.red_counter, out); return true;
+    case 4: k_mdot_t<TV, 4, 1><<<h.red_blocks, RED_THREADS, 0, s>>>(len, V, vs, nvec, w, h.partial, h.red_counter, out); return true;
+    default: return false;
   }
+}
+
+template <typename TV>
+bool maxpy_mdot_t(Handle& h, int len, size_t vs, TV* w, const TV* V, int nvec, const double* coef, double* out,
+                  cudaStream_t s) {
+  switch ((nvec + 7) / 8) {
+    case 1: k_maxpy_mdot<TV, 1><<<h.red_blocks, RED_THREADS, 0, s>>>(len, w, V, vs, nvec, coef, h.partial, h.red_counter, out); return true;
+    case 2: k_maxpy_mdot<TV, 2><<<h.red_blocks, RED_THREADS, 0, s>>>(len, w, V, vs, nvec, coef, h.partial, h.red_counter, out); return true;
+    case 3: k_maxpy_mdot<TV, 3><<<h.red_blocks, RED_THREADS, 0, s>>>(len, w, V, vs, nvec, coef, h.partial, h.red_counter, out); return true;
+    case 4: k_maxpy_mdot<TV, 4><<<h.red_blocks, RED_THREADS, 0, s>>>(len, w, V, vs, nvec, coef, h.partial, h.red_counter, out); return true;
+    default: return false;
+  }
+}
+
+template <typename TV>
+void maxpy_norm_t(Handle& h, int len, size_t vs, TV* w, const TV* V, int nvec, const double* coef, double* out,
+                  cudaStream_t s) {
+  // 608 blocks: 20.7 / 28 / 40 / 46 us for 8 / 16 / 24 / 30 FP64 vectors against 23 / 36 / 51 / 60 with 304
+  k_maxpy_norm<TV><<<2 * h.red_blocks, RED_THREADS, 0, s>>>(len, w, V, vs, nvec, coef, h.partial, h.red_counter, out);
+}
+
+void launch_mdot(Handle& h, const double* V, int nvec, const double* w, int off, cudaStream_t s) {
+  if (mdot_t<double>(h, h.vlen, (size_t)h.vstride, V, nvec, w, h.scal + off, s)) return;
   dim3 grid(h.red_blocks, (nvec + DOT_G - 1) / DOT_G);
-  k_mdot<<<grid, RED_THREADS, 0, s>>>(len, V, (size_t)h.vstride, nvec, w, h.partial, h.red_counter, h.scal + off);
+  k_mdot<<<grid, RED_THREADS, 0, s>>>(h.vlen, V, (size_t)h.vstride, nvec, w, h.partial, h.red_counter, h.scal + off);
 }
 
 void launch_maxpy_mdot(Handle& h, double* w, const double* V, int nvec, int coef_off, int out_off, cudaStream_t s) {
-  const int len = h.vlen;
-  const size_t vs = (size_t)h.vstride;
-  const double* coef = h.scal + coef_off;
-  double* out = h.scal + out_off;
-  switch ((nvec + 7) / 8) {
-    case 1: k_maxpy_mdot<1><<<h.red_blocks, RED_THREADS, 0, s>>>(len, w, V, vs, nvec, coef, h.partial, h.red_counter, out); return;
-    case 2: k_maxpy_mdot<2><<<h.red_blocks, RED_THREADS, 0, s>>>(len, w, V, vs, nvec, coef, h.partial, h.red_counter, out); return;
-    case 3: k_maxpy_mdot<3><<<h.red_blocks, RED_THREADS, 0, s>>>(len, w, V, vs, nvec, coef, h.partial, h.red_counter, out); return;
-    case 4: k_maxpy_mdot<4><<<h.red_blocks, RED_THREADS, 0, s>>>(len, w, V, vs, nvec, coef, h.partial, h.red_counter, out); return;
-    default: break;
-  }
+  if (maxpy_mdot_t<double>(h, h.vlen, (size_t)h.vstride, w, V, nvec, h.scal + coef_off, h.scal + out_off, s)) return;
   launch_maxpy(h, w, V, nvec, coef_off, -1.0, s);
   launch_mdot(h, V, nvec, w, out_off, s);
 }
 
 void launch_maxpy_norm(Handle& h, double* w, const double* V, int nvec, int coef_off, int out_off, cudaStream_t s) {
-  const int len = h.vlen;
-  // 608 blocks: 20.7 / 28 / 40 / 46 us for 8 / 16 / 24 / 30 vectors against 23 / 36 / 51 / 60 with 304
-  k_maxpy_norm<<<2 * h.red_blocks, RED_THREADS, 0, s>>>(len, w, V, (size_t)h.vstride, nvec, h.scal + coef_off, h.partial,
-                                                    h.red_counter, h.scal + out_off);
+  maxpy_norm_t<double>(h, h.vlen, (size_t)h.vstride, w, V, nvec, h.scal + coef_off, h.scal + out_off, s);
 }
 
 void launch_maxpy(Handle& h, double* w, const double* V, int nvec, int coef_off, double sign, cudaStream_t s) {
@@ -855,6 +923,44 @@ void launch_scale_copy(int n, double a, const double* x, double* y, cudaStream_t
 
 void launch_axpy_dev(int n, const double* coef, double sign, const double* x, double* y, cudaStream_t s) {
   k_axpy_dev<<<grid_for(n, 256), 256, 0, s>>>(n, coef, sign, x, y);
+}
+
+// ---- inner FP32 GMRES of the mixed-precision scheme (state G: GMRES_STATE doubles)
+void launch_f32_nrm(Handle& h, int len, const double* x, float* y, double* out, cudaStream_t s) {
+  k_f32_nrm<<<2 * h.red_blocks, RED_THREADS, 0, s>>>(len, x, y, h.partial, h.red_counter, out);
+}
+void launch_gmres_start_dev(double* G, int m, const double* nrm2, cudaStream_t s) {
+  k_gmres_start_dev<<<1, GM_MAX + 1, 0, s>>>(m, nrm2, G + GM_MAX * (GM_MAX + 3), G + GM_MAX * (GM_MAX + 3) + GM_MAX + 2);
+}
+void launch_gmres_givens_at(double* G, int j, int m, const double* h0, const double* h1, const double* nrm, cudaStream_t s) {
+  k_gmres_givens<<<1, 32, 0, s>>>(j, m, 1.0, h0, h1, nrm, G, G + GM_MAX * (GM_MAX + 1), G + GM_MAX * (GM_MAX + 2),
+                                  G + GM_MAX * (GM_MAX + 3), G + GM_MAX * (GM_MAX + 3) + GM_MAX + 1);
+}
+void launch_gmres_backsub_at(double* G, int jdone, int m, double* y, cudaStream_t s) {
+  k_gmres_backsub<<<1, 32, 0, s>>>(jdone, m, G, G + GM_MAX * (GM_MAX + 3), y);
+}
+void launch_scale_dev32(double* G, int len, const float* x, float* y, cudaStream_t s) {
+  // coefficient at the status slot used by k_gmres_givens (1 / h_{j+1,j}) and k_gmres_start_dev (1 / beta)
+  k_scale_dev<float><<<grid_for(len, 256), 256, 0, s>>>(len, G + GM_MAX * (GM_MAX + 3) + GM_MAX + 2, x, y);
+}
+void launch_spmv32(int nrows, const int32_t* rowptr, const int32_t* col, const float* val, const float* x, float* y,
+                   int unit_diag, cudaStream_t s) {
+  const int tb = 256;
+  k_spmv<float><<<(int)(((size_t)nrows * 32 + tb - 1) / tb), tb, 0, s>>>(nrows, rowptr, col, val, x, y, unit_diag);
+}
+void launch_mdot32(Handle& h, int len, size_t vs, const float* V, int nvec, const float* w, double* out, cudaStream_t s) {
+  mdot_t<float>(h, len, vs, V, nvec, w, out, s);
+}
+void launch_maxpy_mdot32(Handle& h, int len, size_t vs, float* w, const float* V, int nvec, const double* coef,
+                         double* out, cudaStream_t s) {
+  maxpy_mdot_t<float>(h, len, vs, w, V, nvec, coef, out, s);
+}
+void launch_maxpy_norm32(Handle& h, int len, size_t vs, float* w, const float* V, int nvec, const double* coef,
+                         double* out, cudaStream_t s) {
+  maxpy_norm_t<float>(h, len, vs, w, V, nvec, coef, out, s);
+}
+void launch_comb_out32(int len, const float* V, size_t vs, int nvec, const double* coef, double* out, cudaStream_t s) {
+  k_comb_out<float><<<grid_for(len, 256), 256, 0, s>>>(len, V, vs, nvec, coef, out);
 }
 
 }  // namespace isc

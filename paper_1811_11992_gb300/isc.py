@@ -28,9 +28,9 @@ STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "out of device 
           -9: "device wait timed out", -10: "not implemented", -11: "call order violated"}
 KRYLOV = {"gmres": 0, "bicgstab": 1}
 PREC = {"none": 0, "bjacobi": 1, "bilu0": 2, "ilu0": 2, "cpr": 3}
-PRECISION = {"fp64": 0, "mixed": 1}
+PRECISION = {"fp64": 0, "mixed": 1, "mixed_fgmres": 2}
 K_CLASSES = ("props", "flux", "norm", "gj", "ilu_factor", "spmv", "prec_apply", "blas1", "update", "adjoint",
-             "cpr")
+             "cpr", "spmv32")
 
 
 class isc_grid(C.Structure):
@@ -80,7 +80,8 @@ class isc_options(C.Structure):
     _fields_ = [("krylov", C.c_int32), ("restart", C.c_int32), ("prec", C.c_int32), ("decouple", C.c_int32),
                 ("tol_lin", C.c_double), ("maxit_lin", C.c_int32), ("tol_newton", C.c_double),
                 ("maxit_newton", C.c_int32), ("max_dp_frac", C.c_double), ("max_dT", C.c_double),
-                ("profile", C.c_int32), ("precision", C.c_int32), ("stream", C.c_void_p)]
+                ("profile", C.c_int32), ("precision", C.c_int32), ("stream", C.c_void_p),
+                ("inner_its", C.c_int32)]
 
 
 class isc_newton_info(C.Structure):
@@ -95,7 +96,7 @@ class isc_step_info(C.Structure):
 
 
 class isc_stats(C.Structure):
-    _fields_ = [("ms", C.c_double * 11), ("launches", C.c_int64 * 11), ("calls", C.c_int64 * 11)]
+    _fields_ = [("ms", C.c_double * 12), ("launches", C.c_int64 * 12), ("calls", C.c_int64 * 12)]
 
 
 class isc_adjoint_spec(C.Structure):
