@@ -49,6 +49,8 @@ def parse():
                     help="time only the headline step (no mixed, CPR-PF, adjoint or end-to-end legs); for profiling")
     ap.add_argument("--grid", default=None,
                     help="NXxNYxNZ: run the same field recipe on a smaller grid (profiling captures)")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "mixed_fgmres"],
+                    help="precision of the timed step's linear solve (the headline is fp64)")
     ap.add_argument("--workload", default="field", choices=["field", "mixed", "large"],
                     help="field: 60x60x20 (the headline); mixed: 100x100x30; large: 200x200x50, 3 facies, 5-spot")
     return ap.parse_args()
@@ -162,7 +164,7 @@ def run_isc(args):
     build.build()
     case = field_case(args.grid, args.workload)
     dt = case.dt0
-    g = isc.Simulator(case, profile=1)
+    g = isc.Simulator(case, profile=1, precision=args.precision, inner_its=INNER_ITS)
     g.init_equilibrium()
     n = case.n
     # resident snapshot of the starting iterate (torch owns the buffers)
@@ -286,13 +288,15 @@ def run_isc(args):
     # roofline of the dominant kernel class
     launches = sum(v["launches"] for v in stats.values())
     dom = max(stats, key=lambda k: stats[k]["ms"])
-    roof = roofline(dom, stats, g, case, kry)
+    roof = roofline(dom, stats, g, case, kry, args.precision)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
+        "data": "synthetic",
         "config": workload_config(case, dt, {"parallelism": f"replicas x{world}",
-                                             "krylov_iterations_per_step": statistics.median(kry) if kry else None},
+                                             "krylov_iterations_per_step": statistics.median(kry) if kry else None,
+                                             "precision": args.precision},
                                   g.nnzb),
         "e2e": e2e,
         "gpu_launches": launches,
@@ -380,7 +384,7 @@ def spmv32_roofline(stats, case, nnzb):
             "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
 
 
-def roofline(dom, stats, g, case, kry):
+def roofline(dom, stats, g, case, kry, precision="fp64"):
     """Algorithmic bytes (or flops) per call of the dominant kernel class over its
     average CUDA-event duration."""
     n, nnzb = case.n, g.nnzb
@@ -424,9 +428,11 @@ def roofline(dom, stats, g, case, kry):
     else:
         out.update(bound="hbm", achieved=ach_gbs, peak=hbm, unit="GB/s", frac=ach_gbs / hbm if hbm else None,
                    peak_source="MEASURED_PEAKS.json hbm_gbs")
-    # DRAM bytes per call from one ncu capture of the current kernels on this grid
-    measured = MEASURED_TRAFFIC.get((dom, case.nx, case.ny, case.nz))
+    # DRAM bytes per call from one ncu capture of the current kernels on this grid (FP64 solve)
+    measured = MEASURED_TRAFFIC.get((dom, case.nx, case.ny, case.nz)) if precision == "fp64" else None
     out["traffic"] = measured[0] if measured else None
+    if precision != "fp64":
+        out["note"] = "bytes and flops of the FP64 operands; this step ran its preconditioner in FP32"
     if measured:
         out["traffic_source"] = measured[1]
     return out
@@ -485,7 +491,8 @@ def run_reference(args):
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
+        "data": "synthetic",
         "config": workload_config(case, case.dt0, {"parallelism": "host oracle, 1 thread"}),
         "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1,
                          "sample": f"one oracle Newton step per timed step on a 30x30x10 block ({ncell} cells), "
