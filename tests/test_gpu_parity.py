@@ -137,9 +137,9 @@ def test_spmv_and_ilu0_apply_match_oracle(Simulator, name):
 @pytest.mark.parametrize("dims", [(2, 1, 1), (3, 1, 1), (33, 1, 1), (5, 4, 3), (17, 3, 2), (13, 7, 5)],
                          ids=lambda d: "x".join(map(str, d)))
 def test_row_panel_spmv_on_ragged_grids(Simulator, dims):
-    """The decoupled SpMV streams panels of 16 block rows (32 in FP32) with bulk
-    copies: cell counts below, at and across panel boundaries, rows with 1 to 6
-    neighbours; exact up to summation order against the oracle's BSR product."""
+    """The decoupled SpMV on degenerate and ragged grids (single cells in a line,
+    odd sizes, rows with 1 to 6 neighbours): exact up to summation order against
+    the oracle's BSR product."""
     case = inp.small_box(*dims)
     a = inp.random_state(case, 515)
     b = inp.random_state(case, 616)
