@@ -140,13 +140,21 @@ def field_case(grid=None, workload="field"):
     return inp.config({"field": 2, "mixed": 3, "large": 5}[workload])
 
 
+def l2_bytes():
+    try:
+        import torch
+        return int(torch.cuda.get_device_properties(torch.cuda.current_device()).L2_cache_size)
+    except Exception:
+        return 126 * 2**20
+
+
 def workload_config(case, dt, extra, nnzb=None):
     nnzb = nnzb if nnzb is not None else case.n * 7
     c = {"workload": f"{case.name} ({case.n} cells, 8 unknowns/cell), first Newton step of "
                      f"the first time step (dt {dt:.0f} s) from the ignited initial state",
          "solver": "GMRES(30), block ILU(0), Gauss-Jordan decoupling, FP64, tol_lin 1e-6",
          "l2": f"inputs larger than L2: the FP64 Jacobian ({nnzb * 512 / 1e6:.0f} MB) and staged properties "
-               f"({case.n * 16 * 9 * 8 / 1e6:.0f} MB) exceed the 129 MB L2"}
+               f"({case.n * 16 * 9 * 8 / 1e6:.0f} MB) exceed the {l2_bytes() / 2**20:.0f} MiB L2"}
     c.update(extra)
     return c
 
@@ -206,6 +214,7 @@ def run_isc(args):
     value = job_throughput(world, args.steps, ms_total)
     kry = [i.krylov_iterations for i in infos]
     e2e = mixed = mixed_fgmres = cpr_block = None
+    mst = fst = None
     if not args.no_extras:
         # end-to-end through the C ABI with host buffers
         uh, ch = g.get_state()
@@ -257,7 +266,7 @@ def run_isc(args):
                 "solve_speedup_vs_fp64": solve_fp64 / solve_leg if solve_leg > 0 else None}
 
         # mixed precision on the same step: FP32 ILU(0) factors and sweeps inside the FP64 GMRES
-        _, mixed = precision_leg("mixed")
+        mst, mixed = precision_leg("mixed")
         # FP32 inner GMRES (FP32 SpMV, Gram-Schmidt and ILU(0)) inside the flexible FP64 GMRES
         fst, mixed_fgmres = precision_leg("mixed_fgmres", inner_its=INNER_ITS)
         mixed_fgmres["inner_its"] = INNER_ITS
@@ -303,6 +312,7 @@ def run_isc(args):
         "kernel_ms": {k: round(v["ms"], 3) for k, v in stats.items()},
         "kernel_launches": {k: v["launches"] for k, v in stats.items()},
         "roofline": roof,
+        "hbm": hbm_table(stats, mst, fst, case, g.nnzb),
         "clocks": clocks,
         "mixed": mixed,
         "mixed_fgmres": mixed_fgmres,
@@ -382,6 +392,31 @@ def spmv32_roofline(stats, case, nnzb):
     ach = byts / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
     return {"kernel": "k_spmv<float>", "bound": "hbm", "calls": calls, "ms_per_call": ms, "bytes_per_call": byts,
             "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
+
+
+def class_gbs(stats, cls, byts):
+    """Algorithmic bytes per call of one kernel class over its mean CUDA-event time."""
+    hbm = measured_peaks().get("hbm_gbs", 6800.0)
+    s = stats.get(cls, {"calls": 0, "ms": 0.0})
+    if not s["calls"] or s["ms"] <= 0:
+        return None
+    ms = s["ms"] / s["calls"]
+    gbs = byts / (ms * 1e-3) / 1e9
+    return {"ms_per_call": ms, "bytes_per_call": byts, "gbs": gbs, "hbm_frac": gbs / hbm}
+
+
+def hbm_table(stats64, stats_mixed, stats_fg, case, nnzb):
+    """SpMV and preconditioner-apply GB/s against the measured HBM bandwidth (the
+    metric's second part): FP64 from the headline step, the FP32 sweeps from the
+    `mixed` leg, the FP32 SpMV from the `mixed_fgmres` leg."""
+    n, off = case.n, nnzb - case.n
+    out = {"spmv_fp64": class_gbs(stats64, "spmv", off * BLOCK_BYTES + 3 * n * 64),
+           "ilu_apply_fp64": class_gbs(stats64, "prec_apply", off * BLOCK_BYTES + 2 * n * 512 + 4 * n * 64)}
+    if stats_mixed is not None:
+        out["ilu_apply_fp32"] = class_gbs(stats_mixed, "prec_apply", off * 260 + 2 * n * 256 + 2 * n * 64 + 2 * n * 32)
+    if stats_fg is not None:
+        out["spmv_fp32"] = class_gbs(stats_fg, "spmv32", off * 260 + 3 * n * 32)
+    return out
 
 
 def roofline(dom, stats, g, case, kry, precision="fp64"):
