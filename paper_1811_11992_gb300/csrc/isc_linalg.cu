@@ -80,36 +80,44 @@ __global__ void __launch_bounds__(256) k_gj(int n, const int32_t* __restrict__ r
       a[m][r] = v;
     }
   }
+  // Magnitudes are compared as the integer bit patterns of |a| (IEEE order equals
+  // numeric order for non-negative values): the pivot search and the singularity
+  // test then run on the integer units, not on GB300's scarce FP64 pipe, and choose
+  // exactly what the floating-point compares would.
+  auto mag = [](double v) { return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull; };
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
     const int pc = d * 8 + k;
     const int pl = pc & 31, pm = pc >> 5;
     int piv = k;
     if (lane == pl) {
-      double best = -1.0;
+      unsigned long long best = 0ull;
+      bool first = true;
 #pragma unroll
       for (int r = k; r < 8; ++r) {
-        double v = fabs(pm ? a[1][r] : a[0][r]);
-        if (v > best) {
+        const unsigned long long v = mag(pm ? a[1][r] : a[0][r]);
+        if (first || v > best) {
           best = v;
           piv = r;
+          first = false;
         }
       }
     }
     piv = __shfl_sync(FULL, piv, pl);
     // max |a| of row piv inside the diagonal block (singularity test)
-    double rm = 0.0;
+    unsigned long long rmb = 0ull;
 #pragma unroll
     for (int m = 0; m < 2; ++m) {
       int cc = lane + 32 * m;
       if (cc >= d * 8 && cc < d * 8 + 8) {
 #pragma unroll
         for (int r = 0; r < 8; ++r)
-          if (r == piv) rm = fmax(rm, fabs(a[m][r]));
+          if (r == piv) rmb = max(rmb, mag(a[m][r]));
       }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) rm = fmax(rm, __shfl_xor_sync(FULL, rm, o));
+    for (int o = 16; o > 0; o >>= 1) rmb = max(rmb, (unsigned long long)__shfl_xor_sync(FULL, rmb, o));
+    const double rm = __longlong_as_double((long long)rmb);
     // swap rows k and piv
     if (piv != k) {
 #pragma unroll
