@@ -363,6 +363,14 @@ int isc_bsr_spmv_device(int32_t nrows, const int32_t* d_rowptr, const int32_t* d
 int isc_bilu0_apply_noalloc(int32_t nx, int32_t ny, int32_t nz, const int32_t* d_rowptr, const double* d_A,
                             const double* d_Dinv, const double* d_r, double* d_z, void* stream);
 
+/* Numerics self-check of the device reciprocal used for the pivots of the
+ * Gauss-Jordan decoupling and of the block ILU(0) / block-Jacobi inverses
+ * (Newton-Raphson from the hardware approximation): for n host doubles x,
+ * y[i] = that reciprocal and z[i] = the device's 1.0 / x[i]. Host buffers,
+ * allocated and freed inside (a diagnostic, not a hot-path call); synchronous
+ * on the default stream. n < 0 or NULL pointers: ISC_ERR_INVALID_ARG. */
+int isc_check_reciprocal(int32_t n, const double* x, double* y, double* z);
+
 /* ------------------------------------------------------------ sensitivities */
 
 /* Parameters theta of the sensitivity analysis. The paper computes no

@@ -1268,6 +1268,23 @@ int isc_spmv(isc_handle* h, const double* x, double* y) {
   return ISC_OK;
 }
 
+int isc_check_reciprocal(int32_t n, const double* x, double* y, double* z) {
+  if (n < 0 || (n > 0 && (!x || !y || !z))) return ISC_ERR_INVALID_ARG;
+  if (n == 0) return ISC_OK;
+  double* d = nullptr;
+  if (cudaMalloc(&d, sizeof(double) * 3 * (size_t)n) != cudaSuccess) return ISC_ERR_NOMEM;
+  int st = ISC_OK;
+  if (cudaMemcpy(d, x, sizeof(double) * n, cudaMemcpyHostToDevice) != cudaSuccess) st = ISC_ERR_CUDA;
+  if (st == ISC_OK) {
+    launch_recip_check(n, d, d + n, d + 2 * (size_t)n, 0);
+    if (cudaMemcpy(y, d + n, sizeof(double) * n, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(z, d + 2 * (size_t)n, sizeof(double) * n, cudaMemcpyDeviceToHost) != cudaSuccess)
+      st = ISC_ERR_CUDA;
+  }
+  cudaFree(d);
+  return st;
+}
+
 int isc_precond_apply(isc_handle* h, const double* r, double* z) {
   if (!h || !r || !z) return ISC_ERR_INVALID_ARG;
   if (!h->prec_built) return set_err(h, ISC_ERR_STATE, "build the preconditioner first");

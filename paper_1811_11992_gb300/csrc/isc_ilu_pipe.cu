@@ -82,6 +82,19 @@ __device__ __forceinline__ Pen make_pen(int nx, int ny, int nz, int j, int k, in
 
 __device__ __forceinline__ int row_start(const Pen& P, int x) { return P.base0 + x * P.L + (x > 0 ? 2 * x - 1 : 0); }
 
+// |v| as an unsigned integer whose order is the numeric order of |v| (IEEE 754)
+template <typename T> struct MagBits;
+template <> struct MagBits<double> {
+  using U = unsigned long long;
+  static constexpr U INF = 0x7ff0000000000000ull;
+  static __device__ __forceinline__ U get(double v) { return (U)__double_as_longlong(v) & 0x7fffffffffffffffull; }
+};
+template <> struct MagBits<float> {
+  using U = unsigned;
+  static constexpr U INF = 0x7f800000u;
+  static __device__ __forceinline__ U get(float v) { return (U)__float_as_int(v) & 0x7fffffffu; }
+};
+
 // Vector element types of the sweeps: FP64 (all-FP64 solve) or FP32 (factors,
 // off-diagonal blocks and the hand-off vector of the mixed-precision solve).
 template <typename T> struct V2;
@@ -508,16 +521,18 @@ __global__ void __launch_bounds__(FWARPS * 32) k_ilu_factor_pipe(int nx, int ny,
       __syncwarp();
       bool bad = false;
       for (int kp = 0; kp < 8; ++kp) {
+        // pivot search on the integer bit patterns of |D| (same choice as a float compare;
+        // keeps the FP64 pipe out of the wavefront's dependent chain)
         int piv = kp;
-        T best = T(-1);
+        typename MagBits<T>::U best = 0;
         for (int q = kp; q < 8; ++q) {
-          const T v = fabs(sD[q * 8 + kp]);
-          if (v > best) {
+          const typename MagBits<T>::U v = MagBits<T>::get(sD[q * 8 + kp]);
+          if (q == kp || v > best) {
             best = v;
             piv = q;
           }
         }
-        if (!(best > T(0)) || !isfinite(best)) {
+        if (best == 0 || best >= MagBits<T>::INF) {  // zero column, or inf / NaN
           bad = true;
           break;
         }
@@ -533,7 +548,7 @@ __global__ void __launch_bounds__(FWARPS * 32) k_ilu_factor_pipe(int nx, int ny,
           }
         }
         __syncwarp();
-        const T inv = T(1) / sD[kp * 8 + kp];
+        const T inv = recip_nr(sD[kp * 8 + kp]);
         const T f = sD[r * 8 + kp];
         __syncwarp();
         if (r == kp) {

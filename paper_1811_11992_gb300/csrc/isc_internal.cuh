@@ -15,6 +15,27 @@ constexpr int NU = 8;
 constexpr int NC = 6;
 constexpr int BS = 8;
 constexpr int BB = 64;          // doubles per 8x8 block
+// 1/x by Newton-Raphson iteration (r <- r + r (1 - x r), each step squaring the
+// relative error) from the hardware approximation rcp.approx.ftz.f64 (about 20
+// correct bits): two steps reach full double precision (within 1 ulp of the
+// correctly rounded quotient; isc_check_reciprocal compares it with 1.0 / x).
+// Subnormal, zero, infinite and NaN x, and |x| >= 2^1022 (whose reciprocal is
+// subnormal, which the approximation flushes to zero) take the ordinary division. A pivot
+// reciprocal costs 4 DFMA this way instead of the division's longer sequence,
+// which matters on GB300's narrow FP64 pipe inside the factorisation wavefront.
+#ifdef __CUDACC__
+__device__ __forceinline__ double recip_nr(double x) {
+  const unsigned long long e = (unsigned long long)__double_as_longlong(x) & 0x7ff0000000000000ull;
+  if (e == 0ull || e >= 0x7fd0000000000000ull) return 1.0 / x;
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  double t = fma(-x, r, 1.0);
+  r = fma(r, t, r);
+  t = fma(-x, r, 1.0);
+  return fma(r, t, r);
+}
+__device__ __forceinline__ float recip_nr(float x) { return 1.0f / x; }
+#endif
 constexpr int NQ = 16;          // staged face quantities per cell
 constexpr int NQD = NQ * 9;     // doubles per cell in the staged buffer (value + 8 tangents)
 constexpr double R_GAS = 8.314462618;
@@ -285,6 +306,7 @@ void launch_maxpy_mdot32(Handle& h, int len, size_t vs, float* w, const float* V
 void launch_maxpy_norm32(Handle& h, int len, size_t vs, float* w, const float* V, int nvec, const double* coef,
                          double* out, cudaStream_t s);
 void launch_comb_out32(int len, const float* V, size_t vs, int nvec, const double* coef, double* out, cudaStream_t s);
+void launch_recip_check(int n, const double* x, double* y, double* z, cudaStream_t s);
 // FP32 ILU(0) apply on FP32 vectors (the factors of the mixed-precision modes)
 void launch_ilu_apply_f32(Handle& h, const float* r, float* z, cudaStream_t s);
 // BLAS-1 with fixed-order two-stage reductions; results land in h.scal[off..]

@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(256) k_gj(int n, const int32_t* __restrict__ r
       if (lane == 0) atomicOr(dstatus, DS_SINGULAR);
       return;
     }
-    const double inv = 1.0 / pv;
+    const double inv = recip_nr(pv);
 #pragma unroll
     for (int m = 0; m < 2; ++m) a[m][k] = a[m][k] * inv;
 #pragma unroll
@@ -307,17 +307,18 @@ __global__ void __launch_bounds__(256) k_ilu_factor(int nx, int ny, int nz, cons
   // invert D by Gauss-Jordan with partial pivoting
   for (int k = 0; k < 8; ++k) {
     if (t == 0 && active) {
+      // pivot search on the integer bit patterns of |D| (the same choice as a float compare)
       int piv = k;
-      double best = -1.0;
+      unsigned long long best = 0ull;
       for (int q = k; q < 8; ++q) {
-        double v = fabs(sD[g][q * 8 + k]);
-        if (v > best) {
+        const unsigned long long v = (unsigned long long)__double_as_longlong(sD[g][q * 8 + k]) & 0x7fffffffffffffffull;
+        if (q == k || v > best) {
           best = v;
           piv = q;
         }
       }
       spiv[g] = piv;
-      if (!(best > 0.0) || !isfinite(best)) sbad[g] = 1;
+      if (best == 0ull || best >= 0x7ff0000000000000ull) sbad[g] = 1;  // zero column, or inf / NaN
     }
     __syncthreads();
     const int piv = spiv[g];
@@ -334,8 +335,9 @@ __global__ void __launch_bounds__(256) k_ilu_factor(int nx, int ny, int nz, cons
     double f = sD[g][r * 8 + k];
     __syncthreads();
     if (active && r == k && !sbad[g]) {
-      sD[g][k * 8 + c] /= pv;
-      sI[g][k * 8 + c] /= pv;
+      const double inv = recip_nr(pv);
+      sD[g][k * 8 + c] *= inv;
+      sI[g][k * 8 + c] *= inv;
     }
     __syncthreads();
     if (active && r != k && !sbad[g]) {
@@ -730,6 +732,14 @@ __global__ void k_comb_out(int len, const TV* __restrict__ V, size_t vstride, in
     out[e] = (double)comb<TV, TV>(V, vstride, nvec, sc, e);
 }
 
+// y = recip_nr(x) and z = 1.0 / x, for the reciprocal self-check
+__global__ void k_recip_check(int n, const double* __restrict__ x, double* __restrict__ y, double* __restrict__ z) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  y[i] = recip_nr(x[i]);
+  z[i] = 1.0 / x[i];
+}
+
 // ------------------------------------------------------------ Newton update
 __global__ void k_update(int n, double* __restrict__ u, const double* __restrict__ du, double max_dp_frac,
                          double max_dT) {
@@ -969,6 +979,10 @@ void launch_maxpy_norm32(Handle& h, int len, size_t vs, float* w, const float* V
 }
 void launch_comb_out32(int len, const float* V, size_t vs, int nvec, const double* coef, double* out, cudaStream_t s) {
   k_comb_out<float><<<grid_for(len, 256), 256, 0, s>>>(len, V, vs, nvec, coef, out);
+}
+
+void launch_recip_check(int n, const double* x, double* y, double* z, cudaStream_t s) {
+  k_recip_check<<<(n + 255) / 256, 256, 0, s>>>(n, x, y, z);
 }
 
 }  // namespace isc

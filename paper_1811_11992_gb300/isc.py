@@ -151,6 +151,7 @@ _SIGS = {
     "isc_bilu0_apply_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
                                           C.c_void_p, C.c_void_p, C.c_void_p]),
     "isc_set_parameters": (C.c_int, [C.c_void_p, c_double_p, c_double_p, c_double_p]),
+    "isc_check_reciprocal": (C.c_int, [C.c_int32, c_double_p, c_double_p, c_double_p]),
     "isc_num_coupled_wells": (C.c_int32, [C.c_void_p]),
     "isc_set_well_bhp": (C.c_int, [C.c_void_p, c_double_p]),
     "isc_get_well_bhp": (C.c_int, [C.c_void_p, c_double_p]),
@@ -503,6 +504,18 @@ def bilu0_apply_noalloc(nx, ny, nz, d_rowptr, d_A, d_Dinv, d_r, d_z, stream=None
     lib = load_library()
     return lib.isc_bilu0_apply_noalloc(nx, ny, nz, C.c_void_p(d_rowptr), C.c_void_p(d_A), C.c_void_p(d_Dinv),
                                        C.c_void_p(d_r), C.c_void_p(d_z), C.c_void_p(stream) if stream else None)
+
+
+def check_reciprocal(x):
+    """(device reciprocal of the pivots, device 1.0 / x) for host doubles x."""
+    lib = load_library()
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.empty_like(x)
+    z = np.empty_like(x)
+    st = lib.isc_check_reciprocal(x.size, _dp(x), _dp(y), _dp(z))
+    if st:
+        raise IscError(st, "isc_check_reciprocal failed")
+    return y, z
 
 
 # the binding uses the C-ABI names
