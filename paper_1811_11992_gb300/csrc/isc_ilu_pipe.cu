@@ -164,9 +164,12 @@ __device__ __forceinline__ T quad_sum(T v) {
 }
 
 // Remote look-ahead: the neighbour-pencil values a cell needs are requested LA
-// cells before they are used (the neighbour pencil normally runs ahead), so a
-// cell normally costs no round trip; entries still NaN on use are re-polled.
-constexpr int LA = 4;
+// cells before they are used; entries still NaN on use are re-polled. A request
+// only finds the value if the consumer trails its producer by about LA cells,
+// so every pencil-to-pencil hand-off adds that lag to the wavefront: one cell
+// ahead is the best measured (sweep pair 347 / 387 / 388 us for LA = 1 / 2 / 4
+// in FP64 at 60x60x20, 241 / 283 / 279 us in FP32).
+constexpr int LA = 1;
 
 template <typename TM>
 __device__ __forceinline__ typename V2<TM>::t ld_remote(const TM* p) {
