@@ -608,10 +608,14 @@ void launch_ilu_factor_pipe(Handle& h, cudaStream_t s) {
                                                            h.dstatus);
 }
 
-constexpr int SWEEP_R = 8;  // cells staged ahead in each warp's shared-memory ring
+// cells staged in each warp's shared-memory ring: 4 keeps an FP64 block of 8 warps at
+// 68 KB, so three blocks (24 warps, also the register limit) fit on an SM; with 8 the
+// 135 KB block allowed one per SM and 3,000 pencils (100x100x30) ran in two rounds
+// (sweep pair 1.13 against 0.89 ms; no difference at 60x60x20)
+constexpr int SWEEP_R = 4;
 
 int sweep_blocks(int npen) {
-  const int warps = npen < 152 * 16 ? npen : 152 * 16;
+  const int warps = npen < 152 * 24 ? npen : 152 * 24;  // 24 resident warps per SM
   return (warps + AWARPS - 1) / AWARPS;
 }
 
