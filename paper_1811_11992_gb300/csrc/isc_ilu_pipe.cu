@@ -593,7 +593,9 @@ __global__ void __launch_bounds__(FWARPS * 32) k_ilu_factor_pipe(int nx, int ny,
 // from the FP32 copy of the blocks (J32, written first) into dinv32.
 void launch_ilu_factor_pipe(Handle& h, cudaStream_t s) {
   const int npen = h.ny * h.nz;
-  const int warps = npen < 152 * 8 ? npen : 152 * 8;
+  // up to 32 warps per SM (38 registers, 12 KB of shared memory per 4-warp block):
+  // more pencils in flight on the larger grids
+  const int warps = npen < 152 * 32 ? npen : 152 * 32;
   const int blocks = (warps + FWARPS - 1) / FWARPS;
   cudaMemsetAsync(h.pipe, 0, 2 * sizeof(int), s);
   if (h.opt.precision != ISC_PRECISION_FP64) {
