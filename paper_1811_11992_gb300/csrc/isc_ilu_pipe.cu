@@ -356,7 +356,7 @@ __global__ void __launch_bounds__(AWARPS * 32) k_ilu_bwd_async(int nx, int ny, i
     for (int q = 0; q < R - 1; ++q) {
       if (q < nx) {
         const int x = nx - 1 - q;
-        stage_cell<TM>(ring + q, base_jk + x, first_of(x), mask_of(x), PEN, A, Dinv, (const double*)nullptr, lane);
+        stage_cell<TM, TM>(ring + q, base_jk + x, first_of(x), mask_of(x), PEN, A, Dinv, yin, lane);
       }
       cp_async_commit();
     }
@@ -379,8 +379,8 @@ __global__ void __launch_bounds__(AWARPS * 32) k_ilu_bwd_async(int nx, int ny, i
         const int i = base_jk + x;
         const int ss = step + R - 1;
         if (ss < nx)
-          stage_cell<TM>(ring + ss % R, base_jk + (nx - 1 - ss), first_of(nx - 1 - ss), mask_of(nx - 1 - ss), PEN, A,
-                         Dinv, (const double*)nullptr, lane);
+          stage_cell<TM, TM>(ring + ss % R, base_jk + (nx - 1 - ss), first_of(nx - 1 - ss), mask_of(nx - 1 - ss), PEN,
+                             A, Dinv, yin, lane);
         cp_async_commit();
         cp_async_wait<R - 1>();
         __syncwarp();
@@ -392,7 +392,7 @@ __global__ void __launch_bounds__(AWARPS * 32) k_ilu_bwd_async(int nx, int ny, i
         if (m & 2) ay = sl_pair<TM>(sl, b++, lane);
         if (m & 4) az = sl_pair<TM>(sl, b, lane);
         const T2 d = sl_pair<TM>(sl, 3, lane);
-        const TM yi = __ldg(yin + (size_t)i * 8 + r);
+        const TM yi = reinterpret_cast<const TM*>(sl->rhs)[r];  // the forward result, staged with the blocks
         TM acc = fma(ax.x, zp0, ax.y * zp1);
         if (hz) {
           if (!settle<TM>(zs + (size_t)(i + nxy) * 8 + c, rz[q], abortf, dstatus)) return;
