@@ -643,29 +643,58 @@ __global__ void k_gmres_givens(int j, int m, double bnorm, const double* __restr
                                const double* __restrict__ h1, const double* __restrict__ nrm2,
                                double* __restrict__ H, double* __restrict__ cs, double* __restrict__ sn,
                                double* __restrict__ g, double* __restrict__ st) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double col[GM_MAX + 1];
-  for (int i = 0; i <= j; ++i) col[i] = h0[i] + h1[i];
-  const double hn = sqrt(fmax(*nrm2, 0.0));
-  col[j + 1] = hn;
-  for (int i = 0; i < j; ++i) {
-    const double a = col[i], c = col[i + 1];
-    col[i] = cs[i] * a + sn[i] * c;
-    col[i + 1] = -sn[i] * a + cs[i] * c;
+  // one warp: the column and the previous rotations are loaded in parallel (two
+  // entries per lane, j <= GM_MAX - 1 < 64), then lane 0 runs the dependent chain of
+  // rotations with the operands fetched by shuffles instead of global loads
+  const int lane = threadIdx.x & 31;
+  if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+  double c0 = 0.0, c1 = 0.0, s0 = 0.0, s1 = 0.0, v0 = 0.0, v1 = 0.0;
+  if (lane <= j) v0 = h0[lane] + h1[lane];
+  if (lane + 32 <= j) v1 = h0[lane + 32] + h1[lane + 32];
+  if (lane < j) {
+    c0 = cs[lane];
+    s0 = sn[lane];
   }
-  const double a = col[j], c = col[j + 1];
+  if (lane + 32 < j) {
+    c1 = cs[lane + 32];
+    s1 = sn[lane + 32];
+  }
+  const double hn = sqrt(fmax(*nrm2, 0.0));
+  // rotated column: entry i is final once rotation i has been applied
+  double out0 = 0.0, out1 = 0.0;
+  double cur = __shfl_sync(FULL, v0, 0);  // running entry i (after rotations < i)
+  for (int i = 0; i < j; ++i) {
+    const double ci = __shfl_sync(FULL, i < 32 ? c0 : c1, i & 31);
+    const double si = __shfl_sync(FULL, i < 32 ? s0 : s1, i & 31);
+    const double nxt = __shfl_sync(FULL, (i + 1) < 32 ? v0 : v1, (i + 1) & 31);
+    const double fin = ci * cur + si * nxt;  // final entry i
+    cur = -si * cur + ci * nxt;              // entry i + 1 after rotation i
+    if (lane == (i & 31)) {
+      if (i < 32) out0 = fin;
+      else out1 = fin;
+    }
+  }
+  // the new rotation on (entry j, hn)
+  const double a = cur, c = hn;
   const double den = hypot(a, c);
   const double cj = den > 0.0 ? a / den : 1.0, sj = den > 0.0 ? c / den : 0.0;
-  cs[j] = cj;
-  sn[j] = sj;
-  col[j] = den > 0.0 ? den : a;
-  for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = col[i];
-  const double gj = g[j];
-  g[j + 1] = -sj * gj;
-  g[j] = cj * gj;
-  st[0] = fabs(g[j + 1]) / bnorm;
-  st[1] = (hn > 0.0 && isfinite(hn)) ? 1.0 / hn : 0.0;
-  st[2] = hn;
+  const double dj = den > 0.0 ? den : a;
+  if (lane == (j & 31)) {
+    if (j < 32) out0 = dj;
+    else out1 = dj;
+  }
+  if (lane <= j) H[(size_t)lane * m + j] = out0;
+  if (lane + 32 <= j) H[(size_t)(lane + 32) * m + j] = out1;
+  if (lane == 0) {
+    cs[j] = cj;
+    sn[j] = sj;
+    const double gj = g[j];
+    g[j + 1] = -sj * gj;
+    g[j] = cj * gj;
+    st[0] = fabs(g[j + 1]) / bnorm;
+    st[1] = (hn > 0.0 && isfinite(hn)) ? 1.0 / hn : 0.0;
+    st[2] = hn;
+  }
 }
 
 __global__ void k_gmres_start(int m, double beta, double* __restrict__ g) {
@@ -673,16 +702,34 @@ __global__ void k_gmres_start(int m, double beta, double* __restrict__ g) {
   if (i <= m) g[i] = (i == 0) ? beta : 0.0;
 }
 
-// y = R^-1 g over the first jdone columns (back substitution), into y
+// y = R^-1 g over the first jdone columns (back substitution), into y: one warp
+// copies R and g into shared memory in parallel, then solves bottom-up with the
+// row products split over the lanes
 __global__ void k_gmres_backsub(int jdone, int m, const double* __restrict__ H, const double* __restrict__ g,
                                 double* __restrict__ y) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  for (int i = jdone - 1; i >= 0; --i) {
-    double acc = g[i];
-    for (int k = i + 1; k < jdone; ++k) acc -= H[(size_t)i * m + k] * y[k];
-    const double d = H[(size_t)i * m + i];
-    y[i] = d != 0.0 ? acc / d : 0.0;  // a zero pivot only follows an exact (lucky) breakdown
+  __shared__ double sR[GM_MAX * GM_MAX];
+  __shared__ double sy[GM_MAX];
+  const int lane = threadIdx.x & 31;
+  if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+  for (int e = lane; e < jdone * jdone; e += 32) {
+    const int i = e / jdone, k = e % jdone;
+    sR[i * GM_MAX + k] = H[(size_t)i * m + k];
   }
+  for (int i = lane; i < jdone; i += 32) sy[i] = g[i];
+  __syncwarp();
+  for (int i = jdone - 1; i >= 0; --i) {
+    double part = 0.0;
+    for (int k = i + 1 + lane; k < jdone; k += 32) part += sR[i * GM_MAX + k] * sy[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(FULL, part, o);
+    if (lane == 0) {
+      const double d = sR[i * GM_MAX + i];
+      const double acc = sy[i] - part;
+      sy[i] = d != 0.0 ? acc / d : 0.0;  // a zero pivot only follows an exact (lucky) breakdown
+    }
+    __syncwarp();
+  }
+  for (int i = lane; i < jdone; i += 32) y[i] = sy[i];
 }
 
 // y = (*coef) x with the coefficient read on the device
