@@ -75,9 +75,10 @@ enum isc_prec { ISC_PREC_NONE = 0, ISC_PREC_BJACOBI = 1, ISC_PREC_BILU0 = 2, ISC
  *   update stay FP64).
  * ISC_PRECISION_MIXED_FGMRES: the FP64 GMRES is flexible and its preconditioner
  *   is options.inner_its iterations of an FP32 GMRES on the FP32 copy of the
- *   decoupled matrix (FP32 SpMV, FP32 Gram-Schmidt, FP32 block ILU(0)); the
- *   outer residual, SpMV, orthogonalisation and update stay FP64. Requires
- *   krylov = GMRES and prec = BILU0. */
+ *   decoupled matrix (FP32 SpMV, FP32 Gram-Schmidt, FP32 block ILU(0), or
+ *   CPR-PF with the FP32 pressure multigrid); the outer residual, SpMV,
+ *   orthogonalisation and update stay FP64. Requires krylov = GMRES and
+ *   prec = BILU0 or CPR. */
 enum isc_precision { ISC_PRECISION_FP64 = 0, ISC_PRECISION_MIXED = 1, ISC_PRECISION_MIXED_FGMRES = 2 };
 enum isc_rxn_kind {
   ISC_RXN_OIL_OXIDATION = 0,   /* r = A e^{-Ea/RT} (y_O2 p)(phi_f S_o rho_o x_i)           */

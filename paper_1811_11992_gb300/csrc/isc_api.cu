@@ -159,7 +159,7 @@ void prec(isc_handle* h, const double* r, double* z) {
 int inner_solve(isc_handle* h, const double* r, double* z);
 
 void prec_cells(isc_handle* h, const double* r, double* z) {
-  if (h->opt.precision == ISC_PRECISION_MIXED_FGMRES && h->opt.prec == ISC_PREC_BILU0) {
+  if (h->opt.precision == ISC_PRECISION_MIXED_FGMRES) {
     inner_solve(h, r, z);
     return;
   }
@@ -182,7 +182,8 @@ void prec_cells(isc_handle* h, const double* r, double* z) {
 }
 
 // z ~ A^-1 r by inner_its iterations of right-preconditioned GMRES in FP32 on the
-// FP32 copy of the (decoupled) matrix with the FP32 block ILU(0),
+// FP32 copy of the (decoupled) matrix with the FP32 block ILU(0) (or CPR-PF with the
+// FP32 pressure multigrid and FP32 ILU(0)),
 // classical Gram-Schmidt applied twice, x0 = 0; the rotations and the final
 // back-substitution run on the device, so the whole solve is a fixed launch
 // sequence with no host round trip. A fixed iteration count keeps it cheap to
@@ -205,7 +206,20 @@ int inner_solve(isc_handle* h, const double* r, double* z) {
   for (int j = 0; j < m; ++j) {
     float* Vj = V + (size_t)j * vs;
     float* Zj = Z + (size_t)j * vs;
-    {
+    if (h->opt.prec == ISC_PREC_CPR) {
+      // CPR-PF on FP32 vectors: FP32 pressure multigrid, r1 = r - A E p (in w32, free until
+      // the SpMV below), FP32 ILU(0) on r1, z += E p
+      {
+        Region rg(h, ISC_K_CPR, cpr_pressure_launches(*h));
+        launch_cpr_pressure32(*h, Vj, h->w32, s);
+      }
+      {
+        Region rg(h, ISC_K_PREC_APPLY, 2);
+        launch_ilu_apply_f32(*h, h->w32, Zj, s);
+      }
+      Region rg(h, ISC_K_CPR, 1);
+      launch_cpr_finish32(*h, Zj, s);
+    } else {
       Region rg(h, ISC_K_PREC_APPLY, 2);
       launch_ilu_apply_f32(*h, Vj, Zj, s);
     }
@@ -568,8 +582,8 @@ int validate_options(isc_handle* h, const isc_options& o) {
       o.precision != ISC_PRECISION_MIXED_FGMRES)
     return set_err(h, ISC_ERR_INVALID_ARG, "unknown precision");
   if (o.precision == ISC_PRECISION_MIXED_FGMRES) {
-    if (o.krylov != ISC_KRYLOV_GMRES || o.prec != ISC_PREC_BILU0)
-      return set_err(h, ISC_ERR_INVALID_ARG, "mixed_fgmres needs krylov = GMRES and prec = BILU0");
+    if (o.krylov != ISC_KRYLOV_GMRES || (o.prec != ISC_PREC_BILU0 && o.prec != ISC_PREC_CPR))
+      return set_err(h, ISC_ERR_INVALID_ARG, "mixed_fgmres needs krylov = GMRES and prec = BILU0 or CPR");
     if (o.inner_its < 1 || o.inner_its > 32) return set_err(h, ISC_ERR_INVALID_ARG, "inner_its must be 1..32");
   }
   if (!(o.tol_lin > 0.0) || o.maxit_lin < 1 || !(o.tol_newton >= 0.0) || o.maxit_newton < 1)

@@ -401,29 +401,31 @@ __global__ void __launch_bounds__(512) k_mg_coarse(const MGLevel<T>* __restrict_
   }
 }
 
-template <typename T>
-__global__ void k_cpr_gather(int n, const double* __restrict__ r, T* __restrict__ b) {
+// RV: the type of the vectors the preconditioner is applied to (FP64 inside the
+// FP64 GMRES, FP32 inside the inner solve of ISC_PRECISION_MIXED_FGMRES)
+template <typename T, typename RV>
+__global__ void k_cpr_gather(int n, const RV* __restrict__ r, T* __restrict__ b) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = (T)r[(size_t)i * 8];
 }
 
 // r1 = r - A E p: thread (i, row) sums the unknown-0 column entries of row i's blocks
-template <typename T>
+template <typename T, typename RV>
 __global__ void k_cpr_residual(int n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                               const double* __restrict__ col0, const double* __restrict__ r, const T* __restrict__ p,
-                               double* __restrict__ r1) {
+                               const double* __restrict__ col0, const RV* __restrict__ r, const T* __restrict__ p,
+                               RV* __restrict__ r1) {
   const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (size_t)n * 8) return;
   const int i = (int)(e >> 3), row = (int)(e & 7);
-  double s = r[e];
+  double s = (double)r[e];
   for (int b = rowptr[i]; b < rowptr[i + 1]; ++b) s -= col0[(size_t)b * 8 + row] * (double)p[col[b]];
-  r1[e] = s;
+  r1[e] = (RV)s;
 }
 
-template <typename T>
-__global__ void k_cpr_add(int n, const T* __restrict__ p, double* __restrict__ z) {
+template <typename T, typename RV>
+__global__ void k_cpr_add(int n, const T* __restrict__ p, RV* __restrict__ z) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) z[(size_t)i * 8] += (double)p[i];
+  if (i < n) z[(size_t)i * 8] += (RV)p[i];
 }
 
 inline int nblk(long long n, int tb) { return (int)((n + tb - 1) / tb); }
@@ -492,13 +494,13 @@ void setup_t(Handle& h, cudaStream_t s) {
   for (int l = 0; l < W.nlev; ++l) k_mg_factor<T><<<nblk(lv[l].nx * lv[l].ny, tb), tb, 0, s>>>(d, l);
 }
 
-template <typename T>
-void pressure_t(Handle& h, const double* r, cudaStream_t s) {
+template <typename T, typename RV>
+void pressure_t(Handle& h, const RV* r, RV* r1, cudaStream_t s) {
   CprWork& W = h.cpr;
   const auto& lv = table<T>(W);
   const MGLevel<T>* d = static_cast<const MGLevel<T>*>(W.d_levels);
   const int tb = 128;
-  k_cpr_gather<T><<<nblk(h.n, tb), tb, 0, s>>>(h.n, r, lv[0].b);
+  k_cpr_gather<T, RV><<<nblk(h.n, tb), tb, 0, s>>>(h.n, r, lv[0].b);
   // threads of a z-line pass: a warp per column (nz <= ZWARP_MAX) or a thread per column
   const bool warp = h.nz <= ZWARP_MAX;
   auto zline = [&](int l, int colour, int zero) {
@@ -522,14 +524,14 @@ void pressure_t(Handle& h, const double* r, cudaStream_t s) {
     zline(l, 0, 0);
     zline(l, 1, 0);
   }
-  k_cpr_residual<T><<<nblk((long long)h.n * 8, 256), 256, 0, s>>>(h.n, h.rowptr, h.col, W.col0, r, lv[0].x, W.r1);
+  k_cpr_residual<T, RV><<<nblk((long long)h.n * 8, 256), 256, 0, s>>>(h.n, h.rowptr, h.col, W.col0, r, lv[0].x, r1);
 }
 
 }  // namespace
 
 int cpr_setup_levels(Handle& h) {
   CprWork& W = h.cpr;
-  const bool fp32 = h.opt.precision == ISC_PRECISION_MIXED;
+  const bool fp32 = h.opt.precision != ISC_PRECISION_FP64;
   if (W.nlev > 0 && W.fp32 == fp32) return ISC_OK;
   cpr_free(h);
   W.fp32 = fp32;
@@ -548,18 +550,27 @@ void launch_cpr_setup(Handle& h, cudaStream_t s) {
 // first stage and the second stage's right-hand side: p (level 0's x) and r1 = r - A E p
 void launch_cpr_pressure(Handle& h, const double* r, cudaStream_t s) {
   if (h.cpr.fp32)
-    pressure_t<float>(h, r, s);
+    pressure_t<float, double>(h, r, h.cpr.r1, s);
   else
-    pressure_t<double>(h, r, s);
+    pressure_t<double, double>(h, r, h.cpr.r1, s);
 }
 
 // z += E p after the second stage wrote z = ILU^-1 r1
 void launch_cpr_finish(Handle& h, double* z, cudaStream_t s) {
   const int tb = 128;
   if (h.cpr.fp32)
-    k_cpr_add<float><<<nblk(h.n, tb), tb, 0, s>>>(h.n, h.cpr.h32[0].x, z);
+    k_cpr_add<float, double><<<nblk(h.n, tb), tb, 0, s>>>(h.n, h.cpr.h32[0].x, z);
   else
-    k_cpr_add<double><<<nblk(h.n, tb), tb, 0, s>>>(h.n, h.cpr.h64[0].x, z);
+    k_cpr_add<double, double><<<nblk(h.n, tb), tb, 0, s>>>(h.n, h.cpr.h64[0].x, z);
+}
+
+// the same on FP32 vectors (inner solve of ISC_PRECISION_MIXED_FGMRES; FP32 multigrid)
+void launch_cpr_pressure32(Handle& h, const float* r, float* r1, cudaStream_t s) {
+  pressure_t<float, float>(h, r, r1, s);
+}
+void launch_cpr_finish32(Handle& h, float* z, cudaStream_t s) {
+  const int tb = 128;
+  k_cpr_add<float, float><<<nblk(h.n, tb), tb, 0, s>>>(h.n, h.cpr.h32[0].x, z);
 }
 
 int cpr_pressure_launches(const Handle& h) { return 1 + 6 * h.cpr.ngrid + 1 + 1; }

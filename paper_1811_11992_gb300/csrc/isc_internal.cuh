@@ -274,6 +274,9 @@ int cpr_setup_levels(Handle& h);
 void launch_cpr_setup(Handle& h, cudaStream_t s);
 void launch_cpr_pressure(Handle& h, const double* r, cudaStream_t s);
 void launch_cpr_finish(Handle& h, double* z, cudaStream_t s);
+// FP32 vectors (inner solve of ISC_PRECISION_MIXED_FGMRES): p and r1 = r - A E p into r1; z += E p
+void launch_cpr_pressure32(Handle& h, const float* r, float* r1, cudaStream_t s);
+void launch_cpr_finish32(Handle& h, float* z, cudaStream_t s);
 int cpr_pressure_launches(const Handle& h);
 void cpr_free(Handle& h);
 // discrete adjoint (isc_adjoint.cu)

@@ -120,3 +120,44 @@ def test_time_steps_with_cpr_match_ilu(Simulator):
     diff = np.max(np.abs(u_c - u_i) / scale)
     assert 5 * k_c <= 3 * k_i, (k_c, k_i, diff)
     assert diff <= 1e-6, (k_c, k_i, diff)
+
+
+@pytest.mark.parametrize("m", [1, 5])
+def test_fgmres_inner_solve_with_cpr_is_the_oracle_gmres_iterate(Simulator, m):
+    """mixed_fgmres with CPR-PF: the inner solve is m GMRES iterations in FP32 with
+    the FP32 CPR-PF (FP32 pressure multigrid, FP32 ILU(0)); the oracle's FP64 GMRES
+    stopped after m iterations with the oracle's CPR-PF, both on the FP32 copy of
+    the GPU's decoupled matrix, gives the same iterate to FP32 accuracy."""
+    dims = (13, 7, 3)
+    case = inp.field_case(*dims, 0, 1, "cpr", 30 * inp.DAY, 40)
+    g = _first_matrix(Simulator, case, precision="mixed_fgmres", inner_its=m)
+    rp, col, Jd = g.jacobian()
+    rp, col = rp.astype(np.int64), col.astype(np.int64)
+    A32 = Jd.astype(np.float32).astype(np.float64)
+    M = cpr.CPRPreconditioner(rp, col, A32, *dims)
+    r = np.random.default_rng(17).standard_normal((8, case.n))
+    z = g.precond_apply(r)
+    x, its, _ = linalg.gmres(lambda v: linalg.bsr_matvec(rp, col, A32, v), r.T.copy(), M, restart=m, rtol=1e-300,
+                             maxit=m)
+    assert its == m
+    err = np.max(np.abs(z - x.T)) / np.abs(x).max()
+    assert err < 1e-2, err
+    assert err > 1e-9, err
+    g.close()
+
+
+def test_cpr_mixed_fgmres_newton_step_matches_fp64(Simulator):
+    """60x60x20, first step of the ramp: CPR-PF with the FP32 inner GMRES reaches the
+    FP64 tolerance and the FP64 CPR-PF state within the Newton tolerance."""
+    case = inp.config(2)
+    dt = inp.adjoint_steps(case)[0]
+    out = {}
+    for precision in ("fp64", "mixed_fgmres"):
+        g = Simulator(case, prec="cpr", precision=precision, tol_newton=1e-8)
+        g.init_equilibrium()
+        info = g.timestep(dt)
+        out[precision] = (g.get_state()[0], info)
+        g.close()
+    scale = np.array([5e6, 1, 1, 1, 1, 300, 1, 1])[:, None]
+    diff = np.max(np.abs(out["mixed_fgmres"][0] - out["fp64"][0]) / scale)
+    assert diff <= 1e-6, diff

@@ -150,7 +150,7 @@ def test_mixed_fgmres_newton_step_on_field_block(Simulator):
     assert np.max(np.abs(res["mixed_fgmres"][0] - res["fp64"][0]) / scale) < 1e-3
 
 
-@pytest.mark.parametrize("opt", [dict(prec="cpr"), dict(krylov="bicgstab"), dict(inner_its=0), dict(inner_its=33)])
+@pytest.mark.parametrize("opt", [dict(prec="bjacobi"), dict(krylov="bicgstab"), dict(inner_its=0), dict(inner_its=33)])
 def test_mixed_fgmres_option_checks(Simulator, opt):
     from paper_1811_11992_gb300.isc import IscError
     case = inp.small_box(3, 3, 2)
