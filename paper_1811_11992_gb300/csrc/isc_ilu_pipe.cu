@@ -611,13 +611,17 @@ void launch_ilu_factor_pipe(Handle& h, cudaStream_t s) {
 }
 
 // cells staged in each warp's shared-memory ring: 4 keeps an FP64 block of 8 warps at
-// 68 KB, so three blocks (24 warps, also the register limit) fit on an SM; with 8 the
+// 68 KB, so three blocks (24 warps) fit on an SM; with 8 the
 // 135 KB block allowed one per SM and 3,000 pencils (100x100x30) ran in two rounds
 // (sweep pair 1.13 against 0.89 ms; no difference at 60x60x20)
 constexpr int SWEEP_R = 4;
 
+// resident warps per SM: 24 for the FP64 sweeps (registers and the 68 KB rings), 32 for
+// the FP32 ones (35 KB rings, fewer registers)
+template <typename TM>
 int sweep_blocks(int npen) {
-  const int warps = npen < 152 * 24 ? npen : 152 * 24;  // 24 resident warps per SM
+  constexpr int per_sm = sizeof(TM) == 8 ? 24 : 32;
+  const int warps = npen < 152 * per_sm ? npen : 152 * per_sm;
   return (warps + AWARPS - 1) / AWARPS;
 }
 
@@ -639,7 +643,7 @@ template <typename TM>
 void sweep_pair(int nx, int ny, int nz, const int32_t* rowptr, const TM* A, const TM* Dinv, const double* r, TM* y,
                 TM* zs, double* z64, int* pipe, int* dstatus, cudaStream_t s) {
   const size_t n8 = (size_t)nx * ny * nz * 8;
-  const int blocks = sweep_blocks(ny * nz);
+  const int blocks = sweep_blocks<TM>(ny * nz);
   const size_t smem = sweep_smem<TM>();
   sweep_attributes<TM>();
   cudaMemsetAsync(pipe, 0, 2 * sizeof(int), s);
@@ -654,7 +658,7 @@ void sweep_pair(int nx, int ny, int nz, const int32_t* rowptr, const TM* A, cons
 // FP32 in, FP32 out (inner solve of ISC_PRECISION_MIXED_FGMRES): y in vec32, z written as the hand-off vector
 void launch_ilu_apply_f32(Handle& h, const float* r, float* z, cudaStream_t s) {
   const size_t n8 = (size_t)h.n * 8;
-  const int blocks = sweep_blocks(h.ny * h.nz);
+  const int blocks = sweep_blocks<float>(h.ny * h.nz);
   const size_t smem = sweep_smem<float>();
   sweep_attributes<float>();
   cudaMemsetAsync(h.pipe, 0, 2 * sizeof(int), s);
