@@ -373,7 +373,7 @@ def measured_peaks():
 
 FP64_PEAK_GFLOPS = 1200.0   # measured DFMA throughput on this GB300
 # dram__bytes_read.sum + dram__bytes_write.sum per call (forward + backward FP64 sweep)
-MEASURED_TRAFFIC = {("prec_apply", 60, 60, 20): (313.55e6, "profiles/k_ilu_sweeps_field_60x60x20.md")}
+MEASURED_TRAFFIC = {("prec_apply", 60, 60, 20): (313.40e6, "profiles/k_ilu_sweeps_field_60x60x20.md")}
 
 
 SOLVE_CLASSES = ("spmv", "spmv32", "prec_apply", "blas1", "ilu_factor")

@@ -237,7 +237,9 @@ __device__ __forceinline__ typename V2<TM>::t sl_pair(const Slot<TM>* sl, int b,
   return *reinterpret_cast<const typename V2<TM>::t*>(&sl->blk[b][2 * lane]);
 }
 
-constexpr int AWARPS = 8;
+// warps per block of the sweeps: 4 (six FP64 blocks per SM) ran the 100x100x30 sweep pair in
+// 0.74-0.76 ms against 0.82 ms with 8 (three blocks per SM); equal at 60x60x20
+constexpr int AWARPS = 4;
 
 template <typename TM, int R, typename RT = double>
 __global__ void __launch_bounds__(AWARPS * 32) k_ilu_fwd_async(int nx, int ny, int nz, const int32_t* __restrict__ rowptr,
@@ -610,10 +612,9 @@ void launch_ilu_factor_pipe(Handle& h, cudaStream_t s) {
                                                            h.dstatus);
 }
 
-// cells staged in each warp's shared-memory ring: 4 keeps an FP64 block of 8 warps at
-// 68 KB, so three blocks (24 warps) fit on an SM; with 8 the
-// 135 KB block allowed one per SM and 3,000 pencils (100x100x30) ran in two rounds
-// (sweep pair 1.13 against 0.89 ms; no difference at 60x60x20)
+// cells staged in each warp's shared-memory ring: 4 keeps an FP64 warp at 8.4 KB, so 24
+// warps fit on an SM; with 8 an 8-warp block took 135 KB, one per SM, and 3,000 pencils
+// (100x100x30) ran in two rounds (sweep pair 1.13 against 0.89 ms; equal at 60x60x20)
 constexpr int SWEEP_R = 4;
 
 // resident warps per SM: 24 for the FP64 sweeps (registers and the 68 KB rings), 32 for
