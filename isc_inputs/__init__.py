@@ -3,7 +3,7 @@
 This module is shared by the oracle, the tests, the CUDA binding and the
 benchmark. It holds DATA only: the paper's fluid and reaction tables
 (Tab:input3 and Tab:input6 of the combustion-tube model, the CO2 column from
-Tab:in2) converted to SI units, the constants this build chooses where the
+Tab:in2) converted to SI units, the constants chosen here where the
 paper gives none, and seeded generators for grids, permeability fields and
 wells. It evaluates none of the method's correlations or equations.
 
