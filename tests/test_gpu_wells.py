@@ -132,3 +132,24 @@ def test_time_step_matches_oracle(Simulator, control):
         Q = model.coupled_phase_rates(case, bp, model.coupled_wells(case)[0], bhp[0])
         assert -sum(np.sum(q) for q in Q) == pytest.approx(CONTROLS["total"][1], rel=1e-8)
     g.close()
+
+
+@pytest.mark.parametrize("prec,precision", [("cpr", "fp64"), ("cpr", "mixed"), ("bilu0", "mixed_fgmres"),
+                                            ("cpr", "mixed_fgmres")])
+def test_coupled_well_time_step_under_other_solvers(Simulator, prec, precision):
+    """The bordered system with CPR-PF and the mixed-precision solves: the well rows
+    follow the cells' preconditioner (block lower-triangular), and the time step
+    reaches the FP64 ILU(0) state and bottom-hole pressure within the Newton
+    tolerance."""
+    case = _case("total")
+    res = {}
+    for key, p, q in (("ref", "bilu0", "fp64"), ("alt", prec, precision)):
+        g = Simulator(case, prec=p, precision=q, tol_newton=1e-10, tol_lin=1e-10, maxit_newton=40)
+        g.init_equilibrium()
+        g.timestep(10.0)
+        res[key] = (g.get_state()[0], g.well_bhp())
+        g.close()
+    (u_r, b_r), (u_a, b_a) = res["ref"], res["alt"]
+    assert abs(b_a[0] - b_r[0]) <= 1e-7 * b_r[0]
+    scale = np.array([5e6, 1, 1, 1, 1, 300, 1, 1])[:, None]
+    assert np.max(np.abs(u_a - u_r) / scale) <= 1e-7
