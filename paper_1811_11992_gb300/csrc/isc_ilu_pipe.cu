@@ -301,11 +301,17 @@ __global__ void __launch_bounds__(AWARPS * 32) k_ilu_fwd_async(int nx, int ny, i
         const TM ri = (TM)reinterpret_cast<const RT*>(sl->rhs)[r];
         TM acc = fma(ax.x, yp0, ax.y * yp1);
         if (hz) {
-          if (!settle<TM>(y + (size_t)(i - nxy) * 8 + c, rz[q], abortf, dstatus)) return;
+          if (!settle<TM>(y + (size_t)(i - nxy) * 8 + c, rz[q], abortf, dstatus)) {
+            cp_async_wait<0>();  // no copy of this warp is left in flight when it leaves
+            return;
+          }
           acc = fma(az.x, rz[q].x, fma(az.y, rz[q].y, acc));
         }
         if (hy) {
-          if (!settle<TM>(y + (size_t)(i - nx) * 8 + c, ry[q], abortf, dstatus)) return;
+          if (!settle<TM>(y + (size_t)(i - nx) * 8 + c, ry[q], abortf, dstatus)) {
+            cp_async_wait<0>();  // no copy of this warp is left in flight when it leaves
+            return;
+          }
           acc = fma(ay.x, ry[q].x, fma(ay.y, ry[q].y, acc));
         }
         const TM t = ri - quad_sum(acc);
@@ -397,11 +403,17 @@ __global__ void __launch_bounds__(AWARPS * 32) k_ilu_bwd_async(int nx, int ny, i
         const TM yi = reinterpret_cast<const TM*>(sl->rhs)[r];  // the forward result, staged with the blocks
         TM acc = fma(ax.x, zp0, ax.y * zp1);
         if (hz) {
-          if (!settle<TM>(zs + (size_t)(i + nxy) * 8 + c, rz[q], abortf, dstatus)) return;
+          if (!settle<TM>(zs + (size_t)(i + nxy) * 8 + c, rz[q], abortf, dstatus)) {
+            cp_async_wait<0>();  // no copy of this warp is left in flight when it leaves
+            return;
+          }
           acc = fma(az.x, rz[q].x, fma(az.y, rz[q].y, acc));
         }
         if (hy) {
-          if (!settle<TM>(zs + (size_t)(i + nx) * 8 + c, ry[q], abortf, dstatus)) return;
+          if (!settle<TM>(zs + (size_t)(i + nx) * 8 + c, ry[q], abortf, dstatus)) {
+            cp_async_wait<0>();  // no copy of this warp is left in flight when it leaves
+            return;
+          }
           acc = fma(ay.x, ry[q].x, fma(ay.y, ry[q].y, acc));
         }
         const TM sr = quad_sum(acc);
