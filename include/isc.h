@@ -372,6 +372,16 @@ int isc_bilu0_apply_noalloc(int32_t nx, int32_t ny, int32_t nz, const int32_t* d
  * on the default stream. n < 0 or NULL pointers: ISC_ERR_INVALID_ARG. */
 int isc_check_reciprocal(int32_t n, const double* x, double* y, double* z);
 
+/* Failure-detection self-test (no GPU fault): runs the ILU(0) forward sweep on a
+ * 4x4x1 grid with its pencil counter started past pencil 0, so the neighbour
+ * value pencil 1 waits for never arrives and the wait ends by its iteration
+ * limit (a few seconds). Returns ISC_ERR_TIMEOUT when the kernel gave up and
+ * reported it in its status word (the expected outcome; the CUDA context stays
+ * usable), ISC_OK if the wait ended otherwise, ISC_ERR_NOMEM / ISC_ERR_CUDA on
+ * allocation or copy failures. Allocates and frees its own buffers; default
+ * stream; synchronous. */
+int isc_check_bounded_wait(void);
+
 /* ------------------------------------------------------------ sensitivities */
 
 /* Parameters theta of the sensitivity analysis. The paper computes no

@@ -26,6 +26,7 @@
 // at offset 2l, i.e. row r = l/4, columns c = 2(l%4), c+1; a row sum is a
 // reduction over the 4 lanes of a quad.
 #include <mutex>
+#include <vector>
 
 #include "isc_internal.cuh"
 
@@ -727,6 +728,61 @@ int noalloc_scratch(double** out) {
 }  // namespace
 
 }  // namespace isc
+
+// Failure-detection self-test: a forward sweep on a 4x4x1 grid whose pencil
+// counter starts at 1, so pencil 0 is never processed and pencil 1's wait on it
+// can only end by its iteration limit. Returns ISC_ERR_TIMEOUT when the bounded
+// wait gave up and reported it (the expected outcome), ISC_OK if it did not.
+extern "C" int isc_check_bounded_wait(void) {
+  using namespace isc;
+  const int nx = 4, ny = 4, nz = 1, n = nx * ny * nz;
+  std::vector<int32_t> rp(n + 1, 0);
+  int nnzb = 0;
+  for (int j = 0; j < ny; ++j)
+    for (int x = 0; x < nx; ++x) {
+      nnzb += 1 + (x > 0) + (x < nx - 1) + (j > 0) + (j < ny - 1);
+      rp[x + nx * j + 1] = nnzb;
+    }
+  std::vector<double> dinv((size_t)n * BB, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int a = 0; a < 8; ++a) dinv[(size_t)i * BB + a * 9] = 1.0;
+  int32_t* d_rp = nullptr;
+  double *d_A = nullptr, *d_D = nullptr, *d_r = nullptr, *d_y = nullptr;
+  int* d_ints = nullptr;
+  int st = ISC_OK;
+  if (cudaMalloc(&d_rp, sizeof(int32_t) * (n + 1)) != cudaSuccess ||
+      cudaMalloc(&d_A, sizeof(double) * (size_t)nnzb * BB) != cudaSuccess ||
+      cudaMalloc(&d_D, sizeof(double) * (size_t)n * BB) != cudaSuccess ||
+      cudaMalloc(&d_r, sizeof(double) * (size_t)n * 8) != cudaSuccess ||
+      cudaMalloc(&d_y, sizeof(double) * (size_t)n * 8) != cudaSuccess ||
+      cudaMalloc(&d_ints, sizeof(int) * 4) != cudaSuccess)
+    st = ISC_ERR_NOMEM;
+  if (st == ISC_OK) {
+    cudaMemcpy(d_rp, rp.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice);
+    cudaMemset(d_A, 0, sizeof(double) * (size_t)nnzb * BB);
+    cudaMemcpy(d_D, dinv.data(), sizeof(double) * (size_t)n * BB, cudaMemcpyHostToDevice);
+    cudaMemset(d_r, 0, sizeof(double) * (size_t)n * 8);
+    cudaMemset(d_y, 0xff, sizeof(double) * (size_t)n * 8);  // NaN sentinel: nothing arrives from pencil 0
+    const int h_ints[4] = {1, 0, 0, 0};                      // counter = 1 (pencil 0 skipped), abort, status
+    cudaMemcpy(d_ints, h_ints, sizeof(h_ints), cudaMemcpyHostToDevice);
+    const size_t smem = sweep_smem<double>();
+    sweep_attributes<double>();
+    k_ilu_fwd_async<double, SWEEP_R><<<1, AWARPS * 32, smem>>>(nx, ny, nz, d_rp, d_A, d_D, d_r, d_y, d_ints,
+                                                                d_ints + 2);
+    int h_status = 0;
+    if (cudaMemcpy(&h_status, d_ints + 2, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+      st = ISC_ERR_CUDA;
+    else
+      st = (h_status & DS_TIMEOUT) ? ISC_ERR_TIMEOUT : ISC_OK;
+  }
+  cudaFree(d_rp);
+  cudaFree(d_A);
+  cudaFree(d_D);
+  cudaFree(d_r);
+  cudaFree(d_y);
+  cudaFree(d_ints);
+  return st;
+}
 
 extern "C" int isc_bilu0_apply_noalloc(int32_t nx, int32_t ny, int32_t nz, const int32_t* d_rowptr,
                                        const double* d_A, const double* d_Dinv, const double* d_r, double* d_z,

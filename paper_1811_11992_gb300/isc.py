@@ -152,6 +152,7 @@ _SIGS = {
                                           C.c_void_p, C.c_void_p, C.c_void_p]),
     "isc_set_parameters": (C.c_int, [C.c_void_p, c_double_p, c_double_p, c_double_p]),
     "isc_check_reciprocal": (C.c_int, [C.c_int32, c_double_p, c_double_p, c_double_p]),
+    "isc_check_bounded_wait": (C.c_int, []),
     "isc_num_coupled_wells": (C.c_int32, [C.c_void_p]),
     "isc_set_well_bhp": (C.c_int, [C.c_void_p, c_double_p]),
     "isc_get_well_bhp": (C.c_int, [C.c_void_p, c_double_p]),
@@ -516,6 +517,11 @@ def check_reciprocal(x):
     if st:
         raise IscError(st, "isc_check_reciprocal failed")
     return y, z
+
+
+def check_bounded_wait():
+    """Status of the bounded-wait self-test (ISC_ERR_TIMEOUT expected)."""
+    return load_library().isc_check_bounded_wait()
 
 
 # the binding uses the C-ABI names
