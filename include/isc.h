@@ -40,6 +40,9 @@
 extern "C" {
 #endif
 
+/* The opaque simulator handle (owns every device allocation; see isc_create). */
+struct isc_handle;
+
 #define ISC_NC 6          /* fluid components */
 #define ISC_NU 8          /* unknowns (and equations) per cell */
 #define ISC_MAX_RXN 8

@@ -76,3 +76,29 @@ def test_ctypes_structures_match_the_header(tmp_path):
         assert got[(S.__name__, "size")] == ctypes.sizeof(S), S.__name__
         for f in S._fields_:
             assert got[(S.__name__, f[0])] == getattr(S, f[0]).offset, (S.__name__, f[0])
+
+
+@pytest.mark.parametrize("lang", ["c99", "c++17"])
+def test_header_compiles_cleanly(tmp_path, lang):
+    """include/isc.h is a self-contained C99 header (and valid C++): no warnings
+    with -Wall -Wextra -pedantic, and a C caller can pass the handle returned by
+    isc_create to every other call (one struct isc_handle type throughout)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc" if lang == "c99" else "g++")
+    if cc is None:
+        pytest.skip("no compiler")
+    src = tmp_path / ("use.c" if lang == "c99" else "use.cpp")
+    src.write_text('#include "isc.h"\n'
+                   "int use(const isc_grid* g, const isc_rock* r, const isc_fluid* f, const isc_reactions* x,\n"
+                   "        const isc_wells* w) {\n"
+                   "  isc_options o; struct isc_handle* h = 0; isc_newton_info info;\n"
+                   "  isc_default_options(&o);\n"
+                   "  if (isc_create(g, r, f, x, w, &o, &h) != ISC_OK) return 1;\n"
+                   "  int st = isc_newton_step(h, 1.0, &info);\n"
+                   "  isc_destroy(h);\n"
+                   "  return st;\n"
+                   "}\n")
+    std = "-std=c99" if lang == "c99" else "-std=c++17"
+    subprocess.run([cc, std, "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"), "-c",
+                    str(src), "-o", str(tmp_path / "use.o")], check=True)
