@@ -102,3 +102,41 @@ def test_header_compiles_cleanly(tmp_path, lang):
     std = "-std=c99" if lang == "c99" else "-std=c++17"
     subprocess.run([cc, std, "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"), "-c",
                     str(src), "-o", str(tmp_path / "use.o")], check=True)
+
+
+def _prototypes():
+    """name -> (return type text, [parameter texts]) for every prototype in the header."""
+    src = open(os.path.join(ROOT, "include", "isc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for m in re.finditer(r"([A-Za-z_][A-Za-z0-9_ \*]*?)\b(isc_[a-z0-9_]+)\s*\(([^;{)]*)\)\s*;", src):
+        params = [p.strip() for p in m.group(3).split(",") if p.strip() and p.strip() != "void"]
+        out[m.group(2)] = (m.group(1).strip(), params)
+    return out
+
+
+def test_binding_signatures_match_the_prototypes():
+    """The ctypes declarations of the binding have the header's parameter count,
+    pointer-ness of every parameter and return kind (void / int / pointer)."""
+    import ctypes as C
+    from paper_1811_11992_gb300 import isc
+    protos = _prototypes()
+    assert set(protos) == set(isc._SIGS)
+    for name, (res, args) in isc._SIGS.items():
+        ret, params = protos[name]
+        assert len(args) == len(params), (name, params)
+        for a, p in zip(args, params):
+            is_ptr = "*" in p or "[" in p  # an array parameter is a pointer
+            ct_ptr = a is C.c_void_p or a is C.c_char_p or (isinstance(a, type) and issubclass(a, C._Pointer))
+            assert is_ptr == ct_ptr, (name, p, a)
+            if not is_ptr:  # scalars: the same width and kind
+                base = p.replace("const", "").split()[0]
+                want = {"int32_t": C.c_int32, "int": C.c_int, "double": C.c_double, "int64_t": C.c_int64,
+                        "size_t": C.c_size_t}[base]
+                assert C.sizeof(a) == C.sizeof(want) and (a is C.c_double) == (want is C.c_double), (name, p, a)
+        if ret.endswith("void") and "*" not in ret:
+            assert res is None, name
+        elif "*" in ret:
+            assert res in (C.c_char_p, C.c_void_p), name
+        else:
+            assert res in (C.c_int, C.c_int32, C.c_int64), (name, ret)
