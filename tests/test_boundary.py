@@ -140,3 +140,31 @@ def test_binding_signatures_match_the_prototypes():
             assert res in (C.c_char_p, C.c_void_p), name
         else:
             assert res in (C.c_int, C.c_int32, C.c_int64), (name, ret)
+
+
+def _enum_values():
+    src = open(os.path.join(ROOT, "include", "isc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(ISC_[A-Z0-9_]+)\s*=\s*(-?\d+)", src)}
+
+
+def test_binding_constants_match_the_header_enums():
+    """The binding's and the input generator's constants equal the header's enum values."""
+    import isc_inputs as inp
+    from paper_1811_11992_gb300 import isc
+    e = _enum_values()
+    assert isc.KRYLOV == {"gmres": e["ISC_KRYLOV_GMRES"], "bicgstab": e["ISC_KRYLOV_BICGSTAB"]}
+    assert isc.PREC["none"] == e["ISC_PREC_NONE"] and isc.PREC["bjacobi"] == e["ISC_PREC_BJACOBI"]
+    assert isc.PREC["bilu0"] == e["ISC_PREC_BILU0"] and isc.PREC["cpr"] == e["ISC_PREC_CPR"]
+    assert isc.PRECISION == {"fp64": e["ISC_PRECISION_FP64"], "mixed": e["ISC_PRECISION_MIXED"],
+                             "mixed_fgmres": e["ISC_PRECISION_MIXED_FGMRES"]}
+    statuses = {v for k, v in e.items() if k == "ISC_OK" or k.startswith("ISC_ERR_")}
+    assert set(isc.STATUS) == statuses
+    assert len(isc.K_CLASSES) == e["ISC_K_COUNT"]
+    for i, name in enumerate(isc.K_CLASSES):
+        assert e["ISC_K_" + name.upper()] == i, name
+    assert (inp.WELL_RATE_INJECTOR, inp.WELL_BHP_PRODUCER, inp.WELL_COUPLED_PRODUCER) == (
+        e["ISC_WELL_RATE_INJECTOR"], e["ISC_WELL_BHP_PRODUCER"], e["ISC_WELL_COUPLED_PRODUCER"])
+    assert (inp.CTRL_BHP, inp.CTRL_WATER_RATE, inp.CTRL_OIL_RATE, inp.CTRL_LIQUID_RATE, inp.CTRL_GAS_RATE,
+            inp.CTRL_TOTAL_RATE) == tuple(e["ISC_CTRL_" + k] for k in ("BHP", "WATER_RATE", "OIL_RATE",
+                                                                       "LIQUID_RATE", "GAS_RATE", "TOTAL_RATE"))
