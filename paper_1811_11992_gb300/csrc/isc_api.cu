@@ -26,7 +26,7 @@ struct isc_handle : public Handle {
 namespace {
 
 // scalar slots in Handle::scal
-constexpr int S_NORM = 0;     // 3 norms (bit patterns of doubles, atomicMax)
+constexpr int S_NORM = 0;     // 3 norms (bit patterns of doubles, atomicMax) and the wells' |F_w| / |target|
 constexpr int S_H0 = 8;       // 72 Gram-Schmidt coefficients
 constexpr int S_H1 = 80;      // 72 re-orthogonalisation coefficients
 constexpr int S_NRM = 152;    // squared norm
@@ -1165,17 +1165,18 @@ int isc_newton_step(isc_handle* h, double dt, isc_newton_info* info) {
     Region rg(h, ISC_K_NORM, 2);
     launch_norms(*h, h->stream);
   }
-  CUDA_TRY(h, cudaMemcpyAsync(h->h_scal, h->scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(h->h_scal + S_NORM, h->scal + S_NORM, 4 * sizeof(double), cudaMemcpyDeviceToHost,
+                              h->stream));
   st = check_device_status(h);  // synchronises
   if (st) {
     info->status = st;
     return st;
   }
-  info->norm_mass = h->h_scal[0] * dt;
-  info->norm_energy = h->h_scal[1] * dt;
-  info->norm_gs = h->h_scal[2];
+  info->norm_mass = h->h_scal[S_NORM] * dt;
+  info->norm_energy = h->h_scal[S_NORM + 1] * dt;
+  info->norm_gs = h->h_scal[S_NORM + 2];
   info->norm = std::max(info->norm_mass, std::max(info->norm_energy, info->norm_gs));
-  if (h->nwc) info->norm = std::max(info->norm, h->h_scal[3]);  // coupled wells: max |F_w| / |target|
+  if (h->nwc) info->norm = std::max(info->norm, h->h_scal[S_NORM + 3]);  // coupled wells: max |F_w| / |target|
   if (!isfinite(info->norm)) {
     info->status = ISC_ERR_NONFINITE;
     return set_err(h, ISC_ERR_NONFINITE, "non-finite residual norm");
