@@ -107,3 +107,81 @@ def test_krylov_matches_dense_lu(solver, prec):
     assert res <= 2e-11
     cond = np.linalg.cond(linalg.bsr_to_dense(rp, col, vd))
     assert np.linalg.norm(x.reshape(-1) - ref) <= 10 * cond * 1e-11 * np.linalg.norm(ref)
+
+
+def test_bsr_matvec_is_the_library_bsr_product():
+    """The oracle's block loop y_i = sum_b A_ib x_col(b) against scipy's BSR product."""
+    import scipy.sparse as sp
+    case = inp.small_box(5, 3, 2)
+    rp, col, val, b = _system(case, 36)
+    x = np.random.default_rng(3).standard_normal(b.shape)
+    A = sp.bsr_matrix((val, col, rp), shape=(case.n * 8, case.n * 8))
+    ref = A @ x.reshape(-1)
+    y = linalg.bsr_matvec(rp, col, val, x).reshape(-1)
+    bound = 1e-13 * (abs(A) @ np.abs(x.reshape(-1)))
+    assert np.all(np.abs(y - ref) <= bound)
+
+
+def _k_eigenvalue_matrix(n, lams, seed):
+    """A = Q diag(lam) Q^T with len(set(lam)) distinct eigenvalues: for a generic b the
+    Krylov space K_j(A, b) has dimension min(j, k), so GMRES from x0 = 0 reaches the
+    exact solution at iteration k and not before."""
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    d = np.resize(np.asarray(lams, dtype=float), n)
+    return (Q * d) @ Q.T, rng.standard_normal(n)
+
+
+@pytest.mark.parametrize("lams", [[2.0], [1.0, 3.0], [1.0, 2.0, 5.0, 9.0], [0.5, 1.0, 2.0, 4.0, 7.0, 11.0]])
+def test_gmres_terminates_at_the_degree_of_the_minimal_polynomial(lams):
+    A, b = _k_eigenvalue_matrix(48, lams, 70 + len(lams))
+    x, its, rel = linalg.gmres(lambda v: A @ v, b, restart=30, rtol=1e-10, maxit=100)
+    assert its == len(lams)
+    assert np.linalg.norm(b - A @ x) <= 1e-10 * np.linalg.norm(b)
+    assert rel == pytest.approx(np.linalg.norm(b - A @ x) / np.linalg.norm(b), rel=1e-6, abs=1e-15)
+
+
+def test_gmres_restart_and_iteration_cap():
+    """GMRES(2) needs more than one cycle on six distinct eigenvalues; maxit caps the
+    total count of Arnoldi steps over all cycles, and each cycle's correction
+    minimises the residual over its Krylov space, so the residual never grows."""
+    A, b = _k_eigenvalue_matrix(48, [0.5, 1.0, 2.0, 4.0, 7.0, 11.0], 81)
+    prev = np.linalg.norm(b)
+    for m in range(1, 8):
+        x, its, rel = linalg.gmres(lambda v: A @ v, b, restart=2, rtol=1e-300, maxit=m)
+        assert its == m
+        r = np.linalg.norm(b - A @ x)
+        assert r <= prev * (1 + 1e-12)
+        prev = r
+    x1, _, _ = linalg.gmres(lambda v: A @ v, b, restart=2, rtol=1e-300, maxit=1)
+    # one Arnoldi step: x = (b.Ab / |Ab|^2) b, the 1-D residual minimiser
+    Ab = A @ b
+    assert np.allclose(x1, (b @ Ab) / (Ab @ Ab) * b, rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("lams", [[3.0], [1.0, 3.0], [1.0, 2.0, 5.0, 9.0]])
+def test_bicgstab_terminates_at_the_degree_of_the_minimal_polynomial(lams):
+    """For symmetric positive definite A and shadow residual r^ = r0, BiCG is CG, whose
+    polynomial annihilates r0 at step k; BiCGSTAB's intermediate residual s is that
+    BiCG residual times the earlier stabilising factors, so it vanishes at step k."""
+    A, b = _k_eigenvalue_matrix(40, lams, 90 + len(lams))
+    for maxit in (100, len(lams)):
+        x, its, rel = linalg.bicgstab(lambda v: A @ v, b, rtol=1e-10, maxit=maxit)
+        assert its == len(lams)
+        assert rel <= 1e-10
+        assert np.linalg.norm(b - A @ x) <= 1e-9 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("solver", ["gmres", "bicgstab"])
+def test_krylov_solvers_are_scale_invariant(solver):
+    """x(s b) = s x(b) with the same iteration count, down to right-hand sides far
+    below unit norm; only b = 0 returns x = 0 at once."""
+    A, b = _k_eigenvalue_matrix(40, [1.0, 2.0, 5.0, 9.0], 95)
+    f = getattr(linalg, solver)
+    x1, i1, _ = f(lambda v: A @ v, b, rtol=1e-10, maxit=100)
+    for s in (1e-6, 1e-150):
+        xs, i_s, _ = f(lambda v: A @ v, s * b, rtol=1e-10, maxit=100)
+        assert i_s == i1
+        assert np.allclose(xs, s * x1, rtol=1e-8, atol=0)
+    x0, i0, r0 = f(lambda v: A @ v, 0 * b, rtol=1e-10, maxit=100)
+    assert i0 == 0 and r0 == 0.0 and not np.any(x0)
