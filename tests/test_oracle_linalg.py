@@ -46,6 +46,28 @@ def test_gauss_jordan_pivoting_handles_zero_leading_entry_and_detects_singular()
         linalg.gauss_jordan_decouple(rp, col, A[None], b)
 
 
+def test_gauss_jordan_singularity_is_judged_against_the_pivot_row():
+    """A pivot counts as zero when it is below 1e-300 times the largest entry of its
+    own row in the diagonal block: an all-zero row is singular (also as the last pivot), and a 1e-290 pivot
+    beside a 1e12 entry is singular while a 1e-280 one is still eliminated exactly."""
+    rp, col = np.array([0, 1]), np.array([0])
+    b = np.linspace(1.0, 2.0, 8)[None, :]
+    for zero_row in (5, 7):
+        A = np.eye(8)
+        A[zero_row] = 0.0
+        with pytest.raises(linalg.SingularBlockError):
+            linalg.gauss_jordan_decouple(rp, col, A[None], b)
+    A = np.eye(8)
+    A[6, 7] = 1e12
+    A[6, 6] = 1e-290
+    with pytest.raises(linalg.SingularBlockError):
+        linalg.gauss_jordan_decouple(rp, col, A[None], b)
+    A[6, 6] = 1e-280
+    vd, bd = linalg.gauss_jordan_decouple(rp, col, A[None], b)
+    ref = np.linalg.solve(A, b[0])
+    assert np.allclose(bd[0], ref, rtol=1e-12, atol=0)
+
+
 def test_decoupled_and_original_systems_have_the_same_solution():
     case = inp.small_box(3, 2, 2)
     rp, col, val, b = _system(case, 32)
@@ -174,14 +196,40 @@ def test_bicgstab_terminates_at_the_degree_of_the_minimal_polynomial(lams):
 
 @pytest.mark.parametrize("solver", ["gmres", "bicgstab"])
 def test_krylov_solvers_are_scale_invariant(solver):
-    """x(s b) = s x(b) with the same iteration count, down to right-hand sides far
-    below unit norm; only b = 0 returns x = 0 at once."""
+    """Scaling b or A by a power of two scales every rounded operation exactly, so
+    x(s b) = s x(b) and x(s A) = x(A) / s bit for bit, with the same iteration count
+    and relative residual, down to right-hand sides near 1e-120 (where the squares
+    in the residual norm are still normal numbers); only b = 0 returns
+    x = 0 at once."""
     A, b = _k_eigenvalue_matrix(40, [1.0, 2.0, 5.0, 9.0], 95)
     f = getattr(linalg, solver)
-    x1, i1, _ = f(lambda v: A @ v, b, rtol=1e-10, maxit=100)
-    for s in (1e-6, 1e-150):
-        xs, i_s, _ = f(lambda v: A @ v, s * b, rtol=1e-10, maxit=100)
-        assert i_s == i1
-        assert np.allclose(xs, s * x1, rtol=1e-8, atol=0)
+    x1, i1, r1 = f(lambda v: A @ v, b, rtol=1e-10, maxit=100)
+    for s in (2.0 ** -20, 2.0 ** -400):
+        xs, i_s, rs = f(lambda v: A @ v, s * b, rtol=1e-10, maxit=100)
+        assert i_s == i1 and rs == r1
+        assert np.array_equal(xs, s * x1)
+    for sa in (2.0 ** -14, 2.0 ** 14):
+        xa, i_a, ra = f(lambda v: sa * (A @ v), b, rtol=1e-10, maxit=100)
+        assert i_a == i1 and ra == r1
+        assert np.array_equal(xa, x1 / sa)
     x0, i0, r0 = f(lambda v: A @ v, 0 * b, rtol=1e-10, maxit=100)
     assert i0 == 0 and r0 == 0.0 and not np.any(x0)
+
+
+def test_bicgstab_step_minimises_the_residual_along_its_stabilising_direction():
+    """One BiCGSTAB step from x0 = 0 (no preconditioner, shadow residual r0 = b): the
+    BiCG half-step x = alpha b with alpha = b.b / b.Ab leaves s = b - alpha Ab, then the
+    stabilising step x += omega s picks omega so that the new residual is orthogonal
+    to A s (the one-dimensional minimal residual)."""
+    A, b = _k_eigenvalue_matrix(40, [1.0, 2.0, 5.0, 9.0], 97)
+    A = A + 0.3 * np.triu(np.random.default_rng(5).standard_normal((40, 40)), 1) / 40
+    x1, its, rel = linalg.bicgstab(lambda v: A @ v, b, rtol=1e-300, maxit=1)
+    assert its == 1
+    alpha = (b @ b) / (b @ (A @ b))
+    s = b - alpha * (A @ b)
+    d = x1 - alpha * b                      # the stabilising correction: a multiple of s
+    assert np.linalg.norm(d - (d @ s) / (s @ s) * s) <= 1e-12 * np.linalg.norm(d)
+    r1 = b - A @ x1
+    As = A @ s
+    assert abs(r1 @ As) <= 1e-12 * np.linalg.norm(r1) * np.linalg.norm(As)
+    assert rel == pytest.approx(np.linalg.norm(r1) / np.linalg.norm(b), rel=1e-10)
