@@ -31,6 +31,9 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 # fastest pins first, so that most mutants die within seconds
 PINS = ["test_oracle_props.py", "test_oracle_residual.py", "test_oracle_linalg.py", "test_oracle_wells.py",
         "test_oracle_cpr.py", "test_oracle_newton.py", "test_oracle_adjoint.py", "test_oracle_adjoint_wells.py"]
+# each module's own pins run first
+OWN = {"linalg": ["test_oracle_linalg.py"], "cpr": ["test_oracle_cpr.py"], "sim": ["test_oracle_newton.py"],
+       "adjoint": ["test_oracle_adjoint.py", "test_oracle_adjoint_wells.py"]}
 SWAP = {ast.Add: ast.Sub, ast.Sub: ast.Add, ast.Mult: ast.Div, ast.Div: ast.Mult}
 CMP = {ast.Lt: ast.LtE, ast.LtE: ast.Lt, ast.Gt: ast.GtE, ast.GtE: ast.Gt}
 
@@ -95,7 +98,8 @@ def run_one(m, timeout, workdir):
             f.write(m["code"])
         env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", PYTHONDONTWRITEBYTECODE="1")
         cmd = [sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu"]
-        cmd += [os.path.join("tests", p) for p in PINS]
+        own = OWN.get(m["module"], [])
+        cmd += [os.path.join("tests", p) for p in own + [q for q in PINS if q not in own]]
         t0 = time.time()
         try:
             p = subprocess.run(cmd, cwd=work, capture_output=True, text=True, env=env, timeout=timeout)

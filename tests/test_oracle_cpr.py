@@ -150,3 +150,55 @@ def test_cpr_cuts_gmres_iterations_on_a_field_block(field_block):
                                    30, 1e-6, 3000)
     assert rel <= 1e-6
     assert its_cpr <= 12 and 3 * its_cpr <= its_ilu, (its_cpr, its_ilu)
+
+
+@pytest.mark.parametrize("dims", [(2, 1, 1), (1, 2, 1)])
+def test_vcycle_on_two_cells_by_hand(dims):
+    """Two cells side by side in x or in y (one column of height 1 each): colour 0 is
+    cell 0, colour 1 is cell 1, and one aggregation step leaves one coarse cell
+    with A_c = a + b + c + d. One pre-smoothing sweep (cell 0 then cell 1), the
+    coarse correction added to both cells, one post-smoothing sweep, written out
+    by hand for A = [[a, b], [c, d]]."""
+    a, b, c, d = 4.0, -1.5, -0.5, 3.0
+    A = sp.csr_matrix(np.array([[a, b], [c, d]]))
+    mg = cpr.AggregationMG(A, *dims)
+    assert mg.dims == [dims, (1, 1, 1)]
+    f0, f1 = 1.0, 2.0
+    x0 = f0 / a                            # pre-smoothing, colour 0 (x1 = 0)
+    x1 = (f1 - c * x0) / d                 # pre-smoothing, colour 1
+    r0 = f0 - a * x0 - b * x1              # r1 = 0 after its own solve
+    r1 = f1 - c * x0 - d * x1
+    e = (r0 + r1) / (a + b + c + d)        # coarse solve, prolonged to both cells
+    x0, x1 = x0 + e, x1 + e
+    x0 = (f0 - b * x1) / a                 # post-smoothing, colour 0
+    x1 = (f1 - c * x0) / d                 # post-smoothing, colour 1
+    np.testing.assert_allclose(mg.vcycle(np.array([f0, f1])), [x0, x1], rtol=1e-14)
+
+
+def test_red_black_half_sweeps_solve_their_own_columns():
+    """In one line-smoothing sweep from x = 0, every colour-0 column is solved
+    with its neighbours still zero (x-y neighbours always have the other colour),
+    and after the colour-1 half-sweep every colour-1 column's equations hold."""
+    nx, ny, nz = 5, 4, 6
+    A = _random_stencil(nx, ny, nz, 11, symmetric=False)
+    mg = cpr.AggregationMG(A, nx, ny, nz)
+    f = np.random.default_rng(12).standard_normal(A.shape[0])
+    x = mg.smooth(0, np.zeros_like(f), f, 1)
+    r = f - A @ x
+    for cy in range(ny):
+        for cx in range(nx):
+            idx = cx + nx * cy + nx * ny * np.arange(nz)
+            if (cx + cy) % 2 == 0:
+                T = A[idx][:, idx].toarray()
+                np.testing.assert_allclose(x[idx], np.linalg.solve(T, f[idx]), rtol=1e-12)
+            else:
+                assert np.max(np.abs(r[idx])) <= 1e-12 * np.max(np.abs(f))
+
+
+def test_cpr_defaults_one_pre_and_one_post_sweep_and_pairwise_aggregation(field_block):
+    """The CPR-PF reading: one V-cycle with one pre- and one post-smoothing sweep,
+    aggregates of 2 x 2 cells in x-y, z kept."""
+    case, rp, col, vd = field_block[:4]
+    P = cpr.CPRPreconditioner(rp, col, vd, case.nx, case.ny, case.nz)
+    assert (P.mg.nu1, P.mg.nu2) == (1, 1)
+    assert P.mg.dims[1] == ((case.nx + 1) // 2, (case.ny + 1) // 2, case.nz)
