@@ -188,3 +188,89 @@ def test_coke_solve_satisfies_its_equation():
     s = case.reactions["stoich"][:, 6]
     g = C - st["coke"] - dt * sum(s[r] * rates[r] for r in range(4))
     assert np.max(np.abs(g) / (np.abs(C) + np.abs(st["coke"]))) < 1e-13
+
+
+def _cells(case, p, T, x_lo=0.6, Sw=0.3, Sg=0.2, n=None):
+    """A column of states u (8, n) with the given pressure, temperature, oil
+    composition and saturations (gas composition away from the constraint is
+    irrelevant to the properties tested here)."""
+    n = n or np.broadcast(np.asarray(p), np.asarray(T), np.asarray(x_lo)).size
+    u = np.zeros((8, n))
+    u[0], u[1], u[2], u[3], u[4], u[5], u[6], u[7] = p, x_lo, 0.05, 0.7, 0.1, T, Sw, Sg
+    return u
+
+
+def test_gas_fractions_of_pure_oils_and_linear_in_the_oil_composition():
+    """y_LO = K_LO x_LO and y_HO = f(S_o) K_HO x_HO with x_HO = 1 - x_LO: a pure
+    LO oil sends no HO to the gas and a pure HO oil no LO; y_HO is proportional
+    to x_HO."""
+    p, T = 3e6, 500.0
+    y1 = model.gas_fractions(FL, p, T, 1.0, 0.1, 0.7, 0.1, 0.3, 0.5)
+    y0 = model.gas_fractions(FL, p, T, 0.0, 0.1, 0.7, 0.1, 0.3, 0.5)
+    assert y1[inp.HO] == 0.0 and y1[inp.LO] > 0.0
+    assert y0[inp.LO] == 0.0 and y0[inp.HO] > 0.0
+    for x in (0.25, 0.6):
+        y = model.gas_fractions(FL, p, T, x, 0.1, 0.7, 0.1, 0.3, 0.5)
+        assert y[inp.HO] == pytest.approx((1.0 - x) * y0[inp.HO], rel=1e-14)
+        assert y[inp.LO] == pytest.approx(x * y1[inp.LO], rel=1e-14)
+
+
+def test_latent_heat_vanishes_at_the_critical_temperature():
+    Tc = FL["Tc"][inp.W]
+    Hv = model.vaporisation_enthalpy(FL, inp.W, np.array([Tc - 0.5, Tc, Tc + 0.5]))
+    assert Hv[0] > 0.0
+    assert Hv[1] == 0.0 and Hv[2] == 0.0
+
+
+def test_liquid_enthalpy_does_not_depend_on_pressure():
+    """The liquid enthalpies are H_gas - H_vap, functions of T (and the oil
+    composition) only; the internal energies are those minus the flow work p/rho."""
+    case = inp.tube_case(n_cells=3)
+    T = 450.0
+    bp = model.base_properties(case, _cells(case, np.array([1e5, 3e6, 2e7]), T))
+    for ph in ("w", "o"):
+        H = bp["U_" + ph] + bp["p"] / bp["rho_" + ph]
+        np.testing.assert_allclose(H, H[0], rtol=1e-12)
+        assert np.all(bp["U_" + ph] < H)
+
+
+def test_porosity_and_rock_energy_at_their_reference():
+    """phi(p_ref, T_ref) = phi_ref with (1/phi) dphi/dp = c_por there (the pore
+    compressibility), and the rock's internal energy is zero at T_ref with
+    dU_r/dT = cv1 + cv2 T (its volumetric heat capacity)."""
+    case = inp.field_case(4, 3, 2, 0, 1, "f", 30 * inp.DAY, 40)
+    rock = case.rock
+    u = _cells(case, rock["p_ref"], rock["T_ref"], n=case.n)
+    bp = model.base_properties(case, u)
+    np.testing.assert_allclose(bp["phi"], case.phi_ref, rtol=1e-15)
+    assert np.all(bp["U_r"] == 0.0)
+    h = 1e-20
+    for k, expect in ((0, rock["cpor"]), (5, None)):
+        uc = u.astype(complex)
+        uc[k] += 1j * h
+        bc = model.base_properties(case, uc)
+        if k == 0:
+            np.testing.assert_allclose(bc["phi"].imag / h / case.phi_ref, expect, rtol=1e-12)
+        else:
+            np.testing.assert_allclose(bc["U_r"].imag / h, rock["cv1"] + rock["cv2"] * rock["T_ref"], rtol=1e-12)
+
+
+def test_coke_takes_pore_volume_and_carries_its_own_energy():
+    """Coke C_c (mol per bulk volume) fills C_c / rho_c of the pore space, so every
+    fluid amount scales by phi_f / phi; at T_ref (rock and coke energies zero) the
+    energy does too. Away from T_ref the energy changes by C_c (cp_c (T - T_ref)
+    - e_f / rho_c), e_f the fluids' energy per pore volume."""
+    case = inp.tube_case(n_cells=4)
+    fl = case.fluid
+    for T in (case.rock["T_ref"], 650.0):
+        u = _cells(case, 2e6, T, n=case.n)
+        bp = model.base_properties(case, u)
+        c = np.array([0.0, 0.1, 0.5, 1.0]) * 0.3 * bp["phi"] * fl["coke_rho"]
+        a0 = model.accumulation(case, bp, 0.0 * c)
+        a1 = model.accumulation(case, bp, c)
+        scale = (bp["phi"] - c / fl["coke_rho"]) / bp["phi"]
+        for k in range(6):
+            np.testing.assert_allclose(a1[k], a0[k] * scale, rtol=1e-13)
+        e_f = (a0[6] - (1.0 - bp["phi"]) * bp["U_r"]) / bp["phi"]
+        dE = c * (fl["coke_cp"] * (T - fl["T_ref"]) - e_f / fl["coke_rho"])
+        np.testing.assert_allclose(a1[6], a0[6] + dE, rtol=1e-12, atol=1e-9 * np.abs(a0[6]).max())
