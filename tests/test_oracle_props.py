@@ -274,3 +274,55 @@ def test_coke_takes_pore_volume_and_carries_its_own_energy():
         e_f = (a0[6] - (1.0 - bp["phi"]) * bp["U_r"]) / bp["phi"]
         dE = c * (fl["coke_cp"] * (T - fl["T_ref"]) - e_f / fl["coke_rho"])
         np.testing.assert_allclose(a1[6], a0[6] + dE, rtol=1e-12, atol=1e-9 * np.abs(a0[6]).max())
+
+
+def test_reaction_rates_special_cases_orders_and_arrhenius():
+    """Crookston rate laws (Sec. 2.2, Reaction Model): the LO and HO oxidations are
+    first order in the oxygen partial pressure and in their oil component's
+    concentration phi_f S_o rho_o x_c, vanish without oxygen, without that
+    component or without oil; cracking stops at the coke cap; coke burning is
+    first order in p_O2 and in C_c with k = A exp(-E_a / RT)."""
+    case = inp.tube_case(n_cells=1)
+    rx = case.reactions
+    kinds = list(rx["kind"])
+    ox = [r for r in range(rx["nr"]) if kinds[r] == inp.RXN_OIL_OXIDATION]
+    crk = [r for r in range(rx["nr"]) if kinds[r] == inp.RXN_CRACKING]
+    cb = [r for r in range(rx["nr"]) if kinds[r] == inp.RXN_COKE_OXIDATION]
+    assert ox and crk and cb
+    coke = np.array([0.3 * rx["coke_max"]])
+
+    def rates(p=3e6, T=600.0, x_lo=0.6, Sw=0.2, Sg=0.3, y_o2=0.1, c=coke):
+        u = _cells(case, p, T, x_lo=x_lo, Sw=Sw, Sg=Sg, n=1)
+        u[2] = y_o2
+        return np.array([r[0] for r in model.reaction_rates(case, model.base_properties(case, u), c)])
+
+    base = rates()
+    assert np.all(base > 0.0)
+    np.testing.assert_allclose(rates(y_o2=0.2)[ox + cb], 2.0 * base[ox + cb], rtol=1e-13)
+    np.testing.assert_allclose(rates(y_o2=0.2)[crk], base[crk], rtol=1e-13)
+    assert np.all(rates(y_o2=0.0)[ox + cb] == 0.0)
+    # oil amount: S_o halves (gas takes its place), the oil reactions halve
+    np.testing.assert_allclose(rates(Sg=0.55)[ox + crk], 0.5 * base[ox + crk], rtol=1e-13)
+    assert np.all(rates(Sg=0.8)[ox + crk] == 0.0)
+    for r in ox + crk:
+        pure_other = 0.0 if rx["comp"][r] == inp.LO else 1.0
+        assert rates(x_lo=pure_other)[r] == 0.0
+    assert np.all(rates(c=np.array([rx["coke_max"]]))[crk] == 0.0)
+    np.testing.assert_allclose(rates(c=2 * coke)[cb], 2.0 * base[cb], rtol=1e-13)
+    T1, T2 = 600.0, 750.0
+    for r in cb:
+        ratio = rates(T=T2)[r] / rates(T=T1)[r]
+        assert ratio == pytest.approx(np.exp(-rx["Ea"][r] / model.R_GAS * (1 / T2 - 1 / T1)), rel=1e-12)
+
+
+@pytest.mark.parametrize("phase", [0, 1, 2])
+def test_specific_weight_is_g_times_the_stored_mass_density(phase):
+    """gamma_alpha / g equals the mass per volume of phase alpha that the
+    accumulation stores when alpha fills the pores alone: sum_c M_c N_c / phi."""
+    case = inp.tube_case(n_cells=1)
+    sat = [(1.0, 0.0), (0.0, 0.0), (0.0, 1.0)][phase]
+    u = _cells(case, 3e6, 500.0, x_lo=0.4, Sw=sat[0], Sg=sat[1], n=1)
+    bp = model.base_properties(case, u)
+    N = model.accumulation(case, bp, np.zeros(1))[:6]
+    mass = sum(case.fluid["M"][c] * N[c] for c in range(6)) / bp["phi"]
+    assert bp["gam"][phase][0] == pytest.approx(case.fluid["gravity"] * mass[0], rel=1e-13)
