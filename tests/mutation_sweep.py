@@ -29,7 +29,7 @@ from concurrent.futures import ThreadPoolExecutor
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 # fastest pins first, so that most mutants die within seconds
-PINS = ["test_oracle_props.py", "test_oracle_residual.py", "test_oracle_linalg.py", "test_oracle_wells.py",
+PINS = ["test_oracle_props.py", "test_oracle_transport.py", "test_oracle_residual.py", "test_oracle_linalg.py", "test_oracle_wells.py",
         "test_oracle_cpr.py", "test_oracle_newton.py", "test_oracle_adjoint.py", "test_oracle_adjoint_wells.py"]
 # each module's own pins run first
 OWN = {"linalg": ["test_oracle_linalg.py"], "cpr": ["test_oracle_cpr.py"], "sim": ["test_oracle_newton.py"],
