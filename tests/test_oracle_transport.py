@@ -179,3 +179,19 @@ def test_oil_reaction_rates_per_stored_mole_of_their_component():
         ratios.append(row)
     ratios = np.array(ratios)
     np.testing.assert_allclose(ratios, ratios[0][None, :].repeat(3, 0), rtol=1e-12)
+
+
+def test_a_single_cell_has_no_face_terms():
+    """One cell, no wells, no reactions: the balance rows are the accumulation
+    change alone, V/dt (N - N_old)."""
+    case = _line(0, n=1)
+    u = _state(1, 4e6, 500.0, 0.3, 0.2)
+    bp = model.base_properties(case, u)
+    acc = model.accumulation(case, bp, np.zeros(1))
+    F0 = model.residual(case, u, np.zeros(1), acc, 50.0)
+    assert np.all(F0[:7] == 0.0)
+    old = [a * 0.9 for a in acc]
+    F1 = model.residual(case, u, np.zeros(1), old, 50.0)
+    V = case.dx * case.dy * case.dz
+    for r in range(7):
+        assert F1[r, 0] == pytest.approx(V / 50.0 * 0.1 * acc[r][0], rel=1e-12)
