@@ -162,3 +162,87 @@ def test_waterflood_matches_buckley_leverett():
             assert front[-1] <= 4 * dx
     assert errs[1] < errs[0] and errs[2] < errs[1]
     assert front[1] < front[0] and front[2] < front[1]
+
+
+def test_safeguard_other_branches():
+    """The remaining branches of the update rule: x_LO pushed above one moves half
+    way to one, y_N2, y_CO2 and S_g halve when they would turn negative, and the
+    pressure and temperature limits hold in the negative direction too."""
+    u = np.array([[5e6], [0.4], [0.2], [0.3], [0.1], [400.0], [0.2], [0.3]])
+    du = np.array([[-3e6], [0.9], [0.0], [-0.5], [-0.2], [-80.0], [0.0], [-0.4]])
+    un = sim.apply_update(u, du)
+    assert un[0, 0] == pytest.approx(4e6)        # dp >= -0.2 p
+    assert un[5, 0] == pytest.approx(350.0)      # dT >= -50 K
+    assert un[1, 0] == pytest.approx(0.7)        # 1 - (1 - 0.4) / 2
+    assert un[2, 0] == 0.2                       # unchanged
+    assert un[3, 0] == pytest.approx(0.15)       # y_N2 halves
+    assert un[4, 0] == pytest.approx(0.05)       # y_CO2 halves
+    assert un[6, 0] == 0.2
+    assert un[7, 0] == pytest.approx(0.15)       # S_g halves
+    # a small update passes through untouched
+    small = 1e-3 * du
+    np.testing.assert_allclose(sim.apply_update(u, small), u + small, rtol=1e-15)
+
+
+def test_step_size_controller():
+    """dt grows or shrinks so that the largest temperature change would be 20 K
+    and the largest saturation change 0.2, by a factor in [0.5, 2], capped at
+    dt_max."""
+    u0 = np.zeros((8, 3))
+    u0[5] = 400.0
+
+    def moved(dT, dS):
+        u1 = u0.copy()
+        u1[5, 1] += dT
+        u1[6, 2] += dS
+        return u1
+
+    assert sim.next_dt(10.0, u0, moved(10.0, 0.05), 1e9) == pytest.approx(20.0)   # both small: x2
+    assert sim.next_dt(10.0, u0, moved(16.0, 0.05), 1e9) == pytest.approx(12.5)   # 20 / 16
+    assert sim.next_dt(10.0, u0, moved(5.0, 0.16), 1e9) == pytest.approx(12.5)    # 0.2 / 0.16
+    assert sim.next_dt(10.0, u0, moved(100.0, 0.0), 1e9) == pytest.approx(5.0)    # floor 0.5
+    assert sim.next_dt(10.0, u0, moved(1.0, 0.0), 15.0) == pytest.approx(15.0)    # dt_max
+    u1 = u0.copy()
+    u1[7, 0] -= 0.4                                                              # S_g counts too
+    assert sim.next_dt(10.0, u0, u1, 1e9) == pytest.approx(5.0)
+
+
+def test_initial_state_recipe():
+    """Uniform p, T, S_w, S_g and x_LO from the recipe, ignited cells at T_ignite,
+    no coke; O2, N2 and CO2 share what the water and oil vapours leave of the gas
+    in the recipe's ratios, so the gas constraint holds in every cell at the
+    initial temperature."""
+    case = inp.tube_case()
+    ini = case.init
+    u, coke = sim.initial_state(case)
+    assert np.all(coke == 0.0)
+    for k, key in ((0, "p"), (1, "x_LO"), (6, "Sw"), (7, "Sg")):
+        assert np.all(u[k] == ini[key])
+    hot = np.zeros(case.n, dtype=bool)
+    hot[case.ignited] = True
+    assert hot.any() and not hot.all()
+    assert np.all(u[5, hot] == ini["T_ignite"]) and np.all(u[5, ~hot] == ini["T"])
+    y = model.gas_fractions(case.fluid, u[0], u[5], u[1], u[2], u[3], u[4], u[6], 1 - u[6] - u[7])
+    np.testing.assert_allclose(sum(y)[~hot], 1.0, rtol=1e-14)
+    r = np.asarray(ini["y_rest"], dtype=float)
+    for g in range(3):
+        np.testing.assert_allclose(u[2 + g] * r.sum(), r[g] * (u[2] + u[3] + u[4]), rtol=1e-14)
+
+
+def test_convergence_norms_are_relative_mass_and_rock_kelvin():
+    """e_mass dt is the residual's mole imbalance as a fraction of the cell's
+    stored moles; e_energy dt is its energy imbalance in kelvin of rock heating."""
+    case = inp.small_box(3, 2, 2)
+    st = inp.random_state(case, 5)
+    u, coke = st["u"], st["coke"]
+    acc = model.accumulation(case, model.base_properties(case, u), coke)
+    ntot = sum(np.abs(acc[c]) for c in range(6))
+    V, dt = model.cell_volume(case), 250.0
+    F = np.zeros((8, case.n))
+    F[3, 4] = V / dt * 1e-6 * ntot[4]
+    F[6, 7] = V / dt * case.rock["cv1"] * 1e-3
+    F[7, 2] = 3e-9
+    e = sim.convergence_norms(case, F, u, coke)
+    assert e[0] * dt == pytest.approx(1e-6, rel=1e-12)
+    assert e[1] * dt == pytest.approx(1e-3, rel=1e-12)
+    assert e[2] == pytest.approx(3e-9, rel=1e-15)
