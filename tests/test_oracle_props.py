@@ -326,3 +326,19 @@ def test_specific_weight_is_g_times_the_stored_mass_density(phase):
     N = model.accumulation(case, bp, np.zeros(1))[:6]
     mass = sum(case.fluid["M"][c] * N[c] for c in range(6)) / bp["phi"]
     assert bp["gam"][phase][0] == pytest.approx(case.fluid["gravity"] * mass[0], rel=1e-13)
+
+
+def test_corey_end_points_and_exponent():
+    """Corey curves of exponent two: each relative permeability is zero at its
+    critical or residual saturation, one at the other end of its mobile range,
+    a quarter half way; Stone II gives k_ro = k_rocw = 1 at connate water
+    without gas and zero at the residual oil of the water-oil table."""
+    Swc, Sorw, Sgc = FL["Swc"], FL["Sorw"], FL["Sgc"]
+    a = np.array
+    krw, kro, krg = model.rel_perms(FL, a([Swc, 1 - Sorw, 0.5 * (Swc + 1 - Sorw), Swc, Swc, Swc]),
+                                    a([0.0, 0.0, 0.0, Sgc, 1 - Swc, 0.5 * (Sgc + 1 - Swc)]))
+    np.testing.assert_allclose(krw[:3], [0.0, 1.0, 0.25], atol=1e-15)
+    np.testing.assert_allclose(krg[3:], [0.0, 1.0, 0.25], atol=1e-15)
+    assert kro[0] == pytest.approx(1.0, abs=1e-15)
+    assert kro[1] == pytest.approx(0.0, abs=1e-15)
+    assert kro[4] == pytest.approx(0.0, abs=1e-15)
