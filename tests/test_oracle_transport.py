@@ -195,3 +195,34 @@ def test_a_single_cell_has_no_face_terms():
     V = case.dx * case.dy * case.dz
     for r in range(7):
         assert F1[r, 0] == pytest.approx(V / 50.0 * 0.1 * acc[r][0], rel=1e-12)
+
+
+@pytest.mark.parametrize("c", [inp.W, inp.LO, inp.HO])
+def test_liquid_compressibility_and_thermal_expansion(c):
+    """At the reference state (1/rho) d rho/dp is the liquid's compressibility
+    c_p and -(1/rho) d rho/dT its thermal expansion c_T1: liquids expand on
+    heating."""
+    fl = inp.small_box(2, 1, 1).fluid
+    p0, T0 = fl["p_ref"], fl["T_ref"]
+    h = 1e-20
+    rho = model.liquid_density(fl, c, np.array([p0]), np.array([T0]))[0]
+    assert rho == pytest.approx(fl["rho_ref"][c], rel=1e-15)
+    dp = model.liquid_density(fl, c, np.array([p0 + 1j * h]), np.array([T0]))[0].imag / h
+    dT = model.liquid_density(fl, c, np.array([p0]), np.array([T0 + 1j * h]))[0].imag / h
+    assert dp / rho == pytest.approx(fl["cp"][c], rel=1e-12)
+    assert -dT / rho == pytest.approx(fl["ct1"][c], rel=1e-12)
+    assert fl["ct1"][c] > 0.0
+
+
+@pytest.mark.parametrize("phase", [0, 1, 2])
+def test_stored_energy_of_a_single_phase_is_enthalpy_density_minus_pressure(phase):
+    """A cell of porosity one filled with one phase stores E = rho h - p per
+    volume (u = h - p v), at any temperature (no rock to heat)."""
+    case = _line(0, n=1, phi=1.0)
+    sat = [(1.0, 0.0), (0.0, 0.0), (0.0, 1.0)][phase]
+    u = _state(1, case.rock["p_ref"], 560.0, sat[0], sat[1], x_lo=0.35, y=(0.1, 0.6, 0.1))
+    bp = model.base_properties(case, u)
+    E = model.accumulation(case, bp, np.zeros(1))[6][0]
+    rho = (bp["rho_w"], bp["rho_o"], bp["rho_g"])[phase][0]
+    H = (bp["H_w"], bp["H_o"], bp["H_g"])[phase][0]
+    assert E == pytest.approx(rho * H - bp["p"][0], rel=1e-12)
