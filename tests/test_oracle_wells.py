@@ -114,3 +114,27 @@ def test_rate_control_is_met_at_newton_convergence(box):
     Q = model.coupled_phase_rates(coupled, bp, model.coupled_wells(coupled)[0], bn[0])
     assert -sum(np.sum(q) for q in Q) == pytest.approx(target, rel=1e-10)
     assert 4.5e6 < bn[0] < 5.0e6    # a smaller rate than at 4.5 MPa needs a higher bottom-hole pressure
+
+
+def test_producers_above_reservoir_pressure_are_shut(box):
+    """Producers only take fluid out: with the bottom-hole pressure (fixed or
+    coupled) above every perforated cell's pressure the well terms vanish, and
+    the residual is the one without the well."""
+    case, u, c = box
+    base = _no_gravity(case)
+    acc = model.old_accumulation(base, u, c)
+    bhp = 1.5 * float(np.max(u[0]))
+    shut = copy.copy(base)
+    shut.wells = [copy.copy(w) for w in base.wells]
+    for w in shut.wells:
+        if w.kind == inp.WELL_BHP_PRODUCER:
+            w.target = bhp
+    none = copy.copy(base)
+    none.wells = [w for w in base.wells if w.kind != inp.WELL_BHP_PRODUCER]
+    F_none = model.residual(none, u, c, acc, 100.0)
+    np.testing.assert_array_equal(model.residual(shut, u, c, acc, 100.0), F_none)
+    coupled = inp.with_coupled_producer(base, inp.CTRL_BHP, bhp, bhp)
+    w = model.coupled_wells(coupled)[0]
+    Q = model.coupled_phase_rates(coupled, model.base_properties(coupled, u), w, bhp)
+    assert all(np.all(q == 0.0) for q in Q)
+    np.testing.assert_array_equal(model.residual(coupled, u, c, acc, 100.0, bhp=np.array([bhp])), F_none)
