@@ -342,3 +342,7 @@ def test_corey_end_points_and_exponent():
     assert kro[0] == pytest.approx(1.0, abs=1e-15)
     assert kro[1] == pytest.approx(0.0, abs=1e-15)
     assert kro[4] == pytest.approx(0.0, abs=1e-15)
+    # without gas Stone II is k_row, down to the small values next to residual oil
+    for d in (0.01, 0.002):
+        _, k, _ = model.rel_perms(FL, a([1 - Sorw - d]), a([0.0]))
+        assert k[0] == pytest.approx((d / (1 - Swc - Sorw)) ** 2, rel=1e-12)
