@@ -68,6 +68,10 @@ def test_tube_runs_to_two_hours():
     opts.solve.solver = "dense"
     u, coke, dts, stats = sim.run(case, case.t_end, 5.0, 150.0, opts)
     assert stats["t"] == pytest.approx(case.t_end)
+    assert sum(dts) == pytest.approx(case.t_end, rel=1e-12)
+    assert stats["steps"] == len(dts) == len(stats["its_per_step"])
+    assert stats["newton"] >= sum(stats["its_per_step"])
+    assert (stats["cuts"] == 0) == (stats["newton"] == sum(stats["its_per_step"]))
     assert 40 <= stats["steps"] <= 80
     So = 1 - u[6] - u[7]
     assert np.all(u[6] > 0) and np.all(u[7] > 0) and np.all(So > 0)
@@ -246,3 +250,58 @@ def test_convergence_norms_are_relative_mass_and_rock_kelvin():
     assert e[0] * dt == pytest.approx(1e-6, rel=1e-12)
     assert e[1] * dt == pytest.approx(1e-3, rel=1e-12)
     assert e[2] == pytest.approx(3e-9, rel=1e-15)
+
+
+def _one_cell_no_sources():
+    import dataclasses
+    base = inp.small_box(2, 1, 1)
+    rx = copy.deepcopy(base.reactions)
+    rx["A"] = np.zeros_like(rx["A"])
+    return dataclasses.replace(base, nx=1, depth=base.depth[:1], phi_ref=base.phi_ref[:1], perm=base.perm[:, :1],
+                               reactions=rx, wells=[], ignited=np.zeros(0, dtype=np.int32))
+
+
+def test_newton_norm_is_relative_mass_kelvin_and_gas_constraint():
+    """The Newton step's convergence measure is the largest of the relative mole
+    imbalance, the energy imbalance in kelvin of rock heating and |sum y - 1|,
+    whatever the step size: one cell that stores 10 % more than at the old time."""
+    case = _one_cell_no_sources()
+    u = np.array([[4e6], [0.5], [0.05], [0.7], [0.1], [480.0], [0.3], [0.2]])
+    acc = model.accumulation(case, model.base_properties(case, u), np.zeros(1))
+    old = [0.9 * a for a in acc]
+    mass = 0.1 * max(abs(acc[c][0]) for c in range(6)) / sum(abs(acc[c][0]) for c in range(6))
+    kelvin = 0.1 * abs(acc[6][0]) / case.rock["cv1"]
+    y = model.gas_fractions(case.fluid, u[0], u[5], u[1], u[2], u[3], u[4], u[6], 1 - u[6] - u[7])
+    gs = abs(float(sum(y)[0]) - 1.0)
+    for dt in (50.0, 5000.0):
+        r = sim.newton_step(case, u, np.zeros(1), old, dt, sim.NewtonOptions(tol=1e-300))
+        assert r["norm"] == pytest.approx(max(mass, kelvin, gs), rel=1e-12)
+
+
+def test_newton_iteration_cap_counts_updates():
+    """timestep succeeds with maxit equal to the number of Newton updates it needs
+    and fails with one fewer."""
+    case = inp.small_box(3, 2, 1)
+    u, c = sim.initial_state(case)
+    opts = sim.NewtonOptions(tol=1e-8)
+    opts.solve.solver = "dense"
+    _, _, its, ok = sim.timestep(case, u, c, 500.0, opts)
+    assert ok and its >= 2
+    opts.maxit = its
+    assert sim.timestep(case, u, c, 500.0, opts)[3]
+    opts.maxit = its - 1
+    assert not sim.timestep(case, u, c, 500.0, opts)[3]
+
+
+def test_well_norm_is_relative_to_the_target():
+    case = inp.with_coupled_producer(inp.small_box(3, 2, 2), inp.CTRL_BHP, 4.0e6, 4.0e6)
+    w = model.coupled_wells(case)[0]
+    assert sim.well_norms(case, [0.01 * w.target]) == [pytest.approx(0.01, rel=1e-15)]
+
+
+def test_oil_saturation_rule_leaves_small_positive_oil_alone():
+    u = np.array([[5e6], [0.4], [0.2], [0.3], [0.1], [400.0], [0.2], [0.3]])
+    du = np.zeros((8, 1))
+    du[7, 0] = 0.4995                            # S_o = 1 - 0.2 - 0.7995 = 5e-4 > 0
+    un = sim.apply_update(u, du)
+    assert un[6, 0] == 0.2 and un[7, 0] == pytest.approx(0.7995, rel=1e-15)
