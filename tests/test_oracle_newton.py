@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import isc_inputs as inp
-from oracle import model, sim
+from oracle import linalg, model, sim
 
 
 def test_newton_converges_quadratically_on_the_tube():
@@ -264,18 +264,27 @@ def _one_cell_no_sources():
 def test_newton_norm_is_relative_mass_kelvin_and_gas_constraint():
     """The Newton step's convergence measure is the largest of the relative mole
     imbalance, the energy imbalance in kelvin of rock heating and |sum y - 1|,
-    whatever the step size: one cell that stores 10 % more than at the old time."""
+    whatever the step size. One cell whose gas fractions sum to one, storing 10 %
+    more moles (energy unchanged), then 10 % more energy (moles unchanged), then
+    with the N2 fraction off by 0.2."""
     case = _one_cell_no_sources()
-    u = np.array([[4e6], [0.5], [0.05], [0.7], [0.1], [480.0], [0.3], [0.2]])
+    u = np.array([[4e6], [0.5], [0.05], [0.0], [0.1], [420.0], [0.3], [0.2]])
+    y = model.gas_fractions(case.fluid, u[0], u[5], u[1], u[2], u[3], u[4], u[6], 1 - u[6] - u[7])
+    u[3] = 1.0 - sum(y)
+    assert 0.0 < u[3, 0] < 1.0
     acc = model.accumulation(case, model.base_properties(case, u), np.zeros(1))
-    old = [0.9 * a for a in acc]
     mass = 0.1 * max(abs(acc[c][0]) for c in range(6)) / sum(abs(acc[c][0]) for c in range(6))
     kelvin = 0.1 * abs(acc[6][0]) / case.rock["cv1"]
-    y = model.gas_fractions(case.fluid, u[0], u[5], u[1], u[2], u[3], u[4], u[6], 1 - u[6] - u[7])
-    gs = abs(float(sum(y)[0]) - 1.0)
+    more_moles = [0.9 * a for a in acc[:6]] + [acc[6]]
+    more_energy = list(acc[:6]) + [0.9 * acc[6]]
+    off = u.copy()
+    off[3] += 0.2
+    acc_off = model.accumulation(case, model.base_properties(case, off), np.zeros(1))
     for dt in (50.0, 5000.0):
-        r = sim.newton_step(case, u, np.zeros(1), old, dt, sim.NewtonOptions(tol=1e-300))
-        assert r["norm"] == pytest.approx(max(mass, kelvin, gs), rel=1e-12)
+        opts = sim.NewtonOptions(tol=1e-300)
+        assert sim.newton_step(case, u, np.zeros(1), more_moles, dt, opts)["norm"] == pytest.approx(mass, rel=1e-10)
+        assert sim.newton_step(case, u, np.zeros(1), more_energy, dt, opts)["norm"] == pytest.approx(kelvin, rel=1e-10)
+        assert sim.newton_step(case, off, np.zeros(1), acc_off, dt, opts)["norm"] == pytest.approx(0.2, rel=1e-10)
 
 
 def test_newton_iteration_cap_counts_updates():
@@ -305,3 +314,36 @@ def test_oil_saturation_rule_leaves_small_positive_oil_alone():
     du[7, 0] = 0.4995                            # S_o = 1 - 0.2 - 0.7995 = 5e-4 > 0
     un = sim.apply_update(u, du)
     assert un[6, 0] == 0.2 and un[7, 0] == pytest.approx(0.7995, rel=1e-15)
+    # x_LO: small positive values pass, values just above one move half way to one
+    for dx, expect in ((-0.3995, 5e-4), (0.65, 0.7)):
+        du = np.zeros((8, 1))
+        du[1, 0] = dx
+        assert sim.apply_update(u, du)[1, 0] == pytest.approx(expect, rel=1e-12)
+
+
+def test_coupled_newton_iteration_cap_counts_updates():
+    """The bordered Newton loop of a case with a coupled producer: maxit is the
+    number of updates allowed, as for the plain loop."""
+    case = inp.with_coupled_producer(inp.small_box(3, 2, 1), inp.CTRL_BHP, 4.5e6, 4.5e6)
+    u, c = sim.initial_state(case)
+    opts = sim.NewtonOptions(tol=1e-8)
+    _, _, _, its, ok = sim.timestep_coupled(case, u, np.array([4.5e6]), c, 500.0, opts)
+    assert ok and its >= 2
+    opts.maxit = its
+    assert sim.timestep_coupled(case, u, np.array([4.5e6]), c, 500.0, opts)[4]
+    opts.maxit = its - 1
+    assert not sim.timestep_coupled(case, u, np.array([4.5e6]), c, 500.0, opts)[4]
+
+
+def test_dense_solve_reports_no_krylov_iterations():
+    case = inp.small_box(2, 2, 1)
+    st = inp.random_state(case, 3)
+    u0, c0 = sim.initial_state(case)
+    acc_old = model.old_accumulation(case, u0, c0)
+    rp, col, val = model.jacobian(case, st["u"], st["coke"], acc_old, 100.0)
+    rhs = np.random.default_rng(2).standard_normal((case.n, 8))
+    x, its, rel = sim.linear_solve(rp, col, val, rhs, sim.SolveOptions(solver="dense"))
+    assert its == 0 and rel == 0.0
+    A = linalg.bsr_to_dense(rp, col, val)
+    ref = np.linalg.solve(A, rhs.reshape(-1))
+    assert np.linalg.norm(x.reshape(-1) - ref) <= 1e-8 * np.linalg.norm(ref)
