@@ -347,3 +347,61 @@ def test_dense_solve_reports_no_krylov_iterations():
     A = linalg.bsr_to_dense(rp, col, val)
     ref = np.linalg.solve(A, rhs.reshape(-1))
     assert np.linalg.norm(x.reshape(-1) - ref) <= 1e-8 * np.linalg.norm(ref)
+
+
+def test_failed_steps_are_halved_and_counted():
+    """A first tube step of 2000 s does not converge within 25 Newton updates; it is
+    halved until it does (twice, to 500 s), each halving is counted, and max_cuts
+    bounds the number of halvings."""
+    case = inp.tube_case(n_cells=10)
+    opts = sim.NewtonOptions(tol=1e-6)
+    opts.solve.solver = "dense"
+    _, _, dts, st = sim.run(case, 2000.0, 2000.0, 1e9, opts, max_steps=1)
+    assert dts == [500.0] and st["cuts"] == 2 and st["steps"] == 1
+    assert sim.run(case, 2000.0, 2000.0, 1e9, opts, max_cuts=2, max_steps=1)[2] == [500.0]
+    with pytest.raises(RuntimeError):
+        sim.run(case, 2000.0, 2000.0, 1e9, opts, max_cuts=1, max_steps=1)
+
+
+def test_coupled_newton_step_limits_the_bottom_hole_pressure_change():
+    """Under a bottom-hole-pressure control the well equation is linear, so the
+    Newton correction is target - bhp; it is limited to 20 % of bhp either way."""
+    for target, expect in ((8.0e6, 4.8e6), (2.0e6, 3.2e6), (4.2e6, 4.2e6)):
+        case = inp.with_coupled_producer(inp.small_box(3, 2, 1), inp.CTRL_BHP, target, 4.0e6)
+        u, c = sim.initial_state(case)
+        acc = model.old_accumulation(case, u, c)
+        r = sim.newton_step_coupled(case, u, np.array([4.0e6]), c, acc, 100.0, sim.NewtonOptions(tol=1e-300))
+        assert r["dbhp"][0] == pytest.approx(target - 4.0e6, rel=1e-9)
+        assert r["bhp"][0] == pytest.approx(expect, rel=1e-12)
+        assert r["its"] == 0
+
+
+def test_coupled_newton_norm_scales_like_the_plain_one():
+    """With its producer shut (bottom-hole pressure above the reservoir, at its
+    target) a coupled case has the residual of the case without the well, and the
+    bordered Newton step reports the plain step's convergence measure at any dt,
+    whether stored moles or stored energy dominate it."""
+    import dataclasses
+    box = inp.small_box(3, 2, 1)
+    rx = copy.deepcopy(box.reactions)
+    rx["A"] = np.zeros_like(rx["A"])
+    # one layer, no injector, no reactions, no ignition: only the stored amounts change
+    base = dataclasses.replace(box, reactions=rx, ignited=np.zeros(0, dtype=np.int32),
+                               wells=[w for w in box.wells if w.kind == inp.WELL_BHP_PRODUCER])
+    u, c = sim.initial_state(base)
+    bhp = 1.5 * float(np.max(u[0]))
+    coupled = inp.with_coupled_producer(base, inp.CTRL_BHP, bhp, bhp)
+    plain = copy.copy(base)
+    plain.wells = [w for w in base.wells if w.kind != inp.WELL_BHP_PRODUCER]
+    acc = model.accumulation(base, model.base_properties(base, u), c)
+    variants = ([0.5 * a for a in acc[:6]] + [acc[6]], list(acc[:6]) + [0.9 * acc[6]])
+    opts = sim.NewtonOptions(tol=1e-300)
+    for old in variants:
+        for dt in (50.0, 5000.0):
+            r0 = sim.newton_step(plain, u, c, old, dt, opts)
+            n1 = sim.newton_step_coupled(coupled, u, np.array([bhp]), c, old, dt, opts)["norm"]
+            assert n1 == pytest.approx(r0["norm"], rel=1e-12)
+            e = r0["norms"]
+            assert r0["norm"] == pytest.approx(max(e[0], e[1]) * dt, rel=1e-12)   # not the gas constraint
+    big = sim.newton_step_coupled(coupled, u, np.array([bhp]), c, acc, 50.0, sim.NewtonOptions(tol=1e300))
+    assert big["converged"] and big["its"] == 0
