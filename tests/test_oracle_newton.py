@@ -202,6 +202,7 @@ def test_step_size_controller():
         return u1
 
     assert sim.next_dt(10.0, u0, moved(10.0, 0.05), 1e9) == pytest.approx(20.0)   # both small: x2
+    assert sim.next_dt(10.0, u0, moved(2.0, 0.01), 1e9) == pytest.approx(20.0)    # growth capped at x2
     assert sim.next_dt(10.0, u0, moved(16.0, 0.05), 1e9) == pytest.approx(12.5)   # 20 / 16
     assert sim.next_dt(10.0, u0, moved(5.0, 0.16), 1e9) == pytest.approx(12.5)    # 0.2 / 0.16
     assert sim.next_dt(10.0, u0, moved(100.0, 0.0), 1e9) == pytest.approx(5.0)    # floor 0.5
