@@ -286,6 +286,8 @@ def test_newton_norm_is_relative_mass_kelvin_and_gas_constraint():
         assert sim.newton_step(case, u, np.zeros(1), more_moles, dt, opts)["norm"] == pytest.approx(mass, rel=1e-10)
         assert sim.newton_step(case, u, np.zeros(1), more_energy, dt, opts)["norm"] == pytest.approx(kelvin, rel=1e-10)
         assert sim.newton_step(case, off, np.zeros(1), acc_off, dt, opts)["norm"] == pytest.approx(0.2, rel=1e-10)
+    done = sim.newton_step(case, u, np.zeros(1), acc, 50.0, sim.NewtonOptions(tol=1e300))
+    assert done["converged"] and done["its"] == 0
 
 
 def test_newton_iteration_cap_counts_updates():
