@@ -1,16 +1,19 @@
 """Benchmark: Newton linearise-and-solve steps per second of the in-situ-combustion
-model on the 60x60x20 field workload (72,000 cells, 8 unknowns per cell).
+model on the large workload (200x200x50 = 2,000,000 cells, 16M unknowns, 3-facies
+permeability, 5-spot wells), with the SpMV and ILU(0)-apply bandwidth against the
+HBM roof and the FP64 against the mixed-precision time to a 1e-6 relative linear
+residual.
 
 One step = the whole hot path on one batch: restore the iterate, property
 evaluation + residual/Jacobian assembly, convergence norms, Gauss-Jordan
 decoupling, block ILU(0) factorisation, GMRES(30) to the relative tolerance,
 safeguarded update. Inputs are resident in HBM for ``value``; ``e2e`` goes
-through the C ABI with host buffers (state in, state out) every step. The
-line also carries the same step with the FP32 preconditioner (``mixed``), with
-an FP32 inner GMRES inside the flexible FP64 GMRES (``mixed_fgmres``, with the
-FP32 SpMV's roofline), the discrete adjoint of a 40x40x10 time loop
-(``adjoint``) and the step with the CPR-PF preconditioner (``cpr``, FP64 and
-mixed).
+through the C ABI with host buffers (state in, state out) every step. The line
+also carries the same step with the FP32 preconditioner (``mixed``), with an
+FP32 inner GMRES inside the flexible FP64 GMRES (``mixed_fgmres``), with the
+CPR-PF preconditioner (``cpr``), the 100x100x30 and 60x60x20 workloads
+(``workloads``), the discrete adjoint of a 40x40x10 time loop (``adjoint``) and
+the oracle's timing on the host (``cpu_baseline``).
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl isc|reference]
 Under torchrun each rank runs an independent replica (the path has no
@@ -32,12 +35,15 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Newton steps/s"
 UNIT = "Newton steps/s"
-FIELD = dict(nx=60, ny=60, nz=20)
-# algorithmic bytes per unit: one FP64 8x8 block = 512 B + 4 B column index
+WORKLOADS = {"field": 2, "mixed": 3, "large": 5}
+# algorithmic bytes: one FP64 8x8 block = 512 B + its 4-byte column index; FP32 256 + 4
 BLOCK_BYTES = 516
+BLOCK_BYTES32 = 260
+SOLVE_CLASSES = ("spmv", "spmv32", "prec_apply", "blas1", "ilu_factor")
+INNER_ITS = 10
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -46,14 +52,16 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the discrete-adjoint measurement")
     ap.add_argument("--no-extras", action="store_true",
-                    help="time only the headline step (no mixed, CPR-PF, adjoint or end-to-end legs); for profiling")
+                    help="time only the headline step (no other legs or workloads); for profiling")
     ap.add_argument("--grid", default=None,
-                    help="NXxNYxNZ: run the same field recipe on a smaller grid (profiling captures)")
+                    help="NXxNYxNZ: run the workload's recipe on another grid (profiling captures)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "mixed_fgmres"],
                     help="precision of the timed step's linear solve (the headline is fp64)")
-    ap.add_argument("--workload", default="field", choices=["field", "mixed", "large"],
-                    help="field: 60x60x20 (the headline); mixed: 100x100x30; large: 200x200x50, 3 facies, 5-spot")
-    return ap.parse_args()
+    ap.add_argument("--prec", default="bilu0", choices=["bilu0", "cpr"],
+                    help="preconditioner of the timed step (the headline is block ILU(0))")
+    ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS),
+                    help="large: 200x200x50 (the headline); mixed: 100x100x30; field: 60x60x20")
+    return ap.parse_args(argv)
 
 
 def max_over_ranks(x, device="cpu"):
@@ -132,12 +140,14 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def field_case(grid=None, workload="field"):
+def workload_case(workload="large", grid=None):
     import isc_inputs as inp
     if grid:
         nx, ny, nz = (int(v) for v in grid.lower().split("x"))
+        if workload == "large":
+            return inp.large_case(nx, ny, nz)
         return inp.field_case(nx, ny, nz, 0, 1, f"field {nx}x{ny}x{nz}", 30 * inp.DAY, 40)
-    return inp.config({"field": 2, "mixed": 3, "large": 5}[workload])
+    return inp.config(WORKLOADS[workload])
 
 
 def l2_bytes():
@@ -148,19 +158,222 @@ def l2_bytes():
         return 126 * 2**20
 
 
-def workload_config(case, dt, extra, nnzb=None):
-    nnzb = nnzb if nnzb is not None else case.n * 7
-    c = {"workload": f"{case.name} ({case.n} cells, 8 unknowns/cell), first Newton step of "
-                     f"the first time step (dt {dt:.0f} s) from the ignited initial state",
-         "solver": "GMRES(30), block ILU(0), Gauss-Jordan decoupling, FP64, tol_lin 1e-6",
-         "l2": f"inputs larger than L2: the FP64 Jacobian ({nnzb * 512 / 1e6:.0f} MB) and staged properties "
-               f"({case.n * 16 * 9 * 8 / 1e6:.0f} MB) exceed the {l2_bytes() / 2**20:.0f} MiB L2"}
-    c.update(extra)
-    return c
+def workload_config(case, world, precision="fp64", prec="bilu0"):
+    """The `config` object of the line: the workload and solver only (measured
+    numbers go elsewhere), identical for the library and the reference arm."""
+    nnzb = case.n + 2 * ((case.nx - 1) * case.ny * case.nz + case.nx * (case.ny - 1) * case.nz
+                         + case.nx * case.ny * (case.nz - 1))
+    pname = {"bilu0": "block ILU(0)", "cpr": "CPR-PF"}[prec]
+    return {"workload": f"{case.name} ({case.n} cells, 8 unknowns/cell), first Newton step of the first time step "
+                        f"(dt {case.dt0:.0f} s) from the ignited initial state",
+            "solver": f"GMRES(30), {pname}, Gauss-Jordan decoupling, tol_lin 1e-6",
+            "precision": precision,
+            "l2": f"inputs larger than L2, no flush: the FP64 Jacobian ({nnzb * 512 / 1e6:.0f} MB) and staged "
+                  f"properties ({case.n * 16 * 9 * 8 / 1e6:.0f} MB) exceed the {l2_bytes() / 2**20:.0f} MiB L2",
+            "parallelism": f"replicas x{world}"}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def hbm_peak():
+    return measured_peaks().get("hbm_gbs", 6800.0)
+
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one call of a kernel
+# class, per cell, from one ncu capture of the current kernels on a smaller grid
+# of the same recipe; a call's traffic grows with the cells it sweeps, so the
+# full-size figure is this times the workload's cells. Keyed by (class, precision).
+MEASURED_TRAFFIC = {
+    ("prec_apply", "fp64"): (313.40e6 / 72000, "field 60x60x20", "profiles/k_ilu_sweeps_field_60x60x20.md"),
+}
+
+
+def class_gbs(stats, cls, byts):
+    """Algorithmic bytes per call of one kernel class over its mean CUDA-event time."""
+    hbm = hbm_peak()
+    s = stats.get(cls, {"calls": 0, "ms": 0.0})
+    if not s["calls"] or s["ms"] <= 0:
+        return None
+    ms = s["ms"] / s["calls"]
+    gbs = byts / (ms * 1e-3) / 1e9
+    return {"ms_per_call": ms, "bytes_per_call": byts, "gbs": gbs, "hbm_frac": gbs / hbm}
+
+
+def spmv_bytes(n, nnzb, fp32=False):
+    """Off-diagonal blocks with their column indices (the decoupled diagonal is
+    the identity and is not read), x for the neighbours and the diagonal, y."""
+    if fp32:
+        return (nnzb - n) * BLOCK_BYTES32 + 3 * n * 32
+    return (nnzb - n) * BLOCK_BYTES + 3 * n * 64
+
+
+def ilu_apply_bytes(n, nnzb, fp32=False):
+    """Block ILU(0) apply, forward then backward substitution: every off-diagonal
+    block with its column index once, the N inverted diagonal blocks once, and
+    four vector passes (r in, the intermediate written and read back, z out;
+    FP32 vectors inside the FP32 sweeps, FP64 r and z at the boundary)."""
+    if fp32:
+        return (nnzb - n) * BLOCK_BYTES32 + n * 256 + 2 * n * 64 + 2 * n * 32
+    return (nnzb - n) * BLOCK_BYTES + n * 512 + 4 * n * 64
+
+
+def ilu_apply_flops(n, nnzb):
+    """Two flops per multiply-add of every off-diagonal block and one diagonal
+    inverse per cell."""
+    return 2 * 64 * (nnzb - n) + 2 * 64 * n
+
+
+def hbm_table(stats64, stats_mixed, stats_fg, case, nnzb):
+    """SpMV and preconditioner-apply GB/s against the measured HBM bandwidth (the
+    metric's second part): FP64 from the headline step, the FP32 sweeps from the
+    `mixed` leg, the FP32 SpMV from the `mixed_fgmres` leg."""
+    n = case.n
+    out = {"spmv_fp64": class_gbs(stats64, "spmv", spmv_bytes(n, nnzb)),
+           "ilu_apply_fp64": class_gbs(stats64, "prec_apply", ilu_apply_bytes(n, nnzb))}
+    if stats_mixed is not None:
+        out["ilu_apply_fp32"] = class_gbs(stats_mixed, "prec_apply", ilu_apply_bytes(n, nnzb, fp32=True))
+    if stats_fg is not None:
+        out["spmv_fp32"] = class_gbs(stats_fg, "spmv32", spmv_bytes(n, nnzb, fp32=True))
+    return out
+
+
+def roofline(dom, stats, case, nnzb, fp64_gflops, precision="fp64"):
+    """Algorithmic bytes (or flops) per call of the dominant kernel class over its
+    average CUDA-event duration, against the measured HBM copy bandwidth or the
+    FP64 FMA rate measured at start-up (whichever bounds the class)."""
+    n = case.n
+    hbm = hbm_peak()
+    s = stats[dom]
+    calls = max(1, s["calls"])
+    ms = s["ms"] / calls
+    fp32 = precision != "fp64"
+    if dom == "spmv":
+        byts, flops = spmv_bytes(n, nnzb), 2 * 64 * (nnzb - n)
+    elif dom == "prec_apply":
+        byts, flops = ilu_apply_bytes(n, nnzb, fp32), ilu_apply_flops(n, nnzb)
+    elif dom == "ilu_factor":
+        # per cell three lower and three upper blocks read, D^-1 written; three
+        # block products A_ik (D_k^-1 A_ki) and one 8x8 inversion
+        byts = (nnzb - n) * BLOCK_BYTES + 2 * n * 512
+        flops = n * (3 * 2 * 2 * 512 + 2 * 512)
+    elif dom == "gj":
+        byts = 2 * (nnzb * BLOCK_BYTES + n * 64)
+        flops = n * 8 * 7 * 2 * 57
+    elif dom in ("props", "flux"):
+        byts, flops = nnzb * 512 + n * (8 + 8 + 7 + 3) * 8, None
+    else:
+        byts, flops = 0, None
+    ach_gbs = byts / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+    out = {"kernel": dom, "calls": calls, "ms_per_call": ms, "bytes_per_call": byts, "flops_per_call": flops}
+    if flops is not None and ms > 0 and not fp32 and flops / max(byts, 1) > fp64_gflops / hbm:
+        # FP64 above the ridge (measured FP64 rate / HBM bandwidth): the FP64 pipe bounds it
+        ach = flops / (ms * 1e-3) / 1e9
+        out.update(bound="alu", achieved=ach, peak=fp64_gflops, unit="GFLOP/s", frac=ach / fp64_gflops,
+                   peak_source="FP64 FMA rate measured at start-up (isc_measure_fma_rates)",
+                   hbm_achieved_gbs=ach_gbs, hbm_frac=ach_gbs / hbm)
+    else:
+        out.update(bound="hbm", achieved=ach_gbs, peak=hbm, unit="GB/s", frac=ach_gbs / hbm,
+                   peak_source="MEASURED_PEAKS.json hbm_gbs")
+    m = MEASURED_TRAFFIC.get((dom, precision))
+    out["traffic"] = m[0] * n if m else None
+    if m:
+        out["traffic_source"] = f"{m[2]} (captured on {m[1]}, scaled per cell to {case.n} cells)"
+    return out
+
+
+def spmv32_roofline(stats, case, nnzb):
+    """The inner solve's FP32 SpMV against the HBM roof."""
+    hbm = hbm_peak()
+    s = stats["spmv32"]
+    calls = max(1, s["calls"])
+    ms = s["ms"] / calls
+    byts = spmv_bytes(case.n, nnzb, fp32=True)
+    ach = byts / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+    return {"kernel": "k_spmv<float>", "bound": "hbm", "calls": calls, "ms_per_call": ms, "bytes_per_call": byts,
+            "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
+
+
+class Bench:
+    """One libisc handle on one workload, its resident starting iterate and the
+    timed Newton step."""
+
+    def __init__(self, case, **opt):
+        import torch
+        from paper_1811_11992_gb300 import isc
+        self.case = case
+        self.g = isc.Simulator(case, profile=1, inner_its=INNER_ITS, **opt)
+        self.g.init_equilibrium()
+        n = case.n
+        self.u0 = torch.empty(8 * n, dtype=torch.float64, device="cuda")
+        self.c0 = torch.empty(n, dtype=torch.float64, device="cuda")
+        self.g.get_state_device(self.u0.data_ptr(), self.c0.data_ptr())
+        torch.cuda.synchronize()
+
+    def step(self):
+        self.g.set_state_device(self.u0.data_ptr(), self.c0.data_ptr())
+        return self.g.newton_step(self.case.dt0)
+
+    def leg(self, steps, warmup, **opt):
+        """Time `steps` Newton steps with the options changed (restored after)."""
+        import torch
+        saved = {k: getattr(self.g.options, k) for k in opt}
+        if opt:
+            self.g.set_options(**opt)
+        for _ in range(warmup):
+            self.step()
+        torch.cuda.synchronize()
+        self.g.reset_stats()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        infos = [self.step() for _ in range(steps)]
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        st = self.g.stats()
+        if opt:
+            self.g.set_options(**saved)
+        return ms, st, infos
+
+    def close(self):
+        self.g.close()
+
+
+def leg_summary(ms, st, infos, steps, solve_ref_ms=None):
+    solve = sum(st[k]["ms"] for k in SOLVE_CLASSES) / steps
+    out = {"value": 1e3 / ms, "unit": UNIT, "ms_per_step": ms,
+           "krylov_iterations_per_step": statistics.median([i.krylov_iterations for i in infos]),
+           "rel_residual": max(i.krylov_rel_residual for i in infos),
+           "solve_ms": solve,
+           "prec_apply_ms_per_call": st["prec_apply"]["ms"] / max(1, st["prec_apply"]["calls"])}
+    if solve_ref_ms is not None:
+        out["solve_ms_fp64"] = solve_ref_ms
+        out["solve_speedup_vs_fp64"] = solve_ref_ms / solve if solve > 0 else None
+    return out
+
+
+def workload_block(cfg, steps, warmup, legs):
+    """Another workload: FP64 and the listed precision legs of its Newton step."""
+    import isc_inputs as inp
+    b = Bench(inp.config(cfg))
+    ms, st, infos = b.leg(steps, warmup)
+    out = {"workload": f"{b.case.name} ({b.case.n} cells)", "fp64": leg_summary(ms, st, infos, steps)}
+    ref = out["fp64"]["solve_ms"]
+    for p in legs:
+        ms, stp, infos = b.leg(steps, warmup, precision=p)
+        out[p] = leg_summary(ms, stp, infos, steps, ref)
+    out["hbm"] = hbm_table(st, None, None, b.case, b.g.nnzb)
+    b.close()
+    return out
 
 
 def run_isc(args):
-    import numpy as np
     import torch
 
     rank, world, local = dist_env()
@@ -170,23 +383,13 @@ def run_isc(args):
     torch.cuda.set_device(local)
     from paper_1811_11992_gb300 import build, isc
     build.build()
-    case = field_case(args.grid, args.workload)
-    dt = case.dt0
-    g = isc.Simulator(case, profile=1, precision=args.precision, inner_its=INNER_ITS)
-    g.init_equilibrium()
+    fp64_gflops, fp32_gflops = isc.measure_fma_rates()
+    case = workload_case(args.workload, args.grid)
+    b = Bench(case, precision=args.precision, prec=args.prec)
+    g = b.g
     n = case.n
-    # resident snapshot of the starting iterate (torch owns the buffers)
-    u0 = torch.empty(8 * n, dtype=torch.float64, device="cuda")
-    c0 = torch.empty(n, dtype=torch.float64, device="cuda")
-    g.get_state_device(u0.data_ptr(), c0.data_ptr())
-    torch.cuda.synchronize()
-
-    def step():
-        g.set_state_device(u0.data_ptr(), c0.data_ptr())
-        return g.newton_step(dt)
-
     for _ in range(args.warmup):
-        step()
+        b.step()
     torch.cuda.synchronize()
     g.reset_stats()
     infos = []
@@ -201,7 +404,7 @@ def run_isc(args):
     t0 = time.perf_counter()
     ev0.record()
     for _ in range(args.steps):
-        infos.append(step())
+        infos.append(b.step())
     ev1.record()
     torch.cuda.synchronize()
     if world > 1:
@@ -213,116 +416,93 @@ def run_isc(args):
     ms_total = max_over_ranks(max(ms_dev, wall * 1e3), "cuda")
     value = job_throughput(world, args.steps, ms_total)
     kry = [i.krylov_iterations for i in infos]
+    headline = leg_summary(ms_total / args.steps, stats, infos, args.steps)
     e2e = mixed = mixed_fgmres = cpr_block = None
     mst = fst = None
+    leg_steps = max(3, args.steps // 4)
+    leg_warm = max(1, min(2, args.warmup))
     if not args.no_extras:
-        # end-to-end through the C ABI with host buffers
-        uh, ch = g.get_state()
-        u_host = torch.from_numpy(uh.reshape(-1).copy()).pin_memory().numpy()
-        c_host = torch.from_numpy(ch.copy()).pin_memory().numpy()
-        g.set_state_device(u0.data_ptr(), c0.data_ptr())
+        # end-to-end through the C ABI with host buffers: the state in from pinned
+        # host memory, the Newton step, the state out
+        g.set_state_device(b.u0.data_ptr(), b.c0.data_ptr())
         u_start, c_start = g.get_state()
         u_start_p = torch.from_numpy(u_start.reshape(-1).copy()).pin_memory().numpy()
         c_start_p = torch.from_numpy(c_start.copy()).pin_memory().numpy()
-        for _ in range(max(1, args.warmup // 2)):
+        for _ in range(leg_warm):
             g.set_state(u_start_p.reshape(8, n), c_start_p)
-            g.newton_step(dt)
+            g.newton_step(case.dt0)
             g.get_state()
-        e2e_steps = max(3, args.steps // 2)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for _ in range(e2e_steps):
+        for _ in range(leg_steps):
             g.set_state(u_start_p.reshape(8, n), c_start_p)
-            g.newton_step(dt)
-            u_out, c_out = g.get_state()
+            g.newton_step(case.dt0)
+            g.get_state()
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
-        e2e_val = job_throughput(world, e2e_steps, max_over_ranks(e2e_s * 1e3, "cuda"))
+        e2e_val = job_throughput(world, leg_steps, max_over_ranks(e2e_s * 1e3, "cuda"))
         io_bytes = 9 * n * 8
-        e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes}
-        solve_fp64 = sum(stats[k]["ms"] for k in SOLVE_CLASSES) / args.steps
-
-        def precision_leg(precision, **extra):
-            """The headline step again under another precision of the linear solve."""
-            g.set_options(precision=precision, **extra)
-            for _ in range(max(1, args.warmup)):
-                step()
-            torch.cuda.synchronize()
-            g.reset_stats()
-            ev0.record()
-            minfo = [step() for _ in range(args.steps)]
-            ev1.record()
-            torch.cuda.synchronize()
-            ms_leg = ev0.elapsed_time(ev1) / args.steps
-            mstats = g.stats()
-            g.set_options(precision="fp64")
-            solve_leg = sum(mstats[k]["ms"] for k in SOLVE_CLASSES) / args.steps
-            return mstats, {
-                "value": 1e3 / ms_leg, "unit": UNIT, "ms_per_step": ms_leg,
-                "krylov_iterations_per_step": statistics.median([i.krylov_iterations for i in minfo]),
-                "rel_residual": max(i.krylov_rel_residual for i in minfo),
-                "prec_apply_ms_per_call": mstats["prec_apply"]["ms"] / max(1, mstats["prec_apply"]["calls"]),
-                "solve_ms_fp64": solve_fp64, "solve_ms": solve_leg,
-                "solve_speedup_vs_fp64": solve_fp64 / solve_leg if solve_leg > 0 else None}
-
-        # mixed precision on the same step: FP32 ILU(0) factors and sweeps inside the FP64 GMRES
-        mst, mixed = precision_leg("mixed")
-        # FP32 inner GMRES (FP32 SpMV, Gram-Schmidt and ILU(0)) inside the flexible FP64 GMRES
-        fst, mixed_fgmres = precision_leg("mixed_fgmres", inner_its=INNER_ITS)
-        mixed_fgmres["inner_its"] = INNER_ITS
-        mixed_fgmres["inner_iterations_per_step"] = mixed_fgmres["krylov_iterations_per_step"] * INNER_ITS
-        mixed_fgmres["roofline_spmv32"] = spmv32_roofline(fst, case, g.nnzb)
-        # CPR-PF (the paper's Example-2 preconditioner) on the same step, FP64 and mixed
-        cpr_block = {}
-        for precision in ("fp64", "mixed"):
-            g.set_options(prec="cpr", precision=precision)
-            for _ in range(max(1, args.warmup)):
-                step()
-            torch.cuda.synchronize()
-            g.reset_stats()
-            ev0.record()
-            cinfo = [step() for _ in range(args.steps)]
-            ev1.record()
-            torch.cuda.synchronize()
-            ms_c = ev0.elapsed_time(ev1) / args.steps
-            cst = g.stats()
-            cpr_block[precision] = {
-                "value": 1e3 / ms_c, "unit": UNIT, "ms_per_step": ms_c,
-                "krylov_iterations_per_step": statistics.median([i.krylov_iterations for i in cinfo]),
-                "rel_residual": max(i.krylov_rel_residual for i in cinfo),
-                "pressure_stage_ms_per_step": cst["cpr"]["ms"] / args.steps,
-                "ilu_stage_ms_per_step": cst["prec_apply"]["ms"] / args.steps,
-                "speedup_vs_ilu0_fp64": ms_total / args.steps / ms_c}
-        g.set_options(prec="bilu0", precision="fp64")
-    # roofline of the dominant kernel class
-    launches = sum(v["launches"] for v in stats.values())
+        e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes,
+               "steps": leg_steps}
+        if args.precision == "fp64" and args.prec == "bilu0":
+            solve_fp64 = headline["solve_ms"]
+            # FP32 ILU(0) factors and sweeps inside the FP64 GMRES
+            ms, mst, mi = b.leg(leg_steps, leg_warm, precision="mixed")
+            mixed = leg_summary(ms, mst, mi, leg_steps, solve_fp64)
+            # FP32 inner GMRES (FP32 SpMV, Gram-Schmidt and ILU(0)) inside the flexible FP64 GMRES
+            ms, fst, fi = b.leg(leg_steps, leg_warm, precision="mixed_fgmres")
+            mixed_fgmres = leg_summary(ms, fst, fi, leg_steps, solve_fp64)
+            mixed_fgmres["inner_its"] = INNER_ITS
+            mixed_fgmres["roofline_spmv32"] = spmv32_roofline(fst, case, g.nnzb)
+            # CPR-PF (the paper's Example-2 preconditioner) on the same step
+            cpr_block = {}
+            for p in ("fp64", "mixed", "mixed_fgmres"):
+                ms, cst, ci = b.leg(leg_steps, leg_warm, prec="cpr", precision=p)
+                cpr_block[p] = leg_summary(ms, cst, ci, leg_steps, solve_fp64)
+                cpr_block[p]["pressure_stage_ms_per_step"] = cst["cpr"]["ms"] / leg_steps
+                cpr_block[p]["speedup_vs_ilu0_fp64"] = (ms_total / args.steps) / ms
     dom = max(stats, key=lambda k: stats[k]["ms"])
-    roof = roofline(dom, stats, g, case, kry, args.precision)
+    roof = roofline(dom, stats, case, g.nnzb, fp64_gflops, args.precision)
+    hbm = hbm_table(stats, mst, fst, case, g.nnzb)
+    launches = sum(v["launches"] for v in stats.values())
+    nnzb = g.nnzb
+    b.close()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
         "data": "synthetic",
-        "config": workload_config(case, dt, {"parallelism": f"replicas x{world}",
-                                             "krylov_iterations_per_step": statistics.median(kry) if kry else None,
-                                             "precision": args.precision},
-                                  g.nnzb),
+        "config": workload_config(case, world, args.precision, args.prec),
+        "krylov_iterations_per_step": statistics.median(kry) if kry else None,
+        "rel_residual": headline["rel_residual"],
         "e2e": e2e,
         "gpu_launches": launches,
         "kernel_ms": {k: round(v["ms"], 3) for k, v in stats.items()},
         "kernel_launches": {k: v["launches"] for k, v in stats.items()},
         "roofline": roof,
-        "hbm": hbm_table(stats, mst, fst, case, g.nnzb),
+        "alu_peaks_gflops": {"fp64": fp64_gflops, "fp32": fp32_gflops,
+                             "how": "isc_measure_fma_rates: register FMA chains on every SM, best of 5"},
+        "hbm": hbm,
         "clocks": clocks,
         "mixed": mixed,
         "mixed_fgmres": mixed_fgmres,
         "cpr": cpr_block,
+        "time_to_1e-6": None if mixed is None else {
+            "fp64_solve_ms": headline["solve_ms"], "mixed_solve_ms": mixed["solve_ms"],
+            "mixed_fgmres_solve_ms": mixed_fgmres["solve_ms"],
+            "fp64_step_ms": headline["ms_per_step"], "mixed_step_ms": mixed["ms_per_step"],
+            "mixed_fgmres_step_ms": mixed_fgmres["ms_per_step"],
+            "rel_residuals": [headline["rel_residual"], mixed["rel_residual"], mixed_fgmres["rel_residual"]]},
     }
-    if not args.no_adjoint and not args.no_extras and args.grid is None and args.workload == "field":
+    if not args.no_extras and args.grid is None and args.workload == "large":
+        line["workloads"] = {
+            "mixed_100x100x30": workload_block(3, leg_steps, leg_warm, ("mixed", "mixed_fgmres")),
+            "field_60x60x20": workload_block(2, leg_steps, leg_warm, ()),
+        }
+    if not args.no_adjoint and not args.no_extras and args.grid is None:
         line["adjoint"] = adjoint_block()
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "field" and args.grid is None:
-        line["cpu_baseline"] = cpu_baseline(max_seconds=30.0)
-    g.close()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.grid is None:
+        line["cpu_baseline"] = cpu_baseline(case, statistics.median(kry) if kry else 0, nnzb)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
@@ -364,174 +544,121 @@ def adjoint_block():
             "kernel_ms": {k: round(v["ms"], 3) for k, v in st.items()}}
 
 
-def measured_peaks():
-    try:
-        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        return {}
-
-
-FP64_PEAK_GFLOPS = 1200.0   # measured DFMA throughput on this GB300
-# dram__bytes_read.sum + dram__bytes_write.sum per call (forward + backward FP64 sweep)
-MEASURED_TRAFFIC = {("prec_apply", 60, 60, 20): (313.40e6, "profiles/k_ilu_sweeps_field_60x60x20.md")}
-
-
-SOLVE_CLASSES = ("spmv", "spmv32", "prec_apply", "blas1", "ilu_factor")
-INNER_ITS = 10
-
-
-def spmv32_roofline(stats, case, nnzb):
-    """The inner solve's FP32 SpMV: FP32 off-diagonal blocks and their column
-    indices, x read twice (neighbours and the unit diagonal) and y written."""
-    peaks = measured_peaks()
-    hbm = peaks.get("hbm_gbs", 6800.0)
-    s = stats["spmv32"]
-    calls = max(1, s["calls"])
-    ms = s["ms"] / calls
-    byts = (nnzb - case.n) * (256 + 4) + 3 * case.n * 32
-    ach = byts / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
-    return {"kernel": "k_spmv<float>", "bound": "hbm", "calls": calls, "ms_per_call": ms, "bytes_per_call": byts,
-            "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
-
-
-def class_gbs(stats, cls, byts):
-    """Algorithmic bytes per call of one kernel class over its mean CUDA-event time."""
-    hbm = measured_peaks().get("hbm_gbs", 6800.0)
-    s = stats.get(cls, {"calls": 0, "ms": 0.0})
-    if not s["calls"] or s["ms"] <= 0:
-        return None
-    ms = s["ms"] / s["calls"]
-    gbs = byts / (ms * 1e-3) / 1e9
-    return {"ms_per_call": ms, "bytes_per_call": byts, "gbs": gbs, "hbm_frac": gbs / hbm}
-
-
-def hbm_table(stats64, stats_mixed, stats_fg, case, nnzb):
-    """SpMV and preconditioner-apply GB/s against the measured HBM bandwidth (the
-    metric's second part): FP64 from the headline step, the FP32 sweeps from the
-    `mixed` leg, the FP32 SpMV from the `mixed_fgmres` leg."""
-    n, off = case.n, nnzb - case.n
-    out = {"spmv_fp64": class_gbs(stats64, "spmv", off * BLOCK_BYTES + 3 * n * 64),
-           "ilu_apply_fp64": class_gbs(stats64, "prec_apply", off * BLOCK_BYTES + 2 * n * 512 + 4 * n * 64)}
-    if stats_mixed is not None:
-        out["ilu_apply_fp32"] = class_gbs(stats_mixed, "prec_apply", off * 260 + 2 * n * 256 + 2 * n * 64 + 2 * n * 32)
-    if stats_fg is not None:
-        out["spmv_fp32"] = class_gbs(stats_fg, "spmv32", off * 260 + 3 * n * 32)
-    return out
-
-
-def roofline(dom, stats, g, case, kry, precision="fp64"):
-    """Algorithmic bytes (or flops) per call of the dominant kernel class over its
-    average CUDA-event duration."""
-    n, nnzb = case.n, g.nnzb
-    peaks = measured_peaks()
-    hbm = peaks.get("hbm_gbs", 6800.0)
-    s = stats[dom]
-    calls = max(1, s["calls"])
-    ms = s["ms"] / calls
-    nlev = case.nx + case.ny + case.nz - 2
-    nlow = nnzb - n  # off-diagonal blocks (both triangles)
-    if dom == "spmv":
-        byts = (nnzb - n) * BLOCK_BYTES + 3 * n * 64
-        flops = 2 * 64 * (nnzb - n)
-    elif dom == "prec_apply":
-        byts = nlow * BLOCK_BYTES + 2 * n * 512 + 4 * n * 64
-        flops = 2 * 64 * (nlow + 2 * n)
-    elif dom == "ilu_factor":
-        byts = (nlow // 2) * 2 * BLOCK_BYTES + 2 * n * 512
-        flops = (nlow // 2) * 2 * 2 * 512 + n * 2 * 512 * 2
-    elif dom == "gj":
-        byts = 2 * (nnzb * BLOCK_BYTES + n * 64)
-        flops = n * 8 * 7 * 2 * 57
-    elif dom in ("props", "flux"):
-        byts = nnzb * 512 + n * (8 + 8 + 7 + 3) * 8
-        flops = None
-    else:
-        byts = 0
-        flops = None
-    ach_gbs = byts / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
-    out = {"kernel": dom, "calls": calls, "ms_per_call": ms, "bytes_per_call": byts}
-    if flops is not None and ms > 0:
-        ach_tf = flops / (ms * 1e-3) / 1e9
-        # FP64 kernels on GB300 sit above the FP64 ridge (1.2 TFLOP/s / 6.8 TB/s = 0.18 flop/B)
-        if flops / max(byts, 1) > FP64_PEAK_GFLOPS / hbm:
-            out.update(bound="alu", achieved=ach_tf, peak=FP64_PEAK_GFLOPS, unit="GFLOP/s",
-                       frac=ach_tf / FP64_PEAK_GFLOPS, peak_source="measured FP64 DFMA probe",
-                       hbm_achieved_gbs=ach_gbs, hbm_frac=ach_gbs / hbm)
-        else:
-            out.update(bound="hbm", achieved=ach_gbs, peak=hbm, unit="GB/s", frac=ach_gbs / hbm,
-                       peak_source="MEASURED_PEAKS.json hbm_gbs")
-    else:
-        out.update(bound="hbm", achieved=ach_gbs, peak=hbm, unit="GB/s", frac=ach_gbs / hbm if hbm else None,
-                   peak_source="MEASURED_PEAKS.json hbm_gbs")
-    # DRAM bytes per call from one ncu capture of the current kernels on this grid (FP64 solve)
-    measured = MEASURED_TRAFFIC.get((dom, case.nx, case.ny, case.nz)) if precision == "fp64" else None
-    out["traffic"] = measured[0] if measured else None
-    if precision != "fp64":
-        out["note"] = "bytes and flops of the FP64 operands; this step ran its preconditioner in FP32"
-    if measured:
-        out["traffic_source"] = measured[1]
-    return out
-
-
 # ------------------------------------------------------------------ oracle
-SAMPLE = dict(nx=30, ny=30, nz=10)
+# Bounded samples of the large workload's recipe (3 facies, 5-spot, same
+# generator): the cpu_baseline breakdown (about 15 s of host work) and the
+# reference arm's per-step sample (about 5 s, so that 25 steps end within a few
+# minutes).
+SAMPLE = (30, 30, 10)
+REF_SAMPLE = (20, 20, 10)
 
 
-def oracle_sample_step():
-    """One oracle Newton step on a 30x30x10 block cut to the field workload's
-    recipe (same generator, 1/8 of the cells)."""
+def oracle_sample_case(dims=SAMPLE):
     import isc_inputs as inp
+    return inp.large_case(*dims)
+
+
+def oracle_sample_step(dims=REF_SAMPLE):
+    """One oracle Newton step (as it stands) on a sample. Returns (s, cells, its)."""
     from oracle import model, sim
-    case = inp.field_case(SAMPLE["nx"], SAMPLE["ny"], SAMPLE["nz"], 0, 1, "field sample 30x30x10", 30 * inp.DAY, 40)
+    case = oracle_sample_case(dims)
     u, c = sim.initial_state(case)
     acc_old = model.old_accumulation(case, u, c)
     opts = sim.NewtonOptions(tol=0.0)
     opts.solve.rtol = 1e-6
     t0 = time.perf_counter()
     r = sim.newton_step(case, u, c, acc_old, case.dt0, opts)
-    return time.perf_counter() - t0, case.n, r
+    return time.perf_counter() - t0, case.n, r["its"]
 
 
-def cpu_baseline(max_seconds=30.0):
-    full = FIELD["nx"] * FIELD["ny"] * FIELD["nz"]
-    secs = []
-    t_start = time.perf_counter()
-    while True:
-        dt, ncell, _ = oracle_sample_step()
-        secs.append(dt)
-        if time.perf_counter() - t_start + dt > max_seconds or len(secs) >= 3:
-            break
-    per = statistics.median(secs)
-    scale = ncell / full
-    return {"value": scale / per, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{len(secs)} oracle Newton step(s) on a 30x30x10 block of the field recipe "
-                      f"({ncell} cells, {per:.2f} s each), scaled by cell count to the 72,000-cell workload"}
+def oracle_breakdown():
+    """The oracle's Newton step on the sample, part by part: residual and
+    Jacobian, Gauss-Jordan, ILU(0) set-up, GMRES(30) to 1e-6 (and its
+    iterations), plus 10 SpMVs and 10 ILU(0) applies on the decoupled matrix."""
+    import numpy as np
+    from oracle import linalg, model, sim
+    case = oracle_sample_case()
+    u, c = sim.initial_state(case)
+    acc_old = model.old_accumulation(case, u, c)
+    dt = case.dt0
+    geom = model.faces(case)
+    t = {}
+    t0 = time.perf_counter()
+    F = model.residual(case, u, c, acc_old, dt, geom)
+    rp, col, J = model.jacobian(case, u, c, acc_old, dt, geom=geom)
+    t["assembly"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    val, rhs = linalg.gauss_jordan_decouple(rp, col, J, -F.T.copy())
+    t["gauss_jordan"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    M = linalg.ILU0Preconditioner(rp, col, val)
+    A = linalg.bsr_to_scipy(rp, col, val)
+    t["ilu_setup"] = time.perf_counter() - t0
+    mv = lambda v: (A @ v.reshape(-1)).reshape(v.shape)
+    t0 = time.perf_counter()
+    _, its, rel = linalg.gmres(mv, rhs, M, 30, 1e-6, 1000)
+    t["gmres"] = time.perf_counter() - t0
+    x = np.random.default_rng(1).standard_normal(rhs.shape)
+    t0 = time.perf_counter()
+    for _ in range(10):
+        mv(x)
+    t["spmv"] = (time.perf_counter() - t0) / 10
+    t0 = time.perf_counter()
+    for _ in range(10):
+        M.apply(x)
+    t["ilu_apply"] = (time.perf_counter() - t0) / 10
+    return t, case.n, its, rel
+
+
+def cpu_baseline(case, kry_full, nnzb):
+    """The oracle as it stands (numpy/scipy, one thread: its sparse products and
+    triangular solves are single-threaded) on the host cores, on the bounded
+    sample; every part of the Newton step costs O(cells), so the full-size
+    figures are per-cell costs times the workload's cells, with the GMRES part
+    taken at the full-size Krylov iteration count the GPU measured on the same
+    matrix recipe (an estimate: the oracle itself never runs 2M cells here)."""
+    t, ns, its, rel = oracle_breakdown()
+    scale = case.n / ns
+    setup = t["assembly"] + t["gauss_jordan"] + t["ilu_setup"]
+    per_it = t["gmres"] / max(its, 1)
+    est = scale * (setup + kry_full * per_it)
+    spmv_full_ms = t["spmv"] * scale * 1e3
+    ilu_full_ms = t["ilu_apply"] * scale * 1e3
+    return {"value": 1.0 / est, "unit": UNIT, "cores": 1, "kind": "oracle", "host_cores": os.cpu_count(),
+            "sample": f"one oracle Newton step on a {SAMPLE[0]}x{SAMPLE[1]}x{SAMPLE[2]} block of the large "
+                      f"workload's recipe ({ns} cells; assembly {t['assembly']:.2f} s, Gauss-Jordan "
+                      f"{t['gauss_jordan']:.2f} s, ILU(0) set-up {t['ilu_setup']:.2f} s, GMRES {t['gmres']:.2f} s "
+                      f"for {its} iterations to {rel:.1e}); estimate = cells x (per-cell set-up + "
+                      f"{kry_full:.0f} full-size iterations x per-cell iteration cost)",
+            "estimate_s_per_step": est,
+            "spmv_s_per_call_sample": t["spmv"], "ilu_apply_s_per_call_sample": t["ilu_apply"],
+            "spmv_gbs_sample": spmv_bytes(ns, 7 * ns) / t["spmv"] / 1e9,
+            "spmv_ms_full_estimate": spmv_full_ms, "ilu_apply_ms_full_estimate": ilu_full_ms}
 
 
 def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
         return
+    case = workload_case(args.workload, args.grid)
     for _ in range(args.warmup):
         oracle_sample_step()
-    full = FIELD["nx"] * FIELD["ny"] * FIELD["nz"]
     t0 = time.perf_counter()
-    ncell = None
+    ncell = its = None
     for _ in range(args.steps):
-        _, ncell, _ = oracle_sample_step()
+        _, ncell, its = oracle_sample_step()
     wall = time.perf_counter() - t0
     per = wall / args.steps
-    value = (ncell / full) / per
-    case = field_case()
+    value = (ncell / case.n) / per
+    sample = (f"one oracle Newton step per timed step on a {REF_SAMPLE[0]}x{REF_SAMPLE[1]}x{REF_SAMPLE[2]} block of the "
+              f"workload's recipe ({ncell} cells, {its} GMRES iterations), scaled by cell count to {case.n} cells")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
-        "data": "synthetic",
-        "config": workload_config(case, case.dt0, {"parallelism": "host oracle, 1 thread"}),
-        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1,
-                         "sample": f"one oracle Newton step per timed step on a 30x30x10 block ({ncell} cells), "
-                                   f"scaled by cell count to the 72,000-cell workload"},
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(case, world, args.precision, args.prec),
+        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1, "host_cores": os.cpu_count(),
+                         "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))

@@ -358,11 +358,12 @@ int isc_bsr_spmv_device(int32_t nrows, const int32_t* d_rowptr, const int32_t* d
  * sweep counters) is a static device array sized for at most
  * ISC_NOALLOC_MAX_CELLS cells (about 4 MB, held by every GPU that loads the
  * library until the process exits). Larger grids return ISC_ERR_INVALID_ARG.
- * The first call on a device resolves that array's device address with the
- * device current; make that first call before any stream capture. All calls
- * share the one array, so calls that overlap on the GPU (different streams or
- * threads) race and must be serialised by the caller. The call synchronises
- * stream and returns ISC_ERR_TIMEOUT if a device-side wait gave up. */
+ * Every call resolves that array's device address with the caller's device
+ * current. All calls share the one array, which keeps the previous call's
+ * contents (the call clears what must start at zero), so calls that overlap on
+ * the GPU (different streams or threads) race and must be serialised by the
+ * caller. The call synchronises stream before it returns: ISC_ERR_TIMEOUT if a
+ * device-side wait gave up, ISC_ERR_CUDA if a launch or copy failed. */
 #define ISC_NOALLOC_MAX_CELLS 65536
 int isc_bilu0_apply_noalloc(int32_t nx, int32_t ny, int32_t nz, const int32_t* d_rowptr, const double* d_A,
                             const double* d_Dinv, const double* d_r, double* d_z, void* stream);
@@ -374,6 +375,16 @@ int isc_bilu0_apply_noalloc(int32_t nx, int32_t ny, int32_t nz, const int32_t* d
  * allocated and freed inside (a diagnostic, not a hot-path call); synchronous
  * on the default stream. n < 0 or NULL pointers: ISC_ERR_INVALID_ARG. */
 int isc_check_reciprocal(int32_t n, const double* x, double* y, double* z);
+
+/* Roofline denominators measured on the current device (a diagnostic, not a
+ * hot-path call): the FMA throughput of a register-resident loop of
+ * independent FMA chains over every SM, best of five CUDA-event-timed runs,
+ * returned in GFLOP/s (2 flops per FMA) for FP64 and FP32. The paper reports no
+ * per-kernel throughput; these give the ALU roof of the FP64 kernels (on GB300
+ * the FP64 pipe, not HBM, bounds a kernel above ~0.18 flop per byte). Either
+ * pointer may be NULL to skip that precision. Allocates and frees a small
+ * output buffer; default stream; synchronous (about 30 ms). */
+int isc_measure_fma_rates(double* fp64_gflops, double* fp32_gflops);
 
 /* Failure-detection self-test (no GPU fault): runs the ILU(0) forward sweep on a
  * 4x4x1 grid with its pencil counter started past pencil 0, so the neighbour

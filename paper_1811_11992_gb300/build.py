@@ -13,7 +13,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libisc.so")
-SOURCES = ["isc_assembly.cu", "isc_linalg.cu", "isc_ilu_pipe.cu", "isc_adjoint.cu", "isc_cpr.cu", "isc_api.cu"]
+SOURCES = ["isc_assembly.cu", "isc_linalg.cu", "isc_ilu_pipe.cu", "isc_adjoint.cu", "isc_cpr.cu", "isc_api.cu", "isc_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-diag-suppress", "177"]
 

@@ -25,7 +25,6 @@
 // Lane layout per 8x8 block (row-major, 64 doubles): lane l holds the double2
 // at offset 2l, i.e. row r = l/4, columns c = 2(l%4), c+1; a row sum is a
 // reduction over the 4 lanes of a quad.
-#include <mutex>
 #include <vector>
 
 #include "isc_internal.cuh"
@@ -645,28 +644,39 @@ size_t sweep_smem() {
 }
 
 template <typename TM>
-void sweep_attributes() {
+cudaError_t sweep_attributes() {
   // idempotent; the rings need more than the default 48 KB of dynamic shared memory
-  cudaFuncSetAttribute(k_ilu_fwd_async<TM, SWEEP_R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sweep_smem<TM>());
-  cudaFuncSetAttribute(k_ilu_fwd_async<TM, SWEEP_R, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)sweep_smem<TM>());
-  cudaFuncSetAttribute(k_ilu_bwd_async<TM, SWEEP_R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sweep_smem<TM>());
+  cudaError_t e = cudaFuncSetAttribute(k_ilu_fwd_async<TM, SWEEP_R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sweep_smem<TM>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_ilu_fwd_async<TM, SWEEP_R, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sweep_smem<TM>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_ilu_bwd_async<TM, SWEEP_R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sweep_smem<TM>());
+  return e;
 }
 
+// Forward and backward sweep on the stream; returns the first error of the
+// attribute calls, the clears or the launches (cudaSuccess if all were issued).
 template <typename TM>
-void sweep_pair(int nx, int ny, int nz, const int32_t* rowptr, const TM* A, const TM* Dinv, const double* r, TM* y,
-                TM* zs, double* z64, int* pipe, int* dstatus, cudaStream_t s) {
+cudaError_t sweep_pair(int nx, int ny, int nz, const int32_t* rowptr, const TM* A, const TM* Dinv, const double* r,
+                       TM* y, TM* zs, double* z64, int* pipe, int* dstatus, cudaStream_t s) {
   const size_t n8 = (size_t)nx * ny * nz * 8;
   const int blocks = sweep_blocks<TM>(ny * nz);
   const size_t smem = sweep_smem<TM>();
-  sweep_attributes<TM>();
-  cudaMemsetAsync(pipe, 0, 2 * sizeof(int), s);
-  cudaMemsetAsync(y, 0xff, sizeof(TM) * n8, s);  // NaN sentinel
+  cudaError_t e = sweep_attributes<TM>();
+  if (e == cudaSuccess) e = cudaMemsetAsync(pipe, 0, 2 * sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(y, 0xff, sizeof(TM) * n8, s);  // NaN sentinel
+  if (e != cudaSuccess) return e;
   k_ilu_fwd_async<TM, SWEEP_R><<<blocks, AWARPS * 32, smem, s>>>(nx, ny, nz, rowptr, A, Dinv, r, y, pipe, dstatus);
-  cudaMemsetAsync(pipe, 0, 2 * sizeof(int), s);
-  cudaMemsetAsync(zs, 0xff, sizeof(TM) * n8, s);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemsetAsync(pipe, 0, 2 * sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(zs, 0xff, sizeof(TM) * n8, s);
+  if (e != cudaSuccess) return e;
   k_ilu_bwd_async<TM, SWEEP_R><<<blocks, AWARPS * 32, smem, s>>>(nx, ny, nz, rowptr, A, Dinv, y, zs, z64, pipe,
                                                                  dstatus);
+  return cudaGetLastError();
 }
 
 // FP32 in, FP32 out (inner solve of ISC_PRECISION_MIXED_FGMRES): y in vec32, z written as the hand-off vector
@@ -706,22 +716,13 @@ namespace {
 constexpr size_t NOALLOC_INTS = 64;  // counter, abort flag, status word, padding to 256 bytes
 static __device__ __align__(256) double g_noalloc_scratch[(size_t)ISC_NOALLOC_MAX_CELLS * 8 + NOALLOC_INTS / 2];
 
-constexpr int MAX_DEVICES = 64;
-std::mutex g_noalloc_mutex;
-double* g_noalloc_ptr[MAX_DEVICES] = {};
-
-// Host code may not use g_noalloc_scratch as an address: resolve the device
-// address once per device, with that device current.
+// Host code may not use g_noalloc_scratch as an address: its device address is
+// resolved on every call, with the caller's device current (cheap next to the
+// synchronising sweeps, and never stale after a context is re-created).
 int noalloc_scratch(double** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return ISC_ERR_CUDA;
-  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_ptr[dev]) {
-    void* ptr = nullptr;
-    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return ISC_ERR_CUDA;
-    g_noalloc_ptr[dev] = static_cast<double*>(ptr);
-  }
-  *out = g_noalloc_ptr[dev];
+  void* ptr = nullptr;
+  if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return ISC_ERR_CUDA;
+  *out = static_cast<double*>(ptr);
   return ISC_OK;
 }
 
@@ -758,19 +759,24 @@ extern "C" int isc_check_bounded_wait(void) {
       cudaMalloc(&d_ints, sizeof(int) * 4) != cudaSuccess)
     st = ISC_ERR_NOMEM;
   if (st == ISC_OK) {
-    cudaMemcpy(d_rp, rp.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice);
-    cudaMemset(d_A, 0, sizeof(double) * (size_t)nnzb * BB);
-    cudaMemcpy(d_D, dinv.data(), sizeof(double) * (size_t)n * BB, cudaMemcpyHostToDevice);
-    cudaMemset(d_r, 0, sizeof(double) * (size_t)n * 8);
-    cudaMemset(d_y, 0xff, sizeof(double) * (size_t)n * 8);  // NaN sentinel: nothing arrives from pencil 0
-    const int h_ints[4] = {1, 0, 0, 0};                      // counter = 1 (pencil 0 skipped), abort, status
-    cudaMemcpy(d_ints, h_ints, sizeof(h_ints), cudaMemcpyHostToDevice);
-    const size_t smem = sweep_smem<double>();
-    sweep_attributes<double>();
-    k_ilu_fwd_async<double, SWEEP_R><<<1, AWARPS * 32, smem>>>(nx, ny, nz, d_rp, d_A, d_D, d_r, d_y, d_ints,
-                                                                d_ints + 2);
+    const int h_ints[4] = {1, 0, 0, 0};  // counter = 1 (pencil 0 skipped), abort, status
+    bool ok = cudaMemcpy(d_rp, rp.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemset(d_A, 0, sizeof(double) * (size_t)nnzb * BB) == cudaSuccess &&
+              cudaMemcpy(d_D, dinv.data(), sizeof(double) * (size_t)n * BB, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemset(d_r, 0, sizeof(double) * (size_t)n * 8) == cudaSuccess &&
+              // NaN sentinel: nothing arrives from pencil 0
+              cudaMemset(d_y, 0xff, sizeof(double) * (size_t)n * 8) == cudaSuccess &&
+              cudaMemcpy(d_ints, h_ints, sizeof(h_ints), cudaMemcpyHostToDevice) == cudaSuccess &&
+              sweep_attributes<double>() == cudaSuccess;
+    if (ok) {
+      const size_t smem = sweep_smem<double>();
+      k_ilu_fwd_async<double, SWEEP_R><<<1, AWARPS * 32, smem>>>(nx, ny, nz, d_rp, d_A, d_D, d_r, d_y, d_ints,
+                                                                  d_ints + 2);
+      ok = cudaGetLastError() == cudaSuccess;
+    }
     int h_status = 0;
-    if (cudaMemcpy(&h_status, d_ints + 2, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    // a set-up or launch failure is ISC_ERR_CUDA, never the "no timeout" answer
+    if (!ok || cudaMemcpy(&h_status, d_ints + 2, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
       st = ISC_ERR_CUDA;
     else
       st = (h_status & DS_TIMEOUT) ? ISC_ERR_TIMEOUT : ISC_OK;
@@ -803,7 +809,8 @@ extern "C" int isc_bilu0_apply_noalloc(int32_t nx, int32_t ny, int32_t nz, const
   // everything that must start at zero (or NaN) is cleared inside: the array
   // keeps the previous call's contents
   if (cudaMemsetAsync(ints, 0, NOALLOC_INTS * sizeof(int), s) != cudaSuccess) return ISC_ERR_CUDA;
-  sweep_pair<double>(nx, ny, nz, d_rowptr, d_A, d_Dinv, d_r, y, d_z, nullptr, pipe, status, s);
+  if (sweep_pair<double>(nx, ny, nz, d_rowptr, d_A, d_Dinv, d_r, y, d_z, nullptr, pipe, status, s) != cudaSuccess)
+    return ISC_ERR_CUDA;
   int h_status = 0;
   if (cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return ISC_ERR_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return ISC_ERR_CUDA;

@@ -153,6 +153,7 @@ _SIGS = {
     "isc_set_parameters": (C.c_int, [C.c_void_p, c_double_p, c_double_p, c_double_p]),
     "isc_check_reciprocal": (C.c_int, [C.c_int32, c_double_p, c_double_p, c_double_p]),
     "isc_check_bounded_wait": (C.c_int, []),
+    "isc_measure_fma_rates": (C.c_int, [c_double_p, c_double_p]),
     "isc_num_coupled_wells": (C.c_int32, [C.c_void_p]),
     "isc_set_well_bhp": (C.c_int, [C.c_void_p, c_double_p]),
     "isc_get_well_bhp": (C.c_int, [C.c_void_p, c_double_p]),
@@ -501,10 +502,24 @@ NOALLOC_MAX_CELLS = 65536
 
 
 def bilu0_apply_noalloc(nx, ny, nz, d_rowptr, d_A, d_Dinv, d_r, d_z, stream=None):
-    """Allocation-free ILU(0) apply on caller-owned device buffers (pointers as ints)."""
+    """Allocation-free ILU(0) apply on caller-owned device buffers (pointers as
+    ints). Raises IscError with the library's status on any failure (grids
+    beyond NOALLOC_MAX_CELLS cells give status -1, invalid argument)."""
     lib = load_library()
-    return lib.isc_bilu0_apply_noalloc(nx, ny, nz, C.c_void_p(d_rowptr), C.c_void_p(d_A), C.c_void_p(d_Dinv),
-                                       C.c_void_p(d_r), C.c_void_p(d_z), C.c_void_p(stream) if stream else None)
+    st = lib.isc_bilu0_apply_noalloc(nx, ny, nz, C.c_void_p(d_rowptr), C.c_void_p(d_A), C.c_void_p(d_Dinv),
+                                     C.c_void_p(d_r), C.c_void_p(d_z), C.c_void_p(stream) if stream else None)
+    if st != ISC_OK:
+        raise IscError(st, "isc_bilu0_apply_noalloc failed")
+
+
+def measure_fma_rates():
+    """(FP64, FP32) FMA throughput of the current device in GFLOP/s."""
+    lib = load_library()
+    f64, f32 = C.c_double(0.0), C.c_double(0.0)
+    st = lib.isc_measure_fma_rates(C.byref(f64), C.byref(f32))
+    if st != ISC_OK:
+        raise IscError(st, "isc_measure_fma_rates failed")
+    return f64.value, f32.value
 
 
 def check_reciprocal(x):

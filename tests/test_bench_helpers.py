@@ -1,5 +1,6 @@
 """The bench line's derived numbers (CPU): per-class GB/s from kernel-class times,
-the FP32 SpMV roofline and the traffic-figure rule for non-FP64 runs."""
+the algorithmic bytes of the SpMV and ILU(0) apply, the roofline's bound
+(FP64 pipe or HBM) and the traffic figure's scaling rule."""
 import importlib.util
 import os
 
@@ -19,6 +20,12 @@ def bench():
 class _Case:
     def __init__(self, nx, ny, nz):
         self.nx, self.ny, self.nz, self.n = nx, ny, nz, nx * ny * nz
+        self.name = f"box {nx}x{ny}x{nz}"
+        self.dt0 = 100.0
+
+
+def _nnzb(nx, ny, nz):
+    return nx * ny * nz + 2 * ((nx - 1) * ny * nz + nx * (ny - 1) * nz + nx * ny * (nz - 1))
 
 
 def test_class_gbs(bench):
@@ -32,25 +39,52 @@ def test_class_gbs(bench):
 
 def test_hbm_table_bytes(bench):
     case = _Case(60, 60, 20)
-    nnzb = 492_000
+    nnzb = _nnzb(60, 60, 20)
+    assert nnzb == 492_000
     st = {k: {"calls": 1, "ms": 1.0, "launches": 1} for k in ("spmv", "prec_apply", "spmv32")}
     t = bench.hbm_table(st, st, st, case, nnzb)
     off = nnzb - case.n
     assert t["spmv_fp64"]["bytes_per_call"] == off * 516 + 3 * case.n * 64
     assert t["spmv_fp32"]["bytes_per_call"] == off * 260 + 3 * case.n * 32
+    # ILU(0) apply: every off-diagonal block once, one inverted diagonal block per cell, four vector passes
+    assert t["ilu_apply_fp64"]["bytes_per_call"] == off * 516 + case.n * 512 + 4 * case.n * 64
     assert t["ilu_apply_fp32"]["bytes_per_call"] < t["ilu_apply_fp64"]["bytes_per_call"]
     assert set(bench.hbm_table(st, None, None, case, nnzb)) == {"spmv_fp64", "ilu_apply_fp64"}
 
 
-def test_fp64_traffic_only_for_fp64_runs(bench):
-    case = _Case(60, 60, 20)
-    st = {"prec_apply": {"calls": 80, "ms": 26.0, "launches": 160}}
+def test_roofline_bound_follows_the_measured_ridge(bench):
+    case = _Case(200, 200, 50)
+    nnzb = _nnzb(200, 200, 50)
+    assert nnzb == 13_880_000
+    st = {"prec_apply": {"calls": 114, "ms": 114 * 3.8, "launches": 228}}
+    # FP64 at 1.2 TFLOP/s: 0.25 flop/B is above the ridge (0.18), so the FP64 pipe bounds the apply
+    r = bench.roofline("prec_apply", st, case, nnzb, 1200.0, "fp64")
+    assert r["bound"] == "alu" and r["unit"] == "GFLOP/s"
+    assert r["achieved"] == pytest.approx(bench.ilu_apply_flops(case.n, nnzb) / 3.8e-3 / 1e9)
+    assert r["hbm_achieved_gbs"] == pytest.approx(r["bytes_per_call"] / 3.8e-3 / 1e9)
+    # the same apply on a GPU with a fast FP64 pipe is bound by HBM
+    r2 = bench.roofline("prec_apply", st, case, nnzb, 60000.0, "fp64")
+    assert r2["bound"] == "hbm" and r2["frac"] == pytest.approx(r2["achieved"] / r2["peak"])
+    # FP32 sweeps are never FP64-bound
+    r3 = bench.roofline("prec_apply", st, case, nnzb, 1200.0, "mixed")
+    assert r3["bound"] == "hbm"
 
-    class G:
-        nnzb = 492_000
-    r64 = bench.roofline("prec_apply", st, G(), case, [80], "fp64")
-    r32 = bench.roofline("prec_apply", st, G(), case, [80], "mixed")
-    assert r64["traffic"] == bench.MEASURED_TRAFFIC[("prec_apply", 60, 60, 20)][0]
-    assert r32["traffic"] is None and "note" in r32
-    # algorithmic bytes per call against the measured HBM copy bandwidth
-    assert r64["hbm_achieved_gbs"] == pytest.approx(r64["bytes_per_call"] / (26.0 / 80 * 1e-3) / 1e9)
+
+def test_traffic_is_scaled_per_cell(bench):
+    case = _Case(200, 200, 50)
+    nnzb = _nnzb(200, 200, 50)
+    st = {"prec_apply": {"calls": 10, "ms": 38.0, "launches": 20}}
+    r = bench.roofline("prec_apply", st, case, nnzb, 1200.0, "fp64")
+    per_cell = bench.MEASURED_TRAFFIC[("prec_apply", "fp64")][0]
+    assert r["traffic"] == pytest.approx(per_cell * case.n)
+    assert "scaled per cell" in r["traffic_source"]
+    assert bench.roofline("spmv", {"spmv": {"calls": 1, "ms": 1.0, "launches": 1}}, case, nnzb, 1200.0,
+                          "fp64")["traffic"] is None
+
+
+def test_reference_and_library_arms_share_the_config(bench):
+    case = _Case(200, 200, 50)
+    a = bench.workload_config(case, 1)
+    b = bench.workload_config(case, 1)
+    assert a == b and "200x200x50" in a["workload"] and a["precision"] == "fp64"
+    assert bench.parse([]).workload == "large"

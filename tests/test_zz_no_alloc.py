@@ -1,8 +1,9 @@
 """The allocation-free ILU(0) apply (isc_bilu0_apply_noalloc) serves callers
 that cannot allocate GPU memory themselves: it must give the same result as
-the library's own preconditioner apply (isc_precond_apply) on the same
-matrix, on two calls in a row (the shared static scratch keeps the previous
-call's contents), and reject grids larger than its fixed scratch."""
+the library's own preconditioner apply (isc_precond_apply) and as the oracle's
+textbook block ILU(0) on the same matrix, on two calls in a row (the shared
+static scratch keeps the previous call's contents), and reject grids larger
+than its fixed scratch."""
 import numpy as np
 import pytest
 
@@ -31,6 +32,7 @@ def test_noalloc_ilu_apply_matches_precond_apply_twice():
     rp, col, Jd = g.jacobian()
     # the inverted ILU(0) diagonal blocks of the same matrix (the caller's input)
     F = linalg.block_ilu0(rp.astype(np.int64), col.astype(np.int64), Jd)
+    M = linalg.ILU0Preconditioner(rp.astype(np.int64), col.astype(np.int64), Jd)
     rows = np.repeat(np.arange(case.n), np.diff(rp))
     Dinv = np.linalg.inv(F[col == rows])
     dev = torch.device("cuda")
@@ -44,14 +46,16 @@ def test_noalloc_ilu_apply_matches_precond_apply_twice():
         d_r = torch.from_numpy(np.ascontiguousarray(r.T).reshape(-1)).to(dev)
         d_z = torch.empty_like(d_r)
         torch.cuda.synchronize()
-        st = isc.bilu0_apply_noalloc(case.nx, case.ny, case.nz, d_rp.data_ptr(), d_A.data_ptr(), d_D.data_ptr(),
-                                     d_r.data_ptr(), d_z.data_ptr())
-        assert st == 0
+        isc.bilu0_apply_noalloc(case.nx, case.ny, case.nz, d_rp.data_ptr(), d_A.data_ptr(), d_D.data_ptr(),
+                                d_r.data_ptr(), d_z.data_ptr())
         z = d_z.cpu().numpy().reshape(case.n, 8).T
         assert np.max(np.abs(z - z_ref)) <= 1e-11 * np.abs(z_ref).max()
+        z_or = M.apply(r.T.copy()).T
+        assert np.max(np.abs(z - z_or)) <= 1e-11 * np.abs(z_or).max()
     # a grid beyond the static scratch is rejected before any GPU work
     too_big = isc.NOALLOC_MAX_CELLS + 1
-    st = isc.bilu0_apply_noalloc(too_big, 1, 1, d_rp.data_ptr(), d_A.data_ptr(), d_D.data_ptr(),
-                                 d_r.data_ptr(), d_z.data_ptr())
-    assert st == -1
+    with pytest.raises(isc.IscError) as err:
+        isc.bilu0_apply_noalloc(too_big, 1, 1, d_rp.data_ptr(), d_A.data_ptr(), d_D.data_ptr(),
+                                d_r.data_ptr(), d_z.data_ptr())
+    assert err.value.status == -1
     g.close()
