@@ -316,6 +316,28 @@ int isc_newton_step(struct isc_handle* h, double dt, isc_newton_info* info);
  * converged state becomes the accepted state. */
 int isc_timestep(struct isc_handle* h, double dt, isc_step_info* info);
 
+/* Replace the assembled system by a caller's one (the method's linear step of
+ * Sec. 3.2 on given data): val, the nnzb*64 BSR blocks on the handle's 7-point
+ * pattern (the rowptr and col that isc_get_jacobian_bsr returns), and F, the
+ * block-major residual (8N); isc_solve then solves J du = -F. decoupled = 1
+ * declares val already decoupled: every diagonal block must be exactly the
+ * identity (checked; ISC_ERR_INVALID_ARG otherwise) and isc_decouple does
+ * nothing; 0 gives an assembled system that isc_decouple will scale. Host
+ * arrays, copied; the preconditioner must be rebuilt; the state is untouched.
+ * Handles with coupled producers return ISC_ERR_UNIMPLEMENTED. Synchronous. */
+int isc_set_system(struct isc_handle* h, const double* val, const double* F, int32_t decoupled);
+/* Solve A x = b for a caller's BSR matrix with the handle's linear solver
+ * (Gauss-Jordan decoupling of Sec. 3.2 if options.decouple, then the
+ * preconditioned Krylov method and tolerance of the options). A is rowptr
+ * (N+1), col (nnzb), val (nnzb*64) and must have the handle's 7-point pattern
+ * (else ISC_ERR_INVALID_ARG: the preconditioner kernels depend on it); b and x
+ * are block-major 8N host arrays. info (may be NULL) receives the Krylov
+ * iterations and the achieved relative residual of the (decoupled) system. It
+ * overwrites the handle's assembled system (isc_set_system with F = -b);
+ * the state is untouched. Synchronous. */
+int isc_solve_external(struct isc_handle* h, const int32_t* rowptr, const int32_t* col, const double* val,
+                       const double* b, double* x, isc_newton_info* info);
+
 /* ---------------------------------------------------------------- exports */
 
 /* Residual F of the last assembly (host, block-major 8N), after decoupling
@@ -334,6 +356,13 @@ int isc_spmv(struct isc_handle* h, const double* x, double* y);
  * isc_build_preconditioner (host, block-major 8N). */
 int isc_build_preconditioner(struct isc_handle* h);
 int isc_precond_apply(struct isc_handle* h, const double* r, double* z);
+/* The inverted diagonal blocks D_i^-1 of the block ILU(0) factors built by the
+ * last isc_build_preconditioner (or isc_solve), D-ILU form: D_i = A_ii -
+ * sum_{k<i} A_ik D_k^-1 A_ki over the 7-point neighbours in natural order;
+ * N*64 host doubles, row-major blocks (the FP32 factors of the mixed modes
+ * converted exactly). ISC_ERR_STATE unless options.prec is BILU0 or CPR and
+ * the preconditioner is built. */
+int isc_get_ilu_diag(struct isc_handle* h, double* dinv);
 int isc_get_stats(struct isc_handle* h, isc_stats* stats);
 int isc_reset_stats(struct isc_handle* h);
 

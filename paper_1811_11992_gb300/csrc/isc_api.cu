@@ -114,7 +114,7 @@ int dalloc(isc_handle* h, T** p, size_t count) {
 void free_all(isc_handle* h) {
   void* ptrs[] = {h->rowptr, h->col, h->level_cells, h->phi_ref, h->depth, h->tx, h->ty, h->tz, h->well_slot,
                   h->slots, h->u, h->coke, h->u_n, h->coke_n, h->acc_n, h->props, h->R, h->J, h->ntot, h->du,
-                  h->rhs, h->dinv, h->J32, h->dinv32, h->vec32, h->V32, h->Z32, h->w32, h->gm_in, h->scal_in, h->V, h->Z, h->w, h->tmp, h->partial, h->scal, h->dstatus, h->pipe, h->red_counter, h->gmres,
+                  h->rhs, h->dinv, h->uhat, h->J32, h->dinv32, h->uhat32, h->vec32, h->V32, h->Z32, h->w32, h->gm_in, h->scal_in, h->V, h->Z, h->w, h->tmp, h->partial, h->scal, h->dstatus, h->pipe, h->red_counter, h->gmres,
                   h->wx, h->wy, h->wz, h->cw, h->bhp, h->bhp_n, h->Dw, h->Bv, h->Cv, h->Fq, h->Dq, h->adj.store, h->adj.ubar, h->adj.cbar, h->adj.lam, h->adj.glnk, h->adj.grx,
                   h->adj.scond, h->adj.kd, h->adj.loss_cell, h->adj.sums, h->adj.inj_first, h->adj.inj_count};
   for (void* p : ptrs)
@@ -255,6 +255,7 @@ int build_prec(isc_handle* h) {
       int e = 0;
       e |= dalloc(h, &h->J32, (size_t)h->nnzb * BB);
       e |= dalloc(h, &h->dinv32, (size_t)h->n * BB);
+      e |= dalloc(h, &h->uhat32, (size_t)h->n * 3 * BB);
       e |= dalloc(h, &h->vec32, (size_t)h->n * 16);
       if (e) return ISC_ERR_NOMEM;
     }
@@ -924,6 +925,7 @@ int isc_create(const isc_grid* grid, const isc_rock* rock, const isc_fluid* fl, 
   e |= dalloc(h, &h->du, len);
   e |= dalloc(h, &h->rhs, len);
   e |= dalloc(h, &h->dinv, (size_t)n * BB);
+  e |= dalloc(h, &h->uhat, (size_t)n * 3 * BB);
   e |= dalloc(h, &h->V, (size_t)(h->restart_alloc + 1) * len);
   e |= dalloc(h, &h->Z, (size_t)h->restart_alloc * len);
   e |= dalloc(h, &h->w, len);
@@ -1238,6 +1240,47 @@ int isc_timestep(isc_handle* h, double dt, isc_step_info* info) {
   return st;
 }
 
+int isc_set_system(isc_handle* h, const double* val, const double* F, int32_t decoupled) {
+  if (!h || !val || !F || (decoupled != 0 && decoupled != 1)) return ISC_ERR_INVALID_ARG;
+  if (h->nwc)
+    return set_err(h, ISC_ERR_UNIMPLEMENTED, "a caller's system cannot carry the coupled producers' border");
+  if (decoupled) {
+    // the unit-diagonal SpMV and the sweeps skip the diagonal blocks: they must be I exactly
+    for (int i = 0; i < h->n; ++i)
+      for (int b = h->h_rowptr[i]; b < h->h_rowptr[i + 1]; ++b)
+        if (h->h_col[b] == i)
+          for (int e = 0; e < BB; ++e)
+            if (val[(size_t)b * BB + e] != ((e % 9 == 0) ? 1.0 : 0.0))
+              return set_err(h, ISC_ERR_INVALID_ARG, "decoupled system: a diagonal block is not the identity");
+  }
+  CUDA_TRY(h, cudaMemcpyAsync(h->J, val, sizeof(double) * BB * (size_t)h->nnzb, cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(h->R, F, sizeof(double) * 8 * (size_t)h->n, cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  h->assembled = true;
+  h->decoupled = decoupled != 0;
+  h->prec_built = false;
+  return ISC_OK;
+}
+
+int isc_solve_external(isc_handle* h, const int32_t* rowptr, const int32_t* col, const double* val, const double* b,
+                       double* x, isc_newton_info* info) {
+  if (!h || !rowptr || !col || !val || !b || !x) return ISC_ERR_INVALID_ARG;
+  if (memcmp(rowptr, h->h_rowptr.data(), sizeof(int32_t) * (h->n + 1)) != 0 ||
+      memcmp(col, h->h_col.data(), sizeof(int32_t) * h->nnzb) != 0)
+    return set_err(h, ISC_ERR_INVALID_ARG, "the matrix must have the handle's 7-point BSR pattern");
+  std::vector<double> F((size_t)8 * h->n);
+  for (size_t k = 0; k < F.size(); ++k) F[k] = -b[k];  // isc_solve solves J du = -F
+  int st = isc_set_system(h, val, F.data(), 0);
+  if (st) return st;
+  if (h->opt.decouple) {
+    st = isc_decouple(h);
+    if (st) return st;
+  }
+  st = isc_solve(h, info);
+  if (st) return st;
+  return isc_get_update(h, x);
+}
+
 int isc_get_residual(isc_handle* h, double* F) {
   if (!h || !F) return ISC_ERR_INVALID_ARG;
   if (!h->assembled) return set_err(h, ISC_ERR_STATE, "assemble first");
@@ -1308,6 +1351,23 @@ int isc_precond_apply(isc_handle* h, const double* r, double* z) {
   prec(h, h->w, h->V);
   CUDA_TRY(h, cudaMemcpyAsync(z, h->V, sizeof(double) * len, cudaMemcpyDeviceToHost, h->stream));
   return check_device_status(h);  // synchronises; reports a sweep whose bounded wait gave up
+}
+
+int isc_get_ilu_diag(isc_handle* h, double* dinv) {
+  if (!h || !dinv) return ISC_ERR_INVALID_ARG;
+  if (!h->prec_built || (h->opt.prec != ISC_PREC_BILU0 && h->opt.prec != ISC_PREC_CPR))
+    return set_err(h, ISC_ERR_STATE, "build the block ILU(0) (or CPR-PF) preconditioner first");
+  const size_t cnt = (size_t)h->n * BB;
+  if (h->opt.precision == ISC_PRECISION_FP64) {
+    CUDA_TRY(h, cudaMemcpyAsync(dinv, h->dinv, sizeof(double) * cnt, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return ISC_OK;
+  }
+  std::vector<float> f(cnt);
+  CUDA_TRY(h, cudaMemcpyAsync(f.data(), h->dinv32, sizeof(float) * cnt, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  for (size_t k = 0; k < cnt; ++k) dinv[k] = (double)f[k];
+  return ISC_OK;
 }
 
 int isc_get_stats(isc_handle* h, isc_stats* st) {

@@ -148,289 +148,412 @@ __device__ __forceinline__ bool poll_vec(const T* v, int c, typename V2<T>::t& o
   }
 }
 
-template <typename T>
-__device__ __forceinline__ typename V2<T>::t zero2() {
-  typename V2<T>::t z;
-  z.x = T(0);
-  z.y = T(0);
-  return z;
-}
+// ------------------------------------------------- sweep kernels
+// Two x-pencils per warp, one per half-warp: a pencil's 8x8 block is spread
+// over 16 lanes, lane h holding row r = h/2 and four columns (two pairs), so a
+// block-vector product is four FMAs per lane and a row sum is ONE shuffle and
+// one add over the lane pair. On GB300 the FP64 pipe is the sweep's scarcest
+// unit; against one pencil per 32-lane warp (quad sums: two adds per row) this
+// halves the reduction adds, and the two pencils of a warp share every
+// shuffle, address and staging instruction. The pair of a warp lies on one
+// anti-diagonal j + k = d of the (y, z) pencil grid, so the two are independent
+// (each waits only on pencils of diagonal d - 1, claimed earlier from the same
+// counter) and share one of their neighbours.
+//
+// Forward sweep  y_i = D_i^-1 (r_i - A_z y_z - A_y y_y - A_x y_{i-1});
+// backward sweep z_i = y_i - Dhat_z z_z - Dhat_y z_y - Dhat_x z_{i+1} with the
+// pre-scaled upper blocks Dhat = D_i^-1 A_{i,up}, which the factorisation
+// computes anyway (they are its D_k^-1 A_ki products) and stores, so the
+// backward sweep reads no D^-1 and does no second product. Signs are folded
+// into FMA operands (a row sum starts from -r_i, the diagonal product uses -D),
+// so no separate subtraction reaches the FP64 pipe.
 
-template <typename T>
-__device__ __forceinline__ T quad_sum(T v) {
-  v += __shfl_xor_sync(FULL, v, 1);
-  v += __shfl_xor_sync(FULL, v, 2);
-  return v;
-}
-
-// Remote look-ahead: the neighbour-pencil values a cell needs are requested LA
-// cells before they are used; entries still NaN on use are re-polled. A request
-// only finds the value if the consumer trails its producer by about LA cells,
-// so every pencil-to-pencil hand-off adds that lag to the wavefront: one cell
-// ahead is the best measured (sweep pair 347 / 387 / 388 us for LA = 1 / 2 / 4
-// in FP64 at 60x60x20, 241 / 283 / 279 us in FP32).
-constexpr int LA = 1;
-
-template <typename TM>
-__device__ __forceinline__ typename V2<TM>::t ld_remote(const TM* p) {
-  typename V2<TM>::t v;
-  ld_relaxed_v2(p, v.x, v.y);
-  return v;
-}
+// the lane's four columns of a block row: (e0, e0 + 1) and (e2, e2 + 1). FP64
+// lanes 4-7 and 12-15 of a half take the two pairs in the other order, so that
+// each 16-byte shared-memory load of a quarter-warp touches 32 distinct banks
+struct LaneCols {
+  int hl, h, r, q, e0, e2, s0, s2;
+};
 
 template <typename TM>
-__device__ __forceinline__ bool ready2(const typename V2<TM>::t& v) {
-  return arrived(v.x) && arrived(v.y);
+__device__ __forceinline__ LaneCols lane_cols() {
+  LaneCols L;
+  const int lane = threadIdx.x & 31;
+  L.hl = lane >> 4;
+  L.h = lane & 15;
+  L.r = L.h >> 1;
+  L.q = L.h & 1;
+  const int sw = sizeof(TM) == 8 ? ((L.h >> 2) & 1) : 0;
+  L.e0 = 4 * L.q + 2 * sw;
+  L.e2 = 4 * L.q + 2 * (1 - sw);
+  // lanes holding the row sums of those columns (both lanes of a row pair hold it)
+  L.s0 = (L.hl << 4) + 2 * L.e0;
+  L.s2 = (L.hl << 4) + 2 * L.e2;
+  return L;
 }
 
-// re-poll until the lane pair is a number everywhere in the warp
+// four entries of block row r (columns e0, e0+1, e2, e2+1) from shared memory
+__device__ __forceinline__ void ld4s(const double* b, const LaneCols& L, double (&x)[4]) {
+  const double2 a = *reinterpret_cast<const double2*>(b + L.r * 8 + L.e0);
+  const double2 c = *reinterpret_cast<const double2*>(b + L.r * 8 + L.e2);
+  x[0] = a.x, x[1] = a.y, x[2] = c.x, x[3] = c.y;
+}
+__device__ __forceinline__ void ld4s(const float* b, const LaneCols& L, float (&x)[4]) {
+  const float4 a = *reinterpret_cast<const float4*>(b + L.r * 8 + L.e0);  // e2 = e0 + 2 in FP32
+  x[0] = a.x, x[1] = a.y, x[2] = a.z, x[3] = a.w;
+}
+
+// the same four entries of a neighbour's 8-vector, relaxed gpu-scope loads (hand-off polling)
+__device__ __forceinline__ void ld4r(const double* v, const LaneCols& L, double (&x)[4]) {
+  ld_relaxed_v2(v + L.e0, x[0], x[1]);
+  ld_relaxed_v2(v + L.e2, x[2], x[3]);
+}
+__device__ __forceinline__ void ld4r(const float* v, const LaneCols& L, float (&x)[4]) {
+  asm volatile("ld.relaxed.gpu.global.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(x[0]), "=f"(x[1]), "=f"(x[2]), "=f"(x[3])
+               : "l"(v + L.e0)
+               : "memory");
+}
+
+// lanes 0 and 1 of a half hold the whole 8-vector after the broadcast: columns 0-3 and 4-7
+__device__ __forceinline__ void st4r(double* v, const LaneCols& L, const double (&x)[4]) {
+  asm volatile("st.relaxed.gpu.global.v2.f64 [%0], {%1, %2};" ::"l"(v + L.e0), "d"(x[0]), "d"(x[1]) : "memory");
+  asm volatile("st.relaxed.gpu.global.v2.f64 [%0], {%1, %2};" ::"l"(v + L.e2), "d"(x[2]), "d"(x[3]) : "memory");
+}
+__device__ __forceinline__ void st4r(float* v, const LaneCols& L, const float (&x)[4]) {
+  asm volatile("st.relaxed.gpu.global.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(v + L.e0), "f"(x[0]), "f"(x[1]),
+               "f"(x[2]), "f"(x[3])
+               : "memory");
+}
+
 template <typename TM>
-__device__ __forceinline__ bool settle(const TM* p, typename V2<TM>::t& v, int* abortf, int* dstatus) {
-  if (__all_sync(FULL, ready2<TM>(v))) return true;
-  return poll_vec<TM>(p, 0, v, abortf, dstatus);
+__device__ __forceinline__ bool arrived4(const TM (&x)[4]) {
+  return arrived(x[0]) && arrived(x[1]) && arrived(x[2]) && arrived(x[3]);
+}
+
+template <typename TM>
+__device__ __forceinline__ void zero4(TM (&x)[4]) {
+  x[0] = x[1] = x[2] = x[3] = TM(0);
+}
+
+// -x without the floating-point pipe (sign bit flip)
+__device__ __forceinline__ double neg_bits(double x) {
+  return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull);
+}
+__device__ __forceinline__ float neg_bits(float x) { return __int_as_float(__float_as_int(x) ^ (int)0x80000000u); }
+
+// Wait until the neighbour values a half needs (z and/or y neighbour pencil,
+// four entries each per lane) are all numbers, across the whole warp. The
+// values were requested one cell ahead; entries still holding the sentinel are
+// re-read. Returns false on abort (a timeout here or elsewhere).
+template <typename TM>
+__device__ __forceinline__ bool await_nbrs(const TM* pz, bool hz, TM (&vz)[4], const TM* py, bool hy, TM (&vy)[4],
+                                           const LaneCols& L, int* abortf, int* dstatus) {
+  for (int spins = 0;; ++spins) {
+    const bool okz = !hz || arrived4<TM>(vz), oky = !hy || arrived4<TM>(vy);
+    if (__all_sync(FULL, okz && oky)) return true;
+    if ((spins & 63) == 63 && __any_sync(FULL, ld_relaxed(abortf) != 0)) return false;
+    if (spins > SPIN_LIMIT) {
+      if ((threadIdx.x & 31) == 0) {
+        atomicOr(dstatus, DS_TIMEOUT);
+        atomicExch(abortf, 1);
+      }
+      return false;
+    }
+    __nanosleep(20);
+    if (!okz) ld4r(pz, L, vz);
+    if (!oky) ld4r(py, L, vy);
+  }
 }
 
 // ------------------------------------------------- shared-memory operand pipeline
-// The operands of a cell (its up-to-three off-diagonal blocks of the sweep
-// direction, D^-1 and the right-hand side) do not depend on the sweep. Each
-// warp streams them into its own ring of R cell slots in shared memory with
-// cp.async, R-1 cells ahead of use, so the per-cell chain no longer waits on
-// DRAM. Every iteration commits exactly one group (possibly empty) and waits
-// until the group of the current cell has landed (a hardware wait).
-template <int BYTES>
-__device__ __forceinline__ void cp_async(void* smem_dst, const void* gsrc) {
+// A cell's operands (its up-to-three off-diagonal blocks of the sweep
+// direction, D^-1 where the sweep needs it, and the right-hand side) do not
+// depend on the sweep. Each warp streams them into its own ring of R slots with
+// 16-byte cp.async copies, R-1 cells ahead of use, so the per-cell chain does
+// not wait on DRAM. Every iteration commits exactly one group (possibly empty)
+// and waits until the group of the current cell has landed (a hardware wait).
+__device__ __forceinline__ void cp16(void* smem_dst, const void* gsrc) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(gsrc), "n"(BYTES) : "memory");
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gsrc) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-template <typename TM>
-struct Slot {
-  TM blk[4][64];   // up to 3 off-diagonal blocks and D^-1 (index 3)
-  double rhs[8];
+template <typename TM, typename RT>
+struct alignas(16) Slot2 {
+  TM blk[2][4][64];  // per half: blocks in fixed positions (direction slots 0..2, D^-1 at 3)
+  RT rhs[2][8];
 };
 
-// issue the copies of one cell into a slot: blocks at row slots first_slot.. (mask says which exist)
-template <typename TM, typename RT = double>
-__device__ __forceinline__ void stage_cell(Slot<TM>* sl, int i, int first_slot, int mask, const Pen& P,
-                                           const TM* __restrict__ A, const TM* __restrict__ Dinv,
-                                           const RT* __restrict__ rhs, int lane) {
-  const int base = row_start(P, i - P.base_jk);
-  int s = first_slot, dst = 0;  // present blocks are packed into blk[0..] in row order
-#pragma unroll
-  for (int b = 0; b < 3; ++b) {
-    if (mask & (1 << b)) {
-      cp_async<2 * sizeof(TM)>(&sl->blk[dst][2 * lane], A + (size_t)(base + s) * BB + 2 * lane);
-      ++s;
-      ++dst;
-    }
-  }
-  cp_async<2 * sizeof(TM)>(&sl->blk[3][2 * lane], Dinv + (size_t)i * BB + 2 * lane);
-  // the right-hand side is FP64, or FP32 in the inner solve of the mixed-precision scheme
-  if (rhs && lane < 8) cp_async<sizeof(RT)>(reinterpret_cast<RT*>(sl->rhs) + lane, rhs + (size_t)i * 8 + lane);
-}
-
+// one block (64 entries) copied by the 16 lanes of a half
 template <typename TM>
-__device__ __forceinline__ typename V2<TM>::t sl_pair(const Slot<TM>* sl, int b, int lane) {
-  return *reinterpret_cast<const typename V2<TM>::t*>(&sl->blk[b][2 * lane]);
+__device__ __forceinline__ void stage_blk(TM* dst, const TM* src, int h) {
+  constexpr int PER = 64 / 16;             // entries per lane
+  constexpr int CH = 16 / sizeof(TM);      // entries per 16-byte copy
+#pragma unroll
+  for (int c = 0; c < PER; c += CH) cp16(dst + h * PER + c, src + h * PER + c);
 }
 
-// warps per block of the sweeps: 4 (six FP64 blocks per SM) ran the 100x100x30 sweep pair in
-// 0.74-0.76 ms against 0.82 ms with 8 (three blocks per SM); equal at 60x60x20
-constexpr int AWARPS = 4;
+// an 8-vector (the right-hand side, or the forward result in the backward sweep)
+template <typename RT>
+__device__ __forceinline__ void stage_vec(RT* dst, const RT* src, int h) {
+  constexpr int CH = 16 / sizeof(RT);
+  if (h < 8 / CH) cp16(dst + h * CH, src + h * CH);
+}
 
-template <typename TM, int R, typename RT = double>
-__global__ void __launch_bounds__(AWARPS * 32) k_ilu_fwd_async(int nx, int ny, int nz, const int32_t* __restrict__ rowptr,
-                                                               const TM* __restrict__ A, const TM* __restrict__ Dinv,
-                                                               const RT* __restrict__ rhs, TM* __restrict__ y,
-                                                               int* __restrict__ pipe, int* __restrict__ dstatus) {
-  using T2 = typename V2<TM>::t;
+// Anti-diagonal task map of the (y, z) pencil grid: diagonal d holds pencils
+// (j, d - j) for j in [jlo, jlo + len), taken two per task in order of j.
+struct Diag {
+  int d, t0, jlo, len;
+};
+
+__device__ __forceinline__ void diag_set(Diag& D, int d, int ny, int nz) {
+  D.d = d;
+  D.jlo = d - (nz - 1) > 0 ? d - (nz - 1) : 0;
+  const int jhi = d < ny - 1 ? d : ny - 1;
+  D.len = jhi - D.jlo + 1;
+}
+
+// move forward to the diagonal holding task t (a warp's tasks only increase);
+// false past the last diagonal
+__device__ __forceinline__ bool diag_seek(Diag& D, int t, int ny, int nz) {
+  while (t >= D.t0 + ((D.len + 1) >> 1)) {
+    D.t0 += (D.len + 1) >> 1;
+    if (D.d >= ny + nz - 2) return false;
+    diag_set(D, D.d + 1, ny, nz);
+  }
+  return true;
+}
+
+// pencil (j, k) of a half for task t on diagonal D; act = the half has a pencil
+__device__ __forceinline__ void task_pencil(const Diag& D, int t, int hl, int& j, int& k, bool& act) {
+  const int j0 = D.jlo + 2 * (t - D.t0);
+  act = hl == 0 || j0 + 1 < D.jlo + D.len;
+  j = act ? j0 + hl : j0;
+  k = D.d - j;
+}
+
+constexpr int AWARPS = 4;  // warps per block of the sweeps
+
+template <typename TM, int R, typename RT>
+__global__ void __launch_bounds__(AWARPS * 32) k_sweep_fwd(int nx, int ny, int nz, const TM* __restrict__ A,
+                                                           const TM* __restrict__ Dinv, const RT* __restrict__ rhs,
+                                                           TM* __restrict__ y, int* __restrict__ pipe,
+                                                           int* __restrict__ dstatus) {
+  using SL = Slot2<TM, RT>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Slot<TM>* ring = reinterpret_cast<Slot<TM>*>(smem_raw) + (threadIdx.x >> 5) * R;
-  const int lane = threadIdx.x & 31;
-  const int r = lane >> 2, c = (lane & 3) * 2;
-  const int npen = ny * nz, nxy = nx * ny;
+  SL* ring = reinterpret_cast<SL*>(smem_raw) + (threadIdx.x >> 5) * R;
+  const LaneCols L = lane_cols<TM>();
+  const int nxy = nx * ny;
   int* counter = pipe;
   int* abortf = pipe + 1;
+  Diag D;
+  diag_set(D, 0, ny, nz);
+  D.t0 = 0;
   for (;;) {
-    int p = 0;
-    if (lane == 0) p = atomicAdd(counter, 1);
-    p = __shfl_sync(FULL, p, 0);
-    if (p >= npen) return;
-    const int j = p % ny, k = p / ny;
-    const bool hy = j > 0, hz = k > 0;
+    int t = 0;
+    if ((threadIdx.x & 31) == 0) t = atomicAdd(counter, 1);
+    t = __shfl_sync(FULL, t, 0);
+    if (!diag_seek(D, t, ny, nz)) return;
+    int j, k;
+    bool act;
+    task_pencil(D, t, L.hl, j, k, act);
+    const bool hy = act && j > 0, hz = act && k > 0;
     const int base_jk = nx * (j + ny * k);
     const Pen PEN = make_pen(nx, ny, nz, j, k, base_jk);
-    // blocks of row (j,k,x) in order -z, -y, -x
-    auto mask_of = [&](int x) { return (hz ? 1 : 0) | (hy ? 2 : 0) | (x > 0 ? 4 : 0); };
+    auto stage = [&](int x) {
+      SL* sl = ring + x % R;
+      if (act) {
+        const int base = row_start(PEN, x);  // BSR row of cell (x, j, k): -z, -y, -x, diag, ...
+        if (hz) stage_blk<TM>(sl->blk[L.hl][0], A + (size_t)base * BB, L.h);
+        if (hy) stage_blk<TM>(sl->blk[L.hl][1], A + (size_t)(base + hz) * BB, L.h);
+        if (x > 0) stage_blk<TM>(sl->blk[L.hl][2], A + (size_t)(base + hz + hy) * BB, L.h);
+        stage_blk<TM>(sl->blk[L.hl][3], Dinv + (size_t)(base_jk + x) * BB, L.h);
+        stage_vec<RT>(sl->rhs[L.hl], rhs + (size_t)(base_jk + x) * 8, L.h);
+      }
+    };
 #pragma unroll 1
-    for (int q = 0; q < R - 1; ++q) {
-      if (q < nx) stage_cell<TM, RT>(ring + q, base_jk + q, 0, mask_of(q), PEN, A, Dinv, rhs, lane);
+    for (int x = 0; x < R - 1; ++x) {
+      if (x < nx) stage(x);
       cp_async_commit();
     }
-    T2 rz[LA], ry[LA];
-#pragma unroll
-    for (int q = 0; q < LA; ++q) {
-      if (q < nx) {
-        if (hz) rz[q] = ld_remote<TM>(y + (size_t)(base_jk + q - nxy) * 8 + c);
-        if (hy) ry[q] = ld_remote<TM>(y + (size_t)(base_jk + q - nx) * 8 + c);
+    TM vz[4], vy[4], yp[4];
+    zero4(vz), zero4(vy), zero4(yp);
+    if (hz) ld4r(y + (size_t)(base_jk - nxy) * 8, L, vz);
+    if (hy) ld4r(y + (size_t)(base_jk - nx) * 8, L, vy);
+    for (int x = 0; x < nx; ++x) {
+      const int i = base_jk + x;
+      if (x + R - 1 < nx) stage(x + R - 1);
+      cp_async_commit();
+      cp_async_wait<R - 1>();
+      __syncwarp();
+      const SL* sl = ring + x % R;
+      TM az[4], ay[4], ax[4], d[4];
+      zero4(az), zero4(ay), zero4(ax), zero4(d);
+      TM acc = TM(0);
+      if (act) {
+        if (hz) ld4s(sl->blk[L.hl][0], L, az);
+        if (hy) ld4s(sl->blk[L.hl][1], L, ay);
+        if (x > 0) ld4s(sl->blk[L.hl][2], L, ax);
+        ld4s(sl->blk[L.hl][3], L, d);
+        if (L.q == 0) acc = -(TM)sl->rhs[L.hl][L.r];
       }
-    }
-    TM yp0 = TM(0), yp1 = TM(0);
-    for (int x0 = 0; x0 < nx; x0 += LA) {
-#pragma unroll
-      for (int q = 0; q < LA; ++q) {
-        const int x = x0 + q;
-        if (x >= nx) break;
-        const int i = base_jk + x;
-        const int xs = x + R - 1;
-        if (xs < nx) stage_cell<TM, RT>(ring + xs % R, base_jk + xs, 0, mask_of(xs), PEN, A, Dinv, rhs, lane);
-        cp_async_commit();
-        cp_async_wait<R - 1>();
-        __syncwarp();
-        const Slot<TM>* sl = ring + x % R;
-        const int m = mask_of(x);
-        int b = 0;
-        T2 az = zero2<TM>(), ay = zero2<TM>(), ax = zero2<TM>();
-        if (m & 1) az = sl_pair<TM>(sl, b++, lane);
-        if (m & 2) ay = sl_pair<TM>(sl, b++, lane);
-        if (m & 4) ax = sl_pair<TM>(sl, b, lane);
-        const T2 d = sl_pair<TM>(sl, 3, lane);
-        const TM ri = (TM)reinterpret_cast<const RT*>(sl->rhs)[r];
-        TM acc = fma(ax.x, yp0, ax.y * yp1);
-        if (hz) {
-          if (!settle<TM>(y + (size_t)(i - nxy) * 8 + c, rz[q], abortf, dstatus)) {
-            cp_async_wait<0>();  // no copy of this warp is left in flight when it leaves
-            return;
-          }
-          acc = fma(az.x, rz[q].x, fma(az.y, rz[q].y, acc));
-        }
-        if (hy) {
-          if (!settle<TM>(y + (size_t)(i - nx) * 8 + c, ry[q], abortf, dstatus)) {
-            cp_async_wait<0>();  // no copy of this warp is left in flight when it leaves
-            return;
-          }
-          acc = fma(ay.x, ry[q].x, fma(ay.y, ry[q].y, acc));
-        }
-        const TM t = ri - quad_sum(acc);
-        const TM t0 = __shfl_sync(FULL, t, 4 * c), t1 = __shfl_sync(FULL, t, 4 * c + 4);
-        const TM yr = quad_sum(fma(d.x, t0, d.y * t1));
-        if ((lane & 3) == 0) st_relaxed(y + (size_t)i * 8 + r, yr);
-        yp0 = __shfl_sync(FULL, yr, 4 * c);
-        yp1 = __shfl_sync(FULL, yr, 4 * c + 4);
-        if (x + LA < nx) {
-          if (hz) rz[q] = ld_remote<TM>(y + (size_t)(i + LA - nxy) * 8 + c);
-          if (hy) ry[q] = ld_remote<TM>(y + (size_t)(i + LA - nx) * 8 + c);
-        }
-        __syncwarp();  // every lane is done with this slot before it is refilled
+      // (the addresses are formed only when the neighbour exists)
+      if (!await_nbrs<TM>(hz ? y + (size_t)(i - nxy) * 8 : y, hz, vz, hy ? y + (size_t)(i - nx) * 8 : y, hy, vy, L,
+                          abortf, dstatus)) {
+        cp_async_wait<0>();  // no copy of this warp is left in flight when it leaves
+        return;
       }
+      // row sums of A v - r: the neighbours' terms, then the x-recurrence term last
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc = fma(az[c], vz[c], acc);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc = fma(ay[c], vy[c], acc);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc = fma(ax[c], yp[c], acc);
+      const TM s = acc + __shfl_xor_sync(FULL, acc, 1);  // -t_r, t = r - A v
+      const TM n0 = __shfl_sync(FULL, s, L.s0), n1 = __shfl_sync(FULL, s, L.s0 + 2);
+      const TM n2 = __shfl_sync(FULL, s, L.s2), n3 = __shfl_sync(FULL, s, L.s2 + 2);
+      TM yr = fma(-d[0], n0, fma(-d[1], n1, fma(-d[2], n2, -d[3] * n3)));  // (D^-1 t)_r, partial
+      yr += __shfl_xor_sync(FULL, yr, 1);
+      yp[0] = __shfl_sync(FULL, yr, L.s0);
+      yp[1] = __shfl_sync(FULL, yr, L.s0 + 2);
+      yp[2] = __shfl_sync(FULL, yr, L.s2);
+      yp[3] = __shfl_sync(FULL, yr, L.s2 + 2);
+      if (act && L.h < 2) st4r(y + (size_t)i * 8, L, yp);
+      if (x + 1 < nx) {
+        if (hz) ld4r(y + (size_t)(i + 1 - nxy) * 8, L, vz);
+        if (hy) ld4r(y + (size_t)(i + 1 - nx) * 8, L, vy);
+      }
+      __syncwarp();  // every lane is done with this slot before it is refilled
     }
     cp_async_wait<0>();
     __syncwarp();
   }
 }
 
-template <typename TM, int R>
-__global__ void __launch_bounds__(AWARPS * 32) k_ilu_bwd_async(int nx, int ny, int nz, const int32_t* __restrict__ rowptr,
-                                                               const TM* __restrict__ A, const TM* __restrict__ Dinv,
-                                                               const TM* __restrict__ yin, TM* __restrict__ zs,
-                                                               double* __restrict__ z64, int* __restrict__ pipe,
-                                                               int* __restrict__ dstatus) {
-  using T2 = typename V2<TM>::t;
+// PRE: the upper blocks are the pre-scaled D^-1 A_{i,up} (array uhat, three
+// per cell in the order +x, +y, +z); otherwise the BSR upper blocks and D^-1.
+template <typename TM, int R, bool PRE>
+__global__ void __launch_bounds__(AWARPS * 32) k_sweep_bwd(int nx, int ny, int nz, const TM* __restrict__ A,
+                                                           const TM* __restrict__ Dinv, const TM* __restrict__ uhat,
+                                                           const TM* __restrict__ yin, TM* __restrict__ zs,
+                                                           double* __restrict__ z64, int* __restrict__ pipe,
+                                                           int* __restrict__ dstatus) {
+  using SL = Slot2<TM, TM>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Slot<TM>* ring = reinterpret_cast<Slot<TM>*>(smem_raw) + (threadIdx.x >> 5) * R;
-  const int lane = threadIdx.x & 31;
-  const int r = lane >> 2, c = (lane & 3) * 2;
-  const int npen = ny * nz, nxy = nx * ny;
+  SL* ring = reinterpret_cast<SL*>(smem_raw) + (threadIdx.x >> 5) * R;
+  const LaneCols L = lane_cols<TM>();
+  const int nxy = nx * ny;
   int* counter = pipe;
   int* abortf = pipe + 1;
+  Diag D;
+  diag_set(D, 0, ny, nz);
+  D.t0 = 0;
   for (;;) {
-    int g = 0;
-    if (lane == 0) g = atomicAdd(counter, 1);
-    g = __shfl_sync(FULL, g, 0);
-    if (g >= npen) return;
-    const int p = npen - 1 - g;
-    const int j = p % ny, k = p / ny;
-    const bool hy = j < ny - 1, hz = k < nz - 1;
-    const int nlow_jk = (k > 0) + (j > 0);
+    int t = 0;
+    if ((threadIdx.x & 31) == 0) t = atomicAdd(counter, 1);
+    t = __shfl_sync(FULL, t, 0);
+    if (!diag_seek(D, t, ny, nz)) return;
+    int jm, km;
+    bool act;
+    task_pencil(D, t, L.hl, jm, km, act);
+    // the backward sweep runs the mirrored grid: its dependencies point to +y and +z
+    const int j = ny - 1 - jm, k = nz - 1 - km;
+    const bool hy = act && j < ny - 1, hz = act && k < nz - 1;
+    const int nlow = (k > 0) + (j > 0);
     const int base_jk = nx * (j + ny * k);
     const Pen PEN = make_pen(nx, ny, nz, j, k, base_jk);
-    // blocks of row (j,k,x) after the diagonal in order +x, +y, +z; slot index of b is its bit
-    auto mask_of = [&](int x) { return (x < nx - 1 ? 1 : 0) | (hy ? 2 : 0) | (hz ? 4 : 0); };
-    auto first_of = [&](int x) { return nlow_jk + (x > 0) + 1; };
-#pragma unroll 1
-    for (int q = 0; q < R - 1; ++q) {
-      if (q < nx) {
-        const int x = nx - 1 - q;
-        stage_cell<TM, TM>(ring + q, base_jk + x, first_of(x), mask_of(x), PEN, A, Dinv, yin, lane);
+    auto stage = [&](int step) {
+      const int x = nx - 1 - step;
+      SL* sl = ring + step % R;
+      if (act) {
+        const int i = base_jk + x;
+        const bool hx = x < nx - 1;
+        if (PRE) {
+          const TM* u = uhat + (size_t)3 * i * BB;
+          if (hx) stage_blk<TM>(sl->blk[L.hl][0], u, L.h);
+          if (hy) stage_blk<TM>(sl->blk[L.hl][1], u + BB, L.h);
+          if (hz) stage_blk<TM>(sl->blk[L.hl][2], u + 2 * BB, L.h);
+        } else {
+          const int up = row_start(PEN, x) + nlow + (x > 0) + 1;  // first block after the diagonal
+          if (hx) stage_blk<TM>(sl->blk[L.hl][0], A + (size_t)up * BB, L.h);
+          if (hy) stage_blk<TM>(sl->blk[L.hl][1], A + (size_t)(up + hx) * BB, L.h);
+          if (hz) stage_blk<TM>(sl->blk[L.hl][2], A + (size_t)(up + hx + hy) * BB, L.h);
+          stage_blk<TM>(sl->blk[L.hl][3], Dinv + (size_t)i * BB, L.h);
+        }
+        stage_vec<TM>(sl->rhs[L.hl], yin + (size_t)i * 8, L.h);  // the forward result
       }
+    };
+#pragma unroll 1
+    for (int step = 0; step < R - 1; ++step) {
+      if (step < nx) stage(step);
       cp_async_commit();
     }
-    T2 rz[LA], ry[LA];
-#pragma unroll
-    for (int q = 0; q < LA; ++q) {
-      if (q < nx) {
-        const int x = nx - 1 - q;
-        if (hz) rz[q] = ld_remote<TM>(zs + (size_t)(base_jk + x + nxy) * 8 + c);
-        if (hy) ry[q] = ld_remote<TM>(zs + (size_t)(base_jk + x + nx) * 8 + c);
+    TM vz[4], vy[4], zp[4];  // zp: the previous cell's z (PRE: -z)
+    zero4(vz), zero4(vy), zero4(zp);
+    if (hz) ld4r(zs + (size_t)(base_jk + nx - 1 + nxy) * 8, L, vz);
+    if (hy) ld4r(zs + (size_t)(base_jk + nx - 1 + nx) * 8, L, vy);
+    for (int step = 0; step < nx; ++step) {
+      const int x = nx - 1 - step;
+      const int i = base_jk + x;
+      if (step + R - 1 < nx) stage(step + R - 1);
+      cp_async_commit();
+      cp_async_wait<R - 1>();
+      __syncwarp();
+      const SL* sl = ring + step % R;
+      TM ux[4], uy[4], uz[4], d[4];
+      zero4(ux), zero4(uy), zero4(uz), zero4(d);
+      TM yi = TM(0);
+      if (act) {
+        if (x < nx - 1) ld4s(sl->blk[L.hl][0], L, ux);
+        if (hy) ld4s(sl->blk[L.hl][1], L, uy);
+        if (hz) ld4s(sl->blk[L.hl][2], L, uz);
+        if (!PRE) ld4s(sl->blk[L.hl][3], L, d);
+        if (L.q == 0) yi = sl->rhs[L.hl][L.r];
       }
-    }
-    TM zp0 = TM(0), zp1 = TM(0);
-    for (int s0 = 0; s0 < nx; s0 += LA) {
-#pragma unroll
-      for (int q = 0; q < LA; ++q) {
-        const int step = s0 + q;
-        if (step >= nx) break;
-        const int x = nx - 1 - step;
-        const int i = base_jk + x;
-        const int ss = step + R - 1;
-        if (ss < nx)
-          stage_cell<TM, TM>(ring + ss % R, base_jk + (nx - 1 - ss), first_of(nx - 1 - ss), mask_of(nx - 1 - ss), PEN,
-                             A, Dinv, yin, lane);
-        cp_async_commit();
-        cp_async_wait<R - 1>();
-        __syncwarp();
-        const Slot<TM>* sl = ring + step % R;
-        const int m = mask_of(x);
-        int b = 0;
-        T2 ax = zero2<TM>(), ay = zero2<TM>(), az = zero2<TM>();
-        if (m & 1) ax = sl_pair<TM>(sl, b++, lane);
-        if (m & 2) ay = sl_pair<TM>(sl, b++, lane);
-        if (m & 4) az = sl_pair<TM>(sl, b, lane);
-        const T2 d = sl_pair<TM>(sl, 3, lane);
-        const TM yi = reinterpret_cast<const TM*>(sl->rhs)[r];  // the forward result, staged with the blocks
-        TM acc = fma(ax.x, zp0, ax.y * zp1);
-        if (hz) {
-          if (!settle<TM>(zs + (size_t)(i + nxy) * 8 + c, rz[q], abortf, dstatus)) {
-            cp_async_wait<0>();  // no copy of this warp is left in flight when it leaves
-            return;
-          }
-          acc = fma(az.x, rz[q].x, fma(az.y, rz[q].y, acc));
-        }
-        if (hy) {
-          if (!settle<TM>(zs + (size_t)(i + nx) * 8 + c, ry[q], abortf, dstatus)) {
-            cp_async_wait<0>();  // no copy of this warp is left in flight when it leaves
-            return;
-          }
-          acc = fma(ay.x, ry[q].x, fma(ay.y, ry[q].y, acc));
-        }
-        const TM sr = quad_sum(acc);
-        const TM s_0 = __shfl_sync(FULL, sr, 4 * c), s_1 = __shfl_sync(FULL, sr, 4 * c + 4);
-        const TM zr = yi - quad_sum(fma(d.x, s_0, d.y * s_1));
-        if ((lane & 3) == 0) {
-          st_relaxed(zs + (size_t)i * 8 + r, zr);
-          if (z64) z64[(size_t)i * 8 + r] = (double)zr;
-        }
-        zp0 = __shfl_sync(FULL, zr, 4 * c);
-        zp1 = __shfl_sync(FULL, zr, 4 * c + 4);
-        if (step + LA < nx) {
-          if (hz) rz[q] = ld_remote<TM>(zs + (size_t)(i - LA + nxy) * 8 + c);
-          if (hy) ry[q] = ld_remote<TM>(zs + (size_t)(i - LA + nx) * 8 + c);
-        }
-        __syncwarp();
+      if (!await_nbrs<TM>(hz ? zs + (size_t)(i + nxy) * 8 : zs, hz, vz, hy ? zs + (size_t)(i + nx) * 8 : zs, hy, vy,
+                          L, abortf, dstatus)) {
+        cp_async_wait<0>();  // no copy of this warp is left in flight when it leaves
+        return;
       }
+      TM acc = PRE ? -yi : TM(0);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc = fma(uz[c], vz[c], acc);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc = fma(uy[c], vy[c], acc);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc = fma(PRE ? -ux[c] : ux[c], zp[c], acc);
+      TM sr = acc + __shfl_xor_sync(FULL, acc, 1);  // PRE: -z_r; else (U z)_r
+      if (!PRE) {
+        const TM t0 = __shfl_sync(FULL, sr, L.s0), t1 = __shfl_sync(FULL, sr, L.s0 + 2);
+        const TM t2 = __shfl_sync(FULL, sr, L.s2), t3 = __shfl_sync(FULL, sr, L.s2 + 2);
+        const TM zr = fma(-d[0], t0, fma(-d[1], t1, fma(-d[2], t2, fma(-d[3], t3, yi))));  // y - D^-1 U z, partial
+        sr = zr + __shfl_xor_sync(FULL, zr, 1);
+      }
+      zp[0] = __shfl_sync(FULL, sr, L.s0);
+      zp[1] = __shfl_sync(FULL, sr, L.s0 + 2);
+      zp[2] = __shfl_sync(FULL, sr, L.s2);
+      zp[3] = __shfl_sync(FULL, sr, L.s2 + 2);
+      if (act && L.h < 2) {
+        TM zo[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) zo[c] = PRE ? neg_bits(zp[c]) : zp[c];
+        st4r(zs + (size_t)i * 8, L, zo);
+        if (z64) {
+          z64[(size_t)i * 8 + L.e0] = (double)zo[0];
+          z64[(size_t)i * 8 + L.e0 + 1] = (double)zo[1];
+          z64[(size_t)i * 8 + L.e2] = (double)zo[2];
+          z64[(size_t)i * 8 + L.e2 + 1] = (double)zo[3];
+        }
+      }
+      if (step + 1 < nx) {
+        if (hz) ld4r(zs + (size_t)(i - 1 + nxy) * 8, L, vz);
+        if (hy) ld4r(zs + (size_t)(i - 1 + nx) * 8, L, vy);
+      }
+      __syncwarp();
     }
     cp_async_wait<0>();
     __syncwarp();
@@ -456,7 +579,8 @@ template <typename T>
 __global__ void __launch_bounds__(FWARPS * 32) k_ilu_factor_pipe(int nx, int ny, int nz,
                                                                  const int32_t* __restrict__ rowptr,
                                                                  const T* __restrict__ A, T* __restrict__ Dinv,
-                                                                 int* __restrict__ pipe, int* __restrict__ dstatus) {
+                                                                 T* __restrict__ uhat, int* __restrict__ pipe,
+                                                                 int* __restrict__ dstatus) {
   using T2 = typename V2<T>::t;
   __shared__ T sm[FWARPS][6][64];
   const int lane = threadIdx.x & 31;
@@ -519,6 +643,13 @@ __global__ void __launch_bounds__(FWARPS * 32) k_ilu_factor_pipe(int nx, int ny,
         __syncwarp();
         sU[r * 8 + c] = m0;  // reuse sU for M
         sU[r * 8 + c + 1] = m1;
+        // M = D_k^-1 A_ki is the pre-scaled upper block of row k towards i (+z, +y, +x for
+        // dl = 0, 1, 2), which the backward sweep applies without D^-1
+        if (uhat) {
+          T* u = uhat + ((size_t)3 * kk + (2 - dl)) * BB + r * 8 + c;
+          u[0] = m0;
+          u[1] = m1;
+        }
         __syncwarp();
         T s0 = T(0), s1 = T(0);
 #pragma unroll
@@ -603,8 +734,9 @@ __global__ void __launch_bounds__(FWARPS * 32) k_ilu_factor_pipe(int nx, int ny,
 
 }  // namespace
 
-// Factor the decoupled blocks: FP64 into dinv, or under mixed precision FP32
-// from the FP32 copy of the blocks (J32, written first) into dinv32.
+// Factor the decoupled blocks: FP64 into dinv (and the pre-scaled upper blocks
+// into uhat), or under mixed precision FP32 from the FP32 copy of the blocks
+// (J32, written first) into dinv32 and uhat32.
 void launch_ilu_factor_pipe(Handle& h, cudaStream_t s) {
   const int npen = h.ny * h.nz;
   // up to 32 warps per SM (38 registers, 12 KB of shared memory per 4-warp block):
@@ -615,93 +747,97 @@ void launch_ilu_factor_pipe(Handle& h, cudaStream_t s) {
   if (h.opt.precision != ISC_PRECISION_FP64) {
     launch_to_f32((size_t)h.nnzb * BB, h.J, h.J32, s);
     cudaMemsetAsync(h.dinv32, 0xff, sizeof(float) * (size_t)h.n * BB, s);  // NaN sentinel
-    k_ilu_factor_pipe<float><<<blocks, FWARPS * 32, 0, s>>>(h.nx, h.ny, h.nz, h.rowptr, h.J32, h.dinv32, h.pipe,
-                                                            h.dstatus);
+    k_ilu_factor_pipe<float><<<blocks, FWARPS * 32, 0, s>>>(h.nx, h.ny, h.nz, h.rowptr, h.J32, h.dinv32, h.uhat32,
+                                                            h.pipe, h.dstatus);
     return;
   }
   cudaMemsetAsync(h.dinv, 0xff, sizeof(double) * (size_t)h.n * BB, s);  // NaN sentinel
-  k_ilu_factor_pipe<double><<<blocks, FWARPS * 32, 0, s>>>(h.nx, h.ny, h.nz, h.rowptr, h.J, h.dinv, h.pipe,
+  k_ilu_factor_pipe<double><<<blocks, FWARPS * 32, 0, s>>>(h.nx, h.ny, h.nz, h.rowptr, h.J, h.dinv, h.uhat, h.pipe,
                                                            h.dstatus);
 }
 
-// cells staged in each warp's shared-memory ring: 4 keeps an FP64 warp at 8.4 KB, so 24
-// warps fit on an SM; with 8 an 8-warp block took 135 KB, one per SM, and 3,000 pencils
-// (100x100x30) ran in two rounds (sweep pair 1.13 against 0.89 ms; equal at 60x60x20)
+namespace {
+
+// cells staged in each warp's shared-memory ring
 constexpr int SWEEP_R = 4;
 
-// resident warps per SM: 24 for the FP64 sweeps (registers and the 68 KB rings), 32 for
-// the FP32 ones (35 KB rings, fewer registers)
-template <typename TM>
-int sweep_blocks(int npen) {
-  constexpr int per_sm = sizeof(TM) == 8 ? 24 : 32;
-  const int warps = npen < 152 * per_sm ? npen : 152 * per_sm;
-  return (warps + AWARPS - 1) / AWARPS;
-}
-
-template <typename TM>
+template <typename TM, typename RT>
 size_t sweep_smem() {
-  return sizeof(Slot<TM>) * SWEEP_R * AWARPS;
+  return sizeof(Slot2<TM, RT>) * SWEEP_R * AWARPS;
 }
 
-template <typename TM>
-cudaError_t sweep_attributes() {
+// tasks of the anti-diagonal map: ceil(len/2) per diagonal of the ny x nz pencil grid
+int sweep_tasks(int ny, int nz) {
+  int t = 0;
+  for (int d = 0; d <= ny + nz - 2; ++d) {
+    const int jlo = d - (nz - 1) > 0 ? d - (nz - 1) : 0;
+    const int jhi = d < ny - 1 ? d : ny - 1;
+    t += (jhi - jlo + 2) / 2;
+  }
+  return t;
+}
+
+// Persistent grid: no more warps than tasks, and no more blocks than fit on
+// the device at once (resident blocks from the occupancy calculator).
+template <typename K>
+int sweep_blocks(K kernel, size_t smem, int tasks) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, AWARPS * 32, smem);
+  if (per_sm < 1) per_sm = 1;
+  const int need = (tasks + AWARPS - 1) / AWARPS;
+  return need < per_sm * sms ? need : per_sm * sms;
+}
+
+template <typename TM, typename RT>
+cudaError_t launch_fwd(int nx, int ny, int nz, const TM* A, const TM* Dinv, const RT* r, TM* y, int* pipe,
+                       int* dstatus, cudaStream_t s) {
+  auto kern = k_sweep_fwd<TM, SWEEP_R, RT>;
+  const size_t smem = sweep_smem<TM, RT>();
   // idempotent; the rings need more than the default 48 KB of dynamic shared memory
-  cudaError_t e = cudaFuncSetAttribute(k_ilu_fwd_async<TM, SWEEP_R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sweep_smem<TM>());
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_ilu_fwd_async<TM, SWEEP_R, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sweep_smem<TM>());
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_ilu_bwd_async<TM, SWEEP_R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sweep_smem<TM>());
-  return e;
-}
-
-// Forward and backward sweep on the stream; returns the first error of the
-// attribute calls, the clears or the launches (cudaSuccess if all were issued).
-template <typename TM>
-cudaError_t sweep_pair(int nx, int ny, int nz, const int32_t* rowptr, const TM* A, const TM* Dinv, const double* r,
-                       TM* y, TM* zs, double* z64, int* pipe, int* dstatus, cudaStream_t s) {
-  const size_t n8 = (size_t)nx * ny * nz * 8;
-  const int blocks = sweep_blocks<TM>(ny * nz);
-  const size_t smem = sweep_smem<TM>();
-  cudaError_t e = sweep_attributes<TM>();
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess) e = cudaMemsetAsync(pipe, 0, 2 * sizeof(int), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(y, 0xff, sizeof(TM) * n8, s);  // NaN sentinel
+  if (e == cudaSuccess) e = cudaMemsetAsync(y, 0xff, sizeof(TM) * (size_t)nx * ny * nz * 8, s);  // NaN sentinel
   if (e != cudaSuccess) return e;
-  k_ilu_fwd_async<TM, SWEEP_R><<<blocks, AWARPS * 32, smem, s>>>(nx, ny, nz, rowptr, A, Dinv, r, y, pipe, dstatus);
-  e = cudaGetLastError();
-  if (e == cudaSuccess) e = cudaMemsetAsync(pipe, 0, 2 * sizeof(int), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(zs, 0xff, sizeof(TM) * n8, s);
-  if (e != cudaSuccess) return e;
-  k_ilu_bwd_async<TM, SWEEP_R><<<blocks, AWARPS * 32, smem, s>>>(nx, ny, nz, rowptr, A, Dinv, y, zs, z64, pipe,
-                                                                 dstatus);
+  kern<<<sweep_blocks(kern, smem, sweep_tasks(ny, nz)), AWARPS * 32, smem, s>>>(nx, ny, nz, A, Dinv, r, y, pipe,
+                                                                                  dstatus);
   return cudaGetLastError();
 }
 
+template <typename TM, bool PRE>
+cudaError_t launch_bwd(int nx, int ny, int nz, const TM* A, const TM* Dinv, const TM* uhat, const TM* y, TM* z,
+                       double* z64, int* pipe, int* dstatus, cudaStream_t s) {
+  auto kern = k_sweep_bwd<TM, SWEEP_R, PRE>;
+  const size_t smem = sweep_smem<TM, TM>();
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) e = cudaMemsetAsync(pipe, 0, 2 * sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(z, 0xff, sizeof(TM) * (size_t)nx * ny * nz * 8, s);  // NaN sentinel
+  if (e != cudaSuccess) return e;
+  kern<<<sweep_blocks(kern, smem, sweep_tasks(ny, nz)), AWARPS * 32, smem, s>>>(nx, ny, nz, A, Dinv, uhat, y, z,
+                                                                                  z64, pipe, dstatus);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
 // FP32 in, FP32 out (inner solve of ISC_PRECISION_MIXED_FGMRES): y in vec32, z written as the hand-off vector
 void launch_ilu_apply_f32(Handle& h, const float* r, float* z, cudaStream_t s) {
-  const size_t n8 = (size_t)h.n * 8;
-  const int blocks = sweep_blocks<float>(h.ny * h.nz);
-  const size_t smem = sweep_smem<float>();
-  sweep_attributes<float>();
-  cudaMemsetAsync(h.pipe, 0, 2 * sizeof(int), s);
-  cudaMemsetAsync(h.vec32, 0xff, sizeof(float) * n8, s);  // NaN sentinel
-  k_ilu_fwd_async<float, SWEEP_R, float><<<blocks, AWARPS * 32, smem, s>>>(h.nx, h.ny, h.nz, h.rowptr, h.J32, h.dinv32,
-                                                                           r, h.vec32, h.pipe, h.dstatus);
-  cudaMemsetAsync(h.pipe, 0, 2 * sizeof(int), s);
-  cudaMemsetAsync(z, 0xff, sizeof(float) * n8, s);
-  k_ilu_bwd_async<float, SWEEP_R><<<blocks, AWARPS * 32, smem, s>>>(h.nx, h.ny, h.nz, h.rowptr, h.J32, h.dinv32, h.vec32,
-                                                                    z, nullptr, h.pipe, h.dstatus);
+  launch_fwd<float, float>(h.nx, h.ny, h.nz, h.J32, h.dinv32, r, h.vec32, h.pipe, h.dstatus, s);
+  launch_bwd<float, true>(h.nx, h.ny, h.nz, h.J32, h.dinv32, h.uhat32, h.vec32, z, nullptr, h.pipe, h.dstatus, s);
 }
 
 void launch_ilu_apply_pipe(Handle& h, const double* r, double* z, cudaStream_t s) {
   if (h.opt.precision != ISC_PRECISION_FP64) {
+    // FP64 right-hand side in, FP32 sweeps, FP64 result out
     const size_t n8 = (size_t)h.n * 8;
-    sweep_pair<float>(h.nx, h.ny, h.nz, h.rowptr, h.J32, h.dinv32, r, h.vec32, h.vec32 + n8, z, h.pipe, h.dstatus, s);
+    launch_fwd<float, double>(h.nx, h.ny, h.nz, h.J32, h.dinv32, r, h.vec32, h.pipe, h.dstatus, s);
+    launch_bwd<float, true>(h.nx, h.ny, h.nz, h.J32, h.dinv32, h.uhat32, h.vec32, h.vec32 + n8, z, h.pipe, h.dstatus,
+                            s);
     return;
   }
-  sweep_pair<double>(h.nx, h.ny, h.nz, h.rowptr, h.J, h.dinv, r, h.tmp, z, nullptr, h.pipe, h.dstatus, s);
+  launch_fwd<double, double>(h.nx, h.ny, h.nz, h.J, h.dinv, r, h.tmp, h.pipe, h.dstatus, s);
+  launch_bwd<double, true>(h.nx, h.ny, h.nz, h.J, h.dinv, h.uhat, h.tmp, z, nullptr, h.pipe, h.dstatus, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -764,15 +900,18 @@ extern "C" int isc_check_bounded_wait(void) {
               cudaMemset(d_A, 0, sizeof(double) * (size_t)nnzb * BB) == cudaSuccess &&
               cudaMemcpy(d_D, dinv.data(), sizeof(double) * (size_t)n * BB, cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemset(d_r, 0, sizeof(double) * (size_t)n * 8) == cudaSuccess &&
-              // NaN sentinel: nothing arrives from pencil 0
-              cudaMemset(d_y, 0xff, sizeof(double) * (size_t)n * 8) == cudaSuccess &&
-              cudaMemcpy(d_ints, h_ints, sizeof(h_ints), cudaMemcpyHostToDevice) == cudaSuccess &&
-              sweep_attributes<double>() == cudaSuccess;
+              cudaMemcpy(d_ints, h_ints, sizeof(h_ints), cudaMemcpyHostToDevice) == cudaSuccess;
     if (ok) {
-      const size_t smem = sweep_smem<double>();
-      k_ilu_fwd_async<double, SWEEP_R><<<1, AWARPS * 32, smem>>>(nx, ny, nz, d_rp, d_A, d_D, d_r, d_y, d_ints,
-                                                                  d_ints + 2);
-      ok = cudaGetLastError() == cudaSuccess;
+      // the forward sweep, its counter then moved past task 0 (pencil 0 of the 4x4x1 grid):
+      // pencil 1 waits for values that never arrive
+      auto kern = k_sweep_fwd<double, SWEEP_R, double>;
+      const size_t smem = sweep_smem<double, double>();
+      ok = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess &&
+           cudaMemset(d_y, 0xff, sizeof(double) * (size_t)n * 8) == cudaSuccess;  // NaN sentinel
+      if (ok) {
+        kern<<<1, AWARPS * 32, smem>>>(nx, ny, nz, d_A, d_D, d_r, d_y, d_ints, d_ints + 2);
+        ok = cudaGetLastError() == cudaSuccess;
+      }
     }
     int h_status = 0;
     // a set-up or launch failure is ISC_ERR_CUDA, never the "no timeout" answer
@@ -809,7 +948,9 @@ extern "C" int isc_bilu0_apply_noalloc(int32_t nx, int32_t ny, int32_t nz, const
   // everything that must start at zero (or NaN) is cleared inside: the array
   // keeps the previous call's contents
   if (cudaMemsetAsync(ints, 0, NOALLOC_INTS * sizeof(int), s) != cudaSuccess) return ISC_ERR_CUDA;
-  if (sweep_pair<double>(nx, ny, nz, d_rowptr, d_A, d_Dinv, d_r, y, d_z, nullptr, pipe, status, s) != cudaSuccess)
+  // the caller gives D^-1 and the BSR blocks only: the backward sweep applies D^-1 itself
+  if (launch_fwd<double, double>(nx, ny, nz, d_A, d_Dinv, d_r, y, pipe, status, s) != cudaSuccess ||
+      launch_bwd<double, false>(nx, ny, nz, d_A, d_Dinv, nullptr, y, d_z, nullptr, pipe, status, s) != cudaSuccess)
     return ISC_ERR_CUDA;
   int h_status = 0;
   if (cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return ISC_ERR_CUDA;

@@ -210,8 +210,10 @@ struct Handle {
   double* du = nullptr;                           // Newton update, block-major 8N
   double* rhs = nullptr;                          // -F, right-hand side of the solve
   double* dinv = nullptr;                         // preconditioner diagonal inverses N*64
+  double* uhat = nullptr;                         // ILU(0): pre-scaled upper blocks D_i^-1 A_{i,up}, 3 per cell (+x, +y, +z)
   float* J32 = nullptr;                           // mixed precision: FP32 copy of the decoupled blocks
   float* dinv32 = nullptr;                        // mixed precision: FP32 D^-1
+  float* uhat32 = nullptr;                        // mixed precision: FP32 pre-scaled upper blocks
   float* vec32 = nullptr;                         // mixed precision: 2 x 8N FP32 sweep vectors
   // Krylov workspace
   double* V = nullptr;                            // (restart+1) vectors of 8N

@@ -140,11 +140,15 @@ _SIGS = {
     "isc_get_residual": (C.c_int, [C.c_void_p, c_double_p]),
     "isc_get_jacobian_bsr": (C.c_int, [C.c_void_p, c_int32_p, c_int32_p, c_double_p]),
     "isc_get_update": (C.c_int, [C.c_void_p, c_double_p]),
+    "isc_set_system": (C.c_int, [C.c_void_p, c_double_p, c_double_p, C.c_int32]),
+    "isc_solve_external": (C.c_int, [C.c_void_p, c_int32_p, c_int32_p, c_double_p, c_double_p, c_double_p,
+                                     C.POINTER(isc_newton_info)]),
     "isc_get_coke": (C.c_int, [C.c_void_p, c_double_p]),
     "isc_spmv": (C.c_int, [C.c_void_p, c_double_p, c_double_p]),
     "isc_build_preconditioner": (C.c_int, [C.c_void_p]),
     "isc_precond_apply": (C.c_int, [C.c_void_p, c_double_p, c_double_p]),
     "isc_get_stats": (C.c_int, [C.c_void_p, C.POINTER(isc_stats)]),
+    "isc_get_ilu_diag": (C.c_int, [C.c_void_p, c_double_p]),
     "isc_reset_stats": (C.c_int, [C.c_void_p]),
     "isc_bsr_spmv_device": (C.c_int, [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                       C.c_int32, C.c_void_p]),
@@ -381,6 +385,25 @@ class Simulator:
         self._check(self.lib.isc_get_update(self.h, _dp(du)))
         return du.T.copy()
 
+    def set_system(self, val, F, decoupled=False):
+        """Load a caller's system: val (nnzb, 8, 8) blocks on this handle's
+        pattern and F (8, N) residual (the solve targets J du = -F)."""
+        v = np.ascontiguousarray(val, np.float64).reshape(self.nnzb, 8, 8)
+        f = np.ascontiguousarray(np.asarray(F, np.float64).reshape(8, self.n).T)
+        self._check(self.lib.isc_set_system(self.h, _dp(v), _dp(f), 1 if decoupled else 0))
+
+    def solve_external(self, rowptr, col, val, b):
+        """x with A x = b for a caller's BSR matrix on this handle's pattern
+        (b and x as (8, N)); returns (x, isc_newton_info)."""
+        rp = np.ascontiguousarray(rowptr, np.int32)
+        cl = np.ascontiguousarray(col, np.int32)
+        v = np.ascontiguousarray(val, np.float64).reshape(self.nnzb, 8, 8)
+        bb = np.ascontiguousarray(np.asarray(b, np.float64).reshape(8, self.n).T)
+        x = np.empty((self.n, 8))
+        info = isc_newton_info()
+        self._check(self.lib.isc_solve_external(self.h, _ip(rp), _ip(cl), _dp(v), _dp(bb), _dp(x), C.byref(info)))
+        return x.T.copy(), info
+
     def coke(self):
         c = np.empty(self.n)
         self._check(self.lib.isc_get_coke(self.h, _dp(c)))
@@ -405,6 +428,12 @@ class Simulator:
         z = np.empty((self.n, 8))
         self._check(self.lib.isc_precond_apply(self.h, _dp(rb), _dp(z)))
         return z.T.copy()
+
+    def ilu_diag(self):
+        """(N, 8, 8) inverted diagonal blocks of the block ILU(0) factors."""
+        d = np.empty((self.n, 8, 8))
+        self._check(self.lib.isc_get_ilu_diag(self.h, _dp(d)))
+        return d
 
     def stats(self):
         s = isc_stats()
