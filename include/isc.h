@@ -250,6 +250,19 @@ const char* isc_last_error(const struct isc_handle* h);
 int32_t isc_num_cells(const struct isc_handle* h);
 int32_t isc_nnzb(const struct isc_handle* h);
 
+/* Heat loss to the overburden and underburden (Sec. 2.1, the last term of the
+ * energy equation, Q_loss = A K_ob ((T(ob) - T_ini)/d - rho); it enters the
+ * discrete energy residual of Sec. 3.1 as an outflow). Reading: every cell of
+ * the top layer (k = 0, faces bit 1) and / or of the bottom layer (k = nz - 1,
+ * faces bit 2) loses A K_ob ((T - T_ini)/d - rho) watts through its horizontal
+ * face (A = dx dy) by conduction into a confining layer of thickness d (m,
+ * > 0) and conductivity K_ob (W/m/K, >= 0) whose far side stays at T_ini (K);
+ * T(ob), the interface temperature, is the cell's temperature and rho (K/m)
+ * the paper's fitted offset. faces = 0 (the default at isc_create) switches
+ * it off. Takes effect at the next assembly. ISC_ERR_INVALID_ARG on
+ * non-finite or out-of-range values. */
+int isc_set_heat_loss(struct isc_handle* h, double K_ob, double d, double T_ini, double rho, int32_t faces);
+
 /* ---------------------------------------------------------------- state */
 
 /* Initial-state recipe: uniform p0, T0, S_w0, S_o0 (S_g = 1 - S_w0 - S_o0),

@@ -187,6 +187,9 @@ class Case:
     t_end: float
     n_steps: int
     dt0: float
+    # heat loss to the overburden / underburden: None, or dict(K_ob W/m/K, d m,
+    # T_ini K, rho K/m, faces: 1 top layer (k = 0), 2 bottom layer (k = nz - 1), 3 both)
+    heat_loss: dict = None
 
     @property
     def n(self) -> int:
@@ -353,6 +356,20 @@ def with_coupled_producer(case: Case, control: int, target: float, bhp_init: flo
             w.bhp_init = bhp_init
         wells.append(w)
     c.wells = wells
+    return c
+
+
+# heat loss of the workloads that enable it: shale cap and base rock conducting
+# 1.7 W/m/K over a 10 m layer back to the initial 300 K, no fitted offset
+HEAT_LOSS = dict(K_ob=1.7, d=10.0, T_ini=300.0, rho=0.0, faces=3)
+
+
+def with_heat_loss(case: Case, **kw) -> Case:
+    """A copy of the case with heat loss to the overburden and underburden
+    (HEAT_LOSS, with any entry overridden by keyword)."""
+    import copy
+    c = copy.copy(case)
+    c.heat_loss = dict(HEAT_LOSS, **kw)
     return c
 
 

@@ -478,10 +478,28 @@ def residual(case, u, coke_old, acc_old, dt, geom=None, return_coke=False, bhp=N
             if st[r, c] != 0.0:
                 F[c] -= V * st[r, c] * rate
         F[6] -= V * case.reactions["dH"][r] * rate
+    F[6] += heat_loss(case, bp["T"])
     F[7] = sum(y) - 1.0
     if return_coke:
         return F, coke
     return F
+
+
+def heat_loss(case, T):
+    """Heat lost to the overburden and underburden (Sec. 2.1, last term of the
+    energy equation; + V Q_loss in the discrete energy residual of Sec. 3.1).
+    Reading: the loss leaves through the horizontal face (area A = dx dy) of
+    every cell of the top layer (k = 0) and / or the bottom layer (k = nz - 1)
+    by conduction, K_ob ((T(ob) - T_ini)/d - rho) per unit area, into a
+    confining layer of thickness d whose far side stays at the initial
+    temperature T_ini; T(ob), the temperature at the interface, is the cell's
+    temperature and rho the fitted offset (K/m). Returns W per cell (N,)."""
+    hl = getattr(case, "heat_loss", None)
+    if not hl:
+        return np.zeros(case.n, dtype=T.dtype)
+    k = np.arange(case.n) // (case.nx * case.ny)
+    nfaces = ((k == 0) & bool(hl["faces"] & 1)).astype(float) + ((k == case.nz - 1) & bool(hl["faces"] & 2))
+    return nfaces * (case.dx * case.dy * hl["K_ob"]) * ((T - hl["T_ini"]) / hl["d"] - hl["rho"])
 
 
 # ------------------------------------------------------------------ Jacobian

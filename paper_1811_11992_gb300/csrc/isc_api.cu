@@ -800,6 +800,7 @@ int isc_create(const isc_grid* grid, const isc_rock* rock, const isc_fluid* fl, 
   h->face_area[0] = grid->dy * grid->dz / grid->dx;
   h->face_area[1] = grid->dx * grid->dz / grid->dy;
   h->face_area[2] = grid->dx * grid->dy / grid->dz;
+  h->area_xy = grid->dx * grid->dy;
   for (int r = 0; r < rx->nr; ++r) {
     h->h_Ea[r] = rx->Ea[r];
     h->h_lnA[r] = log(rx->A[r]);
@@ -1238,6 +1239,19 @@ int isc_timestep(isc_handle* h, double dt, isc_step_info* info) {
   if (st == ISC_OK) st = set_err(h, ISC_ERR_NEWTON_NOCONV, "Newton did not converge within maxit_newton");
   info->status = st;
   return st;
+}
+
+int isc_set_heat_loss(isc_handle* h, double K_ob, double d, double T_ini, double rho, int32_t faces) {
+  if (!h || !(K_ob >= 0.0) || !(d > 0.0) || !(T_ini > 0.0) || !isfinite(K_ob) || !isfinite(d) || !isfinite(rho) ||
+      faces < 0 || faces > 3)
+    return ISC_ERR_INVALID_ARG;
+  h->P.hl_AK = (faces == 0) ? 0.0 : h->area_xy * K_ob;
+  h->P.hl_inv_d = 1.0 / d;
+  h->P.hl_Tini = T_ini;
+  h->P.hl_rho = rho;
+  h->P.hl_faces = faces;
+  h->assembled = h->decoupled = h->prec_built = false;  // the next residual includes it
+  return ISC_OK;
 }
 
 int isc_set_system(isc_handle* h, const double* val, const double* F, int32_t decoupled) {

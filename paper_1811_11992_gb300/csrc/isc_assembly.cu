@@ -148,6 +148,12 @@ __global__ void __launch_bounds__(128) k_props(Params P, const double* __restric
       }
     }
   }
+  // heat loss through the top and / or bottom face of a boundary-layer cell (Sec. 2.1 energy equation)
+  if (P.hl_AK != 0.0) {
+    const int iz = i / (P.nx * P.ny);
+    const int nf = ((iz == 0 && (P.hl_faces & 1)) ? 1 : 0) + ((iz == P.nz - 1 && (P.hl_faces & 2)) ? 1 : 0);
+    if (nf) Rl[6] = Rl[6] + (nf * P.hl_AK) * ((b.T - P.hl_Tini) * P.hl_inv_d - P.hl_rho);
+  }
   D8 sy = b.y[0] + b.y[1] + b.y[2] + b.y[3] + b.y[4] + b.y[5];
   Rl[7] = sy - 1.0;
   // residual (block-major) and diagonal block

@@ -80,6 +80,10 @@ struct Params {
   double stoich[ISC_MAX_RXN][7];
   double A[ISC_MAX_RXN], EaR[ISC_MAX_RXN], dH[ISC_MAX_RXN];
   double coke_max;
+  // heat loss to the overburden / underburden: per boundary face A K_ob ((T - T_ini)/d - rho)
+  double hl_AK;               // dx dy K_ob (0: no heat loss)
+  double hl_inv_d, hl_Tini, hl_rho;
+  int hl_faces;               // 1: top layer (k = 0), 2: bottom layer (k = nz - 1)
   // convergence scaling
   double cv_scale;            // rock volumetric heat capacity for the energy norm
 };
@@ -195,6 +199,7 @@ struct Handle {
   std::vector<WellSlot> h_slots;
   std::vector<WellInfo> h_wells;
   double face_area[3] = {0, 0, 0};                 // A/h of x, y, z faces
+  double area_xy = 0.0;                            // dx dy: a cell's top / bottom face
   double h_Ea[ISC_MAX_RXN] = {}, h_lnA[ISC_MAX_RXN] = {};  // current reaction parameters
   AdjointWork adj;
   CprWork cpr;

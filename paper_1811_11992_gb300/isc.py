@@ -141,6 +141,7 @@ _SIGS = {
     "isc_get_jacobian_bsr": (C.c_int, [C.c_void_p, c_int32_p, c_int32_p, c_double_p]),
     "isc_get_update": (C.c_int, [C.c_void_p, c_double_p]),
     "isc_set_system": (C.c_int, [C.c_void_p, c_double_p, c_double_p, C.c_int32]),
+    "isc_set_heat_loss": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int32]),
     "isc_solve_external": (C.c_int, [C.c_void_p, c_int32_p, c_int32_p, c_double_p, c_double_p, c_double_p,
                                      C.POINTER(isc_newton_info)]),
     "isc_get_coke": (C.c_int, [C.c_void_p, c_double_p]),
@@ -282,6 +283,9 @@ class Simulator:
         self.h = h
         self.nnzb = lib.isc_nnzb(h)
         self.nwc = lib.isc_num_coupled_wells(h)
+        hl = getattr(case, "heat_loss", None)
+        if hl:
+            self.set_heat_loss(**hl)
 
     def _k(self, a):
         self._keep.append(a)
@@ -302,6 +306,10 @@ class Simulator:
             self.close()
         except Exception:
             pass
+
+    def set_heat_loss(self, K_ob, d, T_ini, rho=0.0, faces=3):
+        """Heat loss to the overburden (faces bit 1) and underburden (bit 2)."""
+        self._check(self.lib.isc_set_heat_loss(self.h, float(K_ob), float(d), float(T_ini), float(rho), int(faces)))
 
     # ------------------------------------------------------------- options
     def set_options(self, **kw):
