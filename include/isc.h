@@ -501,6 +501,20 @@ typedef struct isc_adjoint_info {
 int isc_adjoint(struct isc_handle* h, const isc_adjoint_spec* spec, double* loss, double* g_log_k,
                 double* g_Ea, double* g_lnA, isc_adjoint_info* info);
 
+/* The two halves of isc_adjoint, for callers that want the loss now and its
+ * gradient later (the backward pass of an automatic-differentiation framework).
+ * isc_adjoint_forward runs the time loop exactly as isc_adjoint does, returns
+ * L and keeps the checkpoints on the device; it computes no gradient.
+ * isc_adjoint_backward then runs the reverse sweep over those checkpoints
+ * (recomputing each segment), writes the gradients like isc_adjoint (any
+ * pointer may be NULL) and leaves the handle at the loop's final state; it
+ * may be repeated. ISC_ERR_STATE if no forward sweep is stored, or if
+ * isc_set_parameters, isc_set_options or isc_set_heat_loss changed the model
+ * since (a forward sweep must then be run again). The step sizes, checkpoint
+ * interval and tol_adjoint of the forward's spec are kept with the store. */
+int isc_adjoint_forward(struct isc_handle* h, const isc_adjoint_spec* spec, double* loss, isc_adjoint_info* info);
+int isc_adjoint_backward(struct isc_handle* h, double* g_log_k, double* g_Ea, double* g_lnA, isc_adjoint_info* info);
+
 #ifdef __cplusplus
 }
 #endif

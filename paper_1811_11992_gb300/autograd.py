@@ -1,13 +1,16 @@
-"""torch.autograd bridge of the discrete adjoint (isc_adjoint).
+"""torch.autograd bridge of the discrete adjoint (isc_adjoint_forward /
+isc_adjoint_backward).
 
 ``oil_production(sim, dts, log_k, Ea, lnA)`` returns the cumulative produced
 oil mass L (kg) of the implicit-Euler loop with the frozen step sizes ``dts``
 as a 0-d float64 tensor that is differentiable with respect to the per-cell
-ln k multipliers and the reactions' E_a and ln A. The time loop and its
-reverse sweep run in libisc; this module only moves the parameters and the
-gradients between torch tensors and the C ABI. When any input requires a
-gradient, the gradient is computed together with L in the forward call (one
-forward sweep plus one reverse sweep) and ``backward`` scales it.
+ln k multipliers and the reactions' E_a and ln A. ``forward`` runs the time
+loop in libisc and keeps its checkpoints on the device (the loss only);
+``backward`` runs the reverse sweep (one transposed solve per step, segments
+recomputed from their checkpoints) and scales the gradient by the incoming
+one. This module only moves the parameters and the gradients between torch
+tensors and the C ABI. The handle must not get new parameters or options
+between the two calls (the library then refuses the reverse sweep).
 """
 from __future__ import annotations
 
@@ -29,20 +32,21 @@ class CumulativeOilProduction(torch.autograd.Function):
             u0, c0 = initial_state
             sim.set_state(u0, c0)
             sim.begin_step()
-        want = any(ctx.needs_input_grad[:3])
-        L, gk, ge, ga, info = sim.adjoint(dts, checkpoint_every, tol_adjoint, gradient=want)
+        L, info = sim.adjoint_forward(dts, checkpoint_every, tol_adjoint)
+        ctx.sim = sim
         ctx.info = info
-        if want:
-            dev = log_k.device
-            ctx.save_for_backward(torch.from_numpy(gk).to(dev), torch.from_numpy(ge).to(Ea.device),
-                                  torch.from_numpy(ga).to(lnA.device))
+        ctx.devices = (log_k.device, Ea.device, lnA.device)
         return torch.tensor(L, dtype=torch.float64, device=log_k.device)
 
     @staticmethod
     def backward(ctx, gL):
-        gk, ge, ga = ctx.saved_tensors
-        return (gL * gk if ctx.needs_input_grad[0] else None, gL * ge if ctx.needs_input_grad[1] else None,
-                gL * ga if ctx.needs_input_grad[2] else None, None, None, None, None, None)
+        gk, ge, ga, info = ctx.sim.adjoint_backward()
+        ctx.info_backward = info
+        dk, de, da = ctx.devices
+        g = float(gL)
+        return (torch.from_numpy(g * gk).to(dk) if ctx.needs_input_grad[0] else None,
+                torch.from_numpy(g * ge).to(de) if ctx.needs_input_grad[1] else None,
+                torch.from_numpy(g * ga).to(da) if ctx.needs_input_grad[2] else None, None, None, None, None, None)
 
 
 def oil_production(sim, dts, log_k, Ea, lnA, checkpoint_every=5, tol_adjoint=0.0, initial_state=None):

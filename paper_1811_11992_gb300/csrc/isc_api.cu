@@ -594,6 +594,206 @@ int validate_options(isc_handle* h, const isc_options& o) {
 
 }  // namespace
 
+// The forward sweep of the discrete adjoint: the time loop with the frozen step
+// sizes, the loss, and the states kept for the reverse sweep (every K-th state
+// as a checkpoint plus the last segment's states). Records the step sizes so
+// that adjoint_backward can run later on the same store.
+static int adjoint_forward(isc_handle* h, const isc_adjoint_spec* spec, double* loss, isc_adjoint_info* info) {
+  const int N = spec->n_steps, K = spec->checkpoint_every;
+  if (N < 1 || K < 1 || !spec->dt) return set_err(h, ISC_ERR_INVALID_ARG, "n_steps and checkpoint_every must be >= 1");
+  for (int q = 0; q < N; ++q)
+    if (!(spec->dt[q] > 0.0) || !isfinite(spec->dt[q])) return set_err(h, ISC_ERR_INVALID_ARG, "step sizes must be > 0");
+  if (!(spec->tol_adjoint >= 0.0)) return set_err(h, ISC_ERR_INVALID_ARG, "tol_adjoint must be >= 0");
+  if (!h->have_acc) return set_err(h, ISC_ERR_STATE, "isc_begin_step (or isc_init_equilibrium) must come first");
+  if (h->nwc) return set_err(h, ISC_ERR_UNIMPLEMENTED, "the adjoint does not cover coupled producers");
+  const int n = h->n;
+  const size_t len = (size_t)n * 8, SN = (size_t)n * 9;
+  const int ncp = (N + K - 1) / K;
+  const int need = ncp + K + 2;                 // checkpoints, K+1 segment states, the final state
+  const int traj0 = ncp, fin = ncp + K + 1;
+  AdjointWork& A = h->adj;
+  cudaStream_t s = h->stream;
+  A.ready = false;
+  // workspace
+  if (!A.ubar) {
+    int e = 0;
+    e |= dalloc(h, &A.ubar, len);
+    e |= dalloc(h, &A.cbar, n);
+    e |= dalloc(h, &A.lam, len);
+    e |= dalloc(h, &A.glnk, n);
+    e |= dalloc(h, &A.grx, (size_t)2 * ISC_MAX_RXN * n);
+    e |= dalloc(h, &A.scond, n);
+    e |= dalloc(h, &A.kd, n);
+    e |= dalloc(h, &A.loss_cell, n);
+    e |= dalloc(h, &A.sums, 1 + 2 * ISC_MAX_RXN);
+    if (e) return ISC_ERR_NOMEM;
+  }
+  if (A.cap_states < need) {
+    if (A.store) cudaFree(A.store);
+    A.store = nullptr;
+    A.cap_states = 0;
+    if (dalloc(h, &A.store, (size_t)need * SN)) return ISC_ERR_NOMEM;
+    A.cap_states = need;
+  }
+  auto slot = [&](int k) { return A.store + (size_t)k * SN; };
+  auto save = [&](int k) -> int {
+    CUDA_TRY(h, cudaMemcpyAsync(slot(k), h->u, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(h, cudaMemcpyAsync(slot(k) + len, h->coke, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    return ISC_OK;
+  };
+  int st;
+  CUDA_TRY(h, cudaMemsetAsync(A.loss_cell, 0, sizeof(double) * n, s));
+  if ((st = save(0)) || (st = save(traj0))) return st;
+  int seg0 = 0;
+  for (int q = 1; q <= N; ++q) {
+    isc_step_info si;
+    st = isc_timestep(h, spec->dt[q - 1], &si);
+    info->newton_iterations += si.newton_iterations;
+    info->krylov_iterations_forward += si.krylov_iterations;
+    if (st) return info->status = st;
+    {
+      Region rg(h, ISC_K_ADJOINT, 1);
+      launch_oil_rate(*h, spec->dt[q - 1], s);
+    }
+    const int j = q - seg0;
+    if ((st = save(traj0 + j))) return st;
+    if (j == K && q < N) {
+      seg0 = q;
+      if ((st = save(q / K)) || (st = save(traj0))) return st;
+    }
+  }
+  if ((st = save(fin))) return st;
+  launch_row_sums(1, n, A.loss_cell, A.sums, s);
+  double Lsum = 0.0;
+  CUDA_TRY(h, cudaMemcpyAsync(&Lsum, A.sums, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(h, cudaStreamSynchronize(s));
+  info->loss = Lsum;
+  if (loss) *loss = Lsum;
+  A.dts.assign(spec->dt, spec->dt + N);
+  A.K = K;
+  A.tol_adjoint = spec->tol_adjoint;
+  A.loss = Lsum;
+  A.traj_used = false;
+  A.ready = true;
+  return ISC_OK;
+}
+
+// The reverse sweep over the states the last adjoint_forward kept: per step
+// (last to first) one transposed solve and the gradient parts, each earlier
+// segment recomputed from its checkpoint. Leaves the handle at the loop's final state.
+static int adjoint_backward(isc_handle* h, double* g_log_k, double* g_Ea, double* g_lnA, isc_adjoint_info* info) {
+  AdjointWork& A = h->adj;
+  if (!A.ready) return set_err(h, ISC_ERR_STATE, "run the forward sweep (isc_adjoint_forward) first");
+  const int N = (int)A.dts.size(), K = A.K;
+  const int n = h->n, nr = h->P.nr;
+  const size_t len = (size_t)n * 8, SN = (size_t)n * 9;
+  const int ncp = (N + K - 1) / K;
+  const int traj0 = ncp, fin = ncp + K + 1;
+  cudaStream_t s = h->stream;
+  info->loss = A.loss;
+  auto slot = [&](int k) { return A.store + (size_t)k * SN; };
+  auto save = [&](int k) -> int {
+    CUDA_TRY(h, cudaMemcpyAsync(slot(k), h->u, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(h, cudaMemcpyAsync(slot(k) + len, h->coke, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    return ISC_OK;
+  };
+  auto load_accepted = [&](int k) -> int {
+    CUDA_TRY(h, cudaMemcpyAsync(h->u, slot(k), sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(h, cudaMemcpyAsync(h->coke, slot(k) + len, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    return isc_begin_step(h);
+  };
+  CUDA_TRY(h, cudaMemsetAsync(A.ubar, 0, sizeof(double) * len, s));
+  CUDA_TRY(h, cudaMemsetAsync(A.cbar, 0, sizeof(double) * n, s));
+  CUDA_TRY(h, cudaMemsetAsync(A.glnk, 0, sizeof(double) * n, s));
+  CUDA_TRY(h, cudaMemsetAsync(A.grx, 0, sizeof(double) * 2 * ISC_MAX_RXN * n, s));
+  const double tol_saved = h->opt.tol_lin;
+  const double tol_adj = A.tol_adjoint > 0.0 ? A.tol_adjoint : tol_saved;
+  int result = ISC_OK;
+  // the last segment's states are still in the trajectory slots from the forward sweep;
+  // a second backward over the same forward recomputes it too
+  for (int seg = ncp - 1; seg >= 0 && result == ISC_OK; --seg) {
+    const int s0 = seg * K, s1 = std::min(s0 + K, N);
+    if (seg < ncp - 1 || A.traj_used) {
+      // recompute the segment's states from its checkpoint (the Newton path is deterministic)
+      if ((result = load_accepted(seg))) break;
+      if ((result = save(traj0))) break;
+      for (int q = s0 + 1; q <= s1 && result == ISC_OK; ++q) {
+        isc_step_info si;
+        result = isc_timestep(h, A.dts[q - 1], &si);
+        info->newton_iterations += si.newton_iterations;
+        info->krylov_iterations_forward += si.krylov_iterations;
+        info->recomputed_steps++;
+        if (!result) result = save(traj0 + q - s0);
+      }
+      if (result) break;
+    }
+    for (int q = s1; q > s0; --q) {
+      const double dt = A.dts[q - 1];
+      const double* old = slot(traj0 + q - 1 - s0);
+      const double* cur = slot(traj0 + q - s0);
+      cudaMemcpyAsync(h->u_n, old, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
+      cudaMemcpyAsync(h->coke_n, old + len, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+      launch_old_accumulation(*h, s);
+      h->have_acc = true;
+      cudaMemcpyAsync(h->u, cur, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
+      {
+        Region rg(h, ISC_K_ADJOINT, 1);
+        launch_adj_pre(*h, dt, s);
+      }
+      if ((result = isc_assemble(h, dt))) break;
+      {
+        Region rg(h, ISC_K_ADJOINT, 1);
+        launch_bsr_transpose(*h, s);
+      }
+      // J^T lambda = ubar (the transposed system is decoupled and preconditioned like J)
+      cudaMemcpyAsync(h->R, A.ubar, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
+      if (h->opt.decouple && (result = isc_decouple(h))) break;
+      if ((result = build_prec(h))) break;
+      {
+        Region rg(h, ISC_K_BLAS1, 1);
+        launch_scale_copy((int)len, 1.0, h->R, h->rhs, s);
+      }
+      int its = 0;
+      double rel = 0.0;
+      h->opt.tol_lin = tol_adj;
+      if (h->opt.krylov == ISC_KRYLOV_GMRES)
+        result = gmres(h, h->rhs, A.lam, &its, &rel);
+      else
+        result = bicgstab(h, h->rhs, A.lam, &its, &rel);
+      h->opt.tol_lin = tol_saved;
+      info->krylov_iterations_adjoint += its;
+      info->adjoint_rel_residual = std::max(info->adjoint_rel_residual, rel);
+      if (result) break;
+      {
+        Region rg(h, ISC_K_ADJOINT, q > 1 ? 4 : 3);
+        launch_adj_post(*h, q > 1, s);
+      }
+      CUDA_TRY(h, cudaGetLastError());
+    }
+  }
+  A.traj_used = true;
+  h->opt.tol_lin = tol_saved;
+  h->assembled = h->decoupled = h->prec_built = false;
+  if (result == ISC_OK) result = check_device_status(h);
+  // leave the handle at the final state of the time loop
+  int st2 = load_accepted(fin);
+  if (result) return info->status = result;
+  if (st2) return info->status = st2;
+  if (g_log_k) CUDA_TRY(h, cudaMemcpyAsync(g_log_k, A.glnk, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+  if (nr > 0) {
+    launch_row_sums(2 * nr, n, A.grx, A.sums + 1, s);
+    double sums[2 * ISC_MAX_RXN];
+    CUDA_TRY(h, cudaMemcpyAsync(sums, A.sums + 1, sizeof(double) * 2 * nr, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(h, cudaStreamSynchronize(s));
+    for (int r = 0; r < nr; ++r) {
+      if (g_lnA) g_lnA[r] = sums[r];
+      if (g_Ea) g_Ea[r] = sums[nr + r];
+    }
+  }
+  CUDA_TRY(h, cudaStreamSynchronize(s));
+  return ISC_OK;
+}
+
 extern "C" {
 
 void isc_default_options(isc_options* o) {
@@ -1006,6 +1206,7 @@ int isc_set_options(isc_handle* h, const isc_options* o) {
   h->opt = *o;
   h->stream = (cudaStream_t)o->stream;
   h->prec_built = false;
+  h->adj.ready = false;  // a reverse sweep recomputes states with the options of its forward sweep
   return ISC_OK;
 }
 
@@ -1250,6 +1451,7 @@ int isc_set_heat_loss(isc_handle* h, double K_ob, double d, double T_ini, double
   h->P.hl_Tini = T_ini;
   h->P.hl_rho = rho;
   h->P.hl_faces = faces;
+  h->adj.ready = false;  // the stored forward sweep no longer matches the model
   h->assembled = h->decoupled = h->prec_built = false;  // the next residual includes it
   return ISC_OK;
 }
@@ -1477,6 +1679,7 @@ int isc_set_parameters(isc_handle* h, const double* log_k, const double* Ea, con
     }
   }
   h->assembled = h->decoupled = h->prec_built = false;
+  h->adj.ready = false;  // the stored forward sweep belongs to the old parameters
   return ISC_OK;
 }
 
@@ -1496,171 +1699,25 @@ int isc_adjoint(isc_handle* h, const isc_adjoint_spec* spec, double* loss, doubl
   isc_adjoint_info loc{};
   if (!info) info = &loc;
   memset(info, 0, sizeof(*info));
-  const int N = spec->n_steps, K = spec->checkpoint_every;
-  if (N < 1 || K < 1 || !spec->dt) return set_err(h, ISC_ERR_INVALID_ARG, "n_steps and checkpoint_every must be >= 1");
-  for (int q = 0; q < N; ++q)
-    if (!(spec->dt[q] > 0.0) || !isfinite(spec->dt[q])) return set_err(h, ISC_ERR_INVALID_ARG, "step sizes must be > 0");
-  if (!(spec->tol_adjoint >= 0.0)) return set_err(h, ISC_ERR_INVALID_ARG, "tol_adjoint must be >= 0");
-  if (!h->have_acc) return set_err(h, ISC_ERR_STATE, "isc_begin_step (or isc_init_equilibrium) must come first");
-  if (h->nwc) return set_err(h, ISC_ERR_UNIMPLEMENTED, "the adjoint does not cover coupled producers");
-  const bool want_grad = g_log_k || g_Ea || g_lnA;
-  const int n = h->n, nr = h->P.nr;
-  const size_t len = (size_t)n * 8, SN = (size_t)n * 9;
-  const int ncp = (N + K - 1) / K;
-  const int need = ncp + K + 2;                 // checkpoints, K+1 segment states, the final state
-  const int traj0 = ncp, fin = ncp + K + 1;
-  AdjointWork& A = h->adj;
-  cudaStream_t s = h->stream;
-  // workspace
-  if (!A.ubar) {
-    int e = 0;
-    e |= dalloc(h, &A.ubar, len);
-    e |= dalloc(h, &A.cbar, n);
-    e |= dalloc(h, &A.lam, len);
-    e |= dalloc(h, &A.glnk, n);
-    e |= dalloc(h, &A.grx, (size_t)2 * ISC_MAX_RXN * n);
-    e |= dalloc(h, &A.scond, n);
-    e |= dalloc(h, &A.kd, n);
-    e |= dalloc(h, &A.loss_cell, n);
-    e |= dalloc(h, &A.sums, 1 + 2 * ISC_MAX_RXN);
-    if (e) return ISC_ERR_NOMEM;
-  }
-  if (A.cap_states < need) {
-    if (A.store) cudaFree(A.store);
-    A.store = nullptr;
-    A.cap_states = 0;
-    if (dalloc(h, &A.store, (size_t)need * SN)) return ISC_ERR_NOMEM;
-    A.cap_states = need;
-  }
-  auto slot = [&](int k) { return A.store + (size_t)k * SN; };
-  auto save = [&](int k) -> int {
-    CUDA_TRY(h, cudaMemcpyAsync(slot(k), h->u, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
-    CUDA_TRY(h, cudaMemcpyAsync(slot(k) + len, h->coke, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-    return ISC_OK;
-  };
-  auto load_accepted = [&](int k) -> int {
-    CUDA_TRY(h, cudaMemcpyAsync(h->u, slot(k), sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
-    CUDA_TRY(h, cudaMemcpyAsync(h->coke, slot(k) + len, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-    return isc_begin_step(h);
-  };
-  auto step = [&](int q, bool recompute) -> int {
-    isc_step_info si;
-    int st = isc_timestep(h, spec->dt[q], &si);
-    info->newton_iterations += si.newton_iterations;
-    info->krylov_iterations_forward += si.krylov_iterations;
-    if (recompute) info->recomputed_steps++;
-    return st;
-  };
-  int st;
-  // ---------------------------------------------------------- forward sweep
-  CUDA_TRY(h, cudaMemsetAsync(A.loss_cell, 0, sizeof(double) * n, s));
-  if ((st = save(0)) || (st = save(traj0))) return st;
-  int seg0 = 0;
-  for (int q = 1; q <= N; ++q) {
-    if ((st = step(q - 1, false))) return info->status = st;
-    {
-      Region rg(h, ISC_K_ADJOINT, 1);
-      launch_oil_rate(*h, spec->dt[q - 1], s);
-    }
-    const int j = q - seg0;
-    if ((st = save(traj0 + j))) return st;
-    if (j == K && q < N) {
-      seg0 = q;
-      if ((st = save(q / K)) || (st = save(traj0))) return st;
-    }
-  }
-  if ((st = save(fin))) return st;
-  launch_row_sums(1, n, A.loss_cell, A.sums, s);
-  double Lsum = 0.0;
-  CUDA_TRY(h, cudaMemcpyAsync(&Lsum, A.sums, sizeof(double), cudaMemcpyDeviceToHost, s));
-  CUDA_TRY(h, cudaStreamSynchronize(s));
-  info->loss = Lsum;
-  if (loss) *loss = Lsum;
-  if (!want_grad) return ISC_OK;
-  // --------------------------------------------------------- reverse sweep
-  CUDA_TRY(h, cudaMemsetAsync(A.ubar, 0, sizeof(double) * len, s));
-  CUDA_TRY(h, cudaMemsetAsync(A.cbar, 0, sizeof(double) * n, s));
-  CUDA_TRY(h, cudaMemsetAsync(A.glnk, 0, sizeof(double) * n, s));
-  CUDA_TRY(h, cudaMemsetAsync(A.grx, 0, sizeof(double) * 2 * ISC_MAX_RXN * n, s));
-  const double tol_saved = h->opt.tol_lin;
-  const double tol_adj = spec->tol_adjoint > 0.0 ? spec->tol_adjoint : tol_saved;
-  int result = ISC_OK;
-  for (int seg = ncp - 1; seg >= 0 && result == ISC_OK; --seg) {
-    const int s0 = seg * K, s1 = std::min(s0 + K, N);
-    if (seg < ncp - 1) {
-      // recompute the segment's states from its checkpoint (the Newton path is deterministic)
-      if ((result = load_accepted(seg))) break;
-      if ((result = save(traj0))) break;
-      for (int q = s0 + 1; q <= s1 && result == ISC_OK; ++q) {
-        result = step(q - 1, true);
-        if (!result) result = save(traj0 + q - s0);
-      }
-      if (result) break;
-    }
-    for (int q = s1; q > s0; --q) {
-      const double dt = spec->dt[q - 1];
-      const double* old = slot(traj0 + q - 1 - s0);
-      const double* cur = slot(traj0 + q - s0);
-      cudaMemcpyAsync(h->u_n, old, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
-      cudaMemcpyAsync(h->coke_n, old + len, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
-      launch_old_accumulation(*h, s);
-      h->have_acc = true;
-      cudaMemcpyAsync(h->u, cur, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
-      {
-        Region rg(h, ISC_K_ADJOINT, 1);
-        launch_adj_pre(*h, dt, s);
-      }
-      if ((result = isc_assemble(h, dt))) break;
-      {
-        Region rg(h, ISC_K_ADJOINT, 1);
-        launch_bsr_transpose(*h, s);
-      }
-      // J^T lambda = ubar (the transposed system is decoupled and preconditioned like J)
-      cudaMemcpyAsync(h->R, A.ubar, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
-      if (h->opt.decouple && (result = isc_decouple(h))) break;
-      if ((result = build_prec(h))) break;
-      {
-        Region rg(h, ISC_K_BLAS1, 1);
-        launch_scale_copy((int)len, 1.0, h->R, h->rhs, s);
-      }
-      int its = 0;
-      double rel = 0.0;
-      h->opt.tol_lin = tol_adj;
-      if (h->opt.krylov == ISC_KRYLOV_GMRES)
-        result = gmres(h, h->rhs, A.lam, &its, &rel);
-      else
-        result = bicgstab(h, h->rhs, A.lam, &its, &rel);
-      h->opt.tol_lin = tol_saved;
-      info->krylov_iterations_adjoint += its;
-      info->adjoint_rel_residual = std::max(info->adjoint_rel_residual, rel);
-      if (result) break;
-      {
-        Region rg(h, ISC_K_ADJOINT, q > 1 ? 4 : 3);
-        launch_adj_post(*h, q > 1, s);
-      }
-      CUDA_TRY(h, cudaGetLastError());
-    }
-  }
-  h->opt.tol_lin = tol_saved;
-  h->assembled = h->decoupled = h->prec_built = false;
-  if (result == ISC_OK) result = check_device_status(h);
-  // leave the handle at the final state of the time loop
-  int st2 = load_accepted(fin);
-  if (result) return info->status = result;
-  if (st2) return info->status = st2;
-  if (g_log_k) CUDA_TRY(h, cudaMemcpyAsync(g_log_k, A.glnk, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
-  if (nr > 0) {
-    launch_row_sums(2 * nr, n, A.grx, A.sums + 1, s);
-    double sums[2 * ISC_MAX_RXN];
-    CUDA_TRY(h, cudaMemcpyAsync(sums, A.sums + 1, sizeof(double) * 2 * nr, cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(h, cudaStreamSynchronize(s));
-    for (int r = 0; r < nr; ++r) {
-      if (g_lnA) g_lnA[r] = sums[r];
-      if (g_Ea) g_Ea[r] = sums[nr + r];
-    }
-  }
-  CUDA_TRY(h, cudaStreamSynchronize(s));
-  return ISC_OK;
+  int st = adjoint_forward(h, spec, loss, info);
+  if (st || !(g_log_k || g_Ea || g_lnA)) return st;
+  return adjoint_backward(h, g_log_k, g_Ea, g_lnA, info);
+}
+
+int isc_adjoint_forward(isc_handle* h, const isc_adjoint_spec* spec, double* loss, isc_adjoint_info* info) {
+  if (!h || !spec) return ISC_ERR_INVALID_ARG;
+  isc_adjoint_info loc{};
+  if (!info) info = &loc;
+  memset(info, 0, sizeof(*info));
+  return adjoint_forward(h, spec, loss, info);
+}
+
+int isc_adjoint_backward(isc_handle* h, double* g_log_k, double* g_Ea, double* g_lnA, isc_adjoint_info* info) {
+  if (!h) return ISC_ERR_INVALID_ARG;
+  isc_adjoint_info loc{};
+  if (!info) info = &loc;
+  memset(info, 0, sizeof(*info));
+  return adjoint_backward(h, g_log_k, g_Ea, g_lnA, info);
 }
 
 }  // extern "C"

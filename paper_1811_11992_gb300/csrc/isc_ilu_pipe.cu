@@ -758,12 +758,17 @@ void launch_ilu_factor_pipe(Handle& h, cudaStream_t s) {
 
 namespace {
 
-// cells staged in each warp's shared-memory ring
-constexpr int SWEEP_R = 4;
+// cells staged in each warp's shared-memory ring, per precision
+constexpr int SWEEP_R64 = 4;
+constexpr int SWEEP_R32 = 4;
+template <typename TM>
+constexpr int sweep_r() {
+  return sizeof(TM) == 8 ? SWEEP_R64 : SWEEP_R32;
+}
 
 template <typename TM, typename RT>
 size_t sweep_smem() {
-  return sizeof(Slot2<TM, RT>) * SWEEP_R * AWARPS;
+  return sizeof(Slot2<TM, RT>) * sweep_r<TM>() * AWARPS;
 }
 
 // tasks of the anti-diagonal map: ceil(len/2) per diagonal of the ny x nz pencil grid
@@ -793,7 +798,7 @@ int sweep_blocks(K kernel, size_t smem, int tasks) {
 template <typename TM, typename RT>
 cudaError_t launch_fwd(int nx, int ny, int nz, const TM* A, const TM* Dinv, const RT* r, TM* y, int* pipe,
                        int* dstatus, cudaStream_t s) {
-  auto kern = k_sweep_fwd<TM, SWEEP_R, RT>;
+  auto kern = k_sweep_fwd<TM, sweep_r<TM>(), RT>;
   const size_t smem = sweep_smem<TM, RT>();
   // idempotent; the rings need more than the default 48 KB of dynamic shared memory
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -808,7 +813,7 @@ cudaError_t launch_fwd(int nx, int ny, int nz, const TM* A, const TM* Dinv, cons
 template <typename TM, bool PRE>
 cudaError_t launch_bwd(int nx, int ny, int nz, const TM* A, const TM* Dinv, const TM* uhat, const TM* y, TM* z,
                        double* z64, int* pipe, int* dstatus, cudaStream_t s) {
-  auto kern = k_sweep_bwd<TM, SWEEP_R, PRE>;
+  auto kern = k_sweep_bwd<TM, sweep_r<TM>(), PRE>;
   const size_t smem = sweep_smem<TM, TM>();
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess) e = cudaMemsetAsync(pipe, 0, 2 * sizeof(int), s);
@@ -904,7 +909,7 @@ extern "C" int isc_check_bounded_wait(void) {
     if (ok) {
       // the forward sweep, its counter then moved past task 0 (pencil 0 of the 4x4x1 grid):
       // pencil 1 waits for values that never arrive
-      auto kern = k_sweep_fwd<double, SWEEP_R, double>;
+      auto kern = k_sweep_fwd<double, sweep_r<double>(), double>;
       const size_t smem = sweep_smem<double, double>();
       ok = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess &&
            cudaMemset(d_y, 0xff, sizeof(double) * (size_t)n * 8) == cudaSuccess;  // NaN sentinel

@@ -130,6 +130,12 @@ struct AdjointWork {
   double* kd = nullptr;       // (C-bar - gamma) / (dg/dC) per cell (N)
   double* loss_cell = nullptr;// per-cell cumulative produced oil mass (N)
   double* sums = nullptr;     // reduced loss and reaction gradients
+  // the last forward sweep (isc_adjoint_forward) that a reverse sweep can follow
+  bool ready = false;
+  bool traj_used = false;     // the trajectory slots no longer hold the forward sweep's last segment
+  std::vector<double> dts;
+  int K = 1;
+  double tol_adjoint = 0.0, loss = 0.0;
   int32_t* inj_first = nullptr;  // injector wells: first slot and slot count
   int32_t* inj_count = nullptr;
   int n_inj = 0;

@@ -166,6 +166,9 @@ _SIGS = {
     "isc_get_parameters": (C.c_int, [C.c_void_p, c_double_p, c_double_p, c_double_p]),
     "isc_adjoint": (C.c_int, [C.c_void_p, C.POINTER(isc_adjoint_spec), c_double_p, c_double_p, c_double_p,
                               c_double_p, C.POINTER(isc_adjoint_info)]),
+    "isc_adjoint_forward": (C.c_int, [C.c_void_p, C.POINTER(isc_adjoint_spec), c_double_p,
+                                      C.POINTER(isc_adjoint_info)]),
+    "isc_adjoint_backward": (C.c_int, [C.c_void_p, c_double_p, c_double_p, c_double_p, C.POINTER(isc_adjoint_info)]),
 }
 
 
@@ -519,6 +522,24 @@ class Simulator:
         if not gradient:
             return L.value, None, None, None, info_d
         return L.value, gk, ge[:nr], ga[:nr], info_d
+
+    def adjoint_forward(self, dts, checkpoint_every=5, tol_adjoint=0.0):
+        """The time loop with the frozen step sizes dts from the accepted state:
+        returns (L, info) and keeps the checkpoints for adjoint_backward."""
+        d = np.ascontiguousarray(dts, np.float64).reshape(-1)
+        spec = isc_adjoint_spec(len(d), _dp(d), int(checkpoint_every), float(tol_adjoint))
+        info = isc_adjoint_info()
+        L = C.c_double(0.0)
+        self._check(self.lib.isc_adjoint_forward(self.h, C.byref(spec), C.byref(L), C.byref(info)))
+        return L.value, {k: getattr(info, k) for k, _ in isc_adjoint_info._fields_}
+
+    def adjoint_backward(self):
+        """The reverse sweep over the last adjoint_forward: (g_log_k, g_Ea, g_lnA, info)."""
+        nr = int(self.case.reactions["nr"])
+        gk, ge, ga = np.empty(self.n), np.empty(max(nr, 1)), np.empty(max(nr, 1))
+        info = isc_adjoint_info()
+        self._check(self.lib.isc_adjoint_backward(self.h, _dp(gk), _dp(ge), _dp(ga), C.byref(info)))
+        return gk, ge[:nr], ga[:nr], {k: getattr(info, k) for k, _ in isc_adjoint_info._fields_}
 
     def set_state_device(self, d_u, d_coke=None):
         self._check(self.lib.isc_set_state_device(self.h, C.c_void_p(d_u), C.c_void_p(d_coke) if d_coke else None))

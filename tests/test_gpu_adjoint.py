@@ -105,6 +105,9 @@ def test_parameters_change_the_loop_like_the_oracle(box):
 
 
 def test_autograd_function_returns_the_adjoint_gradient(box):
+    """forward runs the loss only; backward runs the reverse sweep (the
+    transposed solves) and gives the gradient of the one-call isc_adjoint bit
+    for bit."""
     torch = pytest.importorskip("torch")
     from paper_1811_11992_gb300.autograd import oil_production
     case, _, _ = box
@@ -114,13 +117,38 @@ def test_autograd_function_returns_the_adjoint_gradient(box):
     Ea = torch.tensor(Ea0, requires_grad=True)
     lnA = torch.tensor(lnA0, requires_grad=True)
     L = oil_production(g, BOX_DTS, lk, Ea, lnA, checkpoint_every=2, tol_adjoint=1e-12)
+    assert L.grad_fn.info["krylov_iterations_adjoint"] == 0          # no transposed solve yet
     (2.0 * L).backward()
+    assert L.grad_fn.info_backward["krylov_iterations_adjoint"] > 0
     g.init_equilibrium()
     L2, gk, ge, ga, _ = g.adjoint(BOX_DTS, checkpoint_every=2, tol_adjoint=1e-12)
     assert float(L) == L2
     np.testing.assert_array_equal(lk.grad.numpy(), 2.0 * gk)
     np.testing.assert_array_equal(Ea.grad.numpy(), 2.0 * ge)
     np.testing.assert_array_equal(lnA.grad.numpy(), 2.0 * ga)
+    g.close()
+
+
+def test_split_adjoint_repeats_and_refuses_a_changed_model(box):
+    from paper_1811_11992_gb300 import isc
+    case, _, _ = box
+    g = _sim(case)
+    g.init_equilibrium()
+    L, info = g.adjoint_forward(BOX_DTS, checkpoint_every=2, tol_adjoint=1e-12)
+    a = g.adjoint_backward()
+    b = g.adjoint_backward()           # the last segment is recomputed the second time
+    for x, y in zip(a[:3], b[:3]):
+        np.testing.assert_array_equal(x, y)
+    g.init_equilibrium()
+    L2, gk, ge, ga, _ = g.adjoint(BOX_DTS, checkpoint_every=2, tol_adjoint=1e-12)
+    assert L == L2
+    np.testing.assert_array_equal(a[0], gk)
+    np.testing.assert_array_equal(a[1], ge)
+    lk0, Ea0, lnA0 = g.get_parameters()
+    g.set_parameters(lk0, Ea0, lnA0)
+    with pytest.raises(isc.IscError) as err:
+        g.adjoint_backward()
+    assert err.value.status == -11
     g.close()
 
 
@@ -135,11 +163,16 @@ def test_adjoint_workload_central_differences():
     case = inp.config(4)
     n, nr = case.n, int(case.reactions["nr"])
     dts = inp.adjoint_steps(case)
+    torch = pytest.importorskip("torch")
+    from paper_1811_11992_gb300.autograd import oil_production
     g = _sim(case, tol_newton=1e-9, tol_lin=1e-6, maxit_lin=3000)
-    g.init_equilibrium()
-    L, gk, ge, ga, info = g.adjoint(dts, checkpoint_every=5, tol_adjoint=1e-10)
-    assert L > 0 and info["recomputed_steps"] == 15
     lk0, Ea0, lnA0 = g.get_parameters()
+    # the gradient through torch.autograd.grad: forward = the loss, backward = the reverse sweep
+    params = [torch.tensor(v, requires_grad=True) for v in (lk0, Ea0, lnA0)]
+    Lt = oil_production(g, dts, *params, checkpoint_every=5, tol_adjoint=1e-10)
+    gk, ge, ga = (t.numpy() for t in torch.autograd.grad(Lt, params))
+    L = float(Lt)
+    assert L > 0 and Lt.grad_fn.info_backward["recomputed_steps"] == 15
     rng = np.random.default_rng(2024)
     h = 1e-6
     rows = []
