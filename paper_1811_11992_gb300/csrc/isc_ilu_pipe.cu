@@ -164,9 +164,9 @@ __device__ __forceinline__ bool poll_vec(const T* v, int c, typename V2<T>::t& o
 // backward sweep z_i = y_i - Dhat_z z_z - Dhat_y z_y - Dhat_x z_{i+1} with the
 // pre-scaled upper blocks Dhat = D_i^-1 A_{i,up}, which the factorisation
 // computes anyway (they are its D_k^-1 A_ki products) and stores, so the
-// backward sweep reads no D^-1 and does no second product. Signs are folded
-// into FMA operands (a row sum starts from -r_i, the diagonal product uses -D),
-// so no separate subtraction reaches the FP64 pipe.
+// backward sweep reads no D^-1 and does no second product. A row sum starts
+// from r_i (or y_i) and subtracts the products with negated FMA operands, so no
+// separate subtraction or negation reaches the FP64 pipe.
 
 // the lane's four columns of a block row: (e0, e0 + 1) and (e2, e2 + 1). FP64
 // lanes 4-7 and 12-15 of a half take the two pairs in the other order, so that
@@ -235,12 +235,6 @@ template <typename TM>
 __device__ __forceinline__ void zero4(TM (&x)[4]) {
   x[0] = x[1] = x[2] = x[3] = TM(0);
 }
-
-// -x without the floating-point pipe (sign bit flip)
-__device__ __forceinline__ double neg_bits(double x) {
-  return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull);
-}
-__device__ __forceinline__ float neg_bits(float x) { return __int_as_float(__float_as_int(x) ^ (int)0x80000000u); }
 
 // Wait until the neighbour values a half needs (z and/or y neighbour pencil,
 // four entries each per lane) are all numbers, across the whole warp. The
@@ -398,7 +392,7 @@ __global__ void __launch_bounds__(AWARPS * 32) k_sweep_fwd(int nx, int ny, int n
         if (hy) ld4s(sl->blk[L.hl][1], L, ay);
         if (x > 0) ld4s(sl->blk[L.hl][2], L, ax);
         ld4s(sl->blk[L.hl][3], L, d);
-        if (L.q == 0) acc = -(TM)sl->rhs[L.hl][L.r];
+        if (L.q == 0) acc = (TM)sl->rhs[L.hl][L.r];
       }
       // (the addresses are formed only when the neighbour exists)
       if (!await_nbrs<TM>(hz ? y + (size_t)(i - nxy) * 8 : y, hz, vz, hy ? y + (size_t)(i - nx) * 8 : y, hy, vy, L,
@@ -406,17 +400,18 @@ __global__ void __launch_bounds__(AWARPS * 32) k_sweep_fwd(int nx, int ny, int n
         cp_async_wait<0>();  // no copy of this warp is left in flight when it leaves
         return;
       }
-      // row sums of A v - r: the neighbours' terms, then the x-recurrence term last
+      // row sums of r - A v: the neighbours' terms, then the x-recurrence term last
+      // (the minus signs are FMA operand modifiers, not instructions)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) acc = fma(az[c], vz[c], acc);
+      for (int c = 0; c < 4; ++c) acc = fma(-az[c], vz[c], acc);
 #pragma unroll
-      for (int c = 0; c < 4; ++c) acc = fma(ay[c], vy[c], acc);
+      for (int c = 0; c < 4; ++c) acc = fma(-ay[c], vy[c], acc);
 #pragma unroll
-      for (int c = 0; c < 4; ++c) acc = fma(ax[c], yp[c], acc);
-      const TM s = acc + __shfl_xor_sync(FULL, acc, 1);  // -t_r, t = r - A v
+      for (int c = 0; c < 4; ++c) acc = fma(-ax[c], yp[c], acc);
+      const TM s = acc + __shfl_xor_sync(FULL, acc, 1);  // t_r, t = r - A v
       const TM n0 = __shfl_sync(FULL, s, L.s0), n1 = __shfl_sync(FULL, s, L.s0 + 2);
       const TM n2 = __shfl_sync(FULL, s, L.s2), n3 = __shfl_sync(FULL, s, L.s2 + 2);
-      TM yr = fma(-d[0], n0, fma(-d[1], n1, fma(-d[2], n2, -d[3] * n3)));  // (D^-1 t)_r, partial
+      TM yr = fma(d[0], n0, fma(d[1], n1, fma(d[2], n2, d[3] * n3)));  // (D^-1 t)_r, partial
       yr += __shfl_xor_sync(FULL, yr, 1);
       yp[0] = __shfl_sync(FULL, yr, L.s0);
       yp[1] = __shfl_sync(FULL, yr, L.s0 + 2);
@@ -492,7 +487,7 @@ __global__ void __launch_bounds__(AWARPS * 32) k_sweep_bwd(int nx, int ny, int n
       if (step < nx) stage(step);
       cp_async_commit();
     }
-    TM vz[4], vy[4], zp[4];  // zp: the previous cell's z (PRE: -z)
+    TM vz[4], vy[4], zp[4];  // zp: the previous cell's z
     zero4(vz), zero4(vy), zero4(zp);
     if (hz) ld4r(zs + (size_t)(base_jk + nx - 1 + nxy) * 8, L, vz);
     if (hy) ld4r(zs + (size_t)(base_jk + nx - 1 + nx) * 8, L, vy);
@@ -519,14 +514,15 @@ __global__ void __launch_bounds__(AWARPS * 32) k_sweep_bwd(int nx, int ny, int n
         cp_async_wait<0>();  // no copy of this warp is left in flight when it leaves
         return;
       }
-      TM acc = PRE ? -yi : TM(0);
+      // PRE: y - Dhat z directly; otherwise U z, then y - D^-1 (U z)
+      TM acc = PRE ? yi : TM(0);
 #pragma unroll
-      for (int c = 0; c < 4; ++c) acc = fma(uz[c], vz[c], acc);
+      for (int c = 0; c < 4; ++c) acc = fma(PRE ? -uz[c] : uz[c], vz[c], acc);
 #pragma unroll
-      for (int c = 0; c < 4; ++c) acc = fma(uy[c], vy[c], acc);
+      for (int c = 0; c < 4; ++c) acc = fma(PRE ? -uy[c] : uy[c], vy[c], acc);
 #pragma unroll
       for (int c = 0; c < 4; ++c) acc = fma(PRE ? -ux[c] : ux[c], zp[c], acc);
-      TM sr = acc + __shfl_xor_sync(FULL, acc, 1);  // PRE: -z_r; else (U z)_r
+      TM sr = acc + __shfl_xor_sync(FULL, acc, 1);  // PRE: z_r; else (U z)_r
       if (!PRE) {
         const TM t0 = __shfl_sync(FULL, sr, L.s0), t1 = __shfl_sync(FULL, sr, L.s0 + 2);
         const TM t2 = __shfl_sync(FULL, sr, L.s2), t3 = __shfl_sync(FULL, sr, L.s2 + 2);
@@ -538,15 +534,12 @@ __global__ void __launch_bounds__(AWARPS * 32) k_sweep_bwd(int nx, int ny, int n
       zp[2] = __shfl_sync(FULL, sr, L.s2);
       zp[3] = __shfl_sync(FULL, sr, L.s2 + 2);
       if (act && L.h < 2) {
-        TM zo[4];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) zo[c] = PRE ? neg_bits(zp[c]) : zp[c];
-        st4r(zs + (size_t)i * 8, L, zo);
+        st4r(zs + (size_t)i * 8, L, zp);
         if (z64) {
-          z64[(size_t)i * 8 + L.e0] = (double)zo[0];
-          z64[(size_t)i * 8 + L.e0 + 1] = (double)zo[1];
-          z64[(size_t)i * 8 + L.e2] = (double)zo[2];
-          z64[(size_t)i * 8 + L.e2 + 1] = (double)zo[3];
+          z64[(size_t)i * 8 + L.e0] = (double)zp[0];
+          z64[(size_t)i * 8 + L.e0 + 1] = (double)zp[1];
+          z64[(size_t)i * 8 + L.e2] = (double)zp[2];
+          z64[(size_t)i * 8 + L.e2 + 1] = (double)zp[3];
         }
       }
       if (step + 1 < nx) {
