@@ -189,7 +189,10 @@ def hbm_peak():
 # of the same recipe; a call's traffic grows with the cells it sweeps, so the
 # full-size figure is this times the workload's cells. Keyed by (class, precision).
 MEASURED_TRAFFIC = {
-    ("prec_apply", "fp64"): (313.40e6 / 72000, "field 60x60x20", "profiles/k_ilu_sweeps_field_60x60x20.md"),
+    ("prec_apply", "fp64"): (1245.53e6 / 320000, "large 40x160x50",
+                             "profiles/k_sweep_fwd_bwd_large_40x160x50.md"),
+    ("prec_apply", "mixed"): (648.48e6 / 320000, "large 40x160x50",
+                              "profiles/k_sweep_fwd_bwd_large_40x160x50.md"),
 }
 
 
@@ -242,36 +245,62 @@ def hbm_table(stats64, stats_mixed, stats_fg, case, nnzb):
     return out
 
 
-def roofline(dom, stats, case, nnzb, fp64_gflops, precision="fp64"):
-    """Algorithmic bytes (or flops) per call of the dominant kernel class over its
-    average CUDA-event duration, against the measured HBM copy bandwidth or the
-    FP64 FMA rate measured at start-up (whichever bounds the class)."""
+def gmres_blas1_work(n, its, restart=30):
+    """Algorithmic bytes and flops of the Gram-Schmidt passes of `its` GMRES(m)
+    iterations on vectors of 8n doubles (classical Gram-Schmidt applied twice):
+    iteration j of a cycle orthogonalises w against k = j + 1 basis vectors in
+    three passes (V^T w; w -= V h0 with V^T w; w -= V h1 with ||w||^2), each
+    reading the k vectors and w (the last two writing w), then scales w into the
+    next basis vector: 8 * len * (3k + 7) bytes and len * (8k + 2) flops."""
+    ln = 8 * n
+    byts = flops = 0
+    for it in range(int(its)):
+        k = it % restart + 1
+        byts += 8 * ln * (3 * k + 7)
+        flops += ln * (8 * k + 2)
+    return byts, flops
+
+
+def class_model(cls, n, nnzb, fp32=False, its=None):
+    """(algorithmic bytes, flops) per call of a kernel class (None when unmodelled)."""
+    if cls == "spmv":
+        return spmv_bytes(n, nnzb), 2 * 64 * (nnzb - n)
+    if cls == "prec_apply":
+        return ilu_apply_bytes(n, nnzb, fp32), ilu_apply_flops(n, nnzb)
+    if cls == "ilu_factor":
+        # per cell three lower and three upper blocks read, D^-1 and the three
+        # pre-scaled upper blocks written; three products D_k^-1 A_ki and A_ik (.),
+        # one 8x8 inversion
+        return (nnzb - n) * BLOCK_BYTES + n * 512 + (nnzb - n) // 2 * 512, n * (3 * 2 * 2 * 512 + 2 * 512)
+    if cls == "gj":
+        return 2 * (nnzb * BLOCK_BYTES + n * 64), n * 8 * 7 * 2 * 57
+    if cls == "blas1" and its:
+        return gmres_blas1_work(n, its)
+    return None, None
+
+
+def roofline(dom, stats, case, nnzb, fp64_gflops, precision="fp64", its=None):
+    """Algorithmic bytes (or flops) per call of a kernel class over its average
+    CUDA-event duration, against the measured HBM copy bandwidth or the FP64 FMA
+    rate measured at start-up (whichever bounds the class: FP64 work above the
+    ridge fp64_gflops / hbm flop per byte is bound by the FP64 pipe). For the
+    Gram-Schmidt class (blas1) the per-call figures are the step's totals over
+    its calls (its: Krylov iterations of the timed steps)."""
     n = case.n
     hbm = hbm_peak()
     s = stats[dom]
     calls = max(1, s["calls"])
     ms = s["ms"] / calls
     fp32 = precision != "fp64"
-    if dom == "spmv":
-        byts, flops = spmv_bytes(n, nnzb), 2 * 64 * (nnzb - n)
-    elif dom == "prec_apply":
-        byts, flops = ilu_apply_bytes(n, nnzb, fp32), ilu_apply_flops(n, nnzb)
-    elif dom == "ilu_factor":
-        # per cell three lower and three upper blocks read, D^-1 written; three
-        # block products A_ik (D_k^-1 A_ki) and one 8x8 inversion
-        byts = (nnzb - n) * BLOCK_BYTES + 2 * n * 512
-        flops = n * (3 * 2 * 2 * 512 + 2 * 512)
-    elif dom == "gj":
-        byts = 2 * (nnzb * BLOCK_BYTES + n * 64)
-        flops = n * 8 * 7 * 2 * 57
-    elif dom in ("props", "flux"):
-        byts, flops = nnzb * 512 + n * (8 + 8 + 7 + 3) * 8, None
-    else:
-        byts, flops = 0, None
-    ach_gbs = byts / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+    byts, flops = class_model(dom, n, nnzb, fp32, its)
+    if dom == "blas1" and byts:
+        byts, flops = byts / calls, flops / calls
     out = {"kernel": dom, "calls": calls, "ms_per_call": ms, "bytes_per_call": byts, "flops_per_call": flops}
+    if byts is None:
+        out.update(bound=None, achieved=None, peak=None, unit=None, frac=None, traffic=None)
+        return out
+    ach_gbs = byts / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
     if flops is not None and ms > 0 and not fp32 and flops / max(byts, 1) > fp64_gflops / hbm:
-        # FP64 above the ridge (measured FP64 rate / HBM bandwidth): the FP64 pipe bounds it
         ach = flops / (ms * 1e-3) / 1e9
         out.update(bound="alu", achieved=ach, peak=fp64_gflops, unit="GFLOP/s", frac=ach / fp64_gflops,
                    peak_source="FP64 FMA rate measured at start-up (isc_measure_fma_rates)",
@@ -279,7 +308,7 @@ def roofline(dom, stats, case, nnzb, fp64_gflops, precision="fp64"):
     else:
         out.update(bound="hbm", achieved=ach_gbs, peak=hbm, unit="GB/s", frac=ach_gbs / hbm,
                    peak_source="MEASURED_PEAKS.json hbm_gbs")
-    m = MEASURED_TRAFFIC.get((dom, precision))
+    m = MEASURED_TRAFFIC.get((dom, "fp64" if not fp32 else "mixed"))
     out["traffic"] = m[0] * n if m else None
     if m:
         out["traffic_source"] = f"{m[2]} (captured on {m[1]}, scaled per cell to {case.n} cells)"
@@ -461,8 +490,12 @@ def run_isc(args):
                 cpr_block[p] = leg_summary(ms, cst, ci, leg_steps, solve_fp64)
                 cpr_block[p]["pressure_stage_ms_per_step"] = cst["cpr"]["ms"] / leg_steps
                 cpr_block[p]["speedup_vs_ilu0_fp64"] = (ms_total / args.steps) / ms
-    dom = max(stats, key=lambda k: stats[k]["ms"])
-    roof = roofline(dom, stats, case, g.nnzb, fp64_gflops, args.precision)
+    its_total = sum(kry)
+    modelled = [k for k in stats if class_model(k, n, g.nnzb, its=its_total)[0] is not None]
+    dom = max(modelled, key=lambda k: stats[k]["ms"])
+    roof = roofline(dom, stats, case, g.nnzb, fp64_gflops, args.precision, its_total)
+    rooflines = {k: roofline(k, stats, case, g.nnzb, fp64_gflops, args.precision, its_total)
+                 for k in ("prec_apply", "spmv", "blas1", "gj", "ilu_factor") if stats[k]["calls"]}
     hbm = hbm_table(stats, mst, fst, case, g.nnzb)
     launches = sum(v["launches"] for v in stats.values())
     nnzb = g.nnzb
@@ -480,6 +513,7 @@ def run_isc(args):
         "kernel_ms": {k: round(v["ms"], 3) for k, v in stats.items()},
         "kernel_launches": {k: v["launches"] for k, v in stats.items()},
         "roofline": roof,
+        "rooflines": rooflines,
         "alu_peaks_gflops": {"fp64": fp64_gflops, "fp32": fp32_gflops,
                              "how": "isc_measure_fma_rates: register FMA chains on every SM, best of 5"},
         "hbm": hbm,

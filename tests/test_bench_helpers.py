@@ -78,6 +78,10 @@ def test_traffic_is_scaled_per_cell(bench):
     per_cell = bench.MEASURED_TRAFFIC[("prec_apply", "fp64")][0]
     assert r["traffic"] == pytest.approx(per_cell * case.n)
     assert "scaled per cell" in r["traffic_source"]
+    # the measured DRAM traffic is within a few per cent of the algorithmic bytes
+    assert abs(r["traffic"] / r["bytes_per_call"] - 1) < 0.05
+    r32 = bench.roofline("prec_apply", st, case, nnzb, 1200.0, "mixed")
+    assert abs(r32["traffic"] / r32["bytes_per_call"] - 1) < 0.05
     assert bench.roofline("spmv", {"spmv": {"calls": 1, "ms": 1.0, "launches": 1}}, case, nnzb, 1200.0,
                           "fp64")["traffic"] is None
 
@@ -88,3 +92,19 @@ def test_reference_and_library_arms_share_the_config(bench):
     b = bench.workload_config(case, 1)
     assert a == b and "200x200x50" in a["workload"] and a["precision"] == "fp64"
     assert bench.parse([]).workload == "large"
+
+
+def test_gram_schmidt_model(bench):
+    # one iteration against one basis vector: 3 passes of (1 vector + w), 2 writes of w,
+    # the scaling pass: (3*1 + 7) vector passes; 8*1 + 2 flops per element
+    b, f = bench.gmres_blas1_work(10, 1)
+    assert b == 8 * 80 * 10 and f == 80 * 10
+    # restart cycles: iteration 31 of GMRES(30) works on one vector again
+    b31, _ = bench.gmres_blas1_work(10, 31)
+    b30, _ = bench.gmres_blas1_work(10, 30)
+    assert b31 - b30 == b
+    case = _Case(200, 200, 50)
+    nnzb = _nnzb(200, 200, 50)
+    st = {"blas1": {"calls": 1140, "ms": 2800.0, "launches": 5700}}
+    r = bench.roofline("blas1", st, case, nnzb, 1057.0, "fp64", its=1140)
+    assert r["bound"] == "alu" and 0.5 < r["frac"] < 1.0

@@ -11,6 +11,7 @@ import pytest
 
 import isc_inputs as inp
 from oracle import linalg, model
+from oracle_system import assembled, decoupled
 
 pytestmark = pytest.mark.gpu
 
@@ -37,13 +38,13 @@ def _assembled(S, case, **opt):
 @pytest.mark.parametrize("dims", [(7, 5, 5), (13, 4, 3), (1, 6, 4)])
 def test_fp32_ilu0_apply_matches_fp64_oracle(Simulator, dims):
     case = inp.small_box(*dims)
-    g, _, _ = _assembled(Simulator, case, precision="mixed")
-    g.decouple()
+    rp, col, _, _, Jd, Fd = decoupled(case, 1201, 1202)
+    g = Simulator(case, precision="mixed")
+    g.set_system(Jd, Fd, decoupled=True)
     g.build_preconditioner()
-    rp, col, Jd = g.jacobian()
     x = np.random.default_rng(9).standard_normal((8, case.n))
     z = g.precond_apply(x)
-    zo = linalg.ILU0Preconditioner(rp.astype(np.int64), col.astype(np.int64), Jd).apply(x.T.copy()).T
+    zo = linalg.ILU0Preconditioner(rp, col, Jd).apply(x.T.copy()).T
     err = np.max(np.abs(z - zo)) / np.abs(zo).max()
     assert err < 2e-5, err          # FP32 factors and sweeps
     assert err > 1e-12              # really FP32
@@ -53,13 +54,13 @@ def test_fp32_ilu0_apply_matches_fp64_oracle(Simulator, dims):
 def test_mixed_solve_reaches_fp64_tolerance(Simulator):
     case = inp.small_box(7, 5, 5)
     tol = 1e-10
-    g, a, b = _assembled(Simulator, case, precision="mixed", tol_lin=tol, maxit_lin=2000)
-    F = g.residual()
-    rp, col, J = g.jacobian()
+    rp, col, J, F = assembled(case, 1201, 1202)
+    g = Simulator(case, precision="mixed", tol_lin=tol, maxit_lin=2000)
+    g.set_system(J, F)
     g.decouple()
     info = g.solve()
     du = g.newton_update()
-    vo, ro = linalg.gauss_jordan_decouple(rp.astype(np.int64), col.astype(np.int64), J, -F.T.copy())
+    vo, ro = linalg.gauss_jordan_decouple(rp, col, J, -F.T.copy())
     res = np.linalg.norm(ro - linalg.bsr_matvec(rp, col, vo, du.T.copy())) / np.linalg.norm(ro)
     assert res <= 2 * tol, res      # FP64 residual in the oracle's own decoupled system
     ref = np.linalg.solve(linalg.bsr_to_dense(rp, col, J), -F.T.reshape(-1)).reshape(case.n, 8).T
@@ -86,32 +87,62 @@ def test_mixed_newton_step_on_field_block(Simulator):
     assert np.max(np.abs(res["mixed"][0] - res["fp64"][0]) / scale) < 1e-3
 
 
+U32 = 2.0 ** -24   # FP32 unit roundoff
+
+
+def _oracle_decoupled(case, dt):
+    """The oracle's decoupled system (assembly of Sec. 3.1, Gauss-Jordan of Sec. 3.2)
+    at the case's initial state for step size dt."""
+    from oracle import sim
+    u0, c0 = sim.initial_state(case)
+    acc = model.old_accumulation(case, u0, c0)
+    F = model.residual(case, u0, c0, acc, dt)
+    rp, col, J = model.jacobian(case, u0, c0, acc, dt)
+    vd, rd = linalg.gauss_jordan_decouple(rp, col, J, F.T.copy())
+    return rp, col, vd, rd
+
+
 @pytest.mark.parametrize("dt,m", [(1000.0, 1), (1000.0, 8), (1000.0, 20), (None, 8), (None, 20)])
 def test_fgmres_inner_solve_is_the_oracle_gmres_iterate(Simulator, dt, m):
     """The preconditioner of mixed_fgmres is m iterations of ILU(0)-preconditioned
     GMRES from x0 = 0 on the FP32 copy of the decoupled matrix: the oracle's FP64
     GMRES stopped after m iterations on that same rounded matrix (and the ILU(0)
     of it) gives the same iterate, to the FP32 arithmetic of the GPU's Krylov
-    vectors, sweeps and SpMV. (Its residual in that matrix is not compared: a
-    1e-6 relative change of the iterate moves it by the condition number times
-    as much.)"""
+    vectors, sweeps and SpMV. The bound is the FP32 unit roundoff times the
+    iterate's sensitivity S to FP32-sized relative perturbations of the matrix
+    and the right-hand side (measured on the oracle: two more GMRES runs with
+    seeded perturbations of size u32), times m (each of the m iterations rounds
+    its products, sweeps and orthogonalisation once more, and those errors add)
+    and a margin of 32. (The residual in that matrix is
+    not compared: a 1e-6 relative change of the iterate moves it by the condition
+    number times as much.) The system is the oracle's, loaded through
+    isc_set_system."""
     case = inp.field_case(13, 7, 3, 0, 1, "field 13x7x3", 30 * inp.DAY, 40)
+    rp, col, vd, rd = _oracle_decoupled(case, dt or case.dt0)
     g = Simulator(case, precision="mixed_fgmres", inner_its=m)
-    g.init_equilibrium()
-    g.assemble(dt or case.dt0)
-    g.decouple()
+    g.set_system(vd, rd.T, decoupled=True)
     g.build_preconditioner()
-    rp, col, Jd = g.jacobian()
-    rp, col = rp.astype(np.int64), col.astype(np.int64)
-    A32 = Jd.astype(np.float32).astype(np.float64)
+    A32 = vd.astype(np.float32).astype(np.float64)
     r = np.random.default_rng(31).standard_normal((8, case.n))
+    r32 = r.astype(np.float32).astype(np.float64)
     z = g.precond_apply(r)
-    M = linalg.ILU0Preconditioner(rp, col, A32)
-    x, its, _ = linalg.gmres(lambda v: linalg.bsr_matvec(rp, col, A32, v), r.T.copy(), M, restart=m, rtol=1e-300,
-                             maxit=m)
-    assert its == m
-    err = np.max(np.abs(z - x.T)) / np.abs(x).max()
-    assert err < 1e-2, err         # observed 2e-7 .. 3e-3
+
+    def gmres_m(A, b):
+        M = linalg.ILU0Preconditioner(rp, col, A)
+        x, its, _ = linalg.gmres(lambda v: linalg.bsr_matvec(rp, col, A, v), b.T.copy(), M, restart=m,
+                                 rtol=1e-300, maxit=m)
+        assert its == m
+        return x.T
+
+    x = gmres_m(A32, r32)
+    rng = np.random.default_rng(32)
+    sens = 0.0
+    for _ in range(2):
+        Ap = A32 * (1 + U32 * rng.choice([-1.0, 1.0], A32.shape))
+        bp = r32 * (1 + U32 * rng.choice([-1.0, 1.0], r32.shape))
+        sens = max(sens, np.max(np.abs(gmres_m(Ap, bp) - x)) / np.abs(x).max() / U32)
+    err = np.max(np.abs(z - x)) / np.abs(x).max()
+    assert err <= 32 * m * max(sens, 1.0) * U32, (err, sens, err / (m * max(sens, 1.0) * U32))
     assert err > 1e-9, err         # really FP32
     g.close()
 
@@ -119,13 +150,13 @@ def test_fgmres_inner_solve_is_the_oracle_gmres_iterate(Simulator, dt, m):
 def test_mixed_fgmres_solve_reaches_fp64_tolerance(Simulator):
     case = inp.small_box(7, 5, 5)
     tol = 1e-10
-    g, a, b = _assembled(Simulator, case, precision="mixed_fgmres", inner_its=10, tol_lin=tol, maxit_lin=400)
-    F = g.residual()
-    rp, col, J = g.jacobian()
+    rp, col, J, F = assembled(case, 1201, 1202)
+    g = Simulator(case, precision="mixed_fgmres", inner_its=10, tol_lin=tol, maxit_lin=400)
+    g.set_system(J, F)
     g.decouple()
     info = g.solve()
     du = g.newton_update()
-    vo, ro = linalg.gauss_jordan_decouple(rp.astype(np.int64), col.astype(np.int64), J, -F.T.copy())
+    vo, ro = linalg.gauss_jordan_decouple(rp, col, J, -F.T.copy())
     res = np.linalg.norm(ro - linalg.bsr_matvec(rp, col, vo, du.T.copy())) / np.linalg.norm(ro)
     assert res <= 2 * tol, res      # FP64 residual in the oracle's own decoupled system
     ref = np.linalg.solve(linalg.bsr_to_dense(rp, col, J), -F.T.reshape(-1)).reshape(case.n, 8).T

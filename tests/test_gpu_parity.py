@@ -11,6 +11,7 @@ import pytest
 
 import isc_inputs as inp
 from oracle import linalg, model, sim
+from oracle_system import assembled, decoupled
 
 pytestmark = pytest.mark.gpu
 
@@ -95,16 +96,16 @@ def test_initial_state_and_ignited_assembly(Simulator):
 
 @pytest.mark.parametrize("name", ["tube12", "box432", "box755"])
 def test_gauss_jordan_kernel_matches_oracle_on_identical_input(Simulator, name):
+    """The oracle's assembled system loaded through isc_set_system, decoupled by
+    the GPU, against the oracle's Gauss-Jordan decoupling of the same system."""
     case = CASES[name]()
-    a = inp.random_state(case, 303)
-    b = inp.random_state(case, 404)
-    g = _gpu_assembled(Simulator, case, a, b, 100.0)
-    F = g.residual()
-    rp, col, J = g.jacobian()
+    rp, col, J, F = assembled(case, 303, 404)
+    g = Simulator(case)
+    g.set_system(J, F)
     g.decouple()
     Fd = g.residual()
     _, _, Jd = g.jacobian()
-    vo, ro = linalg.gauss_jordan_decouple(rp.astype(np.int64), col.astype(np.int64), J, F.T.copy())
+    vo, ro = linalg.gauss_jordan_decouple(rp, col, J, F.T.copy())
     rows = np.repeat(np.arange(case.n), np.diff(rp))
     assert np.all(Jd[col == rows] == np.eye(8))
     err = np.abs(Jd - vo).reshape(len(col), -1).max(axis=1) / np.maximum(np.abs(vo).reshape(len(col), -1).max(axis=1), 1e-300)
@@ -116,11 +117,9 @@ def test_gauss_jordan_kernel_matches_oracle_on_identical_input(Simulator, name):
 @pytest.mark.parametrize("name", ["tube12", "box432", "box755"])
 def test_spmv_and_ilu0_apply_match_oracle(Simulator, name):
     case = CASES[name]()
-    a = inp.random_state(case, 505)
-    b = inp.random_state(case, 606)
-    g = _gpu_assembled(Simulator, case, a, b, 100.0)
-    g.decouple()
-    rp, col, Jd = g.jacobian()
+    rp, col, _, _, Jd, Fd = decoupled(case, 505, 606)
+    g = Simulator(case)
+    g.set_system(Jd, Fd, decoupled=True)
     rng = np.random.default_rng(7)
     x = rng.standard_normal((8, case.n))
     y = g.spmv(x)
@@ -128,7 +127,7 @@ def test_spmv_and_ilu0_apply_match_oracle(Simulator, name):
     assert np.max(np.abs(y - yo)) <= 1e-13 * np.abs(yo).max()
     g.build_preconditioner()
     z = g.precond_apply(x)
-    M = linalg.ILU0Preconditioner(rp.astype(np.int64), col.astype(np.int64), Jd)
+    M = linalg.ILU0Preconditioner(rp, col, Jd)
     zo = M.apply(x.T.copy()).T
     assert np.max(np.abs(z - zo)) <= 1e-11 * np.abs(zo).max()
     g.close()
@@ -141,11 +140,9 @@ def test_row_panel_spmv_on_ragged_grids(Simulator, dims):
     odd sizes, rows with 1 to 6 neighbours): exact up to summation order against
     the oracle's BSR product."""
     case = inp.small_box(*dims)
-    a = inp.random_state(case, 515)
-    b = inp.random_state(case, 616)
-    g = _gpu_assembled(Simulator, case, a, b, 100.0)
-    g.decouple()
-    rp, col, Jd = g.jacobian()
+    rp, col, _, _, Jd, Fd = decoupled(case, 515, 616)
+    g = Simulator(case)
+    g.set_system(Jd, Fd, decoupled=True)
     x = np.random.default_rng(8).standard_normal((8, case.n))
     y = g.spmv(x)
     yo = linalg.bsr_matvec(rp, col, Jd, x.T.copy()).T
@@ -156,17 +153,15 @@ def test_row_panel_spmv_on_ragged_grids(Simulator, dims):
 @pytest.mark.parametrize("krylov,prec", [("gmres", "bilu0"), ("gmres", "bjacobi"), ("bicgstab", "bilu0"), ("gmres", "none")])
 def test_krylov_solution_has_small_residual_in_oracle_matrix(Simulator, krylov, prec):
     case = inp.small_box(4, 3, 2)
-    a = inp.random_state(case, 707)
-    b = inp.random_state(case, 808)
-    g = _gpu_assembled(Simulator, case, a, b, 100.0, krylov=krylov, prec=prec, tol_lin=1e-11, maxit_lin=2000)
-    F = g.residual()
-    rp, col, J = g.jacobian()
+    rp, col, J, F = assembled(case, 707, 808)
+    g = Simulator(case, krylov=krylov, prec=prec, tol_lin=1e-11, maxit_lin=2000)
+    g.set_system(J, F)
     g.decouple()
     info = g.solve()
     du = g.newton_update()
     assert info.krylov_rel_residual <= 1e-11
     # residual of the GPU update in the oracle's decoupled system
-    vo, ro = linalg.gauss_jordan_decouple(rp.astype(np.int64), col.astype(np.int64), J, -F.T.copy())
+    vo, ro = linalg.gauss_jordan_decouple(rp, col, J, -F.T.copy())
     r = ro - linalg.bsr_matvec(rp, col, vo, du.T.copy())
     assert np.linalg.norm(r) <= 2e-11 * np.linalg.norm(ro)
     ref = np.linalg.solve(linalg.bsr_to_dense(rp, col, J), -F.T.reshape(-1)).reshape(case.n, 8).T
@@ -238,12 +233,14 @@ def test_degenerate_grids(Simulator, name):
     _, _, Jo = model.jacobian(case, b["u"], a["coke"], acc_old, dt)
     assert row_scaled_err(g.residual(), Fo) < 1e-10
     assert jac_err(J, Jo, rp, case.n) < 1e-10
-    g.decouple()
-    rp, col, Jd = g.jacobian()
+    # the preconditioner on the oracle's decoupled system of the same grid
+    _, _, Jo_, Fo_ = assembled(case, 31, 32, dt)
+    vd, rd = linalg.gauss_jordan_decouple(rp.astype(np.int64), col.astype(np.int64), Jo_, Fo_.T.copy())
+    g.set_system(vd, rd.T, decoupled=True)
     x = np.random.default_rng(2).standard_normal((8, case.n))
     g.build_preconditioner()
     z = g.precond_apply(x)
-    zo = linalg.ILU0Preconditioner(rp.astype(np.int64), col.astype(np.int64), Jd).apply(x.T.copy()).T
+    zo = linalg.ILU0Preconditioner(rp.astype(np.int64), col.astype(np.int64), vd).apply(x.T.copy()).T
     assert np.max(np.abs(z - zo)) <= 1e-11 * np.abs(zo).max()
     info = g.solve()
     assert info.krylov_rel_residual <= 1e-6

@@ -9,6 +9,7 @@ import pytest
 
 import isc_inputs as inp
 from oracle import linalg
+from oracle_system import decoupled
 
 pytestmark = pytest.mark.gpu
 
@@ -20,21 +21,16 @@ def test_noalloc_ilu_apply_matches_precond_apply_twice():
     from paper_1811_11992_gb300 import Simulator, isc
 
     case = inp.small_box(7, 5, 5)
-    a = inp.random_state(case, 909)
-    b = inp.random_state(case, 910)
+    # the oracle's decoupled system (assembly, Gauss-Jordan) and its textbook block ILU(0)
+    rp, col, _, _, Jd, Fd = decoupled(case, 909, 910)
     g = Simulator(case)
-    g.set_state(a["u"], a["coke"])
-    g.begin_step()
-    g.set_state(b["u"])
-    g.assemble(100.0)
-    g.decouple()
+    g.set_system(Jd, Fd, decoupled=True)
     g.build_preconditioner()
-    rp, col, Jd = g.jacobian()
-    # the inverted ILU(0) diagonal blocks of the same matrix (the caller's input)
-    F = linalg.block_ilu0(rp.astype(np.int64), col.astype(np.int64), Jd)
-    M = linalg.ILU0Preconditioner(rp.astype(np.int64), col.astype(np.int64), Jd)
+    F = linalg.block_ilu0(rp, col, Jd)
+    M = linalg.ILU0Preconditioner(rp, col, Jd)
     rows = np.repeat(np.arange(case.n), np.diff(rp))
     Dinv = np.linalg.inv(F[col == rows])
+    rp = rp.astype(np.int32)
     dev = torch.device("cuda")
     d_rp = torch.from_numpy(rp).to(dev)
     d_A = torch.from_numpy(np.ascontiguousarray(Jd).reshape(-1)).to(dev)
