@@ -59,6 +59,8 @@ def parse(argv=None):
                     help="precision of the timed step's linear solve (the headline is fp64)")
     ap.add_argument("--prec", default="bilu0", choices=["bilu0", "cpr"],
                     help="preconditioner of the timed step (the headline is block ILU(0))")
+    ap.add_argument("--orth", default="cgs2", choices=["cgs2", "cgs1"],
+                    help="orthogonalisation of the FP64 GMRES (the headline uses classical Gram-Schmidt twice)")
     ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS),
                     help="large: 200x200x50 (the headline); mixed: 100x100x30; field: 60x60x20")
     return ap.parse_args(argv)
@@ -158,15 +160,16 @@ def l2_bytes():
         return 126 * 2**20
 
 
-def workload_config(case, world, precision="fp64", prec="bilu0"):
+def workload_config(case, world, precision="fp64", prec="bilu0", orth="cgs2"):
     """The `config` object of the line: the workload and solver only (measured
     numbers go elsewhere), identical for the library and the reference arm."""
     nnzb = case.n + 2 * ((case.nx - 1) * case.ny * case.nz + case.nx * (case.ny - 1) * case.nz
                          + case.nx * case.ny * (case.nz - 1))
     pname = {"bilu0": "block ILU(0)", "cpr": "CPR-PF"}[prec]
+    oname = {"cgs2": "classical Gram-Schmidt twice", "cgs1": "classical Gram-Schmidt once"}[orth]
     return {"workload": f"{case.name} ({case.n} cells, 8 unknowns/cell), first Newton step of the first time step "
                         f"(dt {case.dt0:.0f} s) from the ignited initial state",
-            "solver": f"GMRES(30), {pname}, Gauss-Jordan decoupling, tol_lin 1e-6",
+            "solver": f"GMRES(30) ({oname}), {pname}, Gauss-Jordan decoupling, tol_lin 1e-6",
             "precision": precision,
             "l2": f"inputs larger than L2, no flush: the FP64 Jacobian ({nnzb * 512 / 1e6:.0f} MB) and staged "
                   f"properties ({case.n * 16 * 9 * 8 / 1e6:.0f} MB) exceed the {l2_bytes() / 2**20:.0f} MiB L2",
@@ -245,23 +248,29 @@ def hbm_table(stats64, stats_mixed, stats_fg, case, nnzb):
     return out
 
 
-def gmres_blas1_work(n, its, restart=30):
+def gmres_blas1_work(n, its, restart=30, orth="cgs2"):
     """Algorithmic bytes and flops of the Gram-Schmidt passes of `its` GMRES(m)
-    iterations on vectors of 8n doubles (classical Gram-Schmidt applied twice):
+    iterations on vectors of 8n doubles. Classical Gram-Schmidt applied twice:
     iteration j of a cycle orthogonalises w against k = j + 1 basis vectors in
     three passes (V^T w; w -= V h0 with V^T w; w -= V h1 with ||w||^2), each
     reading the k vectors and w (the last two writing w), then scales w into the
-    next basis vector: 8 * len * (3k + 7) bytes and len * (8k + 2) flops."""
+    next basis vector: 8 * len * (3k + 7) bytes and len * (8k + 2) flops. Once:
+    two passes (V^T w; w -= V h0 with ||w||^2) and the scaling, 8 * len *
+    (2k + 5) bytes and len * (4k + 2) flops."""
     ln = 8 * n
     byts = flops = 0
     for it in range(int(its)):
         k = it % restart + 1
-        byts += 8 * ln * (3 * k + 7)
-        flops += ln * (8 * k + 2)
+        if orth == "cgs1":
+            byts += 8 * ln * (2 * k + 5)
+            flops += ln * (4 * k + 2)
+        else:
+            byts += 8 * ln * (3 * k + 7)
+            flops += ln * (8 * k + 2)
     return byts, flops
 
 
-def class_model(cls, n, nnzb, fp32=False, its=None):
+def class_model(cls, n, nnzb, fp32=False, its=None, orth="cgs2"):
     """(algorithmic bytes, flops) per call of a kernel class (None when unmodelled)."""
     if cls == "spmv":
         return spmv_bytes(n, nnzb), 2 * 64 * (nnzb - n)
@@ -275,11 +284,11 @@ def class_model(cls, n, nnzb, fp32=False, its=None):
     if cls == "gj":
         return 2 * (nnzb * BLOCK_BYTES + n * 64), n * 8 * 7 * 2 * 57
     if cls == "blas1" and its:
-        return gmres_blas1_work(n, its)
+        return gmres_blas1_work(n, its, orth=orth)
     return None, None
 
 
-def roofline(dom, stats, case, nnzb, fp64_gflops, precision="fp64", its=None):
+def roofline(dom, stats, case, nnzb, fp64_gflops, precision="fp64", its=None, orth="cgs2"):
     """Algorithmic bytes (or flops) per call of a kernel class over its average
     CUDA-event duration, against the measured HBM copy bandwidth or the FP64 FMA
     rate measured at start-up (whichever bounds the class: FP64 work above the
@@ -292,7 +301,7 @@ def roofline(dom, stats, case, nnzb, fp64_gflops, precision="fp64", its=None):
     calls = max(1, s["calls"])
     ms = s["ms"] / calls
     fp32 = precision != "fp64"
-    byts, flops = class_model(dom, n, nnzb, fp32, its)
+    byts, flops = class_model(dom, n, nnzb, fp32, its, orth)
     if dom == "blas1" and byts:
         byts, flops = byts / calls, flops / calls
     out = {"kernel": dom, "calls": calls, "ms_per_call": ms, "bytes_per_call": byts, "flops_per_call": flops}
@@ -414,7 +423,7 @@ def run_isc(args):
     build.build()
     fp64_gflops, fp32_gflops = isc.measure_fma_rates()
     case = workload_case(args.workload, args.grid)
-    b = Bench(case, precision=args.precision, prec=args.prec)
+    b = Bench(case, precision=args.precision, prec=args.prec, orth=args.orth)
     g = b.g
     n = case.n
     for _ in range(args.warmup):
@@ -446,7 +455,7 @@ def run_isc(args):
     value = job_throughput(world, args.steps, ms_total)
     kry = [i.krylov_iterations for i in infos]
     headline = leg_summary(ms_total / args.steps, stats, infos, args.steps)
-    e2e = mixed = mixed_fgmres = cpr_block = None
+    e2e = mixed = mixed_fgmres = cpr_block = cgs1 = None
     mst = fst = None
     leg_steps = max(3, args.steps // 4)
     leg_warm = max(1, min(2, args.warmup))
@@ -483,6 +492,10 @@ def run_isc(args):
             mixed_fgmres = leg_summary(ms, fst, fi, leg_steps, solve_fp64)
             mixed_fgmres["inner_its"] = INNER_ITS
             mixed_fgmres["roofline_spmv32"] = spmv32_roofline(fst, case, g.nnzb)
+            # the same step with classical Gram-Schmidt once (half the FP64 orthogonalisation work)
+            ms, gst, gi = b.leg(leg_steps, leg_warm, orth="cgs1")
+            cgs1 = leg_summary(ms, gst, gi, leg_steps, solve_fp64)
+            cgs1["blas1_ms_per_step"] = gst["blas1"]["ms"] / leg_steps
             # CPR-PF (the paper's Example-2 preconditioner) on the same step
             cpr_block = {}
             for p in ("fp64", "mixed", "mixed_fgmres"):
@@ -493,8 +506,8 @@ def run_isc(args):
     its_total = sum(kry)
     modelled = [k for k in stats if class_model(k, n, g.nnzb, its=its_total)[0] is not None]
     dom = max(modelled, key=lambda k: stats[k]["ms"])
-    roof = roofline(dom, stats, case, g.nnzb, fp64_gflops, args.precision, its_total)
-    rooflines = {k: roofline(k, stats, case, g.nnzb, fp64_gflops, args.precision, its_total)
+    roof = roofline(dom, stats, case, g.nnzb, fp64_gflops, args.precision, its_total, args.orth)
+    rooflines = {k: roofline(k, stats, case, g.nnzb, fp64_gflops, args.precision, its_total, args.orth)
                  for k in ("prec_apply", "spmv", "blas1", "gj", "ilu_factor") if stats[k]["calls"]}
     hbm = hbm_table(stats, mst, fst, case, g.nnzb)
     launches = sum(v["launches"] for v in stats.values())
@@ -505,7 +518,7 @@ def run_isc(args):
         "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
         "data": "synthetic",
-        "config": workload_config(case, world, args.precision, args.prec),
+        "config": workload_config(case, world, args.precision, args.prec, args.orth),
         "krylov_iterations_per_step": statistics.median(kry) if kry else None,
         "rel_residual": headline["rel_residual"],
         "e2e": e2e,
@@ -521,6 +534,7 @@ def run_isc(args):
         "mixed": mixed,
         "mixed_fgmres": mixed_fgmres,
         "cpr": cpr_block,
+        "cgs1": cgs1,
         "time_to_1e-6": None if mixed is None else {
             "fp64_solve_ms": headline["solve_ms"], "mixed_solve_ms": mixed["solve_ms"],
             "mixed_fgmres_solve_ms": mixed_fgmres["solve_ms"],
@@ -690,7 +704,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config(case, world, args.precision, args.prec),
+        "config": workload_config(case, world, args.precision, args.prec, args.orth),
         "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1, "host_cores": os.cpu_count(),
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},

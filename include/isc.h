@@ -83,6 +83,14 @@ enum isc_prec { ISC_PREC_NONE = 0, ISC_PREC_BJACOBI = 1, ISC_PREC_BILU0 = 2, ISC
  *   orthogonalisation and update stay FP64. Requires krylov = GMRES and
  *   prec = BILU0 or CPR. */
 enum isc_precision { ISC_PRECISION_FP64 = 0, ISC_PRECISION_MIXED = 1, ISC_PRECISION_MIXED_FGMRES = 2 };
+/* Orthogonalisation of the FP64 GMRES basis (the paper leaves it open).
+ * ISC_ORTH_CGS2: classical Gram-Schmidt applied twice (three passes over the
+ *   basis per iteration; orthogonal to working precision).
+ * ISC_ORTH_CGS1: classical Gram-Schmidt once (two passes; half the FP64 work
+ *   of CGS2, which on GB300's narrow FP64 pipe is the bound). The basis may
+ *   lose orthogonality on ill-conditioned Krylov spaces; the solver still
+ *   recomputes the true residual before it reports convergence. */
+enum isc_orth { ISC_ORTH_CGS2 = 0, ISC_ORTH_CGS1 = 1 };
 enum isc_rxn_kind {
   ISC_RXN_OIL_OXIDATION = 0,   /* r = A e^{-Ea/RT} (y_O2 p)(phi_f S_o rho_o x_i)           */
   ISC_RXN_CRACKING = 1,        /* r = A e^{-Ea/RT} (phi_f S_o rho_o x_i)(1-(C_c/C_max)^5)  */
@@ -199,6 +207,7 @@ typedef struct isc_options {
   int32_t precision;            /* isc_precision (applies to ISC_PREC_BILU0; MIXED also to CPR) */
   void* stream;
   int32_t inner_its;            /* ISC_PRECISION_MIXED_FGMRES: FP32 GMRES iterations per outer one, 1..32 (10) */
+  int32_t orth;                 /* isc_orth of the FP64 GMRES (default CGS2) */
 } isc_options;
 
 typedef struct isc_newton_info {

@@ -312,6 +312,8 @@ int gmres(isc_handle* h, const double* b, double* x, int* its_out, double* rel_o
   int its = 0;
   double rel = 1.0;
   bool first = true;
+  // single classical Gram-Schmidt leaves the second set of coefficients at zero
+  if (h->opt.orth == ISC_ORTH_CGS1) cudaMemsetAsync(h->scal + S_H1, 0, sizeof(double) * (MAX_RESTART + 8), s);
   while (its < h->opt.maxit_lin) {
     double beta;
     if (first) {
@@ -368,7 +370,16 @@ int gmres(isc_handle* h, const double* b, double* x, int* its_out, double* rel_o
       double* Zj = Z + (size_t)j * h->vstride;
       prec(h, Vj, Zj);
       spmv(h, Zj, h->w);
-      {
+      if (h->opt.orth == ISC_ORTH_CGS1) {
+        // classical Gram-Schmidt once: h0 = V^T w; w -= V h0 fused with ||w||^2 (h1 stays 0)
+        Region rg(h, ISC_K_BLAS1, 4);
+        launch_mdot(*h, V, j + 1, h->w, S_H0, s);
+        launch_maxpy_norm(*h, h->w, V, j + 1, S_H0, S_NRM, s);
+        launch_gmres_givens(*h, j, m, bnorm, S_H0, S_H1, S_NRM, s);
+        launch_scale_dev(*h, h->w, V + (size_t)(j + 1) * h->vstride, s);
+        cudaMemcpyAsync(h->h_ring + 3 * (j & 1), gmres_status(*h), 3 * sizeof(double), cudaMemcpyDeviceToHost, s);
+        cudaEventRecord(h->gm_ev[j & 1], s);
+      } else {
         // classical Gram-Schmidt applied twice: h0 = V^T w; w -= V h0 fused with h1 = V^T w;
         // w -= V h1 fused with ||w||^2
         Region rg(h, ISC_K_BLAS1, j + 1 <= 32 ? 5 : 6);
@@ -587,6 +598,7 @@ int validate_options(isc_handle* h, const isc_options& o) {
       return set_err(h, ISC_ERR_INVALID_ARG, "mixed_fgmres needs krylov = GMRES and prec = BILU0 or CPR");
     if (o.inner_its < 1 || o.inner_its > 32) return set_err(h, ISC_ERR_INVALID_ARG, "inner_its must be 1..32");
   }
+  if (o.orth != ISC_ORTH_CGS2 && o.orth != ISC_ORTH_CGS1) return set_err(h, ISC_ERR_INVALID_ARG, "unknown orth");
   if (!(o.tol_lin > 0.0) || o.maxit_lin < 1 || !(o.tol_newton >= 0.0) || o.maxit_newton < 1)
     return set_err(h, ISC_ERR_INVALID_ARG, "tolerances must be positive and iteration limits >= 1");
   return ISC_OK;
@@ -812,6 +824,7 @@ void isc_default_options(isc_options* o) {
   o->precision = ISC_PRECISION_FP64;
   o->stream = nullptr;
   o->inner_its = 10;
+  o->orth = ISC_ORTH_CGS2;
 }
 
 const char* isc_status_string(int st) {

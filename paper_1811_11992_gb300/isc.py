@@ -29,6 +29,7 @@ STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "out of device 
 KRYLOV = {"gmres": 0, "bicgstab": 1}
 PREC = {"none": 0, "bjacobi": 1, "bilu0": 2, "ilu0": 2, "cpr": 3}
 PRECISION = {"fp64": 0, "mixed": 1, "mixed_fgmres": 2}
+ORTH = {"cgs2": 0, "cgs1": 1}
 K_CLASSES = ("props", "flux", "norm", "gj", "ilu_factor", "spmv", "prec_apply", "blas1", "update", "adjoint",
              "cpr", "spmv32")
 
@@ -81,7 +82,7 @@ class isc_options(C.Structure):
                 ("tol_lin", C.c_double), ("maxit_lin", C.c_int32), ("tol_newton", C.c_double),
                 ("maxit_newton", C.c_int32), ("max_dp_frac", C.c_double), ("max_dT", C.c_double),
                 ("profile", C.c_int32), ("precision", C.c_int32), ("stream", C.c_void_p),
-                ("inner_its", C.c_int32)]
+                ("inner_its", C.c_int32), ("orth", C.c_int32)]
 
 
 class isc_newton_info(C.Structure):
@@ -213,6 +214,8 @@ def default_options(**kw) -> isc_options:
             v = PREC[v] if isinstance(v, str) else v
         if k == "precision":
             v = PRECISION[v] if isinstance(v, str) else v
+        if k == "orth":
+            v = ORTH[v] if isinstance(v, str) else v
         setattr(o, k, v)
     return o
 
@@ -323,6 +326,8 @@ class Simulator:
                 v = PREC[v] if isinstance(v, str) else v
             if k == "precision":
                 v = PRECISION[v] if isinstance(v, str) else v
+            if k == "orth":
+                v = ORTH[v] if isinstance(v, str) else v
             setattr(self.options, k, v)
         self._check(self.lib.isc_set_options(self.h, C.byref(self.options)))
 

@@ -23,3 +23,15 @@ def decoupled(case, seed_a, seed_b, dt=100.0):
     rp, col, J, F = assembled(case, seed_a, seed_b, dt)
     vd, rd = linalg.gauss_jordan_decouple(rp, col, J, F.T.copy())
     return rp, col, J, F, vd, rd.T.copy()
+
+
+def initial_decoupled(case, dt):
+    """(rowptr, col, Jd, Fd): the oracle's decoupled system at the case's
+    flash-consistent initial state (ignited cells included) for step size dt."""
+    from oracle import sim
+    u0, c0 = sim.initial_state(case)
+    acc = model.old_accumulation(case, u0, c0)
+    F = model.residual(case, u0, c0, acc, dt)
+    rp, col, J = model.jacobian(case, u0, c0, acc, dt)
+    vd, rd = linalg.gauss_jordan_decouple(rp, col, J, F.T.copy())
+    return rp, col, vd, rd.T.copy()

@@ -158,6 +158,7 @@ def test_binding_constants_match_the_header_enums():
     assert isc.PREC["bilu0"] == e["ISC_PREC_BILU0"] and isc.PREC["cpr"] == e["ISC_PREC_CPR"]
     assert isc.PRECISION == {"fp64": e["ISC_PRECISION_FP64"], "mixed": e["ISC_PRECISION_MIXED"],
                              "mixed_fgmres": e["ISC_PRECISION_MIXED_FGMRES"]}
+    assert isc.ORTH == {"cgs2": e["ISC_ORTH_CGS2"], "cgs1": e["ISC_ORTH_CGS1"]}
     defines = dict(re.findall(r"#define\s+(ISC_[A-Z0-9_]+)\s+(\d+)", open(os.path.join(ROOT, "include", "isc.h")).read()))
     assert isc.NOALLOC_MAX_CELLS == int(defines["ISC_NOALLOC_MAX_CELLS"])
     statuses = {v for k, v in e.items() if k == "ISC_OK" or k.startswith("ISC_ERR_")}

@@ -102,21 +102,39 @@ def _oracle_decoupled(case, dt):
     return rp, col, vd, rd
 
 
+def _gmres_iterate(rp, col, A, b, m, M, rng=None):
+    """The oracle's GMRES iterate after m iterations from x0 = 0 (b, x as (8, N)).
+    With rng, every matrix-vector product and preconditioner application is
+    perturbed by a relative +-u32 per entry: a model of FP32 kernels rounding
+    their outputs at each iteration."""
+    def noisy(v):
+        return v if rng is None else v * (1 + U32 * rng.choice([-1.0, 1.0], v.shape))
+
+    class P:
+        def apply(self, v):
+            return noisy(M.apply(v))
+
+    x, its, _ = linalg.gmres(lambda v: noisy(linalg.bsr_matvec(rp, col, A, v)), b.T.copy(), P(), restart=m,
+                             rtol=1e-300, maxit=m)
+    assert its == m
+    return x.T
+
+
 @pytest.mark.parametrize("dt,m", [(1000.0, 1), (1000.0, 8), (1000.0, 20), (None, 8), (None, 20)])
 def test_fgmres_inner_solve_is_the_oracle_gmres_iterate(Simulator, dt, m):
     """The preconditioner of mixed_fgmres is m iterations of ILU(0)-preconditioned
     GMRES from x0 = 0 on the FP32 copy of the decoupled matrix: the oracle's FP64
     GMRES stopped after m iterations on that same rounded matrix (and the ILU(0)
     of it) gives the same iterate, to the FP32 arithmetic of the GPU's Krylov
-    vectors, sweeps and SpMV. The bound is the FP32 unit roundoff times the
-    iterate's sensitivity S to FP32-sized relative perturbations of the matrix
-    and the right-hand side (measured on the oracle: two more GMRES runs with
-    seeded perturbations of size u32), times m (each of the m iterations rounds
-    its products, sweeps and orthogonalisation once more, and those errors add)
-    and a margin of 32. (The residual in that matrix is
-    not compared: a 1e-6 relative change of the iterate moves it by the condition
-    number times as much.) The system is the oracle's, loaded through
-    isc_set_system."""
+    vectors, sweeps and SpMV. The bound is S u32 times 64: S is the iterate's
+    measured sensitivity to FP32 rounding (two more oracle runs whose every
+    product and preconditioner output carries a relative +-u32 perturbation,
+    largest deviation over u32), 64 covers the rounding accumulated inside each
+    kernel's output (up to 48 products per SpMV row, the sweeps' chains). At
+    the workload's first step GMRES stagnates and S is in the thousands; at a
+    1000 s step it is about 60. (The residual in that matrix is not compared: a
+    1e-6 relative change of the iterate moves it by the condition number times
+    as much.) The system is the oracle's, loaded through isc_set_system."""
     case = inp.field_case(13, 7, 3, 0, 1, "field 13x7x3", 30 * inp.DAY, 40)
     rp, col, vd, rd = _oracle_decoupled(case, dt or case.dt0)
     g = Simulator(case, precision="mixed_fgmres", inner_its=m)
@@ -126,23 +144,13 @@ def test_fgmres_inner_solve_is_the_oracle_gmres_iterate(Simulator, dt, m):
     r = np.random.default_rng(31).standard_normal((8, case.n))
     r32 = r.astype(np.float32).astype(np.float64)
     z = g.precond_apply(r)
-
-    def gmres_m(A, b):
-        M = linalg.ILU0Preconditioner(rp, col, A)
-        x, its, _ = linalg.gmres(lambda v: linalg.bsr_matvec(rp, col, A, v), b.T.copy(), M, restart=m,
-                                 rtol=1e-300, maxit=m)
-        assert its == m
-        return x.T
-
-    x = gmres_m(A32, r32)
+    M = linalg.ILU0Preconditioner(rp, col, A32)
+    x = _gmres_iterate(rp, col, A32, r32, m, M)
     rng = np.random.default_rng(32)
-    sens = 0.0
-    for _ in range(2):
-        Ap = A32 * (1 + U32 * rng.choice([-1.0, 1.0], A32.shape))
-        bp = r32 * (1 + U32 * rng.choice([-1.0, 1.0], r32.shape))
-        sens = max(sens, np.max(np.abs(gmres_m(Ap, bp) - x)) / np.abs(x).max() / U32)
+    sens = max(np.max(np.abs(_gmres_iterate(rp, col, A32, r32, m, M, rng) - x)) for _ in range(2))
+    sens = sens / np.abs(x).max() / U32
     err = np.max(np.abs(z - x)) / np.abs(x).max()
-    assert err <= 32 * m * max(sens, 1.0) * U32, (err, sens, err / (m * max(sens, 1.0) * U32))
+    assert err <= 64 * max(sens, 1.0) * U32, (err, sens, err / (max(sens, 1.0) * U32))
     assert err > 1e-9, err         # really FP32
     g.close()
 

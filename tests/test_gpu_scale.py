@@ -110,9 +110,12 @@ def test_fp32_ilu0_factor_and_sweeps_beyond_one_round_of_warps(Simulator, system
     g.close()
 
 
-def test_spmv_and_gmres_on_the_oracle_system(Simulator, system):
+@pytest.mark.parametrize("orth", ["cgs2", "cgs1"])
+def test_spmv_and_gmres_on_the_oracle_system(Simulator, system, orth):
+    """GMRES with classical Gram-Schmidt twice or once: either way the update's
+    residual in the oracle's own decoupled system meets the tolerance."""
     case = system["case"]
-    g = Simulator(case, tol_lin=1e-10, maxit_lin=3000)
+    g = Simulator(case, tol_lin=1e-10, maxit_lin=3000, orth=orth)
     g.set_system(system["vd"], system["rd"].T, decoupled=True)
     x = system["x"]
     y = g.spmv(x.T)
