@@ -97,14 +97,17 @@ def test_reference_and_library_arms_share_the_config(bench):
 def test_gram_schmidt_model(bench):
     # one iteration against one basis vector: 3 passes of (1 vector + w), 2 writes of w,
     # the scaling pass: (3*1 + 7) vector passes; 8*1 + 2 flops per element
-    b, f = bench.gmres_blas1_work(10, 1)
+    b, f = bench.gmres_blas1_work(10, 1, orth="cgs2")
     assert b == 8 * 80 * 10 and f == 80 * 10
+    # once: two passes of (1 vector + w), one write of w, the scaling: (2*1 + 5) passes; 4*1 + 2 flops
+    b1, f1 = bench.gmres_blas1_work(10, 1, orth="cgs1")
+    assert b1 == 8 * 80 * 7 and f1 == 80 * 6
     # restart cycles: iteration 31 of GMRES(30) works on one vector again
-    b31, _ = bench.gmres_blas1_work(10, 31)
-    b30, _ = bench.gmres_blas1_work(10, 30)
+    b31, _ = bench.gmres_blas1_work(10, 31, orth="cgs2")
+    b30, _ = bench.gmres_blas1_work(10, 30, orth="cgs2")
     assert b31 - b30 == b
     case = _Case(200, 200, 50)
     nnzb = _nnzb(200, 200, 50)
     st = {"blas1": {"calls": 1140, "ms": 2800.0, "launches": 5700}}
-    r = bench.roofline("blas1", st, case, nnzb, 1057.0, "fp64", its=1140)
+    r = bench.roofline("blas1", st, case, nnzb, 1057.0, "fp64", its=1140, orth="cgs2")
     assert r["bound"] == "alu" and 0.5 < r["frac"] < 1.0
