@@ -689,22 +689,17 @@ __global__ void __launch_bounds__(FWARPS * 32) k_ilu_factor_pipe(int nx, int ny,
           }
         }
         __syncwarp();
+        // one FMA per entry for every row: the pivot row becomes p (1 + (inv - 1)) = p inv,
+        // row r != kp becomes a_r - (a_r,kp inv) p; the multiplier costs one FP64 op per lane
         const T inv = recip_nr(sD[kp * 8 + kp]);
-        const T f = sD[r * 8 + kp];
+        const T g = (r == kp) ? inv - T(1) : -sD[r * 8 + kp] * inv;
+        const T p0 = sD[kp * 8 + c], p1 = sD[kp * 8 + c + 1];
+        const T q0 = sI[kp * 8 + c], q1 = sI[kp * 8 + c + 1];
         __syncwarp();
-        if (r == kp) {
-          sD[kp * 8 + c] *= inv;
-          sD[kp * 8 + c + 1] *= inv;
-          sI[kp * 8 + c] *= inv;
-          sI[kp * 8 + c + 1] *= inv;
-        }
-        __syncwarp();
-        if (r != kp) {
-          sD[r * 8 + c] -= f * sD[kp * 8 + c];
-          sD[r * 8 + c + 1] -= f * sD[kp * 8 + c + 1];
-          sI[r * 8 + c] -= f * sI[kp * 8 + c];
-          sI[r * 8 + c + 1] -= f * sI[kp * 8 + c + 1];
-        }
+        sD[r * 8 + c] = fma(g, p0, sD[r * 8 + c]);
+        sD[r * 8 + c + 1] = fma(g, p1, sD[r * 8 + c + 1]);
+        sI[r * 8 + c] = fma(g, q0, sI[r * 8 + c]);
+        sI[r * 8 + c + 1] = fma(g, q1, sI[r * 8 + c + 1]);
         __syncwarp();
       }
       if (bad) {

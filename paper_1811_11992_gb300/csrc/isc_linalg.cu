@@ -1,6 +1,6 @@
 // Linear algebra of the Newton step on the 8x8 block-sparse system.
 //
-// k_gj          Gauss-Jordan decoupling (Sec. 3.2): one warp per block row,
+// k_gj          Gauss-Jordan decoupling (Sec. 3.2): one half-warp per block row,
 //               lanes own columns of the augmented row [J_i,* | F_i], partial
 //               pivoting with warp shuffles; the diagonal block becomes I.
 // k_spmv        y = A x, one warp per block row, each lane streams one double2
@@ -43,14 +43,26 @@ __device__ __forceinline__ bool nbr_exists(int nx, int ny, int nz, int c, int d,
   }
 }
 
+// Gauss-Jordan decoupling, two block rows per warp (one per half-warp). Lane h
+// of a half owns the columns h, h+16, h+32, h+48 of the augmented row
+// [J_i,* | F_i (| B_i)] (at most 7*8 + 2 = 58 of 64 columns), all 8 rows of
+// each, in registers. Per pivot step the FP64 work of a lane is the pivot
+// reciprocal, one multiplier and 4 x 8 updates, shared by the half's 16 lanes:
+// the multipliers -a_rk / a_kk are computed one per lane (lane h for row h % 8)
+// and gathered by shuffles, so the narrow FP64 pipe spends almost all of its
+// issue slots on the elimination itself. The pivot search and the pivot test
+// run on the integer bit patterns of |a| (IEEE order is numeric order for
+// non-negative values), with the exact floating-point test of the singularity
+// threshold only when the exponents leave it undecided.
 __global__ void __launch_bounds__(256) k_gj(int n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                                             double* __restrict__ J, double* __restrict__ R, int* __restrict__ dstatus,
                                             const int32_t* __restrict__ well_slot, const WellSlot* __restrict__ slots,
                                             double* __restrict__ Bv) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (warp >= n) return;
-  const int i = warp;
+  const int h = lane & 15, hb = lane & 16;
+  const int row = ((blockIdx.x * blockDim.x + threadIdx.x) >> 4);
+  const bool live = row < n;
+  const int i = live ? row : n - 1;  // a spare half repeats the last row and stores nothing
   const int b0 = rowptr[i];
   const int nb = rowptr[i + 1] - b0;
   int d = 0;
@@ -58,16 +70,16 @@ __global__ void __launch_bounds__(256) k_gj(int n, const int32_t* __restrict__ r
     if (col[b0 + s] == i) d = s;
   const int nc = nb * 8;
   // a perforation of a coupled producer carries its border column dF/d bhp as
-  // one more column of the augmented row (at most 7*8 + 2 = 58 of 64 columns)
+  // one more column of the augmented row
   int bs = -1;
   if (Bv) {
     const int sl = well_slot[i];
     if (sl >= 0 && slots[sl].wc >= 0) bs = sl;
   }
-  double a[2][8];
+  double a[4][8];
 #pragma unroll
-  for (int m = 0; m < 2; ++m) {
-    int cc = lane + 32 * m;
+  for (int m = 0; m < 4; ++m) {
+    const int cc = h + 16 * m;
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
       double v = 0.0;
@@ -80,35 +92,35 @@ __global__ void __launch_bounds__(256) k_gj(int n, const int32_t* __restrict__ r
       a[m][r] = v;
     }
   }
-  // Magnitudes are compared as the integer bit patterns of |a| (IEEE order equals
-  // numeric order for non-negative values): the pivot search and the singularity
-  // test then run on the integer units, not on GB300's scarce FP64 pipe, and choose
-  // exactly what the floating-point compares would.
   auto mag = [](double v) { return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull; };
+  const int rr = h & 7;  // the row whose multiplier this lane computes
+  bool bad = false;
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
     const int pc = d * 8 + k;
-    const int pl = pc & 31, pm = pc >> 5;
+    const int pl = pc & 15, pm = pc >> 4;
+    // the pivot column as seen by its owner lane
+    double pcol[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) pcol[r] = pm == 0 ? a[0][r] : pm == 1 ? a[1][r] : pm == 2 ? a[2][r] : a[3][r];
     int piv = k;
-    if (lane == pl) {
+    if (h == pl) {
       unsigned long long best = 0ull;
-      bool first = true;
 #pragma unroll
       for (int r = k; r < 8; ++r) {
-        const unsigned long long v = mag(pm ? a[1][r] : a[0][r]);
-        if (first || v > best) {
+        const unsigned long long v = mag(pcol[r]);
+        if (r == k || v > best) {
           best = v;
           piv = r;
-          first = false;
         }
       }
     }
-    piv = __shfl_sync(FULL, piv, pl);
-    // max |a| of row piv inside the diagonal block (singularity test)
+    piv = __shfl_sync(FULL, piv, hb + pl);
+    // largest |a| of row piv inside the diagonal block (columns d*8 .. d*8+7)
     unsigned long long rmb = 0ull;
 #pragma unroll
-    for (int m = 0; m < 2; ++m) {
-      int cc = lane + 32 * m;
+    for (int m = 0; m < 4; ++m) {
+      const int cc = h + 16 * m;
       if (cc >= d * 8 && cc < d * 8 + 8) {
 #pragma unroll
         for (int r = 0; r < 8; ++r)
@@ -116,48 +128,71 @@ __global__ void __launch_bounds__(256) k_gj(int n, const int32_t* __restrict__ r
       }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) rmb = max(rmb, (unsigned long long)__shfl_xor_sync(FULL, rmb, o));
-    const double rm = __longlong_as_double((long long)rmb);
+    for (int o = 8; o > 0; o >>= 1) rmb = max(rmb, (unsigned long long)__shfl_xor_sync(FULL, rmb, o));
     // swap rows k and piv
-    if (piv != k) {
 #pragma unroll
-      for (int m = 0; m < 2; ++m) {
+    for (int m = 0; m < 4; ++m) {
 #pragma unroll
-        for (int r = k + 1; r < 8; ++r) {
-          if (r == piv) {
-            double t = a[m][r];
-            a[m][r] = a[m][k];
-            a[m][k] = t;
-          }
+      for (int r = k + 1; r < 8; ++r) {
+        if (r == piv) {
+          const double t = a[m][r];
+          a[m][r] = a[m][k];
+          a[m][k] = t;
         }
       }
     }
+    // the pivot column after the swap, from its owner lane
     double colk[8];
 #pragma unroll
-    for (int r = 0; r < 8; ++r) colk[r] = __shfl_sync(FULL, pm ? a[1][r] : a[0][r], pl);
+    for (int r = 0; r < 8; ++r)
+      colk[r] = __shfl_sync(FULL, pm == 0 ? a[0][r] : pm == 1 ? a[1][r] : pm == 2 ? a[2][r] : a[3][r], hb + pl);
     const double pv = colk[k];
-    if (!(fabs(pv) > 1e-300 * fmax(rm, 1e-300))) {
-      if (lane == 0) atomicOr(dstatus, DS_SINGULAR);
-      return;
+    // |pv| > 1e-300 max(|row max|, 1e-300): decided on the exponents when pv is a finite
+    // normal number at most 900 binades below the row maximum (then the product side is
+    // below 2^(e - 994) <= |pv|); otherwise in floating point
+    const unsigned long long pb = mag(pv);
+    const int epv = (int)(pb >> 52), erm = (int)(rmb >> 52);
+    bool ok;
+    if (epv > 0 && epv < 0x7ff && epv + 900 >= erm) {
+      ok = true;
+    } else {
+      const double rm = __longlong_as_double((long long)rmb);
+      ok = fabs(pv) > 1e-300 * fmax(rm, 1e-300);
     }
-    const double inv = recip_nr(pv);
+    // a singular half keeps stepping (its lanes take part in every shuffle of the
+    // warp) with a zero reciprocal and stores nothing
+    bad = bad || !ok;
+    const double inv = ok ? recip_nr(pv) : 0.0;
+    // this lane's multiplier -a_rk / a_kk for row rr (0 for the pivot row), gathered by the half
+    double own = 0.0;
 #pragma unroll
-    for (int m = 0; m < 2; ++m) a[m][k] = a[m][k] * inv;
+    for (int r = 0; r < 8; ++r)
+      if (r == rr) own = colk[r];
+    own = rr == k ? 0.0 : -own * inv;
+    double coef[8];
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      if (r == k) continue;
+    for (int r = 0; r < 8; ++r) coef[r] = __shfl_sync(FULL, own, hb + r);
 #pragma unroll
-      for (int m = 0; m < 2; ++m) a[m][r] = a[m][r] - colk[r] * a[m][k];
+    for (int m = 0; m < 4; ++m) {
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+        if (r != k) a[m][r] = fma(coef[r], a[m][k], a[m][r]);
+      a[m][k] = a[m][k] * inv;
     }
   }
+  if (bad) {
+    if (live && h == 0) atomicOr(dstatus, DS_SINGULAR);
+    return;
+  }
+  if (!live) return;
 #pragma unroll
-  for (int m = 0; m < 2; ++m) {
-    int cc = lane + 32 * m;
+  for (int m = 0; m < 4; ++m) {
+    const int cc = h + 16 * m;
     if (cc < nc) {
-      int s = cc / 8, c = cc & 7;
+      const int s = cc / 8, c = cc & 7;
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
-        double v = (s == d) ? (r == c ? 1.0 : 0.0) : a[m][r];
+        const double v = (s == d) ? (r == c ? 1.0 : 0.0) : a[m][r];
         J[(size_t)(b0 + s) * BB + r * 8 + c] = v;
       }
     } else if (cc == nc) {
@@ -842,7 +877,7 @@ int grid_for(size_t work, int tb) {
 
 void launch_gj(Handle& h, cudaStream_t s) {
   int tb = 256;
-  k_gj<<<(h.n * 32 + tb - 1) / tb, tb, 0, s>>>(h.n, h.rowptr, h.col, h.J, h.R, h.dstatus, h.well_slot, h.slots,
+  k_gj<<<(h.n * 16 + tb - 1) / tb, tb, 0, s>>>(h.n, h.rowptr, h.col, h.J, h.R, h.dstatus, h.well_slot, h.slots,
                                                h.nwc > 0 ? h.Bv : nullptr);
 }
 
