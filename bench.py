@@ -389,7 +389,8 @@ def leg_summary(ms, st, infos, steps, solve_ref_ms=None):
            "krylov_iterations_per_step": statistics.median([i.krylov_iterations for i in infos]),
            "rel_residual": max(i.krylov_rel_residual for i in infos),
            "solve_ms": solve,
-           "prec_apply_ms_per_call": st["prec_apply"]["ms"] / max(1, st["prec_apply"]["calls"])}
+           "prec_apply_ms_per_call": st["prec_apply"]["ms"] / max(1, st["prec_apply"]["calls"]),
+           "kernel_ms_per_step": {k: round(v["ms"] / steps, 3) for k, v in st.items() if v["ms"] > 0}}
     if solve_ref_ms is not None:
         out["solve_ms_fp64"] = solve_ref_ms
         out["solve_speedup_vs_fp64"] = solve_ref_ms / solve if solve > 0 else None
