@@ -993,6 +993,152 @@ void launch_update(Handle& h, cudaStream_t s) {
   k_update<<<(h.n + 127) / 128, 128, 0, s>>>(h.n, h.u, h.du, h.opt.max_dp_frac, h.opt.max_dT);
 }
 
+// FP32 Gram-Schmidt passes of the inner solve with 16-byte loads (four elements
+// per lane and load). An FP32 vector carries half the bytes of an FP64 one per
+// element, so with scalar loads too few bytes were in flight per SM to cover
+// the HBM latency; the norm is accumulated in FP32 per lane (about 100 elements
+// each) so that no per-element work reaches the narrow FP64 pipe. Lengths are
+// multiples of 4 (8 per cell) and the vectors 16-byte aligned.
+template <int NG>
+__global__ void __launch_bounds__(RED_THREADS) k_mdot4(int len4, const float4* __restrict__ V, size_t vs4, int nvec,
+                                                       const float4* __restrict__ w, double* __restrict__ partial,
+                                                       unsigned* counter, double* __restrict__ out) {
+  __shared__ double sh[NG * 8][RED_THREADS / 32];
+  float acc[NG][8];
+#pragma unroll
+  for (int g = 0; g < NG; ++g)
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc[g][i] = 0.f;
+  const int stride = gridDim.x * blockDim.x;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < len4; e += stride) {
+    const float4 we = w[e];
+#pragma unroll
+    for (int g = 0; g < NG; ++g)
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        if (g * 8 + i < nvec) {
+          const float4 v = V[(size_t)(g * 8 + i) * vs4 + e];
+          acc[g][i] = fmaf(v.x, we.x, fmaf(v.y, we.y, fmaf(v.z, we.z, fmaf(v.w, we.w, acc[g][i]))));
+        }
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int g = 0; g < NG; ++g) {
+    double a8[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a8[i] = (double)acc[g][i];
+    const double v = warp_reduce8(a8, lane);
+    if ((lane & 3) == 0) sh[g * 8 + red8_index(lane)][warp] = v;
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < nvec; c += blockDim.x) {
+    double v = 0.0;
+#pragma unroll
+    for (int q = 0; q < RED_THREADS / 32; ++q) v += sh[c][q];
+    partial[(size_t)c * gridDim.x + blockIdx.x] = v;
+  }
+  last_block_finish(nvec, gridDim.x, partial, counter, out);
+}
+
+// w <- w - V coef, then out = V^T w (each V_c loaded once for both)
+template <int NG>
+__global__ void __launch_bounds__(RED_THREADS) k_maxpy_mdot4(int len4, float4* __restrict__ w,
+                                                             const float4* __restrict__ V, size_t vs4, int nvec,
+                                                             const double* __restrict__ coef,
+                                                             double* __restrict__ partial, unsigned* counter,
+                                                             double* __restrict__ out) {
+  __shared__ double sh[NG * 8][RED_THREADS / 32];
+  __shared__ float sc[NG * 8];
+  for (int c = threadIdx.x; c < NG * 8; c += blockDim.x) sc[c] = c < nvec ? (float)coef[c] : 0.f;
+  __syncthreads();
+  float acc[NG][8];
+#pragma unroll
+  for (int g = 0; g < NG; ++g)
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc[g][i] = 0.f;
+  const int stride = gridDim.x * blockDim.x;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < len4; e += stride) {
+    float4 v[NG][8];
+#pragma unroll
+    for (int g = 0; g < NG; ++g)
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        v[g][i] = (g * 8 + i < nvec) ? V[(size_t)(g * 8 + i) * vs4 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 we = w[e];
+#pragma unroll
+    for (int g = 0; g < NG; ++g)
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        if (g * 8 + i < nvec) {
+          const float c = sc[g * 8 + i];
+          we.x = fmaf(-c, v[g][i].x, we.x);
+          we.y = fmaf(-c, v[g][i].y, we.y);
+          we.z = fmaf(-c, v[g][i].z, we.z);
+          we.w = fmaf(-c, v[g][i].w, we.w);
+        }
+    w[e] = we;
+#pragma unroll
+    for (int g = 0; g < NG; ++g)
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        if (g * 8 + i < nvec)
+          acc[g][i] = fmaf(v[g][i].x, we.x, fmaf(v[g][i].y, we.y, fmaf(v[g][i].z, we.z, fmaf(v[g][i].w, we.w, acc[g][i]))));
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int g = 0; g < NG; ++g) {
+    double a8[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a8[i] = (double)acc[g][i];
+    const double r = warp_reduce8(a8, lane);
+    if ((lane & 3) == 0) sh[g * 8 + red8_index(lane)][warp] = r;
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < nvec; c += blockDim.x) {
+    double r = 0.0;
+#pragma unroll
+    for (int q = 0; q < RED_THREADS / 32; ++q) r += sh[c][q];
+    partial[(size_t)c * gridDim.x + blockIdx.x] = r;
+  }
+  last_block_finish(nvec, gridDim.x, partial, counter, out);
+}
+
+// w <- w - V coef, then out = ||w||^2
+__global__ void __launch_bounds__(RED_THREADS) k_maxpy_norm4(int len4, float4* __restrict__ w,
+                                                             const float4* __restrict__ V, size_t vs4, int nvec,
+                                                             const double* __restrict__ coef,
+                                                             double* __restrict__ partial, unsigned* counter,
+                                                             double* __restrict__ out) {
+  __shared__ double sh[RED_THREADS / 32];
+  __shared__ float sc[MAX_VEC];
+  for (int c = threadIdx.x; c < nvec; c += blockDim.x) sc[c] = (float)coef[c];
+  __syncthreads();
+  const int stride = gridDim.x * blockDim.x;
+  float nrm = 0.f;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < len4; e += stride) {
+    float4 we = w[e];
+    for (int c0 = 0; c0 < nvec; c0 += DOT_G) {
+      float4 v[DOT_G];
+#pragma unroll
+      for (int g = 0; g < DOT_G; ++g)
+        v[g] = (c0 + g < nvec) ? V[(size_t)(c0 + g) * vs4 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int g = 0; g < DOT_G; ++g) {
+        const float c = (c0 + g < nvec) ? sc[c0 + g] : 0.f;
+        we.x = fmaf(-c, v[g].x, we.x);
+        we.y = fmaf(-c, v[g].y, we.y);
+        we.z = fmaf(-c, v[g].z, we.z);
+        we.w = fmaf(-c, v[g].w, we.w);
+      }
+    }
+    w[e] = we;
+    nrm = fmaf(we.x, we.x, fmaf(we.y, we.y, fmaf(we.z, we.z, fmaf(we.w, we.w, nrm))));
+  }
+  const double b = block_sum((double)nrm, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = b;
+  last_block_finish(1, gridDim.x, partial, counter, out);
+}
+
 // Gram-Schmidt passes over vectors of length len stored vs apart (FP64 for the
 // outer Krylov solve, FP32 for the inner one of the mixed-precision scheme);
 // results (FP64) go to out; reductions use the handle's partial/counter buffers
@@ -1085,15 +1231,45 @@ void launch_spmv32(int nrows, const int32_t* rowptr, const int32_t* col, const f
   const int tb = 256;
   k_spmv<float><<<(int)(((size_t)nrows * 32 + tb - 1) / tb), tb, 0, s>>>(nrows, rowptr, col, val, x, y, unit_diag);
 }
+// the inner solve's vectors are 8N floats stored 8N apart: 16-byte loads unless
+// a caller passes a length or stride that is not a multiple of 4
+static bool vec4_ok(int len, size_t vs, const void* a, const void* b) {
+  return len % 4 == 0 && vs % 4 == 0 && ((uintptr_t)a & 15) == 0 && ((uintptr_t)b & 15) == 0;
+}
 void launch_mdot32(Handle& h, int len, size_t vs, const float* V, int nvec, const float* w, double* out, cudaStream_t s) {
+  if (vec4_ok(len, vs, V, w) && nvec <= 16) {
+    const float4 *V4 = reinterpret_cast<const float4*>(V), *w4 = reinterpret_cast<const float4*>(w);
+    if (nvec <= 8)
+      k_mdot4<1><<<2 * h.red_blocks, RED_THREADS, 0, s>>>(len / 4, V4, vs / 4, nvec, w4, h.partial, h.red_counter, out);
+    else
+      k_mdot4<2><<<2 * h.red_blocks, RED_THREADS, 0, s>>>(len / 4, V4, vs / 4, nvec, w4, h.partial, h.red_counter, out);
+    return;
+  }
   mdot_t<float>(h, len, vs, V, nvec, w, out, s);
 }
 void launch_maxpy_mdot32(Handle& h, int len, size_t vs, float* w, const float* V, int nvec, const double* coef,
                          double* out, cudaStream_t s) {
+  if (vec4_ok(len, vs, V, w) && nvec <= 16) {
+    float4* w4 = reinterpret_cast<float4*>(w);
+    const float4* V4 = reinterpret_cast<const float4*>(V);
+    if (nvec <= 8)
+      k_maxpy_mdot4<1><<<2 * h.red_blocks, RED_THREADS, 0, s>>>(len / 4, w4, V4, vs / 4, nvec, coef, h.partial,
+                                                                h.red_counter, out);
+    else
+      k_maxpy_mdot4<2><<<2 * h.red_blocks, RED_THREADS, 0, s>>>(len / 4, w4, V4, vs / 4, nvec, coef, h.partial,
+                                                                h.red_counter, out);
+    return;
+  }
   maxpy_mdot_t<float>(h, len, vs, w, V, nvec, coef, out, s);
 }
 void launch_maxpy_norm32(Handle& h, int len, size_t vs, float* w, const float* V, int nvec, const double* coef,
                          double* out, cudaStream_t s) {
+  if (vec4_ok(len, vs, V, w)) {
+    k_maxpy_norm4<<<2 * h.red_blocks, RED_THREADS, 0, s>>>(len / 4, reinterpret_cast<float4*>(w),
+                                                           reinterpret_cast<const float4*>(V), vs / 4, nvec, coef,
+                                                           h.partial, h.red_counter, out);
+    return;
+  }
   maxpy_norm_t<float>(h, len, vs, w, V, nvec, coef, out, s);
 }
 void launch_comb_out32(int len, const float* V, size_t vs, int nvec, const double* coef, double* out, cudaStream_t s) {
