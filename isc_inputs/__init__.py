@@ -48,6 +48,7 @@ RXN_COKE_OXIDATION = 2  # k(T) * (y_O2 p) * C_c
 WELL_RATE_INJECTOR = 0
 WELL_BHP_PRODUCER = 1
 WELL_COUPLED_PRODUCER = 2      # producer with a bottom-hole-pressure unknown and a well equation
+WELL_COUPLED_INJECTOR = 3      # injector with a bottom-hole-pressure unknown and a well equation
 
 # controls of a coupled producer: 0 fixes the bottom-hole pressure; otherwise the
 # bits select the phases (1 water, 2 oil, 4 gas) whose summed molar production
@@ -370,6 +371,27 @@ def with_heat_loss(case: Case, **kw) -> Case:
     import copy
     c = copy.copy(case)
     c.heat_loss = dict(HEAT_LOSS, **kw)
+    return c
+
+
+def with_coupled_injector(case: Case, control: int, target: float, bhp_init: float) -> Case:
+    """A copy of the case whose rate injectors become coupled injectors (the
+    injected stream's rate set by a bottom-hole pressure unknown) with the given
+    control (CTRL_BHP or CTRL_TOTAL_RATE) and target, the bottom-hole pressure
+    defined at the depth of the shallowest perforation and starting at bhp_init."""
+    import copy
+    c = copy.copy(case)
+    wells = []
+    for w in case.wells:
+        if w.kind == WELL_RATE_INJECTOR:
+            w = copy.copy(w)
+            w.kind = WELL_COUPLED_INJECTOR
+            w.control = control
+            w.target = target
+            w.ref_depth = float(np.min(case.depth[w.cells]))
+            w.bhp_init = bhp_init
+        wells.append(w)
+    c.wells = wells
     return c
 
 

@@ -135,6 +135,8 @@ def coupled_oil_rate(case, u, bhp):
     M = case.fluid["M"]
     total = 0.0
     for k, w in enumerate(model.coupled_wells(case)):
+        if w.kind != 2:      # injectors produce no oil
+            continue
         c = w.cells
         Q = model.coupled_phase_rates(case, bp, w, bhp[k])
         mo = M[1] * bp["x_lo"][c] + M[2] * bp["x_ho"][c]

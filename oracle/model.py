@@ -356,8 +356,9 @@ def old_accumulation(case, u_old, coke_old):
 
 
 def coupled_wells(case):
-    """The coupled producers (bottom-hole pressure unknown), in case order."""
-    return [w for w in case.wells if w.kind == 2]
+    """The coupled wells (bottom-hole pressure unknown: producers, kind 2, and
+    injectors, kind 3), in case order."""
+    return [w for w in case.wells if w.kind in (2, 3)]
 
 
 def coupled_phase_rates(case, bp, w, bhp):
@@ -376,15 +377,34 @@ def coupled_phase_rates(case, bp, w, bhp):
     return out
 
 
+def coupled_injection_rate(case, bp, w, bhp):
+    """Molar rate (mol/s, into the reservoir) of the injected stream at each
+    perforation of a coupled injector (Sec. 2.2, Well Modeling, for injection).
+    Reading: Peaceman's formula with the perforated cell's total molar
+    mobility, Q = WI sum_alpha(rho_alpha k_r,alpha / mu_alpha)
+    (bhp - p - gamma (z_bh - z)), gamma the specific weight of the injected
+    phase (gas, or water for inj_phase 0) in the cell; inflow only (no
+    back-flow into the well). Returns an (nperf,) array."""
+    c = w.cells
+    lam_t = bp["lam"][0][c] + bp["lam"][1][c] + bp["lam"][2][c]
+    gam = bp["gam"][0 if w.inj_phase == 0 else 2][c]
+    dphi = bhp - bp["p"][c] - gam * (w.ref_depth - case.depth[c])
+    return _where(_re(dphi) > 0.0, w.WI * lam_t * dphi, 0.0 * dphi)
+
+
 def well_equations(case, u, bhp):
-    """Well equations of the coupled producers (Sec. 2.2): bhp - c for a fixed
-    bottom-hole pressure, else the summed production rate (mol/s, positive
-    out of the reservoir) of the controlled phases minus c."""
+    """Well equations of the coupled wells (Sec. 2.2): bhp - c for a fixed
+    bottom-hole pressure; for a producer the summed production rate (mol/s,
+    positive out of the reservoir) of the controlled phases minus c; for an
+    injector the total injected molar rate minus c."""
     bp = base_properties(case, u)
     F = []
     for k, w in enumerate(coupled_wells(case)):
         if w.control == 0:
             F.append(bhp[k] - w.target)
+            continue
+        if w.kind == 3:
+            F.append(np.sum(coupled_injection_rate(case, bp, w, bhp[k])) - w.target)
             continue
         Q = coupled_phase_rates(case, bp, w, bhp[k])
         rate = sum(-np.sum(Q[a]) for a in range(3) if w.control & (1 << a))
@@ -451,6 +471,13 @@ def residual(case, u, coke_old, acc_old, dt, geom=None, return_coke=False, bhp=N
             for c in range(6):
                 F[c, cells] -= share * w.target * w.inj_y[c]
             F[6, cells] -= share * w.target * Hinj
+        elif w.kind == 3:  # coupled injector: the injected stream at a rate set by the bottom-hole pressure
+            k = next(i for i, cw in enumerate(coupled_wells(case)) if cw is w)
+            Q = coupled_injection_rate(case, bp, w, bhp[k])
+            Hinj = injected_enthalpy(case.fluid, w)
+            for c in range(6):
+                F[c, cells] -= Q * w.inj_y[c]
+            F[6, cells] -= Q * Hinj
         elif w.kind == 2:  # coupled producer: the bottom-hole pressure is an unknown
             k = next(i for i, cw in enumerate(coupled_wells(case)) if cw is w)
             Q = coupled_phase_rates(case, bp, w, bhp[k])
