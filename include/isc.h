@@ -96,11 +96,15 @@ enum isc_rxn_kind {
   ISC_RXN_CRACKING = 1,        /* r = A e^{-Ea/RT} (phi_f S_o rho_o x_i)(1-(C_c/C_max)^5)  */
   ISC_RXN_COKE_OXIDATION = 2   /* r = A e^{-Ea/RT} (y_O2 p) C_c                            */
 };
-enum isc_well_kind { ISC_WELL_RATE_INJECTOR = 0, ISC_WELL_BHP_PRODUCER = 1, ISC_WELL_COUPLED_PRODUCER = 2 };
+enum isc_well_kind {
+  ISC_WELL_RATE_INJECTOR = 0, ISC_WELL_BHP_PRODUCER = 1, ISC_WELL_COUPLED_PRODUCER = 2, ISC_WELL_COUPLED_INJECTOR = 3
+};
 /* Controls of a coupled producer: ISC_CTRL_BHP fixes the bottom-hole pressure
  * (target in Pa); otherwise the bits select the phases (1 water, 2 oil, 4 gas)
  * whose summed molar production rate (mol/s, positive out of the reservoir)
- * is fixed at target. */
+ * is fixed at target. A coupled injector takes ISC_CTRL_BHP or
+ * ISC_CTRL_TOTAL_RATE (the injected molar rate, mol/s, positive into the
+ * reservoir); other controls are ISC_ERR_INVALID_ARG. */
 enum isc_well_control {
   ISC_CTRL_BHP = 0, ISC_CTRL_WATER_RATE = 1, ISC_CTRL_OIL_RATE = 2, ISC_CTRL_LIQUID_RATE = 3,
   ISC_CTRL_GAS_RATE = 4, ISC_CTRL_TOTAL_RATE = 7
@@ -170,8 +174,16 @@ typedef struct isc_reactions {
  * one well equation (control, target; see isc_well_control); its perforation
  * at cell i takes Q_alpha = WI lambda_alpha (bhp - p_i - gamma_alpha (ref_depth
  * - z_i)) per phase when that is negative (gamma_alpha the phase's specific
- * weight in the cell), and bhp starts at bhp_init. A cell may be perforated
- * by at most one well. */
+ * weight in the cell), and bhp starts at bhp_init. A coupled injector has the
+ * same unknown and equation; its perforation at cell i takes the stream inj_y
+ * (molar enthalpy at inj_T as for a rate injector) at Q = WI lambda_T (bhp -
+ * p_i - gamma (ref_depth - z_i)) mol/s when that is positive (lambda_T the
+ * cell's total molar mobility, gamma the specific weight of the injected
+ * phase: gas, or water for inj_phase 0); at a Newton iterate where no
+ * perforation flows, a rate-controlled injector's well row is zero and the
+ * linear solve returns ISC_ERR_NONFINITE (the preconditioner's well row
+ * divides by D_w = 0). A cell
+ * may be perforated by at most one well. */
 typedef struct isc_well {
   int32_t kind;
   int32_t n_perf;
@@ -181,9 +193,9 @@ typedef struct isc_well {
   double inj_y[6];
   double inj_T;
   int32_t inj_phase;
-  int32_t control;    /* coupled producer: isc_well_control */
-  double ref_depth;   /* coupled producer: depth of the bottom-hole pressure (m) */
-  double bhp_init;    /* coupled producer: initial bottom-hole pressure (Pa) */
+  int32_t control;    /* coupled well: isc_well_control */
+  double ref_depth;   /* coupled well: depth of the bottom-hole pressure (m) */
+  double bhp_init;    /* coupled well: initial bottom-hole pressure (Pa) */
 } isc_well;
 
 typedef struct isc_wells {
@@ -292,10 +304,10 @@ int isc_set_state_device(struct isc_handle* h, const double* d_u, const double* 
 int isc_get_state_device(struct isc_handle* h, double* d_u, double* d_coke);
 /* Make the current iterate (u, C_c) the accepted state of time level n: stores
  * C_c^n and the accumulation N^n, E^n used by the next residuals (and the
- * coupled producers' bottom-hole pressures). */
+ * coupled wells' bottom-hole pressures). */
 int isc_begin_step(struct isc_handle* h);
-/* Coupled producers (ISC_WELL_COUPLED_PRODUCER), in the order of the wells
- * given at creation. With nwc > 0 the Newton system is bordered: unknowns
+/* Coupled wells (ISC_WELL_COUPLED_PRODUCER, ISC_WELL_COUPLED_INJECTOR), in the
+ * order of the wells given at creation. With nwc > 0 the Newton system is bordered: unknowns
  * (u, bhp), equations (F, F_w); Krylov vectors, isc_spmv and
  * isc_precond_apply then have length 8N + nwc (the well entries last), and
  * the preconditioner is block lower-triangular (the cells' preconditioner,
@@ -305,7 +317,7 @@ int32_t isc_num_coupled_wells(const struct isc_handle* h);
 int isc_set_well_bhp(struct isc_handle* h, const double* bhp);
 int isc_get_well_bhp(struct isc_handle* h, double* bhp);
 /* After isc_assemble (before decoupling): the border of the Newton system,
- * for the coupled producers' perforations in creation order,
+ * for the coupled wells' perforations in creation order,
  * B[q*8 + r] = dF_r(cell of q)/d bhp, C[q*8 + k] = dF_w/du_k(cell of q), and
  * per coupled well D[w] = dF_w/d bhp_w and Fw[w] the well equation (host
  * arrays; any may be NULL). */
@@ -346,7 +358,7 @@ int isc_timestep(struct isc_handle* h, double dt, isc_step_info* info);
  * identity (checked; ISC_ERR_INVALID_ARG otherwise) and isc_decouple does
  * nothing; 0 gives an assembled system that isc_decouple will scale. Host
  * arrays, copied; the preconditioner must be rebuilt; the state is untouched.
- * Handles with coupled producers return ISC_ERR_UNIMPLEMENTED. Synchronous. */
+ * Handles with coupled wells return ISC_ERR_UNIMPLEMENTED. Synchronous. */
 int isc_set_system(struct isc_handle* h, const double* val, const double* F, int32_t decoupled);
 /* Solve A x = b for a caller's BSR matrix with the handle's linear solver
  * (Gauss-Jordan decoupling of Sec. 3.2 if options.decouple, then the

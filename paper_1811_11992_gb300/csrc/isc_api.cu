@@ -564,6 +564,14 @@ int refresh_parameters(isc_handle* h) {
       sl.WI = h->h_WI0[W.first + q] * exp(h->h_lnk[sl.cell]);
       wsum += sl.WI;
     }
+    if (W.kind == ISC_WELL_COUPLED_INJECTOR) {
+      // the stream's composition and molar enthalpy; the rate follows the bottom-hole pressure
+      for (int q = 0; q < W.count; ++q) {
+        WellSlot& sl = h->h_slots[W.first + q];
+        for (int c = 0; c < 6; ++c) sl.src[c] = W.inj_y[c];
+        sl.src[6] = W.Hinj;
+      }
+    }
     if (W.kind != ISC_WELL_RATE_INJECTOR) continue;
     for (int q = 0; q < W.count; ++q) {
       WellSlot& sl = h->h_slots[W.first + q];
@@ -617,7 +625,7 @@ static int adjoint_forward(isc_handle* h, const isc_adjoint_spec* spec, double* 
     if (!(spec->dt[q] > 0.0) || !isfinite(spec->dt[q])) return set_err(h, ISC_ERR_INVALID_ARG, "step sizes must be > 0");
   if (!(spec->tol_adjoint >= 0.0)) return set_err(h, ISC_ERR_INVALID_ARG, "tol_adjoint must be >= 0");
   if (!h->have_acc) return set_err(h, ISC_ERR_STATE, "isc_begin_step (or isc_init_equilibrium) must come first");
-  if (h->nwc) return set_err(h, ISC_ERR_UNIMPLEMENTED, "the adjoint does not cover coupled producers");
+  if (h->nwc) return set_err(h, ISC_ERR_UNIMPLEMENTED, "the adjoint does not cover coupled wells");
   const int n = h->n;
   const size_t len = (size_t)n * 8, SN = (size_t)n * 9;
   const int ncp = (N + K - 1) / K;
@@ -1024,15 +1032,18 @@ int isc_create(const isc_grid* grid, const isc_rock* rock, const isc_fluid* fl, 
   std::vector<CoupledWell> coupled;
   for (int w = 0; w < wells->nw; ++w) {
     const isc_well& W = wells->wells[w];
-    if (W.n_perf < 1 || !W.cells || !W.WI || W.kind < ISC_WELL_RATE_INJECTOR || W.kind > ISC_WELL_COUPLED_PRODUCER) {
+    if (W.n_perf < 1 || !W.cells || !W.WI || W.kind < ISC_WELL_RATE_INJECTOR || W.kind > ISC_WELL_COUPLED_INJECTOR) {
       delete h;
       return ISC_ERR_INVALID_ARG;
     }
-    const bool is_coupled = W.kind == ISC_WELL_COUPLED_PRODUCER;
+    const bool is_coupled = W.kind == ISC_WELL_COUPLED_PRODUCER || W.kind == ISC_WELL_COUPLED_INJECTOR;
+    const bool injects = W.kind == ISC_WELL_RATE_INJECTOR || W.kind == ISC_WELL_COUPLED_INJECTOR;
     if (is_coupled) {
       const int ctl = W.control;
-      const bool ok = (ctl == ISC_CTRL_BHP || (ctl >= 1 && ctl <= 7)) && W.target == W.target &&
-                      W.target != 0.0 && W.bhp_init > 0.0;
+      // a coupled injector fixes its bottom-hole pressure or its total injected rate
+      const bool ctl_ok = W.kind == ISC_WELL_COUPLED_PRODUCER ? (ctl >= ISC_CTRL_BHP && ctl <= ISC_CTRL_TOTAL_RATE)
+                                                              : (ctl == ISC_CTRL_BHP || ctl == ISC_CTRL_TOTAL_RATE);
+      const bool ok = ctl_ok && W.target == W.target && W.target != 0.0 && W.bhp_init > 0.0;
       if (!ok) {
         delete h;
         return ISC_ERR_INVALID_ARG;
@@ -1051,7 +1062,7 @@ int isc_create(const isc_grid* grid, const isc_rock* rock, const isc_fluid* fl, 
     info.count = W.n_perf;
     info.target = W.target;
     for (int c = 0; c < 6; ++c) info.inj_y[c] = W.inj_y[c];
-    if (W.kind == ISC_WELL_RATE_INJECTOR) {
+    if (injects) {
       // molar enthalpy of the injected stream at T_inj
       double T = W.inj_T, Tr = fl->T_ref, Hinj = 0.0;
       for (int c = 0; c < 6; ++c) {
@@ -1071,8 +1082,10 @@ int isc_create(const isc_grid* grid, const isc_rock* rock, const isc_fluid* fl, 
         }
       }
       info.Hinj = Hinj;
-      inj_first.push_back(info.first);
-      inj_count.push_back(info.count);
+      if (W.kind == ISC_WELL_RATE_INJECTOR) {
+        inj_first.push_back(info.first);
+        inj_count.push_back(info.count);
+      }
     }
     for (int q = 0; q < W.n_perf; ++q) {
       int c = W.cells[q];
@@ -1087,6 +1100,7 @@ int isc_create(const isc_grid* grid, const isc_rock* rock, const isc_fluid* fl, 
       sl.wc = is_coupled ? (int)coupled.size() - 1 : -1;
       sl.control = W.control;
       sl.zref = W.ref_depth;
+      sl.phase = W.inj_phase == 0 ? 0 : 2;
       well_slot[c] = (int32_t)h->h_slots.size();
       h->h_slots.push_back(sl);
       h->h_WI0.push_back(W.WI[q]);

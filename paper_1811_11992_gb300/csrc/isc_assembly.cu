@@ -133,6 +133,30 @@ __global__ void __launch_bounds__(128) k_props(Params P, const double* __restric
       }
       Fq[sl] = fq;
       Dq[sl] = dq;
+    } else if (w.kind == ISC_WELL_COUPLED_INJECTOR) {
+      // The injected stream (mole fractions src[0..5], molar enthalpy src[6])
+      // enters at Q = WI lambda_T (bhp - p - gamma (z_ref - z)) mol/s with the
+      // cell's total molar mobility lambda_T and the injected phase's specific
+      // weight gamma, inflow only (Sec. 2.2, Well Modeling, for injection).
+      // Border: dF/d bhp = -dQ/d bhp times the stream; for a rate control the
+      // perforation's Q, its u-gradient and its bhp-derivative.
+      const D8 lamT = b.lam[0] + b.lam[1] + b.lam[2];
+      const D8 dphi = bhp[w.wc] - b.p - b.gam[w.phase] * (w.zref - depth[i]);
+      const bool flows = dphi.v > 0.0;
+      const D8 Q = (w.WI * lamT) * dphi;
+      const double dQ = flows ? w.WI * lamT.v : 0.0;
+      if (flows) {
+#pragma unroll
+        for (int r = 0; r < 7; ++r) Rl[r] = Rl[r] - Q * w.src[r];
+      }
+      const bool rate = w.control != ISC_CTRL_BHP;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        Bv[(size_t)sl * 8 + k] = k < 7 ? -dQ * w.src[k] : 0.0;
+        Cv[(size_t)sl * 8 + k] = (rate && flows) ? Q.d[k] : 0.0;
+      }
+      Fq[sl] = flows ? Q.v : 0.0;
+      Dq[sl] = dQ;
     } else {
       D8 dpw = w.bhp - b.p;
       if (dpw.v < 0.0) {
@@ -368,8 +392,10 @@ __global__ void __launch_bounds__(256) k_flux(Params P, const double* __restrict
   for (int k = 0; k < 8; ++k) Jd[k] += dd[k];
 }
 
-// Well equations of the coupled producers (Sec. 2.2): bhp - c, or the summed
-// production rate of the controlled phases minus c; their bhp-derivatives;
+// Well equations of the coupled wells (Sec. 2.2): bhp - c, or the summed
+// production rate of the controlled phases (producer) or the total injected
+// rate (injector) minus c, the perforation terms coming from k_props; their
+// bhp-derivatives;
 // and max |F_w| / |c| into norm_out. One thread, fixed order (wells are few).
 __global__ void k_well_eq(int nwc, const CoupledWell* __restrict__ cw, const double* __restrict__ Fq,
                           const double* __restrict__ Dq, const double* __restrict__ bhp, double* __restrict__ Rw,

@@ -95,13 +95,15 @@ struct WellSlot {
   double WI;
   double bhp;                 // producer
   double share;               // injector: WI / sum of the well's WI
-  double src[7];              // injector: mol/s per component and J/s
-  int wc;                     // coupled producer: its index among the coupled wells, else -1
-  int control;                // coupled producer: ISC_CTRL_*
-  double zref;                // coupled producer: depth of the bottom-hole pressure
+  double src[7];              // rate injector: mol/s per component and J/s; coupled injector: the
+                              // stream's mole fractions and molar enthalpy (J/mol)
+  int wc;                     // coupled well: its index among the coupled wells, else -1
+  int control;                // coupled well: ISC_CTRL_*
+  double zref;                // coupled well: depth of the bottom-hole pressure
+  int phase;                  // coupled injector: phase whose specific weight sets the head (0 water, 2 gas)
 };
 
-// One coupled producer (bottom-hole pressure unknown) on the device.
+// One coupled well (bottom-hole pressure unknown) on the device.
 struct CoupledWell {
   int control;
   int first, count;           // slot range

@@ -426,9 +426,9 @@ class Simulator:
         return c
 
     def spmv(self, x):
-        """y = A x for x given as (8, N) (no coupled producers; else spmv_full)."""
+        """y = A x for x given as (8, N) (no coupled wells; else spmv_full)."""
         if self.nwc:
-            raise ValueError("the system has coupled producers: use spmv_full")
+            raise ValueError("the system has coupled wells: use spmv_full")
         xb = np.ascontiguousarray(np.asarray(x, np.float64).reshape(8, self.n).T)
         y = np.empty((self.n, 8))
         self._check(self.lib.isc_spmv(self.h, _dp(xb), _dp(y)))
@@ -439,7 +439,7 @@ class Simulator:
 
     def precond_apply(self, r):
         if self.nwc:
-            raise ValueError("the system has coupled producers: use precond_apply_full")
+            raise ValueError("the system has coupled wells: use precond_apply_full")
         rb = np.ascontiguousarray(np.asarray(r, np.float64).reshape(8, self.n).T)
         z = np.empty((self.n, 8))
         self._check(self.lib.isc_precond_apply(self.h, _dp(rb), _dp(z)))
@@ -459,7 +459,7 @@ class Simulator:
     def reset_stats(self):
         self._check(self.lib.isc_reset_stats(self.h))
 
-    # ---------------------------------------------------- coupled producers
+    # -------------------------------------------------------- coupled wells
     def well_bhp(self):
         b = np.empty(max(self.nwc, 1))
         self._check(self.lib.isc_get_well_bhp(self.h, _dp(b)))
@@ -471,7 +471,7 @@ class Simulator:
 
     def well_system(self):
         """(B (nperf, 8), C (nperf, 8), D (nwc,), Fw (nwc,)) after assemble."""
-        nperf = sum(len(w.cells) for w in self.case.wells if w.kind == 2)
+        nperf = sum(len(w.cells) for w in self.case.wells if w.kind in (2, 3))
         B, Cm = np.empty((max(nperf, 1), 8)), np.empty((max(nperf, 1), 8))
         D, Fw = np.empty(max(self.nwc, 1)), np.empty(max(self.nwc, 1))
         self._check(self.lib.isc_get_well_system(self.h, _dp(B), _dp(Cm), _dp(D), _dp(Fw)))

@@ -168,8 +168,9 @@ def test_binding_constants_match_the_header_enums():
         assert e["ISC_K_" + name.upper()] == i, name
     assert (inp.RXN_OIL_OXIDATION, inp.RXN_CRACKING, inp.RXN_COKE_OXIDATION) == (
         e["ISC_RXN_OIL_OXIDATION"], e["ISC_RXN_CRACKING"], e["ISC_RXN_COKE_OXIDATION"])
-    assert (inp.WELL_RATE_INJECTOR, inp.WELL_BHP_PRODUCER, inp.WELL_COUPLED_PRODUCER) == (
-        e["ISC_WELL_RATE_INJECTOR"], e["ISC_WELL_BHP_PRODUCER"], e["ISC_WELL_COUPLED_PRODUCER"])
+    assert (inp.WELL_RATE_INJECTOR, inp.WELL_BHP_PRODUCER, inp.WELL_COUPLED_PRODUCER, inp.WELL_COUPLED_INJECTOR) == (
+        e["ISC_WELL_RATE_INJECTOR"], e["ISC_WELL_BHP_PRODUCER"], e["ISC_WELL_COUPLED_PRODUCER"],
+        e["ISC_WELL_COUPLED_INJECTOR"])
     assert (inp.CTRL_BHP, inp.CTRL_WATER_RATE, inp.CTRL_OIL_RATE, inp.CTRL_LIQUID_RATE, inp.CTRL_GAS_RATE,
             inp.CTRL_TOTAL_RATE) == tuple(e["ISC_CTRL_" + k] for k in ("BHP", "WATER_RATE", "OIL_RATE",
                                                                        "LIQUID_RATE", "GAS_RATE", "TOTAL_RATE"))
