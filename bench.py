@@ -50,6 +50,9 @@ def parse(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="isc", choices=["isc", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-fullsize", action="store_true",
+                    help="also time the oracle's SpMV and ILU(0) apply on the full-size matrix (about 2 min and "
+                         "40 GB of host memory at 200x200x50; skipped with a note when less memory is free)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the discrete-adjoint measurement")
     ap.add_argument("--no-extras", action="store_true",
                     help="time only the headline step (no other legs or workloads); for profiling")
@@ -555,6 +558,8 @@ def run_isc(args):
         line["adjoint"] = adjoint_block()
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.grid is None:
         line["cpu_baseline"] = cpu_baseline(case, statistics.median(kry) if kry else 0, nnzb)
+        if args.cpu_fullsize:
+            line["cpu_baseline"]["fullsize_kernels"] = oracle_fullsize_kernels(case)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
@@ -686,6 +691,60 @@ def cpu_baseline(case, kry_full, nnzb):
             "spmv_s_per_call_sample": t["spmv"], "ilu_apply_s_per_call_sample": t["ilu_apply"],
             "spmv_gbs_sample": spmv_bytes(ns, 7 * ns) / t["spmv"] / 1e9,
             "spmv_ms_full_estimate": spmv_full_ms, "ilu_apply_ms_full_estimate": ilu_full_ms}
+
+
+def host_mem_available_gb():
+    try:
+        with open("/proc/meminfo") as f:
+            for ln in f:
+                if ln.startswith("MemAvailable:"):
+                    return int(ln.split()[1]) / 1e6
+    except OSError:
+        pass
+    return 0.0
+
+
+def oracle_fullsize_kernels(case, need_gb=96.0):
+    """The oracle's SpMV (scipy CSR product) and block ILU(0) apply (two scipy
+    sparse triangular solves and the D^-1 products) timed on the workload's
+    full-size pattern, as they stand, on one host thread. The matrix and factor
+    values are synthetic (identity diagonal blocks, constant off-diagonal
+    entries): neither routine's cost depends on the values, and the oracle's
+    own factorisation (a Python loop over the cells) is not part of the apply."""
+    import numpy as np
+    from oracle import linalg, model
+    avail = host_mem_available_gb()
+    if avail < need_gb:
+        return {"skipped": f"{avail:.0f} GB of host memory available, {need_gb:.0f} GB needed"}
+    t0 = time.perf_counter()
+    rp, col = model.bsr_pattern(case)
+    n, nnzb = case.n, len(col)
+    val = np.full((nnzb, 8, 8), 1.0e-3)
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    val[col == rows] = np.eye(8)
+    del rows
+    prep = time.perf_counter() - t0
+    A = linalg.bsr_to_scipy(rp, col, val)
+    x = np.ones(8 * n)
+    A @ x
+    t0 = time.perf_counter()
+    for _ in range(3):
+        A @ x
+    spmv = (time.perf_counter() - t0) / 3
+    del A
+    t0 = time.perf_counter()
+    M = linalg.ILU0Preconditioner(rp, col, val, factors=val)
+    setup = time.perf_counter() - t0
+    r = np.ones((n, 8))
+    t0 = time.perf_counter()
+    for _ in range(2):
+        M.apply(r)
+    ilu = (time.perf_counter() - t0) / 2
+    return {"cells": n, "nnzb": nnzb, "cores": 1, "spmv_s_per_call": spmv, "ilu_apply_s_per_call": ilu,
+            "spmv_gbs_at_algorithmic_bytes": spmv_bytes(n, nnzb) / spmv / 1e9, "csr_setup_s": setup, "pattern_and_values_s": prep,
+            "host_mem_available_gb": avail,
+            "note": "synthetic values on the full-size pattern; CSR conversion and triangular-factor set-up "
+                    "are outside the timed calls"}
 
 
 def run_reference(args):

@@ -121,9 +121,11 @@ class ILU0Preconditioner:
     use scipy's sparse triangular solver on the scalar form of L and of
     blockdiag(U)^-1 U (both triangular with a stored unit diagonal)."""
 
-    def __init__(self, rowptr, col, val):
+    def __init__(self, rowptr, col, val, factors=None):
+        """factors: the block ILU(0) factor blocks F (as block_ilu0 returns
+        them) when already known; by default they are computed from val."""
         self.n = len(rowptr) - 1
-        F = block_ilu0(rowptr, col, val)
+        F = block_ilu0(rowptr, col, val) if factors is None else factors
         rows = np.repeat(np.arange(self.n), np.diff(rowptr))
         low = col < rows
         dia = col == rows

@@ -111,3 +111,18 @@ def test_gram_schmidt_model(bench):
     st = {"blas1": {"calls": 1140, "ms": 2800.0, "launches": 5700}}
     r = bench.roofline("blas1", st, case, nnzb, 1057.0, "fp64", its=1140, orth="cgs2")
     assert r["bound"] == "alu" and 0.5 < r["frac"] < 1.0
+
+
+def test_fullsize_oracle_kernel_timing_runs_and_skips_without_memory(bench):
+    """The opt-in full-size timing of the oracle's SpMV and ILU(0) apply, on a
+    tiny grid of the same recipe: it runs the oracle's routines on the
+    workload's own pattern, and declines with a note when the host lacks the
+    memory the full-size matrix needs."""
+    import isc_inputs as inp
+    case = inp.large_case(6, 5, 4)
+    r = bench.oracle_fullsize_kernels(case, need_gb=0.0)
+    assert r["cells"] == case.n and r["nnzb"] == 7 * case.n - 2 * (case.ny * case.nz + case.nx * case.nz
+                                                                     + case.nx * case.ny)
+    assert r["spmv_s_per_call"] > 0 and r["ilu_apply_s_per_call"] > 0 and r["cores"] == 1
+    skipped = bench.oracle_fullsize_kernels(case, need_gb=1.0e9)
+    assert set(skipped) == {"skipped"}
