@@ -54,6 +54,30 @@ def test_loss_and_full_gradient_match_oracle_tangent(box):
     g.close()
 
 
+def test_gradient_with_heat_loss_matches_oracle_tangent():
+    """The same comparison with heat loss to the overburden and underburden switched
+    on (Sec. 2.1): the loss term enters every step's Jacobian (the temperature
+    column of the energy row), which the reverse sweep transposes."""
+    case = inp.with_heat_loss(inp.small_box(4, 3, 2))
+    us, cs = adjoint.trajectory(case, BOX_DTS, tol=1e-11)
+    n, nr = case.n, int(case.reactions["nr"])
+    g = _sim(case)
+    g.init_equilibrium()
+    L, gk, ge, ga, info = g.adjoint(BOX_DTS, checkpoint_every=2, tol_adjoint=1e-12)
+    assert L == pytest.approx(adjoint.loss(case, BOX_DTS, us), rel=1e-8)
+    ref_k = np.array([adjoint.tangent(case, BOX_DTS, us, cs, np.eye(n)[i], np.zeros(nr), np.zeros(nr))
+                      for i in range(n)])
+    ref_e = np.array([adjoint.tangent(case, BOX_DTS, us, cs, np.zeros(n), np.eye(nr)[r], np.zeros(nr))
+                      for r in range(nr)])
+    for got, ref in ((gk, ref_k), (ge, ref_e)):
+        scale = np.abs(ref).max()
+        np.testing.assert_allclose(got, ref, rtol=1e-6, atol=1e-8 * scale)
+    # the loss changes the trajectory: the gradient differs from the one without it
+    us0, cs0 = adjoint.trajectory(inp.small_box(4, 3, 2), BOX_DTS, tol=1e-11)
+    assert not np.allclose(adjoint.loss(inp.small_box(4, 3, 2), BOX_DTS, us0), L, rtol=1e-9)
+    g.close()
+
+
 def test_checkpointing_recomputes_bit_exactly(box):
     case, _, _ = box
     g = _sim(case)
