@@ -1,30 +1,26 @@
-// Pencil-pipelined triangular sweeps of the block ILU(0) preconditioner.
+// Pencil-pipelined block ILU(0): the factorisation and the two triangular
+// sweeps of the preconditioner.
 //
 // For the 7-point pattern in natural order, ILU(0) keeps the off-diagonal
 // blocks of A and changes only the diagonal (D-ILU form):
+//   D_i       = A_ii - sum_{k in {i-1, i-nx, i-nxy}} A_ik D_k^-1 A_ki
 //   forward   y_i = D_i^-1 (r_i - A_{i,i-1} y_{i-1} - A_{i,i-nx} y_{i-nx} - A_{i,i-nxy} y_{i-nxy})
 //   backward  z_i = y_i - D_i^-1 (A_{i,i+1} z_{i+1} + A_{i,i+nx} z_{i+nx} + A_{i,i+nxy} z_{i+nxy})
 // Cell i depends on its x-predecessor (same pencil) and on the pencils
-// (j-1,k) and (j,k-1) at the same x. One warp owns a whole x-pencil, so the
-// x-recurrence stays in registers; pencils are taken from a counter in
-// dependency order (so a warp only ever waits on pencils already held by
-// running warps). The cross-pencil hand-off is the data itself: the output
-// vector is filled with a NaN sentinel before a sweep and a consumer polls the
-// neighbour's 64-byte block vector until the sentinel is gone; these values
-// are requested LA cells before use. The matrix operands of upcoming cells are streamed into a
-// per-warp shared-memory ring with cp.async. Row starts are computed, not
-// loaded. Every wait is bounded: on timeout the kernel raises DS_TIMEOUT and a
-// global abort flag that makes every other waiter return.
+// (j-1,k) and (j,k-1) at the same x. A pencil's x-recurrence stays in the
+// registers of the warp (or half-warp) that owns it; pencils are taken from a
+// counter in dependency order, so a warp only ever waits on pencils already
+// held by running warps. The cross-pencil hand-off is the data itself: the
+// output vector is filled with a NaN sentinel before a sweep and a consumer
+// polls the neighbour's 64-byte block vector until the sentinel is gone,
+// requesting it one cell before use. The matrix operands of upcoming cells
+// are streamed into a per-warp shared-memory ring with cp.async. Row starts
+// are computed, not loaded. Every wait is bounded: on timeout the kernel raises
+// DS_TIMEOUT and a global abort flag that makes every other waiter return.
 //
-// Measured on the 60x60x20 field step, a lone pencil costs ~0.3 us (FP32) to
-// ~0.6 us (FP64) per cell of sequential recurrence, and each pencil-to-pencil
-// hand-off adds about one cell time plus ~0.5 us; the sweep time is that
-// per-cell chain times the nx + ny + nz - 2 cells of the wavefront, not memory
-// bandwidth.
-//
-// Lane layout per 8x8 block (row-major, 64 doubles): lane l holds the double2
-// at offset 2l, i.e. row r = l/4, columns c = 2(l%4), c+1; a row sum is a
-// reduction over the 4 lanes of a quad.
+// The sweep time is the FP64 pipe (FP64) or HBM (FP32) in steady state plus
+// the wavefront's fill and drain: a hand-off between pencils costs about one
+// cell time plus an L2 round trip, over the ny + nz - 2 pencil diagonals.
 #include <vector>
 
 #include "isc_internal.cuh"
