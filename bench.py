@@ -273,8 +273,25 @@ def gmres_blas1_work(n, its, restart=30, orth="cgs1"):
     return byts, flops
 
 
+# Executed FP64 flops per cell of the assembly kernels (2 DFMA + DADD + DMUL from an
+# ncu count of the dual-number tangent code, which has no closed-form flop count),
+# profiles/fp64_instruction_counts_large_100x100x30.md
+ASSEMBLY_FLOPS_PER_CELL = {"props": 5810.0, "flux": 3928.0 + 434.0}  # flux: face pass + gather
+
+
 def class_model(cls, n, nnzb, fp32=False, its=None, orth="cgs1"):
     """(algorithmic bytes, flops) per call of a kernel class (None when unmodelled)."""
+    if cls == "props":
+        # reads u (64 B), the old accumulation (56 B), C_c^n and phi_ref (16 B); writes R (64 B),
+        # the diagonal block (512 B) and the staged face quantities (16 x 9 doubles)
+        return n * (64 + 56 + 16 + 64 + 512 + 16 * 9 * 8), n * ASSEMBLY_FLOPS_PER_CELL["props"]
+    if cls == "flux":
+        # face pass: reads the staged quantities (each cell's once from DRAM) and the
+        # transmissibilities, writes the off-diagonal blocks, adds to R and the diagonal block,
+        # parks the +side shares (7 rows x 9 doubles per face); gather: reads them back and adds
+        # them to R and the diagonal block
+        return (n * (16 * 9 * 8 + 3 * 8) + (nnzb - n) * 512 + 2 * n * (64 + 512) * 2 + 2 * n * 3 * 7 * 9 * 8,
+                n * ASSEMBLY_FLOPS_PER_CELL["flux"])
     if cls == "spmv":
         return spmv_bytes(n, nnzb), 2 * 64 * (nnzb - n)
     if cls == "prec_apply":
@@ -510,11 +527,12 @@ def run_isc(args):
                 cpr_block[p]["pressure_stage_ms_per_step"] = cst["cpr"]["ms"] / leg_steps
                 cpr_block[p]["speedup_vs_ilu0_fp64"] = (ms_total / args.steps) / ms
     its_total = sum(kry)
-    modelled = [k for k in stats if class_model(k, n, g.nnzb, its=its_total)[0] is not None]
+    modelled = [k for k in stats if k not in ASSEMBLY_FLOPS_PER_CELL
+                and class_model(k, n, g.nnzb, its=its_total)[0] is not None]
     dom = max(modelled, key=lambda k: stats[k]["ms"])
     roof = roofline(dom, stats, case, g.nnzb, fp64_gflops, args.precision, its_total, args.orth)
     rooflines = {k: roofline(k, stats, case, g.nnzb, fp64_gflops, args.precision, its_total, args.orth)
-                 for k in ("prec_apply", "spmv", "blas1", "gj", "ilu_factor") if stats[k]["calls"]}
+                 for k in ("prec_apply", "spmv", "blas1", "gj", "ilu_factor", "props", "flux") if stats[k]["calls"]}
     hbm = hbm_table(stats, mst, fst, case, g.nnzb)
     launches = sum(v["launches"] for v in stats.values())
     nnzb = g.nnzb

@@ -113,7 +113,7 @@ int dalloc(isc_handle* h, T** p, size_t count) {
 
 void free_all(isc_handle* h) {
   void* ptrs[] = {h->rowptr, h->col, h->level_cells, h->phi_ref, h->depth, h->tx, h->ty, h->tz, h->well_slot,
-                  h->slots, h->u, h->coke, h->u_n, h->coke_n, h->acc_n, h->props, h->R, h->J, h->ntot, h->du,
+                  h->slots, h->u, h->coke, h->u_n, h->coke_n, h->acc_n, h->props, h->fbuf, h->R, h->J, h->ntot, h->du,
                   h->rhs, h->dinv, h->uhat, h->J32, h->dinv32, h->uhat32, h->vec32, h->V32, h->Z32, h->w32, h->gm_in, h->scal_in, h->V, h->Z, h->w, h->tmp, h->partial, h->scal, h->dstatus, h->pipe, h->red_counter, h->gmres,
                   h->wx, h->wy, h->wz, h->cw, h->bhp, h->bhp_n, h->Dw, h->Bv, h->Cv, h->Fq, h->Dq, h->adj.store, h->adj.ubar, h->adj.cbar, h->adj.lam, h->adj.glnk, h->adj.grx,
                   h->adj.scond, h->adj.kd, h->adj.loss_cell, h->adj.sums, h->adj.inj_first, h->adj.inj_count};
@@ -1147,6 +1147,7 @@ int isc_create(const isc_grid* grid, const isc_rock* rock, const isc_fluid* fl, 
   e |= dalloc(h, &h->coke_n, n);
   e |= dalloc(h, &h->acc_n, (size_t)n * 7);
   e |= dalloc(h, &h->props, (size_t)n * NQD);
+  e |= dalloc(h, &h->fbuf, (size_t)n * 2 * 3 * 7 * 9);
   e |= dalloc(h, &h->R, len);
   e |= dalloc(h, &h->J, (size_t)h->nnzb * BB);
   e |= dalloc(h, &h->ntot, n);
@@ -1308,7 +1309,7 @@ int isc_assemble(isc_handle* h, double dt) {
     launch_props(*h, h->stream);
   }
   {
-    Region rg(h, ISC_K_FLUX, 1);
+    Region rg(h, ISC_K_FLUX, 2);  // face pass and gather
     launch_flux(*h, h->stream);
   }
   if (h->nwc) {

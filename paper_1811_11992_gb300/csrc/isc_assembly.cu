@@ -5,13 +5,13 @@
 //           reactions and wells -> residual, diagonal Jacobian block and the
 //           staged face quantities (lambda_alpha * carried quantity, gamma,
 //           K_T with their derivatives).
-// k_flux    one thread per (cell, equation row): the six faces of the cell,
-//           upstream weighting per phase, harmonic transmissibility, face
-//           fluxes and their derivatives w.r.t. both cells; adds to the
-//           residual and the diagonal block, writes the off-diagonal blocks.
-//           Each face is evaluated in its canonical (lo, hi) orientation by
-//           the same code in both cells, so the two contributions are exact
-//           negatives of each other.
+// k_flux    one thread per (direction, cell, equation row): the cell's face
+//           towards +x, +y or +z, evaluated once in its (lo, hi) orientation:
+//           upstream weighting per phase, harmonic transmissibility, the face
+//           flux and its derivatives w.r.t. both cells; writes both cells'
+//           off-diagonal blocks of the face and parks the two cells' shares of
+//           the residual and diagonal block (exact negatives of each other) for
+// k_flux_gather, which adds each cell's shares from its six faces.
 #include <math.h>
 
 #include "dual8.cuh"
@@ -312,30 +312,36 @@ __device__ __forceinline__ double face_flux(const Params& P, int r, int lo, int 
   return F;
 }
 
+// Face pass: thread (direction d, cell i, row r) evaluates the flux of row r
+// over the face between i and its neighbour j towards +d, once per face
+// (blockIdx.y is the direction: three threads per cell and row keep enough
+// independent faces in flight). It writes both cells' off-diagonal block rows
+// of the face (no other thread writes them) and parks the two cells' shares
+// of the residual and of the diagonal block in fbuf, for k_flux_gather (a
+// cell's row is shared by the faces of six threads, so it is not added to here).
+// fbuf layout: (((side * 3 + d) * 7 + r) * 9 + c) * N + cell; side 0: the
+// share of the face's -side cell i (flux out, d/du_i), side 1: that of its
+// +side cell j (the exact negatives: flux in, -d/du_j); c = 0 the residual
+// share, c = 1..8 the diagonal-block row share. Written only where the face
+// exists.
 __global__ void __launch_bounds__(256) k_flux(Params P, const double* __restrict__ u, const double* __restrict__ props,
                                               const double* __restrict__ tx, const double* __restrict__ ty,
                                               const double* __restrict__ tz, const double* __restrict__ depth,
-                                              const int32_t* __restrict__ rowptr, double* __restrict__ R,
-                                              double* __restrict__ J) {
+                                              const int32_t* __restrict__ rowptr, double* __restrict__ J,
+                                              double* __restrict__ fbuf) {
   const int r = threadIdx.x >> 5;
   const int i = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int dir = blockIdx.y;
   if (i >= P.n) return;
-  const int nx = P.nx, ny = P.ny, nxy = P.nx * P.ny;
+  const int n = P.n, nx = P.nx, ny = P.ny, nxy = P.nx * P.ny;
   const int ix = i % nx, iy = (i / nx) % ny, iz = i / nxy;
-  // neighbours in BSR column order: -z, -y, -x, (diag), +x, +y, +z
-  int nb[6];
-  bool has[6] = {iz > 0, iy > 0, ix > 0, ix < nx - 1, iy < ny - 1, iz < P.nz - 1};
-  nb[0] = i - nxy;
-  nb[1] = i - nx;
-  nb[2] = i - 1;
-  nb[3] = i + 1;
-  nb[4] = i + nx;
-  nb[5] = i + nxy;
+  const bool lz = iz > 0, ly = iy > 0, lx = ix > 0;
   const int base = rowptr[i];
-  const int dslot = (int)has[0] + (int)has[1] + (int)has[2];
+  const int dslot = (int)lz + (int)ly + (int)lx;
   if (r == 7) {
     // the gas constraint has no flux: its off-diagonal rows are zero (the
-    // buffer may hold the previous, decoupled system)
+    // buffer may hold the previous, decoupled system); one direction does it
+    if (dir != 0) return;
     const int nblk = rowptr[i + 1] - base;
     for (int s = 0; s < nblk; ++s) {
       if (s == dslot) continue;
@@ -345,49 +351,64 @@ __global__ void __launch_bounds__(256) k_flux(Params P, const double* __restrict
     }
     return;
   }
-  double Rsum = 0.0;
+  const bool has = dir == 0 ? ix < nx - 1 : dir == 1 ? iy < ny - 1 : iz < P.nz - 1;
+  if (!has) return;
+  const int j = i + (dir == 0 ? 1 : dir == 1 ? nx : nxy);
+  const double Tf = dir == 0 ? tx[i] : dir == 1 ? ty[i] : tz[i];
+  const double Gf = dir == 0 ? P.gx : dir == 1 ? P.gy : P.gz;
+  double dlo[8], dhi[8];
+  const double F = face_flux(P, r, i, j, Tf, Gf, depth[i] - depth[j], u, props, dlo, dhi);
+  // cell i's +dir block (after the diagonal: +x, +y, +z, those present)
+  const int si = dslot + 1 + (dir >= 1 ? (int)(ix < nx - 1) : 0) + (dir == 2 ? (int)(iy < ny - 1) : 0);
+  double* Jb = J + (size_t)(base + si) * BB + r * 8;
+#pragma unroll
+  for (int k = 0; k < 8; k += 2) *reinterpret_cast<double2*>(Jb + k) = make_double2(dhi[k], dhi[k + 1]);
+  // cell j's -dir block (its lower neighbours before it: -z, -y when dir is x; -z when dir is y)
+  const int jy = iy + (dir == 1), jz = iz + (dir == 2);
+  const int sj = dir == 0 ? (int)(jz > 0) + (int)(jy > 0) : dir == 1 ? (int)(jz > 0) : 0;
+  double* Jn = J + (size_t)(rowptr[j] + sj) * BB + r * 8;
+#pragma unroll
+  for (int k = 0; k < 8; k += 2) *reinterpret_cast<double2*>(Jn + k) = make_double2(-dlo[k], -dlo[k + 1]);
+  double* f0 = fbuf + (size_t)((dir * 7 + r) * 9) * n + i;
+  double* f1 = fbuf + (size_t)(((3 + dir) * 7 + r) * 9) * n + j;
+  __stcs(f0, F);
+  __stcs(f1, -F);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    __stcs(f0 + (size_t)(1 + k) * n, dlo[k]);
+    __stcs(f1 + (size_t)(1 + k) * n, -dhi[k]);
+  }
+}
+
+// Gather pass: thread (cell i, row r < 7) adds the shares that the face pass
+// parked for cell i from its six faces to its residual and diagonal block.
+__global__ void __launch_bounds__(256) k_flux_gather(Params P, const int32_t* __restrict__ rowptr,
+                                                     const double* __restrict__ fbuf, double* __restrict__ R,
+                                                     double* __restrict__ J) {
+  const int r = threadIdx.x >> 5;
+  const int i = blockIdx.x * 32 + (threadIdx.x & 31);
+  if (i >= P.n || r == 7) return;
+  const int n = P.n, nx = P.nx, ny = P.ny, nxy = P.nx * P.ny;
+  const int ix = i % nx, iy = (i / nx) % ny, iz = i / nxy;
+  // side 0: faces towards +x, +y, +z; side 1: faces towards -x, -y, -z
+  const bool has[2][3] = {{ix < nx - 1, iy < ny - 1, iz < P.nz - 1}, {ix > 0, iy > 0, iz > 0}};
+  double Rs = 0.0;
   double dd[8];
 #pragma unroll
   for (int k = 0; k < 8; ++k) dd[k] = 0.0;
-  int slot = 0;
-  for (int f = 0; f < 6; ++f) {
-    if (f == 3) ++slot;  // skip the diagonal slot
-    if (!has[f]) continue;
-    int j = nb[f];
-    int lo = min(i, j), hi = max(i, j);
-    double Tf, Gf;
-    if (f == 2 || f == 3) {
-      Tf = tx[lo];
-      Gf = P.gx;
-    } else if (f == 1 || f == 4) {
-      Tf = ty[lo];
-      Gf = P.gy;
-    } else {
-      Tf = tz[lo];
-      Gf = P.gz;
+#pragma unroll
+  for (int side = 0; side < 2; ++side)
+#pragma unroll
+    for (int dir = 0; dir < 3; ++dir) {
+      if (!has[side][dir]) continue;
+      const double* fb = fbuf + (size_t)(((side * 3 + dir) * 7 + r) * 9) * n + i;
+      Rs += __ldcs(fb);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) dd[k] += __ldcs(fb + (size_t)(1 + k) * n);
     }
-    double dz = depth[lo] - depth[hi];
-    double dlo[8], dhi[8];
-    double F = face_flux(P, r, lo, hi, Tf, Gf, dz, u, props, dlo, dhi);
-    const bool own_lo = (i == lo);
-    double* Jb = J + (size_t)(base + slot) * BB + r * 8;
-    if (own_lo) {
-      Rsum += F;
-#pragma unroll
-      for (int k = 0; k < 8; ++k) dd[k] += dlo[k];
-#pragma unroll
-      for (int k = 0; k < 8; k += 2) *reinterpret_cast<double2*>(Jb + k) = make_double2(dhi[k], dhi[k + 1]);
-    } else {
-      Rsum -= F;
-#pragma unroll
-      for (int k = 0; k < 8; ++k) dd[k] -= dhi[k];
-#pragma unroll
-      for (int k = 0; k < 8; k += 2) *reinterpret_cast<double2*>(Jb + k) = make_double2(-dlo[k], -dlo[k + 1]);
-    }
-    ++slot;
-  }
-  R[(size_t)i * 8 + r] += Rsum;
-  double* Jd = J + (size_t)(base + dslot) * BB + r * 8;
+  const int dslot = (int)has[1][0] + (int)has[1][1] + (int)has[1][2];
+  R[(size_t)i * 8 + r] += Rs;
+  double* Jd = J + (size_t)(rowptr[i] + dslot) * BB + r * 8;
 #pragma unroll
   for (int k = 0; k < 8; ++k) Jd[k] += dd[k];
 }
@@ -482,7 +503,8 @@ void launch_props(Handle& h, cudaStream_t s) {
 }
 
 void launch_flux(Handle& h, cudaStream_t s) {
-  k_flux<<<(h.n + 31) / 32, 256, 0, s>>>(h.P, h.u, h.props, h.tx, h.ty, h.tz, h.depth, h.rowptr, h.R, h.J);
+  k_flux<<<dim3((h.n + 31) / 32, 3), 256, 0, s>>>(h.P, h.u, h.props, h.tx, h.ty, h.tz, h.depth, h.rowptr, h.J, h.fbuf);
+  k_flux_gather<<<(h.n + 31) / 32, 256, 0, s>>>(h.P, h.rowptr, h.fbuf, h.R, h.J);
 }
 
 void launch_old_accumulation(Handle& h, cudaStream_t s) {
