@@ -500,21 +500,24 @@ typedef struct isc_adjoint_info {
  * isc_init_equilibrium or a converged isc_timestep) the call runs the
  * spec->n_steps implicit-Euler steps with Newton as isc_timestep does (the
  * handle's options), and evaluates the loss
- *     L = sum_n dt_n sum_{BHP producer perforations} (M_LO (Q_o x_LO + Q_g y_LO)
- *                                                     + M_HO (Q_o x_HO + Q_g y_HO))
+ *     L = sum_n dt_n sum_{producer perforations} (M_LO (Q_o x_LO + Q_g y_LO)
+ *                                                 + M_HO (Q_o x_HO + Q_g y_HO))
  * the cumulative LO + HO mass (kg) produced in any phase at the converged
- * states (Peaceman rates of Sec. 2.2, outflow only). If any gradient pointer
- * is non-NULL it then sweeps the steps backwards: per step one transposed
- * linear solve J_n^T lambda_n = ubar_n with the preconditioned Krylov method
- * of the options (the transposed blocks are decoupled and factored like J),
- * the coke equation entering through the implicit-function theorem, and
- * accumulates
+ * states (Peaceman rates of Sec. 2.2, outflow only; fixed-BHP producers and
+ * coupled producers, the latter at their converged bottom-hole pressures). If
+ * any gradient pointer is non-NULL it then sweeps the steps backwards: per
+ * step one transposed linear solve J_n^T lambda_n = ubar_n with the
+ * preconditioned Krylov method of the options (the transposed blocks are
+ * decoupled and factored like J; with coupled wells the transposed bordered
+ * system, whose well rows carry dL/d bhp and whose multipliers weight the well
+ * equations' ln k terms), the coke equation entering through the
+ * implicit-function theorem, and accumulates
  *   g_log_k  N host doubles  dL/d log_k (as set by isc_set_parameters),
  *   g_Ea     nr host doubles dL/dE_a (per J/mol),
  *   g_lnA    nr host doubles dL/d ln A.
  * Each may be NULL. States are kept every spec->checkpoint_every steps
- * ((ceil(n_steps/K) + K + 2) x 9N doubles of device memory, allocated on first
- * use and kept with the handle) and recomputed bit-exactly during the reverse
+ * ((ceil(n_steps/K) + K + 2) x (9N + nwc) doubles of device memory, allocated
+ * on first use and kept with the handle) and recomputed bit-exactly during the reverse
  * sweep. loss (may be NULL) and info->loss receive L. On success the handle is
  * at the final state of the loop. A step that does not converge returns
  * ISC_ERR_NEWTON_NOCONV (the handle keeps its last accepted state); a

@@ -33,18 +33,30 @@ __device__ __forceinline__ int producer_slot(const int32_t* __restrict__ well_sl
 }
 
 // loss_cell[i] += dt * (oil mass rate produced in cell i) at the converged u^n
+// (and, for a coupled producer's perforation, its converged bottom-hole pressure)
 __global__ void __launch_bounds__(128) k_oil_rate(Params P, const double* __restrict__ u,
                                                   const double* __restrict__ phi_ref,
                                                   const int32_t* __restrict__ well_slot,
-                                                  const WellSlot* __restrict__ slots, double dt,
+                                                  const WellSlot* __restrict__ slots, const double* __restrict__ bhp,
+                                                  const double* __restrict__ depth, double dt,
                                                   double* __restrict__ loss_cell) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= P.n) return;
-  WellSlot w;
-  if (!producer_slot(well_slot, slots, i, &w)) return;
+  const int sl = well_slot[i];
+  if (sl < 0) return;
+  const WellSlot w = slots[sl];
+  if (w.kind != ISC_WELL_BHP_PRODUCER && w.kind != ISC_WELL_COUPLED_PRODUCER) return;
   Base b;
   base_properties(P, u, i, phi_ref[i], b);
-  loss_cell[i] += dt * oil_production(P, b, w.WI, w.bhp).v;
+  if (w.kind == ISC_WELL_BHP_PRODUCER) {
+    loss_cell[i] += dt * oil_production(P, b, w.WI, w.bhp).v;
+  } else {
+    D8 Q[3];
+    double dQ[3];
+    bool on[3];
+    coupled_producer_rates(b, w.WI, bhp[w.wc], w.zref, depth[i], Q, dQ, on);
+    loss_cell[i] += dt * oil_of_rates(P, b, Q).v;
+  }
 }
 
 // ubar^n += Phi_u^T Cbar^n + dt dP/du;  glnk += dt P (the produced rate is linear in WI)
@@ -52,7 +64,8 @@ __global__ void __launch_bounds__(128) k_adj_pre(Params P, const double* __restr
                                                  const double* __restrict__ coke_old,
                                                  const double* __restrict__ phi_ref,
                                                  const int32_t* __restrict__ well_slot,
-                                                 const WellSlot* __restrict__ slots, const double* __restrict__ cbar,
+                                                 const WellSlot* __restrict__ slots, const double* __restrict__ bhp,
+                                                 const double* __restrict__ depth, const double* __restrict__ cbar,
                                                  double* __restrict__ ubar, double* __restrict__ glnk,
                                                  int* __restrict__ dstatus) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -69,6 +82,16 @@ __global__ void __launch_bounds__(128) k_adj_pre(Params P, const double* __restr
   WellSlot w;
   if (producer_slot(well_slot, slots, i, &w)) {
     D8 q = oil_production(P, b, w.WI, w.bhp);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) g[k] += P.dt * q.d[k];
+    glnk[i] += P.dt * q.v;
+  } else if (well_slot[i] >= 0 && w.kind == ISC_WELL_COUPLED_PRODUCER) {
+    // the same with the converged bottom-hole pressure; its own derivative is k_adj_wells_pre's
+    D8 Q[3];
+    double dQ[3];
+    bool on[3];
+    coupled_producer_rates(b, w.WI, bhp[w.wc], w.zref, depth[i], Q, dQ, on);
+    const D8 q = oil_of_rates(P, b, Q);
 #pragma unroll
     for (int k = 0; k < 8; ++k) g[k] += P.dt * q.d[k];
     glnk[i] += P.dt * q.v;
@@ -376,6 +399,87 @@ __global__ void __launch_bounds__(128) k_adj_old(Params P, const double* __restr
   cbar[i] = Vdt * gc + kd[i];
 }
 
+// Coupled wells, before the transposed solve: the right-hand side of each
+// well's row, ubar_w = dt dP/d bhp_w (the produced oil's bottom-hole-pressure
+// derivative; zero for injectors). One thread per coupled well, its
+// perforations in fixed order.
+__global__ void k_adj_wells_pre(Params P, int nwc, const CoupledWell* __restrict__ cw,
+                                const WellSlot* __restrict__ slots, const double* __restrict__ u,
+                                const double* __restrict__ phi_ref, const double* __restrict__ bhp,
+                                const double* __restrict__ depth, double* __restrict__ ubar_w) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= nwc) return;
+  const CoupledWell c = cw[w];
+  double s = 0.0;
+  for (int q = c.first; q < c.first + c.count; ++q) {
+    const WellSlot sl = slots[q];
+    if (sl.kind != ISC_WELL_COUPLED_PRODUCER) continue;
+    Base b;
+    base_properties(P, u, sl.cell, phi_ref[sl.cell], b);
+    D8 Q[3];
+    double dQ[3];
+    bool on[3];
+    coupled_producer_rates(b, sl.WI, bhp[w], sl.zref, depth[sl.cell], Q, dQ, on);
+    const double mo = P.M[1] * b.xlo.v + P.M[2] * b.xho.v;
+    const double mg = P.M[1] * b.y[1].v + P.M[2] * b.y[2].v;
+    s += -(dQ[1] * mo + dQ[2] * mg);
+  }
+  ubar_w[w] = P.dt * s;
+}
+
+// Coupled wells, after the transposed solve: the ln k terms of their
+// perforations. A perforation's residual terms F_well and its part f_q of a
+// rate-controlled well equation are linear in WI = WI_0 exp(ln k), so
+// glnk[cell] += -(lambda_cell . F_well + mu_w f_q), mu_w the well row's
+// multiplier. One thread per coupled well, perforations in fixed order.
+__global__ void k_adj_wells_post(Params P, int nwc, const CoupledWell* __restrict__ cw,
+                                 const WellSlot* __restrict__ slots, const double* __restrict__ u,
+                                 const double* __restrict__ phi_ref, const double* __restrict__ bhp,
+                                 const double* __restrict__ depth, const double* __restrict__ lam,
+                                 double* __restrict__ glnk) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= nwc) return;
+  const CoupledWell c = cw[w];
+  const double mu = lam[(size_t)P.n * 8 + w];
+  for (int q = c.first; q < c.first + c.count; ++q) {
+    const WellSlot sl = slots[q];
+    const int i = sl.cell;
+    Base b;
+    base_properties(P, u, i, phi_ref[i], b);
+    const double* l = lam + (size_t)i * 8;
+    double Fw[7] = {0, 0, 0, 0, 0, 0, 0};
+    double fq = 0.0;
+    if (sl.kind == ISC_WELL_COUPLED_PRODUCER) {
+      D8 Q[3];
+      double dQ[3];
+      bool on[3];
+      coupled_producer_rates(b, sl.WI, bhp[w], sl.zref, depth[i], Q, dQ, on);
+      Fw[0] = -Q[0].v - Q[2].v * b.y[0].v;
+      Fw[1] = -Q[1].v * b.xlo.v - Q[2].v * b.y[1].v;
+      Fw[2] = -Q[1].v * b.xho.v - Q[2].v * b.y[2].v;
+#pragma unroll
+      for (int k = 3; k < 6; ++k) Fw[k] = -Q[2].v * b.y[k].v;
+      Fw[6] = -(Q[0].v * b.H[0].v + Q[1].v * b.H[1].v + Q[2].v * b.H[2].v);
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        if (c.control & (1 << a)) fq -= Q[a].v;
+    } else {
+      bool flows;
+      double dQ;
+      const D8 Q = coupled_injector_rate(b, sl.WI, bhp[w], sl.zref, depth[i], sl.phase, &flows, &dQ);
+      if (flows) {
+#pragma unroll
+        for (int r = 0; r < 7; ++r) Fw[r] = -Q.v * sl.src[r];
+        if (c.control != ISC_CTRL_BHP) fq = Q.v;
+      }
+    }
+    double t = mu * fq;
+#pragma unroll
+    for (int r = 0; r < 7; ++r) t += l[r] * Fw[r];
+    glnk[i] -= t;
+  }
+}
+
 // out[r] = sum_i x[r*len + i], one block per row, fixed order.
 __global__ void __launch_bounds__(256) k_row_sums(int len, const double* __restrict__ x, double* __restrict__ out) {
   __shared__ double sh[256];
@@ -395,7 +499,8 @@ __global__ void __launch_bounds__(256) k_row_sums(int len, const double* __restr
 
 void launch_oil_rate(Handle& h, double dt, cudaStream_t s) {
   int tb = 128;
-  k_oil_rate<<<(h.n + tb - 1) / tb, tb, 0, s>>>(h.P, h.u, h.phi_ref, h.well_slot, h.slots, dt, h.adj.loss_cell);
+  k_oil_rate<<<(h.n + tb - 1) / tb, tb, 0, s>>>(h.P, h.u, h.phi_ref, h.well_slot, h.slots, h.bhp, h.depth, dt,
+                                                h.adj.loss_cell);
 }
 
 void launch_adj_pre(Handle& h, double dt, cudaStream_t s) {
@@ -403,8 +508,11 @@ void launch_adj_pre(Handle& h, double dt, cudaStream_t s) {
   Params P = h.P;
   P.dt = dt;
   P.inv_dt = 1.0 / dt;
-  k_adj_pre<<<(h.n + tb - 1) / tb, tb, 0, s>>>(P, h.u, h.coke_n, h.phi_ref, h.well_slot, h.slots, h.adj.cbar,
-                                               h.adj.ubar, h.adj.glnk, h.dstatus);
+  k_adj_pre<<<(h.n + tb - 1) / tb, tb, 0, s>>>(P, h.u, h.coke_n, h.phi_ref, h.well_slot, h.slots, h.bhp, h.depth,
+                                               h.adj.cbar, h.adj.ubar, h.adj.glnk, h.dstatus);
+  if (h.nwc)
+    k_adj_wells_pre<<<(h.nwc + 31) / 32, 32, 0, s>>>(P, h.nwc, h.cw, h.slots, h.u, h.phi_ref, h.bhp, h.depth,
+                                                     h.adj.ubar + (size_t)h.n * 8);
 }
 
 void launch_bsr_transpose(Handle& h, cudaStream_t s) {
@@ -422,6 +530,9 @@ void launch_adj_post(Handle& h, bool has_old, cudaStream_t s) {
                                   a.grx, a.kd);
   if (a.n_inj > 0)
     k_adj_inj<<<(a.n_inj + 31) / 32, 32, 0, s>>>(a.n_inj, a.inj_first, a.inj_count, h.slots, a.lam, a.glnk);
+  if (h.nwc)
+    k_adj_wells_post<<<(h.nwc + 31) / 32, 32, 0, s>>>(h.P, h.nwc, h.cw, h.slots, h.u, h.phi_ref, h.bhp, h.depth,
+                                                      a.lam, a.glnk);
   if (has_old) k_adj_old<<<grid, tb, 0, s>>>(h.P, h.u_n, h.coke_n, h.phi_ref, a.lam, a.kd, a.ubar, a.cbar);
 }
 

@@ -625,9 +625,9 @@ static int adjoint_forward(isc_handle* h, const isc_adjoint_spec* spec, double* 
     if (!(spec->dt[q] > 0.0) || !isfinite(spec->dt[q])) return set_err(h, ISC_ERR_INVALID_ARG, "step sizes must be > 0");
   if (!(spec->tol_adjoint >= 0.0)) return set_err(h, ISC_ERR_INVALID_ARG, "tol_adjoint must be >= 0");
   if (!h->have_acc) return set_err(h, ISC_ERR_STATE, "isc_begin_step (or isc_init_equilibrium) must come first");
-  if (h->nwc) return set_err(h, ISC_ERR_UNIMPLEMENTED, "the adjoint does not cover coupled wells");
   const int n = h->n;
-  const size_t len = (size_t)n * 8, SN = (size_t)n * 9;
+  // a stored state: u (8N), C_c (N), the coupled wells' bottom-hole pressures
+  const size_t len = (size_t)n * 8, SN = (size_t)n * 9 + h->nwc;
   const int ncp = (N + K - 1) / K;
   const int need = ncp + K + 2;                 // checkpoints, K+1 segment states, the final state
   const int traj0 = ncp, fin = ncp + K + 1;
@@ -637,9 +637,10 @@ static int adjoint_forward(isc_handle* h, const isc_adjoint_spec* spec, double* 
   // workspace
   if (!A.ubar) {
     int e = 0;
-    e |= dalloc(h, &A.ubar, len);
+    // ubar and lambda hold the cells' 8N entries and the coupled wells' rows (Krylov vector length)
+    e |= dalloc(h, &A.ubar, (size_t)h->vstride);
     e |= dalloc(h, &A.cbar, n);
-    e |= dalloc(h, &A.lam, len);
+    e |= dalloc(h, &A.lam, (size_t)h->vstride);
     e |= dalloc(h, &A.glnk, n);
     e |= dalloc(h, &A.grx, (size_t)2 * ISC_MAX_RXN * n);
     e |= dalloc(h, &A.scond, n);
@@ -659,6 +660,8 @@ static int adjoint_forward(isc_handle* h, const isc_adjoint_spec* spec, double* 
   auto save = [&](int k) -> int {
     CUDA_TRY(h, cudaMemcpyAsync(slot(k), h->u, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
     CUDA_TRY(h, cudaMemcpyAsync(slot(k) + len, h->coke, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    if (h->nwc)
+      CUDA_TRY(h, cudaMemcpyAsync(slot(k) + len + n, h->bhp, sizeof(double) * h->nwc, cudaMemcpyDeviceToDevice, s));
     return ISC_OK;
   };
   int st;
@@ -706,7 +709,7 @@ static int adjoint_backward(isc_handle* h, double* g_log_k, double* g_Ea, double
   if (!A.ready) return set_err(h, ISC_ERR_STATE, "run the forward sweep (isc_adjoint_forward) first");
   const int N = (int)A.dts.size(), K = A.K;
   const int n = h->n, nr = h->P.nr;
-  const size_t len = (size_t)n * 8, SN = (size_t)n * 9;
+  const size_t len = (size_t)n * 8, SN = (size_t)n * 9 + h->nwc, vlen = (size_t)h->vlen;
   const int ncp = (N + K - 1) / K;
   const int traj0 = ncp, fin = ncp + K + 1;
   cudaStream_t s = h->stream;
@@ -715,14 +718,18 @@ static int adjoint_backward(isc_handle* h, double* g_log_k, double* g_Ea, double
   auto save = [&](int k) -> int {
     CUDA_TRY(h, cudaMemcpyAsync(slot(k), h->u, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
     CUDA_TRY(h, cudaMemcpyAsync(slot(k) + len, h->coke, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    if (h->nwc)
+      CUDA_TRY(h, cudaMemcpyAsync(slot(k) + len + n, h->bhp, sizeof(double) * h->nwc, cudaMemcpyDeviceToDevice, s));
     return ISC_OK;
   };
   auto load_accepted = [&](int k) -> int {
     CUDA_TRY(h, cudaMemcpyAsync(h->u, slot(k), sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
     CUDA_TRY(h, cudaMemcpyAsync(h->coke, slot(k) + len, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    if (h->nwc)
+      CUDA_TRY(h, cudaMemcpyAsync(h->bhp, slot(k) + len + n, sizeof(double) * h->nwc, cudaMemcpyDeviceToDevice, s));
     return isc_begin_step(h);
   };
-  CUDA_TRY(h, cudaMemsetAsync(A.ubar, 0, sizeof(double) * len, s));
+  CUDA_TRY(h, cudaMemsetAsync(A.ubar, 0, sizeof(double) * vlen, s));
   CUDA_TRY(h, cudaMemsetAsync(A.cbar, 0, sizeof(double) * n, s));
   CUDA_TRY(h, cudaMemsetAsync(A.glnk, 0, sizeof(double) * n, s));
   CUDA_TRY(h, cudaMemsetAsync(A.grx, 0, sizeof(double) * 2 * ISC_MAX_RXN * n, s));
@@ -756,8 +763,9 @@ static int adjoint_backward(isc_handle* h, double* g_log_k, double* g_Ea, double
       launch_old_accumulation(*h, s);
       h->have_acc = true;
       cudaMemcpyAsync(h->u, cur, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
+      if (h->nwc) cudaMemcpyAsync(h->bhp, cur + len + n, sizeof(double) * h->nwc, cudaMemcpyDeviceToDevice, s);
       {
-        Region rg(h, ISC_K_ADJOINT, 1);
+        Region rg(h, ISC_K_ADJOINT, h->nwc ? 2 : 1);
         launch_adj_pre(*h, dt, s);
       }
       if ((result = isc_assemble(h, dt))) break;
@@ -765,27 +773,32 @@ static int adjoint_backward(isc_handle* h, double* g_log_k, double* g_Ea, double
         Region rg(h, ISC_K_ADJOINT, 1);
         launch_bsr_transpose(*h, s);
       }
-      // J^T lambda = ubar (the transposed system is decoupled and preconditioned like J)
-      cudaMemcpyAsync(h->R, A.ubar, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
-      if (h->opt.decouple && (result = isc_decouple(h))) break;
-      if ((result = build_prec(h))) break;
-      {
-        Region rg(h, ISC_K_BLAS1, 1);
-        launch_scale_copy((int)len, 1.0, h->R, h->rhs, s);
-      }
+      // [J C^T-border; B^T D]: the transposed bordered system exchanges the border
+      // column (dF/d bhp per perforation) and the well rows (dF_w/du); D is its own transpose
+      std::swap(h->Bv, h->Cv);
+      // J^T lambda = ubar (the transposed system is decoupled and preconditioned like J);
+      // the wells' rows take dP/d bhp
+      cudaMemcpyAsync(h->R, A.ubar, sizeof(double) * vlen, cudaMemcpyDeviceToDevice, s);
       int its = 0;
       double rel = 0.0;
-      h->opt.tol_lin = tol_adj;
-      if (h->opt.krylov == ISC_KRYLOV_GMRES)
-        result = gmres(h, h->rhs, A.lam, &its, &rel);
-      else
-        result = bicgstab(h, h->rhs, A.lam, &its, &rel);
-      h->opt.tol_lin = tol_saved;
+      if (!(h->opt.decouple && (result = isc_decouple(h))) && !(result = build_prec(h))) {
+        {
+          Region rg(h, ISC_K_BLAS1, 1);
+          launch_scale_copy((int)vlen, 1.0, h->R, h->rhs, s);
+        }
+        h->opt.tol_lin = tol_adj;
+        if (h->opt.krylov == ISC_KRYLOV_GMRES)
+          result = gmres(h, h->rhs, A.lam, &its, &rel);
+        else
+          result = bicgstab(h, h->rhs, A.lam, &its, &rel);
+        h->opt.tol_lin = tol_saved;
+      }
+      std::swap(h->Bv, h->Cv);
       info->krylov_iterations_adjoint += its;
       info->adjoint_rel_residual = std::max(info->adjoint_rel_residual, rel);
       if (result) break;
       {
-        Region rg(h, ISC_K_ADJOINT, q > 1 ? 4 : 3);
+        Region rg(h, ISC_K_ADJOINT, (q > 1 ? 4 : 3) + (h->nwc ? 1 : 0));
         launch_adj_post(*h, q > 1, s);
       }
       CUDA_TRY(h, cudaGetLastError());

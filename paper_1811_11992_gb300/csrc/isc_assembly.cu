@@ -92,16 +92,17 @@ __global__ void __launch_bounds__(128) k_props(Params P, const double* __restric
       // Also the border of the Newton system: dF/d bhp (B), and for a rate
       // control the perforation's part of the well equation, its u-gradient
       // (C) and its bhp-derivative.
-      const double bw = bhp[w.wc];
-      const double zi = depth[i];
       double bcol[8] = {0, 0, 0, 0, 0, 0, 0, 0}, crow[8] = {0, 0, 0, 0, 0, 0, 0, 0};
       double fq = 0.0, dq = 0.0;
+      D8 Qa[3];
+      double dQa[3];
+      bool on[3];
+      coupled_producer_rates(b, w.WI, bhp[w.wc], w.zref, depth[i], Qa, dQa, on);
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        const D8 dphi = bw - b.p - b.gam[a] * (w.zref - zi);
-        if (!(dphi.v < 0.0)) continue;
-        const D8 Q = (w.WI * b.lam[a]) * dphi;
-        const double dQ = w.WI * b.lam[a].v;
+        if (!on[a]) continue;
+        const D8 Q = Qa[a];
+        const double dQ = dQa[a];
         if (a == 0) {
           Rl[0] = Rl[0] - Q;
           bcol[0] -= dQ;
@@ -140,11 +141,9 @@ __global__ void __launch_bounds__(128) k_props(Params P, const double* __restric
       // weight gamma, inflow only (Sec. 2.2, Well Modeling, for injection).
       // Border: dF/d bhp = -dQ/d bhp times the stream; for a rate control the
       // perforation's Q, its u-gradient and its bhp-derivative.
-      const D8 lamT = b.lam[0] + b.lam[1] + b.lam[2];
-      const D8 dphi = bhp[w.wc] - b.p - b.gam[w.phase] * (w.zref - depth[i]);
-      const bool flows = dphi.v > 0.0;
-      const D8 Q = (w.WI * lamT) * dphi;
-      const double dQ = flows ? w.WI * lamT.v : 0.0;
+      bool flows;
+      double dQ;
+      const D8 Q = coupled_injector_rate(b, w.WI, bhp[w.wc], w.zref, depth[i], w.phase, &flows, &dQ);
       if (flows) {
 #pragma unroll
         for (int r = 0; r < 7; ++r) Rl[r] = Rl[r] - Q * w.src[r];

@@ -296,6 +296,46 @@ __device__ __forceinline__ void rate_dC(const Params& P, int r, const Base& b, d
 
 // Oil mass (LO + HO, any phase) leaving through a BHP producer perforation
 // per second, Peaceman rates (Sec. 2.2 Well Modeling), outflow only.
+// Phase rates of a coupled producer's perforation (Sec. 2.2, Well Modeling):
+// Q_a = WI lambda_a (bhp - p - gamma_a (zref - z)) where that is negative
+// (outflow, on[a]), else zero; dQ[a] = dQ_a / d bhp.
+__device__ __forceinline__ void coupled_producer_rates(const Base& b, double WI, double bhp, double zref, double zi,
+                                                       D8 (&Q)[3], double (&dQ)[3], bool (&on)[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const D8 dphi = bhp - b.p - b.gam[a] * (zref - zi);
+    on[a] = dphi.v < 0.0;
+    if (on[a]) {
+      Q[a] = (WI * b.lam[a]) * dphi;
+      dQ[a] = WI * b.lam[a].v;
+    } else {
+      Q[a] = dc(0.0);
+      dQ[a] = 0.0;
+    }
+  }
+}
+
+// Molar rate of the injected stream at a coupled injector's perforation:
+// Q = WI lambda_T (bhp - p - gamma (zref - z)) where that is positive (inflow),
+// lambda_T the cell's total molar mobility and gamma the injected phase's
+// specific weight; *flows and *dQ = dQ / d bhp (zero when not flowing).
+__device__ __forceinline__ D8 coupled_injector_rate(const Base& b, double WI, double bhp, double zref, double zi,
+                                                    int phase, bool* flows, double* dQ) {
+  const D8 lamT = b.lam[0] + b.lam[1] + b.lam[2];
+  const D8 dphi = bhp - b.p - b.gam[phase] * (zref - zi);
+  *flows = dphi.v > 0.0;
+  *dQ = *flows ? WI * lamT.v : 0.0;
+  return (WI * lamT) * dphi;
+}
+
+// Oil mass rate (LO + HO carried by the oil and gas phases, kg/s, positive
+// when produced) of a perforation's phase rates Q (negative = outflow).
+__device__ __forceinline__ D8 oil_of_rates(const Params& P, const Base& b, const D8 (&Q)[3]) {
+  D8 mo = P.M[1] * b.xlo + P.M[2] * b.xho;
+  D8 mg = P.M[1] * b.y[1] + P.M[2] * b.y[2];
+  return -(Q[1] * mo + Q[2] * mg);
+}
+
 __device__ __forceinline__ D8 oil_production(const Params& P, const Base& b, double WI, double bhp) {
   D8 dpw = bhp - b.p;
   if (!(dpw.v < 0.0)) return dc(0.0);
