@@ -549,6 +549,248 @@ __global__ void __launch_bounds__(AWARPS * 32) k_sweep_bwd(int nx, int ny, int n
   }
 }
 
+// ------------------------------------------------- one pencil per warp (small grids)
+// On grids with few pencils the wavefront's latency, not the FP64 pipe's
+// throughput, sets the sweep time, and a lone pencil's cell costs fewer FP64
+// warp instructions when all 32 lanes serve it: lane l holds row r = l/4,
+// columns c = 2(l%4), c+1 of each 8x8 block (two FMAs per block and lane; row
+// sums over the lane quad). Pencils are claimed in natural (j, then k) order;
+// the backward sweep uses the unscaled upper blocks and D^-1.
+template <typename T>
+__device__ __forceinline__ typename V2<T>::t zero2() {
+  typename V2<T>::t z;
+  z.x = T(0);
+  z.y = T(0);
+  return z;
+}
+
+template <typename T>
+__device__ __forceinline__ T quad_sum(T v) {
+  v += __shfl_xor_sync(FULL, v, 1);
+  v += __shfl_xor_sync(FULL, v, 2);
+  return v;
+}
+
+// wait until the lane pair of the neighbour's vector, requested one cell ahead, is final in the whole warp
+template <typename T>
+__device__ __forceinline__ bool settle(const T* p, typename V2<T>::t& v, int* abortf, int* dstatus) {
+  if (__all_sync(FULL, arrived(v.x) && arrived(v.y))) return true;
+  return poll_vec<T>(p, 0, v, abortf, dstatus);
+}
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async_n(void* smem_dst, const void* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(gsrc), "n"(BYTES) : "memory");
+}
+
+template <typename TM>
+struct Slot1 {
+  TM blk[4][64];  // up to 3 off-diagonal blocks of the sweep direction, packed in row order, and D^-1 (index 3)
+  double rhs[8];
+};
+
+// the copies of one cell into a slot: the blocks at row slots first_slot.. that mask marks
+template <typename TM, typename RT>
+__device__ __forceinline__ void stage_cell1(Slot1<TM>* sl, int i, int first_slot, int mask, const Pen& P,
+                                            const TM* __restrict__ A, const TM* __restrict__ Dinv,
+                                            const RT* __restrict__ rhs, int lane) {
+  const int base = row_start(P, i - P.base_jk);
+  int s = first_slot, dst = 0;
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    if (mask & (1 << b)) {
+      cp_async_n<2 * sizeof(TM)>(&sl->blk[dst][2 * lane], A + (size_t)(base + s) * BB + 2 * lane);
+      ++s;
+      ++dst;
+    }
+  }
+  cp_async_n<2 * sizeof(TM)>(&sl->blk[3][2 * lane], Dinv + (size_t)i * BB + 2 * lane);
+  if (lane < 8) cp_async_n<sizeof(RT)>(reinterpret_cast<RT*>(sl->rhs) + lane, rhs + (size_t)i * 8 + lane);
+}
+
+template <typename TM>
+__device__ __forceinline__ typename V2<TM>::t sl_pair(const Slot1<TM>* sl, int b, int lane) {
+  return *reinterpret_cast<const typename V2<TM>::t*>(&sl->blk[b][2 * lane]);
+}
+
+template <typename TM, int R, typename RT>
+__global__ void __launch_bounds__(AWARPS * 32) k_sweep1_fwd(int nx, int ny, int nz, const TM* __restrict__ A,
+                                                            const TM* __restrict__ Dinv, const RT* __restrict__ rhs,
+                                                            TM* __restrict__ y, int* __restrict__ pipe,
+                                                            int* __restrict__ dstatus) {
+  using T2 = typename V2<TM>::t;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Slot1<TM>* ring = reinterpret_cast<Slot1<TM>*>(smem_raw) + (threadIdx.x >> 5) * R;
+  const int lane = threadIdx.x & 31;
+  const int r = lane >> 2, c = (lane & 3) * 2;
+  const int npen = ny * nz, nxy = nx * ny;
+  int* counter = pipe;
+  int* abortf = pipe + 1;
+  for (;;) {
+    int p = 0;
+    if (lane == 0) p = atomicAdd(counter, 1);
+    p = __shfl_sync(FULL, p, 0);
+    if (p >= npen) return;
+    const int j = p % ny, k = p / ny;
+    const bool hy = j > 0, hz = k > 0;
+    const int base_jk = nx * (j + ny * k);
+    const Pen PEN = make_pen(nx, ny, nz, j, k, base_jk);
+    // blocks of row (j, k, x) in order -z, -y, -x
+    auto mask_of = [&](int x) { return (hz ? 1 : 0) | (hy ? 2 : 0) | (x > 0 ? 4 : 0); };
+#pragma unroll 1
+    for (int q = 0; q < R - 1; ++q) {
+      if (q < nx) stage_cell1<TM, RT>(ring + q, base_jk + q, 0, mask_of(q), PEN, A, Dinv, rhs, lane);
+      cp_async_commit();
+    }
+    T2 rz = zero2<TM>(), ry = zero2<TM>();
+    if (hz) ld_relaxed_v2(y + (size_t)(base_jk - nxy) * 8 + c, rz.x, rz.y);
+    if (hy) ld_relaxed_v2(y + (size_t)(base_jk - nx) * 8 + c, ry.x, ry.y);
+    TM yp0 = TM(0), yp1 = TM(0);
+    for (int x = 0; x < nx; ++x) {
+      const int i = base_jk + x;
+      if (x + R - 1 < nx)
+        stage_cell1<TM, RT>(ring + (x + R - 1) % R, base_jk + x + R - 1, 0, mask_of(x + R - 1), PEN, A, Dinv, rhs,
+                            lane);
+      cp_async_commit();
+      cp_async_wait<R - 1>();
+      __syncwarp();
+      const Slot1<TM>* sl = ring + x % R;
+      const int m = mask_of(x);
+      int b = 0;
+      T2 az = zero2<TM>(), ay = zero2<TM>(), ax = zero2<TM>();
+      if (m & 1) az = sl_pair<TM>(sl, b++, lane);
+      if (m & 2) ay = sl_pair<TM>(sl, b++, lane);
+      if (m & 4) ax = sl_pair<TM>(sl, b, lane);
+      const T2 d = sl_pair<TM>(sl, 3, lane);
+      // the row sum starts from r_i / 4 on each lane of the quad and subtracts with negated FMA operands
+      TM acc = (TM)reinterpret_cast<const RT*>(sl->rhs)[r] * TM(0.25);
+      acc = fma(-ax.x, yp0, fma(-ax.y, yp1, acc));
+      if (hz) {
+        if (!settle<TM>(y + (size_t)(i - nxy) * 8 + c, rz, abortf, dstatus)) {
+          cp_async_wait<0>();  // no copy of this warp is left in flight when it leaves
+          return;
+        }
+        acc = fma(-az.x, rz.x, fma(-az.y, rz.y, acc));
+      }
+      if (hy) {
+        if (!settle<TM>(y + (size_t)(i - nx) * 8 + c, ry, abortf, dstatus)) {
+          cp_async_wait<0>();
+          return;
+        }
+        acc = fma(-ay.x, ry.x, fma(-ay.y, ry.y, acc));
+      }
+      const TM t = quad_sum(acc);  // t_r = r - A v
+      const TM t0 = __shfl_sync(FULL, t, 4 * c), t1 = __shfl_sync(FULL, t, 4 * c + 4);
+      const TM yr = quad_sum(fma(d.x, t0, d.y * t1));
+      if ((lane & 3) == 0) st_relaxed(y + (size_t)i * 8 + r, yr);
+      yp0 = __shfl_sync(FULL, yr, 4 * c);
+      yp1 = __shfl_sync(FULL, yr, 4 * c + 4);
+      if (x + 1 < nx) {
+        if (hz) ld_relaxed_v2(y + (size_t)(i + 1 - nxy) * 8 + c, rz.x, rz.y);
+        if (hy) ld_relaxed_v2(y + (size_t)(i + 1 - nx) * 8 + c, ry.x, ry.y);
+      }
+      __syncwarp();  // every lane is done with this slot before it is refilled
+    }
+    cp_async_wait<0>();
+    __syncwarp();
+  }
+}
+
+template <typename TM, int R>
+__global__ void __launch_bounds__(AWARPS * 32) k_sweep1_bwd(int nx, int ny, int nz, const TM* __restrict__ A,
+                                                            const TM* __restrict__ Dinv, const TM* __restrict__ yin,
+                                                            TM* __restrict__ zs, double* __restrict__ z64,
+                                                            int* __restrict__ pipe, int* __restrict__ dstatus) {
+  using T2 = typename V2<TM>::t;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Slot1<TM>* ring = reinterpret_cast<Slot1<TM>*>(smem_raw) + (threadIdx.x >> 5) * R;
+  const int lane = threadIdx.x & 31;
+  const int r = lane >> 2, c = (lane & 3) * 2;
+  const int npen = ny * nz, nxy = nx * ny;
+  int* counter = pipe;
+  int* abortf = pipe + 1;
+  for (;;) {
+    int g = 0;
+    if (lane == 0) g = atomicAdd(counter, 1);
+    g = __shfl_sync(FULL, g, 0);
+    if (g >= npen) return;
+    const int p = npen - 1 - g;
+    const int j = p % ny, k = p / ny;
+    const bool hy = j < ny - 1, hz = k < nz - 1;
+    const int nlow_jk = (k > 0) + (j > 0);
+    const int base_jk = nx * (j + ny * k);
+    const Pen PEN = make_pen(nx, ny, nz, j, k, base_jk);
+    // blocks of row (j, k, x) after the diagonal in order +x, +y, +z
+    auto mask_of = [&](int x) { return (x < nx - 1 ? 1 : 0) | (hy ? 2 : 0) | (hz ? 4 : 0); };
+    auto first_of = [&](int x) { return nlow_jk + (x > 0) + 1; };
+#pragma unroll 1
+    for (int q = 0; q < R - 1; ++q) {
+      if (q < nx) {
+        const int x = nx - 1 - q;
+        stage_cell1<TM, TM>(ring + q, base_jk + x, first_of(x), mask_of(x), PEN, A, Dinv, yin, lane);
+      }
+      cp_async_commit();
+    }
+    T2 rz = zero2<TM>(), ry = zero2<TM>();
+    if (hz) ld_relaxed_v2(zs + (size_t)(base_jk + nx - 1 + nxy) * 8 + c, rz.x, rz.y);
+    if (hy) ld_relaxed_v2(zs + (size_t)(base_jk + nx - 1 + nx) * 8 + c, ry.x, ry.y);
+    TM zp0 = TM(0), zp1 = TM(0);
+    for (int step = 0; step < nx; ++step) {
+      const int x = nx - 1 - step;
+      const int i = base_jk + x;
+      const int ss = step + R - 1;
+      if (ss < nx)
+        stage_cell1<TM, TM>(ring + ss % R, base_jk + (nx - 1 - ss), first_of(nx - 1 - ss), mask_of(nx - 1 - ss), PEN,
+                            A, Dinv, yin, lane);
+      cp_async_commit();
+      cp_async_wait<R - 1>();
+      __syncwarp();
+      const Slot1<TM>* sl = ring + step % R;
+      const int m = mask_of(x);
+      int b = 0;
+      T2 ax = zero2<TM>(), ay = zero2<TM>(), az = zero2<TM>();
+      if (m & 1) ax = sl_pair<TM>(sl, b++, lane);
+      if (m & 2) ay = sl_pair<TM>(sl, b++, lane);
+      if (m & 4) az = sl_pair<TM>(sl, b, lane);
+      const T2 d = sl_pair<TM>(sl, 3, lane);
+      const TM yi = reinterpret_cast<const TM*>(sl->rhs)[r];  // the forward result, staged with the blocks
+      TM acc = fma(ax.x, zp0, ax.y * zp1);
+      if (hz) {
+        if (!settle<TM>(zs + (size_t)(i + nxy) * 8 + c, rz, abortf, dstatus)) {
+          cp_async_wait<0>();
+          return;
+        }
+        acc = fma(az.x, rz.x, fma(az.y, rz.y, acc));
+      }
+      if (hy) {
+        if (!settle<TM>(zs + (size_t)(i + nx) * 8 + c, ry, abortf, dstatus)) {
+          cp_async_wait<0>();
+          return;
+        }
+        acc = fma(ay.x, ry.x, fma(ay.y, ry.y, acc));
+      }
+      const TM sr = quad_sum(acc);  // (U z)_r
+      const TM s0 = __shfl_sync(FULL, sr, 4 * c), s1 = __shfl_sync(FULL, sr, 4 * c + 4);
+      // z_r = y_r - (D^-1 U z)_r: the quad sum starts from y_r / 4 on each lane
+      const TM zr = quad_sum(fma(-d.x, s0, fma(-d.y, s1, yi * TM(0.25))));
+      if ((lane & 3) == 0) {
+        st_relaxed(zs + (size_t)i * 8 + r, zr);
+        if (z64) z64[(size_t)i * 8 + r] = (double)zr;
+      }
+      zp0 = __shfl_sync(FULL, zr, 4 * c);
+      zp1 = __shfl_sync(FULL, zr, 4 * c + 4);
+      if (step + 1 < nx) {
+        if (hz) ld_relaxed_v2(zs + (size_t)(i - 1 + nxy) * 8 + c, rz.x, rz.y);
+        if (hy) ld_relaxed_v2(zs + (size_t)(i - 1 + nx) * 8 + c, ry.x, ry.y);
+      }
+      __syncwarp();
+    }
+    cp_async_wait<0>();
+    __syncwarp();
+  }
+}
+
 // slot of neighbour direction d (0 -z, 1 -y, 2 -x, 3 diag, 4 +x, 5 +y, 6 +z) in the sorted BSR row of cell c
 __device__ __forceinline__ int slot_of(int nx, int ny, int nz, int c, int d) {
   const int ix = c % nx, iy = (c / nx) % ny, iz = c / (nx * ny);
@@ -779,9 +1021,31 @@ int sweep_blocks(K kernel, size_t smem, int tasks) {
   return need < per_sm * sms ? need : per_sm * sms;
 }
 
+// Grids with at most this many x-pencils run the one-pencil-per-warp sweeps
+// (latency-bound wavefront); larger grids the pencil pairs (FP64-pipe- or
+// HBM-bound). Measured per apply, one pencil / pairs: 1,200 pencils (60x60x20)
+// 0.331 / 0.393 ms FP64, 0.230 / 0.249 ms FP32; 3,000 (100x100x30) 0.739 /
+// 0.759 and 0.423 / 0.441; 3,600 (120x120x30) 0.990 / 0.900 and 0.512 / 0.532.
+constexpr int SWEEP1_MAX_PENCILS64 = 3000;
+constexpr int SWEEP1_MAX_PENCILS32 = 3600;
+template <typename TM>
+constexpr int sweep1_max() {
+  return sizeof(TM) == 8 ? SWEEP1_MAX_PENCILS64 : SWEEP1_MAX_PENCILS32;
+}
+
 template <typename TM, typename RT>
 cudaError_t launch_fwd(int nx, int ny, int nz, const TM* A, const TM* Dinv, const RT* r, TM* y, int* pipe,
                        int* dstatus, cudaStream_t s) {
+  if (ny * nz <= sweep1_max<TM>()) {
+    auto kern = k_sweep1_fwd<TM, sweep_r<TM>(), RT>;
+    const size_t smem = sizeof(Slot1<TM>) * sweep_r<TM>() * AWARPS;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaMemsetAsync(pipe, 0, 2 * sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(y, 0xff, sizeof(TM) * (size_t)nx * ny * nz * 8, s);  // NaN sentinel
+    if (e != cudaSuccess) return e;
+    kern<<<sweep_blocks(kern, smem, ny * nz), AWARPS * 32, smem, s>>>(nx, ny, nz, A, Dinv, r, y, pipe, dstatus);
+    return cudaGetLastError();
+  }
   auto kern = k_sweep_fwd<TM, sweep_r<TM>(), RT>;
   const size_t smem = sweep_smem<TM, RT>();
   // idempotent; the rings need more than the default 48 KB of dynamic shared memory
@@ -797,6 +1061,16 @@ cudaError_t launch_fwd(int nx, int ny, int nz, const TM* A, const TM* Dinv, cons
 template <typename TM, bool PRE>
 cudaError_t launch_bwd(int nx, int ny, int nz, const TM* A, const TM* Dinv, const TM* uhat, const TM* y, TM* z,
                        double* z64, int* pipe, int* dstatus, cudaStream_t s) {
+  if (ny * nz <= sweep1_max<TM>()) {  // (the one-pencil sweep applies D^-1 to the unscaled upper blocks)
+    auto kern = k_sweep1_bwd<TM, sweep_r<TM>()>;
+    const size_t smem = sizeof(Slot1<TM>) * sweep_r<TM>() * AWARPS;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaMemsetAsync(pipe, 0, 2 * sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(z, 0xff, sizeof(TM) * (size_t)nx * ny * nz * 8, s);  // NaN sentinel
+    if (e != cudaSuccess) return e;
+    kern<<<sweep_blocks(kern, smem, ny * nz), AWARPS * 32, smem, s>>>(nx, ny, nz, A, Dinv, y, z, z64, pipe, dstatus);
+    return cudaGetLastError();
+  }
   auto kern = k_sweep_bwd<TM, sweep_r<TM>(), PRE>;
   const size_t smem = sweep_smem<TM, TM>();
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
