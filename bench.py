@@ -193,13 +193,26 @@ def hbm_peak():
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one call of a kernel
 # class, per cell, from one ncu capture of the current kernels on a smaller grid
 # of the same recipe; a call's traffic grows with the cells it sweeps, so the
-# full-size figure is this times the workload's cells. Keyed by (class, precision).
+# full-size figure is this times the workload's cells. Keyed by (class, precision,
+# sweep layout): grids with few pencils run the one-pencil-per-warp sweeps.
 MEASURED_TRAFFIC = {
-    ("prec_apply", "fp64"): (1245.53e6 / 320000, "large 40x160x50",
-                             "profiles/k_sweep_fwd_bwd_large_40x160x50.md"),
-    ("prec_apply", "mixed"): (648.48e6 / 320000, "large 40x160x50",
-                              "profiles/k_sweep_fwd_bwd_large_40x160x50.md"),
+    ("prec_apply", "fp64", "pair"): (1245.53e6 / 320000, "large 40x160x50",
+                                     "profiles/k_sweep_fwd_bwd_large_40x160x50.md"),
+    ("prec_apply", "mixed", "pair"): (648.48e6 / 320000, "large 40x160x50",
+                                      "profiles/k_sweep_fwd_bwd_large_40x160x50.md"),
+    ("prec_apply", "fp64", "single"): (313.37e6 / 72000, "field 60x60x20",
+                                       "profiles/k_sweep1_fwd_bwd_field_60x60x20.md"),
+    ("prec_apply", "mixed", "single"): (157.89e6 / 72000, "field 60x60x20",
+                                        "profiles/k_sweep1_fwd_bwd_field_60x60x20.md"),
 }
+# the largest ny * nz that runs the one-pencil-per-warp sweeps (SWEEP1_MAX_PENCILS64 /
+# SWEEP1_MAX_PENCILS32 of the library's ILU(0) sweeps)
+SWEEP1_MAX_PENCILS = {"fp64": 3000, "mixed": 3600}
+
+
+def sweep_layout(case, precision):
+    key = "fp64" if precision == "fp64" else "mixed"
+    return "single" if case.ny * case.nz <= SWEEP1_MAX_PENCILS[key] else "pair"
 
 
 def class_gbs(stats, cls, byts):
@@ -337,7 +350,7 @@ def roofline(dom, stats, case, nnzb, fp64_gflops, precision="fp64", its=None, or
     else:
         out.update(bound="hbm", achieved=ach_gbs, peak=hbm, unit="GB/s", frac=ach_gbs / hbm,
                    peak_source="MEASURED_PEAKS.json hbm_gbs")
-    m = MEASURED_TRAFFIC.get((dom, "fp64" if not fp32 else "mixed"))
+    m = MEASURED_TRAFFIC.get((dom, "fp64" if not fp32 else "mixed", sweep_layout(case, precision)))
     out["traffic"] = m[0] * n if m else None
     if m:
         out["traffic_source"] = f"{m[2]} (captured on {m[1]}, scaled per cell to {case.n} cells)"

@@ -75,7 +75,7 @@ def test_traffic_is_scaled_per_cell(bench):
     nnzb = _nnzb(200, 200, 50)
     st = {"prec_apply": {"calls": 10, "ms": 38.0, "launches": 20}}
     r = bench.roofline("prec_apply", st, case, nnzb, 1200.0, "fp64")
-    per_cell = bench.MEASURED_TRAFFIC[("prec_apply", "fp64")][0]
+    per_cell = bench.MEASURED_TRAFFIC[("prec_apply", "fp64", "pair")][0]
     assert r["traffic"] == pytest.approx(per_cell * case.n)
     assert "scaled per cell" in r["traffic_source"]
     # the measured DRAM traffic is within a few per cent of the algorithmic bytes
@@ -126,3 +126,18 @@ def test_fullsize_oracle_kernel_timing_runs_and_skips_without_memory(bench):
     assert r["spmv_s_per_call"] > 0 and r["ilu_apply_s_per_call"] > 0 and r["cores"] == 1
     skipped = bench.oracle_fullsize_kernels(case, need_gb=1.0e9)
     assert set(skipped) == {"skipped"}
+
+
+def test_sweep_layout_thresholds_match_the_library(bench):
+    """The bench picks the traffic figure of the sweep layout the library runs:
+    its thresholds are the library's constants."""
+    import re
+    src = open(os.path.join(ROOT, "paper_1811_11992_gb300", "csrc", "isc_ilu_pipe.cu")).read()
+    lib = {k: int(v) for k, v in re.findall(r"constexpr int (SWEEP1_MAX_PENCILS\d\d) = (\d+);", src)}
+    assert bench.SWEEP1_MAX_PENCILS == {"fp64": lib["SWEEP1_MAX_PENCILS64"], "mixed": lib["SWEEP1_MAX_PENCILS32"]}
+    small, large = _Case(60, 60, 20), _Case(200, 200, 50)
+    assert bench.sweep_layout(small, "fp64") == "single" and bench.sweep_layout(large, "fp64") == "pair"
+    nnzb = _nnzb(60, 60, 20)
+    st = {"prec_apply": {"calls": 10, "ms": 3.2, "launches": 20}}
+    r = bench.roofline("prec_apply", st, small, nnzb, 1200.0, "fp64")
+    assert r["traffic"] == pytest.approx(bench.MEASURED_TRAFFIC[("prec_apply", "fp64", "single")][0] * small.n)
