@@ -300,10 +300,10 @@ def class_model(cls, n, nnzb, fp32=False, its=None, orth="cgs1"):
         return n * (64 + 56 + 16 + 64 + 512 + 16 * 9 * 8), n * ASSEMBLY_FLOPS_PER_CELL["props"]
     if cls == "flux":
         # face pass: reads the staged quantities (each cell's once from DRAM) and the
-        # transmissibilities, writes the off-diagonal blocks, adds to R and the diagonal block,
-        # parks the +side shares (7 rows x 9 doubles per face); gather: reads them back and adds
-        # them to R and the diagonal block
-        return (n * (16 * 9 * 8 + 3 * 8) + (nnzb - n) * 512 + 2 * n * (64 + 512) * 2 + 2 * n * 3 * 7 * 9 * 8,
+        # transmissibilities, writes the off-diagonal blocks, parks the face fluxes (3 x 7
+        # doubles per cell); gather: reads the fluxes and rows 0..6 of the off-diagonal blocks
+        # back, adds to R and the diagonal block
+        return (n * (16 * 9 * 8 + 3 * 8) + (nnzb - n) * (512 + 448) + 2 * n * 3 * 7 * 8 + n * (64 + 512) * 2,
                 n * ASSEMBLY_FLOPS_PER_CELL["flux"])
     if cls == "spmv":
         return spmv_bytes(n, nnzb), 2 * 64 * (nnzb - n)

@@ -1160,7 +1160,7 @@ int isc_create(const isc_grid* grid, const isc_rock* rock, const isc_fluid* fl, 
   e |= dalloc(h, &h->coke_n, n);
   e |= dalloc(h, &h->acc_n, (size_t)n * 7);
   e |= dalloc(h, &h->props, (size_t)n * NQD);
-  e |= dalloc(h, &h->fbuf, (size_t)n * 2 * 3 * 7 * 9);
+  e |= dalloc(h, &h->fbuf, (size_t)n * 3 * 7);
   e |= dalloc(h, &h->R, len);
   e |= dalloc(h, &h->J, (size_t)h->nnzb * BB);
   e |= dalloc(h, &h->ntot, n);

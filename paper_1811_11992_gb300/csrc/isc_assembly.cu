@@ -9,9 +9,9 @@
 //           towards +x, +y or +z, evaluated once in its (lo, hi) orientation:
 //           upstream weighting per phase, harmonic transmissibility, the face
 //           flux and its derivatives w.r.t. both cells; writes both cells'
-//           off-diagonal blocks of the face and parks the two cells' shares of
-//           the residual and diagonal block (exact negatives of each other) for
-// k_flux_gather, which adds each cell's shares from its six faces.
+//           off-diagonal blocks of the face and parks the flux for
+// k_flux_gather, which adds each cell's residual and diagonal-block shares of
+//           its six faces (the diagonal shares read back from those blocks).
 #include <math.h>
 
 #include "dual8.cuh"
@@ -311,18 +311,16 @@ __device__ __forceinline__ double face_flux(const Params& P, int r, int lo, int 
   return F;
 }
 
-// Face pass: thread (direction d, cell i, row r) evaluates the flux of row r
-// over the face between i and its neighbour j towards +d, once per face
+// Face pass: thread (direction d, cell i, row r) evaluates the flux F of row
+// r over the face between i and its neighbour j towards +d, once per face
 // (blockIdx.y is the direction: three threads per cell and row keep enough
 // independent faces in flight). It writes both cells' off-diagonal block rows
-// of the face (no other thread writes them) and parks the two cells' shares
-// of the residual and of the diagonal block in fbuf, for k_flux_gather (a
-// cell's row is shared by the faces of six threads, so it is not added to here).
-// fbuf layout: (((side * 3 + d) * 7 + r) * 9 + c) * N + cell; side 0: the
-// share of the face's -side cell i (flux out, d/du_i), side 1: that of its
-// +side cell j (the exact negatives: flux in, -d/du_j); c = 0 the residual
-// share, c = 1..8 the diagonal-block row share. Written only where the face
-// exists.
+// of the face, J(i, +d) = dF/du_j and J(j, -d) = -dF/du_i (no other thread
+// writes them), and parks F in fbuf[(d * 7 + r) * N + i] for k_flux_gather:
+// a cell's own row is shared by the faces of six threads, so it is not added
+// to here. The diagonal-block shares are the negatives of those two
+// off-diagonal rows (dF/du_i for i, -dF/du_j for j), which the gather reads
+// back from J.
 __global__ void __launch_bounds__(256) k_flux(Params P, const double* __restrict__ u, const double* __restrict__ props,
                                               const double* __restrict__ tx, const double* __restrict__ ty,
                                               const double* __restrict__ tz, const double* __restrict__ depth,
@@ -368,44 +366,53 @@ __global__ void __launch_bounds__(256) k_flux(Params P, const double* __restrict
   double* Jn = J + (size_t)(rowptr[j] + sj) * BB + r * 8;
 #pragma unroll
   for (int k = 0; k < 8; k += 2) *reinterpret_cast<double2*>(Jn + k) = make_double2(-dlo[k], -dlo[k + 1]);
-  double* f0 = fbuf + (size_t)((dir * 7 + r) * 9) * n + i;
-  double* f1 = fbuf + (size_t)(((3 + dir) * 7 + r) * 9) * n + j;
-  __stcs(f0, F);
-  __stcs(f1, -F);
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    __stcs(f0 + (size_t)(1 + k) * n, dlo[k]);
-    __stcs(f1 + (size_t)(1 + k) * n, -dhi[k]);
-  }
+  fbuf[(size_t)(dir * 7 + r) * n + i] = F;
 }
 
-// Gather pass: thread (cell i, row r < 7) adds the shares that the face pass
-// parked for cell i from its six faces to its residual and diagonal block.
+// Gather pass: thread (cell i, row r < 7) adds cell i's shares of its six
+// faces to its residual (+F over the faces towards +x, +y, +z, -F over those
+// towards -x, -y, -z, F from fbuf) and to its diagonal block row: minus the
+// face's off-diagonal row in the neighbour's row of J (the neighbour's -d
+// block for a face towards +d, its +d block for a face towards -d).
 __global__ void __launch_bounds__(256) k_flux_gather(Params P, const int32_t* __restrict__ rowptr,
                                                      const double* __restrict__ fbuf, double* __restrict__ R,
                                                      double* __restrict__ J) {
   const int r = threadIdx.x >> 5;
   const int i = blockIdx.x * 32 + (threadIdx.x & 31);
   if (i >= P.n || r == 7) return;
-  const int n = P.n, nx = P.nx, ny = P.ny, nxy = P.nx * P.ny;
+  const int n = P.n, nx = P.nx, ny = P.ny, nz = P.nz, nxy = P.nx * P.ny;
   const int ix = i % nx, iy = (i / nx) % ny, iz = i / nxy;
-  // side 0: faces towards +x, +y, +z; side 1: faces towards -x, -y, -z
-  const bool has[2][3] = {{ix < nx - 1, iy < ny - 1, iz < P.nz - 1}, {ix > 0, iy > 0, iz > 0}};
   double Rs = 0.0;
   double dd[8];
 #pragma unroll
   for (int k = 0; k < 8; ++k) dd[k] = 0.0;
 #pragma unroll
-  for (int side = 0; side < 2; ++side)
+  for (int dir = 0; dir < 3; ++dir) {
+    const int e = dir == 0 ? 1 : dir == 1 ? nx : nxy;
+    const int c = dir == 0 ? ix : dir == 1 ? iy : iz, cmax = dir == 0 ? nx : dir == 1 ? ny : nz;
+    if (c < cmax - 1) {
+      // face (i, j = i + e): the neighbour's -dir block holds -dF/du_i
+      const int j = i + e;
+      const int jy = iy + (dir == 1), jz = iz + (dir == 2);
+      const int sj = dir == 0 ? (int)(jz > 0) + (int)(jy > 0) : dir == 1 ? (int)(jz > 0) : 0;
+      Rs += fbuf[(size_t)(dir * 7 + r) * n + i];
+      const double* b = J + (size_t)(rowptr[j] + sj) * BB + r * 8;
 #pragma unroll
-    for (int dir = 0; dir < 3; ++dir) {
-      if (!has[side][dir]) continue;
-      const double* fb = fbuf + (size_t)(((side * 3 + dir) * 7 + r) * 9) * n + i;
-      Rs += __ldcs(fb);
-#pragma unroll
-      for (int k = 0; k < 8; ++k) dd[k] += __ldcs(fb + (size_t)(1 + k) * n);
+      for (int k = 0; k < 8; ++k) dd[k] -= b[k];
     }
-  const int dslot = (int)has[1][0] + (int)has[1][1] + (int)has[1][2];
+    if (c > 0) {
+      // face (j = i - e, i): the neighbour's +dir block holds dF/du_i
+      const int j = i - e;
+      const int jx = ix - (dir == 0), jy = iy - (dir == 1), jz = iz - (dir == 2);
+      const int sj = (int)(jz > 0) + (int)(jy > 0) + (int)(jx > 0) + 1 + (dir >= 1 ? (int)(jx < nx - 1) : 0) +
+                     (dir == 2 ? (int)(jy < ny - 1) : 0);
+      Rs -= fbuf[(size_t)(dir * 7 + r) * n + j];
+      const double* b = J + (size_t)(rowptr[j] + sj) * BB + r * 8;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) dd[k] -= b[k];
+    }
+  }
+  const int dslot = (int)(iz > 0) + (int)(iy > 0) + (int)(ix > 0);
   R[(size_t)i * 8 + r] += Rs;
   double* Jd = J + (size_t)(rowptr[i] + dslot) * BB + r * 8;
 #pragma unroll

@@ -217,8 +217,8 @@ struct Handle {
   double* acc_n = nullptr;                        // accumulation of the accepted state (7N SoA)
   // device: assembly
   double* props = nullptr;                        // staged face quantities (NQD * N)
-  double* fbuf = nullptr;                         // face pass: both cells' shares of each face's flux and
-                                                  // diagonal-block row, parked for the gather (2*3*7*9*N)
+  double* fbuf = nullptr;                         // face pass: each face's flux per row, parked for the
+                                                  // gather (3 directions * 7 rows * N)
   double* R = nullptr;                            // residual, block-major 8N
   double* J = nullptr;                            // BSR values nnzb*64
   double* ntot = nullptr;                         // per-cell total moles (norm scaling)
