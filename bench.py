@@ -289,7 +289,7 @@ def gmres_blas1_work(n, its, restart=30, orth="cgs1"):
 # Executed FP64 flops per cell of the assembly kernels (2 DFMA + DADD + DMUL from an
 # ncu count of the dual-number tangent code, which has no closed-form flop count),
 # profiles/fp64_instruction_counts_large_100x100x30.md
-ASSEMBLY_FLOPS_PER_CELL = {"props": 5810.0, "flux": 3928.0 + 434.0}  # flux: face pass + gather
+ASSEMBLY_FLOPS_PER_CELL = {"props": 5810.0, "flux": 3742.0 + 434.0}  # flux: face pass + gather
 
 
 def class_model(cls, n, nnzb, fp32=False, its=None, orth="cgs1"):

@@ -217,10 +217,16 @@ def _degenerate(name):
         return inp.small_box(1, 4, 3)
     if name == "flat":
         return inp.small_box(5, 3, 1)
+    if name == "ny1":
+        return inp.small_box(5, 1, 4)
+    if name == "column":
+        case = inp.small_box(1, 1, 6)
+        case.wells = case.wells[:1]           # both wells of the box would share the column
+        return case
     raise ValueError(name)
 
 
-@pytest.mark.parametrize("name", ["single", "pair", "nx1", "flat"])
+@pytest.mark.parametrize("name", ["single", "pair", "nx1", "flat", "ny1", "column"])
 def test_degenerate_grids(Simulator, name):
     case = _degenerate(name)
     a = inp.random_state(case, 31)
