@@ -489,6 +489,7 @@ def run_isc(args):
     value = job_throughput(world, args.steps, ms_total)
     kry = [i.krylov_iterations for i in infos]
     headline = leg_summary(ms_total / args.steps, stats, infos, args.steps)
+    dev_bytes = g.device_bytes()    # the handle's arrays for the timed configuration
     e2e = mixed = mixed_fgmres = cpr_block = orth_leg = None
     mst = fst = None
     leg_steps = max(3, args.steps // 4)
@@ -547,6 +548,8 @@ def run_isc(args):
     rooflines = {k: roofline(k, stats, case, g.nnzb, fp64_gflops, args.precision, its_total, args.orth)
                  for k in ("prec_apply", "spmv", "blas1", "gj", "ilu_factor", "props", "flux") if stats[k]["calls"]}
     hbm = hbm_table(stats, mst, fst, case, g.nnzb)
+    device_memory = {"bytes": dev_bytes, "bytes_per_cell": dev_bytes / n,
+                     "bytes_with_all_legs": g.device_bytes()}   # + FP32 copies, inner basis, CPR levels
     launches = sum(v["launches"] for v in stats.values())
     nnzb = g.nnzb
     b.close()
@@ -567,6 +570,7 @@ def run_isc(args):
         "alu_peaks_gflops": {"fp64": fp64_gflops, "fp32": fp32_gflops,
                              "how": "isc_measure_fma_rates: register FMA chains on every SM, best of 5"},
         "hbm": hbm,
+        "device_memory": device_memory,
         "clocks": clocks,
         "mixed": mixed,
         "mixed_fgmres": mixed_fgmres,

@@ -399,6 +399,15 @@ int isc_precond_apply(struct isc_handle* h, const double* r, double* z);
 int isc_get_ilu_diag(struct isc_handle* h, double* dinv);
 int isc_get_stats(struct isc_handle* h, isc_stats* stats);
 int isc_reset_stats(struct isc_handle* h);
+/* Bytes of device memory the handle holds now: the arrays allocated by
+ * isc_create (Jacobian blocks, state, staged face quantities, ILU factors,
+ * the GMRES basis of options.restart + 1 vectors) and the workspaces
+ * allocated on first use (FP32 preconditioner copies and inner FP32 GMRES
+ * basis of the mixed modes, CPR multigrid levels, adjoint checkpoints), as
+ * requested from cudaMalloc (the allocator's rounding not included). Excludes
+ * the CUDA context, module code and pinned host memory. Host-only: launches
+ * nothing. ISC_ERR_INVALID_ARG on a null pointer. */
+int isc_get_device_bytes(struct isc_handle* h, uint64_t* bytes);
 
 /* ---------------------------------------------------------------- kernels */
 

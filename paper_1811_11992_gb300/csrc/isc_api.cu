@@ -106,9 +106,18 @@ int check_device_status(isc_handle* h) {
 
 template <typename T>
 int dalloc(isc_handle* h, T** p, size_t count) {
-  cudaError_t e = cudaMalloc((void**)p, sizeof(T) * std::max<size_t>(count, 1));
+  const size_t bytes = sizeof(T) * std::max<size_t>(count, 1);
+  cudaError_t e = cudaMalloc((void**)p, bytes);
   if (e != cudaSuccess) return set_err(h, ISC_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  h->dev_sizes[(void*)*p] = bytes;
   return ISC_OK;
+}
+
+// frees an allocation made by dalloc before the handle's end
+void dfree(isc_handle* h, void* p) {
+  if (!p) return;
+  h->dev_sizes.erase(p);
+  cudaFree(p);
 }
 
 void free_all(isc_handle* h) {
@@ -119,6 +128,7 @@ void free_all(isc_handle* h) {
                   h->adj.scond, h->adj.kd, h->adj.loss_cell, h->adj.sums, h->adj.inj_first, h->adj.inj_count};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  h->dev_sizes.clear();
   cpr_free(*h);
   if (h->h_scal) cudaFreeHost(h->h_scal);
   if (h->h_status) cudaFreeHost(h->h_status);
@@ -261,8 +271,7 @@ int build_prec(isc_handle* h) {
     }
     if (h->opt.precision == ISC_PRECISION_MIXED_FGMRES && h->inner_alloc < h->opt.inner_its) {
       // inner FP32 GMRES workspace, (re)allocated when inner_its grows
-      for (void* q : {(void*)h->V32, (void*)h->Z32, (void*)h->w32, (void*)h->gm_in, (void*)h->scal_in})
-        if (q) cudaFree(q);
+      for (void* q : {(void*)h->V32, (void*)h->Z32, (void*)h->w32, (void*)h->gm_in, (void*)h->scal_in}) dfree(h, q);
       h->V32 = h->Z32 = h->w32 = nullptr;
       h->gm_in = h->scal_in = nullptr;
       const size_t n8 = (size_t)h->n * 8;
@@ -650,7 +659,7 @@ static int adjoint_forward(isc_handle* h, const isc_adjoint_spec* spec, double* 
     if (e) return ISC_ERR_NOMEM;
   }
   if (A.cap_states < need) {
-    if (A.store) cudaFree(A.store);
+    dfree(h, A.store);
     A.store = nullptr;
     A.cap_states = 0;
     if (dalloc(h, &A.store, (size_t)need * SN)) return ISC_ERR_NOMEM;
@@ -1631,6 +1640,14 @@ int isc_get_stats(isc_handle* h, isc_stats* st) {
   if (!h || !st) return ISC_ERR_INVALID_ARG;
   resolve_timers(h);
   *st = h->stats;
+  return ISC_OK;
+}
+
+int isc_get_device_bytes(isc_handle* h, uint64_t* bytes) {
+  if (!h || !bytes) return ISC_ERR_INVALID_ARG;
+  uint64_t t = h->cpr.bytes;
+  for (const auto& kv : h->dev_sizes) t += kv.second;
+  *bytes = t;
   return ISC_OK;
 }
 

@@ -460,6 +460,7 @@ int setup_levels_t(Handle& h) {
   size_t total = 0;
   for (auto& L : lv) total += (size_t)L.n * 11;
   if (cudaMalloc(&W.pool, sizeof(T) * total) != cudaSuccess) return ISC_ERR_NOMEM;
+  W.bytes += sizeof(T) * total;
   T* q = static_cast<T*>(W.pool);
   for (auto& L : lv) {
     L.c = q;
@@ -474,6 +475,7 @@ int setup_levels_t(Handle& h) {
     q += L.n;
   }
   if (cudaMalloc(&W.d_levels, sizeof(MGLevel<T>) * lv.size()) != cudaSuccess) return ISC_ERR_NOMEM;
+  W.bytes += sizeof(MGLevel<T>) * lv.size();
   if (cudaMemcpy(W.d_levels, lv.data(), sizeof(MGLevel<T>) * lv.size(), cudaMemcpyHostToDevice) != cudaSuccess)
     return ISC_ERR_CUDA;
   W.nlev = (int)lv.size();
@@ -537,6 +539,7 @@ int cpr_setup_levels(Handle& h) {
   W.fp32 = fp32;
   if (cudaMalloc((void**)&W.col0, sizeof(double) * (size_t)h.nnzb * 8) != cudaSuccess) return ISC_ERR_NOMEM;
   if (cudaMalloc((void**)&W.r1, sizeof(double) * (size_t)h.n * 8) != cudaSuccess) return ISC_ERR_NOMEM;
+  W.bytes = sizeof(double) * ((size_t)h.nnzb * 8 + (size_t)h.n * 8);
   return fp32 ? setup_levels_t<float>(h) : setup_levels_t<double>(h);
 }
 

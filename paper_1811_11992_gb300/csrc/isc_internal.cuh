@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "isc.h"
@@ -166,6 +167,7 @@ struct CprWork {
   double* r1 = nullptr;               // right-hand side of the second stage, block-major 8N
   int nlev = 0, ngrid = 0;            // levels; levels done by grid-wide kernels
   bool fp32 = false;                  // precision of the level arrays
+  size_t bytes = 0;                   // device bytes of pool, d_levels, col0 and r1
 };
 
 // device status word bits
@@ -178,6 +180,7 @@ struct KTimer {
 struct Handle {
   // sizes
   int nx = 0, ny = 0, nz = 0, n = 0, nnzb = 0, nlevels = 0;
+  std::unordered_map<void*, size_t> dev_sizes;  // bytes of every live allocation made through dalloc
   Params P{};
   isc_options opt{};
   cudaStream_t stream = nullptr;

@@ -152,6 +152,7 @@ _SIGS = {
     "isc_get_stats": (C.c_int, [C.c_void_p, C.POINTER(isc_stats)]),
     "isc_get_ilu_diag": (C.c_int, [C.c_void_p, c_double_p]),
     "isc_reset_stats": (C.c_int, [C.c_void_p]),
+    "isc_get_device_bytes": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64)]),
     "isc_bsr_spmv_device": (C.c_int, [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                       C.c_int32, C.c_void_p]),
     "isc_bilu0_apply_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -458,6 +459,12 @@ class Simulator:
 
     def reset_stats(self):
         self._check(self.lib.isc_reset_stats(self.h))
+
+    def device_bytes(self):
+        """Bytes of device memory the handle holds now (isc_get_device_bytes)."""
+        b = C.c_uint64()
+        self._check(self.lib.isc_get_device_bytes(self.h, C.byref(b)))
+        return int(b.value)
 
     # -------------------------------------------------------- coupled wells
     def well_bhp(self):
