@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(128) k_adj_pre(Params P, const double* __restr
 // place, the warps of blocks with j < i do nothing.
 __global__ void __launch_bounds__(256) k_bsr_transpose(int n, const int32_t* __restrict__ rowptr,
                                                        const int32_t* __restrict__ col, double* __restrict__ J) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int warp = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);  // 32 nnzb may pass 2^32
   const int lane = threadIdx.x & 31;
   const int nnzb = rowptr[n];
   if (warp >= nnzb) return;
