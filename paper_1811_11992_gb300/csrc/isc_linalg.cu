@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(256) k_spmv(int n, const int32_t* __restrict__
   for (int b = b0; b < b1; ++b) {
     int j = __ldg(col + b);
     if (unit_diag && j == row) continue;
-    T2 v = __ldg(reinterpret_cast<const T2*>(val + (size_t)b * BB) + lane);
+    T2 v = __ldcs(reinterpret_cast<const T2*>(val + (size_t)b * BB) + lane);  // streamed once: evict first
     T2 xv = __ldg(reinterpret_cast<const T2*>(x + (size_t)j * 8 + c));
     acc = fma(v.x, xv.x, acc);
     acc = fma(v.y, xv.y, acc);

@@ -346,9 +346,14 @@ class Simulator:
         cc = None if coke is None else np.ascontiguousarray(coke, np.float64)
         self._check(self.lib.isc_set_state(self.h, _dp(u), None if cc is None else _dp(cc)))
 
-    def get_state(self):
-        u = np.empty((8, self.n))
-        coke = np.empty(self.n)
+    def get_state(self, u=None, coke=None):
+        """The state as (8, N) and (N,) float64 arrays: new ones, or the caller's
+        own (pinned host buffers, for one, which the copy reaches directly)."""
+        u = np.empty((8, self.n)) if u is None else u
+        coke = np.empty(self.n) if coke is None else coke
+        for a, shape in ((u, (8, self.n)), (coke, (self.n,))):
+            if a.dtype != np.float64 or a.shape != shape or not a.flags["C_CONTIGUOUS"]:
+                raise ValueError(f"get_state needs a C-contiguous float64 array of shape {shape}")
         self._check(self.lib.isc_get_state(self.h, _dp(u), _dp(coke)))
         return u, coke
 
