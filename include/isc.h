@@ -350,6 +350,38 @@ int isc_newton_step(struct isc_handle* h, double dt, isc_newton_info* info);
  * converged state becomes the accepted state. */
 int isc_timestep(struct isc_handle* h, double dt, isc_step_info* info);
 
+/* Result of isc_run. */
+typedef struct isc_run_info {
+  int32_t status;
+  int32_t steps;                /* accepted time steps */
+  int32_t cuts;                 /* step halvings after failed attempts */
+  int32_t newton_iterations;    /* Newton solves, failed attempts included */
+  int64_t krylov_iterations;    /* Krylov iterations, failed attempts included */
+  double t;                     /* time reached, from 0 at the call's start (s) */
+  double dt_next;               /* the controller's next step after the last one (s) */
+} isc_run_info;
+
+/* Time loop of the implicit-Euler scheme (Sec. 3.1) from the accepted state
+ * (isc_init_equilibrium or the last accepted step; the handle keeps no clock,
+ * so time runs from 0 to t_end here). Each step tries dt = min(dt, t_end - t)
+ * with isc_timestep; when that fails with ISC_ERR_NEWTON_NOCONV,
+ * ISC_ERR_KRYLOV_NOCONV, ISC_ERR_NONFINITE, ISC_ERR_COKE or
+ * ISC_ERR_SINGULAR_BLOCK the accepted state is restored and dt halves, at most
+ * max_cuts times in a row (then that status is returned, with info->t the time
+ * reached); any other error returns at once. After an accepted step of length
+ * dt with largest changes dT = max |T_new - T_old| and
+ * dS = max(|S_w,new - S_w,old|, |S_g,new - S_g,old|) over the cells, the next
+ * step is min(dt * clamp(min(dT_target / dT, dS_target / dS), 0.5, 2), dt_max)
+ * (dT and dS taken as at least 1e-12; the paper fixes no step controller:
+ * targets of 20 K and 0.2 are a common choice). Stops at t_end or after
+ * max_steps accepted steps. dt_history (may be NULL) receives the accepted
+ * step lengths, room for max_steps doubles. Allocates 3N + 2 doubles of
+ * device memory on its first call. Synchronous. ISC_ERR_INVALID_ARG for
+ * t_end < 0, dt0, dt_max or a target not positive, max_cuts < 0 or
+ * max_steps < 1; ISC_ERR_STATE before any accepted state. */
+int isc_run(struct isc_handle* h, double t_end, double dt0, double dt_max, double dT_target, double dS_target,
+            int32_t max_cuts, int32_t max_steps, double* dt_history, isc_run_info* info);
+
 /* Replace the assembled system by a caller's one (the method's linear step of
  * Sec. 3.2 on given data): val, the nnzb*64 BSR blocks on the handle's 7-point
  * pattern (the rowptr and col that isc_get_jacobian_bsr returns), and F, the

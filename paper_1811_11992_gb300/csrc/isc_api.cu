@@ -125,7 +125,7 @@ void free_all(isc_handle* h) {
                   h->slots, h->u, h->coke, h->u_n, h->coke_n, h->acc_n, h->props, h->fbuf, h->R, h->J, h->ntot, h->du,
                   h->rhs, h->dinv, h->uhat, h->J32, h->dinv32, h->uhat32, h->vec32, h->V32, h->Z32, h->w32, h->gm_in, h->scal_in, h->V, h->Z, h->w, h->tmp, h->partial, h->scal, h->dstatus, h->pipe, h->red_counter, h->gmres,
                   h->wx, h->wy, h->wz, h->cw, h->bhp, h->bhp_n, h->Dw, h->Bv, h->Cv, h->Fq, h->Dq, h->adj.store, h->adj.ubar, h->adj.cbar, h->adj.lam, h->adj.glnk, h->adj.grx,
-                  h->adj.scond, h->adj.kd, h->adj.loss_cell, h->adj.sums, h->adj.inj_first, h->adj.inj_count};
+                  h->adj.scond, h->adj.kd, h->adj.loss_cell, h->adj.sums, h->adj.inj_first, h->adj.inj_count, h->u_prev, h->run_max};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   h->dev_sizes.clear();
@@ -1490,6 +1490,77 @@ int isc_timestep(isc_handle* h, double dt, isc_step_info* info) {
   if (st == ISC_OK) st = set_err(h, ISC_ERR_NEWTON_NOCONV, "Newton did not converge within maxit_newton");
   info->status = st;
   return st;
+}
+
+namespace {
+// failures of a time step that a shorter step can cure (the state is restored)
+bool cut_cures(int st) {
+  return st == ISC_ERR_NEWTON_NOCONV || st == ISC_ERR_KRYLOV_NOCONV || st == ISC_ERR_NONFINITE ||
+         st == ISC_ERR_COKE || st == ISC_ERR_SINGULAR_BLOCK;
+}
+}  // namespace
+
+int isc_run(isc_handle* h, double t_end, double dt0, double dt_max, double dT_target, double dS_target,
+            int32_t max_cuts, int32_t max_steps, double* dt_history, isc_run_info* info) {
+  if (!h || !(t_end >= 0.0) || !isfinite(t_end) || !(dt0 > 0.0) || !isfinite(dt0) || !(dt_max > 0.0) ||
+      !(dT_target > 0.0) || !(dS_target > 0.0) || max_cuts < 0 || max_steps < 1)
+    return ISC_ERR_INVALID_ARG;
+  isc_run_info loc{};
+  if (!info) info = &loc;
+  memset(info, 0, sizeof(*info));
+  if (!h->have_acc) return set_err(h, ISC_ERR_STATE, "isc_begin_step (or isc_init_equilibrium) must come first");
+  const int n = h->n;
+  if (!h->u_prev) {
+    int e = dalloc(h, &h->u_prev, (size_t)3 * n);
+    e |= dalloc(h, &h->run_max, 2);
+    if (e) return ISC_ERR_NOMEM;
+  }
+  cudaStream_t s = h->stream;
+  double t = 0.0, dt = dt0;
+  while (t < t_end * (1.0 - 1e-12) && info->steps < max_steps) {
+    dt = std::min(dt, t_end - t);
+    // T, S_w, S_g of the accepted state (rows 5..7 of the SoA state, contiguous)
+    CUDA_TRY(h, cudaMemcpyAsync(h->u_prev, h->u_n + (size_t)5 * n, sizeof(double) * 3 * n,
+                                cudaMemcpyDeviceToDevice, s));
+    int st = ISC_OK;
+    for (int c = 0;; ++c) {
+      isc_step_info si{};
+      st = isc_timestep(h, dt, &si);  // on failure the accepted state is restored
+      info->newton_iterations += si.newton_iterations;
+      info->krylov_iterations += si.krylov_iterations;
+      if (st == ISC_OK || !cut_cures(st) || c == max_cuts) break;
+      info->cuts++;
+      dt *= 0.5;
+    }
+    if (st != ISC_OK) {
+      info->status = st;
+      info->t = t;
+      info->dt_next = dt;
+      if (cut_cures(st))
+        set_err(h, st, "time step at t = " + std::to_string(t) + " s failed after " + std::to_string(max_cuts) +
+                           " halvings: " + h->last_error);
+      return st;
+    }
+    // the controller: the largest changes of T and of S_w, S_g over the accepted step
+    CUDA_TRY(h, cudaMemsetAsync(h->run_max, 0, 2 * sizeof(unsigned long long), s));
+    launch_max_change(n, h->u + (size_t)5 * n, h->u_prev, h->run_max, s);
+    CUDA_TRY(h, cudaGetLastError());
+    unsigned long long mx[2];
+    CUDA_TRY(h, cudaMemcpyAsync(mx, h->run_max, sizeof(mx), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(h, cudaStreamSynchronize(s));
+    double dT, dS;
+    memcpy(&dT, &mx[0], sizeof(double));
+    memcpy(&dS, &mx[1], sizeof(double));
+    if (dt_history) dt_history[info->steps] = dt;
+    info->steps++;
+    t += dt;
+    const double f = std::min(dT_target / std::max(dT, 1e-12), dS_target / std::max(dS, 1e-12));
+    dt = std::min(dt * std::min(std::max(f, 0.5), 2.0), dt_max);
+  }
+  info->t = t;
+  info->dt_next = dt;
+  info->status = ISC_OK;
+  return ISC_OK;
 }
 
 int isc_set_heat_loss(isc_handle* h, double K_ob, double d, double T_ini, double rho, int32_t faces) {

@@ -253,6 +253,9 @@ struct Handle {
   double* gm_in = nullptr;                        // GMRES_STATE
   double* scal_in = nullptr;                      // 256: h0, h1, ||w||^2, y
   int inner_alloc = 0;
+  // step controller of isc_run (allocated on its first call)
+  double* u_prev = nullptr;                       // T, S_w, S_g of the accepted state before the step (3N)
+  unsigned long long* run_max = nullptr;          // max |dT| and max |dS| over the cells, as bit patterns
   double* h_ring = nullptr;                       // pinned: two slots of GMRES status (rel, 1/h, h)
   cudaEvent_t gm_ev[2] = {nullptr, nullptr};      // completion of those copies
   int restart_alloc = 0;
@@ -306,6 +309,7 @@ void launch_bsr_transpose(Handle& h, cudaStream_t s);
 void launch_adj_post(Handle& h, bool has_old, cudaStream_t s);
 void launch_row_sums(int nrows, int len, const double* x, double* out, cudaStream_t s);
 void launch_to_f32(size_t n, const double* x, float* y, cudaStream_t s);
+void launch_max_change(int n, const double* a, const double* b, unsigned long long* out, cudaStream_t s);
 // GMRES bookkeeping on the device (isc_linalg.cu); the buffer Handle::gmres holds
 // GMRES_STATE doubles
 constexpr int GMRES_STATE = 64 * 67 + 64 + 8;

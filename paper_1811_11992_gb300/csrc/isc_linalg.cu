@@ -903,6 +903,33 @@ __global__ void k_to_f32(size_t n, const double* __restrict__ x, float* __restri
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += stride) y[e] = (float)x[e];
 }
 
+// The step controller's state changes: max |a - b| over the first n entries
+// (temperature) into out[0] and over the next 2n (S_w, S_g) into out[1], as the
+// bit patterns of non-negative doubles (IEEE order is numeric order there, so
+// the integer maximum is the floating-point one and the result does not depend
+// on the order of the blocks). out must be zero on entry.
+__global__ void __launch_bounds__(256) k_max_change(int n, const double* __restrict__ a,
+                                                    const double* __restrict__ b, unsigned long long* out) {
+  unsigned long long mT = 0ull, mS = 0ull;
+  const size_t len = (size_t)3 * n, stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) {
+    const unsigned long long d = (unsigned long long)__double_as_longlong(fabs(a[e] - b[e]));
+    if (e < (size_t)n)
+      mT = max(mT, d);
+    else
+      mS = max(mS, d);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    mT = max(mT, (unsigned long long)__shfl_xor_sync(FULL, mT, o));
+    mS = max(mS, (unsigned long long)__shfl_xor_sync(FULL, mS, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(out, mT);
+    atomicMax(out + 1, mS);
+  }
+}
+
 int grid_for(size_t work, int tb) {
   size_t b = (work + tb - 1) / tb;
   if (b > 152 * 16) b = 152 * 16;
@@ -984,6 +1011,10 @@ void launch_scale_dev(Handle& h, const double* x, double* y, cudaStream_t s) {
 }
 
 const double* gmres_status(const Handle& h) { return h.gmres + GM_MAX * (GM_MAX + 3) + GM_MAX + 1; }
+
+void launch_max_change(int n, const double* a, const double* b, unsigned long long* out, cudaStream_t s) {
+  k_max_change<<<grid_for((size_t)3 * n, 256), 256, 0, s>>>(n, a, b, out);
+}
 
 void launch_to_f32(size_t n, const double* x, float* y, cudaStream_t s) {
   k_to_f32<<<grid_for(n, 256), 256, 0, s>>>(n, x, y);

@@ -96,6 +96,11 @@ class isc_step_info(C.Structure):
                 ("final_norm", C.c_double)]
 
 
+class isc_run_info(C.Structure):
+    _fields_ = [("status", C.c_int32), ("steps", C.c_int32), ("cuts", C.c_int32), ("newton_iterations", C.c_int32),
+                ("krylov_iterations", C.c_int64), ("t", C.c_double), ("dt_next", C.c_double)]
+
+
 class isc_stats(C.Structure):
     _fields_ = [("ms", C.c_double * 12), ("launches", C.c_int64 * 12), ("calls", C.c_int64 * 12)]
 
@@ -138,6 +143,8 @@ _SIGS = {
     "isc_update": (C.c_int, [C.c_void_p]),
     "isc_newton_step": (C.c_int, [C.c_void_p, C.c_double, C.POINTER(isc_newton_info)]),
     "isc_timestep": (C.c_int, [C.c_void_p, C.c_double, C.POINTER(isc_step_info)]),
+    "isc_run": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int32,
+                          C.c_int32, c_double_p, C.POINTER(isc_run_info)]),
     "isc_get_residual": (C.c_int, [C.c_void_p, c_double_p]),
     "isc_get_jacobian_bsr": (C.c_int, [C.c_void_p, c_int32_p, c_int32_p, c_double_p]),
     "isc_get_update": (C.c_int, [C.c_void_p, c_double_p]),
@@ -388,6 +395,17 @@ class Simulator:
         if check:
             self._check(st)
         return info
+
+    def run(self, t_end, dt0, dt_max, dT_target=20.0, dS_target=0.2, max_cuts=8, max_steps=100000, check=True):
+        """Time loop with step cuts and the step controller (isc_run) from the
+        accepted state over t_end seconds: (isc_run_info, accepted step lengths)."""
+        hist = np.zeros(int(max_steps))
+        info = isc_run_info()
+        st = self.lib.isc_run(self.h, float(t_end), float(dt0), float(dt_max), float(dT_target), float(dS_target),
+                              int(max_cuts), int(max_steps), _dp(hist), C.byref(info))
+        if check:
+            self._check(st)
+        return info, hist[:info.steps].copy()
 
     # ------------------------------------------------------------- exports
     def residual(self):
