@@ -321,7 +321,7 @@ __device__ __forceinline__ double face_flux(const Params& P, int r, int lo, int 
 // to here. The diagonal-block shares are the negatives of those two
 // off-diagonal rows (dF/du_i for i, -dF/du_j for j), which the gather reads
 // back from J.
-__global__ void __launch_bounds__(256) k_flux(Params P, const double* __restrict__ u, const double* __restrict__ props,
+__global__ void __launch_bounds__(256, 3) k_flux(Params P, const double* __restrict__ u, const double* __restrict__ props,
                                               const double* __restrict__ tx, const double* __restrict__ ty,
                                               const double* __restrict__ tz, const double* __restrict__ depth,
                                               const int32_t* __restrict__ rowptr, double* __restrict__ J,
