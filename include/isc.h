@@ -373,7 +373,7 @@ typedef struct isc_run_info {
  * dS = max(|S_w,new - S_w,old|, |S_g,new - S_g,old|) over the cells, the next
  * step is min(dt * clamp(min(dT_target / dT, dS_target / dS), 0.5, 2), dt_max)
  * (dT and dS taken as at least 1e-12; the paper fixes no step controller:
- * targets of 20 K and 0.2 are a common choice). Stops at t_end or after
+ * the oracle's loop uses 20 K and 0.2). Stops at t_end or after
  * max_steps accepted steps. dt_history (may be NULL) receives the accepted
  * step lengths, room for max_steps doubles. Allocates 3N + 2 doubles of
  * device memory on its first call. Synchronous. ISC_ERR_INVALID_ARG for
