@@ -17,8 +17,11 @@ from oracle import linalg, model
 pytestmark = pytest.mark.gpu
 
 # 4 x 80 x 64: 20,480 cells and 5,120 pencils, more than the 152 SMs x 32 resident warps
-# of the FP32 sweeps and the factorisation (4,864) and than the FP64 sweeps' 152 x 24
-GRIDS = [(4, 80, 64), (3, 90, 70)]
+# of the factorisation (4,864, one pencil per warp). The sweeps hold two pencils per warp on
+# grids this large: 2 x 160 x 100 (32,000 cells, 16,000 pencils, 8,000 pencil pairs) is
+# beyond both the FP64 sweeps' 152 x 24 resident warps (3,648) and the FP32 sweeps'
+# 152 x 32 (4,864), so that there warps take a second pair from the counter as well.
+GRIDS = [(4, 80, 64), (3, 90, 70), (2, 160, 100)]
 
 
 @pytest.fixture(scope="module")
@@ -122,6 +125,13 @@ def test_spmv_and_gmres_on_the_oracle_system(Simulator, system, orth):
     yo = linalg.bsr_to_scipy(system["rp"], system["col"], system["vd"]) @ x.reshape(-1)
     yo = yo.reshape(case.n, 8).T
     assert np.max(np.abs(y - yo)) <= 1e-13 * np.abs(yo).max()
+    if case.n > 25_000:
+        # the 2 x 160 x 100 grid is here for the sweeps' second round of pencil pairs; the
+        # system of a random state on it is beyond GMRES(30) with ILU(0) at this tolerance
+        # (the oracle's own GMRES stands at a relative residual of 8e-3 after 300
+        # iterations), so there only the SpMV is compared
+        g.close()
+        return
     info = g.solve()
     du = g.newton_update()
     # the update's residual in the oracle's own decoupled system (J du = -F)
