@@ -174,3 +174,38 @@ def test_binding_constants_match_the_header_enums():
     assert (inp.CTRL_BHP, inp.CTRL_WATER_RATE, inp.CTRL_OIL_RATE, inp.CTRL_LIQUID_RATE, inp.CTRL_GAS_RATE,
             inp.CTRL_TOTAL_RATE) == tuple(e["ISC_CTRL_" + k] for k in ("BHP", "WATER_RATE", "OIL_RATE",
                                                                        "LIQUID_RATE", "GAS_RATE", "TOTAL_RATE"))
+
+
+def test_every_handle_call_rejects_a_null_handle_without_a_gpu():
+    """Every entry point that takes the handle answers a NULL one before any
+    CUDA work: ISC_ERR_INVALID_ARG from the int-returning calls, nothing from
+    isc_destroy, 0 from the size and count queries and a message from
+    isc_last_error."""
+    import ctypes as C
+    from paper_1811_11992_gb300 import isc
+    lib = isc.load_library()
+    protos = _prototypes()
+    seen = 0
+    for name, (ret, params) in protos.items():
+        if not params or "isc_handle" not in params[0] or "**" in params[0]:
+            continue
+        fn = getattr(lib, name)
+        args = [None]
+        for p in params[1:]:
+            if "*" in p or "[" in p:
+                args.append(None)
+            elif "double" in p:
+                args.append(1.0)
+            else:
+                args.append(1)
+        res = fn(*args)
+        if name == "isc_destroy":
+            assert res is None
+        elif name == "isc_last_error":
+            assert res and b"null" in res
+        elif name in ("isc_num_cells", "isc_nnzb", "isc_num_coupled_wells"):
+            assert res == 0, name
+        else:
+            assert res == _enum_values()["ISC_ERR_INVALID_ARG"], name
+        seen += 1
+    assert seen >= 40
