@@ -233,6 +233,60 @@ def _fill(arr, values):
     C.memmove(C.addressof(arr), flat.ctypes.data, flat.nbytes)
 
 
+def create_args(case, keep):
+    """The isc_create arguments of a Case: (isc_grid, isc_rock, isc_fluid,
+    isc_reactions, isc_wells). The numpy arrays their pointers refer to are
+    appended to keep, which must outlive the isc_create call."""
+
+    def _k(a):
+        keep.append(a)
+        return a
+
+    g = isc_grid(case.nx, case.ny, case.nz, case.dx, case.dy, case.dz,
+                 _dp(_k(np.ascontiguousarray(case.depth, np.float64))))
+    r = case.rock
+    rock = isc_rock(_dp(_k(np.ascontiguousarray(case.phi_ref, np.float64))),
+                    _dp(_k(np.ascontiguousarray(case.perm, np.float64).reshape(-1))),
+                    r["cpor"], r["ctpor"], r["cptpor"], r["p_ref"], r["T_ref"], r["cv1"], r["cv2"], r["K_rock"])
+    fl = isc_fluid()
+    f = case.fluid
+    for k in ("M", "pc", "Tc", "rho_ref", "cp", "ct1", "ct2", "cpt", "cpg", "hvr", "ev", "avg", "bvg",
+              "avisc", "bvisc", "kv", "K_phase"):
+        _fill(getattr(fl, k), f[k])
+    for k in ("p_ref", "T_ref", "coke_rho", "coke_cp", "coke_K", "coke_M", "Swc", "Sorw", "Sgc", "Sorg",
+              "per_eps", "gravity"):
+        setattr(fl, k, float(f[k]))
+    rx = isc_reactions()
+    x = case.reactions
+    rx.nr = int(x["nr"])
+    for i in range(rx.nr):
+        rx.kind[i] = int(x["kind"][i])
+        rx.comp[i] = int(x["comp"][i])
+        rx.A[i] = float(x["A"][i])
+        rx.Ea[i] = float(x["Ea"][i])
+        rx.dH[i] = float(x["dH"][i])
+        for c in range(7):
+            rx.stoich[i][c] = float(x["stoich"][i][c])
+    rx.coke_max = float(x["coke_max"])
+    wl = (isc_well * max(1, len(case.wells)))()
+    for i, w in enumerate(case.wells):
+        cells = _k(np.ascontiguousarray(w.cells, np.int32))
+        WI = _k(np.ascontiguousarray(w.WI, np.float64))
+        wl[i].kind = int(w.kind)
+        wl[i].n_perf = len(cells)
+        wl[i].cells = _ip(cells)
+        wl[i].WI = _dp(WI)
+        wl[i].target = float(w.target)
+        _fill(wl[i].inj_y, w.inj_y)
+        wl[i].inj_T = float(w.inj_T)
+        wl[i].inj_phase = int(getattr(w, "inj_phase", 2))
+        wl[i].control = int(getattr(w, "control", 0))
+        wl[i].ref_depth = float(getattr(w, "ref_depth", 0.0))
+        wl[i].bhp_init = float(getattr(w, "bhp_init", 0.0))
+    wells = isc_wells(len(case.wells), _k(wl))
+    return g, rock, fl, rx, wells
+
+
 class Simulator:
     """A libisc handle built from an ``isc_inputs.Case``."""
 
@@ -243,48 +297,7 @@ class Simulator:
         n = case.n
         self.n = n
         self._keep = []
-        g = isc_grid(case.nx, case.ny, case.nz, case.dx, case.dy, case.dz,
-                     _dp(self._k(np.ascontiguousarray(case.depth, np.float64))))
-        r = case.rock
-        rock = isc_rock(_dp(self._k(np.ascontiguousarray(case.phi_ref, np.float64))),
-                        _dp(self._k(np.ascontiguousarray(case.perm, np.float64).reshape(-1))),
-                        r["cpor"], r["ctpor"], r["cptpor"], r["p_ref"], r["T_ref"], r["cv1"], r["cv2"], r["K_rock"])
-        fl = isc_fluid()
-        f = case.fluid
-        for k in ("M", "pc", "Tc", "rho_ref", "cp", "ct1", "ct2", "cpt", "cpg", "hvr", "ev", "avg", "bvg",
-                  "avisc", "bvisc", "kv", "K_phase"):
-            _fill(getattr(fl, k), f[k])
-        for k in ("p_ref", "T_ref", "coke_rho", "coke_cp", "coke_K", "coke_M", "Swc", "Sorw", "Sgc", "Sorg",
-                  "per_eps", "gravity"):
-            setattr(fl, k, float(f[k]))
-        rx = isc_reactions()
-        x = case.reactions
-        rx.nr = int(x["nr"])
-        for i in range(rx.nr):
-            rx.kind[i] = int(x["kind"][i])
-            rx.comp[i] = int(x["comp"][i])
-            rx.A[i] = float(x["A"][i])
-            rx.Ea[i] = float(x["Ea"][i])
-            rx.dH[i] = float(x["dH"][i])
-            for c in range(7):
-                rx.stoich[i][c] = float(x["stoich"][i][c])
-        rx.coke_max = float(x["coke_max"])
-        wl = (isc_well * max(1, len(case.wells)))()
-        for i, w in enumerate(case.wells):
-            cells = self._k(np.ascontiguousarray(w.cells, np.int32))
-            WI = self._k(np.ascontiguousarray(w.WI, np.float64))
-            wl[i].kind = int(w.kind)
-            wl[i].n_perf = len(cells)
-            wl[i].cells = _ip(cells)
-            wl[i].WI = _dp(WI)
-            wl[i].target = float(w.target)
-            _fill(wl[i].inj_y, w.inj_y)
-            wl[i].inj_T = float(w.inj_T)
-            wl[i].inj_phase = int(getattr(w, "inj_phase", 2))
-            wl[i].control = int(getattr(w, "control", 0))
-            wl[i].ref_depth = float(getattr(w, "ref_depth", 0.0))
-            wl[i].bhp_init = float(getattr(w, "bhp_init", 0.0))
-        wells = isc_wells(len(case.wells), wl)
+        g, rock, fl, rx, wells = create_args(case, self._keep)
         if options is None:
             options = default_options(**opt_kw)
         self.options = options
