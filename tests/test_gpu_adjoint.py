@@ -146,7 +146,7 @@ def test_autograd_function_returns_the_adjoint_gradient(box):
     assert L.grad_fn.info_backward["krylov_iterations_adjoint"] > 0
     g.init_equilibrium()
     L2, gk, ge, ga, _ = g.adjoint(BOX_DTS, checkpoint_every=2, tol_adjoint=1e-12)
-    assert float(L) == L2
+    assert L.item() == L2
     np.testing.assert_array_equal(lk.grad.numpy(), 2.0 * gk)
     np.testing.assert_array_equal(Ea.grad.numpy(), 2.0 * ge)
     np.testing.assert_array_equal(lnA.grad.numpy(), 2.0 * ga)
