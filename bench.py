@@ -204,7 +204,17 @@ MEASURED_TRAFFIC = {
                                        "profiles/k_sweep1_fwd_bwd_field_60x60x20.md"),
     ("prec_apply", "mixed", "single"): (157.89e6 / 72000, "field 60x60x20",
                                         "profiles/k_sweep1_fwd_bwd_field_60x60x20.md"),
+    # the SpMV has one layout (its figure holds for either sweep layout)
+    ("spmv", "fp64", None): ((222.2e6 + 5.7e6) / 72000, "field 60x60x20", "profiles/k_spmv8_field_60x60x20.md"),
+    ("spmv32", "mixed", None): ((112.09e6 + 3.26e6) / 72000, "field 60x60x20",
+                                "profiles/k_spmv_f32_field_60x60x20.md"),
 }
+
+
+def measured_traffic(cls, precision, case):
+    """(bytes per cell, workload, source) of the class's ncu DRAM traffic, or None."""
+    p = "fp64" if precision == "fp64" else "mixed"
+    return MEASURED_TRAFFIC.get((cls, p, sweep_layout(case, precision))) or MEASURED_TRAFFIC.get((cls, p, None))
 # the largest ny * nz that runs the one-pencil-per-warp sweeps (SWEEP1_MAX_PENCILS64 /
 # SWEEP1_MAX_PENCILS32 of the library's ILU(0) sweeps)
 SWEEP1_MAX_PENCILS = {"fp64": 3000, "mixed": 3600}
@@ -350,7 +360,7 @@ def roofline(dom, stats, case, nnzb, fp64_gflops, precision="fp64", its=None, or
     else:
         out.update(bound="hbm", achieved=ach_gbs, peak=hbm, unit="GB/s", frac=ach_gbs / hbm,
                    peak_source="MEASURED_PEAKS.json hbm_gbs")
-    m = MEASURED_TRAFFIC.get((dom, "fp64" if not fp32 else "mixed", sweep_layout(case, precision)))
+    m = measured_traffic(dom, precision, case)
     out["traffic"] = m[0] * n if m else None
     if m:
         out["traffic_source"] = f"{m[2]} (captured on {m[1]}, scaled per cell to {case.n} cells)"
@@ -365,9 +375,11 @@ def spmv32_roofline(stats, case, nnzb):
     ms = s["ms"] / calls
     byts = spmv_bytes(case.n, nnzb, fp32=True)
     ach = byts / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+    m = measured_traffic("spmv32", "mixed", case)
     return {"kernel": "k_spmv<float>", "bound": "hbm", "calls": calls, "ms_per_call": ms, "bytes_per_call": byts,
             "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-            "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs", "traffic": m[0] * case.n,
+            "traffic_source": f"{m[2]} (captured on {m[1]}, scaled per cell to {case.n} cells)"}
 
 
 class Bench:

@@ -82,7 +82,13 @@ def test_traffic_is_scaled_per_cell(bench):
     assert abs(r["traffic"] / r["bytes_per_call"] - 1) < 0.05
     r32 = bench.roofline("prec_apply", st, case, nnzb, 1200.0, "mixed")
     assert abs(r32["traffic"] / r32["bytes_per_call"] - 1) < 0.05
-    assert bench.roofline("spmv", {"spmv": {"calls": 1, "ms": 1.0, "launches": 1}}, case, nnzb, 1200.0,
+    # the SpMVs' figures (one layout) within a few per cent of their algorithmic bytes too
+    rs = bench.roofline("spmv", {"spmv": {"calls": 1, "ms": 1.0, "launches": 1}}, case, nnzb, 1200.0, "fp64")
+    assert abs(rs["traffic"] / rs["bytes_per_call"] - 1) < 0.05
+    r32s = bench.spmv32_roofline({"spmv32": {"calls": 1, "ms": 0.6, "launches": 1}}, case, nnzb)
+    assert abs(r32s["traffic"] / r32s["bytes_per_call"] - 1) < 0.05
+    # a class without a capture has no traffic figure
+    assert bench.roofline("gj", {"gj": {"calls": 1, "ms": 25.0, "launches": 1}}, case, nnzb, 1200.0,
                           "fp64")["traffic"] is None
 
 
