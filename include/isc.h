@@ -500,6 +500,19 @@ int isc_measure_fma_rates(double* fp64_gflops, double* fp32_gflops);
  * stream; synchronous. */
 int isc_check_bounded_wait(void);
 
+/* Self-check of the index arithmetic of the ILU(0) sweeps and factorisation
+ * (a diagnostic, not a hot-path call): those kernels compute the start of
+ * each cell's BSR row of the 7-point pattern (columns sorted, one block per
+ * existing neighbour and the diagonal) in closed form instead of loading it.
+ * Given the nx x ny x nz grid and that pattern's rowptr (host, N + 1 int32,
+ * copied), a kernel compares both closed forms with it for every cell, and the
+ * total block count with rowptr[N]; *mismatches receives the number of cells
+ * that differ and *first_cell the smallest of them (-1 if none). Synchronous,
+ * allocates N + 1 ints of device memory for the call. ISC_ERR_INVALID_ARG for
+ * an empty grid, a null pointer or a grid beyond the handle's limits. */
+int isc_check_row_starts(int32_t nx, int32_t ny, int32_t nz, const int32_t* rowptr, int64_t* mismatches,
+                         int32_t* first_cell);
+
 /* ------------------------------------------------------------ sensitivities */
 
 /* Parameters theta of the sensitivity analysis. The paper computes no

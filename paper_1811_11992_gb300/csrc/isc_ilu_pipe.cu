@@ -1127,7 +1127,73 @@ int noalloc_scratch(double** out) {
 
 }  // namespace
 
+namespace {
+
+// Both closed forms of the BSR row starts that the sweeps and the factorisation
+// compute instead of loading rowptr (rowptr_of per cell, row_start along a
+// pencil) against rowptr itself: one thread per cell, mismatches counted, the
+// first mismatching cell kept (atomicMin).
+__global__ void k_check_row_starts(int nx, int ny, int nz, const int32_t* __restrict__ rowptr,
+                                   unsigned long long* __restrict__ count, int* __restrict__ first) {
+  const long long n = (long long)nx * ny * nz;
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c <= n; c += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)c;
+    bool ok;
+    if (c == n) {
+      ok = 7 * i - (2 * ny * nz + 2 * nx * nz + 2 * nx * ny) == rowptr[n];  // the total block count
+    } else {
+      const int x = i % nx, j = (i / nx) % ny, k = i / (nx * ny);
+      const Pen P = make_pen(nx, ny, nz, j, k, i - x);
+      ok = rowptr_of(nx, ny, nz, i) == rowptr[i] && row_start(P, x) == rowptr[i];
+    }
+    if (!ok) {
+      atomicAdd(count, 1ull);
+      atomicMin(first, i);
+    }
+  }
+}
+
+}  // namespace
+
 }  // namespace isc
+
+extern "C" int isc_check_row_starts(int32_t nx, int32_t ny, int32_t nz, const int32_t* rowptr, int64_t* mismatches,
+                                    int32_t* first_cell) {
+  using namespace isc;
+  if (nx < 1 || ny < 1 || nz < 1 || !rowptr || !mismatches || !first_cell) return ISC_ERR_INVALID_ARG;
+  const long long n = (long long)nx * ny * nz;
+  if (n * 7 > (long long)INT32_MAX || n > (1LL << 28)) return ISC_ERR_INVALID_ARG;
+  int32_t* d_rp = nullptr;
+  unsigned long long* d_count = nullptr;
+  int* d_first = nullptr;
+  int st = ISC_OK;
+  if (cudaMalloc(&d_rp, sizeof(int32_t) * (size_t)(n + 1)) != cudaSuccess ||
+      cudaMalloc(&d_count, sizeof(unsigned long long)) != cudaSuccess || cudaMalloc(&d_first, sizeof(int)) != cudaSuccess)
+    st = ISC_ERR_NOMEM;
+  if (st == ISC_OK) {
+    const int big = INT32_MAX;
+    bool ok = cudaMemcpy(d_rp, rowptr, sizeof(int32_t) * (size_t)(n + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemset(d_count, 0, sizeof(unsigned long long)) == cudaSuccess &&
+              cudaMemcpy(d_first, &big, sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
+    if (ok) {
+      k_check_row_starts<<<152 * 8, 256>>>(nx, ny, nz, d_rp, d_count, d_first);
+      ok = cudaGetLastError() == cudaSuccess;
+    }
+    unsigned long long cnt = 0;
+    int first = big;
+    if (!ok || cudaMemcpy(&cnt, d_count, sizeof(cnt), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(&first, d_first, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      st = ISC_ERR_CUDA;
+    } else {
+      *mismatches = (int64_t)cnt;
+      *first_cell = cnt ? first : -1;
+    }
+  }
+  cudaFree(d_rp);
+  cudaFree(d_count);
+  cudaFree(d_first);
+  return st;
+}
 
 // Failure-detection self-test: a forward sweep on a 4x4x1 grid whose pencil
 // counter starts at 1, so pencil 0 is never processed and pencil 1's wait on it

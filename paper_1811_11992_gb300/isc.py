@@ -167,6 +167,8 @@ _SIGS = {
     "isc_set_parameters": (C.c_int, [C.c_void_p, c_double_p, c_double_p, c_double_p]),
     "isc_check_reciprocal": (C.c_int, [C.c_int32, c_double_p, c_double_p, c_double_p]),
     "isc_check_bounded_wait": (C.c_int, []),
+    "isc_check_row_starts": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, c_int32_p, C.POINTER(C.c_int64),
+                                       C.POINTER(C.c_int32)]),
     "isc_measure_fma_rates": (C.c_int, [c_double_p, c_double_p]),
     "isc_num_coupled_wells": (C.c_int32, [C.c_void_p]),
     "isc_set_well_bhp": (C.c_int, [C.c_void_p, c_double_p]),
@@ -643,6 +645,17 @@ def check_reciprocal(x):
 def check_bounded_wait():
     """Status of the bounded-wait self-test (ISC_ERR_TIMEOUT expected)."""
     return load_library().isc_check_bounded_wait()
+
+
+def check_row_starts(nx, ny, nz, rowptr):
+    """(mismatching cells, first of them or -1) of the sweeps' closed-form BSR
+    row starts against rowptr (isc_check_row_starts)."""
+    rp = np.ascontiguousarray(rowptr, np.int32)
+    cnt, first = C.c_int64(), C.c_int32()
+    st = load_library().isc_check_row_starts(int(nx), int(ny), int(nz), _ip(rp), C.byref(cnt), C.byref(first))
+    if st != ISC_OK:
+        raise IscError(st, "isc_check_row_starts failed")
+    return int(cnt.value), int(first.value)
 
 
 # the binding uses the C-ABI names
