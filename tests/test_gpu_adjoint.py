@@ -198,7 +198,7 @@ def test_adjoint_workload_central_differences():
     params = [torch.tensor(v, requires_grad=True) for v in (lk0, Ea0, lnA0)]
     Lt = oil_production(g, dts, *params, checkpoint_every=5, tol_adjoint=1e-10)
     gk, ge, ga = (t.numpy() for t in torch.autograd.grad(Lt, params))
-    L = float(Lt)
+    L = Lt.item()
     assert L > 0 and Lt.grad_fn.info_backward["recomputed_steps"] == 15
     rng = np.random.default_rng(2024)
     h = 1e-6
