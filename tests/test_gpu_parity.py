@@ -223,10 +223,14 @@ def _degenerate(name):
         case = inp.small_box(1, 1, 6)
         case.wells = case.wells[:1]           # both wells of the box would share the column
         return case
+    if name == "nowells":
+        case = inp.small_box(3, 3, 2)
+        case.wells = []                       # a closed box: no source term anywhere
+        return case
     raise ValueError(name)
 
 
-@pytest.mark.parametrize("name", ["single", "pair", "nx1", "flat", "ny1", "column"])
+@pytest.mark.parametrize("name", ["single", "pair", "nx1", "flat", "ny1", "column", "nowells"])
 def test_degenerate_grids(Simulator, name):
     case = _degenerate(name)
     a = inp.random_state(case, 31)
