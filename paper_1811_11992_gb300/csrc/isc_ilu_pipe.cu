@@ -1025,7 +1025,8 @@ int sweep_blocks(K kernel, size_t smem, int tasks) {
 // (latency-bound wavefront); larger grids the pencil pairs (FP64-pipe- or
 // HBM-bound). Measured per apply, one pencil / pairs: 1,200 pencils (60x60x20)
 // 0.331 / 0.393 ms FP64, 0.230 / 0.249 ms FP32; 3,000 (100x100x30) 0.739 /
-// 0.759 and 0.423 / 0.441; 3,600 (120x120x30) 0.990 / 0.900 and 0.512 / 0.532.
+// 0.759 and 0.423 / 0.441; 3,600 (120x120x30) 0.990 / 0.900 and 0.512 / 0.532;
+// 10,000 (200x200x50) FP32 1.53 / 1.16.
 constexpr int SWEEP1_MAX_PENCILS64 = 3000;
 constexpr int SWEEP1_MAX_PENCILS32 = 3600;
 template <typename TM>
