@@ -13,7 +13,6 @@ import pytest
 
 import isc_inputs as inp
 
-pytestmark = pytest.mark.gpu
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -54,7 +53,11 @@ def _c_struct(var, obj, lens):
     return decl, body
 
 
-def test_c_program_runs_the_time_loop_like_the_binding(tmp_path):
+T_END, DT0, DT_MAX = 600.0, 5.0, 150.0
+
+
+def _program(tmp_path):
+    """Generate and compile the C99 program; (executable, case)."""
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         pytest.skip("no C compiler")
@@ -76,7 +79,7 @@ def test_c_program_runs_the_time_loop_like_the_binding(tmp_path):
         body += b
     ini = case.init
     ign = np.asarray(case.ignited, np.int32)
-    t_end, dt0, dt_max = 600.0, 5.0, 150.0
+    t_end, dt0, dt_max = T_END, DT0, DT_MAX
     src = ["#include <stdio.h>", "#include <string.h>", '#include "isc.h"', ""] + decl + [
         "int main(void) {",
         "  isc_grid g; isc_rock rock; isc_fluid fl; isc_reactions rx; isc_wells wells;",
@@ -111,6 +114,22 @@ def test_c_program_runs_the_time_loop_like_the_binding(tmp_path):
     exe = tmp_path / "tube"
     subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(tmp_path / "tube.c"),
                     "-L", libdir, "-lisc", f"-Wl,-rpath,{libdir}", "-o", str(exe)], check=True)
+    return exe, case
+
+
+def test_c_program_compiles_against_the_header(tmp_path):
+    """The generated program (every input structure filled field by field)
+    compiles with -Wall -Werror and links against libisc.so, without a GPU."""
+    exe, _ = _program(tmp_path)
+    assert exe.exists()
+
+
+@pytest.mark.gpu
+def test_c_program_runs_the_time_loop_like_the_binding(tmp_path):
+    from paper_1811_11992_gb300 import isc
+    exe, case = _program(tmp_path)
+    n = case.n
+    t_end, dt0, dt_max = T_END, DT0, DT_MAX
     out = subprocess.run([str(exe)], check=True, capture_output=True, text=True, timeout=600).stdout.split()
     steps, cuts, newton = int(out[0]), int(out[1]), int(out[2])
     t = float(out[3])
